@@ -1,0 +1,354 @@
+/*
+ * part_oracle.c -- plain FP64 CPU oracle for the particle advance.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg; never by the product path.  Shares no code
+ * with the CUDA library.  Build: gcc -O2 -ffp-contract=off -fopenmp -shared.
+ *
+ * Every routine states the definition it writes out.  Loops over particles in
+ * the per-particle routines are independent (OpenMP may split them); sums that
+ * combine particles (the deposit) run strictly in particle index order.
+ *
+ * Parity unpinned: the code-unit synchrotron coefficient c_r = c0 (|B|^2/2 +
+ * U_rad) (the paper prints c_r only in cgs units, Eq. rad_losses).
+ */
+#include "part_oracle.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- shape functions (textbook; the paper only says LPs "sample" fluid
+ * quantities, Sec. 2).  xi = (cell centre - particle) in cell units.        */
+double or_shape(int shape, double xi) {
+  double a = fabs(xi);
+  if (shape == OR_CIC) {              /* hat function, support |xi| < 1     */
+    return a < 1.0 ? 1.0 - a : 0.0;
+  }
+  /* TSC: quadratic B-spline, support |xi| < 3/2 */
+  if (a <= 0.5) return 0.75 - a * a;
+  if (a < 1.5) { double b = 1.5 - a; return 0.5 * b * b; }
+  return 0.0;
+}
+
+/* Cell index j = floor((x - xmin) / dx) with 1/dx formed once; the upper edge
+ * tie (rounding to j == n) goes to n-1.  delta = (s - j) - 1/2.             */
+void or_cell_coord(const or_grid* g, const double* x, int* j, double* delta) {
+  for (int a = 0; a < 3; ++a) {
+    if (a >= g->dim) { j[a] = 0; delta[a] = 0.0; continue; }
+    double inv = 1.0 / g->dx[a];
+    double s = (x[a] - g->xmin[a]) * inv;
+    double f = floor(s);
+    int jj = (int)f;
+    if (jj >= g->n[a]) jj = g->n[a] - 1;
+    if (jj < 0) jj = 0;
+    j[a] = jj;
+    delta[a] = (s - (double)jj) - 0.5;
+  }
+}
+
+/* Periodic wrap by one domain length L = n dx into [xmin, xmin + L). */
+double or_wrap(const or_grid* g, int axis, double x) {
+  double L = (double)g->n[axis] * g->dx[axis];
+  double xmax = g->xmin[axis] + L;
+  if (x < g->xmin[axis]) x = x + L;
+  else if (x >= xmax) x = x - L;
+  return x;
+}
+
+static int64_t cell_linear(const or_grid* g, int jx, int jy, int jz) {
+  return ((int64_t)jz * g->n[1] + jy) * g->n[0] + jx;
+}
+
+static int pmod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+
+/* F(x_p) = sum_k W(k_x - d_x) W(k_y - d_y) W(k_z - d_z) f[j + k], periodic,
+ * k in {-1,0,1}^dim, cell-centred fields [comp][z][y][x].                   */
+void or_gather(const or_grid* g, int shape, const double* fields, int ncomp,
+               const double* x, double* out) {
+  int j[3]; double d[3];
+  or_cell_coord(g, x, j, d);
+  int64_t G = (int64_t)g->n[0] * g->n[1] * g->n[2];
+  for (int c = 0; c < ncomp; ++c) out[c] = 0.0;
+  int kz0 = g->dim == 3 ? -1 : 0, kz1 = g->dim == 3 ? 1 : 0;
+  for (int kz = kz0; kz <= kz1; ++kz) {
+    double wz = g->dim == 3 ? or_shape(shape, kz - d[2]) : 1.0;
+    for (int ky = -1; ky <= 1; ++ky) {
+      double wy = or_shape(shape, ky - d[1]);
+      for (int kx = -1; kx <= 1; ++kx) {
+        double wx = or_shape(shape, kx - d[0]);
+        double w = (wz * wy) * wx;
+        int64_t cell = cell_linear(g, pmod(j[0] + kx, g->n[0]), pmod(j[1] + ky, g->n[1]),
+                                   pmod(j[2] + kz, g->n[2]));
+        for (int c = 0; c < ncomp; ++c) out[c] += w * fields[(int64_t)c * G + cell];
+      }
+    }
+  }
+}
+
+/* Relativistic Boris (Boris 1970; Birdsall & Langdon Sec. 15-4), c = 1:
+ *   h = (q/m) dt/2;  u- = u + h E;  g- = sqrt(1 + |u-|^2)
+ *   t = h B / g-;  s = 2 t / (1 + |t|^2)
+ *   u' = u- + u- x t;  u+ = u- + u' x s;  u_new = u+ + h E                   */
+void or_boris_kick(double* u, const double* E, const double* B, double qm, double dt) {
+  double h = qm * dt * 0.5;
+  double um[3], t[3], s[3], up[3], upl[3];
+  for (int a = 0; a < 3; ++a) um[a] = u[a] + h * E[a];
+  double gm = sqrt(1.0 + (um[0] * um[0] + um[1] * um[1] + um[2] * um[2]));
+  for (int a = 0; a < 3; ++a) t[a] = (h / gm) * B[a];
+  double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  for (int a = 0; a < 3; ++a) s[a] = 2.0 * t[a] / (1.0 + t2);
+  upl[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
+  upl[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
+  upl[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
+  up[0] = um[0] + (upl[1] * s[2] - upl[2] * s[1]);
+  up[1] = um[1] + (upl[2] * s[0] - upl[0] * s[2]);
+  up[2] = um[2] + (upl[0] * s[1] - upl[1] * s[0]);
+  for (int a = 0; a < 3; ++a) u[a] = up[a] + h * E[a];
+}
+
+/* One step: fields sampled at x^n (E = comps 0-2, B = comps 3-5), Boris kick,
+ * drift x^{n+1} = x^n + dt u^{n+1}/gamma^{n+1} on the dim spatial axes, wrap.
+ * The force deposited later is F_p = w_p (u^{n+1} - u^n)/dt (m = 1).        */
+void or_boris_step(const or_grid* g, int shape, const double* fields6, int64_t n,
+                   double* x, double* u, const double* w, double qm, double dt,
+                   double* F_out, double* x_old_out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < n; ++p) {
+    double xp[3], up[3], f[6], u0[3];
+    for (int a = 0; a < 3; ++a) { xp[a] = x[a * n + p]; up[a] = u[a * n + p]; u0[a] = up[a]; }
+    if (x_old_out) for (int a = 0; a < 3; ++a) x_old_out[a * n + p] = xp[a];
+    or_gather(g, shape, fields6, 6, xp, f);
+    or_boris_kick(up, f, f + 3, qm, dt);
+    double gam = sqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+    for (int a = 0; a < g->dim; ++a) xp[a] = or_wrap(g, a, xp[a] + dt * (up[a] / gam));
+    for (int a = 0; a < 3; ++a) { x[a * n + p] = xp[a]; u[a * n + p] = up[a]; }
+    if (F_out) {
+      double wp = w ? w[p] : 1.0;
+      for (int a = 0; a < 3; ++a) F_out[a * n + p] = wp * ((up[a] - u0[a]) / dt);
+    }
+  }
+}
+
+/* F_g = sum_p W(x_g - x_p) F_p with the gather's shape and stencil; particle
+ * index order, then the stencil order of or_gather.                         */
+void or_deposit(const or_grid* g, int shape, int64_t n, const double* x,
+                const double* F, double* out) {
+  int64_t G = (int64_t)g->n[0] * g->n[1] * g->n[2];
+  memset(out, 0, sizeof(double) * 3 * G);
+  int kz0 = g->dim == 3 ? -1 : 0, kz1 = g->dim == 3 ? 1 : 0;
+  for (int64_t p = 0; p < n; ++p) {
+    double xp[3] = {x[p], x[n + p], x[2 * n + p]};
+    int j[3]; double d[3];
+    or_cell_coord(g, xp, j, d);
+    for (int kz = kz0; kz <= kz1; ++kz) {
+      double wz = g->dim == 3 ? or_shape(shape, kz - d[2]) : 1.0;
+      for (int ky = -1; ky <= 1; ++ky) {
+        double wy = or_shape(shape, ky - d[1]);
+        for (int kx = -1; kx <= 1; ++kx) {
+          double wx = or_shape(shape, kx - d[0]);
+          double w = (wz * wy) * wx;
+          int64_t cell = cell_linear(g, pmod(j[0] + kx, g->n[0]), pmod(j[1] + ky, g->n[1]),
+                                     pmod(j[2] + kz, g->n[2]));
+          for (int c = 0; c < 3; ++c) out[(int64_t)c * G + cell] += w * F[(int64_t)c * n + p];
+        }
+      }
+    }
+  }
+}
+
+void or_deposit_cell(const or_grid* g, int shape, int64_t n, const double* x,
+                     const double* F, int64_t cell, double* out3) {
+  out3[0] = out3[1] = out3[2] = 0.0;
+  int kz0 = g->dim == 3 ? -1 : 0, kz1 = g->dim == 3 ? 1 : 0;
+  for (int64_t p = 0; p < n; ++p) {
+    double xp[3] = {x[p], x[n + p], x[2 * n + p]};
+    int j[3]; double d[3];
+    or_cell_coord(g, xp, j, d);
+    for (int kz = kz0; kz <= kz1; ++kz) {
+      for (int ky = -1; ky <= 1; ++ky) {
+        for (int kx = -1; kx <= 1; ++kx) {
+          int64_t c0 = cell_linear(g, pmod(j[0] + kx, g->n[0]), pmod(j[1] + ky, g->n[1]),
+                                   pmod(j[2] + kz, g->n[2]));
+          if (c0 != cell) continue;
+          double wz = g->dim == 3 ? or_shape(shape, kz - d[2]) : 1.0;
+          double w = (wz * or_shape(shape, ky - d[1])) * or_shape(shape, kx - d[0]);
+          for (int c = 0; c < 3; ++c) out3[c] += w * F[(int64_t)c * n + p];
+        }
+      }
+    }
+  }
+}
+
+/* Cell key: the grid is cut into bricks of b[0] x b[1] x b[2] cells (the last
+ * brick on an axis may be partial); key = brick index * brick volume + cell
+ * index inside the brick, both x-fastest.  A bijection from cells to keys.  */
+uint32_t or_cell_key(const or_grid* g, const int* b, const int* j) {
+  int nb0 = (g->n[0] + b[0] - 1) / b[0], nb1 = (g->n[1] + b[1] - 1) / b[1];
+  int64_t V = (int64_t)b[0] * b[1] * b[2];
+  int64_t brick = ((int64_t)(j[2] / b[2]) * nb1 + j[1] / b[1]) * nb0 + j[0] / b[0];
+  int64_t local = ((int64_t)(j[2] % b[2]) * b[1] + j[1] % b[1]) * b[0] + j[0] % b[0];
+  return (uint32_t)(brick * V + local);
+}
+
+int64_t or_key_count(const or_grid* g, const int* b) {
+  int64_t nb = 1;
+  for (int a = 0; a < 3; ++a) nb *= (g->n[a] + b[a] - 1) / b[a];
+  return nb * b[0] * b[1] * b[2];
+}
+
+void or_keys(const or_grid* g, const int* b, int64_t n, const double* x, uint32_t* keys) {
+  for (int64_t p = 0; p < n; ++p) {
+    double xp[3] = {x[p], x[n + p], x[2 * n + p]};
+    int j[3]; double d[3];
+    or_cell_coord(g, xp, j, d);
+    keys[p] = or_cell_key(g, b, j);
+  }
+}
+
+typedef struct { uint32_t key; uint32_t idx; } kv_t;
+static int kv_cmp(const void* a, const void* b) {
+  const kv_t* x = (const kv_t*)a; const kv_t* y = (const kv_t*)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+/* Stable sort by key: ordering (key, original index) pairs lexicographically
+ * keeps equal keys in their current order.                                  */
+void or_stable_sort(int64_t n, const uint32_t* keys, uint32_t* perm) {
+  kv_t* t = (kv_t*)malloc(sizeof(kv_t) * (n > 0 ? n : 1));
+  for (int64_t p = 0; p < n; ++p) { t[p].key = keys[p]; t[p].idx = (uint32_t)p; }
+  qsort(t, (size_t)n, sizeof(kv_t), kv_cmp);
+  for (int64_t p = 0; p < n; ++p) perm[p] = t[p].idx;
+  free(t);
+}
+
+void or_cell_start(int64_t nkeys, int64_t n, const uint32_t* sk, uint32_t* cs) {
+  int64_t p = 0;
+  for (int64_t c = 0; c <= nkeys; ++c) {
+    while (p < n && (int64_t)sk[p] < c) ++p;
+    cs[c] = (uint32_t)p;
+  }
+}
+
+/* LP advection, Eq. push, with a second-order Runge-Kutta (Heun) step:
+ *   v1 = v(x^n); x* = x^n + dt v1; v2 = v(x*); x^{n+1} = x^n + dt (v1+v2)/2
+ * then samples at x^{n+1}: n_new = rho, gamma_g = 1/sqrt(1-|v|^2) (proper
+ * time d tau = dt/gamma_g, Sec. 2), b2m = (|B(x^n)|^2 + |B(x^{n+1})|^2)/2.  */
+void or_lp_rk2_step(const or_grid* g, int shape, const double* vel, const double* rho,
+                    const double* bfield, int64_t n, double* x, double dt,
+                    double* n_new, double* b2m, double* gam) {
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < n; ++p) {
+    double x0[3], xs[3], x1[3], v1[3], v2[3], b0[3], b1[3], v3[3], r;
+    for (int a = 0; a < 3; ++a) x0[a] = xs[a] = x1[a] = x[a * n + p];
+    or_gather(g, shape, vel, 3, x0, v1);
+    or_gather(g, shape, bfield, 3, x0, b0);
+    for (int a = 0; a < g->dim; ++a) xs[a] = or_wrap(g, a, x0[a] + dt * v1[a]);
+    or_gather(g, shape, vel, 3, xs, v2);
+    for (int a = 0; a < g->dim; ++a)
+      x1[a] = or_wrap(g, a, x0[a] + dt * (0.5 * (v1[a] + v2[a])));
+    or_gather(g, shape, rho, 1, x1, &r);
+    or_gather(g, shape, bfield, 3, x1, b1);
+    or_gather(g, shape, vel, 3, x1, v3);
+    for (int a = 0; a < 3; ++a) x[a * n + p] = x1[a];
+    double bb0 = b0[0] * b0[0] + b0[1] * b0[1] + b0[2] * b0[2];
+    double bb1 = b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2];
+    double vv = v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2];
+    n_new[p] = r;
+    b2m[p] = 0.5 * (bb0 + bb1);
+    gam[p] = 1.0 / sqrt(1.0 - vv);
+  }
+}
+
+/* Spectral update away from shocks, Eq. cr_chi, by exact characteristics.
+ * Along a characteristic d eps/d tau = -a3 eps - c_r eps^2, a3 = div(u)/3
+ * (Eqs. cr_N, rad_losses).  With y = 1/eps this is linear, dy/dtau = a3 y +
+ * c_r, so over d tau with a3, c_r frozen:  y1 = A y0 + C,
+ *   A = exp(a3 dtau),  C = c_r dtau expm1(a3 dtau)/(a3 dtau).
+ * Continuity (div(n u) = 0, Sec. 2) gives a3 dtau = ln(n_old/n_new)/3.
+ * chi dEps is conserved along characteristics (Eq. cr_chi is a conservation
+ * law in eps), so with s = A + C eps0: eps1 = eps0/s, chi1 = chi0 s^2/A.
+ * c_r = c0 (|B|^2/2 + U_rad) in code units, dtau = dt/gamma_g.             */
+void or_spec_update(int nb, int64_t n, double* chi, double* eng, double* n_old,
+                    const double* n_new, const double* b2m, const double* gam,
+                    double dt, double c0, double u_rad) {
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < n; ++p) {
+    double dtau = dt / gam[p];
+    double L = log(n_old[p] / n_new[p]) / 3.0;
+    double A = exp(L);
+    double cr = c0 * (0.5 * b2m[p] + u_rad);
+    double C = cr * dtau * (L == 0.0 ? 1.0 : expm1(L) / L);
+    for (int i = 0; i < nb; ++i) {
+      double e = eng[(int64_t)i * n + p];
+      double s = A + C * e;
+      eng[(int64_t)i * n + p] = e / s;
+      chi[(int64_t)i * n + p] = (chi[(int64_t)i * n + p] * (s * s)) / A;
+    }
+    n_old[p] = n_new[p];
+  }
+}
+
+/* Eq. initSpec on N_b log-spaced nodes from emin to emax (both included). */
+void or_init_spectrum(int nb, double emin, double emax, double p, double N0,
+                      double* eng, double* chi) {
+  double la = log(emin), lb = log(emax);
+  double norm = N0 * (1.0 - p) / (pow(emax, 1.0 - p) - pow(emin, 1.0 - p));
+  for (int i = 0; i < nb; ++i) {
+    double e = nb > 1 ? exp(la + (lb - la) * ((double)i / (double)(nb - 1))) : emin;
+    eng[i] = e;
+    chi[i] = norm * pow(e, -p);
+  }
+}
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+ * -> 64-bit multiplies with a word permutation and a Weyl-sequence key.    */
+void or_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Draw r in (0,1) from a 32-bit word: (r + 1/2) 2^-32 (exact in double). */
+static double u01(uint32_t r) { return ((double)r + 0.5) * 2.3283064365386963e-10; }
+
+/* Particle p: key = seed; counter (p, 0) gives the position (uniform over
+ * the domain), counter (p, 1) gives three Box-Muller normals for u (each
+ * component N(0, u_th^2)); w = 1; id = p.                                   */
+void or_init_particles(const or_grid* g, int64_t n, uint64_t seed, double u_th,
+                       double* x, double* u, double* w, uint64_t* id) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < n; ++p) {
+    uint32_t c0[4] = {(uint32_t)p, (uint32_t)((uint64_t)p >> 32), 0u, 0u};
+    uint32_t c1[4] = {(uint32_t)p, (uint32_t)((uint64_t)p >> 32), 1u, 0u};
+    uint32_t r0[4], r1[4];
+    or_philox4x32_10(c0, key, r0);
+    or_philox4x32_10(c1, key, r1);
+    for (int a = 0; a < 3; ++a) {
+      double L = (double)g->n[a] * g->dx[a];
+      x[a * n + p] = or_wrap(g, a, g->xmin[a] + L * u01(r0[a]));
+    }
+    double rad0 = sqrt(-2.0 * log(u01(r1[0])));
+    double rad1 = sqrt(-2.0 * log(u01(r1[2])));
+    double ph0 = (2.0 * M_PI) * u01(r1[1]);
+    double ph1 = (2.0 * M_PI) * u01(r1[3]);
+    u[p] = u_th * (rad0 * cos(ph0));
+    u[n + p] = u_th * (rad0 * sin(ph0));
+    u[2 * n + p] = u_th * (rad1 * cos(ph1));
+    if (w) w[p] = 1.0;
+    if (id) id[p] = (uint64_t)p;
+  }
+}

@@ -1,0 +1,85 @@
+/*
+ * part_oracle.h -- plain FP64 CPU oracle for the particle advance.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code
+ * with the CUDA path.  Everything is double precision, processed in particle
+ * index order, compiled without floating-point contraction (-ffp-contract=off).
+ *
+ * Sources (the paper: "The PLUTO Code on GPUs: Offloading Lagrangian Particle
+ * Methods"):
+ *   Eq. push            LP advection dx/dt = v(x)                 (Sec. 2)
+ *   proper time         d tau = dt / gamma_g                       (Sec. 2)
+ *   Eq. rad_losses      d eps/d tau = -c_r eps^2                   (Sec. 2)
+ *   Eq. cr_chi          d chi/d tau + d_eps[(-eps/3 div u - c_r eps^2) chi] = 0
+ *   Eq. initSpec        chi_i = N0 (1-p)/(emax^(1-p)-emin^(1-p)) eps_i^-p  (Sec. 4.1.2)
+ *   Appendix A          particle record: pos, speed, chi[128], eng[128], id
+ * Where the paper is silent the oracle uses textbook definitions:
+ *   TSC / CIC shape functions (Hockney & Eastwood), relativistic Boris push
+ *   (Boris 1970; Birdsall & Langdon), Philox4x32-10 (Salmon et al., SC'11).
+ *
+ * Parity unpinned: the absolute synchrotron coefficient scaling (c0, U_B in
+ * code units) -- the paper gives c_r only in cgs form.
+ */
+#ifndef PART_ORACLE_H
+#define PART_ORACLE_H
+#include <stdint.h>
+
+typedef struct {
+  int dim;          /* 2 or 3 spatial dimensions                         */
+  int n[3];         /* cells per axis; n[2] == 1 when dim == 2            */
+  double xmin[3];   /* lower domain corner                               */
+  double dx[3];     /* cell width per axis                               */
+} or_grid;
+
+enum { OR_CIC = 1, OR_TSC = 2 };
+
+/* shape function W(xi), xi in cell units */
+double or_shape(int shape, double xi);
+/* cell coordinate j and offset delta = s - j - 1/2 of position x, per axis */
+void or_cell_coord(const or_grid* g, const double* x, int* j, double* delta);
+/* wrap one coordinate periodically into [xmin, xmin + n dx) */
+double or_wrap(const or_grid* g, int axis, double x);
+/* interpolate ncomp cell-centred fields [comp][z][y][x] at x */
+void or_gather(const or_grid* g, int shape, const double* fields, int ncomp,
+               const double* x, double* out);
+/* relativistic Boris kick (c = 1, u = gamma v), fields at the particle */
+void or_boris_kick(double* u, const double* E, const double* B, double qm, double dt);
+/* one Boris step for n particles: gather at x^n, kick, drift, wrap.
+ * x, u: [3][n]; w: [n] (may be NULL => 1); F_out [3][n] (may be NULL) gets
+ * w (u^{n+1}-u^n)/dt; x_old_out [3][n] (may be NULL) gets x^n.            */
+void or_boris_step(const or_grid* g, int shape, const double* fields6, int64_t n,
+                   double* x, double* u, const double* w, double qm, double dt,
+                   double* F_out, double* x_old_out);
+/* scatter F [3][n] at positions x [3][n] onto out [3][G] (overwritten) */
+void or_deposit(const or_grid* g, int shape, int64_t n, const double* x,
+                const double* F, double* out);
+/* deposit onto one cell only (sampling check); out3 gets the 3 components */
+void or_deposit_cell(const or_grid* g, int shape, int64_t n, const double* x,
+                     const double* F, int64_t cell, double* out3);
+/* brick-ordered cell key of cell coordinates j with brick dims b */
+uint32_t or_cell_key(const or_grid* g, const int* b, const int* j);
+int64_t or_key_count(const or_grid* g, const int* b);
+/* keys of n positions [3][n] */
+void or_keys(const or_grid* g, const int* b, int64_t n, const double* x, uint32_t* keys);
+/* stable sort: perm gets the particle indices ordered by key */
+void or_stable_sort(int64_t n, const uint32_t* keys, uint32_t* perm);
+/* cs[c] = #particles with key < c for c in [0, nkeys] (sorted keys input) */
+void or_cell_start(int64_t nkeys, int64_t n, const uint32_t* sorted_keys, uint32_t* cs);
+/* Heun RK2 LP advection on velocity fields vel [3][G]; samples at x^{n+1} */
+void or_lp_rk2_step(const or_grid* g, int shape, const double* vel, const double* rho,
+                    const double* bfield, int64_t n, double* x, double dt,
+                    double* n_new, double* b2m, double* gam);
+/* exact-characteristic spectral update; chi, eng are bin-major [nb][n] */
+void or_spec_update(int nb, int64_t n, double* chi, double* eng, double* n_old,
+                    const double* n_new, const double* b2m, const double* gam,
+                    double dt, double c0, double u_rad);
+/* initial power-law spectrum on log-spaced nodes, Eq. initSpec */
+void or_init_spectrum(int nb, double emin, double emax, double p, double N0,
+                      double* eng, double* chi);
+/* Philox4x32-10 block function */
+void or_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
+/* particle initialisation from Philox draws: uniform x, Maxwellian u */
+void or_init_particles(const or_grid* g, int64_t n, uint64_t seed, double u_th,
+                       double* x, double* u, double* w, uint64_t* id);
+#endif
