@@ -1,0 +1,180 @@
+/*
+ * part.h -- C ABI of the B300 particle-advance library (libpart.so).
+ *
+ * The library advances particles on a periodic Cartesian grid, one CUDA
+ * stream per context:
+ *   - Lagrangian particles (LPs): advection with the fluid velocity (Eq. push,
+ *     Sec. 2) by a two-stage Runge-Kutta step (Sec. 3.3, Table codeTiming:
+ *     Particles_RK#1 / Particles_RK#2), and the per-particle energy-spectrum
+ *     update of Eq. cr_chi (Sec. 2; Particles_Spectra in Table codeTiming);
+ *   - charged test/cosmic-ray particles: relativistic Boris push with fields
+ *     gathered by TSC or CIC weights, and the deposit of the particle force
+ *     density back onto the grid (the MHD-PIC coupling named in Sec. 1).
+ * Particles are stored as structures of arrays (Sec. 3.2, "Ensure coalesced
+ * access to memory"), with the record of Appendix A (pos, speed, chi[nb],
+ * eng[nb], id).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a part_status and never aborts.  Argument errors are
+ *     found on the host before any launch and return PART_EINVAL with a
+ *     message in part_last_error().
+ *   - Work is enqueued asynchronously on the context's stream.  Errors found
+ *     by kernels (non-finite state, a particle outside its sorted cell, a
+ *     bounded wait that ran out) are latched in a device status word and
+ *     reported by the next part_sync().
+ *   - The library allocates no device memory.  All device memory is passed in
+ *     by the caller: a workspace of part_workspace_size() bytes (256-byte
+ *     aligned) and the particle/field/output arrays.  The caller keeps every
+ *     buffer alive until the work that uses it has completed (part_sync or a
+ *     stream synchronisation).
+ *   - All pointers to particle, field and output data are DEVICE pointers.
+ *   - Units: c = 1, particle mass m = 1, u = gamma v.
+ *   - Grid: cell-centred fields, layout [comp][z][y][x] (x fastest), cell
+ *     (jx,jy,jz) centred at xmin + (j + 1/2) dx.  All axes periodic.  For
+ *     dim == 2 the grid has n[2] == 1 and only x, y move (2D3V).
+ */
+#ifndef PART_H
+#define PART_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct part_ctx part_ctx; /* opaque; one per stream and particle set */
+
+typedef enum {
+  PART_OK = 0,
+  PART_EINVAL = 1,        /* bad argument (host-side check)                 */
+  PART_ENOMEM = 2,        /* workspace too small                            */
+  PART_ECUDA = 3,         /* a CUDA runtime call failed                     */
+  PART_ETIMEOUT = 4,      /* a bounded device wait ran out                  */
+  PART_ENONFINITE = 5,    /* NaN/Inf met in particle state or samples       */
+  PART_EUNSUPPORTED = 6,  /* valid request this build does not implement    */
+  PART_EDOMAIN = 7        /* a particle was not in the cell it was sorted by */
+} part_status;
+
+typedef enum { PART_FP64 = 0, PART_MIXED = 1 } part_prec;
+typedef enum { PART_CIC = 1, PART_TSC = 2 } part_shape;
+typedef enum { PART_BORIS = 0, PART_LP_RK2 = 1 } part_mode;
+
+typedef struct {
+  int dim;          /* 2 or 3                                              */
+  int n[3];         /* cells per axis, each >= 1; n[2] must be 1 if dim==2 */
+  double xmin[3];   /* lower corner                                        */
+  double dx[3];     /* cell widths (> 0)                                   */
+  int periodic[3];  /* must all be 1 (open boundaries are not built)       */
+} part_grid;
+
+/* Brick (cell tile) dimensions the library sorts and stages by: 8x8x8 in 3D,
+ * 16x16x1 in 2D.  A cell's sort key is
+ *   key = brick_index * (b0*b1*b2) + local_index,
+ * brick_index = (bz*nby + by)*nbx + bx with nb_a = ceil(n_a/b_a), local_index
+ * = (lz*b1 + ly)*b0 + lx, (b, l) = (j / b_a, j % b_a) per axis.  The last
+ * brick on an axis may be partial; keys then skip the missing cells.
+ * nkeys gets the key-space size nbx*nby*nbz*b0*b1*b2.                      */
+part_status part_brick_dims(const part_grid* grid, int brick[3], int64_t* nkeys);
+
+/* Workspace bytes for a context: padded field copy, sort buffers, cell_start,
+ * deposit partials, LP samples, status word.  capacity = maximum particles,
+ * nbins = spectral bins (LP mode; ignored otherwise).                     */
+part_status part_workspace_size(const part_grid* grid, part_prec prec, part_mode mode,
+                                int64_t capacity, int nbins, size_t* bytes);
+
+/* Create a context.  workspace: device memory of at least
+ * part_workspace_size() bytes, 256-byte aligned, owned by the caller and
+ * kept alive until part_destroy.  cuda_stream: a cudaStream_t (NULL = the
+ * legacy default stream).  Supported: PART_BORIS with PART_FP64 or
+ * PART_MIXED; PART_LP_RK2 with PART_FP64.  Returns PART_ENOMEM if ws_bytes
+ * is too small.                                                            */
+part_status part_init(part_ctx** out, const part_grid* grid, part_prec prec,
+                      part_shape shape, part_mode mode, int64_t capacity, int nbins,
+                      void* workspace, size_t ws_bytes, void* cuda_stream);
+part_status part_destroy(part_ctx* ctx);
+
+/* Copy a field snapshot into the context's padded, ghost-filled copy.
+ * fields: device, [ncomp][z][y][x] contiguous, element type f64 (PART_FP64
+ * context) or f32 (PART_MIXED context); field_prec must match.
+ * PART_BORIS: ncomp = 6 (E then B).  PART_LP_RK2: ncomp = 7 (fluid velocity
+ * v[3], density rho, B[3]) -- the fluid quantities LPs sample (Sec. 2).
+ * The copy is stream-ordered; the source may be freed once it completes.  */
+part_status part_set_fields(part_ctx* ctx, const void* fields, int ncomp, part_prec field_prec);
+
+/* Bind caller-owned particle arrays (device, component-major, row stride n):
+ *   PART_FP64 / BORIS : x_or_cell = double[3][n] positions, off = NULL,
+ *                       u = double[3][n], w = double[n] or NULL (w = 1)
+ *   PART_MIXED / BORIS: x_or_cell = int32[n] linear cell (jz*ny+jy)*nx+jx,
+ *                       off = float[3][n] offsets from the cell centre in
+ *                       cell units, in [-1/2, 1/2]; u = float[3][n];
+ *                       w = float[n] or NULL
+ *   PART_LP_RK2       : x_or_cell = double[3][n], chi, eng = double[nb][n]
+ *                       (bin-major), n_old = double[n] (density sampled at
+ *                       the previous step); u, w = NULL
+ * id (uint64[n]) is optional in every mode; when given it is permuted with
+ * the particles so the caller can undo a sort.  0 <= n <= capacity.       */
+part_status part_bind_particles(part_ctx* ctx, int64_t n, void* x_or_cell, void* off,
+                                void* u, void* w, uint64_t* id, double* chi, double* eng,
+                                double* n_old);
+
+/* Sort the bound particles by cell key (stable: equal keys keep their current
+ * order), permuting every bound array in place, and rebuild cell_start.
+ * Required before a push with deposit enabled.                            */
+part_status part_sort(part_ctx* ctx);
+
+/* Device pointer to cell_start[nkeys + 1] (valid after part_sort): the
+ * particles of key k are [cell_start[k], cell_start[k+1]).                */
+part_status part_cell_start(part_ctx* ctx, const uint32_t** cell_start, int64_t* nkeys);
+
+/* Turn on (1) or off (0) the fused force deposit of part_gather_push.     */
+part_status part_enable_deposit(part_ctx* ctx, int on);
+
+/* PART_BORIS: nsteps steps of gather (fields at x^n with the context's
+ * shape) + relativistic Boris kick + drift + periodic wrap.  With deposit on,
+ * nsteps must be 1, the particles must have been sorted since the last push,
+ * and the kick's force density F_p = w_p (u^{n+1} - u^n)/dt is reduced onto
+ * the grid with the weights at x^n (see part_deposit).
+ * PART_LP_RK2: nsteps Heun steps x* = x + dt v(x), x' = x + dt (v(x)+v(x*))/2
+ * of Eq. push, then samples at the new position for spec_update: density,
+ * the mean of |B|^2 at the old and new position, and gamma_g.  q_over_m is
+ * ignored in LP mode.                                                      */
+part_status part_gather_push(part_ctx* ctx, double q_over_m, double dt, int nsteps);
+
+/* Write the force density deposited by the last part_gather_push into
+ * grid_out (device, double[3][G], overwritten):
+ *   F_g = sum_p W(x_g - x_p^n) F_p.
+ * Deterministic: no floating-point atomics; the same inputs give the same
+ * bits on every run.                                                       */
+part_status part_deposit(part_ctx* ctx, double* grid_out);
+
+/* Spectral update of every LP (Eq. cr_chi with Eq. rad_losses), using the
+ * samples of the last PART_LP_RK2 push.  Per LP: dtau = dt/gamma_g (Sec. 2),
+ * A = (n_old/n_new)^{1/3}, c_r = c0 (|B|^2/2 + u_rad),
+ * C = c_r dtau expm1(ln A)/ln A; per bin, s = A + C eps:
+ *   eps <- eps/s,  chi <- chi s^2/A;  then n_old <- n_new.                 */
+part_status spec_update(part_ctx* ctx, double dt, double c0, double u_rad);
+
+/* Initialise the bound particles on the device from Philox4x32-10 draws
+ * (key = seed; counter (p, 0) -> uniform position over the domain, counter
+ * (p, 1) -> Maxwellian u with per-component std u_th by Box-Muller), w = 1,
+ * id = p.  LP mode: u_th ignored; every LP gets the power law of Eq. initSpec
+ * on nb log-spaced energies in [eps_min, eps_max] with index p_index and
+ * integral N0, and n_old = density sampled at its position.              */
+part_status part_init_particles(part_ctx* ctx, uint64_t seed, double u_th, double eps_min,
+                                double eps_max, double p_index, double N0);
+
+/* Wait for the context's stream; return (and clear) the first latched device
+ * error, else PART_OK.                                                     */
+part_status part_sync(part_ctx* ctx);
+
+/* Message for the last non-OK status of this context (never NULL).        */
+const char* part_last_error(const part_ctx* ctx);
+
+/* Kernel launches this context has enqueued since creation.               */
+int64_t part_launch_count(const part_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PART_H */

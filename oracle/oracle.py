@@ -48,7 +48,8 @@ def make_grid(dim: int, n, xmin=(-1.0, -1.0, -1.0), dx=None) -> Grid:
     if dim == 2:
         n[2] = 1
     if dx is None:
-        dx = [2.0 / n[0], 2.0 / n[1], 2.0 / n[2] if dim == 3 else 1.0]
+        # an inactive z axis (dim 2) spans the same [-1, 1) as the others
+        dx = [2.0 / n[0], 2.0 / n[1], 2.0 / n[2] if dim == 3 else 2.0]
     g = Grid()
     g.dim = dim
     for a in range(3):

@@ -1,0 +1,205 @@
+"""ctypes binding of libpart.so (include/part.h), argument marshalling only.
+
+Every computation runs in the CUDA library; this module turns torch tensors
+into device pointers, allocates the caller-owned workspace with torch, and
+raises PartError on any non-OK status.  If libpart.so is missing or cannot be
+loaded the import fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpart.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "part.h")
+
+FP64, MIXED = 0, 1
+CIC, TSC = 1, 2
+BORIS, LP_RK2 = 0, 1
+
+STATUS = {0: "PART_OK", 1: "PART_EINVAL", 2: "PART_ENOMEM", 3: "PART_ECUDA",
+          4: "PART_ETIMEOUT", 5: "PART_ENONFINITE", 6: "PART_EUNSUPPORTED",
+          7: "PART_EDOMAIN"}
+
+
+class PartError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+class Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("xmin", C.c_double * 3),
+                ("dx", C.c_double * 3), ("periodic", C.c_int * 3)]
+
+
+def make_grid(dim: int, n, xmin=(-1.0, -1.0, -1.0), L=(2.0, 2.0, 2.0)) -> Grid:
+    """Periodic grid of n cells per axis on [xmin, xmin + L); dim 2 -> n[2] = 1."""
+    if isinstance(n, int):
+        n = (n, n, n if dim == 3 else 1)
+    n = list(n) + [1] * (3 - len(n))
+    if dim == 2:
+        n[2] = 1
+    g = Grid()
+    g.dim = dim
+    for a in range(3):
+        g.n[a] = int(n[a])
+        g.xmin[a] = float(xmin[a])
+        g.dx[a] = float(L[a]) / n[a] if (a < dim) else float(L[a])
+        g.periodic[a] = 1
+    return g
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2602_23434_b300/build.py "
+                          "(there is no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    G = C.POINTER(Grid)
+    st = C.c_int
+    sigs = {
+        "part_brick_dims": (st, [G, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+        "part_workspace_size": (st, [G, C.c_int, C.c_int, C.c_int64, C.c_int,
+                                     C.POINTER(C.c_size_t)]),
+        "part_init": (st, [C.POINTER(P), G, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int, P,
+                           C.c_size_t, P]),
+        "part_destroy": (st, [P]),
+        "part_set_fields": (st, [P, P, C.c_int, C.c_int]),
+        "part_bind_particles": (st, [P, C.c_int64, P, P, P, P, P, P, P, P]),
+        "part_sort": (st, [P]),
+        "part_cell_start": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
+        "part_enable_deposit": (st, [P, C.c_int]),
+        "part_gather_push": (st, [P, C.c_double, C.c_double, C.c_int]),
+        "part_deposit": (st, [P, P]),
+        "spec_update": (st, [P, C.c_double, C.c_double, C.c_double]),
+        "part_init_particles": (st, [P, C.c_uint64, C.c_double, C.c_double, C.c_double,
+                                     C.c_double, C.c_double]),
+        "part_sync": (st, [P]),
+        "part_last_error": (C.c_char_p, [P]),
+        "part_launch_count": (C.c_int64, [P]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def header_functions(path: str = HEADER) -> list[str]:
+    """Names of the functions include/part.h declares."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(",
+                                 txt, flags=re.M)) - {"if", "while"})
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Part:
+    """One library context: workspace, stream, bound particles and fields."""
+
+    def __init__(self, grid: Grid, prec: int = FP64, shape: int = TSC, mode: int = BORIS,
+                 capacity: int = 0, nbins: int = 0, stream=None, device=None):
+        import torch
+        self.torch = torch
+        self.L = lib()
+        self.grid = grid
+        self.prec, self.shape, self.mode = prec, shape, mode
+        self.capacity, self.nbins = capacity, nbins
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = C.c_size_t()
+        self._check(self.L.part_workspace_size(C.byref(grid), prec, mode, capacity, nbins,
+                                               C.byref(nbytes)), None)
+        self.ws_bytes = nbytes.value
+        # torch's caching allocator returns 512-byte aligned blocks
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=self.device)
+        self.ctx = C.c_void_p()
+        self._check(self.L.part_init(C.byref(self.ctx), C.byref(grid), prec, shape, mode,
+                                     capacity, nbins, C.c_void_p(self.ws.data_ptr()),
+                                     self.ws_bytes, C.c_void_p(self.stream.cuda_stream)), None)
+        self._keep = ()
+        b = (C.c_int * 3)()
+        nk = C.c_int64()
+        self._check(self.L.part_brick_dims(C.byref(grid), b, C.byref(nk)))
+        self.brick = tuple(b)
+        self.nkeys = nk.value
+
+    def _check(self, code: int, ctx="self"):
+        if code != 0:
+            c = self.ctx if ctx == "self" else None
+            msg = self.L.part_last_error(c)
+            raise PartError(code, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            self.L.part_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ calls
+    def set_fields(self, fields):
+        assert fields.is_cuda and fields.is_contiguous()
+        prec = FP64 if fields.dtype == self.torch.float64 else MIXED
+        self._check(self.L.part_set_fields(self.ctx, _ptr(fields), fields.shape[0], prec))
+        self._fields = fields
+
+    def bind(self, n, x, off=None, u=None, w=None, ids=None, chi=None, eng=None, n_old=None):
+        self._check(self.L.part_bind_particles(self.ctx, n, _ptr(x), _ptr(off), _ptr(u),
+                                               _ptr(w), _ptr(ids), _ptr(chi), _ptr(eng),
+                                               _ptr(n_old)))
+        self._keep = (x, off, u, w, ids, chi, eng, n_old)
+
+    def sort(self):
+        self._check(self.L.part_sort(self.ctx))
+
+    def cell_start(self):
+        """View of cell_start[nkeys + 1] inside the workspace (int64 copy)."""
+        p = C.c_void_p()
+        nk = C.c_int64()
+        self._check(self.L.part_cell_start(self.ctx, C.byref(p), C.byref(nk)))
+        off = p.value - self.ws.data_ptr()
+        raw = self.ws[off: off + 4 * (nk.value + 1)]
+        return raw.view(self.torch.int32).to(self.torch.int64) & 0xFFFFFFFF
+
+    def enable_deposit(self, on=True):
+        self._check(self.L.part_enable_deposit(self.ctx, 1 if on else 0))
+
+    def gather_push(self, qm: float, dt: float, nsteps: int = 1):
+        self._check(self.L.part_gather_push(self.ctx, qm, dt, nsteps))
+
+    def deposit(self, out):
+        assert out.is_cuda and out.dtype == self.torch.float64 and out.is_contiguous()
+        self._check(self.L.part_deposit(self.ctx, _ptr(out)))
+
+    def spec_update(self, dt: float, c0: float, u_rad: float = 0.0):
+        self._check(self.L.spec_update(self.ctx, dt, c0, u_rad))
+
+    def init_particles(self, seed: int, u_th: float = 0.0, eps_min: float = 1.0,
+                       eps_max: float = 1e6, p_index: float = 2.2, N0: float = 1e-6):
+        self._check(self.L.part_init_particles(self.ctx, seed, u_th, eps_min, eps_max,
+                                               p_index, N0))
+
+    def sync(self):
+        self._check(self.L.part_sync(self.ctx))
+
+    def launches(self) -> int:
+        return int(self.L.part_launch_count(self.ctx))

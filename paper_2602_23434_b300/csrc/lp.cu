@@ -1,0 +1,220 @@
+// lp.cu -- Lagrangian-particle advection (Eq. push, Heun RK2) and the
+// per-bin spectral update of Eq. cr_chi (exact characteristics).
+//
+// Fields: padded FP64 copy with 7 components: v[3], rho, B[3] (the fluid
+// quantities an LP samples, Sec. 2).  Spectra are bin-major [nb][n], so every
+// bin access of a warp is one coalesced 256-byte row.
+#include "part_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ double wrap_axis(double v, double lo, double hi, double L) {
+  if (v < lo) v = v + L;
+  else if (v >= hi) v = v - L;
+  return v;
+}
+
+// Stencil of position x: padded row origin and weights per axis.
+template <int SHAPE, int DIM>
+struct Stencil {
+  int64_t base;     // padded index of the (-1,-1,-1) corner
+  double wx[3], wy[3], wz[3];
+  bool finite;
+  __device__ __forceinline__ Stencil(const Geo& g, const double* xp) {
+    int j[3] = {0, 0, 0};
+    double d[3] = {0.0, 0.0, 0.0};
+    finite = true;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      double s = __dmul_rn(__dsub_rn(xp[a], g.xmin[a]), g.inv_dx[a]);
+      if (!isfinite(s)) {
+        finite = false;
+        s = 0.0;
+      }
+      double f = floor(s);
+      j[a] = f >= (double)g.n[a] ? g.n[a] - 1 : (f < 0.0 ? 0 : (int)f);
+      d[a] = __dsub_rn(__dsub_rn(s, (double)j[a]), 0.5);
+    }
+    shape_weights<SHAPE>(d[0], wx);
+    shape_weights<SHAPE>(d[1], wy);
+    wz[0] = 0.0;
+    wz[1] = 1.0;
+    wz[2] = 0.0;
+    if (DIM == 3) shape_weights<SHAPE>(d[2], wz);
+    base = ((int64_t)j[2] * g.pn[1] + j[1]) * g.pn[0] + j[0];
+  }
+  // sum over the stencil of components [c0, c0 + NC)
+  template <int NC>
+  __device__ __forceinline__ void gather(const double* __restrict__ fp, const Geo& g, int c0,
+                                         double* out) const {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) out[c] = 0.0;
+#pragma unroll
+    for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
+      const int zo = DIM == 3 ? kz : 0;
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky) {
+        const double wzy = wz[kz] * wy[ky];
+        const int64_t row = base + ((int64_t)zo * g.pn[1] + ky) * g.pn[0];
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+          const double ww = wzy * wx[kx];
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            out[c] += ww * __ldg(fp + (int64_t)(c0 + c) * g.pplane + row + kx);
+        }
+      }
+    }
+  }
+};
+
+template <int SHAPE, int DIM>
+__global__ void __launch_bounds__(256)
+    k_lp_rk2(const double* __restrict__ fp, const Geo g, double* __restrict__ x, int64_t n,
+             double dt, double* __restrict__ samples, int* __restrict__ status) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    double x0[3], xs[3], x1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x0[a] = xs[a] = x1[a] = x[a * n + p];
+    double v1[3], b0[3], v2[3], v3[3], b1[3], r;
+    Stencil<SHAPE, DIM> s0(g, x0);
+    s0.template gather<3>(fp, g, 0, v1);
+    s0.template gather<3>(fp, g, 4, b0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) xs[a] = wrap_axis(x0[a] + dt * v1[a], g.xmin[a], g.xmax[a], g.L[a]);
+    Stencil<SHAPE, DIM> ss(g, xs);
+    ss.template gather<3>(fp, g, 0, v2);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+      x1[a] = wrap_axis(x0[a] + dt * (0.5 * (v1[a] + v2[a])), g.xmin[a], g.xmax[a], g.L[a]);
+    Stencil<SHAPE, DIM> s1(g, x1);
+    s1.template gather<1>(fp, g, 3, &r);
+    s1.template gather<3>(fp, g, 4, b1);
+    s1.template gather<3>(fp, g, 0, v3);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a * n + p] = x1[a];
+    const double bb0 = b0[0] * b0[0] + b0[1] * b0[1] + b0[2] * b0[2];
+    const double bb1 = b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2];
+    const double vv = v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2];
+    const double gam = 1.0 / sqrt(1.0 - vv);
+    samples[p] = r;
+    samples[n + p] = 0.5 * (bb0 + bb1);
+    samples[2 * n + p] = gam;
+    if (!(s0.finite && ss.finite && s1.finite && isfinite(gam) && isfinite(r) && r > 0.0))
+      atomicOr(status, ST_NONFINITE);
+  }
+}
+
+// Per LP: dtau = dt/gamma_g; ln A = ln(n_old/n_new)/3; c_r = c0 (|B|^2/2 +
+// u_rad); C = c_r dtau expm1(ln A)/ln A.  Per bin: s = A + C eps;
+// eps <- eps/s; chi <- chi s^2/A.  Bins are unrolled 8 at a time so that
+// eight independent row loads are in flight per thread.
+__global__ void __launch_bounds__(256)
+    k_spec_update(double* __restrict__ chi, double* __restrict__ eng, double* __restrict__ n_old,
+                  const double* __restrict__ samples, int64_t n, int nb, double dt, double c0,
+                  double u_rad, int* __restrict__ status) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const double nn = samples[p], b2 = samples[n + p], gam = samples[2 * n + p];
+    const double dtau = dt / gam;
+    const double L = log(n_old[p] / nn) / 3.0;
+    const double A = exp(L);
+    const double invA = exp(-L);
+    const double cr = c0 * (0.5 * b2 + u_rad);
+    const double C = cr * dtau * (L == 0.0 ? 1.0 : expm1(L) / L);
+    if (!(isfinite(A) && isfinite(C))) atomicOr(status, ST_NONFINITE);
+    double* ep = eng + p;
+    double* cp = chi + p;
+    int i = 0;
+    for (; i + 8 <= nb; i += 8) {
+      double e[8], c[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        e[k] = ep[(int64_t)(i + k) * n];
+        c[k] = cp[(int64_t)(i + k) * n];
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const double s = A + C * e[k];
+        ep[(int64_t)(i + k) * n] = e[k] / s;
+        cp[(int64_t)(i + k) * n] = (c[k] * (s * s)) * invA;
+      }
+    }
+    for (; i < nb; ++i) {
+      const double e = ep[(int64_t)i * n];
+      const double s = A + C * e;
+      ep[(int64_t)i * n] = e / s;
+      cp[(int64_t)i * n] = (cp[(int64_t)i * n] * (s * s)) * invA;
+    }
+    n_old[p] = nn;
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 148 * 64) b = 148 * 64;
+  return (int)b;
+}
+
+template <int SHAPE, int DIM>
+cudaError_t lp_launch(part_ctx* c, double dt) {
+  k_lp_rk2<SHAPE, DIM><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
+      (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_lp_push(part_ctx* c, double dt, int nsteps) {
+  (void)nsteps;
+  if (c->n == 0) return cudaSuccess;
+  if (c->shape == PART_TSC)
+    return c->geo.dim == 3 ? lp_launch<PART_TSC, 3>(c, dt) : lp_launch<PART_TSC, 2>(c, dt);
+  return c->geo.dim == 3 ? lp_launch<PART_CIC, 3>(c, dt) : lp_launch<PART_CIC, 2>(c, dt);
+}
+
+cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad) {
+  if (c->n == 0) return cudaSuccess;
+  k_spec_update<<<grid_for(c->n, 256), 256, 0, c->stream>>>(
+      c->chi, c->eng, c->n_old, c->samples, c->n, c->nbins, dt, c0, u_rad, c->status);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+// Gather of one scalar component, used by the LP initialisation.
+template <int SHAPE, int DIM>
+__global__ void k_lp_sample_rho(const double* __restrict__ fp, const Geo g,
+                                const double* __restrict__ x, int64_t n,
+                                double* __restrict__ n_old) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    double xp[3] = {x[p], x[n + p], x[2 * n + p]};
+    Stencil<SHAPE, DIM> s(g, xp);
+    double r;
+    s.template gather<1>(fp, g, 3, &r);
+    n_old[p] = r;
+  }
+}
+
+cudaError_t launch_lp_sample_rho(part_ctx* c) {
+  if (c->n == 0) return cudaSuccess;
+  const int gb = grid_for(c->n, 256);
+  const double* fp = (const double*)c->fpad;
+  const double* x = (const double*)c->x;
+  if (c->shape == PART_TSC) {
+    if (c->geo.dim == 3)
+      k_lp_sample_rho<PART_TSC, 3><<<gb, 256, 0, c->stream>>>(fp, c->geo, x, c->n, c->n_old);
+    else
+      k_lp_sample_rho<PART_TSC, 2><<<gb, 256, 0, c->stream>>>(fp, c->geo, x, c->n, c->n_old);
+  } else {
+    if (c->geo.dim == 3)
+      k_lp_sample_rho<PART_CIC, 3><<<gb, 256, 0, c->stream>>>(fp, c->geo, x, c->n, c->n_old);
+    else
+      k_lp_sample_rho<PART_CIC, 2><<<gb, 256, 0, c->stream>>>(fp, c->geo, x, c->n, c->n_old);
+  }
+  c->launches++;
+  return cudaGetLastError();
+}

@@ -1,0 +1,165 @@
+// part_internal.cuh -- shared definitions of the CUDA particle library.
+//
+// Geometry, status bits, the context record and the small PTX wrappers
+// (mbarrier, TMA tensor copies) used by the kernels.  sm_103a only.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "part.h"
+
+// ---------------------------------------------------------------- status bits
+// Latched by kernels with atomicOr into the workspace status word.
+enum : int {
+  ST_TIMEOUT = 1,     // a bounded mbarrier wait ran out
+  ST_NONFINITE = 2,   // NaN / Inf in particle state or samples
+  ST_DOMAIN = 4,      // particle outside the cell range it was sorted into
+};
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;   // keys per radix tile
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kScanBlock = 1024;                      // elements per scan block
+constexpr int kPushThreads = 256;                     // brick kernel CTA size
+
+// Geometry handed to kernels by value.
+struct Geo {
+  int dim;
+  int n[3];
+  int b[3];        // brick (cell tile) dims
+  int nb[3];       // bricks per axis (last may be partial)
+  int h[3];        // stencil halo per axis: 1, or 0 for z in 2D
+  int e[3];        // extended (haloed) tile dims b + 2h
+  int pn[3];       // padded field dims: x pitch, y, z (ghost layer of h)
+  int box[3];      // TMA box dims (x rounded to a 16-byte multiple)
+  int V;           // cells per brick
+  int ev;          // cells per extended tile
+  int64_t G;       // cells
+  int64_t nkeys;   // key-space size = bricks * V
+  int64_t nbricks;
+  int64_t pplane;  // padded elements per field component
+  double xmin[3], dx[3], inv_dx[3], L[3], xmax[3];
+};
+
+struct part_ctx {
+  part_grid grid;
+  part_prec prec;
+  part_shape shape;
+  part_mode mode;
+  int64_t capacity;
+  int nbins;
+  cudaStream_t stream;
+  Geo geo;
+  int ncomp;        // field components (6 Boris, 7 LP)
+  int esize;        // field element bytes
+  // workspace carve-up
+  char* ws;
+  size_t ws_bytes;
+  void* fpad;       // padded fields [ncomp][pz][py][px]
+  uint32_t* keys[2];
+  uint32_t* vals[2];
+  uint32_t* hist;   // radix tile histograms (digit-major)
+  uint32_t* hsum;   // scan block sums
+  uint32_t* cstart; // cell_start [nkeys + 1]
+  void* tmp;        // permute scratch, 8 bytes * capacity
+  double* dpart;    // deposit partials [nbricks][3][ev]
+  double* samples;  // LP samples [3][capacity]: n_new, b2m, gamma_g
+  int* status;      // device status word
+  CUtensorMap tmap; // TMA map of fpad
+  bool tmap_ok;
+  // bound particles
+  int64_t n;
+  void* x;
+  void* off;
+  void* u;
+  void* w;
+  uint64_t* id;
+  double* chi;
+  double* eng;
+  double* n_old;
+  bool bound, fields_set, sorted, deposit_on, deposit_ready, samples_ready;
+  int64_t launches;
+  std::string err;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after a fixed number of polls and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 20); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// 4-D tiled TMA load global -> shared, completion signalled on bar.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(smem_addr(bar))
+      : "memory");
+}
+
+// ---------------------------------------------------------------- shape weights
+// Three-point weights at offsets k = -1, 0, +1 from the particle's cell for
+// offset d = (s - j) - 1/2 in [-1/2, 1/2].  TSC: quadratic B-spline; CIC: hat
+// (one of the outer weights is zero).
+template <int SHAPE, typename T>
+__device__ __forceinline__ void shape_weights(T d, T* w) {
+  if (SHAPE == PART_TSC) {
+    T a = T(0.5) - d, b = T(0.5) + d;
+    w[0] = T(0.5) * (a * a);
+    w[1] = T(0.75) - d * d;
+    w[2] = T(0.5) * (b * b);
+  } else {
+    w[0] = d < T(0) ? -d : T(0);
+    w[1] = T(1) - (d < T(0) ? -d : d);
+    w[2] = d > T(0) ? d : T(0);
+  }
+}
+
+// ---------------------------------------------------------------- host glue
+// Kernel launchers implemented in the .cu files; each returns a cudaError_t
+// of its launch and counts the launches it made in *launches.
+cudaError_t launch_pad_fields(part_ctx* c, const void* src);
+cudaError_t launch_sort(part_ctx* c);
+cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps);
+cudaError_t launch_deposit_combine(part_ctx* c, double* out);
+cudaError_t launch_lp_push(part_ctx* c, double dt, int nsteps);
+cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad);
+cudaError_t launch_init(part_ctx* c, uint64_t seed, double u_th, double emin, double emax,
+                        double p, double N0);

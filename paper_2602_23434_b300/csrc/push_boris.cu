@@ -1,0 +1,438 @@
+// push_boris.cu -- gather + relativistic Boris push (+ fused force deposit).
+//
+// Brick kernel (sorted particles, one CTA per 8x8x8 / 16x16 cell brick):
+//   1. one thread issues a 4-D TMA copy of the brick's haloed field box
+//      (all components) into shared memory; cell_start of the brick is read;
+//   2. the CTA walks the brick's particles in chunks of blockDim: TSC/CIC
+//      weights, gather from shared memory, Boris kick, drift, periodic wrap,
+//      coalesced SoA loads/stores;
+//   3. deposit (optional): each particle leaves its weights and force in
+//      shared memory; each thread owns cells of the haloed tile and sums the
+//      contributions of the chunk's particles in a fixed order (stencil
+//      offset, then particle index).  Register accumulators, no atomics;
+//   4. the haloed tile is written as this brick's partial; a second kernel
+//      adds, per grid cell, the partials of the bricks covering it in fixed
+//      order.  The result is bitwise reproducible.
+// Particle-order kernel (any order, no deposit): nsteps fused steps with the
+// state in registers and the stencil read from the padded global copy.
+#include "part_internal.cuh"
+
+namespace {
+
+constexpr int kT = kPushThreads;
+
+__host__ __device__ constexpr int ntargets(int dim) {
+  return dim == 3 ? (10 * 10 * 10 + kT - 1) / kT : (18 * 18 + kT - 1) / kT;
+}
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Shared-memory carve of the brick kernel.
+struct BrickSmem {
+  size_t box, cs, bar, rec, total;
+};
+__host__ __device__ inline BrickSmem brick_smem(const Geo& g, int ncomp, int esize) {
+  BrickSmem s;
+  s.box = 0;
+  size_t bbytes = (size_t)ncomp * g.box[0] * g.box[1] * g.box[2] * esize;
+  s.cs = align_up(bbytes, 128);
+  s.bar = align_up(s.cs + (size_t)(g.V + 1) * 4, 16);
+  s.rec = align_up(s.bar + 16, 128);
+  s.total = s.rec + (size_t)18 * kT * 8;
+  return s;
+}
+
+__device__ __forceinline__ double wrap_axis(double v, double lo, double hi, double L) {
+  if (v < lo) v = v + L;
+  else if (v >= hi) v = v - L;
+  return v;
+}
+
+// Relativistic Boris kick (c = 1): half E kick, rotation about B with
+// t = h B / gamma-, s = 2t/(1+t^2), half E kick; h = (q/m) dt / 2.
+__device__ __forceinline__ void boris_f64(double* u, const double* E, const double* B, double h) {
+  double um0 = u[0] + h * E[0], um1 = u[1] + h * E[1], um2 = u[2] + h * E[2];
+  double gi = rsqrt(1.0 + (um0 * um0 + um1 * um1 + um2 * um2));
+  double hg = h * gi;
+  double t0 = hg * B[0], t1 = hg * B[1], t2 = hg * B[2];
+  double sf = 2.0 / (1.0 + (t0 * t0 + t1 * t1 + t2 * t2));
+  double s0 = sf * t0, s1 = sf * t1, s2 = sf * t2;
+  double p0 = um0 + (um1 * t2 - um2 * t1);
+  double p1 = um1 + (um2 * t0 - um0 * t2);
+  double p2 = um2 + (um0 * t1 - um1 * t0);
+  double q0 = um0 + (p1 * s2 - p2 * s1);
+  double q1 = um1 + (p2 * s0 - p0 * s2);
+  double q2 = um2 + (p0 * s1 - p1 * s0);
+  u[0] = q0 + h * E[0];
+  u[1] = q1 + h * E[1];
+  u[2] = q2 + h * E[2];
+}
+
+// ---------------------------------------------------------------- brick kernel, FP64
+template <int SHAPE, int DIM, bool DEP>
+__global__ void __launch_bounds__(kT, 2)
+    k_boris_brick_f64(const __grid_constant__ CUtensorMap tmap, const Geo g,
+                      double* __restrict__ x, double* __restrict__ u,
+                      const double* __restrict__ w, int64_t n,
+                      const uint32_t* __restrict__ cstart, double* __restrict__ dpart,
+                      double qm, double dt, int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const BrickSmem L = brick_smem(g, 6, 8);
+  const int tid = threadIdx.x;
+  const int bvol = g.box[0] * g.box[1] * g.box[2];
+  double* sbox = reinterpret_cast<double*>(smem);
+  uint32_t* scs = reinterpret_cast<uint32_t*>(smem + L.cs);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+  int* sflag = reinterpret_cast<int*>(smem + L.bar + 8);
+  double* rw = reinterpret_cast<double*>(smem + L.rec);  // [9][kT] wz*wy
+  double* rf = rw + 9 * kT;                              // [9][kT] wx[k]*F[c]
+
+  const int64_t brick = blockIdx.x;
+  const int bx = (int)(brick % g.nb[0]);
+  const int by = (int)((brick / g.nb[0]) % g.nb[1]);
+  const int bz = (int)(brick / ((int64_t)g.nb[0] * g.nb[1]));
+  const int o0 = bx * g.b[0], o1 = by * g.b[1], o2 = bz * g.b[2];
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    *sflag = 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(bar, (uint32_t)(6 * bvol * 8));
+    // padded index of cell c is c + h, so the box starting one cell below the
+    // brick origin starts at padded coordinate o
+    tma_load_4d(sbox, &tmap, bar, o0, o1, o2, 0);
+  }
+  for (int i = tid; i <= g.V; i += kT) scs[i] = cstart[brick * g.V + i];
+  if (!mbar_wait_bounded(bar, 0)) atomicOr(sflag, 1);
+  __syncthreads();
+  if (*sflag) {
+    if (tid == 0) {
+      atomicOr(status, ST_TIMEOUT);
+      mbar_wait_bounded(bar, 0);
+    }
+    return;
+  }
+
+  constexpr int NT = ntargets(DIM);
+  double acc[NT][3];
+#pragma unroll
+  for (int q = 0; q < NT; ++q) acc[q][0] = acc[q][1] = acc[q][2] = 0.0;
+
+  const double h = 0.5 * qm * dt;
+  const uint32_t p0 = scs[0], p1 = scs[g.V];
+  const int org[3] = {o0, o1, o2};
+  for (uint32_t base = p0; base < p1; base += kT) {
+    const uint32_t p = base + tid;
+    double wyz[9], fxc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) wyz[k] = fxc[k] = 0.0;
+    if (p < p1) {
+      double xp[3], up[3], uo[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        xp[a] = x[a * n + p];
+        up[a] = u[a * n + p];
+        uo[a] = up[a];
+      }
+      int l[3] = {0, 0, 0};
+      double d[3] = {0.0, 0.0, 0.0};
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        double s = __dmul_rn(__dsub_rn(xp[a], g.xmin[a]), g.inv_dx[a]);
+        double f = floor(s);
+        int j = f >= (double)g.n[a] ? g.n[a] - 1 : (f < 0.0 ? 0 : (int)f);
+        d[a] = __dsub_rn(__dsub_rn(s, (double)j), 0.5);
+        l[a] = j - org[a];
+        ok = ok && l[a] >= 0 && l[a] < g.b[a] && isfinite(s);
+      }
+      if (ok) {  // the particle must sit in the cell it was sorted into
+        const int lc = (l[2] * g.b[1] + l[1]) * g.b[0] + l[0];
+        ok = p >= scs[lc] && p < scs[lc + 1];
+      }
+      if (!ok) {
+        atomicOr(status, ST_DOMAIN);
+      } else {
+        double wx[3], wy[3], wz[3] = {0.0, 1.0, 0.0};
+        shape_weights<SHAPE>(d[0], wx);
+        shape_weights<SHAPE>(d[1], wy);
+        if (DIM == 3) shape_weights<SHAPE>(d[2], wz);
+        double f[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
+          const int zz = DIM == 3 ? l[2] + kz : 0;
+#pragma unroll
+          for (int ky = 0; ky < 3; ++ky) {
+            const double wzy = wz[kz] * wy[ky];
+            wyz[kz * 3 + ky] = wzy;
+            const int row = (zz * g.box[1] + l[1] + ky) * g.box[0] + l[0];
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+              const double ww = wzy * wx[kx];
+              const double* sp = sbox + row + kx;
+#pragma unroll
+              for (int c = 0; c < 6; ++c) f[c] += ww * sp[c * bvol];
+            }
+          }
+        }
+        boris_f64(up, f, f + 3, h);
+        const double gi = rsqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+          xp[a] = wrap_axis(xp[a] + dt * (up[a] * gi), g.xmin[a], g.xmax[a], g.L[a]);
+        bool fin = isfinite(up[0]) && isfinite(up[1]) && isfinite(up[2]) &&
+                   isfinite(xp[0]) && isfinite(xp[1]) && isfinite(xp[2]);
+        if (!fin) atomicOr(status, ST_NONFINITE);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          x[a * n + p] = xp[a];
+          u[a * n + p] = up[a];
+        }
+        if (DEP) {
+          const double wdt = (w ? w[p] : 1.0) / dt;
+          double F[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) F[a] = (up[a] - uo[a]) * wdt;
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) fxc[kx * 3 + c] = wx[kx] * F[c];
+        }
+      }
+    }
+    if (DEP) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        rw[k * kT + tid] = wyz[k];
+        rf[k * kT + tid] = fxc[k];
+      }
+      __syncthreads();
+      const int hz = DIM == 3 ? 1 : 0;
+#pragma unroll
+      for (int q = 0; q < NT; ++q) {
+        const int t = tid + q * kT;
+        if (t < g.ev) {
+          const int ex = t % g.e[0];
+          const int ey = (t / g.e[0]) % g.e[1];
+          const int ez = t / (g.e[0] * g.e[1]);
+          for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
+            const int lz = ez - hz - (kz - 1);
+            if (lz < 0 || lz >= g.b[2]) continue;
+            for (int ky = 0; ky < 3; ++ky) {
+              const int ly = ey - ky;
+              if (ly < 0 || ly >= g.b[1]) continue;
+              for (int kx = 0; kx < 3; ++kx) {
+                const int lx = ex - kx;
+                if (lx < 0 || lx >= g.b[0]) continue;
+                const int ls = (lz * g.b[1] + ly) * g.b[0] + lx;
+                uint32_t r0 = scs[ls], r1 = scs[ls + 1];
+                r0 = r0 > base ? r0 : base;
+                r1 = r1 < base + kT ? r1 : base + kT;
+                for (uint32_t r = r0; r < r1; ++r) {
+                  const int i = (int)(r - base);
+                  const double ww = rw[(kz * 3 + ky) * kT + i];
+                  acc[q][0] += ww * rf[(kx * 3 + 0) * kT + i];
+                  acc[q][1] += ww * rf[(kx * 3 + 1) * kT + i];
+                  acc[q][2] += ww * rf[(kx * 3 + 2) * kT + i];
+                }
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (DEP) {
+#pragma unroll
+    for (int q = 0; q < NT; ++q) {
+      const int t = tid + q * kT;
+      if (t < g.ev)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dpart[(brick * 3 + c) * g.ev + t] = acc[q][c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- particle order, FP64
+template <int SHAPE, int DIM>
+__global__ void __launch_bounds__(256)
+    k_boris_particles_f64(const double* __restrict__ fp, const Geo g, double* __restrict__ x,
+                          double* __restrict__ u, int64_t n, double qm, double dt, int nsteps,
+                          int* __restrict__ status) {
+  const double h = 0.5 * qm * dt;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    double xp[3], up[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      xp[a] = x[a * n + p];
+      up[a] = u[a * n + p];
+    }
+    bool bad = false;
+    for (int st = 0; st < nsteps; ++st) {
+      int j[3] = {0, 0, 0};
+      double d[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        double s = __dmul_rn(__dsub_rn(xp[a], g.xmin[a]), g.inv_dx[a]);
+        if (!isfinite(s)) {
+          bad = true;
+          s = 0.0;
+        }
+        double f = floor(s);
+        j[a] = f >= (double)g.n[a] ? g.n[a] - 1 : (f < 0.0 ? 0 : (int)f);
+        d[a] = __dsub_rn(__dsub_rn(s, (double)j[a]), 0.5);
+      }
+      double wx[3], wy[3], wz[3] = {0.0, 1.0, 0.0};
+      shape_weights<SHAPE>(d[0], wx);
+      shape_weights<SHAPE>(d[1], wy);
+      if (DIM == 3) shape_weights<SHAPE>(d[2], wz);
+      double f[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+      for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
+        const int zz = DIM == 3 ? j[2] + kz : 0;
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
+          const double wzy = wz[kz] * wy[ky];
+          const int64_t row = ((int64_t)zz * g.pn[1] + j[1] + ky) * g.pn[0] + j[0];
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) {
+            const double ww = wzy * wx[kx];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) f[c] += ww * __ldg(fp + c * g.pplane + row + kx);
+          }
+        }
+      }
+      boris_f64(up, f, f + 3, h);
+      const double gi = rsqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+#pragma unroll
+      for (int a = 0; a < DIM; ++a)
+        xp[a] = wrap_axis(xp[a] + dt * (up[a] * gi), g.xmin[a], g.xmax[a], g.L[a]);
+    }
+    if (bad || !(isfinite(up[0]) && isfinite(up[1]) && isfinite(up[2]) && isfinite(xp[0]) &&
+                 isfinite(xp[1]) && isfinite(xp[2])))
+      atomicOr(status, ST_NONFINITE);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      x[a * n + p] = xp[a];
+      u[a * n + p] = up[a];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- deposit combine
+// out[c][g] = sum over the bricks whose haloed tile covers cell g (or one of
+// its periodic images), in fixed (z, y, x, image) order, of their partials.
+__global__ void __launch_bounds__(256)
+    k_dep_combine(const double* __restrict__ dpart, double* __restrict__ out, const Geo g) {
+  for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < g.G;
+       gi += (int64_t)gridDim.x * blockDim.x) {
+    int j[3];
+    j[0] = (int)(gi % g.n[0]);
+    j[1] = (int)((gi / g.n[0]) % g.n[1]);
+    j[2] = (int)(gi / ((int64_t)g.n[0] * g.n[1]));
+    int cb[3][9], ce[3][9], cnt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cnt[a] = 0;
+      if (g.h[a] == 0) {
+        cb[a][0] = j[a] / g.b[a];
+        ce[a][0] = j[a] - cb[a][0] * g.b[a];
+        cnt[a] = 1;
+        continue;
+      }
+      const int bj = j[a] / g.b[a];
+      for (int db = -1; db <= 1; ++db) {
+        int bb = ((bj + db) % g.nb[a] + g.nb[a]) % g.nb[a];
+        bool dup = false;
+        for (int q = 0; q < cnt[a]; ++q) dup = dup || (cb[a][q] == bb);
+        if (dup) continue;
+        for (int m = -1; m <= 1; ++m) {
+          int ee = j[a] + m * g.n[a] - bb * g.b[a] + g.h[a];
+          if (ee >= 0 && ee < g.e[a] && cnt[a] < 9) {
+            cb[a][cnt[a]] = bb;
+            ce[a][cnt[a]] = ee;
+            cnt[a]++;
+          }
+        }
+      }
+    }
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int qz = 0; qz < cnt[2]; ++qz)
+      for (int qy = 0; qy < cnt[1]; ++qy)
+        for (int qx = 0; qx < cnt[0]; ++qx) {
+          const int64_t br = ((int64_t)cb[2][qz] * g.nb[1] + cb[1][qy]) * g.nb[0] + cb[0][qx];
+          const int t = (ce[2][qz] * g.e[1] + ce[1][qy]) * g.e[0] + ce[0][qx];
+          const double* pp = dpart + br * 3 * g.ev + t;
+          s0 += pp[0];
+          s1 += pp[g.ev];
+          s2 += pp[2 * (int64_t)g.ev];
+        }
+    out[gi] = s0;
+    out[g.G + gi] = s1;
+    out[2 * g.G + gi] = s2;
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 148 * 64) b = 148 * 64;
+  return (int)b;
+}
+
+template <int SHAPE, int DIM, bool DEP>
+cudaError_t brick_f64(part_ctx* c, double qm, double dt) {
+  auto kern = k_boris_brick_f64<SHAPE, DIM, DEP>;
+  const BrickSmem L = brick_smem(c->geo, 6, 8);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)L.total);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)c->geo.nbricks, kT, L.total, c->stream>>>(
+      c->tmap, c->geo, (double*)c->x, (double*)c->u, (const double*)c->w, c->n, c->cstart,
+      c->dpart, qm, dt, c->status);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+template <int SHAPE, int DIM>
+cudaError_t particles_f64(part_ctx* c, double qm, double dt, int nsteps) {
+  k_boris_particles_f64<SHAPE, DIM><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
+      (const double*)c->fpad, c->geo, (double*)c->x, (double*)c->u, c->n, qm, dt, nsteps,
+      c->status);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+template <int SHAPE, int DIM>
+cudaError_t dispatch_f64(part_ctx* c, double qm, double dt, int nsteps) {
+  if (c->sorted && nsteps == 1) {
+    return c->deposit_on ? brick_f64<SHAPE, DIM, true>(c, qm, dt)
+                         : brick_f64<SHAPE, DIM, false>(c, qm, dt);
+  }
+  return particles_f64<SHAPE, DIM>(c, qm, dt, nsteps);
+}
+
+}  // namespace
+
+cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps) {
+  if (c->n == 0) return cudaSuccess;
+  const int dim = c->geo.dim;
+  if (c->prec == PART_FP64) {
+    if (c->shape == PART_TSC)
+      return dim == 3 ? dispatch_f64<PART_TSC, 3>(c, qm, dt, nsteps)
+                      : dispatch_f64<PART_TSC, 2>(c, qm, dt, nsteps);
+    return dim == 3 ? dispatch_f64<PART_CIC, 3>(c, qm, dt, nsteps)
+                    : dispatch_f64<PART_CIC, 2>(c, qm, dt, nsteps);
+  }
+  return cudaErrorNotSupported;
+}
+
+cudaError_t launch_deposit_combine(part_ctx* c, double* out) {
+  k_dep_combine<<<grid_for(c->geo.G, 256), 256, 0, c->stream>>>(c->dpart, out, c->geo);
+  c->launches++;
+  return cudaGetLastError();
+}

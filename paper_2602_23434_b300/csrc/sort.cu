@@ -1,0 +1,327 @@
+// sort.cu -- bit-exact stable cell sort of the bound particles.
+//
+// keys  : brick-ordered cell key of every particle (integer arithmetic on the
+//         cell index j = floor((x - xmin) * (1/dx)), both roundings explicit).
+// radix : LSD radix sort of (key, index), 8-bit digits, reduce-then-scan:
+//         per-tile digit histograms -> exclusive scan (digit-major) -> stable
+//         per-tile scatter ranked with warp match masks.  No inter-CTA waits.
+// permute: every bound array is gathered through the permutation into the
+//         scratch buffer and copied back (in-place semantics for the caller).
+// cell_start: cs[k] = first sorted particle with key >= k, k in [0, nkeys].
+#include "part_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ uint32_t brick_key(const Geo& g, int jx, int jy, int jz) {
+  int bx = jx / g.b[0], by = jy / g.b[1], bz = jz / g.b[2];
+  int lx = jx - bx * g.b[0], ly = jy - by * g.b[1], lz = jz - bz * g.b[2];
+  int64_t brick = ((int64_t)bz * g.nb[1] + by) * g.nb[0] + bx;
+  return (uint32_t)(brick * g.V + (lz * g.b[1] + ly) * g.b[0] + lx);
+}
+
+__device__ __forceinline__ int cell_of(const Geo& g, int a, double xa, int* status) {
+  double s = __dmul_rn(__dsub_rn(xa, g.xmin[a]), g.inv_dx[a]);
+  if (!isfinite(s)) {
+    atomicOr(status, ST_NONFINITE);
+    return 0;
+  }
+  double f = floor(s);
+  if (f >= (double)g.n[a]) return g.n[a] - 1;
+  if (f < 0.0) return 0;
+  return (int)f;
+}
+
+__global__ void k_keys_f64(const double* __restrict__ x, int64_t n, Geo g,
+                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                           int* status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int j[3] = {0, 0, 0};
+    for (int a = 0; a < g.dim; ++a) j[a] = cell_of(g, a, x[a * n + i], status);
+    keys[i] = brick_key(g, j[0], j[1], j[2]);
+    vals[i] = (uint32_t)i;
+  }
+}
+
+__global__ void k_keys_cell(const int32_t* __restrict__ cell, int64_t n, Geo g,
+                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                            int* status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = cell[i];
+    if (c < 0 || c >= g.G) {
+      atomicOr(status, ST_DOMAIN);
+      c = c < 0 ? 0 : g.G - 1;
+    }
+    int jx = (int)(c % g.n[0]);
+    int64_t r = c / g.n[0];
+    int jy = (int)(r % g.n[1]);
+    int jz = (int)(r / g.n[1]);
+    keys[i] = brick_key(g, jx, jy, jz);
+    vals[i] = (uint32_t)i;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+    k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                 uint32_t* __restrict__ hist, int64_t ntiles) {
+  __shared__ uint32_t h[kRadix];
+  const int tid = threadIdx.x;
+  h[tid] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+  for (int it = 0; it < kSortItems; ++it) {
+    int64_t i = base + it * kSortThreads + tid;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & (kRadix - 1)], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)tid * ntiles + blockIdx.x] = h[tid];
+}
+
+// Block-wide exclusive scan of one value per thread (256 threads).
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot,
+                                                         uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t wv = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+    uint32_t wi = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < (int)(blockDim.x >> 5)) warp_tot[lane] = wi - wv;
+    if (lane == 31) *total = wi;
+  }
+  __syncthreads();
+  uint32_t r = warp_tot[warp] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+// Scan phase 1: sums of kScanBlock-element blocks.
+__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t* __restrict__ a, int64_t m,
+                                                     uint32_t* __restrict__ sums) {
+  __shared__ uint32_t wt[8];
+  __shared__ uint32_t tot;
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  uint32_t s = 0;
+  for (int k = 0; k < kScanBlock / 256; ++k) {
+    int64_t i = base + k * 256 + threadIdx.x;
+    if (i < m) s += a[i];
+  }
+  block_exclusive_scan(s, wt, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Scan phase 2: exclusive scan of the block sums in one CTA.
+__global__ void __launch_bounds__(256) k_scan_top(uint32_t* __restrict__ sums, int64_t nblk) {
+  __shared__ uint32_t wt[8];
+  __shared__ uint32_t tot;
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < nblk; base += 256) {
+    int64_t i = base + threadIdx.x;
+    uint32_t v = i < nblk ? sums[i] : 0;
+    uint32_t e = block_exclusive_scan(v, wt, &tot);
+    if (i < nblk) sums[i] = carry + e;
+    carry += tot;
+    __syncthreads();
+  }
+}
+
+// Scan phase 3: exclusive scan inside each block plus its block offset.
+__global__ void __launch_bounds__(256) k_scan_down(uint32_t* __restrict__ a, int64_t m,
+                                                   const uint32_t* __restrict__ sums) {
+  __shared__ uint32_t wt[8];
+  __shared__ uint32_t tot;
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  const int per = kScanBlock / 256;
+  uint32_t v[kScanBlock / 256];
+  uint32_t s = 0;
+  for (int k = 0; k < per; ++k) {
+    int64_t i = base + (int64_t)threadIdx.x * per + k;
+    v[k] = i < m ? a[i] : 0;
+    s += v[k];
+  }
+  uint32_t e = block_exclusive_scan(s, wt, &tot) + sums[blockIdx.x];
+  for (int k = 0; k < per; ++k) {
+    int64_t i = base + (int64_t)threadIdx.x * per + k;
+    if (i < m) a[i] = e;
+    e += v[k];
+  }
+}
+
+// Stable scatter of one radix pass.  Warp w of the tile owns the contiguous
+// key segment [w*32*ITEMS, (w+1)*32*ITEMS); keys are ranked within the warp
+// in index order, then offset by the counts of lower warps and by the scanned
+// tile histogram.
+__global__ void __launch_bounds__(kSortThreads)
+    k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                    uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                    int shift, const uint32_t* __restrict__ hscan, int64_t ntiles) {
+  constexpr int W = kSortThreads / 32;
+  __shared__ uint32_t wh[W][kRadix];
+  __shared__ uint32_t tbase[kRadix];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < W * kRadix; i += kSortThreads) (&wh[0][0])[i] = 0;
+  tbase[tid] = hscan[(int64_t)tid * ntiles + blockIdx.x];
+  __syncthreads();
+  const int64_t seg = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * 32 * kSortItems;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t kk[kSortItems], vv[kSortItems], pos[kSortItems];
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t i = seg + r * 32 + lane;
+    bool valid = i < n;
+    uint32_t key = valid ? kin[i] : 0u;
+    uint32_t val = valid ? vin[i] : 0u;
+    uint32_t d = valid ? ((key >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t rank = __popc(peers & lt);
+    int leader = __ffs(peers) - 1;
+    uint32_t before = valid ? wh[warp][d] : 0u;
+    __syncwarp();
+    if (valid && lane == leader) wh[warp][d] = before + __popc(peers);
+    __syncwarp();
+    kk[r] = key;
+    vv[r] = val;
+    pos[r] = before + rank;
+  }
+  __syncthreads();
+  {
+    uint32_t run = 0;
+    for (int w = 0; w < W; ++w) {
+      uint32_t t = wh[w][tid];
+      wh[w][tid] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t i = seg + r * 32 + lane;
+    if (i < n) {
+      uint32_t d = (kk[r] >> shift) & (kRadix - 1);
+      uint32_t dst = tbase[d] + wh[warp][d] + pos[r];
+      if (dst < (uint64_t)n) {  // always true for a consistent histogram
+        kout[dst] = kk[r];
+        vout[dst] = vv[r];
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_gather(const T* __restrict__ src, T* __restrict__ dst,
+                         const uint32_t* __restrict__ perm, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+  {
+    const uint32_t s = perm[i];
+    dst[i] = s < (uint64_t)n ? src[s] : T(0);
+  }
+}
+
+__global__ void k_cell_start(const uint32_t* __restrict__ sk, int64_t n, int64_t nkeys,
+                             uint32_t* __restrict__ cs) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = i == 0 ? 0 : (int64_t)sk[i - 1] + 1;
+    int64_t hi = i == n ? nkeys : (int64_t)sk[i];
+    if (hi > nkeys) hi = nkeys;
+    for (int64_t c = lo; c <= hi; ++c) cs[c] = (uint32_t)i;
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 148 * 64) b = 148 * 64;
+  return (int)b;
+}
+
+template <typename T>
+cudaError_t permute_plane(part_ctx* c, T* arr, const uint32_t* perm) {
+  const int64_t n = c->n;
+  k_gather<T><<<grid_for(n, 256), 256, 0, c->stream>>>(arr, (T*)c->tmp, perm, n);
+  c->launches++;
+  return cudaMemcpyAsync(arr, c->tmp, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream);
+}
+
+}  // namespace
+
+cudaError_t launch_sort(part_ctx* c) {
+  const Geo& g = c->geo;
+  const int64_t n = c->n;
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  if (n > 0) {
+    if (c->mode == PART_BORIS && c->prec == PART_MIXED)
+      k_keys_cell<<<grid_for(n, 256), 256, 0, s>>>((const int32_t*)c->x, n, g, c->keys[0],
+                                                   c->vals[0], c->status);
+    else
+      k_keys_f64<<<grid_for(n, 256), 256, 0, s>>>((const double*)c->x, n, g, c->keys[0],
+                                                  c->vals[0], c->status);
+    c->launches++;
+    int bits = 0;
+    while (bits < 32 && ((int64_t)1 << bits) < g.nkeys) ++bits;
+    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    const int64_t m = ntiles * kRadix;
+    const int64_t nblk = (m + kScanBlock - 1) / kScanBlock;
+    int cur = 0;
+    for (int shift = 0; shift < bits; shift += kRadixBits) {
+      k_radix_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(c->keys[cur], n, shift, c->hist,
+                                                             ntiles);
+      k_scan_reduce<<<(unsigned)nblk, 256, 0, s>>>(c->hist, m, c->hsum);
+      k_scan_top<<<1, 256, 0, s>>>(c->hsum, nblk);
+      k_scan_down<<<(unsigned)nblk, 256, 0, s>>>(c->hist, m, c->hsum);
+      k_radix_scatter<<<(unsigned)ntiles, kSortThreads, 0, s>>>(
+          c->keys[cur], c->vals[cur], c->keys[cur ^ 1], c->vals[cur ^ 1], n, shift, c->hist,
+          ntiles);
+      c->launches += 5;
+      cur ^= 1;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const uint32_t* perm = c->vals[cur];
+    const uint32_t* sk = c->keys[cur];
+    k_cell_start<<<grid_for(n + 1, 256), 256, 0, s>>>(sk, n, g.nkeys, c->cstart);
+    c->launches++;
+    // permute the bound arrays
+    if (c->mode == PART_BORIS && c->prec == PART_FP64) {
+      for (int a = 0; a < 3; ++a) {
+        if ((e = permute_plane<double>(c, (double*)c->x + a * n, perm))) return e;
+        if ((e = permute_plane<double>(c, (double*)c->u + a * n, perm))) return e;
+      }
+      if (c->w && (e = permute_plane<double>(c, (double*)c->w, perm))) return e;
+    } else if (c->mode == PART_BORIS) {
+      if ((e = permute_plane<int32_t>(c, (int32_t*)c->x, perm))) return e;
+      for (int a = 0; a < 3; ++a) {
+        if ((e = permute_plane<float>(c, (float*)c->off + a * n, perm))) return e;
+        if ((e = permute_plane<float>(c, (float*)c->u + a * n, perm))) return e;
+      }
+      if (c->w && (e = permute_plane<float>(c, (float*)c->w, perm))) return e;
+    } else {
+      for (int a = 0; a < 3; ++a)
+        if ((e = permute_plane<double>(c, (double*)c->x + a * n, perm))) return e;
+      for (int b = 0; b < c->nbins; ++b) {
+        if ((e = permute_plane<double>(c, c->chi + (int64_t)b * n, perm))) return e;
+        if ((e = permute_plane<double>(c, c->eng + (int64_t)b * n, perm))) return e;
+      }
+      if (c->n_old && (e = permute_plane<double>(c, c->n_old, perm))) return e;
+    }
+    if (c->id && (e = permute_plane<uint64_t>(c, c->id, perm))) return e;
+  } else {
+    k_cell_start<<<1, 256, 0, s>>>(c->keys[0], 0, g.nkeys, c->cstart);
+    c->launches++;
+  }
+  return cudaGetLastError();
+}

@@ -1,0 +1,62 @@
+"""The C-ABI library loads without a GPU and exports what include/part.h
+declares; the host-only entry points validate their arguments.  No compute
+call is made here."""
+import ctypes as C
+
+import pytest
+
+from paper_2602_23434_b300 import _lib as P
+from paper_2602_23434_b300.build import build
+
+
+@pytest.fixture(scope="module")
+def L():
+    build()
+    return P.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = P.header_functions()
+    assert "part_gather_push" in names and "spec_update" in names and len(names) >= 16
+    for nm in names:
+        assert hasattr(L, nm), nm
+
+
+def test_brick_dims_and_key_space(L):
+    b = (C.c_int * 3)()
+    nk = C.c_int64()
+    g = P.make_grid(3, 128)
+    assert L.part_brick_dims(C.byref(g), b, C.byref(nk)) == 0
+    assert tuple(b) == (8, 8, 8) and nk.value == 128 ** 3
+    g = P.make_grid(3, (20, 20, 20))
+    assert L.part_brick_dims(C.byref(g), b, C.byref(nk)) == 0
+    assert nk.value == 27 * 512                    # partial bricks keep full key blocks
+    g = P.make_grid(2, 64)
+    assert L.part_brick_dims(C.byref(g), b, C.byref(nk)) == 0
+    assert tuple(b) == (16, 16, 1) and nk.value == 64 * 64
+
+
+def test_workspace_size_and_validation(L):
+    sz = C.c_size_t()
+    g = P.make_grid(3, 128)
+    assert L.part_workspace_size(C.byref(g), P.FP64, P.BORIS, 1 << 24, 0, C.byref(sz)) == 0
+    assert 0.5e9 < sz.value < 1e9
+    assert L.part_workspace_size(C.byref(g), P.FP64, P.LP_RK2, 1 << 22, 128, C.byref(sz)) == 0
+    bad = P.make_grid(3, 16)
+    bad.dim = 4
+    assert L.part_workspace_size(C.byref(bad), P.FP64, P.BORIS, 10, 0, C.byref(sz)) == 1
+    bad = P.make_grid(3, 16)
+    bad.periodic[1] = 0
+    assert L.part_workspace_size(C.byref(bad), P.FP64, P.BORIS, 10, 0, C.byref(sz)) == 6
+    bad = P.make_grid(3, 16)
+    bad.dx[0] = 0.0
+    assert L.part_workspace_size(C.byref(bad), P.FP64, P.BORIS, 10, 0, C.byref(sz)) == 1
+    # LP mode keeps FP64 spectra
+    assert L.part_workspace_size(C.byref(g), P.MIXED, P.LP_RK2, 10, 128, C.byref(sz)) == 6
+    assert L.part_workspace_size(C.byref(g), P.FP64, P.LP_RK2, 10, 0, C.byref(sz)) == 1
+    assert b"nbins" in L.part_last_error(None)
+    # part_init refuses a NULL / misaligned workspace before touching CUDA
+    ctx = C.c_void_p()
+    assert L.part_init(C.byref(ctx), C.byref(g), 0, 2, 0, 10, 0, None, 0, None) == 1
+    assert L.part_init(C.byref(ctx), C.byref(g), 0, 2, 0, 10, 0, C.c_void_p(0x1001), 1 << 30,
+                       None) == 1

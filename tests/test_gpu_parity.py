@@ -1,0 +1,261 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (FP64 path): cell keys, sort permutation and cell_start bit-exact;
+particle state 1e-12 relative per step, max(|ref|, scale) normalised;
+deposit 1e-12 relative to the sum of |contributions| to the cell; deposit
+run-to-run bitwise.  Differences come only from FMA contraction and the
+order of sums, so 1e-12 leaves three orders of magnitude of margin.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2602_23434_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2602_23434_b300 import _lib as P  # noqa: E402  (loads libpart.so lazily)
+
+
+def _grids(dim, n):
+    return O.make_grid(dim, (n, n, n)), P.make_grid(dim, n)
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def _host(t):
+    return t.detach().cpu().numpy()
+
+
+def _pdiff(a, b, L=2.0):
+    d = a - b
+    return d - L * np.round(d / L)
+
+
+def _rel(gpu, ref, scale):
+    return np.max(np.abs(gpu - ref) / np.maximum(np.abs(ref), scale)) if gpu.size else 0.0
+
+
+CASES = [(3, 20, 8), (2, 40, 16)]     # (dim, n, particles per cell): partial bricks
+
+
+@pytest.mark.parametrize("dim,n,ppc", CASES + [(3, 8, 3), (3, 5, 2)])
+def test_sort_bit_exact(dim, n, ppc):
+    og, pg = _grids(dim, n)
+    G = n ** dim
+    N = G * ppc + 7                         # ragged tail
+    x, u, w, ids = synth.particles(dim, None, N, 11 + n)
+    p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=N)
+    xd, ud, wd, idd = _dev(x), _dev(u), _dev(w), torch.as_tensor(ids.astype(np.int64)).cuda()
+    p.bind(N, xd, u=ud, w=wd, ids=idd)
+    p.sort()
+    cs = _host(p.cell_start())
+    p.sync()
+    keys = O.keys(og, p.brick, x)
+    perm = O.stable_sort(keys)
+    assert np.array_equal(_host(idd), ids[perm].astype(np.int64))
+    assert np.array_equal(_host(xd), x[:, perm])
+    assert np.array_equal(_host(ud), u[:, perm])
+    assert np.array_equal(cs, O.cell_start(p.nkeys, keys[perm]).astype(np.int64))
+
+
+@pytest.mark.parametrize("N", [0, 1, 31, 33, 4096, 4097])
+def test_sort_edge_counts(N):
+    og, pg = _grids(3, 16)
+    x, u, w, ids = synth.particles(3, None, max(N, 1), 5)
+    x, u, ids = x[:, :N].copy(), u[:, :N].copy(), ids[:N].copy()
+    p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=max(N, 1))
+    xd, ud = _dev(x if N else np.zeros((3, 1))), _dev(u if N else np.zeros((3, 1)))
+    idd = torch.as_tensor(ids.astype(np.int64) if N else np.zeros(1, np.int64)).cuda()
+    p.bind(N, xd, u=ud, ids=idd)
+    p.sort()
+    cs = _host(p.cell_start())
+    p.sync()
+    keys = O.keys(og, p.brick, x) if N else np.zeros(0, np.uint32)
+    perm = O.stable_sort(keys)
+    if N:
+        assert np.array_equal(_host(idd)[:N], ids[perm].astype(np.int64))
+    assert np.array_equal(cs, O.cell_start(p.nkeys, keys[perm]).astype(np.int64))
+
+
+def _boris_case(dim, n, ppc, shape, seed, turbulent=True):
+    og, pg = _grids(dim, n)
+    G = n ** dim
+    N = G * ppc + 13
+    if turbulent:
+        f = synth.em_fields(dim, n, seed, v_rms=0.05)
+    else:
+        f = synth.uniform_em_fields(dim, n, B=(0.0, 0.0, 1.0))
+    x, u, w, ids = synth.particles(dim, None, N, seed + 1, u_th=0.3)
+    w = np.random.default_rng(seed).uniform(0.5, 2.0, N)
+    return og, pg, f.reshape(6, -1), x, u, w, ids, N
+
+
+@pytest.mark.parametrize("dim,n,ppc", CASES)
+@pytest.mark.parametrize("shape", [P.TSC, P.CIC])
+def test_boris_push_and_deposit_fp64(dim, n, ppc, shape):
+    og, pg, f, x, u, w, ids, N = _boris_case(dim, n, ppc, shape, 21)
+    qm, dt = 1.0, 0.5 * (2.0 / n)
+    p = P.Part(pg, P.FP64, shape, P.BORIS, capacity=N)
+    p.set_fields(_dev(f))
+    xd, ud, wd = _dev(x), _dev(u), _dev(w)
+    idd = torch.as_tensor(ids.astype(np.int64)).cuda()
+    p.bind(N, xd, u=ud, w=wd, ids=idd)
+    p.enable_deposit(True)
+    p.sort()
+    torch.cuda.synchronize()
+    xs, us, ws = _host(xd), _host(ud), _host(wd)      # sorted input state
+    p.gather_push(qm, dt, 1)
+    out = torch.empty((3, og.n[0] * og.n[1] * og.n[2]), dtype=torch.float64, device="cuda")
+    p.deposit(out)
+    p.sync()
+    xr, ur, F, xo = O.boris_step(og, shape, f, xs, us, ws, qm, dt, True)
+    assert np.max(np.abs(_pdiff(_host(xd), xr))) <= 1e-12 * 2.0
+    assert _rel(_host(ud), ur, np.max(np.abs(ur))) <= 1e-12
+    dref = O.deposit(og, shape, xo, F)
+    dabs = O.deposit(og, shape, xo, np.abs(F))
+    dg = _host(out)
+    assert np.max(np.abs(dg - dref) / np.maximum(dabs, 1e-300)) <= 1e-12
+    # bitwise reproducible: same inputs, same bits
+    xd2, ud2 = _dev(xs), _dev(us)
+    p.bind(N, xd2, u=ud2, w=_dev(ws))
+    p.sort()
+    p.gather_push(qm, dt, 1)
+    out2 = torch.empty_like(out)
+    p.deposit(out2)
+    p.sync()
+    assert torch.equal(out, out2)
+    assert torch.equal(xd, xd2) and torch.equal(ud, ud2)
+
+
+def test_boris_uniform_field_config_shape():
+    """2D 64^2, B = z, E = 0, fused multi-step particle-order kernel vs 20
+    oracle steps (the 2D uniform-field workload, scaled down in steps)."""
+    og, pg, f, x, u, w, ids, N = _boris_case(2, 64, 16, P.TSC, 31, turbulent=False)
+    qm, dt, steps = 1.0, 0.1, 20
+    p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=N)
+    p.set_fields(_dev(f))
+    xd, ud = _dev(x), _dev(u)
+    p.bind(N, xd, u=ud)
+    p.gather_push(qm, dt, steps)
+    p.sync()
+    xr, ur = x, u
+    for _ in range(steps):
+        xr, ur, _, _ = O.boris_step(og, P.TSC, f, xr, ur, None, qm, dt)
+    assert np.max(np.abs(_pdiff(_host(xd), xr))) <= 1e-12 * 2.0 * steps
+    assert _rel(_host(ud), ur, np.max(np.abs(ur))) <= 1e-12 * steps
+    # |u| conserved by the rotation (E = 0)
+    assert np.max(np.abs(np.linalg.norm(_host(ud), axis=0) / np.linalg.norm(u, axis=0) - 1)) \
+        < 1e-13
+
+
+@pytest.mark.parametrize("dim,n", [(3, 20), (2, 40)])
+def test_lp_step_and_spectra(dim, n):
+    og, pg = _grids(dim, n)
+    vel, rho, B = synth.fluid_snapshot(dim, n, 41, v_rms=0.05)
+    f7 = np.concatenate([vel, rho, B]).reshape(7, -1)
+    N = n ** dim * 2 + 5
+    nb = 128
+    p = P.Part(pg, P.FP64, P.TSC, P.LP_RK2, capacity=N, nbins=nb)
+    p.set_fields(_dev(f7))
+    xd = torch.zeros((3, N), dtype=torch.float64, device="cuda")
+    chi = torch.zeros((nb, N), dtype=torch.float64, device="cuda")
+    eng = torch.zeros_like(chi)
+    nold = torch.zeros(N, dtype=torch.float64, device="cuda")
+    p.bind(N, xd, chi=chi, eng=eng, n_old=nold)
+    p.init_particles(77, 0.0, 1.0, 1e6, 2.2, 1e-6)
+    p.sync()
+    # initialisation vs the oracle
+    xo, _, _, _ = O.init_particles(og, N, 77, 0.0)
+    assert np.array_equal(_host(xd), xo)
+    e1, c1 = O.init_spectrum(nb, 1.0, 1e6, 2.2, 1e-6)
+    assert _rel(_host(eng), e1[:, None] * np.ones(N), 0) <= 1e-14
+    assert _rel(_host(chi), c1[:, None] * np.ones(N), 0) <= 1e-13
+    r0 = np.array([O.gather(og, P.TSC, rho.reshape(1, -1), xo[:, i])[0] for i in range(N)])
+    assert _rel(_host(nold), r0, 0) <= 1e-13
+    # one RK2 step + spectral update
+    dt, c0 = 0.5 * 2.0 / n, 2e-3
+    x0, ch0, en0, no0 = _host(xd), _host(chi), _host(eng), _host(nold)
+    p.gather_push(0.0, dt, 1)
+    p.spec_update(dt, c0, 0.1)
+    p.sync()
+    xr, n_new, b2m, gam = O.lp_rk2_step(og, P.TSC, vel.reshape(3, -1), rho.reshape(1, -1),
+                                        B.reshape(3, -1), x0, dt)
+    assert np.max(np.abs(_pdiff(_host(xd), xr))) <= 1e-12 * 2.0
+    chr_, enr, nor = O.spec_update(ch0, en0, no0, n_new, b2m, gam, dt, c0, 0.1)
+    assert _rel(_host(eng), enr, 0) <= 1e-12
+    assert _rel(_host(chi), chr_, 0) <= 1e-12
+    assert _rel(_host(nold), nor, 0) <= 1e-12
+
+
+def test_init_particles_fp64_and_mixed():
+    og, pg = _grids(3, 24)
+    N = 50001
+    p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=N)
+    xd = torch.zeros((3, N), dtype=torch.float64, device="cuda")
+    ud = torch.zeros_like(xd)
+    wd = torch.zeros(N, dtype=torch.float64, device="cuda")
+    idd = torch.zeros(N, dtype=torch.int64, device="cuda")
+    p.bind(N, xd, u=ud, w=wd, ids=idd)
+    p.init_particles(1235, 0.1)
+    p.sync()
+    xo, uo, wo, io = O.init_particles(og, N, 1235, 0.1)
+    assert np.array_equal(_host(xd), xo)           # positions decide cells: bit-exact
+    assert _rel(_host(ud), uo, 0.1) <= 1e-14
+    assert np.array_equal(_host(wd), wo) and np.array_equal(_host(idd), io.astype(np.int64))
+    pm = P.Part(pg, P.MIXED, P.TSC, P.BORIS, capacity=N)
+    cell = torch.zeros(N, dtype=torch.int32, device="cuda")
+    off = torch.zeros((3, N), dtype=torch.float32, device="cuda")
+    uf = torch.zeros((3, N), dtype=torch.float32, device="cuda")
+    pm.bind(N, cell, off=off, u=uf)
+    pm.init_particles(1235, 0.1)
+    pm.sync()
+    c = _host(cell).astype(np.int64)
+    j = np.stack([c % 24, (c // 24) % 24, c // 576])
+    pos = -1.0 + (j + 0.5 + _host(off)) * (2.0 / 24)
+    assert np.max(np.abs(pos - xo)) <= 2.0 / 24 * 6e-8
+    assert np.all(np.abs(_host(off)) <= 0.5)
+    assert _rel(_host(uf).astype(np.float64), uo, 0.1) <= 1e-6
+
+
+def test_error_paths():
+    og, pg = _grids(3, 16)
+    N = 1000
+    f = synth.uniform_em_fields(3, 16).reshape(6, -1)
+    x, u, w, ids = synth.particles(3, None, N, 3)
+    p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=N)
+    with pytest.raises(P.PartError) as e:
+        p.gather_push(1.0, 0.1, 1)                   # no particles bound
+    assert e.value.name == "PART_EINVAL"
+    xd, ud = _dev(x), _dev(u)
+    p.bind(N, xd, u=ud)
+    with pytest.raises(P.PartError):
+        p.gather_push(1.0, 0.1, 1)                   # no fields
+    p.set_fields(_dev(f))
+    p.enable_deposit(True)
+    with pytest.raises(P.PartError) as e:
+        p.gather_push(1.0, 0.1, 1)                   # deposit without sort
+    assert "part_sort" in str(e.value)
+    with pytest.raises(P.PartError):
+        p.bind(N + 1, xd, u=ud)                      # over capacity
+    with pytest.raises(P.PartError):
+        p.set_fields(_dev(f[:5]))                    # wrong ncomp
+    # a particle moved out of its sorted cell -> PART_EDOMAIN, nothing faults
+    p.bind(N, xd, u=ud)
+    p.sort()
+    xd[0, 0] = xd[0, 0] + 0.3          # one cell away from its sorted cell
+    p.gather_push(1.0, 0.01, 1)
+    with pytest.raises(P.PartError) as e:
+        p.sync()
+    assert e.value.name == "PART_EDOMAIN"
+    # non-finite state -> PART_ENONFINITE
+    p.enable_deposit(False)
+    ud[1, 3] = float("nan")
+    p.gather_push(1.0, 0.01, 1)
+    with pytest.raises(P.PartError) as e:
+        p.sync()
+    assert e.value.name == "PART_ENONFINITE"
+    p.sync()                                         # status cleared
