@@ -1,0 +1,458 @@
+#!/usr/bin/env python3
+"""Benchmark of the particle advance on one B300 (or N independent replicas).
+
+Headline workload: 3D periodic 128^3 grid, turbulent B (64 Kolmogorov modes,
+dB/B0 = 1), E = -v x B (solenoidal v, rms 0.01 c), 8 particles per cell
+(16,777,216), relativistic Boris push with TSC gather and the deterministic
+TSC deposit of the force density, FP64.  One step = part_sort + part_gather_push
+(fused deposit) + part_deposit.  Metric: particle-steps/s.
+
+Also reported on the same line: the Lagrangian-particle workload (128^3 fluid
+snapshot, 4M LPs x 128 bins, RK2 + spectral update, FP64), the 2D
+uniform-field workload (64^2, 65,536 particles, 100 fused steps), the FP64
+roofline of the dominant kernel, end-to-end throughput through host buffers,
+and the oracle timed on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs its own replica (no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2602_23434_b300 import synth  # noqa: E402
+
+METRIC = ("particle-steps/s and % HBM roofline, FP64 vs mixed FP32 at stated error; "
+          "serving p50/p99")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_NOMINAL_TFLOPS = 1.25      # B300 dense FP64 (non-tensor), nominal
+FALLBACK_HBM_GBS = 6400.0
+
+# Algorithmic FP64 flops of one fused particle step (TSC, 3D, deposit on),
+# FMA = 2 flops: cell coordinates 12, weights 24, gather 27*(2 mul) + 27*6*2
+# = 360 (with the 9 wz*wy products counted in the 36 products), Boris 58,
+# gamma + drift 17, force + deposit 7 + 9 + 27*3*2 = 178.
+FLOP_PER_PSTEP_BORIS_DEP = 12 + 24 + 360 + 58 + 17 + 178
+# Algorithmic HBM bytes of one particle step: state x,u read+write 96, w read 8,
+# field stencil 6*8 B per cell / 8 particles per cell = 6, deposit 3*8 / 8 = 3.
+BYTES_PER_PSTEP_BORIS_DEP = 96 + 8 + 6 + 3
+# LP step: x r/w 48, chi+eng r/w 4096 (128 bins), n_old r/w 16, samples w+r 48,
+# fields: 7 comps * 8 B per cell / 2 LPs per cell, 3 gathers at ~one cell = 84
+BYTES_PER_LPSTEP = 48 + 4096 + 16 + 48 + 84
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- workloads
+def dt_turbulent(f6, n: int, qm: float = 1.0):
+    bmax = float(np.sqrt((f6[3:] ** 2).sum(axis=0)).max())
+    return min(0.1 / (qm * bmax), 0.5 * (2.0 / n))
+
+
+class BorisWorkload:
+    """Headline FP64 workload: 128^3 turbulent, 8 ppc, Boris + TSC + deposit."""
+
+    def __init__(self, torch, P, n=128, ppc=8, seed=1236):
+        self.torch, self.P = torch, P
+        self.n = n
+        self.N = n ** 3 * ppc
+        self.seed = seed
+        f = synth.em_fields(3, n, seed)
+        self.dt = dt_turbulent(f, n)
+        self.qm = 1.0
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.f = torch.as_tensor(f.reshape(6, -1)).to(dev)
+        self.part = P.Part(P.make_grid(3, n), P.FP64, P.TSC, P.BORIS, capacity=self.N)
+        self.part.set_fields(self.f)
+        self.x = torch.empty((3, self.N), dtype=torch.float64, device=dev)
+        self.u = torch.empty_like(self.x)
+        self.w = torch.empty(self.N, dtype=torch.float64, device=dev)
+        self.ids = torch.empty(self.N, dtype=torch.int64, device=dev)
+        self.out = torch.empty((3, n ** 3), dtype=torch.float64, device=dev)
+        self.part.bind(self.N, self.x, u=self.u, w=self.w, ids=self.ids)
+        self.part.init_particles(seed, 0.1)
+        self.part.enable_deposit(True)
+        self.part.sync()
+
+    def step(self, ev=None):
+        p = self.part
+        p.sort()
+        if ev is not None:
+            ev[0].record(p.stream)
+        p.gather_push(self.qm, self.dt, 1)
+        if ev is not None:
+            ev[1].record(p.stream)
+        p.deposit(self.out)
+
+
+def time_steps(torch, stream, fn, K: int, W: int, per_step_events=False):
+    for _ in range(W):
+        fn(None)
+    torch.cuda.synchronize()
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)] if per_step_events else [None] * K
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(K):
+        fn(kev[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    kern_ms = [a.elapsed_time(b) for a, b in kev] if per_step_events else []
+    return total_ms, kern_ms
+
+
+def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1237):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    vel, rho, B = synth.fluid_snapshot(3, n, seed)
+    f7 = torch.as_tensor(np.concatenate([vel, rho, B]).reshape(7, -1)).to(dev)
+    p = P.Part(P.make_grid(3, n), P.FP64, P.TSC, P.LP_RK2, capacity=nlp, nbins=nb)
+    p.set_fields(f7)
+    x = torch.empty((3, nlp), dtype=torch.float64, device=dev)
+    chi = torch.empty((nb, nlp), dtype=torch.float64, device=dev)
+    eng = torch.empty_like(chi)
+    nold = torch.empty(nlp, dtype=torch.float64, device=dev)
+    p.bind(nlp, x, chi=chi, eng=eng, n_old=nold)
+    p.init_particles(seed, 0.0, 1.0, 1e6, 2.2, 1e-6)
+    p.sort()                                   # once: locality of the field gathers
+    p.sync()
+    dt = 0.5 * 2.0 / n
+    # cooling break near eps ~ 1e3 after 100 steps with <U_B> = (B0^2 + dB^2)/2 = 1
+    c0 = 1.0 / (1e3 * 1.0 * 100 * dt)
+    evs = []
+
+    def step(ev):
+        p.gather_push(0.0, dt, 1)
+        if ev is not None:
+            ev[0].record(p.stream)
+        p.spec_update(dt, c0, 0.0)
+        if ev is not None:
+            ev[1].record(p.stream)
+
+    l0 = p.launches()
+    total, kern = time_steps(torch, p.stream, step, K, W, per_step_events=True)
+    p.sync()
+    launches = (p.launches() - l0) * K // (K + W)
+    ms = total / K
+    spec_ms = float(np.mean(kern))
+    del chi, eng
+    return {"workload": f"LP 3D {n}^3 snapshot, {nlp} LPs x {nb} bins, RK2 + TSC + spectra, "
+                        "FP64",
+            "value": nlp * K / (total / 1e3), "unit": "LP-steps/s", "ms_per_step": ms,
+            "spec_update_ms": spec_ms,
+            "spec_update_GBps": nlp * 2 * 2 * nb * 8 / (spec_ms / 1e3) / 1e9,
+            "c0": c0, "dt": dt, "gpu_launches_per_step": launches}
+
+
+def run_2d(torch, P, n=64, ppc=16, steps=100, seed=1235):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    N = n * n * ppc
+    f = torch.as_tensor(synth.uniform_em_fields(2, n, B=(0, 0, 1.0)).reshape(6, -1)).to(dev)
+    p = P.Part(P.make_grid(2, n), P.FP64, P.TSC, P.BORIS, capacity=N)
+    p.set_fields(f)
+    x = torch.empty((3, N), dtype=torch.float64, device=dev)
+    u = torch.empty_like(x)
+    p.bind(N, x, u=u)
+    p.init_particles(seed, 0.1)
+    p.sort()
+    p.sync()
+    dt = 0.1
+
+    def run(ev):
+        p.gather_push(1.0, dt, steps)
+
+    total, _ = time_steps(torch, p.stream, run, 5, 3)
+    p.sync()
+    return {"workload": f"2D {n}^2 uniform B, {N} particles, {steps} fused Boris steps, FP64",
+            "value": N * steps * 5 / (total / 1e3), "unit": "particle-steps/s",
+            "ms_per_run": total / 5}
+
+
+# ----------------------------------------------------------------------------- e2e
+def run_e2e(torch, wl: BorisWorkload, K: int):
+    """Same step through the C ABI with the particle state in pinned host
+    memory: H2D of x, u, w, the step, D2H of x, u and the deposited grid."""
+    N = wl.N
+    hx = torch.empty((3, N), dtype=torch.float64, pin_memory=True)
+    hu = torch.empty_like(hx, pin_memory=True)
+    hw = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    hout = torch.empty(wl.out.shape, dtype=torch.float64, pin_memory=True)
+    hx.copy_(wl.x)
+    hu.copy_(wl.u)
+    hw.copy_(wl.w)
+    s = wl.part.stream
+    h2d = (hx.numel() + hu.numel() + hw.numel()) * 8
+    d2h = (hx.numel() + hu.numel() + hout.numel()) * 8
+
+    def one(ev):
+        with torch.cuda.stream(s):
+            wl.x.copy_(hx, non_blocking=True)
+            wl.u.copy_(hu, non_blocking=True)
+            wl.w.copy_(hw, non_blocking=True)
+            wl.step()
+            hx.copy_(wl.x, non_blocking=True)
+            hu.copy_(wl.u, non_blocking=True)
+            hout.copy_(wl.out, non_blocking=True)
+        s.synchronize()
+
+    one(None)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        one(None)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": N * K / dt, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+# ----------------------------------------------------------------------------- oracle
+def cpu_baseline(budget_s: float = 12.0, n=128, seed=1236):
+    """The oracle as it stands (OpenMP over particles in the push; sort and
+    deposit sequential), one step = keys + stable sort + permute + Boris step
+    + deposit, on a sample of the headline workload's particles."""
+    from oracle import oracle as O
+    f = synth.em_fields(3, n, seed).reshape(6, -1)
+    g = O.make_grid(3, (n, n, n))
+    dt = dt_turbulent(f.reshape(6, n, n, n), n)
+    brick = (8, 8, 8)
+
+    def one_step(x, u, w):
+        k = O.keys(g, brick, x)
+        perm = O.stable_sort(k)
+        x, u, w = x[:, perm], u[:, perm], w[perm]
+        x1, u1, F, xo = O.boris_step(g, O.TSC, f, x, u, w, 1.0, dt, True)
+        O.deposit(g, O.TSC, xo, F)
+        return x1, u1, w
+
+    Ns = 1 << 16
+    x, u, w, _ = O.init_particles(g, Ns, seed, 0.1)
+    t0 = time.perf_counter()
+    one_step(x, u, w)
+    t1 = time.perf_counter() - t0
+    # scale the sample so that ~budget seconds of steps are timed
+    steps = 3
+    Ns = int(min(1 << 22, max(1 << 16, Ns * budget_s / steps / max(t1, 1e-3))))
+    x, u, w, _ = O.init_particles(g, Ns, seed, 0.1)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        x, u, w = one_step(x, u, w)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": Ns * steps / el, "unit": "particle-steps/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{Ns} of the 16,777,216 particles of the 128^3 workload, {steps} "
+                      f"steps (keys, stable sort, permute, Boris step, deposit), {el:.1f} s"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cb = cpu_baseline(budget_s=max(5.0, 4.0 * args.steps / max(args.steps, 1)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"],
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "3D periodic 128^3 turbulent B, E=-vxB, 16,777,216 "
+                                   "particles (8/cell), Boris + TSC gather + TSC deposit, "
+                                   "FP64 (oracle, host cores, bounded sample)"},
+            "cpu_baseline": {"value": cb["value"], "unit": cb["unit"], "cores": cb["cores"],
+                             "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "vs_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-extras", action="store_true", help="headline workload only")
+    ap.add_argument("--grid", type=int, default=128,
+                    help="cells per axis of the headline workload (128 = the stated one; "
+                         "smaller only for profiling captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    from paper_2602_23434_b300 import _lib as P
+    from paper_2602_23434_b300.build import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        build()
+    if dist:
+        dist.barrier()
+
+    wl = BorisWorkload(torch, P, n=args.grid)
+    stream = wl.part.stream
+    l0 = wl.part.launches()
+    # warm-up
+    for _ in range(args.warmup):
+        wl.step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    l1 = wl.part.launches()
+    total_ms, kern_ms = time_steps(torch, stream, wl.step, args.steps, 0, per_step_events=True)
+    launches = wl.part.launches() - l1
+    clocks = clk.stop()
+    wl.part.sync()
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = wl.N * args.steps * world / (total_ms / 1e3)
+    kmean = float(np.mean(kern_ms))
+    hbm, hbm_kind = peaks()
+    achieved_tf = FLOP_PER_PSTEP_BORIS_DEP * wl.N / (kmean / 1e3) / 1e12
+    achieved_gbs = BYTES_PER_PSTEP_BORIS_DEP * wl.N / (kmean / 1e3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "3D periodic 128^3, B = z + turbulent dB (64 Kolmogorov modes, "
+                               "dB/B0 = 1), E = -v x B (solenoidal v, rms 0.01 c), "
+                               "16,777,216 particles (8/cell), u_th = 0.1, step = sort + "
+                               "Boris/TSC gather + TSC force deposit, FP64",
+                   "particles": wl.N, "grid": [args.grid] * 3, "dt": wl.dt,
+                   "l2": "inputs larger than L2 (about 2 GB of state, fields and deposit "
+                         "touched per step vs 126 MB L2); no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "kernel": "k_boris_brick_f64 (TSC, 3D, deposit)",
+                     "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tf / FP64_NOMINAL_TFLOPS, "traffic": None,
+                     "flop_per_particle_step": FLOP_PER_PSTEP_BORIS_DEP,
+                     "kernel_ms": kmean,
+                     "peak_note": "FP64 non-tensor nominal (recipe); FP64 is 1/64 of FP32 on "
+                                  "B300"},
+        "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved_gbs / hbm,
+                         "bytes_per_particle_step": BYTES_PER_PSTEP_BORIS_DEP,
+                         "peak_kind": hbm_kind},
+        "clocks": clocks, "gpu_launches": launches,
+    }
+    if rank == 0:
+        line["e2e"] = run_e2e(torch, wl, max(3, args.steps // 4))
+    del wl
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_extras:
+        try:
+            line["lp"] = run_lp(torch, P, max(5, args.steps // 2), 3)
+        except Exception as e:  # report, do not hide
+            line["lp"] = {"error": repr(e)}
+        try:
+            line["boris_2d"] = run_2d(torch, P)
+        except Exception as e:
+            line["boris_2d"] = {"error": repr(e)}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
