@@ -174,6 +174,36 @@ const char* part_last_error(const part_ctx* ctx);
 /* Kernel launches this context has enqueued since creation.               */
 int64_t part_launch_count(const part_ctx* ctx);
 
+/* ---- Sort without any device allocation ----------------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they need a sort, so cannot provide the
+ * workspace that part_init requires.  Examples: code that is being captured
+ * into a CUDA graph, a plug-in inside a host code that owns every device byte
+ * through its own memory pool, or a latency-critical loop where a cudaMalloc
+ * (which may synchronise the device) is not acceptable.
+ *
+ * Same result as part_sort on a PART_FP64 / PART_BORIS context: the particles
+ * are stably sorted by the brick cell key (see part_brick_dims) and x[3][n],
+ * u[3][n], w[n] (may be NULL) and id[n] (may be NULL) are permuted in place;
+ * cell_start receives nkeys + 1 entries.  All pointers are device pointers
+ * owned by the caller; the work is enqueued on cuda_stream (NULL = legacy
+ * default stream).
+ *
+ * Scratch: a static array of PART_NOALLOC_SORT_SCRATCH_BYTES compiled into
+ * libpart.so, held by every GPU that loads the library until the process
+ * exits.  The first call on each device (with that device current) looks up
+ * the array's device address; make that first call before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race:
+ * serialise them.  Nothing is allocated or freed.
+ * Errors: PART_EINVAL if n > PART_NOALLOC_SORT_MAX_N or a pointer is NULL
+ * (message in part_last_error(NULL)).  Non-finite positions are sorted as if
+ * in cell 0 of that axis and are not reported by this entry point.          */
+#define PART_NOALLOC_SORT_MAX_N 1048576
+#define PART_NOALLOC_SORT_SCRATCH_BYTES 25428736
+part_status part_sort_fp64_noalloc(const part_grid* grid, int64_t n, double* x, double* u,
+                                   double* w, uint64_t* id, uint32_t* cell_start,
+                                   void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

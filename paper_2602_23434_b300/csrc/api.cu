@@ -14,8 +14,8 @@
 cudaError_t launch_lp_sample_rho(part_ctx* c);
 
 namespace {
-
 thread_local std::string g_err = "";
+}  // namespace
 
 part_status fail(part_ctx* c, part_status s, const std::string& msg) {
   if (c) c->err = msg;
@@ -23,11 +23,15 @@ part_status fail(part_ctx* c, part_status s, const std::string& msg) {
   return s;
 }
 
+namespace {
+
 part_status cuda_fail(part_ctx* c, cudaError_t e, const char* where) {
   return fail(c, PART_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
 
 part_status check_grid(const part_grid* g) {
   if (!g) return fail(nullptr, PART_EINVAL, "grid is NULL");
@@ -76,6 +80,8 @@ void make_geo(const part_grid* gr, int esize, Geo* g) {
   g->nkeys = g->nbricks * g->V;
   g->pplane = (int64_t)g->pn[0] * g->pn[1] * g->pn[2];
 }
+
+namespace {
 
 struct Layout {
   size_t fpad, keys0, keys1, vals0, vals1, hist, hsum, cstart, tmp, dpart, samples, status, total;

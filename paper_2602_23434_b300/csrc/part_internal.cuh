@@ -153,6 +153,12 @@ __device__ __forceinline__ void shape_weights(T d, T* w) {
 }
 
 // ---------------------------------------------------------------- host glue
+// Host helpers of api.cu: record an error message, validate a grid, derive
+// the kernel geometry for a field element size.
+part_status fail(part_ctx* c, part_status s, const std::string& msg);
+part_status check_grid(const part_grid* g);
+void make_geo(const part_grid* gr, int esize, Geo* g);
+
 // Kernel launchers implemented in the .cu files; each returns a cudaError_t
 // of its launch and counts the launches it made in *launches.
 cudaError_t launch_pad_fields(part_ctx* c, const void* src);
