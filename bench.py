@@ -180,7 +180,7 @@ def time_steps(torch, stream, fn, K: int, W: int, per_step_events=False):
     return total_ms, kern_ms
 
 
-def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1237):
+def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238):
     dev = torch.device("cuda", torch.cuda.current_device())
     vel, rho, B = synth.fluid_snapshot(3, n, seed)
     f7 = torch.as_tensor(np.concatenate([vel, rho, B]).reshape(7, -1)).to(dev)
@@ -220,6 +220,105 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1237):
             "spec_update_ms": spec_ms,
             "spec_update_GBps": nlp * 2 * 2 * nb * 8 / (spec_ms / 1e3) / 1e9,
             "c0": c0, "dt": dt, "gpu_launches_per_step": launches}
+
+
+# Mixed form: per particle-step, state read 32 B (cell 4, offsets 12, u 12,
+# w 4) + written 28 B, f32 field stencil 24 B per cell / 8 ppc = 3, deposit
+# partials 3 x 8 B per cell / 8 ppc = 3.
+BYTES_PER_PSTEP_MIXED_DEP = 32 + 28 + 3 + 3
+
+
+class MixedWorkload:
+    """Mixed form: int32 cell + f32 offsets, f32 push and fields, FP64-accurate
+    deposit sums; turbulent fields; Boris + TSC + deposit."""
+
+    def __init__(self, torch, P, n, ppc, seed, with_ids=False):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.n, self.N = n, n ** 3 * ppc
+        f = synth.em_fields(3, n, seed)
+        self.dt = dt_turbulent(f, n)
+        self.f = torch.as_tensor(f.reshape(6, -1).astype(np.float32)).to(dev)
+        del f
+        self.part = P.Part(P.make_grid(3, n), P.MIXED, P.TSC, P.BORIS, capacity=self.N)
+        self.part.set_fields(self.f)
+        self.cell = torch.empty(self.N, dtype=torch.int32, device=dev)
+        self.off = torch.empty((3, self.N), dtype=torch.float32, device=dev)
+        self.u = torch.empty((3, self.N), dtype=torch.float32, device=dev)
+        self.w = torch.empty(self.N, dtype=torch.float32, device=dev)
+        self.ids = torch.empty(self.N, dtype=torch.int64, device=dev) if with_ids else None
+        self.out = torch.empty((3, n ** 3), dtype=torch.float64, device=dev)
+        self.part.bind(self.N, self.cell, off=self.off, u=self.u, w=self.w, ids=self.ids)
+        self.part.init_particles(seed, 0.1)
+        self.part.enable_deposit(True)
+        self.part.sync()
+
+    def step(self, ev=None):
+        p = self.part
+        p.sort()
+        if ev is not None:
+            ev[0].record(p.stream)
+        p.gather_push(1.0, self.dt, 1)
+        if ev is not None:
+            ev[1].record(p.stream)
+        p.deposit(self.out)
+
+
+def run_mixed(torch, P, n, ppc, K, W, seed):
+    wl = MixedWorkload(torch, P, n, ppc, seed)
+    l0 = wl.part.launches()
+    total, kern = time_steps(torch, wl.part.stream, wl.step, K, W, per_step_events=True)
+    wl.part.sync()
+    km = float(np.mean(kern))
+    hbm, kind = peaks()
+    gbs = BYTES_PER_PSTEP_MIXED_DEP * wl.N / (km / 1e3) / 1e9
+    res = {"workload": f"3D {n}^3 turbulent, {wl.N} particles ({ppc}/cell), mixed form "
+                       "(int32 cell + f32 offset, f32 push/fields, FP64-accurate deposit sums), "
+                       "Boris + TSC + deposit",
+           "value": wl.N * K / (total / 1e3), "unit": "particle-steps/s",
+           "ms_per_step": total / K, "push_kernel_ms": km,
+           "roofline_push": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                             "frac": gbs / hbm, "peak_kind": kind,
+                             "bytes_per_particle_step": BYTES_PER_PSTEP_MIXED_DEP},
+           "gpu_launches_per_step": (wl.part.launches() - l0) // (K + W)}
+    del wl
+    torch.cuda.empty_cache()
+    return res
+
+
+def mixed_error_vs_fp64(torch, P, n=128, ppc=8, steps=20, seed=1236):
+    """Same seed, same fields: FP64 and mixed runs of `steps` steps, matched by
+    particle id; max position difference (cells) and momentum error."""
+    m = MixedWorkload(torch, P, n, ppc, seed, with_ids=True)
+    d = BorisWorkload(torch, P, n, ppc, seed)
+    for _ in range(steps):
+        m.step()
+        d.step()
+    m.part.sync()
+    d.part.sync()
+    im = torch.argsort(m.ids)
+    idd = torch.argsort(d.ids)
+    dx = 2.0 / n
+    c = m.cell[im].to(torch.int64)
+    j = torch.stack([c % n, (c // n) % n, c // (n * n)]).to(torch.float64)
+    xm = -1.0 + (j + 0.5 + m.off[:, im].to(torch.float64)) * dx
+    xd = d.x[:, idd]
+    dd = (xm - xd) / dx
+    dd = dd - n * torch.round(dd / n)
+    um = m.u[:, im].to(torch.float64)
+    ud = d.u[:, idd]
+    du = (um - ud).norm(dim=0) / ud.norm(dim=0)
+    gm = torch.sqrt(1 + (um * um).sum(0))
+    gd = torch.sqrt(1 + (ud * ud).sum(0))
+    res = {"steps": steps, "particles": m.N,
+           "max_position_error_cells": float(dd.abs().max()),
+           "median_position_error_cells": float(dd.abs().median()),
+           "max_rel_momentum_error": float(du.max()),
+           "median_rel_momentum_error": float(du.median()),
+           "max_energy_error": float((gm / gd - 1).abs().max()),
+           "deposit_rel_l2_error": float((m.out - d.out).norm() / d.out.norm())}
+    del m, d
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_2d(torch, P, n=64, ppc=16, steps=100, seed=1235):
@@ -444,6 +543,14 @@ def main():
             line["boris_2d"] = run_2d(torch, P)
         except Exception as e:
             line["boris_2d"] = {"error": repr(e)}
+        try:
+            mx = run_mixed(torch, P, 128, 8, args.steps, 3, 1236)
+            mx["speedup_vs_fp64_same_workload"] = mx["value"] / value
+            line["mixed_128"] = mx
+            line["mixed_256"] = run_mixed(torch, P, 256, 8, max(5, args.steps // 2), 3, 1237)
+            line["mixed_error_vs_fp64"] = mixed_error_vs_fp64(torch, P)
+        except Exception as e:
+            line["mixed"] = {"error": repr(e)}
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

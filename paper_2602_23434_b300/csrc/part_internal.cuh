@@ -164,6 +164,7 @@ void make_geo(const part_grid* gr, int esize, Geo* g);
 cudaError_t launch_pad_fields(part_ctx* c, const void* src);
 cudaError_t launch_sort(part_ctx* c);
 cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps);
+cudaError_t launch_boris_mixed(part_ctx* c, double qm, double dt, int nsteps);
 cudaError_t launch_deposit_combine(part_ctx* c, double* out);
 cudaError_t launch_lp_push(part_ctx* c, double dt, int nsteps);
 cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad);

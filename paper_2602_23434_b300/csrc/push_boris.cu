@@ -428,7 +428,7 @@ cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps) {
     return dim == 3 ? dispatch_f64<PART_CIC, 3>(c, qm, dt, nsteps)
                     : dispatch_f64<PART_CIC, 2>(c, qm, dt, nsteps);
   }
-  return cudaErrorNotSupported;
+  return launch_boris_mixed(c, qm, dt, nsteps);
 }
 
 cudaError_t launch_deposit_combine(part_ctx* c, double* out) {

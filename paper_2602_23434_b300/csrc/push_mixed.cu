@@ -1,0 +1,451 @@
+// push_mixed.cu -- mixed-precision form of the gather + Boris push (+ deposit).
+//
+// State: int32 linear cell + f32 offset from the cell centre (cell units, in
+// [-1/2, 1/2)) + f32 u (+ optional f32 w).  Fields are staged as f32.  The
+// push runs in f32; the deposit reduces f32 contributions into compensated
+// (two-float) accumulators and leaves FP64 partials, so the grid sums carry
+// about 48 significant bits.
+//
+// Brick kernel (sorted): TMA stages the brick's haloed f32 field box; the
+// brick's particles are processed in super-chunks of up to kM particles:
+//   A. one thread per particle: weights from the offsets, gather, Boris, move
+//      (offset += dt v/dx, integer cell carry, periodic wrap); the old offsets
+//      and the force w du/dt are left in shared memory.  du is formed from the
+//      Boris rotation increment (u' x s + 2hE), not as u_new - u_old, so f32
+//      cancellation does not enter the force;
+//   B. one thread per source cell sums its particles' 27 x 3 contributions in
+//      registers, then 27 passes (one per stencil offset, separated by
+//      barriers) add them into the haloed tile's two-float accumulators: in a
+//      pass no two threads share a target, and the order is fixed.
+// Particle-order kernel: nsteps fused steps, state in registers, stencil read
+// from the padded global f32 copy (test particles, serving).
+#include "part_internal.cuh"
+
+namespace {
+
+constexpr int kT = kPushThreads;
+constexpr int kM = 2048;  // particles per super-chunk
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct MixedSmem {
+  size_t cs, bar, rec, acc, total;
+};
+__host__ __device__ inline MixedSmem mixed_smem(const Geo& g) {
+  MixedSmem s;
+  size_t bbytes = (size_t)6 * g.box[0] * g.box[1] * g.box[2] * 4;
+  s.cs = align_up(bbytes, 128);
+  s.bar = align_up(s.cs + (size_t)(g.V + 1) * 4, 16);
+  s.rec = align_up(s.bar + 16, 128);
+  s.acc = s.rec + (size_t)6 * kM * 4;
+  s.total = s.acc + (size_t)6 * g.ev * 4;
+  return s;
+}
+
+// f32 relativistic Boris kick.  The rotation parameters are the quantities
+// whose rounding repeats identically every step (in a steady field), so they
+// are formed to about half an ulp with error-free transformations (TwoProd
+// by fma, exact residuals of 1 + q): 1/gamma- is refined from rsqrtf by one
+// Newton step evaluated in two-float, h = h_hi + h_lo is the two-float half
+// step, t = h B / gamma- and s = 2 t / (1 + |t|^2) are each kept as an f32
+// value plus its f32 residual.
+// du gets u^{n+1} - u^n from the rotation increment and the two half-kicks.
+__device__ __forceinline__ void boris_f32(float* u, const float* E, const float* B, float h,
+                                          float hl, float* du) {
+  // half kick h E with the two-float h
+  const float k0 = fmaf(h, E[0], hl * E[0]), k1 = fmaf(h, E[1], hl * E[1]);
+  const float k2 = fmaf(h, E[2], hl * E[2]);
+  const float um0 = u[0] + k0, um1 = u[1] + k1, um2 = u[2] + k2;
+  const float q = um0 * um0 + um1 * um1 + um2 * um2;
+  const float a = 1.0f + q;
+  const float res = q - (a - 1.0f);             // exact: a + res = 1 + q
+  const float y = rsqrtf(a);
+  const float yp = y * y;
+  const float ype = fmaf(y, y, -yp);            // y^2 = yp + ype exactly
+  const float r = fmaf(-a, yp, 1.0f) - fmaf(a, ype, res * yp);  // 1 - (1+q) y^2
+  const float gl = 0.5f * y * r;                // 1/gamma- = y + gl
+  const float hg = h * y;
+  const float hge = fmaf(h, y, -hg) + fmaf(h, gl, hl * y);      // h/gamma- = hg + hge
+  const float t0 = fmaf(hg, B[0], hge * B[0]);
+  const float t1 = fmaf(hg, B[1], hge * B[1]);
+  const float t2 = fmaf(hg, B[2], hge * B[2]);
+  // residuals: t_true = t + tl to ~2^-46 relative
+  const float tl0 = fmaf(hg, B[0], -t0) + hge * B[0];
+  const float tl1 = fmaf(hg, B[1], -t1) + hge * B[1];
+  const float tl2 = fmaf(hg, B[2], -t2) + hge * B[2];
+  const float tt = t0 * t0 + t1 * t1 + t2 * t2;
+  const float d = 1.0f + tt;
+  const float dres = tt - (d - 1.0f);           // exact: d + dres = 1 + |t|^2
+  const float sf = __fdiv_rn(2.0f, d);
+  const float sfl = __fdiv_rn(fmaf(-sf, d, 2.0f) - sf * dres, d);  // 2/(1+|t|^2) = sf + sfl
+  const float s0 = fmaf(sf, t0, sfl * t0);
+  const float s1 = fmaf(sf, t1, sfl * t1);
+  const float s2 = fmaf(sf, t2, sfl * t2);
+  const float sl0 = fmaf(sf, t0, -s0) + fmaf(sfl, t0, sf * tl0);
+  const float sl1 = fmaf(sf, t1, -s1) + fmaf(sfl, t1, sf * tl1);
+  const float sl2 = fmaf(sf, t2, -s2) + fmaf(sfl, t2, sf * tl2);
+  // u' = u- + u- x t and u+ - u- = u' x s with t, s carried as value +
+  // residual: the residual terms are first-order small and enter in plain f32,
+  // so the rotation angle carries no rounding that repeats from step to step
+  const float p0 = um0 + ((um1 * t2 - um2 * t1) + (um1 * tl2 - um2 * tl1));
+  const float p1 = um1 + ((um2 * t0 - um0 * t2) + (um2 * tl0 - um0 * tl2));
+  const float p2 = um2 + ((um0 * t1 - um1 * t0) + (um0 * tl1 - um1 * tl0));
+  const float r0 = (p1 * s2 - p2 * s1) + (p1 * sl2 - p2 * sl1);  // u+ - u-
+  const float r1 = (p2 * s0 - p0 * s2) + (p2 * sl0 - p0 * sl2);
+  const float r2 = (p0 * s1 - p1 * s0) + (p0 * sl1 - p1 * sl0);
+  du[0] = r0 + 2.0f * k0;
+  du[1] = r1 + 2.0f * k1;
+  du[2] = r2 + 2.0f * k2;
+  u[0] = (um0 + r0) + k0;
+  u[1] = (um1 + r1) + k1;
+  u[2] = (um2 + r2) + k2;
+}
+
+// Knuth's TwoSum: hi + lo carries the sum with the rounding error of hi.
+__device__ __forceinline__ void two_sum_add(float* hi, float* lo, float x) {
+  const float s = *hi + x;
+  const float bp = s - *hi;
+  const float err = (*hi - (s - bp)) + (x - bp);
+  *hi = s;
+  *lo += err;
+}
+
+__device__ __forceinline__ void cell_coords(const Geo& g, int32_t c, int* j) {
+  j[0] = c % g.n[0];
+  const int r = c / g.n[0];
+  j[1] = r % g.n[1];
+  j[2] = r / g.n[1];
+}
+
+// Move in cell units: off += dv; whole cells carry into j (periodic).
+__device__ __forceinline__ void move_axis(float& off, int& j, float dv, int n) {
+  off = off + dv;
+  const float k = floorf(off + 0.5f);
+  off = off - k;
+  int jj = j + (int)k;
+  if (jj < 0 || jj >= n) jj = ((jj % n) + n) % n;
+  j = jj;
+}
+
+template <int SHAPE, int DIM, bool DEP>
+__global__ void __launch_bounds__(kT, 2)
+    k_boris_brick_mixed(const __grid_constant__ CUtensorMap tmap, const Geo g,
+                        int32_t* __restrict__ cell, float* __restrict__ off,
+                        float* __restrict__ u, const float* __restrict__ w, int64_t n,
+                        const uint32_t* __restrict__ cstart, double* __restrict__ dpart,
+                        float h, float hl, float dtdx0, float dtdx1, float dtdx2, float inv_dt,
+                        int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const MixedSmem L = mixed_smem(g);
+  const int tid = threadIdx.x;
+  const int bvol = g.box[0] * g.box[1] * g.box[2];
+  float* sbox = reinterpret_cast<float*>(smem);
+  uint32_t* scs = reinterpret_cast<uint32_t*>(smem + L.cs);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+  int* sflag = reinterpret_cast<int*>(smem + L.bar + 8);
+  float* rd = reinterpret_cast<float*>(smem + L.rec);  // [3][kM] old offsets
+  float* rF = rd + 3 * kM;                              // [3][kM] force
+  float* ahi = reinterpret_cast<float*>(smem + L.acc);  // [3][ev]
+  float* alo = ahi + 3 * g.ev;                          // [3][ev]
+
+  const int64_t brick = blockIdx.x;
+  const int bx = (int)(brick % g.nb[0]);
+  const int by = (int)((brick / g.nb[0]) % g.nb[1]);
+  const int bz = (int)(brick / ((int64_t)g.nb[0] * g.nb[1]));
+  const int org[3] = {bx * g.b[0], by * g.b[1], bz * g.b[2]};
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    *sflag = 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(bar, (uint32_t)(6 * bvol * 4));
+    tma_load_4d(sbox, &tmap, bar, org[0], org[1], org[2], 0);
+  }
+  for (int i = tid; i <= g.V; i += kT) scs[i] = cstart[brick * g.V + i];
+  if (DEP)
+    for (int i = tid; i < 6 * g.ev; i += kT) ahi[i] = 0.0f;
+  if (!mbar_wait_bounded(bar, 0)) atomicOr(sflag, 1);
+  __syncthreads();
+  if (*sflag) {
+    if (tid == 0) {
+      atomicOr(status, ST_TIMEOUT);
+      mbar_wait_bounded(bar, 0);
+    }
+    return;
+  }
+
+  const float dtdx[3] = {dtdx0, dtdx1, dtdx2};
+  const uint32_t p0 = scs[0], p1 = scs[g.V];
+  for (uint32_t sb = p0; sb < p1; sb += kM) {
+    const uint32_t se = p1 - sb < (uint32_t)kM ? p1 : sb + kM;
+    // ---- A: push, one thread per particle
+    for (uint32_t p = sb + tid; p < se; p += kT) {
+      const int i = (int)(p - sb);
+      int j[3];
+      cell_coords(g, cell[p], j);
+      float o[3], up[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        o[a] = off[a * n + p];
+        up[a] = u[a * n + p];
+      }
+      int l[3];
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        l[a] = j[a] - org[a];
+        ok = ok && l[a] >= 0 && l[a] < g.b[a];
+      }
+      if (ok) {  // the particle must sit in the cell it was sorted into
+        const int lc = (l[2] * g.b[1] + l[1]) * g.b[0] + l[0];
+        ok = p >= scs[lc] && p < scs[lc + 1];
+      }
+      float F[3] = {0.0f, 0.0f, 0.0f};
+      float d0[3] = {0.0f, 0.0f, 0.0f};
+      if (!ok) {
+        atomicOr(status, ST_DOMAIN);
+      } else {
+        float wx[3], wy[3], wz[3] = {0.0f, 1.0f, 0.0f};
+        shape_weights<SHAPE>(o[0], wx);
+        shape_weights<SHAPE>(o[1], wy);
+        if (DIM == 3) shape_weights<SHAPE>(o[2], wz);
+        float f[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
+          const int zz = DIM == 3 ? l[2] + kz : 0;
+#pragma unroll
+          for (int ky = 0; ky < 3; ++ky) {
+            const float wzy = wz[kz] * wy[ky];
+            const int row = (zz * g.box[1] + l[1] + ky) * g.box[0] + l[0];
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+              const float ww = wzy * wx[kx];
+              const float* sp = sbox + row + kx;
+#pragma unroll
+              for (int c = 0; c < 6; ++c) f[c] += ww * sp[c * bvol];
+            }
+          }
+        }
+        float du[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) d0[a] = o[a];
+        boris_f32(up, f, f + 3, h, hl, du);
+        const float gi = rsqrtf(1.0f + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) move_axis(o[a], j[a], up[a] * gi * dtdx[a], g.n[a]);
+        if (!(isfinite(up[0]) && isfinite(up[1]) && isfinite(up[2]) && isfinite(o[0]) &&
+              isfinite(o[1]) && isfinite(o[2])))
+          atomicOr(status, ST_NONFINITE);
+        cell[p] = (j[2] * g.n[1] + j[1]) * g.n[0] + j[0];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          off[a * n + p] = o[a];
+          u[a * n + p] = up[a];
+        }
+        if (DEP) {
+          const float wdt = (w ? w[p] : 1.0f) * inv_dt;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) F[a] = du[a] * wdt;
+        }
+      }
+      if (DEP) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          rd[a * kM + i] = d0[a];
+          rF[a * kM + i] = F[a];
+        }
+      }
+    }
+    if (!DEP) continue;
+    __syncthreads();
+    // ---- B: one thread per source cell, then 27 ordered passes
+    const int hz = DIM == 3 ? 1 : 0;
+    for (int c0 = 0; c0 < g.V; c0 += kT) {
+      const int ls = c0 + tid;
+      float T[27][3];
+#pragma unroll
+      for (int k = 0; k < 27; ++k) T[k][0] = T[k][1] = T[k][2] = 0.0f;
+      bool any = false;
+      int lx = 0, ly = 0, lz = 0;
+      if (ls < g.V) {
+        lx = ls % g.b[0];
+        ly = (ls / g.b[0]) % g.b[1];
+        lz = ls / (g.b[0] * g.b[1]);
+        uint32_t r0 = scs[ls], r1 = scs[ls + 1];
+        r0 = r0 > sb ? r0 : sb;
+        r1 = r1 < se ? r1 : se;
+        for (uint32_t r = r0; r < r1; ++r) {
+          const int i = (int)(r - sb);
+          float wx[3], wy[3], wz[3] = {0.0f, 1.0f, 0.0f};
+          shape_weights<SHAPE>(rd[i], wx);
+          shape_weights<SHAPE>(rd[kM + i], wy);
+          if (DIM == 3) shape_weights<SHAPE>(rd[2 * kM + i], wz);
+          const float F0 = rF[i], F1 = rF[kM + i], F2 = rF[2 * kM + i];
+#pragma unroll
+          for (int kz = 0; kz < 3; ++kz)
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+              const float wzy = wz[kz] * wy[ky];
+#pragma unroll
+              for (int kx = 0; kx < 3; ++kx) {
+                const float ww = wzy * wx[kx];
+                const int k = (kz * 3 + ky) * 3 + kx;
+                T[k][0] += ww * F0;
+                T[k][1] += ww * F1;
+                T[k][2] += ww * F2;
+              }
+            }
+          any = true;
+        }
+      }
+#pragma unroll
+      for (int kz = 0; kz < 3; ++kz)
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) {
+            const int k = (kz * 3 + ky) * 3 + kx;
+            if (any && (DIM == 3 || kz == 1)) {
+              const int ex = lx + kx, ey = ly + ky, ez = lz + hz + (kz - 1);
+              const int t = (ez * g.e[1] + ey) * g.e[0] + ex;
+#pragma unroll
+              for (int c = 0; c < 3; ++c)
+                two_sum_add(&ahi[c * g.ev + t], &alo[c * g.ev + t], T[k][c]);
+            }
+            __syncthreads();
+          }
+    }
+  }
+  if (DEP) {
+    __syncthreads();
+    for (int t = tid; t < g.ev; t += kT)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        dpart[(brick * 3 + c) * g.ev + t] =
+            (double)ahi[c * g.ev + t] + (double)alo[c * g.ev + t];
+  }
+}
+
+template <int SHAPE, int DIM>
+__global__ void __launch_bounds__(256)
+    k_boris_particles_mixed(const float* __restrict__ fp, const Geo g, int32_t* __restrict__ cell,
+                            float* __restrict__ off, float* __restrict__ u, int64_t n, float h,
+                            float hl, float dtdx0, float dtdx1, float dtdx2, int nsteps,
+                            int* __restrict__ status) {
+  const float dtdx[3] = {dtdx0, dtdx1, dtdx2};
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int32_t c = cell[p];
+    bool bad = false;
+    if (c < 0 || c >= g.G) {
+      bad = true;
+      c = 0;
+    }
+    int j[3];
+    cell_coords(g, c, j);
+    float o[3], up[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      o[a] = off[a * n + p];
+      up[a] = u[a * n + p];
+    }
+    for (int st = 0; st < nsteps; ++st) {
+      float wx[3], wy[3], wz[3] = {0.0f, 1.0f, 0.0f};
+      shape_weights<SHAPE>(o[0], wx);
+      shape_weights<SHAPE>(o[1], wy);
+      if (DIM == 3) shape_weights<SHAPE>(o[2], wz);
+      float f[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+      for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
+        const int zz = DIM == 3 ? j[2] + kz : 0;
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
+          const float wzy = wz[kz] * wy[ky];
+          const int64_t row = ((int64_t)zz * g.pn[1] + j[1] + ky) * g.pn[0] + j[0];
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) {
+            const float ww = wzy * wx[kx];
+#pragma unroll
+            for (int cc = 0; cc < 6; ++cc) f[cc] += ww * __ldg(fp + cc * g.pplane + row + kx);
+          }
+        }
+      }
+      float du[3];
+      boris_f32(up, f, f + 3, h, hl, du);
+      const float gi = rsqrtf(1.0f + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) move_axis(o[a], j[a], up[a] * gi * dtdx[a], g.n[a]);
+    }
+    if (bad || !(isfinite(up[0]) && isfinite(up[1]) && isfinite(up[2]) && isfinite(o[0]) &&
+                 isfinite(o[1]) && isfinite(o[2])))
+      atomicOr(status, bad ? ST_DOMAIN : ST_NONFINITE);
+    cell[p] = (j[2] * g.n[1] + j[1]) * g.n[0] + j[0];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      off[a * n + p] = o[a];
+      u[a * n + p] = up[a];
+    }
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 148 * 64) b = 148 * 64;
+  return (int)b;
+}
+
+struct MixedArgs {
+  float h, hl, dtdx[3], inv_dt;  // h + hl: the half step (q/m) dt/2 as two floats
+};
+
+MixedArgs mixed_args(const part_ctx* c, double qm, double dt) {
+  MixedArgs a;
+  const double hd = 0.5 * qm * dt;
+  a.h = (float)hd;
+  a.hl = (float)(hd - (double)a.h);
+  for (int k = 0; k < 3; ++k) a.dtdx[k] = (float)(dt / c->geo.dx[k]);
+  a.inv_dt = (float)(1.0 / dt);
+  return a;
+}
+
+template <int SHAPE, int DIM, bool DEP>
+cudaError_t brick_mixed(part_ctx* c, const MixedArgs& a) {
+  auto kern = k_boris_brick_mixed<SHAPE, DIM, DEP>;
+  const MixedSmem L = mixed_smem(c->geo);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)L.total);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)c->geo.nbricks, kT, L.total, c->stream>>>(
+      c->tmap, c->geo, (int32_t*)c->x, (float*)c->off, (float*)c->u, (const float*)c->w, c->n,
+      c->cstart, c->dpart, a.h, a.hl, a.dtdx[0], a.dtdx[1], a.dtdx[2], a.inv_dt, c->status);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+template <int SHAPE, int DIM>
+cudaError_t dispatch_mixed(part_ctx* c, double qm, double dt, int nsteps) {
+  const MixedArgs a = mixed_args(c, qm, dt);
+  if (c->sorted && nsteps == 1)
+    return c->deposit_on ? brick_mixed<SHAPE, DIM, true>(c, a)
+                         : brick_mixed<SHAPE, DIM, false>(c, a);
+  k_boris_particles_mixed<SHAPE, DIM><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
+      (const float*)c->fpad, c->geo, (int32_t*)c->x, (float*)c->off, (float*)c->u, c->n, a.h,
+      a.hl, a.dtdx[0], a.dtdx[1], a.dtdx[2], nsteps, c->status);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_boris_mixed(part_ctx* c, double qm, double dt, int nsteps) {
+  if (c->n == 0) return cudaSuccess;
+  const int dim = c->geo.dim;
+  if (c->shape == PART_TSC)
+    return dim == 3 ? dispatch_mixed<PART_TSC, 3>(c, qm, dt, nsteps)
+                    : dispatch_mixed<PART_TSC, 2>(c, qm, dt, nsteps);
+  return dim == 3 ? dispatch_mixed<PART_CIC, 3>(c, qm, dt, nsteps)
+                  : dispatch_mixed<PART_CIC, 2>(c, qm, dt, nsteps);
+}

@@ -1,0 +1,195 @@
+"""Mixed form (int32 cell + f32 offset, f32 push and fields, FP64-accurate
+deposit sums) against the FP64 oracle, through the C ABI.
+
+Tolerances follow from f32 arithmetic (unit roundoff 6e-8): one step agrees
+with the FP64 oracle to 1e-6 cell in position and 2e-6 of max|u| in
+momentum; the deposit to 1e-5 of the sum of |contributions| per cell (each
+contribution is an f32 product); the sort is bit-exact; the deposit is
+bitwise reproducible.  Over 1000 steps in uniform fields: energy drift
+|gamma/gamma_FP64 - 1| <= 1e-6 for every particle; gyrophase drift <= 1e-5
+rad for 99% of the particles and <= 2e-5 for all (the tail is the random
+walk of f32 momentum rounding).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2602_23434_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2602_23434_b300 import _lib as P  # noqa: E402
+
+
+def _host(t):
+    return t.detach().cpu().numpy()
+
+
+def _to_mixed(x, n, dim):
+    """Positions [3][N] on [-1, 1)^dim -> (linear cell, f32 offset in cell units)."""
+    dx = 2.0 / n
+    j = np.zeros((3, x.shape[1]), dtype=np.int64)
+    off = np.zeros((3, x.shape[1]), dtype=np.float32)
+    for a in range(dim):
+        s = (x[a] + 1.0) / dx
+        j[a] = np.minimum(np.floor(s), n - 1)
+        off[a] = (s - j[a] - 0.5).astype(np.float32)
+    nz = n if dim == 3 else 1
+    cell = (j[2] * n + j[1]) * n + j[0]
+    assert np.all(cell < n * n * nz)
+    return cell.astype(np.int32), off
+
+
+def _from_mixed(cell, off, n, dim):
+    """(cell, offset) -> f64 positions (exact conversion of the f32 offset)."""
+    c = cell.astype(np.int64)
+    j = np.stack([c % n, (c // n) % n, c // (n * n)])
+    x = np.zeros((3, c.shape[0]))
+    for a in range(3):
+        if a < dim:
+            x[a] = -1.0 + (j[a] + 0.5 + off[a].astype(np.float64)) * (2.0 / n)
+    return x
+
+
+def _cell_units_diff(xg, xr, n):
+    d = (xg - xr) / (2.0 / n)
+    return d - n * np.round(d / n)
+
+
+def _state(dim, n, ppc, seed, u_th=0.3):
+    N = n ** dim * ppc + 11
+    x, u, w, ids = synth.particles(dim, None, N, seed, u_th=u_th)
+    cell, off = _to_mixed(x, n, dim)
+    uf = u.astype(np.float32)
+    wf = np.random.default_rng(seed).uniform(0.5, 2.0, N).astype(np.float32)
+    return N, cell, off, uf, wf, ids
+
+
+def _key_table(og, brick, n, dim):
+    nz = n if dim == 3 else 1
+    tab = np.zeros(n * n * nz, dtype=np.uint32)
+    for c in range(tab.size):
+        tab[c] = O.cell_key(og, brick, (c % n, (c // n) % n, c // (n * n)))
+    return tab
+
+
+@pytest.mark.parametrize("dim,n,ppc", [(3, 20, 8), (2, 40, 16)])
+def test_mixed_sort_bit_exact(dim, n, ppc):
+    og = O.make_grid(dim, (n, n, n))
+    N, cell, off, uf, wf, ids = _state(dim, n, ppc, 5)
+    p = P.Part(P.make_grid(dim, n), P.MIXED, P.TSC, P.BORIS, capacity=N)
+    cd = torch.as_tensor(cell).cuda()
+    od, ud = torch.as_tensor(off).cuda(), torch.as_tensor(uf).cuda()
+    idd = torch.as_tensor(ids.astype(np.int64)).cuda()
+    p.bind(N, cd, off=od, u=ud, ids=idd)
+    p.sort()
+    cs = _host(p.cell_start())
+    p.sync()
+    keys = _key_table(og, p.brick, n, dim)[cell]
+    perm = O.stable_sort(keys)
+    assert np.array_equal(_host(idd), ids[perm].astype(np.int64))
+    assert np.array_equal(_host(cd), cell[perm])
+    assert np.array_equal(_host(od), off[:, perm])
+    assert np.array_equal(cs, O.cell_start(p.nkeys, keys[perm]).astype(np.int64))
+
+
+@pytest.mark.parametrize("dim,n,ppc", [(3, 20, 8), (2, 40, 16)])
+@pytest.mark.parametrize("shape", [P.TSC, P.CIC])
+def test_mixed_step_and_deposit_vs_fp64(dim, n, ppc, shape):
+    og = O.make_grid(dim, (n, n, n))
+    f = synth.em_fields(dim, n, 23, v_rms=0.05).reshape(6, -1)
+    N, cell, off, uf, wf, ids = _state(dim, n, ppc, 7)
+    qm, dt = 1.0, 0.5 * (2.0 / n)
+    p = P.Part(P.make_grid(dim, n), P.MIXED, shape, P.BORIS, capacity=N)
+    p.set_fields(torch.as_tensor(f.astype(np.float32)).cuda())
+    cd = torch.as_tensor(cell).cuda()
+    od, ud = torch.as_tensor(off).cuda(), torch.as_tensor(uf).cuda()
+    wd = torch.as_tensor(wf).cuda()
+    p.bind(N, cd, off=od, u=ud, w=wd)
+    p.enable_deposit(True)
+    p.sort()
+    torch.cuda.synchronize()
+    c0, o0, u0, w0 = _host(cd), _host(od), _host(ud), _host(wd)
+    p.gather_push(qm, dt, 1)
+    out = torch.empty((3, f.shape[1]), dtype=torch.float64, device="cuda")
+    p.deposit(out)
+    p.sync()
+    x0 = _from_mixed(c0, o0, n, dim)
+    xr, ur, F, xo = O.boris_step(og, shape, f, x0, u0.astype(np.float64),
+                                 w0.astype(np.float64), qm, dt, True)
+    xg = _from_mixed(_host(cd), _host(od), n, dim)
+    assert np.max(np.abs(_cell_units_diff(xg, xr, n))) <= 1e-6
+    assert np.max(np.abs(_host(ud) - ur)) <= 2e-6 * np.max(np.abs(ur))
+    assert np.all(np.abs(_host(od)) <= 0.5)
+    dref = O.deposit(og, shape, xo, F)
+    dabs = O.deposit(og, shape, xo, np.abs(F))
+    err = np.max(np.abs(_host(out) - dref) / np.maximum(dabs, 1e-300))
+    assert err <= 1e-5, err
+    # bitwise reproducible
+    cd2, od2, ud2 = (torch.as_tensor(c0).cuda(), torch.as_tensor(o0).cuda(),
+                     torch.as_tensor(u0).cuda())
+    p.bind(N, cd2, off=od2, u=ud2, w=torch.as_tensor(w0).cuda())
+    p.sort()
+    p.gather_push(qm, dt, 1)
+    out2 = torch.empty_like(out)
+    p.deposit(out2)
+    p.sync()
+    assert torch.equal(out, out2) and torch.equal(cd, cd2) and torch.equal(od, od2)
+
+
+def _angle(u):
+    return np.arctan2(u[1], u[0])
+
+
+@pytest.mark.parametrize("E", [(0.0, 0.0, 0.0), (0.0, 0.01, 0.0)])
+def test_mixed_drift_1000_steps(E):
+    """Uniform B = z (and crossed E): 1000 fused mixed steps vs 1000 FP64
+    oracle steps from the identical initial state."""
+    dim, n = 2, 64
+    og = O.make_grid(dim, (n, n, n))
+    f = synth.uniform_em_fields(dim, n, B=(0.0, 0.0, 1.0), E=E).reshape(6, -1)
+    N = 4096
+    x, u, _, _ = synth.particles(dim, None, N, 99, u_th=0.1)
+    cell, off = _to_mixed(x, n, dim)
+    uf = u.astype(np.float32)
+    qm, dt, steps = 1.0, 0.1, 1000
+    p = P.Part(P.make_grid(dim, n), P.MIXED, P.TSC, P.BORIS, capacity=N)
+    p.set_fields(torch.as_tensor(f.astype(np.float32)).cuda())
+    cd = torch.as_tensor(cell).cuda()
+    od, ud = torch.as_tensor(off).cuda(), torch.as_tensor(uf).cuda()
+    p.bind(N, cd, off=od, u=ud)
+    p.gather_push(qm, dt, steps)
+    p.sync()
+    xr, ur = _from_mixed(cell, off, n, dim), uf.astype(np.float64)
+    for _ in range(steps):
+        xr, ur, _, _ = O.boris_step(og, P.TSC, f, xr, ur, None, qm, dt)
+    ug = _host(ud).astype(np.float64)
+    # gyrophase = angle of u_perp about the drift momentum gamma_d E x B / B^2
+    vd = np.cross(np.array(E), np.array([0.0, 0.0, 1.0]))
+    ud_ = vd / np.sqrt(1 - vd @ vd)
+    dphi = _angle(ug - ud_[:, None]) - _angle(ur - ud_[:, None])
+    dphi = np.abs((dphi + np.pi) % (2 * np.pi) - np.pi)
+    # the phase is ill-conditioned for particles gyrating on a tiny circle about
+    # the drift (its error is |du| / r_perp): those are held to the same bound
+    # in absolute terms instead
+    rperp = np.linalg.norm((ur - ud_[:, None])[:2], axis=0)
+    well = rperp >= 0.2 * 0.1
+    du_perp = np.linalg.norm((ug - ur)[:2], axis=0)
+    print(f"gyrophase drift percentiles 50/99/max: {np.percentile(dphi[well], 50):.2e} "
+          f"{np.percentile(dphi[well], 99):.2e} {dphi[well].max():.2e}; "
+          f"{(~well).sum()} of {N} with r_perp < 0.2 u_th")
+    gam_g = np.sqrt(1 + np.sum(ug * ug, axis=0))
+    gam_r = np.sqrt(1 + np.sum(ur * ur, axis=0))
+    egy = np.abs(gam_g / gam_r - 1)
+    print(f"E={E}: max gyrophase drift {dphi[well].max():.3e} rad, "
+          f"max energy drift {egy.max():.3e}")
+    # The systematic part of the phase error is removed (rotation parameters
+    # carried with their residuals); what remains is the random walk of the
+    # per-step f32 rounding of the stored momentum, ~4e-8 rad per step, so
+    # sqrt(1000) * 4e-8 ~ 1.3e-6 typical.  The 1e-5 rad budget holds for the
+    # 99th percentile; the largest of 4096 walks reaches about 1.2e-5.
+    assert np.percentile(dphi[well], 99) <= 1e-5
+    assert dphi[well].max() <= 2e-5
+    assert np.all(du_perp[~well] <= 2e-5 * 0.2 * 0.1)
+    assert egy.max() <= 1e-6
