@@ -174,6 +174,64 @@ const char* part_last_error(const part_ctx* ctx);
 /* Kernel launches this context has enqueued since creation.               */
 int64_t part_launch_count(const part_ctx* ctx);
 
+/* ---- Serving: continuous batching of test-particle requests --------------
+ * Test particles (no deposit) of many independent requests advance against
+ * field snapshots that stay resident on the device, each snapshot being a
+ * PART_MIXED / PART_BORIS context whose fields are set.  The caller (the
+ * scheduler) cuts the active requests into work items each round; one
+ * persistent kernel, replayed from a CUDA graph, advances every item.  Every
+ * particle is advanced with the same arithmetic as part_gather_push with
+ * nsteps > 1, so a request's result does not depend on what else is batched
+ * with it or on how its steps are sliced.  Not in the paper: it serves the
+ * particle push of Sec. 2 to many clients at once.                          */
+typedef struct {
+  int32_t* cell;       /* request state, device: int32 cell[stride]          */
+  float* off;          /*   f32 off[3][stride] (cell units, [-1/2, 1/2))     */
+  float* u;            /*   f32 u[3][stride]                                 */
+  int64_t stride;      /* particles of the request (row stride of off, u)    */
+  int64_t first;       /* first particle of this item                        */
+  int32_t count;       /* particles in this item, >= 0                       */
+  int32_t nsteps;      /* steps this item advances, >= 0                     */
+  int32_t snapshot;    /* index into the server's snapshot list              */
+  int32_t reserved;    /* 0                                                  */
+  double q_over_m;     /* charge-to-mass ratio of the request                */
+  double dt;           /* time step of the request, != 0                     */
+} part_work_item;      /* 72 bytes                                           */
+
+typedef struct part_server part_server;
+
+/* Device workspace and pinned host staging bytes of a server for nsnap
+ * snapshots and at most max_items items per round.                         */
+part_status part_server_sizes(int nsnap, int max_items, size_t* device_bytes,
+                              size_t* host_bytes);
+
+/* Create a server over nsnap snapshot contexts (all PART_MIXED, PART_BORIS,
+ * fields set, one shape and dim).  workspace: device, 256-byte aligned;
+ * host_stage: pinned host memory (cudaHostAlloc / pinned tensor) of
+ * host_bytes, in which the caller writes the work list (part_server_items).
+ * threads: CTA size (128..512, multiple of 32); ctas_per_sm: persistent CTAs
+ * per SM.  cuda_stream must be a created stream (not a default stream: the
+ * round is captured into a CUDA graph); the snapshot contexts should use the
+ * same stream.  The snapshot contexts must outlive the server.             */
+part_status part_server_init(part_server** out, part_ctx* const* snapshots, int nsnap,
+                             int max_items, void* workspace, size_t ws_bytes,
+                             void* host_stage, size_t host_bytes, void* cuda_stream,
+                             int threads, int ctas_per_sm);
+
+/* Host pointer to the work-item array inside the pinned staging buffer.    */
+part_work_item* part_server_items(part_server* s);
+
+/* Validate the first nitems items on the host (PART_EINVAL on a bad item,
+ * nothing launched), then enqueue one round: the copy of the work list to
+ * the device and the persistent kernel, as one CUDA graph (captured on the
+ * first call).  The staging buffer must not be rewritten until the round has
+ * completed (part_server_sync).                                            */
+part_status part_server_run(part_server* s, int nitems);
+
+/* Wait for the last round; return (and clear) a latched device error.      */
+part_status part_server_sync(part_server* s);
+part_status part_server_destroy(part_server* s);
+
 /* ---- Sort without any device allocation ----------------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory when they need a sort, so cannot provide the

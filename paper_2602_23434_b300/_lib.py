@@ -53,6 +53,16 @@ def make_grid(dim: int, n, xmin=(-1.0, -1.0, -1.0), L=(2.0, 2.0, 2.0)) -> Grid:
     return g
 
 
+class WorkItem(C.Structure):
+    """part_work_item of include/part.h (72 bytes)."""
+    _fields_ = [("cell", C.c_void_p), ("off", C.c_void_p), ("u", C.c_void_p),
+                ("stride", C.c_int64), ("first", C.c_int64), ("count", C.c_int32),
+                ("nsteps", C.c_int32), ("snapshot", C.c_int32), ("reserved", C.c_int32),
+                ("q_over_m", C.c_double), ("dt", C.c_double)]
+
+
+assert C.sizeof(WorkItem) == 72
+
 _lib = None
 
 
@@ -87,6 +97,15 @@ def lib():
         "part_sync": (st, [P]),
         "part_last_error": (C.c_char_p, [P]),
         "part_launch_count": (C.c_int64, [P]),
+        "part_sort_fp64_noalloc": (st, [G, C.c_int64, P, P, P, P, P, P]),
+        "part_server_sizes": (st, [C.c_int, C.c_int, C.POINTER(C.c_size_t),
+                                   C.POINTER(C.c_size_t)]),
+        "part_server_init": (st, [C.POINTER(P), C.POINTER(P), C.c_int, C.c_int, P, C.c_size_t,
+                                  P, C.c_size_t, P, C.c_int, C.c_int]),
+        "part_server_items": (C.POINTER(WorkItem), [P]),
+        "part_server_run": (st, [P, C.c_int]),
+        "part_server_sync": (st, [P]),
+        "part_server_destroy": (st, [P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)

@@ -88,6 +88,16 @@ struct part_ctx {
   std::string err;
 };
 
+// Serving: the device header of a work list and one resident snapshot.
+struct ServeHeader {
+  int nitems;
+  int pad[63];
+};
+struct SnapEntry {
+  const float* fp;  // padded f32 field copy of the snapshot's context
+  Geo g;
+};
+
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -165,6 +175,9 @@ cudaError_t launch_pad_fields(part_ctx* c, const void* src);
 cudaError_t launch_sort(part_ctx* c);
 cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps);
 cudaError_t launch_boris_mixed(part_ctx* c, double qm, double dt, int nsteps);
+cudaError_t launch_serve_kernel(int shape, int dim, const ServeHeader* hdr,
+                                const part_work_item* items, const SnapEntry* snaps, int nsnap,
+                                int* status, int grid, int threads, cudaStream_t stream);
 cudaError_t launch_deposit_combine(part_ctx* c, double* out);
 cudaError_t launch_lp_push(part_ctx* c, double dt, int nsteps);
 cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad);

@@ -328,6 +328,75 @@ __global__ void __launch_bounds__(kT, 2)
   }
 }
 
+// nsteps fused steps of one particle in registers: gather from the padded
+// global f32 copy, Boris, move.  Shared by the particle-order kernel and the
+// serving kernel so a particle gets the same bits whichever runs it.
+template <int SHAPE, int DIM>
+__device__ __forceinline__ void advance_mixed(const float* __restrict__ fp, const Geo& g, int* j,
+                                              float* o, float* up, float h, float hl,
+                                              const float* dtdx, int nsteps) {
+  for (int st = 0; st < nsteps; ++st) {
+    float wx[3], wy[3], wz[3] = {0.0f, 1.0f, 0.0f};
+    shape_weights<SHAPE>(o[0], wx);
+    shape_weights<SHAPE>(o[1], wy);
+    if (DIM == 3) shape_weights<SHAPE>(o[2], wz);
+    float f[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
+      const int zz = DIM == 3 ? j[2] + kz : 0;
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky) {
+        const float wzy = wz[kz] * wy[ky];
+        const int64_t row = ((int64_t)zz * g.pn[1] + j[1] + ky) * g.pn[0] + j[0];
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+          const float ww = wzy * wx[kx];
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) f[cc] += ww * __ldg(fp + cc * g.pplane + row + kx);
+        }
+      }
+    }
+    float du[3];
+    boris_f32(up, f, f + 3, h, hl, du);
+    const float gi = rsqrtf(1.0f + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) move_axis(o[a], j[a], up[a] * gi * dtdx[a], g.n[a]);
+  }
+}
+
+// Load one particle (stride = row stride of the SoA arrays), advance, store.
+template <int SHAPE, int DIM>
+__device__ __forceinline__ void particle_mixed(const float* __restrict__ fp, const Geo& g,
+                                               int32_t* __restrict__ cell, float* __restrict__ off,
+                                               float* __restrict__ u, int64_t stride, int64_t p,
+                                               float h, float hl, const float* dtdx, int nsteps,
+                                               int* __restrict__ status) {
+  int32_t c = cell[p];
+  bool bad = false;
+  if (c < 0 || c >= g.G) {
+    bad = true;
+    c = 0;
+  }
+  int j[3];
+  cell_coords(g, c, j);
+  float o[3], up[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    o[a] = off[a * stride + p];
+    up[a] = u[a * stride + p];
+  }
+  advance_mixed<SHAPE, DIM>(fp, g, j, o, up, h, hl, dtdx, nsteps);
+  if (bad || !(isfinite(up[0]) && isfinite(up[1]) && isfinite(up[2]) && isfinite(o[0]) &&
+               isfinite(o[1]) && isfinite(o[2])))
+    atomicOr(status, bad ? ST_DOMAIN : ST_NONFINITE);
+  cell[p] = (j[2] * g.n[1] + j[1]) * g.n[0] + j[0];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    off[a * stride + p] = o[a];
+    u[a * stride + p] = up[a];
+  }
+}
+
 template <int SHAPE, int DIM>
 __global__ void __launch_bounds__(256)
     k_boris_particles_mixed(const float* __restrict__ fp, const Geo g, int32_t* __restrict__ cell,
@@ -336,57 +405,44 @@ __global__ void __launch_bounds__(256)
                             int* __restrict__ status) {
   const float dtdx[3] = {dtdx0, dtdx1, dtdx2};
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    int32_t c = cell[p];
-    bool bad = false;
-    if (c < 0 || c >= g.G) {
-      bad = true;
-      c = 0;
-    }
-    int j[3];
-    cell_coords(g, c, j);
-    float o[3], up[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      o[a] = off[a * n + p];
-      up[a] = u[a * n + p];
-    }
-    for (int st = 0; st < nsteps; ++st) {
-      float wx[3], wy[3], wz[3] = {0.0f, 1.0f, 0.0f};
-      shape_weights<SHAPE>(o[0], wx);
-      shape_weights<SHAPE>(o[1], wy);
-      if (DIM == 3) shape_weights<SHAPE>(o[2], wz);
-      float f[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-      for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
-        const int zz = DIM == 3 ? j[2] + kz : 0;
-#pragma unroll
-        for (int ky = 0; ky < 3; ++ky) {
-          const float wzy = wz[kz] * wy[ky];
-          const int64_t row = ((int64_t)zz * g.pn[1] + j[1] + ky) * g.pn[0] + j[0];
-#pragma unroll
-          for (int kx = 0; kx < 3; ++kx) {
-            const float ww = wzy * wx[kx];
-#pragma unroll
-            for (int cc = 0; cc < 6; ++cc) f[cc] += ww * __ldg(fp + cc * g.pplane + row + kx);
-          }
-        }
+       p += (int64_t)gridDim.x * blockDim.x)
+    particle_mixed<SHAPE, DIM>(fp, g, cell, off, u, n, p, h, hl, dtdx, nsteps, status);
+}
+
+// Persistent serving kernel: CTA b takes work items b, b + gridDim.x, ...
+// (static assignment, no inter-CTA waits).  Each item is a slice of one
+// request's particles to advance nsteps steps against one resident field
+// snapshot; the per-item step parameters are formed in FP64 exactly as the
+// host forms them for part_gather_push.
+template <int SHAPE, int DIM>
+__global__ void __launch_bounds__(512)
+    k_serve_mixed(const ServeHeader* __restrict__ hdr, const part_work_item* __restrict__ items,
+                  const SnapEntry* __restrict__ snaps, int nsnap, int* __restrict__ status) {
+  __shared__ part_work_item s_it;
+  __shared__ SnapEntry s_sn;
+  __shared__ float s_par[5];
+  const int nitems = hdr->nitems;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_it = items[it];
+      int sn = s_it.snapshot;
+      if (sn < 0 || sn >= nsnap) {
+        atomicOr(status, ST_DOMAIN);
+        s_it.count = 0;
+        sn = 0;
       }
-      float du[3];
-      boris_f32(up, f, f + 3, h, hl, du);
-      const float gi = rsqrtf(1.0f + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) move_axis(o[a], j[a], up[a] * gi * dtdx[a], g.n[a]);
+      s_sn = snaps[sn];
+      const double hd = 0.5 * s_it.q_over_m * s_it.dt;
+      s_par[0] = (float)hd;
+      s_par[1] = (float)(hd - (double)s_par[0]);
+      for (int a = 0; a < 3; ++a) s_par[2 + a] = (float)(s_it.dt / s_sn.g.dx[a]);
     }
-    if (bad || !(isfinite(up[0]) && isfinite(up[1]) && isfinite(up[2]) && isfinite(o[0]) &&
-                 isfinite(o[1]) && isfinite(o[2])))
-      atomicOr(status, bad ? ST_DOMAIN : ST_NONFINITE);
-    cell[p] = (j[2] * g.n[1] + j[1]) * g.n[0] + j[0];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      off[a * n + p] = o[a];
-      u[a * n + p] = up[a];
-    }
+    __syncthreads();
+    const float dtdx[3] = {s_par[2], s_par[3], s_par[4]};
+    for (int64_t q = threadIdx.x; q < s_it.count; q += blockDim.x)
+      particle_mixed<SHAPE, DIM>(s_sn.fp, s_sn.g, s_it.cell, s_it.off, s_it.u, s_it.stride,
+                                 s_it.first + q, s_par[0], s_par[1], dtdx, s_it.nsteps, status);
   }
 }
 
@@ -448,4 +504,21 @@ cudaError_t launch_boris_mixed(part_ctx* c, double qm, double dt, int nsteps) {
                     : dispatch_mixed<PART_TSC, 2>(c, qm, dt, nsteps);
   return dim == 3 ? dispatch_mixed<PART_CIC, 3>(c, qm, dt, nsteps)
                   : dispatch_mixed<PART_CIC, 2>(c, qm, dt, nsteps);
+}
+
+cudaError_t launch_serve_kernel(int shape, int dim, const ServeHeader* hdr,
+                                const part_work_item* items, const SnapEntry* snaps, int nsnap,
+                                int* status, int grid, int threads, cudaStream_t stream) {
+  if (shape == PART_TSC) {
+    if (dim == 3)
+      k_serve_mixed<PART_TSC, 3><<<grid, threads, 0, stream>>>(hdr, items, snaps, nsnap, status);
+    else
+      k_serve_mixed<PART_TSC, 2><<<grid, threads, 0, stream>>>(hdr, items, snaps, nsnap, status);
+  } else {
+    if (dim == 3)
+      k_serve_mixed<PART_CIC, 3><<<grid, threads, 0, stream>>>(hdr, items, snaps, nsnap, status);
+    else
+      k_serve_mixed<PART_CIC, 2><<<grid, threads, 0, stream>>>(hdr, items, snaps, nsnap, status);
+  }
+  return cudaGetLastError();
 }
