@@ -321,6 +321,58 @@ def mixed_error_vs_fp64(torch, P, n=128, ppc=8, steps=20, seed=1236):
     return res
 
 
+def run_serving(torch, requests=200, seed=1239, load=0.7, budget_gb=16.0):
+    """Poisson stream of test-particle requests against 4 resident snapshots
+    (128^3 x2, 256^3 x2, turbulent, f32): N log-uniform in [1e3, 1e7],
+    steps log-uniform in [10, 1000], mixed precision, admitted by device
+    memory, batched by the persistent graph-replayed kernel.  The arrival rate
+    is `load` x the autotuned capacity / E[N steps]."""
+    from paper_2602_23434_b300 import serving as S
+    cap = 10 ** 7
+    snaps = [S.make_snapshot(torch, 128, seed, cap), S.make_snapshot(torch, 128, seed + 1, cap),
+             S.make_snapshot(torch, 256, seed + 2, cap), S.make_snapshot(torch, 256, seed + 3, cap)]
+    tune = S.autotune(torch, snaps, candidates=[(128, 4, 2048), (256, 4, 2048), (256, 8, 2048),
+                                                (512, 4, 4096)], n=1 << 22, steps=16,
+                      cache_path=os.path.join(ROOT, "_build", "autotune.json"))
+    rate = tune["psteps_per_s"]
+    en = (1e7 - 1e3) / np.log(1e4)
+    es = (1000 - 10) / np.log(100)
+    lam = load * rate / (en * es)
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / lam, requests)
+    arrivals = np.cumsum(gaps)
+    ns = np.exp(rng.uniform(np.log(1e3), np.log(1e7), requests)).astype(np.int64)
+    steps = np.exp(rng.uniform(np.log(10), np.log(1000), requests)).astype(np.int64)
+    which = rng.integers(0, 4, requests)
+    srv = S.Server(torch, snaps, int(budget_gb * 2 ** 30), chunk=tune["chunk"], slice_steps=32,
+                   threads=tune["threads"], ctas_per_sm=tune["ctas_per_sm"])
+    t0 = time.perf_counter()
+    srv.clock = lambda: time.perf_counter() - t0
+    k = 0
+    while k < requests or srv.queue or srv.active:
+        now = srv.clock()
+        while k < requests and arrivals[k] <= now:
+            srv.submit(int(which[k]), int(ns[k]), int(steps[k]), seed=seed * 1000 + k,
+                       arrival=float(arrivals[k]))
+            k += 1
+        if not srv.round() and k < requests:
+            time.sleep(max(0.0, min(0.01, arrivals[k] - srv.clock())))
+    wall = srv.clock()
+    st = srv.stats()
+    srv.close()
+    res = {"workload": f"{requests} Poisson requests at {load:.0%} of measured capacity, "
+                       "N ~ logU[1e3, 1e7], steps ~ logU[10, 1000], 4 resident snapshots "
+                       "(128^3 x2, 256^3 x2, f32), mixed precision",
+           "value": st["particle_steps"] / wall, "unit": "particle-steps/s",
+           "throughput_busy": st["throughput_busy"], "p50_s": st["p50_s"],
+           "p99_s": st["p99_s"], "rounds": st["rounds"], "wall_s": wall,
+           "arrival_rate_per_s": lam, "capacity_psteps_per_s": rate,
+           "autotune": {k2: tune[k2] for k2 in ("threads", "ctas_per_sm", "chunk")}}
+    del snaps
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_2d(torch, P, n=64, ppc=16, steps=100, seed=1235):
     dev = torch.device("cuda", torch.cuda.current_device())
     N = n * n * ppc
@@ -451,6 +503,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-extras", action="store_true", help="headline workload only")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests in the serving stream (the full stated stream is 2000)")
     ap.add_argument("--grid", type=int, default=128,
                     help="cells per axis of the headline workload (128 = the stated one; "
                          "smaller only for profiling captures)")
@@ -551,6 +605,10 @@ def main():
             line["mixed_error_vs_fp64"] = mixed_error_vs_fp64(torch, P)
         except Exception as e:
             line["mixed"] = {"error": repr(e)}
+        try:
+            line["serving"] = run_serving(torch, requests=args.serve_requests)
+        except Exception as e:
+            line["serving"] = {"error": repr(e)}
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
