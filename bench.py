@@ -495,6 +495,23 @@ def reference_arm(args):
 
 
 # ----------------------------------------------------------------------------- main
+def only(args):
+    """One secondary workload at --grid cells per axis (profiling captures)."""
+    import torch
+    from paper_2602_23434_b300 import _lib as P
+    from paper_2602_23434_b300.build import build
+    build()
+    if args.only == "mixed":
+        res = run_mixed(torch, P, args.grid, 8, args.steps, args.warmup, 1237)
+    elif args.only == "lp":
+        res = run_lp(torch, P, args.steps, args.warmup, n=args.grid,
+                     nlp=max(1 << 16, 2 * args.grid ** 3))
+    else:
+        res = run_serving(torch, requests=args.serve_requests)
+    print(json.dumps({"only": args.only, "grid": args.grid, **res}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -508,11 +525,16 @@ def main():
     ap.add_argument("--grid", type=int, default=128,
                     help="cells per axis of the headline workload (128 = the stated one; "
                          "smaller only for profiling captures)")
+    ap.add_argument("--only", choices=["mixed", "lp", "serving"], default=None,
+                    help="run one secondary workload alone at --grid cells per axis and print "
+                         "its result (for profiling captures); no headline line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
+    if args.only:
+        return only(args)
 
     import torch
     from paper_2602_23434_b300 import _lib as P

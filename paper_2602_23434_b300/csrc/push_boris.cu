@@ -7,10 +7,12 @@
 //      weights, gather from shared memory, Boris kick, drift, periodic wrap,
 //      coalesced SoA loads/stores;
 //   3. deposit (optional): each particle leaves its weights and force in
-//      shared memory; each thread owns cells of the haloed tile and sums the
-//      contributions of the chunk's particles in a fixed order (stencil
-//      offset, then particle index).  Register accumulators, no atomics;
-//   4. the haloed tile is written as this brick's partial; a second kernel
+//      shared memory; then warp w takes the chunk's source cells with x index
+//      w mod 8, one lane per stencil offset: every lane loops over the same
+//      particles (no divergence) and adds into the warp's private window of
+//      haloed-tile columns, in a fixed order.  No atomics;
+//   4. the windows are combined in warp order into the brick's haloed tile,
+//      written as this brick's partial; a second kernel
 //      adds, per grid cell, the partials of the bricks covering it in fixed
 //      order.  The result is bitwise reproducible.
 // Particle-order kernel (any order, no deposit): nsteps fused steps with the
@@ -21,15 +23,19 @@ namespace {
 
 constexpr int kT = kPushThreads;
 
-__host__ __device__ constexpr int ntargets(int dim) {
-  return dim == 3 ? (10 * 10 * 10 + kT - 1) / kT : (18 * 18 + kT - 1) / kT;
-}
-
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Shared-memory carve of the brick kernel.
+constexpr int kRS = kT + 1;      // record row stride (doubles): odd, so rows hit other banks
+constexpr int kWarps = kT / 32;
+
+// Deposit windows: warp w owns the source cells whose x index is w mod 8, so
+// its targets lie in the ext-tile columns w..w+2 (and w+8..w+10 for 16-wide
+// 2D bricks): kSlots(DIM) columns x e1 x e2 targets x 3 components.
+__host__ __device__ constexpr int kslots(int dim) { return dim == 3 ? 3 : 6; }
+
 struct BrickSmem {
-  size_t box, cs, bar, rec, total;
+  size_t box, cs, bar, rec, win, total;
 };
 __host__ __device__ inline BrickSmem brick_smem(const Geo& g, int ncomp, int esize) {
   BrickSmem s;
@@ -38,7 +44,8 @@ __host__ __device__ inline BrickSmem brick_smem(const Geo& g, int ncomp, int esi
   s.cs = align_up(bbytes, 128);
   s.bar = align_up(s.cs + (size_t)(g.V + 1) * 4, 16);
   s.rec = align_up(s.bar + 16, 128);
-  s.total = s.rec + (size_t)18 * kT * 8;
+  s.win = align_up(s.rec + (size_t)18 * kRS * 8, 128);
+  s.total = s.win + (size_t)kWarps * kslots(g.dim) * g.e[1] * g.e[2] * 3 * 8;
   return s;
 }
 
@@ -70,7 +77,7 @@ __device__ __forceinline__ void boris_f64(double* u, const double* E, const doub
 
 // ---------------------------------------------------------------- brick kernel, FP64
 template <int SHAPE, int DIM, bool DEP>
-__global__ void __launch_bounds__(kT, 2)
+__global__ void __launch_bounds__(kT, 1)
     k_boris_brick_f64(const __grid_constant__ CUtensorMap tmap, const Geo g,
                       double* __restrict__ x, double* __restrict__ u,
                       const double* __restrict__ w, int64_t n,
@@ -84,8 +91,12 @@ __global__ void __launch_bounds__(kT, 2)
   uint32_t* scs = reinterpret_cast<uint32_t*>(smem + L.cs);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
   int* sflag = reinterpret_cast<int*>(smem + L.bar + 8);
-  double* rw = reinterpret_cast<double*>(smem + L.rec);  // [9][kT] wz*wy
-  double* rf = rw + 9 * kT;                              // [9][kT] wx[k]*F[c]
+  double* rw = reinterpret_cast<double*>(smem + L.rec);  // [9][kRS] wz*wy
+  double* rf = rw + 9 * kRS;                             // [9][kRS] wx[k]*F[c]
+  double* win = reinterpret_cast<double*>(smem + L.win); // [warp][slot][e2][e1][3]
+  constexpr int NS = kslots(DIM);
+  const int wsize = NS * g.e[1] * g.e[2] * 3;
+  const int warp = tid >> 5, lane = tid & 31;
 
   const int64_t brick = blockIdx.x;
   const int bx = (int)(brick % g.nb[0]);
@@ -105,6 +116,8 @@ __global__ void __launch_bounds__(kT, 2)
     tma_load_4d(sbox, &tmap, bar, o0, o1, o2, 0);
   }
   for (int i = tid; i <= g.V; i += kT) scs[i] = cstart[brick * g.V + i];
+  if (DEP)
+    for (int i = tid; i < kWarps * wsize; i += kT) win[i] = 0.0;
   if (!mbar_wait_bounded(bar, 0)) atomicOr(sflag, 1);
   __syncthreads();
   if (*sflag) {
@@ -115,14 +128,10 @@ __global__ void __launch_bounds__(kT, 2)
     return;
   }
 
-  constexpr int NT = ntargets(DIM);
-  double acc[NT][3];
-#pragma unroll
-  for (int q = 0; q < NT; ++q) acc[q][0] = acc[q][1] = acc[q][2] = 0.0;
-
   const double h = 0.5 * qm * dt;
   const uint32_t p0 = scs[0], p1 = scs[g.V];
   const int org[3] = {o0, o1, o2};
+  int cfirst = 0;  // first brick cell with particles at or after `base`
   for (uint32_t base = p0; base < p1; base += kT) {
     const uint32_t p = base + tid;
     double wyz[9], fxc[9];
@@ -205,53 +214,70 @@ __global__ void __launch_bounds__(kT, 2)
     if (DEP) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        rw[k * kT + tid] = wyz[k];
-        rf[k * kT + tid] = fxc[k];
+        rw[k * kRS + tid] = wyz[k];
+        rf[k * kRS + tid] = fxc[k];
       }
       __syncthreads();
-      const int hz = DIM == 3 ? 1 : 0;
-#pragma unroll
-      for (int q = 0; q < NT; ++q) {
-        const int t = tid + q * kT;
-        if (t < g.ev) {
-          const int ex = t % g.e[0];
-          const int ey = (t / g.e[0]) % g.e[1];
-          const int ez = t / (g.e[0] * g.e[1]);
-          for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
-            const int lz = ez - hz - (kz - 1);
-            if (lz < 0 || lz >= g.b[2]) continue;
-            for (int ky = 0; ky < 3; ++ky) {
-              const int ly = ey - ky;
-              if (ly < 0 || ly >= g.b[1]) continue;
-              for (int kx = 0; kx < 3; ++kx) {
-                const int lx = ex - kx;
-                if (lx < 0 || lx >= g.b[0]) continue;
-                const int ls = (lz * g.b[1] + ly) * g.b[0] + lx;
-                uint32_t r0 = scs[ls], r1 = scs[ls + 1];
-                r0 = r0 > base ? r0 : base;
-                r1 = r1 < base + kT ? r1 : base + kT;
-                for (uint32_t r = r0; r < r1; ++r) {
-                  const int i = (int)(r - base);
-                  const double ww = rw[(kz * 3 + ky) * kT + i];
-                  acc[q][0] += ww * rf[(kx * 3 + 0) * kT + i];
-                  acc[q][1] += ww * rf[(kx * 3 + 1) * kT + i];
-                  acc[q][2] += ww * rf[(kx * 3 + 2) * kT + i];
-                }
-              }
-            }
+      // cells whose particles meet this chunk: [cfirst, clast]
+      const uint32_t bend = base + kT < p1 ? base + kT : p1;
+      while (scs[cfirst + 1] <= base) ++cfirst;
+      int clast = cfirst;
+      while (clast + 1 < g.V && scs[clast + 1] < bend) ++clast;
+      // warp w: cells s with s mod 8 == w, one lane per stencil offset; every
+      // lane loops over the same particles, so the loop does not diverge
+      const int s0 = cfirst + ((warp - cfirst % 8) + 8) % 8;
+      for (int sc = s0; sc <= clast; sc += 8) {
+        uint32_t r0 = scs[sc], r1 = scs[sc + 1];
+        r0 = r0 > base ? r0 : base;
+        r1 = r1 < bend ? r1 : bend;
+        const int nk = DIM == 3 ? 27 : 9;
+        if (lane < nk && r0 < r1) {
+          const int kz = DIM == 3 ? lane / 9 : 1;
+          const int ky = DIM == 3 ? (lane / 3) % 3 : lane / 3;
+          const int kx = lane % 3;
+          const double* pw = rw + (kz * 3 + ky) * kRS;
+          const double* pf = rf + (kx * 3) * kRS;
+          double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+          for (uint32_t r = r0; r < r1; ++r) {
+            const int i = (int)(r - base);
+            const double ww = pw[i];
+            a0 += ww * pf[i];
+            a1 += ww * pf[kRS + i];
+            a2 += ww * pf[2 * kRS + i];
           }
+          const int lx = sc % g.b[0], ly = (sc / g.b[0]) % g.b[1], lz = sc / (g.b[0] * g.b[1]);
+          const int ex = lx + kx, ey = ly + ky, ez = DIM == 3 ? lz + kz : 0;
+          const int col = ex - warp < 3 ? ex - warp : ex - warp - 5;   // slot in the window
+          double* wp = win + warp * wsize + ((col * g.e[2] + ez) * g.e[1] + ey) * 3;
+          wp[0] += a0;
+          wp[1] += a1;
+          wp[2] += a2;
         }
+        __syncwarp();
       }
       __syncthreads();
     }
   }
   if (DEP) {
-#pragma unroll
-    for (int q = 0; q < NT; ++q) {
-      const int t = tid + q * kT;
-      if (t < g.ev)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) dpart[(brick * 3 + c) * g.ev + t] = acc[q][c];
+    // combine the warp windows in warp order into the brick's haloed tile
+    for (int t = tid; t < g.ev; t += kT) {
+      const int ex = t % g.e[0], ey = (t / g.e[0]) % g.e[1], ez = t / (g.e[0] * g.e[1]);
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+      for (int w = 0; w < kWarps; ++w) {
+        int col = ex - w;
+        if (col < 0) continue;
+        if (col >= 3) {
+          if (DIM == 3 || col < 8 || col >= 11) continue;
+          col -= 5;
+        }
+        const double* wp = win + w * wsize + ((col * g.e[2] + ez) * g.e[1] + ey) * 3;
+        s0 += wp[0];
+        s1 += wp[1];
+        s2 += wp[2];
+      }
+      dpart[(brick * 3 + 0) * g.ev + t] = s0;
+      dpart[(brick * 3 + 1) * g.ev + t] = s1;
+      dpart[(brick * 3 + 2) * g.ev + t] = s2;
     }
   }
 }
