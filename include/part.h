@@ -119,8 +119,13 @@ part_status part_bind_particles(part_ctx* ctx, int64_t n, void* x_or_cell, void*
                                 double* n_old);
 
 /* Sort the bound particles by cell key (stable: equal keys keep their current
- * order), permuting every bound array in place, and rebuild cell_start.
- * Required before a push with deposit enabled.                            */
+ * order), permuting every bound array, and rebuild cell_start.  Required
+ * before a push with deposit enabled.  Boris modes: the sorted state is
+ * gathered into the workspace and the next one-step push reads it from there
+ * while writing the bound arrays (no copy-back pass); any other call that
+ * needs the bound arrays (part_sync, part_bind_particles, part_sort, a
+ * multi-step push) first copies it home.  Between part_sort and the next such
+ * call the bound arrays must be neither read nor written by the caller.    */
 part_status part_sort(part_ctx* ctx);
 
 /* Device pointer to cell_start[nkeys + 1] (valid after part_sort): the

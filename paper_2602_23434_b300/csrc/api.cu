@@ -65,8 +65,11 @@ void make_geo(const part_grid* gr, int esize, Geo* g) {
     g->inv_dx[a] = 1.0 / gr->dx[a];
     g->L[a] = (double)gr->n[a] * gr->dx[a];
     g->xmax[a] = gr->xmin[a] + g->L[a];
+    g->invn[a] = 1.0f / (float)gr->n[a];
   }
-  const int q = 16 / esize;  // elements per 16 bytes
+  // FP64: component planes with the x pitch rounded to 16 bytes.  f32 (mixed
+  // form): cells interleave 8 floats (32 bytes), so no x rounding is needed.
+  const int q = esize == 4 ? 1 : 16 / esize;
   g->pn[0] = (g->n[0] + 2 * g->h[0] + q - 1) / q * q;
   g->pn[1] = g->n[1] + 2 * g->h[1];
   g->pn[2] = g->n[2] + 2 * g->h[2];
@@ -84,11 +87,15 @@ void make_geo(const part_grid* gr, int esize, Geo* g) {
 namespace {
 
 struct Layout {
-  size_t fpad, keys0, keys1, vals0, vals1, hist, hsum, cstart, tmp, dpart, samples, status, total;
+  size_t fpad, keys0, keys1, vals0, vals1, hist, hsum, cstart, tmp, dpart, samples, status,
+      alt_x, alt_off, alt_u, alt_w, alt_id, total;
 };
 
 int ncomp_of(part_mode m) { return m == PART_BORIS ? 6 : 7; }
 int esize_of(part_prec p) { return p == PART_FP64 ? 8 : 4; }
+// components stored per cell of the padded copy: the mixed form keeps E, B
+// and two zero pads interleaved per cell (one 32-byte record)
+int fcomp_of(part_prec p, part_mode m) { return p == PART_MIXED ? 8 : ncomp_of(m); }
 
 Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int nbins) {
   Layout L;
@@ -102,7 +109,7 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   const int64_t ntiles = (c1 + kSortTile - 1) / kSortTile;
   const int64_t hlen = ntiles * kRadix;
   const int64_t nblk = (hlen + kScanBlock - 1) / kScanBlock;
-  L.fpad = take((size_t)ncomp_of(mode) * g.pplane * esize_of(prec));
+  L.fpad = take((size_t)fcomp_of(prec, mode) * g.pplane * esize_of(prec));
   L.keys0 = take((size_t)c1 * 4);
   L.keys1 = take((size_t)c1 * 4);
   L.vals0 = take((size_t)c1 * 4);
@@ -116,6 +123,14 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   L.dpart = take(mode == PART_BORIS ? (size_t)g.nbricks * 3 * g.ev * 8 : 0);
   L.samples = take(mode == PART_LP_RK2 ? (size_t)3 * c1 * 8 : 0);
   L.status = take(256);
+  // alternate particle buffers of the Boris modes (sorted state awaiting the push)
+  const bool alt = mode == PART_BORIS;
+  const size_t e = esize_of(prec);
+  L.alt_x = take(alt ? (size_t)c1 * (prec == PART_FP64 ? 3 * 8 : 4) : 0);
+  L.alt_off = take(alt && prec == PART_MIXED ? (size_t)c1 * 12 : 0);
+  L.alt_u = take(alt ? (size_t)c1 * 3 * e : 0);
+  L.alt_w = take(alt ? (size_t)c1 * e : 0);
+  L.alt_id = take(alt ? (size_t)c1 * 8 : 0);
   L.total = off;
   return L;
 }
@@ -150,6 +165,20 @@ part_status encode_tmap(part_ctx* c) {
                            (cuuint64_t)g.pplane * es};
   cuuint32_t box[4] = {(cuuint32_t)g.box[0], (cuuint32_t)g.box[1], (cuuint32_t)g.box[2],
                        (cuuint32_t)c->ncomp};
+  if (c->fcomp == 8) {  // cell-interleaved f32: (comp, x, y, z), 32 bytes per cell
+    const cuuint64_t cb = 8 * es;
+    dims[0] = 8;
+    dims[1] = (cuuint64_t)g.pn[0];
+    dims[2] = (cuuint64_t)g.pn[1];
+    dims[3] = (cuuint64_t)g.pn[2];
+    strides[0] = cb;
+    strides[1] = cb * g.pn[0];
+    strides[2] = cb * g.pn[0] * g.pn[1];
+    box[0] = 8;
+    box[1] = (cuuint32_t)g.box[0];
+    box[2] = (cuuint32_t)g.box[1];
+    box[3] = (cuuint32_t)g.box[2];
+  }
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = encode(&c->tmap,
                       c->esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
@@ -215,6 +244,7 @@ part_status part_init(part_ctx** out, const part_grid* grid, part_prec prec, par
   c->nbins = mode == PART_LP_RK2 ? nbins : 0;
   c->stream = (cudaStream_t)cuda_stream;
   c->ncomp = ncomp_of(mode);
+  c->fcomp = fcomp_of(prec, mode);
   c->esize = esize_of(prec);
   make_geo(grid, c->esize, &c->geo);
   Layout L = layout_of(c->geo, prec, mode, capacity, c->nbins);
@@ -236,6 +266,13 @@ part_status part_init(part_ctx** out, const part_grid* grid, part_prec prec, par
   c->dpart = mode == PART_BORIS ? (double*)(c->ws + L.dpart) : nullptr;
   c->samples = mode == PART_LP_RK2 ? (double*)(c->ws + L.samples) : nullptr;
   c->status = (int*)(c->ws + L.status);
+  if (mode == PART_BORIS) {
+    c->alt_x = c->ws + L.alt_x;
+    c->alt_off = prec == PART_MIXED ? c->ws + L.alt_off : nullptr;
+    c->alt_u = c->ws + L.alt_u;
+    c->alt_w = c->ws + L.alt_w;
+    c->alt_id = (uint64_t*)(c->ws + L.alt_id);
+  }
   cudaError_t e = cudaMemsetAsync(c->status, 0, 256, c->stream);
   if (e != cudaSuccess) {
     part_status r = cuda_fail(nullptr, e, "status reset");
@@ -274,6 +311,10 @@ part_status part_bind_particles(part_ctx* c, int64_t n, void* x_or_cell, void* o
                                 double* n_old) {
   if (check_ctx(c)) return PART_EINVAL;
   if (n < 0 || n > c->capacity) return fail(c, PART_EINVAL, "n must be in [0, capacity]");
+  if (c->pending) {  // sorted state of the previous arrays goes home first
+    cudaError_t e = flush_pending(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "part_bind_particles");
+  }
   if (n > 0 && !x_or_cell) return fail(c, PART_EINVAL, "positions are NULL");
   if (c->mode == PART_BORIS) {
     if (n > 0 && !u) return fail(c, PART_EINVAL, "u is NULL");
@@ -302,7 +343,8 @@ part_status part_bind_particles(part_ctx* c, int64_t n, void* x_or_cell, void* o
 part_status part_sort(part_ctx* c) {
   if (check_ctx(c)) return PART_EINVAL;
   if (!c->bound) return fail(c, PART_EINVAL, "no particles bound");
-  cudaError_t e = launch_sort(c);
+  cudaError_t e = flush_pending(c);
+  if (e == cudaSuccess) e = launch_sort(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_sort");
   c->sorted = true;
   return PART_OK;
@@ -335,7 +377,14 @@ part_status part_gather_push(part_ctx* c, double q_over_m, double dt, int nsteps
       return fail(c, PART_EINVAL, "deposit needs nsteps == 1 (fused steps are test particles)");
     if (c->deposit_on && !c->sorted)
       return fail(c, PART_EINVAL, "deposit needs part_sort since the last push");
+    // the brick kernel (sorted, one step) reads the pending sorted state
+    // directly; every other path needs it in the bound arrays first
+    if (c->pending && !(c->sorted && nsteps == 1)) {
+      e = flush_pending(c);
+      if (e != cudaSuccess) return cuda_fail(c, e, "part_gather_push");
+    }
     e = launch_boris(c, q_over_m, dt, nsteps);
+    c->pending = false;
     if (e == cudaErrorNotSupported)
       return fail(c, PART_EUNSUPPORTED, "this precision/mode has no kernel in this build");
     c->deposit_ready = c->deposit_on;
@@ -383,6 +432,7 @@ part_status part_init_particles(part_ctx* c, uint64_t seed, double u_th, double 
   } else if (!std::isfinite(u_th) || u_th < 0.0) {
     return fail(c, PART_EINVAL, "u_th must be finite and >= 0");
   }
+  c->pending = false;  // every bound array is overwritten
   cudaError_t e = launch_init(c, seed, u_th, eps_min, eps_max, p_index, N0);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_init_particles");
   c->sorted = false;
@@ -394,7 +444,9 @@ part_status part_init_particles(part_ctx* c, uint64_t seed, double u_th, double 
 part_status part_sync(part_ctx* c) {
   if (check_ctx(c)) return PART_EINVAL;
   int st = 0;
-  cudaError_t e = cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = flush_pending(c);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_sync");
   if (st == 0) return PART_OK;

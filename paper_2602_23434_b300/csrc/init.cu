@@ -158,6 +158,29 @@ __global__ void k_pad_fields(const T* __restrict__ src, T* __restrict__ dst, con
   }
 }
 
+// Mixed form: cell-interleaved copy, 8 floats per padded cell (6 components,
+// 2 zero pads), so one stencil point is two 16-byte loads.
+__global__ void k_pad_fields_aos8(const float* __restrict__ src, float* __restrict__ dst,
+                                  const Geo g, int ncomp) {
+  const int64_t total = 8 * g.pplane;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(q & 7);
+    const int64_t r = q >> 3;
+    const int px = (int)(r % g.pn[0]);
+    const int py = (int)((r / g.pn[0]) % g.pn[1]);
+    const int pz = (int)(r / ((int64_t)g.pn[0] * g.pn[1]));
+    if (c >= ncomp || px >= g.n[0] + 2 * g.h[0]) {
+      dst[q] = 0.0f;
+      continue;
+    }
+    const int sx = (px - g.h[0] + g.n[0]) % g.n[0];
+    const int sy = (py - g.h[1] + g.n[1]) % g.n[1];
+    const int sz = (pz - g.h[2] + g.n[2]) % g.n[2];
+    dst[q] = src[(int64_t)c * g.G + ((int64_t)sz * g.n[1] + sy) * g.n[0] + sx];
+  }
+}
+
 int grid_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -168,8 +191,11 @@ int grid_for(int64_t n, int threads) {
 }  // namespace
 
 cudaError_t launch_pad_fields(part_ctx* c, const void* src) {
-  const int64_t total = (int64_t)c->ncomp * c->geo.pplane;
-  if (c->esize == 8)
+  const int64_t total = (int64_t)c->fcomp * c->geo.pplane;
+  if (c->fcomp == 8 && c->esize == 4)
+    k_pad_fields_aos8<<<grid_for(total, 256), 256, 0, c->stream>>>(
+        (const float*)src, (float*)c->fpad, c->geo, c->ncomp);
+  else if (c->esize == 8)
     k_pad_fields<double><<<grid_for(total, 256), 256, 0, c->stream>>>(
         (const double*)src, (double*)c->fpad, c->geo, c->ncomp);
   else

@@ -45,46 +45,59 @@ struct Geo {
   int64_t nbricks;
   int64_t pplane;  // padded elements per field component
   double xmin[3], dx[3], inv_dx[3], L[3], xmax[3];
+  float invn[3];   // 1/n per axis, for the float-reciprocal cell decode
 };
 
+// Every member has a default initializer: a context built on the stack (the
+// no-allocation sort) starts with null buffers and no pending state.
 struct part_ctx {
-  part_grid grid;
-  part_prec prec;
-  part_shape shape;
-  part_mode mode;
-  int64_t capacity;
-  int nbins;
-  cudaStream_t stream;
-  Geo geo;
-  int ncomp;        // field components (6 Boris, 7 LP)
-  int esize;        // field element bytes
+  part_grid grid{};
+  part_prec prec{};
+  part_shape shape{};
+  part_mode mode{};
+  int64_t capacity{};
+  int nbins{};
+  cudaStream_t stream{};
+  Geo geo{};
+  int ncomp{};        // field components (6 Boris, 7 LP)
+  int fcomp{};        // components per cell as stored: SoA ncomp, or 8 (cell-interleaved f32)
+  int esize{};        // field element bytes
   // workspace carve-up
-  char* ws;
-  size_t ws_bytes;
-  void* fpad;       // padded fields [ncomp][pz][py][px]
-  uint32_t* keys[2];
-  uint32_t* vals[2];
-  uint32_t* hist;   // radix tile histograms (digit-major)
-  uint32_t* hsum;   // scan block sums
-  uint32_t* cstart; // cell_start [nkeys + 1]
-  void* tmp;        // permute scratch, 8 bytes * capacity
-  double* dpart;    // deposit partials [nbricks][3][ev]
-  double* samples;  // LP samples [3][capacity]: n_new, b2m, gamma_g
-  int* status;      // device status word
-  CUtensorMap tmap; // TMA map of fpad
-  bool tmap_ok;
+  char* ws{};
+  size_t ws_bytes{};
+  void* fpad{};       // padded fields [ncomp][pz][py][px]
+  uint32_t* keys[2] = {};
+  uint32_t* vals[2] = {};
+  uint32_t* hist{};   // radix tile histograms (digit-major)
+  uint32_t* hsum{};   // scan block sums
+  uint32_t* cstart{}; // cell_start [nkeys + 1]
+  void* tmp{};        // permute scratch, 8 bytes * capacity
+  double* dpart{};    // deposit partials [nbricks][3][ev]
+  double* samples{};  // LP samples [3][capacity]: n_new, b2m, gamma_g
+  // Boris modes: alternate particle buffers.  part_sort gathers the bound
+  // arrays into them ("pending"); the next brick push reads them and writes
+  // the caller's arrays, so no copy-back pass is needed.  NULL: in-place sort.
+  void* alt_x{};      // FP64: double[3][cap]   mixed: int32 cell[cap]
+  void* alt_off{};    // mixed: float[3][cap]
+  void* alt_u{};      // FP64: double[3][cap]   mixed: float[3][cap]
+  void* alt_w{};      // FP64: double[cap]      mixed: float[cap]
+  uint64_t* alt_id{}; // uint64[cap]
+  bool pending{};     // sorted state lives in the alt buffers
+  int* status{};      // device status word
+  CUtensorMap tmap{};  // TMA map of fpad
+  bool tmap_ok{};
   // bound particles
-  int64_t n;
-  void* x;
-  void* off;
-  void* u;
-  void* w;
-  uint64_t* id;
-  double* chi;
-  double* eng;
-  double* n_old;
-  bool bound, fields_set, sorted, deposit_on, deposit_ready, samples_ready;
-  int64_t launches;
+  int64_t n{};
+  void* x{};
+  void* off{};
+  void* u{};
+  void* w{};
+  uint64_t* id{};
+  double* chi{};
+  double* eng{};
+  double* n_old{};
+  bool bound{}, fields_set{}, sorted{}, deposit_on{}, deposit_ready{}, samples_ready{};
+  int64_t launches{};
   std::string err;
 };
 
@@ -144,6 +157,11 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// Finite test on the exponent bits (integer pipe): true unless v is Inf/NaN.
+__device__ __forceinline__ bool finite_bits(double v) {
+  return ((unsigned)__double2hiint(v) & 0x7ff00000u) != 0x7ff00000u;
+}
+
 // ---------------------------------------------------------------- shape weights
 // Three-point weights at offsets k = -1, 0, +1 from the particle's cell for
 // offset d = (s - j) - 1/2 in [-1/2, 1/2].  TSC: quadratic B-spline; CIC: hat
@@ -173,6 +191,7 @@ void make_geo(const part_grid* gr, int esize, Geo* g);
 // of its launch and counts the launches it made in *launches.
 cudaError_t launch_pad_fields(part_ctx* c, const void* src);
 cudaError_t launch_sort(part_ctx* c);
+cudaError_t flush_pending(part_ctx* c);  // copy pending sorted state to the bound arrays
 cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps);
 cudaError_t launch_boris_mixed(part_ctx* c, double qm, double dt, int nsteps);
 cudaError_t launch_serve_kernel(int shape, int dim, const ServeHeader* hdr,

@@ -79,10 +79,11 @@ __device__ __forceinline__ void boris_f64(double* u, const double* E, const doub
 template <int SHAPE, int DIM, bool DEP>
 __global__ void __launch_bounds__(kT, 1)
     k_boris_brick_f64(const __grid_constant__ CUtensorMap tmap, const Geo g,
-                      double* __restrict__ x, double* __restrict__ u,
-                      const double* __restrict__ w, int64_t n,
+                      const double* xs, const double* us, const double* ws,
+                      const uint64_t* ids, double* x, double* u, double* wd, uint64_t* idd,
+                      int64_t n,
                       const uint32_t* __restrict__ cstart, double* __restrict__ dpart,
-                      double qm, double dt, int* __restrict__ status) {
+                      double qm, double dt, double inv_dt, int* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char smem[];
   const BrickSmem L = brick_smem(g, 6, 8);
   const int tid = threadIdx.x;
@@ -141,10 +142,13 @@ __global__ void __launch_bounds__(kT, 1)
       double xp[3], up[3], uo[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        xp[a] = x[a * n + p];
-        up[a] = u[a * n + p];
+        xp[a] = xs[a * n + p];
+        up[a] = us[a * n + p];
         uo[a] = up[a];
       }
+      const double wp = ws ? ws[p] : 1.0;
+      if (ws && wd != ws) wd[p] = wp;             // carry the read-only planes over
+      if (ids && idd != ids) idd[p] = ids[p];
       int l[3] = {0, 0, 0};
       double d[3] = {0.0, 0.0, 0.0};
       bool ok = true;
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(kT, 1)
         int j = f >= (double)g.n[a] ? g.n[a] - 1 : (f < 0.0 ? 0 : (int)f);
         d[a] = __dsub_rn(__dsub_rn(s, (double)j), 0.5);
         l[a] = j - org[a];
-        ok = ok && l[a] >= 0 && l[a] < g.b[a] && isfinite(s);
+        ok = ok && l[a] >= 0 && l[a] < g.b[a] && finite_bits(s);
       }
       if (ok) {  // the particle must sit in the cell it was sorted into
         const int lc = (l[2] * g.b[1] + l[1]) * g.b[0] + l[0];
@@ -163,6 +167,11 @@ __global__ void __launch_bounds__(kT, 1)
       }
       if (!ok) {
         atomicOr(status, ST_DOMAIN);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {  // left as it was
+          x[a * n + p] = xp[a];
+          u[a * n + p] = up[a];
+        }
       } else {
         double wx[3], wy[3], wz[3] = {0.0, 1.0, 0.0};
         shape_weights<SHAPE>(d[0], wx);
@@ -191,8 +200,8 @@ __global__ void __launch_bounds__(kT, 1)
 #pragma unroll
         for (int a = 0; a < DIM; ++a)
           xp[a] = wrap_axis(xp[a] + dt * (up[a] * gi), g.xmin[a], g.xmax[a], g.L[a]);
-        bool fin = isfinite(up[0]) && isfinite(up[1]) && isfinite(up[2]) &&
-                   isfinite(xp[0]) && isfinite(xp[1]) && isfinite(xp[2]);
+        bool fin = finite_bits(up[0]) && finite_bits(up[1]) && finite_bits(up[2]) &&
+                   finite_bits(xp[0]) && finite_bits(xp[1]) && finite_bits(xp[2]);
         if (!fin) atomicOr(status, ST_NONFINITE);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -200,7 +209,7 @@ __global__ void __launch_bounds__(kT, 1)
           u[a * n + p] = up[a];
         }
         if (DEP) {
-          const double wdt = (w ? w[p] : 1.0) / dt;
+          const double wdt = wp * inv_dt;
           double F[3];
 #pragma unroll
           for (int a = 0; a < 3; ++a) F[a] = (up[a] - uo[a]) * wdt;
@@ -417,9 +426,13 @@ cudaError_t brick_f64(part_ctx* c, double qm, double dt) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L.total);
   if (e != cudaSuccess) return e;
+  const bool alt = c->pending;  // sorted state waits in the alternate buffers
   kern<<<(unsigned)c->geo.nbricks, kT, L.total, c->stream>>>(
-      c->tmap, c->geo, (double*)c->x, (double*)c->u, (const double*)c->w, c->n, c->cstart,
-      c->dpart, qm, dt, c->status);
+      c->tmap, c->geo, (const double*)(alt ? c->alt_x : c->x),
+      (const double*)(alt ? c->alt_u : c->u),
+      (const double*)(c->w ? (alt ? c->alt_w : c->w) : nullptr),
+      c->id ? (alt ? c->alt_id : c->id) : nullptr, (double*)c->x, (double*)c->u,
+      (double*)c->w, c->id, c->n, c->cstart, c->dpart, qm, dt, 1.0 / dt, c->status);
   c->launches++;
   return cudaGetLastError();
 }

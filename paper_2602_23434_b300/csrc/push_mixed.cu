@@ -33,7 +33,7 @@ struct MixedSmem {
 };
 __host__ __device__ inline MixedSmem mixed_smem(const Geo& g) {
   MixedSmem s;
-  size_t bbytes = (size_t)6 * g.box[0] * g.box[1] * g.box[2] * 4;
+  size_t bbytes = (size_t)8 * g.box[0] * g.box[1] * g.box[2] * 4;  // 8 floats per cell
   s.cs = align_up(bbytes, 128);
   s.bar = align_up(s.cs + (size_t)(g.V + 1) * 4, 16);
   s.rec = align_up(s.bar + 16, 128);
@@ -110,11 +110,41 @@ __device__ __forceinline__ void two_sum_add(float* hi, float* lo, float x) {
   *lo += err;
 }
 
+// q = c / n, r = c % n for 0 <= c < 2^24 by a float reciprocal and one exact
+// integer correction (the float quotient is within 1 of the true one).
+__device__ __forceinline__ int divmod_f(int c, int n, float invn, int* r) {
+  int q = (int)(__int2float_rn(c) * invn);
+  int rr = c - q * n;
+  if (rr < 0) {
+    --q;
+    rr += n;
+  } else if (rr >= n) {
+    ++q;
+    rr -= n;
+  }
+  *r = rr;
+  return q;
+}
+
 __device__ __forceinline__ void cell_coords(const Geo& g, int32_t c, int* j) {
-  j[0] = c % g.n[0];
-  const int r = c / g.n[0];
-  j[1] = r % g.n[1];
-  j[2] = r / g.n[1];
+  if (g.G <= (1 << 24) && c >= 0) {
+    const int r = divmod_f(c, g.n[0], g.invn[0], &j[0]);
+    j[2] = divmod_f(r, g.n[1], g.invn[1], &j[1]);
+  } else {
+    j[0] = c % g.n[0];
+    const int r = c / g.n[0];
+    j[1] = r % g.n[1];
+    j[2] = r / g.n[1];
+  }
+}
+
+// Stencil point accumulate: six field components of one cell (two 16-byte
+// loads of the cell-interleaved copy) weighted by ww, as three paired FMAs.
+__device__ __forceinline__ void acc_point(float2* f, float ww, float4 a, float4 b) {
+  const float2 w2 = make_float2(ww, ww);
+  f[0] = __ffma2_rn(w2, make_float2(a.x, a.y), f[0]);
+  f[1] = __ffma2_rn(w2, make_float2(a.z, a.w), f[1]);
+  f[2] = __ffma2_rn(w2, make_float2(b.x, b.y), f[2]);
 }
 
 // Move in cell units: off += dv; whole cells carry into j (periodic).
@@ -130,8 +160,9 @@ __device__ __forceinline__ void move_axis(float& off, int& j, float dv, int n) {
 template <int SHAPE, int DIM, bool DEP>
 __global__ void __launch_bounds__(kT, 2)
     k_boris_brick_mixed(const __grid_constant__ CUtensorMap tmap, const Geo g,
-                        int32_t* __restrict__ cell, float* __restrict__ off,
-                        float* __restrict__ u, const float* __restrict__ w, int64_t n,
+                        const int32_t* cells, const float* offs, const float* us,
+                        const float* w, const uint64_t* ids, int32_t* cell, float* off,
+                        float* u, float* wd, uint64_t* idd, int64_t n,
                         const uint32_t* __restrict__ cstart, double* __restrict__ dpart,
                         float h, float hl, float dtdx0, float dtdx1, float dtdx2, float inv_dt,
                         int* __restrict__ status) {
@@ -160,8 +191,8 @@ __global__ void __launch_bounds__(kT, 2)
   }
   __syncthreads();
   if (tid == 0) {
-    mbar_arrive_expect_tx(bar, (uint32_t)(6 * bvol * 4));
-    tma_load_4d(sbox, &tmap, bar, org[0], org[1], org[2], 0);
+    mbar_arrive_expect_tx(bar, (uint32_t)(8 * bvol * 4));
+    tma_load_4d(sbox, &tmap, bar, 0, org[0], org[1], org[2]);
   }
   for (int i = tid; i <= g.V; i += kT) scs[i] = cstart[brick * g.V + i];
   if (DEP)
@@ -178,19 +209,42 @@ __global__ void __launch_bounds__(kT, 2)
 
   const float dtdx[3] = {dtdx0, dtdx1, dtdx2};
   const uint32_t p0 = scs[0], p1 = scs[g.V];
+  int cfirst = 0;  // first brick cell with particles at or after the super-chunk start
   for (uint32_t sb = p0; sb < p1; sb += kM) {
     const uint32_t se = p1 - sb < (uint32_t)kM ? p1 : sb + kM;
-    // ---- A: push, one thread per particle
-    for (uint32_t p = sb + tid; p < se; p += kT) {
-      const int i = (int)(p - sb);
-      int j[3];
-      cell_coords(g, cell[p], j);
-      float o[3], up[3];
+    // ---- A: push, one thread per particle; the next particle's state is
+    // loaded before the current one is computed
+    uint32_t p = sb + tid;
+    int32_t nc = 0;
+    float no[3] = {0.f, 0.f, 0.f}, nu[3] = {0.f, 0.f, 0.f}, nw = 1.0f;
+    if (p < se) {
+      nc = cells[p];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        o[a] = off[a * n + p];
-        up[a] = u[a * n + p];
+        no[a] = offs[a * n + p];
+        nu[a] = us[a * n + p];
       }
+      if (w) nw = w[p];
+    }
+    for (; p < se; p += kT) {
+      const int i = (int)(p - sb);
+      const int32_t ccur = nc;
+      float o[3] = {no[0], no[1], no[2]}, up[3] = {nu[0], nu[1], nu[2]};
+      const float wcur = nw;
+      if (p + kT < se) {
+        const uint32_t pn = p + kT;
+        nc = cells[pn];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          no[a] = offs[a * n + pn];
+          nu[a] = us[a * n + pn];
+        }
+        if (w) nw = w[pn];
+      }
+      if (w && wd != w) wd[p] = wcur;             // carry the read-only planes over
+      if (ids && idd != ids) idd[p] = ids[p];
+      int j[3];
+      cell_coords(g, ccur, j);
       int l[3];
       bool ok = true;
 #pragma unroll
@@ -206,12 +260,19 @@ __global__ void __launch_bounds__(kT, 2)
       float d0[3] = {0.0f, 0.0f, 0.0f};
       if (!ok) {
         atomicOr(status, ST_DOMAIN);
+        cell[p] = ccur;  // left as it was
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          off[a * n + p] = o[a];
+          u[a * n + p] = up[a];
+        }
       } else {
         float wx[3], wy[3], wz[3] = {0.0f, 1.0f, 0.0f};
         shape_weights<SHAPE>(o[0], wx);
         shape_weights<SHAPE>(o[1], wy);
         if (DIM == 3) shape_weights<SHAPE>(o[2], wz);
-        float f[6] = {0, 0, 0, 0, 0, 0};
+        float2 f2[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        const float4* sb4 = reinterpret_cast<const float4*>(sbox);
 #pragma unroll
         for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
           const int zz = DIM == 3 ? l[2] + kz : 0;
@@ -220,14 +281,11 @@ __global__ void __launch_bounds__(kT, 2)
             const float wzy = wz[kz] * wy[ky];
             const int row = (zz * g.box[1] + l[1] + ky) * g.box[0] + l[0];
 #pragma unroll
-            for (int kx = 0; kx < 3; ++kx) {
-              const float ww = wzy * wx[kx];
-              const float* sp = sbox + row + kx;
-#pragma unroll
-              for (int c = 0; c < 6; ++c) f[c] += ww * sp[c * bvol];
-            }
+            for (int kx = 0; kx < 3; ++kx)
+              acc_point(f2, wzy * wx[kx], sb4[2 * (row + kx)], sb4[2 * (row + kx) + 1]);
           }
         }
+        const float f[6] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y};
         float du[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) d0[a] = o[a];
@@ -245,7 +303,7 @@ __global__ void __launch_bounds__(kT, 2)
           u[a * n + p] = up[a];
         }
         if (DEP) {
-          const float wdt = (w ? w[p] : 1.0f) * inv_dt;
+          const float wdt = wcur * inv_dt;
 #pragma unroll
           for (int a = 0; a < 3; ++a) F[a] = du[a] * wdt;
         }
@@ -260,16 +318,20 @@ __global__ void __launch_bounds__(kT, 2)
     }
     if (!DEP) continue;
     __syncthreads();
-    // ---- B: one thread per source cell, then 27 ordered passes
+    // ---- B: one thread per source cell of this super-chunk, then 27 ordered
+    // passes
     const int hz = DIM == 3 ? 1 : 0;
-    for (int c0 = 0; c0 < g.V; c0 += kT) {
+    while (scs[cfirst + 1] <= sb) ++cfirst;
+    int clast = cfirst;
+    while (clast + 1 < g.V && scs[clast + 1] < se) ++clast;
+    for (int c0 = cfirst; c0 <= clast; c0 += kT) {
       const int ls = c0 + tid;
       float T[27][3];
 #pragma unroll
       for (int k = 0; k < 27; ++k) T[k][0] = T[k][1] = T[k][2] = 0.0f;
       bool any = false;
       int lx = 0, ly = 0, lz = 0;
-      if (ls < g.V) {
+      if (ls <= clast) {
         lx = ls % g.b[0];
         ly = (ls / g.b[0]) % g.b[1];
         lz = ls / (g.b[0] * g.b[1]);
@@ -340,7 +402,8 @@ __device__ __forceinline__ void advance_mixed(const float* __restrict__ fp, cons
     shape_weights<SHAPE>(o[0], wx);
     shape_weights<SHAPE>(o[1], wy);
     if (DIM == 3) shape_weights<SHAPE>(o[2], wz);
-    float f[6] = {0, 0, 0, 0, 0, 0};
+    float2 f2[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    const float4* fp4 = reinterpret_cast<const float4*>(fp);
 #pragma unroll
     for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
       const int zz = DIM == 3 ? j[2] + kz : 0;
@@ -349,13 +412,11 @@ __device__ __forceinline__ void advance_mixed(const float* __restrict__ fp, cons
         const float wzy = wz[kz] * wy[ky];
         const int64_t row = ((int64_t)zz * g.pn[1] + j[1] + ky) * g.pn[0] + j[0];
 #pragma unroll
-        for (int kx = 0; kx < 3; ++kx) {
-          const float ww = wzy * wx[kx];
-#pragma unroll
-          for (int cc = 0; cc < 6; ++cc) f[cc] += ww * __ldg(fp + cc * g.pplane + row + kx);
-        }
+        for (int kx = 0; kx < 3; ++kx)
+          acc_point(f2, wzy * wx[kx], __ldg(fp4 + 2 * (row + kx)), __ldg(fp4 + 2 * (row + kx) + 1));
       }
     }
+    float f[6] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y};
     float du[3];
     boris_f32(up, f, f + 3, h, hl, du);
     const float gi = rsqrtf(1.0f + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
@@ -474,9 +535,14 @@ cudaError_t brick_mixed(part_ctx* c, const MixedArgs& a) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L.total);
   if (e != cudaSuccess) return e;
+  const bool alt = c->pending;  // sorted state waits in the alternate buffers
   kern<<<(unsigned)c->geo.nbricks, kT, L.total, c->stream>>>(
-      c->tmap, c->geo, (int32_t*)c->x, (float*)c->off, (float*)c->u, (const float*)c->w, c->n,
-      c->cstart, c->dpart, a.h, a.hl, a.dtdx[0], a.dtdx[1], a.dtdx[2], a.inv_dt, c->status);
+      c->tmap, c->geo, (const int32_t*)(alt ? c->alt_x : c->x),
+      (const float*)(alt ? c->alt_off : c->off), (const float*)(alt ? c->alt_u : c->u),
+      (const float*)(c->w ? (alt ? c->alt_w : c->w) : nullptr),
+      c->id ? (alt ? c->alt_id : c->id) : nullptr, (int32_t*)c->x, (float*)c->off,
+      (float*)c->u, (float*)c->w, c->id, c->n, c->cstart, c->dpart, a.h, a.hl, a.dtdx[0],
+      a.dtdx[1], a.dtdx[2], a.inv_dt, c->status);
   c->launches++;
   return cudaGetLastError();
 }

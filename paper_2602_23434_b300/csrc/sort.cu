@@ -242,6 +242,32 @@ __global__ void k_cell_start(const uint32_t* __restrict__ sk, int64_t n, int64_t
   }
 }
 
+// One pass over the permutation: every bound plane of particle perm[i] is
+// copied to slot i of the alternate buffers.  NP double/float planes of the
+// position-like arrays are handled by the caller's choice of template.
+template <typename TX, int NX, typename TV>
+__global__ void k_gather_state(const TX* __restrict__ x, const float* __restrict__ off,
+                               const TV* __restrict__ u, const TV* __restrict__ w,
+                               const uint64_t* __restrict__ id, TX* __restrict__ ax,
+                               float* __restrict__ aoff, TV* __restrict__ au,
+                               TV* __restrict__ aw, uint64_t* __restrict__ aid,
+                               const uint32_t* __restrict__ perm, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t s = perm[i];
+    if (s >= (uint64_t)n) continue;  // never for a consistent permutation
+#pragma unroll
+    for (int a = 0; a < NX; ++a) ax[a * n + i] = x[a * n + s];
+    if (off)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) aoff[a * n + i] = off[a * n + s];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) au[a * n + i] = u[a * n + s];
+    if (w) aw[i] = w[s];
+    if (id) aid[i] = id[s];
+  }
+}
+
 int grid_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -296,6 +322,20 @@ cudaError_t launch_sort(part_ctx* c) {
     k_cell_start<<<grid_for(n + 1, 256), 256, 0, s>>>(sk, n, g.nkeys, c->cstart);
     c->launches++;
     // permute the bound arrays
+    if (c->mode == PART_BORIS && c->alt_x) {
+      if (c->prec == PART_FP64)
+        k_gather_state<double, 3, double><<<grid_for(n, 256), 256, 0, s>>>(
+            (const double*)c->x, nullptr, (const double*)c->u, (const double*)c->w, c->id,
+            (double*)c->alt_x, nullptr, (double*)c->alt_u, (double*)c->alt_w, c->alt_id, perm, n);
+      else
+        k_gather_state<int32_t, 1, float><<<grid_for(n, 256), 256, 0, s>>>(
+            (const int32_t*)c->x, (const float*)c->off, (const float*)c->u, (const float*)c->w,
+            c->id, (int32_t*)c->alt_x, (float*)c->alt_off, (float*)c->alt_u, (float*)c->alt_w,
+            c->alt_id, perm, n);
+      c->launches++;
+      c->pending = true;
+      return cudaGetLastError();
+    }
     if (c->mode == PART_BORIS && c->prec == PART_FP64) {
       for (int a = 0; a < 3; ++a) {
         if ((e = permute_plane<double>(c, (double*)c->x + a * n, perm))) return e;
@@ -324,4 +364,23 @@ cudaError_t launch_sort(part_ctx* c) {
     c->launches++;
   }
   return cudaGetLastError();
+}
+
+cudaError_t flush_pending(part_ctx* c) {
+  if (!c->pending) return cudaSuccess;
+  c->pending = false;
+  const int64_t n = c->n;
+  if (n == 0) return cudaSuccess;
+  const size_t e = c->prec == PART_FP64 ? 8 : 4;
+  const int nx = c->prec == PART_FP64 ? 3 : 1;
+  cudaError_t r = cudaMemcpyAsync(c->x, c->alt_x, e * nx * n, cudaMemcpyDeviceToDevice, c->stream);
+  if (r == cudaSuccess && c->off)
+    r = cudaMemcpyAsync(c->off, c->alt_off, 12 * n, cudaMemcpyDeviceToDevice, c->stream);
+  if (r == cudaSuccess)
+    r = cudaMemcpyAsync(c->u, c->alt_u, 3 * e * n, cudaMemcpyDeviceToDevice, c->stream);
+  if (r == cudaSuccess && c->w)
+    r = cudaMemcpyAsync(c->w, c->alt_w, e * n, cudaMemcpyDeviceToDevice, c->stream);
+  if (r == cudaSuccess && c->id)
+    r = cudaMemcpyAsync(c->id, c->alt_id, 8 * n, cudaMemcpyDeviceToDevice, c->stream);
+  return r;
 }

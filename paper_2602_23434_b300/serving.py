@@ -176,6 +176,7 @@ class Server:
             sp.bind(r.n, r.cell, off=r.off, u=r.u)
             sp.init_particles(r.seed, r.u_th)
             sp.sort()
+            sp.sync()                      # sorted state into the request's arrays
             self.used += need
             r.admitted = self.clock()
             if r.remaining == 0:

@@ -109,7 +109,7 @@ def test_mixed_step_and_deposit_vs_fp64(dim, n, ppc, shape):
     p.bind(N, cd, off=od, u=ud, w=wd)
     p.enable_deposit(True)
     p.sort()
-    torch.cuda.synchronize()
+    p.sync()
     c0, o0, u0, w0 = _host(cd), _host(od), _host(ud), _host(wd)
     p.gather_push(qm, dt, 1)
     out = torch.empty((3, f.shape[1]), dtype=torch.float64, device="cuda")

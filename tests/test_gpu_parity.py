@@ -106,7 +106,7 @@ def test_boris_push_and_deposit_fp64(dim, n, ppc, shape):
     p.bind(N, xd, u=ud, w=wd, ids=idd)
     p.enable_deposit(True)
     p.sort()
-    torch.cuda.synchronize()
+    p.sync()
     xs, us, ws = _host(xd), _host(ud), _host(wd)      # sorted input state
     p.gather_push(qm, dt, 1)
     out = torch.empty((3, og.n[0] * og.n[1] * og.n[2]), dtype=torch.float64, device="cuda")
@@ -246,6 +246,7 @@ def test_error_paths():
     # a particle moved out of its sorted cell -> PART_EDOMAIN, nothing faults
     p.bind(N, xd, u=ud)
     p.sort()
+    p.sync()                                         # sorted state in the bound arrays
     xd[0, 0] = xd[0, 0] + 0.3          # one cell away from its sorted cell
     p.gather_push(1.0, 0.01, 1)
     with pytest.raises(P.PartError) as e:
