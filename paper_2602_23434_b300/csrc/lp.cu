@@ -43,7 +43,8 @@ struct Stencil {
     if (DIM == 3) shape_weights<SHAPE>(d[2], wz);
     base = ((int64_t)j[2] * g.pn[1] + j[1]) * g.pn[0] + j[0];
   }
-  // sum over the stencil of components [c0, c0 + NC)
+  // sum over the stencil of components [c0, c0 + NC); the 27 weight products
+  // are formed once for all NC components
   template <int NC>
   __device__ __forceinline__ void gather(const double* __restrict__ fp, const Geo& g, int c0,
                                          double* out) const {
@@ -66,6 +67,30 @@ struct Stencil {
       }
     }
   }
+  // components {0,1,2} (v) and {4,5,6} (B) in one stencil pass
+  __device__ __forceinline__ void gather_vb(const double* __restrict__ fp, const Geo& g,
+                                            double* v, double* b) const {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = b[c] = 0.0;
+#pragma unroll
+    for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
+      const int zo = DIM == 3 ? kz : 0;
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky) {
+        const double wzy = wz[kz] * wy[ky];
+        const int64_t row = base + ((int64_t)zo * g.pn[1] + ky) * g.pn[0];
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+          const double ww = wzy * wx[kx];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            v[c] += ww * __ldg(fp + (int64_t)c * g.pplane + row + kx);
+            b[c] += ww * __ldg(fp + (int64_t)(4 + c) * g.pplane + row + kx);
+          }
+        }
+      }
+    }
+  }
 };
 
 template <int SHAPE, int DIM>
@@ -79,8 +104,7 @@ __global__ void __launch_bounds__(256)
     for (int a = 0; a < 3; ++a) x0[a] = xs[a] = x1[a] = x[a * n + p];
     double v1[3], b0[3], v2[3], v3[3], b1[3], r;
     Stencil<SHAPE, DIM> s0(g, x0);
-    s0.template gather<3>(fp, g, 0, v1);
-    s0.template gather<3>(fp, g, 4, b0);
+    s0.gather_vb(fp, g, v1, b0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) xs[a] = wrap_axis(x0[a] + dt * v1[a], g.xmin[a], g.xmax[a], g.L[a]);
     Stencil<SHAPE, DIM> ss(g, xs);
@@ -89,9 +113,17 @@ __global__ void __launch_bounds__(256)
     for (int a = 0; a < DIM; ++a)
       x1[a] = wrap_axis(x0[a] + dt * (0.5 * (v1[a] + v2[a])), g.xmin[a], g.xmax[a], g.L[a]);
     Stencil<SHAPE, DIM> s1(g, x1);
-    s1.template gather<1>(fp, g, 3, &r);
-    s1.template gather<3>(fp, g, 4, b1);
-    s1.template gather<3>(fp, g, 0, v3);
+    {
+      double o[7];  // v, rho, B at the new position in one stencil pass
+      s1.template gather<7>(fp, g, 0, o);
+      v3[0] = o[0];
+      v3[1] = o[1];
+      v3[2] = o[2];
+      r = o[3];
+      b1[0] = o[4];
+      b1[1] = o[5];
+      b1[2] = o[6];
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) x[a * n + p] = x1[a];
     const double bb0 = b0[0] * b0[0] + b0[1] * b0[1] + b0[2] * b0[2];
@@ -109,7 +141,8 @@ __global__ void __launch_bounds__(256)
 // Per LP: dtau = dt/gamma_g; ln A = ln(n_old/n_new)/3; c_r = c0 (|B|^2/2 +
 // u_rad); C = c_r dtau expm1(ln A)/ln A.  Per bin: s = A + C eps;
 // eps <- eps/s; chi <- chi s^2/A.  Bins are unrolled 8 at a time so that
-// eight independent row loads are in flight per thread.
+// eight independent row loads are in flight per thread, and the 8 divisions
+// share one (FP64 division is ~6x an FMA on this part).
 __global__ void __launch_bounds__(256)
     k_spec_update(double* __restrict__ chi, double* __restrict__ eng, double* __restrict__ n_old,
                   const double* __restrict__ samples, int64_t n, int nb, double dt, double c0,
@@ -128,17 +161,35 @@ __global__ void __launch_bounds__(256)
     double* cp = chi + p;
     int i = 0;
     for (; i + 8 <= nb; i += 8) {
-      double e[8], c[8];
+      double e[8], c[8], sv[8], pre[8], r[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         e[k] = ep[(int64_t)(i + k) * n];
         c[k] = cp[(int64_t)(i + k) * n];
       }
+      // 1/s for the 8 bins from one division (Montgomery's simultaneous
+      // inversion): prefix products, invert the last, unwind.
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const double s = A + C * e[k];
-        ep[(int64_t)(i + k) * n] = e[k] / s;
-        cp[(int64_t)(i + k) * n] = (c[k] * (s * s)) * invA;
+        sv[k] = A + C * e[k];
+        pre[k] = k == 0 ? sv[0] : pre[k - 1] * sv[k];
+      }
+      double inv = 1.0 / pre[7];
+      if (finite_bits(inv) && inv != 0.0) {
+#pragma unroll
+        for (int k = 7; k > 0; --k) {
+          r[k] = inv * pre[k - 1];
+          inv = inv * sv[k];
+        }
+        r[0] = inv;
+      } else {  // products left the double range: divide bin by bin
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = 1.0 / sv[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        ep[(int64_t)(i + k) * n] = e[k] * r[k];
+        cp[(int64_t)(i + k) * n] = (c[k] * (sv[k] * sv[k])) * invA;
       }
     }
     for (; i < nb; ++i) {
