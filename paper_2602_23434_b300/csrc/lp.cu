@@ -27,12 +27,11 @@ struct Stencil {
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       double s = __dmul_rn(__dsub_rn(xp[a], g.xmin[a]), g.inv_dx[a]);
-      if (!isfinite(s)) {
+      if (!finite_bits(s)) {
         finite = false;
         s = 0.0;
       }
-      double f = floor(s);
-      j[a] = f >= (double)g.n[a] ? g.n[a] - 1 : (f < 0.0 ? 0 : (int)f);
+      j[a] = floor_clamp_bits(s, g.n[a] - 1);
       d[a] = __dsub_rn(__dsub_rn(s, (double)j[a]), 0.5);
     }
     shape_weights<SHAPE>(d[0], wx);

@@ -162,6 +162,21 @@ __device__ __forceinline__ bool finite_bits(double v) {
   return ((unsigned)__double2hiint(v) & 0x7ff00000u) != 0x7ff00000u;
 }
 
+// min(floor(s), hi) for s >= 0, and 0 for s < 0, from the bits of s on the
+// integer pipe (exactly the value floor() gives; floor and compares would be
+// FP64-pipe instructions).  s >= 2^31, +Inf and NaN give hi: callers test
+// finiteness separately.
+__device__ __forceinline__ int floor_clamp_bits(double s, int hi) {
+  const long long b = __double_as_longlong(s);
+  if (b < 0) return 0;                            // negative, or -0.0
+  const int e = (int)(b >> 52) - 1023;            // unbiased exponent
+  if (e < 0) return 0;                            // 0 <= s < 1
+  if (e >= 31) return hi;
+  const long long m = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+  const int j = (int)(m >> (52 - e));
+  return j > hi ? hi : j;
+}
+
 // ---------------------------------------------------------------- shape weights
 // Three-point weights at offsets k = -1, 0, +1 from the particle's cell for
 // offset d = (s - j) - 1/2 in [-1/2, 1/2].  TSC: quadratic B-spline; CIC: hat

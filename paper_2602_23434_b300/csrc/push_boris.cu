@@ -155,8 +155,7 @@ __global__ void __launch_bounds__(kT, 1)
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         double s = __dmul_rn(__dsub_rn(xp[a], g.xmin[a]), g.inv_dx[a]);
-        double f = floor(s);
-        int j = f >= (double)g.n[a] ? g.n[a] - 1 : (f < 0.0 ? 0 : (int)f);
+        int j = floor_clamp_bits(s, g.n[a] - 1);
         d[a] = __dsub_rn(__dsub_rn(s, (double)j), 0.5);
         l[a] = j - org[a];
         ok = ok && l[a] >= 0 && l[a] < g.b[a] && finite_bits(s);
@@ -313,12 +312,11 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         double s = __dmul_rn(__dsub_rn(xp[a], g.xmin[a]), g.inv_dx[a]);
-        if (!isfinite(s)) {
+        if (!finite_bits(s)) {
           bad = true;
           s = 0.0;
         }
-        double f = floor(s);
-        j[a] = f >= (double)g.n[a] ? g.n[a] - 1 : (f < 0.0 ? 0 : (int)f);
+        j[a] = floor_clamp_bits(s, g.n[a] - 1);
         d[a] = __dsub_rn(__dsub_rn(s, (double)j[a]), 0.5);
       }
       double wx[3], wy[3], wz[3] = {0.0, 1.0, 0.0};

@@ -21,14 +21,11 @@ __device__ __forceinline__ uint32_t brick_key(const Geo& g, int jx, int jy, int 
 
 __device__ __forceinline__ int cell_of(const Geo& g, int a, double xa, int* status) {
   double s = __dmul_rn(__dsub_rn(xa, g.xmin[a]), g.inv_dx[a]);
-  if (!isfinite(s)) {
+  if (!finite_bits(s)) {
     atomicOr(status, ST_NONFINITE);
     return 0;
   }
-  double f = floor(s);
-  if (f >= (double)g.n[a]) return g.n[a] - 1;
-  if (f < 0.0) return 0;
-  return (int)f;
+  return floor_clamp_bits(s, g.n[a] - 1);
 }
 
 __global__ void k_keys_f64(const double* __restrict__ x, int64_t n, Geo g,
