@@ -48,6 +48,13 @@ FLOP_PER_PSTEP_BORIS_DEP = 12 + 24 + 360 + 58 + 17 + 178
 # Algorithmic HBM bytes of one particle step: state x,u read+write 96, w read 8,
 # field stencil 6*8 B per cell / 8 particles per cell = 6, deposit 3*8 / 8 = 3.
 BYTES_PER_PSTEP_BORIS_DEP = 96 + 8 + 6 + 3
+# DRAM bytes (read + write) per particle of one launch of the FP64 brick kernel,
+# from the ncu capture in profiles/ncu_boris_brick_fp64_64cube.md (64^3 case,
+# 252.7 MB for 2,097,152 particles), scaled to a launch by the particle count.
+TRAFFIC_PER_PARTICLE_BRICK_F64 = 252.713728e6 / 2097152
+# Same for the mixed brick kernel, profiles/ncu_boris_brick_mixed_128cube.md
+# (128^3 case, 1206.8 MB for 16,777,216 particles).
+TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1206.793984e6 / 16777216
 # LP step: x r/w 48, chi+eng r/w 4096 (128 bins), n_old r/w 16, samples w+r 48,
 # fields: 7 comps * 8 B per cell / 2 LPs per cell, 3 gathers at ~one cell = 84
 BYTES_PER_LPSTEP = 48 + 4096 + 16 + 48 + 84
@@ -278,7 +285,8 @@ def run_mixed(torch, P, n, ppc, K, W, seed):
            "ms_per_step": total / K, "push_kernel_ms": km,
            "roofline_push": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                              "frac": gbs / hbm, "peak_kind": kind,
-                             "bytes_per_particle_step": BYTES_PER_PSTEP_MIXED_DEP},
+                             "bytes_per_particle_step": BYTES_PER_PSTEP_MIXED_DEP,
+                             "traffic": TRAFFIC_PER_PARTICLE_BRICK_MIXED * wl.N},
            "gpu_launches_per_step": (wl.part.launches() - l0) // (K + W)}
     del wl
     torch.cuda.empty_cache()
@@ -595,7 +603,10 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "kernel": "k_boris_brick_f64 (TSC, 3D, deposit)",
                      "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_NOMINAL_TFLOPS, "traffic": None,
+                     "frac": achieved_tf / FP64_NOMINAL_TFLOPS,
+                     "traffic": TRAFFIC_PER_PARTICLE_BRICK_F64 * wl.N,
+                     "traffic_unit": "bytes per launch (ncu dram read+write, scaled by "
+                                     "particles from the 64^3 capture)",
                      "flop_per_particle_step": FLOP_PER_PSTEP_BORIS_DEP,
                      "kernel_ms": kmean,
                      "peak_note": "FP64 non-tensor nominal (recipe); FP64 is 1/64 of FP32 on "
