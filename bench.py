@@ -136,11 +136,12 @@ def dt_turbulent(f6, n: int, qm: float = 1.0):
 class BorisWorkload:
     """Headline FP64 workload: 128^3 turbulent, 8 ppc, Boris + TSC + deposit."""
 
-    def __init__(self, torch, P, n=128, ppc=8, seed=1236):
+    def __init__(self, torch, P, n=128, ppc=8, seed=1236, pseed=None):
         self.torch, self.P = torch, P
         self.n = n
         self.N = n ** 3 * ppc
         self.seed = seed
+        pseed = seed if pseed is None else pseed   # particle draws (per replica)
         f = synth.em_fields(3, n, seed)
         self.dt = dt_turbulent(f, n)
         self.qm = 1.0
@@ -154,7 +155,7 @@ class BorisWorkload:
         self.ids = torch.empty(self.N, dtype=torch.int64, device=dev)
         self.out = torch.empty((3, n ** 3), dtype=torch.float64, device=dev)
         self.part.bind(self.N, self.x, u=self.u, w=self.w, ids=self.ids)
-        self.part.init_particles(seed, 0.1)
+        self.part.init_particles(pseed, 0.1)
         self.part.enable_deposit(True)
         self.part.sync()
 
@@ -548,9 +549,8 @@ def main():
     from paper_2602_23434_b300 import _lib as P
     from paper_2602_23434_b300.build import build
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2602_23434_b300 import replicas as R
+    rank, world, local = R.env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -561,7 +561,7 @@ def main():
     if dist:
         dist.barrier()
 
-    wl = BorisWorkload(torch, P, n=args.grid)
+    wl = BorisWorkload(torch, P, n=args.grid, seed=1236, pseed=R.rank_seed(1236, rank))
     stream = wl.part.stream
     l0 = wl.part.launches()
     # warm-up
@@ -578,11 +578,8 @@ def main():
     launches = wl.part.launches() - l1
     clocks = clk.stop()
     wl.part.sync()
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = wl.N * args.steps * world / (total_ms / 1e3)
+    total_ms = R.max_over_ranks(total_ms, dist, device="cuda")
+    value = R.job_rate(wl.N, args.steps, world, total_ms / 1e3)
     kmean = float(np.mean(kern_ms))
     hbm, hbm_kind = peaks()
     achieved_tf = FLOP_PER_PSTEP_BORIS_DEP * wl.N / (kmean / 1e3) / 1e12
