@@ -95,6 +95,8 @@ def lib():
             "or_philox4x32_10": (None, [_U32, _U32, _U32]),
             "or_init_particles": (None, [G, C.c_int64, C.c_uint64, C.c_double, _D, _D, _D,
                                          _U64]),
+            "or_compact_map": (C.c_int64, [C.c_int64, C.POINTER(C.c_uint8),
+                                           C.POINTER(C.c_int64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -254,3 +256,12 @@ def init_particles(g: Grid, n: int, seed: int, u_th: float):
     lib().or_init_particles(C.byref(g), n, seed, u_th, _d(x), _d(u), _d(w),
                             ids.ctypes.data_as(_U64))
     return x, u, w, ids
+
+
+def compact_map(deleted):
+    """Sec. 3.2 compaction: (n_keep, src) with src[j] the old index in slot j."""
+    d = np.ascontiguousarray(deleted, dtype=np.uint8)
+    src = np.zeros(max(d.shape[0], 1), dtype=np.int64)
+    nk = lib().or_compact_map(d.shape[0], d.ctypes.data_as(C.POINTER(C.c_uint8)),
+                              src.ctypes.data_as(C.POINTER(C.c_int64)))
+    return int(nk), src[:nk]

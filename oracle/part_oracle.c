@@ -352,3 +352,34 @@ void or_init_particles(const or_grid* g, int64_t n, uint64_t seed, double u_th,
     if (id) id[p] = (uint64_t)p;
   }
 }
+
+/* Compaction after deletions, following the five steps of Sec. 3.2:
+ *  1. flag and count the N_del particles to delete (holes);
+ *  2. save the hole indices, in increasing order;
+ *  3. if there are holes, collect the fillers: particles stored at an index
+ *     at or beyond N_p - N_del that are not deleted, in increasing order;
+ *  4. copy the k-th filler into the k-th hole below N_p - N_del;
+ *  5. shrink to N_p - N_del.
+ * The result is given as the source index of every kept slot.               */
+int64_t or_compact_map(int64_t n, const uint8_t* del, int64_t* src) {
+  int64_t ndel = 0;
+  for (int64_t i = 0; i < n; ++i) ndel += del[i] ? 1 : 0;              /* step 1 */
+  const int64_t nkeep = n - ndel;
+  int64_t* holes = (int64_t*)malloc(sizeof(int64_t) * (ndel > 0 ? ndel : 1));
+  int64_t nh = 0;
+  for (int64_t i = 0; i < n; ++i)                                       /* step 2 */
+    if (del[i]) holes[nh++] = i;
+  for (int64_t j = 0; j < nkeep; ++j) src[j] = j;
+  if (ndel > 0) {
+    int64_t k = 0;
+    for (int64_t i = nkeep; i < n; ++i) {                               /* step 3 */
+      if (del[i]) continue;
+      /* step 4: the k-th filler goes to the k-th hole (all holes that lie
+       * below nkeep come first in the sorted hole list) */
+      src[holes[k]] = i;
+      ++k;
+    }
+  }
+  free(holes);
+  return nkeep;                                                         /* step 5 */
+}

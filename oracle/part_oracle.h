@@ -82,4 +82,8 @@ void or_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
 /* particle initialisation from Philox draws: uniform x, Maxwellian u */
 void or_init_particles(const or_grid* g, int64_t n, uint64_t seed, double u_th,
                        double* x, double* u, double* w, uint64_t* id);
+/* Hole/filler compaction of Sec. 3.2 (the paper's five steps): given the
+ * deletion flags of n particles, returns n_keep and src[j] (j < n_keep) = the
+ * old index of the particle that ends up in slot j.                        */
+int64_t or_compact_map(int64_t n, const uint8_t* del, int64_t* src);
 #endif

@@ -477,3 +477,30 @@ def test_init_particles_statistics():
     assert np.array_equal(x2, x[:, :1000]) and np.array_equal(u2, u[:, :1000])
     x3, _, _, _ = O.init_particles(g, 1000, 1236, 0.1)
     assert not np.array_equal(x3, x2)
+
+
+# --------------------------------------------------------------- compaction (Sec. 3.2)
+def test_compaction_invariants():
+    """Sec. 3.2: after compaction the kept slots hold exactly the particles not
+    deleted; a particle below N_p - N_del that survives never moves; only as
+    many particles move as there are holes below N_p - N_del; the movers come
+    from the tail and fill the holes in index order."""
+    rng = np.random.default_rng(12)
+    cases = [np.zeros(0, bool), np.zeros(7, bool), np.ones(7, bool)]
+    for n, frac in ((1, 0.5), (33, 0.1), (1000, 0.5), (5000, 0.9), (4097, 0.01)):
+        cases.append(rng.random(n) < frac)
+    tail = np.zeros(100, bool)
+    tail[90:] = True
+    head = np.zeros(100, bool)
+    head[:10] = True
+    cases += [tail, head]
+    for d in cases:
+        n = d.shape[0]
+        nk, src = O.compact_map(d)
+        assert nk == n - d.sum()
+        assert sorted(src.tolist()) == sorted(np.flatnonzero(~d).tolist())
+        moved = [j for j in range(nk) if src[j] != j]
+        holes = [j for j in range(nk) if d[j]]
+        assert moved == holes                                   # exactly the holes move
+        assert all(src[j] >= nk for j in moved)                 # fillers from the tail
+        assert [src[j] for j in moved] == sorted(src[j] for j in moved)
