@@ -230,6 +230,56 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238):
             "c0": c0, "dt": dt, "gpu_launches_per_step": launches}
 
 
+def run_compact(torch, P, n=128, ppc=8, fracs=(0.01, 0.1), K=10, seed=1240):
+    """Sec. 3.2 hole/filler compaction of the headline FP64 state (x, u, w, id:
+    64 B per particle) with a random fraction of the particles flagged.  Each
+    timed call starts from the same restored state (the restore is untimed).
+    Algorithmic bytes: the mask (1 B per particle), each filler's record read
+    and written (2 x 64 B), and the rows after the first of x and u moved to
+    the new row stride (2 x 4 x 8 B per survivor)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    N = n ** 3 * ppc
+    p = P.Part(P.make_grid(3, n), P.FP64, P.TSC, P.BORIS, capacity=N)
+    x = torch.empty((3, N), dtype=torch.float64, device=dev)
+    u, w = torch.empty_like(x), torch.empty(N, dtype=torch.float64, device=dev)
+    ids = torch.empty(N, dtype=torch.int64, device=dev)
+    p.bind(N, x, u=u, w=w, ids=ids)
+    p.init_particles(seed, 0.1)
+    p.sync()
+    keep = [t.clone() for t in (x, u, w, ids)]
+    hbm, hbm_kind = peaks()
+    out = {"workload": f"{N} FP64 particles (128^3 x 8), x, u, w, id; random deletion",
+           "unit": "GB/s", "peak": hbm, "peak_kind": hbm_kind, "cases": []}
+    rng = np.random.default_rng(seed)
+    for frac in fracs:
+        d = rng.random(N) < frac
+        nk = int(N - d.sum())
+        nfill = int(d[:nk].sum())
+        dmask = torch.as_tensor(d.astype(np.uint8)).to(dev)
+        ms = []
+        for k in range(K + 3):
+            for t, s0 in zip((x, u, w, ids), keep):
+                t.copy_(s0)
+            p.bind(N, x, u=u, w=w, ids=ids)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(p.stream)
+            got = p.compact(dmask)
+            e1.record(p.stream)
+            torch.cuda.synchronize()
+            assert got == nk
+            if k >= 3:
+                ms.append(e0.elapsed_time(e1))
+        t = float(np.median(ms))
+        alg = N + 2 * 64 * nfill + 2 * 4 * 8 * nk
+        out["cases"].append({"deleted_frac": frac, "n_new": nk, "fillers": nfill, "ms": t,
+                             "particles_per_s": N / (t / 1e3),
+                             "algorithmic_bytes": alg, "achieved_GBps": alg / (t / 1e3) / 1e9,
+                             "frac": alg / (t / 1e3) / 1e9 / hbm})
+    del keep, x, u, w, ids
+    return out
+
+
 # Mixed form: per particle-step, state read 32 B (cell 4, offsets 12, u 12,
 # w 4) + written 28 B, f32 field stencil 24 B per cell / 8 ppc = 3, deposit
 # partials 3 x 8 B per cell / 8 ppc = 3.
@@ -512,6 +562,8 @@ def only(args):
     build()
     if args.only == "mixed":
         res = run_mixed(torch, P, args.grid, 8, args.steps, args.warmup, 1237)
+    elif args.only == "compact":
+        res = run_compact(torch, P, n=args.grid, K=max(3, args.steps))
     elif args.only == "lp":
         res = run_lp(torch, P, args.steps, args.warmup, n=args.grid,
                      nlp=max(1 << 16, 2 * args.grid ** 3))
@@ -534,7 +586,7 @@ def main():
     ap.add_argument("--grid", type=int, default=128,
                     help="cells per axis of the headline workload (128 = the stated one; "
                          "smaller only for profiling captures)")
-    ap.add_argument("--only", choices=["mixed", "lp", "serving"], default=None,
+    ap.add_argument("--only", choices=["mixed", "lp", "serving", "compact"], default=None,
                     help="run one secondary workload alone at --grid cells per axis and print "
                          "its result (for profiling captures); no headline line")
     args = ap.parse_args()
@@ -635,6 +687,10 @@ def main():
             line["mixed_error_vs_fp64"] = mixed_error_vs_fp64(torch, P)
         except Exception as e:
             line["mixed"] = {"error": repr(e)}
+        try:
+            line["compact"] = run_compact(torch, P)
+        except Exception as e:
+            line["compact"] = {"error": repr(e)}
         try:
             line["serving"] = run_serving(torch, requests=args.serve_requests)
         except Exception as e:

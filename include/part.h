@@ -128,6 +128,16 @@ part_status part_bind_particles(part_ctx* ctx, int64_t n, void* x_or_cell, void*
  * call the bound arrays must be neither read nor written by the caller.    */
 part_status part_sort(part_ctx* ctx);
 
+/* Remove the particles flagged in deleted (device uint8[n], nonzero = delete)
+ * by the hole/filler compaction of Sec. 3.2 ("Ensure coalesced access to
+ * memory"): the k-th deleted slot below n_new = n - N_del receives the k-th
+ * surviving particle stored at or beyond n_new (both in index order), then the
+ * set shrinks to n_new.  Every bound array is updated and re-laid out with row
+ * stride n_new (component a of particle p at a*n_new + p); the context's n
+ * becomes n_new.  Synchronises the stream once to read N_del.  Invalidates
+ * the sort.                                                                 */
+part_status part_compact(part_ctx* ctx, const uint8_t* deleted, int64_t* n_new);
+
 /* Device pointer to cell_start[nkeys + 1] (valid after part_sort): the
  * particles of key k are [cell_start[k], cell_start[k+1]).                */
 part_status part_cell_start(part_ctx* ctx, const uint32_t** cell_start, int64_t* nkeys);

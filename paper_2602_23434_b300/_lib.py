@@ -88,6 +88,7 @@ def lib():
         "part_bind_particles": (st, [P, C.c_int64, P, P, P, P, P, P, P, P]),
         "part_sort": (st, [P]),
         "part_cell_start": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
+        "part_compact": (st, [P, P, C.POINTER(C.c_int64)]),
         "part_enable_deposit": (st, [P, C.c_int]),
         "part_gather_push": (st, [P, C.c_double, C.c_double, C.c_int]),
         "part_deposit": (st, [P, P]),
@@ -198,6 +199,13 @@ class Part:
         off = p.value - self.ws.data_ptr()
         raw = self.ws[off: off + 4 * (nk.value + 1)]
         return raw.view(self.torch.int32).to(self.torch.int64) & 0xFFFFFFFF
+
+    def compact(self, deleted) -> int:
+        """Sec. 3.2 compaction by a device uint8 mask; returns the new count (the
+        bound arrays now have row stride n_new)."""
+        nn = C.c_int64()
+        self._check(self.L.part_compact(self.ctx, _ptr(deleted), C.byref(nn)))
+        return nn.value
 
     def enable_deposit(self, on=True):
         self._check(self.L.part_enable_deposit(self.ctx, 1 if on else 0))

@@ -110,7 +110,7 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   const int64_t hlen = ntiles * kRadix;
   const int64_t nblk = (hlen + kScanBlock - 1) / kScanBlock;
   L.fpad = take((size_t)fcomp_of(prec, mode) * g.pplane * esize_of(prec));
-  L.keys0 = take((size_t)c1 * 4);
+  L.keys0 = take((size_t)(c1 + 1) * 4);  // +1: compaction scans n + 1 flags
   L.keys1 = take((size_t)c1 * 4);
   L.vals0 = take((size_t)c1 * 4);
   L.vals1 = take((size_t)c1 * 4);
@@ -347,6 +347,23 @@ part_status part_sort(part_ctx* c) {
   if (e == cudaSuccess) e = launch_sort(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_sort");
   c->sorted = true;
+  return PART_OK;
+}
+
+part_status part_compact(part_ctx* c, const uint8_t* deleted, int64_t* n_new) {
+  if (check_ctx(c)) return PART_EINVAL;
+  if (!c->bound) return fail(c, PART_EINVAL, "no particles bound");
+  if (!n_new) return fail(c, PART_EINVAL, "n_new is NULL");
+  if (c->n > 0 && !deleted) return fail(c, PART_EINVAL, "deleted mask is NULL");
+  cudaError_t e = flush_pending(c);
+  int64_t nn = c->n;
+  if (e == cudaSuccess) e = launch_compact(c, deleted, &nn);
+  if (e != cudaSuccess) return cuda_fail(c, e, "part_compact");
+  c->n = nn;
+  *n_new = nn;
+  c->sorted = false;
+  c->deposit_ready = false;
+  c->samples_ready = false;
   return PART_OK;
 }
 

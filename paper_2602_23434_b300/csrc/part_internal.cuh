@@ -207,6 +207,7 @@ void make_geo(const part_grid* gr, int esize, Geo* g);
 cudaError_t launch_pad_fields(part_ctx* c, const void* src);
 cudaError_t launch_sort(part_ctx* c);
 cudaError_t flush_pending(part_ctx* c);  // copy pending sorted state to the bound arrays
+cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew);
 cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps);
 cudaError_t launch_boris_mixed(part_ctx* c, double qm, double dt, int nsteps);
 cudaError_t launch_serve_kernel(int shape, int dim, const ServeHeader* hdr,

@@ -8,6 +8,7 @@
 // permute: every bound array is gathered through the permutation into the
 //         scratch buffer and copied back (in-place semantics for the caller).
 // cell_start: cs[k] = first sorted particle with key >= k, k in [0, nkeys].
+#include <algorithm>
 #include "part_internal.cuh"
 
 namespace {
@@ -265,6 +266,38 @@ __global__ void k_gather_state(const TX* __restrict__ x, const float* __restrict
   }
 }
 
+// ---- compaction (Sec. 3.2): D = exclusive scan of the deletion flags over
+// n + 1 entries (D[n] = N_del); the k-th hole below n_keep = n - N_del takes
+// the k-th surviving particle at or beyond n_keep.
+__global__ void k_del_flags(const uint8_t* __restrict__ del, int64_t n, uint32_t* __restrict__ f) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    f[i] = (i < n && del[i]) ? 1u : 0u;
+}
+
+__global__ void k_hole_pos(const uint8_t* __restrict__ del, const uint32_t* __restrict__ D,
+                           int64_t n, uint32_t* __restrict__ hole_pos) {
+  const int64_t nkeep = n - (int64_t)D[n];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nkeep;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (del[i]) hole_pos[D[i]] = (uint32_t)i;
+}
+
+// Move one plane of element type T (row stride n): filler i -> its hole.
+template <typename T>
+__global__ void k_fill_holes(T* __restrict__ a, const uint8_t* __restrict__ del,
+                             const uint32_t* __restrict__ D,
+                             const uint32_t* __restrict__ hole_pos, int64_t n) {
+  const int64_t nkeep = n - (int64_t)D[n];
+  const int64_t base = (int64_t)D[nkeep];
+  for (int64_t i = nkeep + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (del[i]) continue;
+    const int64_t k = (i - nkeep) - ((int64_t)D[i] - base);  // filler rank
+    a[hole_pos[k]] = a[i];
+  }
+}
+
 int grid_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -380,4 +413,82 @@ cudaError_t flush_pending(part_ctx* c) {
   if (r == cudaSuccess && c->id)
     r = cudaMemcpyAsync(c->id, c->alt_id, 8 * n, cudaMemcpyDeviceToDevice, c->stream);
   return r;
+}
+
+namespace {
+
+template <typename T>
+cudaError_t fill_rows(part_ctx* c, T* base, int rows, const uint8_t* del, int64_t n,
+                      int64_t nnew, int gb) {
+  for (int r = 0; r < rows; ++r) {
+    k_fill_holes<T><<<gb, 256, 0, c->stream>>>(base + (int64_t)r * n, del, c->keys[0],
+                                               c->keys[1], n);
+    c->launches++;
+  }
+  // Rows r >= 1 move from stride n to stride nnew: row r shifts down by
+  // S = r (n - nnew) elements.  Copied in stream-ordered chunks of S, no chunk
+  // overlaps its own source, and each chunk overwrites only source already
+  // copied; when that would take many chunks, through the scratch row.
+  for (int r = 1; r < rows && nnew < n; ++r) {
+    T* src = base + (int64_t)r * n;
+    T* dst = base + (int64_t)r * nnew;
+    const int64_t S = (int64_t)r * (n - nnew);
+    cudaError_t e = cudaSuccess;
+    if ((nnew + S - 1) / S <= 16) {
+      for (int64_t o = 0; o < nnew && e == cudaSuccess; o += S)
+        e = cudaMemcpyAsync(dst + o, src + o, sizeof(T) * std::min(S, nnew - o),
+                            cudaMemcpyDeviceToDevice, c->stream);
+    } else {
+      e = cudaMemcpyAsync(c->tmp, src, sizeof(T) * nnew, cudaMemcpyDeviceToDevice, c->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dst, c->tmp, sizeof(T) * nnew, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew_out) {
+  const int64_t n = c->n;
+  cudaStream_t s = c->stream;
+  if (n == 0) {
+    *nnew_out = 0;
+    return cudaSuccess;
+  }
+  const int gb = grid_for(n + 1, 256);
+  const int64_t m = n + 1;
+  const int64_t nblk = (m + kScanBlock - 1) / kScanBlock;
+  uint32_t* D = c->keys[0];
+  uint32_t* sums = c->vals[1];
+  k_del_flags<<<gb, 256, 0, s>>>(del, n, D);
+  k_scan_reduce<<<(unsigned)nblk, 256, 0, s>>>(D, m, sums);
+  k_scan_top<<<1, 256, 0, s>>>(sums, nblk);
+  k_scan_down<<<(unsigned)nblk, 256, 0, s>>>(D, m, sums);
+  k_hole_pos<<<gb, 256, 0, s>>>(del, D, n, c->keys[1]);
+  c->launches += 5;
+  uint32_t ndel = 0;
+  cudaError_t e = cudaMemcpyAsync(&ndel, D + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  const int64_t nnew = n - (int64_t)ndel;
+  if (c->mode == PART_BORIS && c->prec == PART_FP64) {
+    if ((e = fill_rows<double>(c, (double*)c->x, 3, del, n, nnew, gb))) return e;
+    if ((e = fill_rows<double>(c, (double*)c->u, 3, del, n, nnew, gb))) return e;
+    if (c->w && (e = fill_rows<double>(c, (double*)c->w, 1, del, n, nnew, gb))) return e;
+  } else if (c->mode == PART_BORIS) {
+    if ((e = fill_rows<int32_t>(c, (int32_t*)c->x, 1, del, n, nnew, gb))) return e;
+    if ((e = fill_rows<float>(c, (float*)c->off, 3, del, n, nnew, gb))) return e;
+    if ((e = fill_rows<float>(c, (float*)c->u, 3, del, n, nnew, gb))) return e;
+    if (c->w && (e = fill_rows<float>(c, (float*)c->w, 1, del, n, nnew, gb))) return e;
+  } else {
+    if ((e = fill_rows<double>(c, (double*)c->x, 3, del, n, nnew, gb))) return e;
+    if ((e = fill_rows<double>(c, c->chi, c->nbins, del, n, nnew, gb))) return e;
+    if ((e = fill_rows<double>(c, c->eng, c->nbins, del, n, nnew, gb))) return e;
+    if (c->n_old && (e = fill_rows<double>(c, c->n_old, 1, del, n, nnew, gb))) return e;
+  }
+  if (c->id && (e = fill_rows<uint64_t>(c, c->id, 1, del, n, nnew, gb))) return e;
+  *nnew_out = nnew;
+  return cudaGetLastError();
 }
