@@ -97,6 +97,12 @@ def lib():
                                          _U64]),
             "or_compact_map": (C.c_int64, [C.c_int64, C.POINTER(C.c_uint8),
                                            C.POINTER(C.c_int64)]),
+            "or_rh_compression": (C.c_double, [C.c_double, C.c_double]),
+            "or_dsa_index": (C.c_double, [C.c_double]),
+            "or_shock_cells": (None, [G, _D, _D, C.c_double, _D]),
+            "or_shock_convolve": (None, [C.c_int, _D, _D, C.c_double, C.c_double, _D]),
+            "or_lp_shock": (None, [G, _D, C.c_int, C.c_int64, _D, _D, _D,
+                                   C.POINTER(C.c_uint8)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -265,3 +271,37 @@ def compact_map(deleted):
     nk = lib().or_compact_map(d.shape[0], d.ctypes.data_as(C.POINTER(C.c_uint8)),
                               src.ctypes.data_as(C.POINTER(C.c_int64)))
     return int(nk), src[:nk]
+
+
+def rh_compression(gamma: float, mach: float) -> float:
+    return lib().or_rh_compression(gamma, mach)
+
+
+def dsa_index(r: float) -> float:
+    return lib().or_dsa_index(r)
+
+
+def shock_cells(g: Grid, vel, rho, r_min: float):
+    """Per-cell compression ratio of detected shocks (0 = none), shape [G]."""
+    rho = _f64(rho).reshape(-1)
+    out = np.zeros(rho.shape[0])
+    lib().or_shock_cells(C.byref(g), _d(_f64(vel).reshape(3, -1)), _d(rho), r_min, _d(out))
+    return out
+
+
+def shock_convolve(eng, chi, q: float, cn: float):
+    """Eq. convolution_spectra on one spectrum; returns chi_out."""
+    eng, chi = _f64(eng), _f64(chi)
+    out = np.zeros(chi.shape[0])
+    lib().or_shock_convolve(chi.shape[0], _d(eng), _d(chi), q, cn, _d(out))
+    return out
+
+
+def lp_shock(g: Grid, r_cell, x, chi, eng, state):
+    """Shock update on copies; returns (chi, state)."""
+    chi = _f64(chi).copy()
+    st = np.ascontiguousarray(state, dtype=np.uint8).copy()
+    nb, n = chi.shape
+    lib().or_lp_shock(C.byref(g), _d(_f64(r_cell)), nb, n, _d(_f64(x)), _d(chi),
+                      _d(_f64(eng)), st.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return chi, st

@@ -383,3 +383,114 @@ int64_t or_compact_map(int64_t n, const uint8_t* del, int64_t* src) {
   free(holes);
   return nkeep;                                                         /* step 5 */
 }
+
+/* ---- diffusive shock acceleration (Sec. 2, Eqs. convolution_spectra, slope)
+ *
+ * Compression ratio of a hydrodynamic shock from the Rankine-Hugoniot jump
+ * conditions (Sec. 4.1.2): r = (gamma+1) M^2 / (2 + (gamma-1) M^2).        */
+double or_rh_compression(double gamma, double mach) {
+  double m2 = mach * mach;
+  return (gamma + 1.0) * m2 / (2.0 + (gamma - 1.0) * m2);
+}
+
+/* Power-law index of the accelerated spectrum, Eq. slope, non-relativistic
+ * shock (the relativistic correction q_R is zero): q = 3r/(r-1).            */
+double or_dsa_index(double r) { return 3.0 * r / (r - 1.0); }
+
+/* Shock cells.  The paper leaves the detection criterion to the fluid code;
+ * this oracle uses: cell c is a shock cell if, along some axis a < dim, the
+ * flow converges across c (v_a(c + e_a) - v_a(c - e_a) < 0) and the density
+ * ratio of those two neighbours, max/min, is at least r_min.  Its
+ * compression ratio is the largest such ratio over the axes; 0 elsewhere.
+ * Periodic neighbours; vel [3][G], rho [G] cell-centred.                    */
+void or_shock_cells(const or_grid* g, const double* vel, const double* rho, double r_min,
+                    double* r_cell) {
+  int64_t G = (int64_t)g->n[0] * g->n[1] * g->n[2];
+  for (int jz = 0; jz < g->n[2]; ++jz)
+    for (int jy = 0; jy < g->n[1]; ++jy)
+      for (int jx = 0; jx < g->n[0]; ++jx) {
+        int j[3] = {jx, jy, jz};
+        double best = 0.0;
+        for (int a = 0; a < g->dim; ++a) {
+          int jp[3] = {jx, jy, jz}, jm[3] = {jx, jy, jz};
+          jp[a] = pmod(j[a] + 1, g->n[a]);
+          jm[a] = pmod(j[a] - 1, g->n[a]);
+          int64_t cp = cell_linear(g, jp[0], jp[1], jp[2]);
+          int64_t cm = cell_linear(g, jm[0], jm[1], jm[2]);
+          double dv = vel[a * G + cp] - vel[a * G + cm];
+          if (dv < 0.0) {
+            double hi = rho[cp] > rho[cm] ? rho[cp] : rho[cm];
+            double lo = rho[cp] > rho[cm] ? rho[cm] : rho[cp];
+            double ratio = hi / lo;
+            if (ratio > best) best = ratio;
+          }
+        }
+        r_cell[cell_linear(g, jx, jy, jz)] = best >= r_min ? best : 0.0;
+      }
+}
+
+/* Eq. convolution_spectra on one spectrum of nb bins (energies increasing):
+ *   chi_out(eps_i) = cn * integral_{eps_0}^{eps_i} chi_in(e) (eps_i/e)^(2-q) de/e.
+ * Between adjacent bins chi_in is the power law through the two bin values
+ * (the bins are log-spaced; a power-law spectrum is represented exactly), so
+ * each segment integral is closed-form: with R = e1/e0 and local index
+ * s = ln(c1/c0)/ln R, a = s + q - 2,
+ *   integral_{e0}^{e1} c0 (e/e0)^s (eps_i/e)^(2-q) de/e
+ *     = c0 (eps_i/e0)^(2-q) (R^a - 1)/a,   (R^a - 1)/a = expm1(a ln R)/a.
+ * A segment with a zero endpoint contributes 0 (the limit of the power law
+ * through a vanishing value).  chi_out at the lowest bin is 0.              */
+void or_shock_convolve(int nb, const double* eng, const double* chi_in, double q, double cn,
+                       double* chi_out) {
+  for (int i = 0; i < nb; ++i) {
+    double sum = 0.0;
+    for (int j = 1; j <= i; ++j) {
+      double e0 = eng[j - 1], e1 = eng[j], c0 = chi_in[j - 1], c1 = chi_in[j];
+      if (!(c0 > 0.0 && c1 > 0.0 && e1 > e0)) continue;
+      double lnR = log(e1 / e0);
+      double s = log(c1 / c0) / lnR;
+      double a = s + q - 2.0;
+      double I = a == 0.0 ? lnR : expm1(a * lnR) / a;
+      sum += c0 * pow(eng[i] / e0, 2.0 - q) * I;
+    }
+    chi_out[i] = cn * sum;
+  }
+}
+
+/* Shock update of the LP spectra after a step's smooth update.  An LP whose
+ * cell at x (the cell containing it) is a shock cell, and that was not in a
+ * shock cell at the end of its previous step (state[p] == 0), takes
+ * Eq. convolution_spectra with q = or_dsa_index(r) and cn = q / r: the
+ * test-particle solution conserves particle number per unit fluid density,
+ * chi = N/n (Eq. chi), across a jump n_d = r n_u.  state[p] becomes 1 in a
+ * shock cell and 0 elsewhere.  chi, eng bin-major [nb][n].                  */
+void or_lp_shock(const or_grid* g, const double* r_cell, int nb, int64_t n, const double* x,
+                 double* chi, const double* eng, uint8_t* state) {
+#pragma omp parallel
+  {
+    double* e = (double*)malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1));
+    double* ci = (double*)malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1));
+    double* co = (double*)malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1));
+#pragma omp for schedule(static)
+    for (int64_t p = 0; p < n; ++p) {
+      double xp[3] = {x[p], x[n + p], x[2 * n + p]};
+      int j[3]; double d[3];
+      or_cell_coord(g, xp, j, d);
+      double r = r_cell[cell_linear(g, j[0], j[1], j[2])];
+      if (r > 0.0) {
+        if (!state[p]) {
+          double q = or_dsa_index(r);
+          for (int i = 0; i < nb; ++i) {
+            e[i] = eng[(int64_t)i * n + p];
+            ci[i] = chi[(int64_t)i * n + p];
+          }
+          or_shock_convolve(nb, e, ci, q, q / r, co);
+          for (int i = 0; i < nb; ++i) chi[(int64_t)i * n + p] = co[i];
+        }
+        state[p] = 1;
+      } else {
+        state[p] = 0;
+      }
+    }
+    free(e); free(ci); free(co);
+  }
+}

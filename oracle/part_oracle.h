@@ -13,6 +13,9 @@
  *   Eq. rad_losses      d eps/d tau = -c_r eps^2                   (Sec. 2)
  *   Eq. cr_chi          d chi/d tau + d_eps[(-eps/3 div u - c_r eps^2) chi] = 0
  *   Eq. initSpec        chi_i = N0 (1-p)/(emax^(1-p)-emin^(1-p)) eps_i^-p  (Sec. 4.1.2)
+ *   Eq. convolution_spectra  chi_out = C int chi_in (eps/eps')^(2-q) d eps'/eps'  (Sec. 2)
+ *   Eq. slope           q(r) = 3r/(r-1) (+ q_R, zero for non-relativistic shocks)
+ *   Rankine-Hugoniot    r = (gamma+1) M^2/(2 + (gamma-1) M^2)      (Sec. 4.1.2)
  *   Appendix A          particle record: pos, speed, chi[128], eng[128], id
  * Where the paper is silent the oracle uses textbook definitions:
  *   TSC / CIC shape functions (Hockney & Eastwood), relativistic Boris push
@@ -86,4 +89,17 @@ void or_init_particles(const or_grid* g, int64_t n, uint64_t seed, double u_th,
  * deletion flags of n particles, returns n_keep and src[j] (j < n_keep) = the
  * old index of the particle that ends up in slot j.                        */
 int64_t or_compact_map(int64_t n, const uint8_t* del, int64_t* src);
+/* Rankine-Hugoniot compression ratio r(gamma, M) */
+double or_rh_compression(double gamma, double mach);
+/* Eq. slope without the relativistic correction: q = 3r/(r-1) */
+double or_dsa_index(double r);
+/* per-cell compression ratio of detected shocks (0: no shock), [G] */
+void or_shock_cells(const or_grid* g, const double* vel, const double* rho, double r_min,
+                    double* r_cell);
+/* Eq. convolution_spectra on one spectrum (piecewise power law in chi_in) */
+void or_shock_convolve(int nb, const double* eng, const double* chi_in, double q, double cn,
+                       double* chi_out);
+/* shock update of n LP spectra at positions x; state[n] = inside a shock cell */
+void or_lp_shock(const or_grid* g, const double* r_cell, int nb, int64_t n, const double* x,
+                 double* chi, const double* eng, uint8_t* state);
 #endif

@@ -504,3 +504,206 @@ def test_compaction_invariants():
         assert moved == holes                                   # exactly the holes move
         assert all(src[j] >= nk for j in moved)                 # fillers from the tail
         assert [src[j] for j in moved] == sorted(src[j] for j in moved)
+
+
+# ---------------------------------------------------------------- shock (DSA)
+def _shock_e2():
+    vals = {}
+    for ln in open(os.path.join(HERE, "golden", "shock_e2.txt")):
+        ln = ln.split("#")[0].split()
+        if len(ln) == 2:
+            vals[ln[0]] = float(ln[1])
+    return vals
+
+
+def test_rh_compression_and_slope_match_the_shock_test():
+    """Sec. 4.1.2: M = v_u / sqrt(gamma p_u / rho_u), r ~ 3.64, and the
+    post-shock energy slope q - 2 ~ 2.14 (Eq. slope, Fig. shock caption);
+    r -> (gamma+1)/(gamma-1) for strong shocks and r = 1 at M = 1."""
+    e2 = _shock_e2()
+    g = e2["gamma"]
+    M = e2["v_u"] / np.sqrt(g * e2["p_u"] / e2["rho_u"])
+    r = O.rh_compression(g, M)
+    assert abs(r - e2["r_printed"]) < 0.005
+    assert abs(r - 40.0 / 11.0) < 1e-14                 # M^2 = 30 exactly
+    q = O.dsa_index(r)
+    assert abs((q - 2.0) - e2["slope_printed"]) < 0.005
+    assert abs(O.rh_compression(g, 1e8) - (g + 1) / (g - 1)) < 1e-12
+    assert abs(O.rh_compression(g, 1.0) - 1.0) < 1e-15
+    assert abs(O.dsa_index(4.0) - 4.0) < 1e-15          # strong shock: q = 4
+
+
+def _power_law_out(eng, K, p, q, cn):
+    """Closed form of Eq. convolution_spectra for chi_in = K eps^-p:
+    cn K eps^(2-q) (eps^(q-2-p) - eps0^(q-2-p)) / (q-2-p)."""
+    a = q - 2.0 - p
+    return cn * K * eng ** (2.0 - q) * (eng ** a - eng[0] ** a) / a
+
+
+def test_shock_convolution_of_a_power_law_is_exact():
+    """A power-law input is represented exactly by the per-segment power
+    laws, so the oracle must reproduce the closed-form integral."""
+    for nb, p, q in ((128, 9.0, 120.0 / 29.0), (40, 2.2, 4.0), (17, 0.5, 5.5)):
+        eng = np.exp(np.linspace(np.log(1e2), np.log(1e4), nb))
+        chi = 3e-7 * eng ** -p
+        out = O.shock_convolve(eng, chi, q, 1.7)
+        ref = _power_law_out(eng, 3e-7, p, q, 1.7)
+        assert out[0] == 0.0
+        assert np.max(np.abs(out[1:] - ref[1:]) / ref[1:]) < 1e-11
+
+
+def test_shock_post_spectrum_slope_within_paper_bound():
+    """Sec. 4.1.2: the post-shock spectrum of the Eq. initSpec spectrum
+    (p = 9 on [1e2, 1e4], 128 bins) follows eps^-(q-2) over the upper decade
+    within the paper's 0.5%."""
+    e2 = _shock_e2()
+    eng, chi = O.init_spectrum(int(e2["nb"]), e2["eps_min"], e2["eps_max"], e2["p_index"],
+                               e2["N0"])
+    r = 40.0 / 11.0
+    q = O.dsa_index(r)
+    out = O.shock_convolve(eng, chi, q, q / r)
+    up = eng >= 1e3
+    slope = -np.polyfit(np.log(eng[up]), np.log(out[up]), 1)[0]
+    assert abs(slope - (q - 2.0)) / (q - 2.0) <= e2["slope_rel_err"]
+    assert abs(slope - (q - 2.0)) / (q - 2.0) <= 1e-6     # and far inside it
+
+
+def test_shock_convolution_causal_and_exponent_sign():
+    """Only one segment non-zero: chi_out vanishes up to it and is exactly
+    eps^(2-q) beyond (wrong sign or a transposed index fails this)."""
+    nb, k = 30, 11
+    eng = np.exp(np.linspace(0.0, 5.0, nb))
+    chi = np.zeros(nb)
+    chi[k], chi[k + 1] = 2.0, 1.5
+    q = 4.3
+    out = O.shock_convolve(eng, chi, q, 1.0)
+    assert np.all(out[: k + 1] == 0.0) and out[k + 1] > 0.0
+    ratio = out[k + 2:] / out[k + 1: -1]
+    assert np.allclose(ratio, (eng[k + 2:] / eng[k + 1: -1]) ** (2.0 - q), rtol=1e-13)
+    # brute force of that one segment: midpoint rule with 2e5 sub-steps
+    e0, e1 = eng[k], eng[k + 1]
+    t = np.linspace(np.log(e0), np.log(e1), 200001)
+    tm = 0.5 * (t[1:] + t[:-1])
+    s = np.log(1.5 / 2.0) / np.log(e1 / e0)
+    f = 2.0 * np.exp(s * (tm - np.log(e0))) * np.exp((2.0 - q) * (np.log(eng[-1]) - tm))
+    assert abs(np.sum(f) * (t[1] - t[0]) - out[-1]) / out[-1] < 1e-9
+
+
+def test_shock_number_conservation():
+    """cn = q/r conserves particles per unit fluid density (Eq. chi across a
+    density jump r): the integral of chi_out over [eps_0, inf) equals that
+    of chi_in (tail beyond the last bin in closed form).  The number of the
+    sampled output is taken by quadrature, whose error near the steep low
+    end is O(dln eps^2): 2e-5 at 8000 bins over ten decades."""
+    r = 40.0 / 11.0
+    q = O.dsa_index(r)
+    nb = 8000
+    eng = np.exp(np.linspace(np.log(1e2), np.log(1e12), nb))
+    chi = 1e-6 * (eng / 1e2) ** -9.0
+    out = O.shock_convolve(eng, chi, q, q / r)
+
+    def integral(c):  # piecewise power law through c; trapezoid next to a zero
+        e0, e1, c0, c1 = eng[:-1], eng[1:], c[:-1], c[1:]
+        ok = (c0 > 0) & (c1 > 0)
+        s = np.log(c1[ok] / c0[ok]) / np.log(e1[ok] / e0[ok])
+        pw = np.sum(c0[ok] * e0[ok] * ((e1[ok] / e0[ok]) ** (s + 1.0) - 1.0) / (s + 1.0))
+        return pw + np.sum(0.5 * (c0[~ok] + c1[~ok]) * (e1[~ok] - e0[~ok]))
+
+    n_in = integral(chi) + chi[-1] * eng[-1] / 8.0
+    n_out = integral(out) + out[-1] * eng[-1] / (q - 3.0)
+    assert abs(n_out - n_in) / n_in < 1e-4
+
+
+def _shock_snapshot(n, r, rho_u=50.0, v_u=0.1):
+    """Analytic stationary shock at x = 0 on [-1,1]^2 (Rankine-Hugoniot):
+    x < 0 upstream (rho_u, v_u), x > 0 downstream (r rho_u, v_u / r)."""
+    xc = -1.0 + (np.arange(n) + 0.5) * (2.0 / n)
+    down = np.broadcast_to(xc[None, :] > 0.0, (n, n))
+    rho = np.where(down, r * rho_u, rho_u)[None]
+    vel = np.zeros((3, 1, n, n))
+    vel[0] = np.where(down, v_u / r, v_u)
+    return vel, rho
+
+
+def test_shock_cells_on_the_rh_snapshot():
+    """The two columns beside x = 0 are shock cells with the exact jump r;
+    the periodic seam at x = +-1 is an expansion and smooth compressions
+    below r_min are not flagged."""
+    n = 32
+    g = O.make_grid(2, (n, n, 1))
+    r = 40.0 / 11.0
+    vel, rho = _shock_snapshot(n, r)
+    rc = O.shock_cells(g, vel, rho, 1.5).reshape(n, n)
+    flagged = np.argwhere(rc > 0)
+    assert set(flagged[:, 1].tolist()) == {n // 2 - 1, n // 2}
+    assert flagged.shape[0] == 2 * n
+    assert np.all(rc[rc > 0] == (r * 50.0) / 50.0)
+    xc = -1.0 + (np.arange(n) + 0.5) * (2.0 / n)
+    v2 = np.zeros((3, 1, n, n))
+    v2[0] = -0.1 * np.sin(np.pi * xc)[None, :]
+    r2 = (1.0 + 0.2 * np.cos(np.pi * xc))[None, None, :] * np.ones((1, n, n))
+    assert np.all(O.shock_cells(g, v2, r2, 1.5) == 0.0)
+
+
+def test_lp_shock_applies_once_per_crossing():
+    """An LP sitting in a shock cell is convolved once; after leaving the
+    shock its state resets."""
+    n = 32
+    g = O.make_grid(2, (n, n, 1))
+    r = 40.0 / 11.0
+    vel, rho = _shock_snapshot(n, r)
+    rc = O.shock_cells(g, vel, rho, 1.5)
+    x = np.array([[-0.01, -0.5], [0.3, 0.3], [0.0, 0.0]])   # LP 0 in a shock cell
+    eng1, chi1 = O.init_spectrum(64, 1e2, 1e4, 9.0, 1e-6)
+    eng = np.repeat(eng1[:, None], 2, axis=1)
+    chi = np.repeat(chi1[:, None], 2, axis=1)
+    st = np.zeros(2, np.uint8)
+    c1, s1 = O.lp_shock(g, rc, x, chi, eng, st)
+    q = O.dsa_index(r)
+    assert np.array_equal(c1[:, 0], O.shock_convolve(eng1, chi1, q, q / r))
+    assert np.array_equal(c1[:, 1], chi1) and s1.tolist() == [1, 0]
+    c2, s2 = O.lp_shock(g, rc, x, c1, eng, s1)
+    assert np.array_equal(c2, c1) and s2.tolist() == [1, 0]
+    x[0, 0] = -0.5
+    c3, s3 = O.lp_shock(g, rc, x, c2, eng, s2)
+    assert np.array_equal(c3, c2) and s3.tolist() == [0, 0]
+
+
+def test_shock_test_end_to_end_on_the_oracle():
+    """Sec. 4.1.2 on the oracle: 100 LPs placed upstream of the stationary
+    shock are advected through it (Heun RK2, TSC) with the smooth spectral
+    update every step and the shock update after it; each LP is convolved
+    exactly once, and its post-shock spectrum falls as eps^-(q-2) over its
+    upper decade within the paper's 0.5% (weak cooling, c0 = 1e-8)."""
+    e2 = _shock_e2()
+    n, N = int(e2["grid"]), int(e2["n_lp"])
+    g = O.make_grid(2, (n, n, 1))
+    r = O.rh_compression(e2["gamma"], e2["v_u"] / np.sqrt(e2["gamma"] * e2["p_u"] / e2["rho_u"]))
+    vel, rho = _shock_snapshot(n, r, e2["rho_u"], e2["v_u"])
+    B = np.zeros((3, 1, n, n))
+    B[0] = 1.0                                   # B = (1, 0, 0), Sec. 4.1.2
+    rc = O.shock_cells(g, vel, rho, 1.5)
+    rng = np.random.default_rng(3)
+    x = np.zeros((3, N))
+    x[0] = rng.uniform(-0.6, -0.2, N)
+    x[1] = rng.uniform(-1.0, 1.0, N)
+    e1, c1 = O.init_spectrum(int(e2["nb"]), e2["eps_min"], e2["eps_max"], e2["p_index"],
+                             e2["N0"])
+    eng = np.repeat(e1[:, None], N, axis=1)
+    chi = np.repeat(c1[:, None], N, axis=1)
+    nold = np.array([O.gather(g, 2, rho, x[:, p])[0] for p in range(N)])
+    st = np.zeros(N, np.uint8)
+    crossings = np.zeros(N, int)
+    dt = 0.5 * (2.0 / n) / e2["v_u"]
+    for _ in range(100):
+        x, nn, b2, gm = O.lp_rk2_step(g, 2, vel, rho, B, x, dt)
+        chi, eng, nold = O.spec_update(chi, eng, nold, nn, b2, gm, dt, 1e-8)
+        prev = st
+        chi, st = O.lp_shock(g, rc, x, chi, eng, st)
+        crossings += (st == 1) & (prev == 0)
+    assert np.all(crossings == 1) and np.all(x[0] > 0.02)
+    q = O.dsa_index(r)
+    for p in range(N):
+        up = eng[:, p] >= eng[-1, p] / 10.0
+        slope = -np.polyfit(np.log(eng[up, p]), np.log(chi[up, p]), 1)[0]
+        assert abs(slope - (q - 2.0)) / (q - 2.0) <= e2["slope_rel_err"]
