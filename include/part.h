@@ -167,8 +167,38 @@ part_status part_deposit(part_ctx* ctx, double* grid_out);
  * samples of the last PART_LP_RK2 push.  Per LP: dtau = dt/gamma_g (Sec. 2),
  * A = (n_old/n_new)^{1/3}, c_r = c0 (|B|^2/2 + u_rad),
  * C = c_r dtau expm1(ln A)/ln A; per bin, s = A + C eps:
- *   eps <- eps/s,  chi <- chi s^2/A;  then n_old <- n_new.                 */
+ *   eps <- eps/s,  chi <- chi s^2/A;  then n_old <- n_new.
+ * With shocks enabled, every LP that the last push moved into a shock cell
+ * (from outside one) then takes the shock update of part_enable_shocks.
+ * part_sort or part_compact between the push and this call invalidate the
+ * samples (PART_EINVAL).                                                   */
 part_status spec_update(part_ctx* ctx, double dt, double c0, double u_rad);
+
+/* Diffusive shock acceleration of the LP spectra (PART_LP_RK2 only).
+ * Shock cells are found in the current fields (recomputed by every
+ * part_set_fields): along an axis a < dim, a cell whose neighbours' flow
+ * converges (v_a(j+1) - v_a(j-1) < 0) and whose neighbour density ratio
+ * max/min is >= r_min is a shock cell with compression ratio r = the largest
+ * such ratio.  (The paper leaves the criterion to the fluid code.)
+ * state: device uint8[n], caller-owned and caller-initialised (0 = not in a
+ * shock cell), one flag per bound LP; it is permuted by part_sort and moved
+ * by part_compact with the LPs.  part_bind_particles disables shocks; call
+ * this again after binding.  NULL disables shocks.  r_min must be > 1.
+ * After a push, an LP whose cell at x^{n+1} is a shock cell and whose flag is
+ * 0 is listed; its flag then follows its cell (1 in a shock cell, 0
+ * elsewhere).  spec_update applies Eq. convolution_spectra to each listed LP
+ * after the smooth update:
+ *   chi(eps_i) <- cn * integral_{eps_0}^{eps_i} chi(e) (eps_i/e)^(2-q) de/e,
+ * q = 3r/(r-1) (Eq. slope; the relativistic correction q_R is not built),
+ * cn = q/r (particle number per unit fluid density is conserved across the
+ * jump n_d = r n_u), chi between adjacent bins taken as the power law through
+ * the two bin values, eps_0 = the LP's lowest bin energy (chi there becomes
+ * 0).  Bin energies are unchanged.  Requires bound particles and fields.   */
+part_status part_enable_shocks(part_ctx* ctx, double r_min, uint8_t* state);
+
+/* Device pointer to the shock cells r[G] (cell order as the fields; 0 = no
+ * shock), valid while shocks are enabled and the fields are unchanged.     */
+part_status part_shock_cells(part_ctx* ctx, const double** r_cell, int64_t* ncells);
 
 /* Initialise the bound particles on the device from Philox4x32-10 draws
  * (key = seed; counter (p, 0) -> uniform position over the domain, counter

@@ -89,6 +89,8 @@ def lib():
         "part_sort": (st, [P]),
         "part_cell_start": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
         "part_compact": (st, [P, P, C.POINTER(C.c_int64)]),
+        "part_enable_shocks": (st, [P, C.c_double, P]),
+        "part_shock_cells": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
         "part_enable_deposit": (st, [P, C.c_int]),
         "part_gather_push": (st, [P, C.c_double, C.c_double, C.c_int]),
         "part_deposit": (st, [P, P]),
@@ -206,6 +208,20 @@ class Part:
         nn = C.c_int64()
         self._check(self.L.part_compact(self.ctx, _ptr(deleted), C.byref(nn)))
         return nn.value
+
+    def enable_shocks(self, r_min: float, state):
+        """Diffusive shock acceleration of the LP spectra (Eq. convolution_spectra);
+        state: device uint8[n] per-LP flags (None disables)."""
+        self._check(self.L.part_enable_shocks(self.ctx, r_min, _ptr(state)))
+        self._keep_shock = state
+
+    def shock_cells(self):
+        """View of the per-cell compression ratios r[G] (0: no shock)."""
+        p = C.c_void_p()
+        nc = C.c_int64()
+        self._check(self.L.part_shock_cells(self.ctx, C.byref(p), C.byref(nc)))
+        off = p.value - self.ws.data_ptr()
+        return self.ws[off: off + 8 * nc.value].view(self.torch.float64)
 
     def enable_deposit(self, on=True):
         self._check(self.L.part_enable_deposit(self.ctx, 1 if on else 0))

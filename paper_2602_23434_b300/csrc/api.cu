@@ -88,7 +88,7 @@ namespace {
 
 struct Layout {
   size_t fpad, keys0, keys1, vals0, vals1, hist, hsum, cstart, tmp, dpart, samples, status,
-      alt_x, alt_off, alt_u, alt_w, alt_id, total;
+      alt_x, alt_off, alt_u, alt_w, alt_id, shock_r, shock_list, shock_rs, total;
 };
 
 int ncomp_of(part_mode m) { return m == PART_BORIS ? 6 : 7; }
@@ -131,6 +131,11 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   L.alt_u = take(alt ? (size_t)c1 * 3 * e : 0);
   L.alt_w = take(alt ? (size_t)c1 * e : 0);
   L.alt_id = take(alt ? (size_t)c1 * 8 : 0);
+  // LP mode: shock cells and the list of LPs shocked by the last push
+  const bool lp = mode == PART_LP_RK2;
+  L.shock_r = take(lp ? (size_t)g.G * 8 : 0);
+  L.shock_list = take(lp ? (size_t)(c1 + 1) * 4 : 0);
+  L.shock_rs = take(lp ? (size_t)c1 * 8 : 0);
   L.total = off;
   return L;
 }
@@ -273,6 +278,11 @@ part_status part_init(part_ctx** out, const part_grid* grid, part_prec prec, par
     c->alt_w = c->ws + L.alt_w;
     c->alt_id = (uint64_t*)(c->ws + L.alt_id);
   }
+  if (mode == PART_LP_RK2) {
+    c->shock_r = (double*)(c->ws + L.shock_r);
+    c->shock_list = (uint32_t*)(c->ws + L.shock_list);
+    c->shock_rs = (double*)(c->ws + L.shock_rs);
+  }
   cudaError_t e = cudaMemsetAsync(c->status, 0, 256, c->stream);
   if (e != cudaSuccess) {
     part_status r = cuda_fail(nullptr, e, "status reset");
@@ -301,6 +311,7 @@ part_status part_set_fields(part_ctx* c, const void* fields, int ncomp, part_pre
                                                       : "LP mode needs ncomp = 7 (v, rho, B)");
   if (field_prec != c->prec) return fail(c, PART_EINVAL, "field_prec must match the context");
   cudaError_t e = launch_pad_fields(c, fields);
+  if (e == cudaSuccess && c->shk) e = launch_shock_cells(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_set_fields");
   c->fields_set = true;
   return PART_OK;
@@ -333,6 +344,8 @@ part_status part_bind_particles(part_ctx* c, int64_t n, void* x_or_cell, void* o
   c->chi = c->mode == PART_LP_RK2 ? chi : nullptr;
   c->eng = c->mode == PART_LP_RK2 ? eng : nullptr;
   c->n_old = c->mode == PART_LP_RK2 ? n_old : nullptr;
+  c->shk = nullptr;  // shock flags belong to the previous particle set
+  c->shock_listed = false;
   c->bound = true;
   c->sorted = false;
   c->deposit_ready = false;
@@ -347,6 +360,8 @@ part_status part_sort(part_ctx* c) {
   if (e == cudaSuccess) e = launch_sort(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_sort");
   c->sorted = true;
+  c->samples_ready = false;  // LP samples are in the old particle order
+  c->shock_listed = false;
   return PART_OK;
 }
 
@@ -364,6 +379,35 @@ part_status part_compact(part_ctx* c, const uint8_t* deleted, int64_t* n_new) {
   c->sorted = false;
   c->deposit_ready = false;
   c->samples_ready = false;
+  c->shock_listed = false;
+  return PART_OK;
+}
+
+part_status part_enable_shocks(part_ctx* c, double r_min, uint8_t* state) {
+  if (check_ctx(c)) return PART_EINVAL;
+  if (c->mode != PART_LP_RK2) return fail(c, PART_EINVAL, "shocks need LP mode");
+  if (!state) {
+    c->shk = nullptr;
+    c->shock_listed = false;
+    return PART_OK;
+  }
+  if (!(std::isfinite(r_min) && r_min > 1.0)) return fail(c, PART_EINVAL, "r_min must be > 1");
+  if (!c->bound) return fail(c, PART_EINVAL, "bind the particles first");
+  if (!c->fields_set) return fail(c, PART_EINVAL, "part_set_fields first");
+  c->shk = state;
+  c->r_min = r_min;
+  c->shock_listed = false;
+  cudaError_t e = launch_shock_cells(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "part_enable_shocks");
+  return PART_OK;
+}
+
+part_status part_shock_cells(part_ctx* c, const double** r_cell, int64_t* ncells) {
+  if (check_ctx(c)) return PART_EINVAL;
+  if (!r_cell || !ncells) return fail(c, PART_EINVAL, "NULL output");
+  if (!c->shk) return fail(c, PART_EINVAL, "shocks are not enabled");
+  *r_cell = c->shock_r;
+  *ncells = c->geo.G;
   return PART_OK;
 }
 
@@ -409,6 +453,7 @@ part_status part_gather_push(part_ctx* c, double q_over_m, double dt, int nsteps
     if (nsteps != 1) return fail(c, PART_EINVAL, "LP mode advances one step per call");
     e = launch_lp_push(c, dt, nsteps);
     c->samples_ready = true;
+    c->shock_listed = c->shk != nullptr;
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "part_gather_push");
   c->sorted = false;
@@ -432,6 +477,8 @@ part_status spec_update(part_ctx* c, double dt, double c0, double u_rad) {
   if (!std::isfinite(dt) || !std::isfinite(c0) || !std::isfinite(u_rad))
     return fail(c, PART_EINVAL, "dt, c0, u_rad must be finite");
   cudaError_t e = launch_spec_update(c, dt, c0, u_rad);
+  if (e == cudaSuccess && c->shock_listed) e = launch_shock_convolve(c);
+  c->shock_listed = false;
   if (e != cudaSuccess) return cuda_fail(c, e, "spec_update");
   c->samples_ready = false;
   return PART_OK;

@@ -18,6 +18,7 @@ __device__ __forceinline__ double wrap_axis(double v, double lo, double hi, doub
 template <int SHAPE, int DIM>
 struct Stencil {
   int64_t base;     // padded index of the (-1,-1,-1) corner
+  int64_t cell;     // linear index of the cell containing x
   double wx[3], wy[3], wz[3];
   bool finite;
   __device__ __forceinline__ Stencil(const Geo& g, const double* xp) {
@@ -41,6 +42,7 @@ struct Stencil {
     wz[2] = 0.0;
     if (DIM == 3) shape_weights<SHAPE>(d[2], wz);
     base = ((int64_t)j[2] * g.pn[1] + j[1]) * g.pn[0] + j[0];
+    cell = ((int64_t)j[2] * g.n[1] + j[1]) * g.n[0] + j[0];
   }
   // sum over the stencil of components [c0, c0 + NC); the 27 weight products
   // are formed once for all NC components
@@ -92,10 +94,43 @@ struct Stencil {
   }
 };
 
-template <int SHAPE, int DIM>
+// Shock bookkeeping of one LP at its new cell: an LP entering a shock cell
+// (flag 0 -> 1) is appended to the list with the cell's compression ratio;
+// the flag follows the cell.  Appends are warp-aggregated (one atomic per
+// warp); list order is irrelevant, each entry is processed on its own.
+__device__ __forceinline__ void shock_mark(int64_t p, int64_t cell,
+                                           const double* __restrict__ shock_r,
+                                           uint8_t* __restrict__ shk,
+                                           uint32_t* __restrict__ list,
+                                           double* __restrict__ rs) {
+  const double rr = shock_r[cell];
+  const uint8_t st = shk[p];
+  const bool take = rr > 0.0 && st == 0;
+  if (rr > 0.0) {
+    if (st == 0) shk[p] = 1;
+  } else if (st != 0) {
+    shk[p] = 0;
+  }
+  const unsigned act = __activemask();
+  const unsigned m = __ballot_sync(act, take);
+  if (take) {
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(list, (uint32_t)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    const uint32_t slot = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+    list[1 + slot] = (uint32_t)p;
+    rs[slot] = rr;
+  }
+}
+
+template <int SHAPE, int DIM, bool SHOCK>
 __global__ void __launch_bounds__(256)
     k_lp_rk2(const double* __restrict__ fp, const Geo g, double* __restrict__ x, int64_t n,
-             double dt, double* __restrict__ samples, int* __restrict__ status) {
+             double dt, double* __restrict__ samples, int* __restrict__ status,
+             const double* __restrict__ shock_r, uint8_t* __restrict__ shk,
+             uint32_t* __restrict__ list, double* __restrict__ rs) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     double x0[3], xs[3], x1[3];
@@ -134,6 +169,7 @@ __global__ void __launch_bounds__(256)
     samples[2 * n + p] = gam;
     if (!(s0.finite && ss.finite && s1.finite && isfinite(gam) && isfinite(r) && r > 0.0))
       atomicOr(status, ST_NONFINITE);
+    if (SHOCK) shock_mark(p, s1.cell, shock_r, shk, list, rs);
   }
 }
 
@@ -210,10 +246,97 @@ int grid_for(int64_t n, int threads) {
 
 template <int SHAPE, int DIM>
 cudaError_t lp_launch(part_ctx* c, double dt) {
-  k_lp_rk2<SHAPE, DIM><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
-      (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status);
+  const int gb = grid_for(c->n, 256);
+  if (c->shk) {
+    cudaError_t e = cudaMemsetAsync(c->shock_list, 0, sizeof(uint32_t), c->stream);
+    if (e != cudaSuccess) return e;
+    k_lp_rk2<SHAPE, DIM, true><<<gb, 256, 0, c->stream>>>(
+        (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status,
+        c->shock_r, c->shk, c->shock_list, c->shock_rs);
+  } else {
+    k_lp_rk2<SHAPE, DIM, false><<<gb, 256, 0, c->stream>>>(
+        (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status,
+        nullptr, nullptr, nullptr, nullptr);
+  }
   c->launches++;
   return cudaGetLastError();
+}
+
+// Shock cells from the padded fields (periodic ghost layer of one cell):
+// along each axis a < dim, a converging flow across the cell (v_a(+1) -
+// v_a(-1) < 0) with neighbour density ratio max/min >= r_min marks it; the
+// cell keeps the largest such ratio, 0 if none.
+__global__ void k_shock_cells(const double* __restrict__ fp, const Geo g, double r_min,
+                              double* __restrict__ r_cell) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.G;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int jx = (int)(c % g.n[0]);
+    const int jy = (int)((c / g.n[0]) % g.n[1]);
+    const int jz = (int)(c / ((int64_t)g.n[0] * g.n[1]));
+    const int64_t q = ((int64_t)(jz + g.h[2]) * g.pn[1] + (jy + g.h[1])) * g.pn[0] + (jx + g.h[0]);
+    double best = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= g.dim) break;
+      const int64_t st = a == 0 ? 1 : a == 1 ? (int64_t)g.pn[0] : (int64_t)g.pn[0] * g.pn[1];
+      const double dv = fp[a * g.pplane + q + st] - fp[a * g.pplane + q - st];
+      if (dv < 0.0) {
+        const double rp = fp[3 * g.pplane + q + st], rm = fp[3 * g.pplane + q - st];
+        const double hi = rp > rm ? rp : rm, lo = rp > rm ? rm : rp;
+        const double ratio = hi / lo;
+        if (ratio > best) best = ratio;
+      }
+    }
+    r_cell[c] = best >= r_min ? best : 0.0;
+  }
+}
+
+// Eq. convolution_spectra for each listed LP, one thread per LP, so only
+// shocked LPs do the work and a warp never idles on unshocked lanes.  With
+// chi_in the power law through adjacent bin values, the kernel
+// (eps_i/e)^(2-q) separates: chi_out_i = cn S_i / w_i, w = eps^(q-2),
+// S_i = sum_{j<=i} dln eps_j h_{j-1} expm1(d_j)/d_j, h = chi w,
+// d_j = ln(h_j/h_{j-1}) -- a running sum over the bins, O(N_b) per LP.
+// q = 3r/(r-1) (Eq. slope, non-relativistic), cn = q/r (particle number per
+// unit fluid density conserved across the jump).
+__global__ void __launch_bounds__(128)
+    k_shock_convolve(const uint32_t* __restrict__ list, const double* __restrict__ rs,
+                     double* __restrict__ chi, const double* __restrict__ eng, int64_t n,
+                     int nb, int* __restrict__ status) {
+  const uint32_t cnt = list[0];
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
+       t += gridDim.x * blockDim.x) {
+    const int64_t p = list[1 + t];
+    const double r = rs[t];
+    const double q = 3.0 * r / (r - 1.0);
+    const double cn = q / r;
+    const double qm2 = q - 2.0;
+    double ep = eng[p];
+    double lep = log(ep);
+    double hp = chi[p] * exp(qm2 * lep);
+    chi[p] = 0.0;
+    double S = 0.0;
+    bool ok = true;
+    for (int j = 1; j < nb; ++j) {
+      const double e = eng[(int64_t)j * n + p];
+      const double cj = chi[(int64_t)j * n + p];
+      const double le = log(e);
+      const double w = exp(qm2 * le);
+      const double h = cj * w;
+      if (hp > 0.0 && h > 0.0 && e > ep) {
+        const double d = log(h / hp);
+        const double D = le - lep;
+        S += d == 0.0 ? D * hp : D * hp * (expm1(d) / d);
+      }
+      const double out = cn * (S / w);
+      ok = ok && isfinite(out);
+      chi[(int64_t)j * n + p] = out;
+      ep = e;
+      lep = le;
+      hp = h;
+    }
+    if (!ok) atomicOr(status, ST_NONFINITE);
+  }
 }
 
 }  // namespace
@@ -224,6 +347,23 @@ cudaError_t launch_lp_push(part_ctx* c, double dt, int nsteps) {
   if (c->shape == PART_TSC)
     return c->geo.dim == 3 ? lp_launch<PART_TSC, 3>(c, dt) : lp_launch<PART_TSC, 2>(c, dt);
   return c->geo.dim == 3 ? lp_launch<PART_CIC, 3>(c, dt) : lp_launch<PART_CIC, 2>(c, dt);
+}
+
+cudaError_t launch_shock_cells(part_ctx* c) {
+  k_shock_cells<<<grid_for(c->geo.G, 256), 256, 0, c->stream>>>(
+      (const double*)c->fpad, c->geo, c->r_min, c->shock_r);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shock_convolve(part_ctx* c) {
+  if (c->n == 0) return cudaSuccess;
+  int64_t b = (c->n + 127) / 128;
+  if (b > 148 * 8) b = 148 * 8;
+  k_shock_convolve<<<(unsigned)b, 128, 0, c->stream>>>(c->shock_list, c->shock_rs, c->chi,
+                                                       c->eng, c->n, c->nbins, c->status);
+  c->launches++;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad) {

@@ -96,6 +96,13 @@ struct part_ctx {
   double* chi{};
   double* eng{};
   double* n_old{};
+  // LP shocks (Eq. convolution_spectra)
+  double* shock_r{};       // [G] compression ratio of each shock cell, 0 elsewhere
+  uint32_t* shock_list{};  // [0]: count; [1 + k]: LPs shocked by the last push
+  double* shock_rs{};      // [k]: compression ratio each listed LP saw
+  uint8_t* shk{};          // caller's per-LP "in a shock cell" flags; NULL: shocks off
+  double r_min{};
+  bool shock_listed{};     // the last push filled the list
   bool bound{}, fields_set{}, sorted{}, deposit_on{}, deposit_ready{}, samples_ready{};
   int64_t launches{};
   std::string err;
@@ -208,6 +215,8 @@ cudaError_t launch_pad_fields(part_ctx* c, const void* src);
 cudaError_t launch_sort(part_ctx* c);
 cudaError_t flush_pending(part_ctx* c);  // copy pending sorted state to the bound arrays
 cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew);
+cudaError_t launch_shock_cells(part_ctx* c);       // shock_r from the padded LP fields
+cudaError_t launch_shock_convolve(part_ctx* c);    // Eq. convolution_spectra on the list
 cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps);
 cudaError_t launch_boris_mixed(part_ctx* c, double qm, double dt, int nsteps);
 cudaError_t launch_serve_kernel(int shape, int dim, const ServeHeader* hdr,

@@ -387,6 +387,7 @@ cudaError_t launch_sort(part_ctx* c) {
         if ((e = permute_plane<double>(c, c->eng + (int64_t)b * n, perm))) return e;
       }
       if (c->n_old && (e = permute_plane<double>(c, c->n_old, perm))) return e;
+      if (c->shk && (e = permute_plane<uint8_t>(c, c->shk, perm))) return e;
     }
     if (c->id && (e = permute_plane<uint64_t>(c, c->id, perm))) return e;
   } else {
@@ -487,6 +488,7 @@ cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew_out) {
     if ((e = fill_rows<double>(c, c->chi, c->nbins, del, n, nnew, gb))) return e;
     if ((e = fill_rows<double>(c, c->eng, c->nbins, del, n, nnew, gb))) return e;
     if (c->n_old && (e = fill_rows<double>(c, c->n_old, 1, del, n, nnew, gb))) return e;
+    if (c->shk && (e = fill_rows<uint8_t>(c, c->shk, 1, del, n, nnew, gb))) return e;
   }
   if (c->id && (e = fill_rows<uint64_t>(c, c->id, 1, del, n, nnew, gb))) return e;
   *nnew_out = nnew;
