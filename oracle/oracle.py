@@ -88,6 +88,8 @@ def lib():
             "or_cell_start": (None, [C.c_int64, C.c_int64, _U32, _U32]),
             "or_lp_rk2_step": (None, [G, C.c_int, _D, _D, _D, C.c_int64, _D, C.c_double,
                                       _D, _D, _D]),
+            "or_lp_rk3_step": (None, [G, C.c_int, _D, _D, _D, C.c_int64, _D, C.c_double,
+                                      _D, _D, _D]),
             "or_spec_update": (None, [C.c_int, C.c_int64, _D, _D, _D, _D, _D, _D,
                                       C.c_double, C.c_double, C.c_double]),
             "or_init_spectrum": (None, [C.c_int, C.c_double, C.c_double, C.c_double,
@@ -227,6 +229,16 @@ def lp_rk2_step(g: Grid, shape: int, vel, rho, bfield, x, dt: float):
     n = x.shape[1]
     n_new, b2m, gam = np.zeros(n), np.zeros(n), np.zeros(n)
     lib().or_lp_rk2_step(C.byref(g), shape, _d(_f64(vel)), _d(_f64(rho)), _d(_f64(bfield)),
+                         n, _d(x), dt, _d(n_new), _d(b2m), _d(gam))
+    return x, n_new, b2m, gam
+
+
+def lp_rk3_step(g: Grid, shape: int, vel, rho, bfield, x, dt: float):
+    """One SSP-RK3 step on a copy of x; returns (x, n_new, b2m, gam)."""
+    x = _f64(x).copy()
+    n = x.shape[1]
+    n_new, b2m, gam = np.zeros(n), np.zeros(n), np.zeros(n)
+    lib().or_lp_rk3_step(C.byref(g), shape, _d(_f64(vel)), _d(_f64(rho)), _d(_f64(bfield)),
                          n, _d(x), dt, _d(n_new), _d(b2m), _d(gam))
     return x, n_new, b2m, gam
 

@@ -73,6 +73,10 @@ void or_cell_start(int64_t nkeys, int64_t n, const uint32_t* sorted_keys, uint32
 void or_lp_rk2_step(const or_grid* g, int shape, const double* vel, const double* rho,
                     const double* bfield, int64_t n, double* x, double dt,
                     double* n_new, double* b2m, double* gam);
+/* third-order SSP Runge-Kutta LP advection (same arguments as RK2) */
+void or_lp_rk3_step(const or_grid* g, int shape, const double* vel, const double* rho,
+                    const double* bfield, int64_t n, double* x, double dt,
+                    double* n_new, double* b2m, double* gam);
 /* exact-characteristic spectral update; chi, eng are bin-major [nb][n] */
 void or_spec_update(int nb, int64_t n, double* chi, double* eng, double* n_old,
                     const double* n_new, const double* b2m, const double* gam,

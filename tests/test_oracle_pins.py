@@ -350,6 +350,68 @@ def test_lp_simple_advection_second_order():
     assert 1.8 < order1 < 2.3 and 1.8 < order2 < 2.3, errs
 
 
+def _rotation_error(step, nsteps, n=64, r0=0.5):
+    """Solid rotation v = (-y, x) sampled on the grid (TSC reproduces a
+    linear field exactly away from the periodic seam): one LP at radius r0,
+    one period; distance from its start."""
+    g = O.make_grid(2, (n, n))
+    xc = -1 + (np.arange(n) + 0.5) * 2 / n
+    X, Y = np.meshgrid(xc, xc)
+    vel = np.stack([-Y, X, np.zeros_like(X)]).reshape(3, -1)
+    rho, bf = np.ones((1, n * n)), np.zeros((3, n * n))
+    dt = 2 * math.pi / nsteps
+    x = np.array([[r0], [0.0], [0.0]])
+    for _ in range(nsteps):
+        x, _, _, _ = step(g, O.TSC, vel, rho, bf, x, dt)
+    return math.hypot(x[0, 0] - r0, x[1, 0])
+
+
+def test_lp_rk_orders_on_solid_rotation():
+    """The time order of both schemes against the closed form (a circle):
+    errors fall by 2^2 (Heun) and 2^3 (SSP-RK3) per halving of dt."""
+    for step, order in ((O.lp_rk2_step, 2.0), (O.lp_rk3_step, 3.0)):
+        e = [_rotation_error(step, k) for k in (50, 100, 200, 400)]
+        for a, b in zip(e, e[1:]):
+            assert abs(math.log2(a / b) - order) < 0.02, (order, e)
+
+
+def test_lp_rk3_uniform_velocity_exact():
+    n = 16
+    g = O.make_grid(3, (n, n, n))
+    G = n ** 3
+    vel = np.full((3, G), 0.2)
+    rng = np.random.default_rng(8)
+    x0 = rng.uniform(-1, 1, (3, 50))
+    x = x0.copy()
+    for _ in range(40):
+        x, _, _, _ = O.lp_rk3_step(g, O.TSC, vel, np.ones((1, G)), np.zeros((3, G)), x, 0.03)
+    assert np.max(np.abs(x - ((x0 + 0.2 * 40 * 0.03 + 1) % 2 - 1))) < 1e-13
+
+
+def test_lp_simple_advection_rk3_is_interpolation_limited():
+    """Sec. 4.1.1 with SSP-RK3: the velocity sampled from cell centres by TSC
+    carries an O(dx^2) error (the stencil's second moment), so at fixed CFL
+    the position error falls as n^-2 for both schemes, and RK3 and RK2 differ
+    by far less than either error (the time error is not what is left)."""
+    errs = {2: [], 3: []}
+    for n in (32, 64, 128):
+        g = O.make_grid(2, (n, n))
+        yc = -1 + (np.arange(n) + 0.5) * 2 / n
+        vy = np.repeat((2 + np.sin(np.pi * yc))[:, None], n, axis=1)
+        vel = np.stack([np.zeros_like(vy), vy, np.zeros_like(vy)]).reshape(3, -1)
+        rho, bf = np.ones((1, n * n)), np.zeros((3, n * n))
+        nsteps = int(round(10.0 / (0.3 * (2 / n) / 3)))
+        dt = 10.0 / nsteps
+        for order, step in ((2, O.lp_rk2_step), (3, O.lp_rk3_step)):
+            x = np.zeros((3, 1))
+            for _ in range(nsteps):
+                x, _, _, _ = step(g, O.TSC, vel, rho, bf, x, dt)
+            errs[order].append(abs((x[1, 0] - _e1_exact(10.0) + 1) % 2 - 1))
+    for k in (0, 1):
+        assert 1.9 < math.log2(errs[3][k] / errs[3][k + 1]) < 2.1
+    assert all(abs(a - b) < 0.05 * b for a, b in zip(errs[2], errs[3]))
+
+
 # --------------------------------------------------------------- spectra
 def _spec_inputs(nb=64, n=5, emin=1.0, emax=1e6, p=2.2, N0=1e-6):
     eng1, chi1 = O.init_spectrum(nb, emin, emax, p, N0)
