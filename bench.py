@@ -188,7 +188,7 @@ def time_steps(torch, stream, fn, K: int, W: int, per_step_events=False):
     return total_ms, kern_ms
 
 
-def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238):
+def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, order=2):
     dev = torch.device("cuda", torch.cuda.current_device())
     vel, rho, B = synth.fluid_snapshot(3, n, seed)
     f7 = torch.as_tensor(np.concatenate([vel, rho, B]).reshape(7, -1)).to(dev)
@@ -199,6 +199,7 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238):
     eng = torch.empty_like(chi)
     nold = torch.empty(nlp, dtype=torch.float64, device=dev)
     p.bind(nlp, x, chi=chi, eng=eng, n_old=nold)
+    p.set_lp_order(order)
     p.init_particles(seed, 0.0, 1.0, 1e6, 2.2, 1e-6)
     p.sort()                                   # once: locality of the field gathers
     p.sync()
@@ -222,8 +223,8 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238):
     ms = total / K
     spec_ms = float(np.mean(kern))
     del chi, eng
-    return {"workload": f"LP 3D {n}^3 snapshot, {nlp} LPs x {nb} bins, RK2 + TSC + spectra, "
-                        "FP64",
+    return {"workload": f"LP 3D {n}^3 snapshot, {nlp} LPs x {nb} bins, "
+                        f"{'RK2' if order == 2 else 'SSP-RK3'} + TSC + spectra, FP64",
             "value": nlp * K / (total / 1e3), "unit": "LP-steps/s", "ms_per_step": ms,
             "spec_update_ms": spec_ms,
             "spec_update_GBps": nlp * 2 * 2 * nb * 8 / (spec_ms / 1e3) / 1e9,
@@ -278,6 +279,63 @@ def run_compact(torch, P, n=128, ppc=8, fracs=(0.01, 0.1), K=10, seed=1240):
                              "frac": alg / (t / 1e3) / 1e9 / hbm})
     del keep, x, u, w, ids
     return out
+
+
+def run_lp_shock(torch, P, K: int, W: int, n=160, ppc=4, nb=128, seed=1241):
+    """The paper's shock configuration per GPU (Sec. 4.1.2 extended to 3D,
+    Sec. 5): a stationary planar shock at x = 0 (Rankine-Hugoniot, rho_u = 50,
+    v_u = 0.1, r = 40/11, B = (1, 0, 0)) on a 160^3 grid, 4 LPs per cell
+    (16.4M), each with 128 bins on [1e2, 1e4], p = 9; step = Heun RK2 + TSC
+    gather, smooth spectral update, shock detection and Eq.
+    convolution_spectra for the LPs entering the shock."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    r = 40.0 / 11.0
+    xc = -1.0 + (np.arange(n) + 0.5) * (2.0 / n)
+    down = np.broadcast_to(xc > 0.0, (n, n, n))
+    f7 = np.zeros((7, n, n, n))
+    f7[0] = np.where(down, 0.1 / r, 0.1)
+    f7[3] = np.where(down, 50.0 * r, 50.0)
+    f7[4] = 1.0
+    N = n ** 3 * ppc
+    p = P.Part(P.make_grid(3, n), P.FP64, P.TSC, P.LP_RK2, capacity=N, nbins=nb)
+    p.set_fields(torch.as_tensor(f7.reshape(7, -1)).to(dev))
+    del f7
+    x = torch.empty((3, N), dtype=torch.float64, device=dev)
+    chi = torch.empty((nb, N), dtype=torch.float64, device=dev)
+    eng = torch.empty_like(chi)
+    nold = torch.empty(N, dtype=torch.float64, device=dev)
+    st = torch.zeros(N, dtype=torch.uint8, device=dev)
+    p.bind(N, x, chi=chi, eng=eng, n_old=nold)
+    p.init_particles(seed, 0.0, 1e2, 1e4, 9.0, 1e-6)
+    p.sort()
+    p.enable_shocks(1.5, st)
+    p.sync()
+    dt = 0.5 * (2.0 / n) / 0.1
+
+    def step(ev):
+        p.gather_push(0.0, dt, 1)
+        if ev is not None:
+            ev[0].record(p.stream)
+        p.spec_update(dt, 1e-8, 0.0)
+        if ev is not None:
+            ev[1].record(p.stream)
+
+    l0 = p.launches()
+    total, kern = time_steps(torch, p.stream, step, K, W, per_step_events=True)
+    p.sync()
+    launches = (p.launches() - l0) // (K + W)
+    in_shock = int(st.sum().item())
+    ms = total / K
+    spec_ms = float(np.mean(kern))
+    del chi, eng
+    return {"workload": f"LP 3D stationary planar shock (Rankine-Hugoniot, r = 40/11) {n}^3, "
+                        f"{N} LPs x {nb} bins on [1e2, 1e4], p = 9, RK2 + TSC + spectra + "
+                        "shock detection + Eq. convolution_spectra, FP64",
+            "value": N * K / (total / 1e3), "unit": "LP-steps/s", "ms_per_step": ms,
+            "spec_update_and_shock_ms": spec_ms, "lps_in_shock_cells_at_end": in_shock,
+            "paper_context": "Particles_RK#1 + RK#2 + Spectra = 341 ms per step for 1.65e7 "
+                             "LPs on one A100 of a Leonardo node (paper's timing table)",
+            "dt": dt, "gpu_launches_per_step": launches}
 
 
 # Mixed form: per particle-step, state read 32 B (cell 4, offsets 12, u 12,
@@ -562,6 +620,8 @@ def only(args):
     build()
     if args.only == "mixed":
         res = run_mixed(torch, P, args.grid, 8, args.steps, args.warmup, 1237)
+    elif args.only == "shock":
+        res = run_lp_shock(torch, P, max(3, args.steps), 3, n=args.grid)
     elif args.only == "compact":
         res = run_compact(torch, P, n=args.grid, K=max(3, args.steps))
     elif args.only == "lp":
@@ -586,7 +646,8 @@ def main():
     ap.add_argument("--grid", type=int, default=128,
                     help="cells per axis of the headline workload (128 = the stated one; "
                          "smaller only for profiling captures)")
-    ap.add_argument("--only", choices=["mixed", "lp", "serving", "compact"], default=None,
+    ap.add_argument("--only", choices=["mixed", "lp", "serving", "compact", "shock"],
+                    default=None,
                     help="run one secondary workload alone at --grid cells per axis and print "
                          "its result (for profiling captures); no headline line")
     args = ap.parse_args()
@@ -676,6 +737,10 @@ def main():
         except Exception as e:  # report, do not hide
             line["lp"] = {"error": repr(e)}
         try:
+            line["lp_rk3"] = run_lp(torch, P, max(5, args.steps // 2), 3, order=3)
+        except Exception as e:
+            line["lp_rk3"] = {"error": repr(e)}
+        try:
             line["boris_2d"] = run_2d(torch, P)
         except Exception as e:
             line["boris_2d"] = {"error": repr(e)}
@@ -687,6 +752,10 @@ def main():
             line["mixed_error_vs_fp64"] = mixed_error_vs_fp64(torch, P)
         except Exception as e:
             line["mixed"] = {"error": repr(e)}
+        try:
+            line["lp_shock"] = run_lp_shock(torch, P, max(5, args.steps // 2), 3)
+        except Exception as e:
+            line["lp_shock"] = {"error": repr(e)}
         try:
             line["compact"] = run_compact(torch, P)
         except Exception as e:

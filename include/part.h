@@ -156,6 +156,16 @@ part_status part_enable_deposit(part_ctx* ctx, int on);
  * ignored in LP mode.                                                      */
 part_status part_gather_push(part_ctx* ctx, double q_over_m, double dt, int nsteps);
 
+/* Time marching of the LP push (PART_LP_RK2 contexts; default 2).
+ * order 2: Heun, as part_gather_push states.  order 3: the three-stage
+ * strong-stability-preserving Runge-Kutta scheme of Shu & Osher (the paper
+ * runs its advection test with 2nd- and 3rd-order RK, Sec. 4.1.1), in
+ * stage-velocity form: k1 = v(x), k2 = v(x + dt k1),
+ * k3 = v(x + dt (k1 + k2)/4), x' = x + dt (k1 + k2 + 4 k3)/6; each sampled
+ * position is wrapped, the samples at x' are as for order 2.
+ * Other orders or modes: PART_EINVAL.                                      */
+part_status part_set_lp_order(part_ctx* ctx, int order);
+
 /* Write the force density deposited by the last part_gather_push into
  * grid_out (device, double[3][G], overwritten):
  *   F_g = sum_p W(x_g - x_p^n) F_p.

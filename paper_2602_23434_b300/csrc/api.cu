@@ -383,6 +383,14 @@ part_status part_compact(part_ctx* c, const uint8_t* deleted, int64_t* n_new) {
   return PART_OK;
 }
 
+part_status part_set_lp_order(part_ctx* c, int order) {
+  if (check_ctx(c)) return PART_EINVAL;
+  if (c->mode != PART_LP_RK2) return fail(c, PART_EINVAL, "the RK order is an LP-mode setting");
+  if (order != 2 && order != 3) return fail(c, PART_EINVAL, "order must be 2 or 3");
+  c->lp_order = order;
+  return PART_OK;
+}
+
 part_status part_enable_shocks(part_ctx* c, double r_min, uint8_t* state) {
   if (check_ctx(c)) return PART_EINVAL;
   if (c->mode != PART_LP_RK2) return fail(c, PART_EINVAL, "shocks need LP mode");

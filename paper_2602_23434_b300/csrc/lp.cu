@@ -1,4 +1,4 @@
-// lp.cu -- Lagrangian-particle advection (Eq. push, Heun RK2) and the
+// lp.cu -- Lagrangian-particle advection (Eq. push, Heun RK2 or SSP-RK3) and the
 // per-bin spectral update of Eq. cr_chi (exact characteristics).
 //
 // Fields: padded FP64 copy with 7 components: v[3], rho, B[3] (the fluid
@@ -125,7 +125,10 @@ __device__ __forceinline__ void shock_mark(int64_t p, int64_t cell,
   }
 }
 
-template <int SHAPE, int DIM, bool SHOCK>
+// ORDER 2: Heun, x' = x + dt (k1 + k2)/2.  ORDER 3: three-stage SSP
+// Runge-Kutta (Shu & Osher) in stage-velocity form, k3 = v(x + dt (k1+k2)/4),
+// x' = x + dt (k1 + k2 + 4 k3)/6; the wrap only enters the sampled positions.
+template <int SHAPE, int DIM, bool SHOCK, int ORDER>
 __global__ void __launch_bounds__(256)
     k_lp_rk2(const double* __restrict__ fp, const Geo g, double* __restrict__ x, int64_t n,
              double dt, double* __restrict__ samples, int* __restrict__ status,
@@ -143,9 +146,24 @@ __global__ void __launch_bounds__(256)
     for (int a = 0; a < DIM; ++a) xs[a] = wrap_axis(x0[a] + dt * v1[a], g.xmin[a], g.xmax[a], g.L[a]);
     Stencil<SHAPE, DIM> ss(g, xs);
     ss.template gather<3>(fp, g, 0, v2);
+    bool fin = s0.finite && ss.finite;
+    if (ORDER == 2) {
 #pragma unroll
-    for (int a = 0; a < DIM; ++a)
-      x1[a] = wrap_axis(x0[a] + dt * (0.5 * (v1[a] + v2[a])), g.xmin[a], g.xmax[a], g.L[a]);
+      for (int a = 0; a < DIM; ++a)
+        x1[a] = wrap_axis(x0[a] + dt * (0.5 * (v1[a] + v2[a])), g.xmin[a], g.xmax[a], g.L[a]);
+    } else {
+      double xb[3] = {x0[0], x0[1], x0[2]}, k3[3];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a)
+        xb[a] = wrap_axis(x0[a] + dt * (0.25 * (v1[a] + v2[a])), g.xmin[a], g.xmax[a], g.L[a]);
+      Stencil<SHAPE, DIM> sb(g, xb);
+      sb.template gather<3>(fp, g, 0, k3);
+      fin = fin && sb.finite;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a)
+        x1[a] = wrap_axis(x0[a] + dt * ((v1[a] + v2[a] + 4.0 * k3[a]) / 6.0), g.xmin[a],
+                          g.xmax[a], g.L[a]);
+    }
     Stencil<SHAPE, DIM> s1(g, x1);
     {
       double o[7];  // v, rho, B at the new position in one stencil pass
@@ -167,7 +185,7 @@ __global__ void __launch_bounds__(256)
     samples[p] = r;
     samples[n + p] = 0.5 * (bb0 + bb1);
     samples[2 * n + p] = gam;
-    if (!(s0.finite && ss.finite && s1.finite && isfinite(gam) && isfinite(r) && r > 0.0))
+    if (!(fin && s1.finite && isfinite(gam) && isfinite(r) && r > 0.0))
       atomicOr(status, ST_NONFINITE);
     if (SHOCK) shock_mark(p, s1.cell, shock_r, shk, list, rs);
   }
@@ -244,22 +262,28 @@ int grid_for(int64_t n, int threads) {
   return (int)b;
 }
 
-template <int SHAPE, int DIM>
-cudaError_t lp_launch(part_ctx* c, double dt) {
+template <int SHAPE, int DIM, int ORDER>
+cudaError_t lp_launch_order(part_ctx* c, double dt) {
   const int gb = grid_for(c->n, 256);
   if (c->shk) {
     cudaError_t e = cudaMemsetAsync(c->shock_list, 0, sizeof(uint32_t), c->stream);
     if (e != cudaSuccess) return e;
-    k_lp_rk2<SHAPE, DIM, true><<<gb, 256, 0, c->stream>>>(
+    k_lp_rk2<SHAPE, DIM, true, ORDER><<<gb, 256, 0, c->stream>>>(
         (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status,
         c->shock_r, c->shk, c->shock_list, c->shock_rs);
   } else {
-    k_lp_rk2<SHAPE, DIM, false><<<gb, 256, 0, c->stream>>>(
+    k_lp_rk2<SHAPE, DIM, false, ORDER><<<gb, 256, 0, c->stream>>>(
         (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status,
         nullptr, nullptr, nullptr, nullptr);
   }
   c->launches++;
   return cudaGetLastError();
+}
+
+template <int SHAPE, int DIM>
+cudaError_t lp_launch(part_ctx* c, double dt) {
+  return c->lp_order == 3 ? lp_launch_order<SHAPE, DIM, 3>(c, dt)
+                          : lp_launch_order<SHAPE, DIM, 2>(c, dt);
 }
 
 // Shock cells from the padded fields (periodic ghost layer of one cell):

@@ -102,6 +102,7 @@ struct part_ctx {
   double* shock_rs{};      // [k]: compression ratio each listed LP saw
   uint8_t* shk{};          // caller's per-LP "in a shock cell" flags; NULL: shocks off
   double r_min{};
+  int lp_order{2};         // LP time marching: 2 (Heun) or 3 (SSP-RK3)
   bool shock_listed{};     // the last push filled the list
   bool bound{}, fields_set{}, sorted{}, deposit_on{}, deposit_ready{}, samples_ready{};
   int64_t launches{};
