@@ -1,6 +1,7 @@
 // push_boris.cu -- gather + relativistic Boris push (+ fused force deposit).
 //
-// Brick kernel (sorted particles, one CTA per 8x8x8 / 16x16 cell brick):
+// Brick kernel (sorted particles, one CTA per 8x8x8 / 16x16 cell brick;
+// with the deposit, warp-specialised: 8 push warps, 8 deposit warps):
 //   1. one thread issues a 4-D TMA copy of the brick's haloed field box
 //      (all components) into shared memory; cell_start of the brick is read;
 //   2. the CTA walks the brick's particles in chunks of blockDim: TSC/CIC
@@ -37,15 +38,16 @@ __host__ __device__ constexpr int kslots(int dim) { return dim == 3 ? 3 : 6; }
 struct BrickSmem {
   size_t box, cs, bar, rec, win, total;
 };
-__host__ __device__ inline BrickSmem brick_smem(const Geo& g, int ncomp, int esize) {
+// dep: two record buffers [2][18][kRS] and the deposit windows follow the box
+__host__ __device__ inline BrickSmem brick_smem(const Geo& g, int ncomp, int esize, bool dep) {
   BrickSmem s;
   s.box = 0;
   size_t bbytes = (size_t)ncomp * g.box[0] * g.box[1] * g.box[2] * esize;
   s.cs = align_up(bbytes, 128);
   s.bar = align_up(s.cs + (size_t)(g.V + 1) * 4, 16);
   s.rec = align_up(s.bar + 16, 128);
-  s.win = align_up(s.rec + (size_t)18 * kRS * 8, 128);
-  s.total = s.win + (size_t)kWarps * kslots(g.dim) * g.e[1] * g.e[2] * 3 * 8;
+  s.win = align_up(s.rec + (dep ? (size_t)2 * 18 * kRS * 8 : 0), 128);
+  s.total = s.win + (dep ? (size_t)kWarps * kslots(g.dim) * g.e[1] * g.e[2] * 3 * 8 : 0);
   return s;
 }
 
@@ -76,35 +78,186 @@ __device__ __forceinline__ void boris_f64(double* u, const double* E, const doub
 }
 
 // ---------------------------------------------------------------- brick kernel, FP64
+// One particle of a chunk: weights, gather from the staged box, Boris, drift,
+// wrap, store; with DEP, its deposit record (9 z-y weight products and the 9
+// x-weighted force terms) is returned in wyz / fxc (zero if it has none).
 template <int SHAPE, int DIM, bool DEP>
-__global__ void __launch_bounds__(kT, 1)
-    k_boris_brick_f64(const __grid_constant__ CUtensorMap tmap, const Geo g,
-                      const double* xs, const double* us, const double* ws,
-                      const uint64_t* ids, double* x, double* u, double* wd, uint64_t* idd,
-                      int64_t n,
-                      const uint32_t* __restrict__ cstart, double* __restrict__ dpart,
-                      double qm, double dt, double inv_dt, int* __restrict__ status) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const BrickSmem L = brick_smem(g, 6, 8);
+__device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int bvol,
+                                         const uint32_t* scs, const int* org, uint32_t p,
+                                         const double* xs, const double* us,
+                                         const double* ws, const uint64_t* ids, double* x,
+                                         double* u, double* wd, uint64_t* idd, int64_t n,
+                                         double h, double dt, double inv_dt, int* status,
+                                         double* wyz, double* fxc) {
+  double xp[3], up[3], uo[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    xp[a] = xs[a * n + p];
+    up[a] = us[a * n + p];
+    uo[a] = up[a];
+  }
+  const double wp = ws ? ws[p] : 1.0;
+  if (ws && wd != ws) wd[p] = wp;             // carry the read-only planes over
+  if (ids && idd != ids) idd[p] = ids[p];
+  int l[3] = {0, 0, 0};
+  double d[3] = {0.0, 0.0, 0.0};
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    double sa = __dmul_rn(__dsub_rn(xp[a], g.xmin[a]), g.inv_dx[a]);
+    int j = floor_clamp_bits(sa, g.n[a] - 1);
+    d[a] = __dsub_rn(__dsub_rn(sa, (double)j), 0.5);
+    l[a] = j - org[a];
+    ok = ok && l[a] >= 0 && l[a] < g.b[a] && finite_bits(sa);
+  }
+  if (ok) {  // the particle must sit in the cell it was sorted into
+    const int lc = (l[2] * g.b[1] + l[1]) * g.b[0] + l[0];
+    ok = p >= scs[lc] && p < scs[lc + 1];
+  }
+  if (!ok) {
+    atomicOr(status, ST_DOMAIN);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {  // left as it was
+      x[a * n + p] = xp[a];
+      u[a * n + p] = up[a];
+    }
+    return;
+  }
+  double wx[3], wy[3], wz[3] = {0.0, 1.0, 0.0};
+  shape_weights<SHAPE>(d[0], wx);
+  shape_weights<SHAPE>(d[1], wy);
+  if (DIM == 3) shape_weights<SHAPE>(d[2], wz);
+  double f[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
+    const int zz = DIM == 3 ? l[2] + kz : 0;
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) {
+      const double wzy = wz[kz] * wy[ky];
+      if (DEP) wyz[kz * 3 + ky] = wzy;
+      const int row = (zz * g.box[1] + l[1] + ky) * g.box[0] + l[0];
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const double ww = wzy * wx[kx];
+        const double* sp = sbox + row + kx;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) f[c] += ww * sp[c * bvol];
+      }
+    }
+  }
+  boris_f64(up, f, f + 3, h);
+  const double gi = rsqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+#pragma unroll
+  for (int a = 0; a < DIM; ++a)
+    xp[a] = wrap_axis(xp[a] + dt * (up[a] * gi), g.xmin[a], g.xmax[a], g.L[a]);
+  bool fin = finite_bits(up[0]) && finite_bits(up[1]) && finite_bits(up[2]) &&
+             finite_bits(xp[0]) && finite_bits(xp[1]) && finite_bits(xp[2]);
+  if (!fin) atomicOr(status, ST_NONFINITE);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    x[a * n + p] = xp[a];
+    u[a * n + p] = up[a];
+  }
+  if (DEP) {
+    const double wdt = wp * inv_dt;
+    double F[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) F[a] = (up[a] - uo[a]) * wdt;
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) fxc[kx * 3 + c] = wx[kx] * F[c];
+  }
+}
+
+// Deposit of one chunk [base, bend) by deposit warp `warp` (0..7): the cells
+// s with s mod 8 == warp, one lane per stencil offset; every lane loops over
+// the same particles, so the loop does not diverge.  Adds into the warp's
+// private window in a fixed order.  cfirst: first cell with particles at or
+// after base (carried across chunks).
+template <int DIM>
+__device__ __forceinline__ void deposit_chunk(const Geo& g, const uint32_t* scs,
+                                              const double* rw, const double* rf, double* win,
+                                              int wsize, int warp, int lane, uint32_t base,
+                                              uint32_t bend, int& cfirst) {
+  while (scs[cfirst + 1] <= base) ++cfirst;
+  int clast = cfirst;
+  while (clast + 1 < g.V && scs[clast + 1] < bend) ++clast;
+  const int s0 = cfirst + ((warp - cfirst % 8) + 8) % 8;
+  for (int sc = s0; sc <= clast; sc += 8) {
+    uint32_t r0 = scs[sc], r1 = scs[sc + 1];
+    r0 = r0 > base ? r0 : base;
+    r1 = r1 < bend ? r1 : bend;
+    const int nk = DIM == 3 ? 27 : 9;
+    if (lane < nk && r0 < r1) {
+      const int kz = DIM == 3 ? lane / 9 : 1;
+      const int ky = DIM == 3 ? (lane / 3) % 3 : lane / 3;
+      const int kx = lane % 3;
+      const double* pw = rw + (kz * 3 + ky) * kRS;
+      const double* pf = rf + (kx * 3) * kRS;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+      for (uint32_t r = r0; r < r1; ++r) {
+        const int i = (int)(r - base);
+        const double ww = pw[i];
+        a0 += ww * pf[i];
+        a1 += ww * pf[kRS + i];
+        a2 += ww * pf[2 * kRS + i];
+      }
+      const int lx = sc % g.b[0], ly = (sc / g.b[0]) % g.b[1], lz = sc / (g.b[0] * g.b[1]);
+      const int ex = lx + kx, ey = ly + ky, ez = DIM == 3 ? lz + kz : 0;
+      const int col = ex - warp < 3 ? ex - warp : ex - warp - 5;   // slot in the window
+      double* wp = win + warp * wsize + ((col * g.e[2] + ez) * g.e[1] + ey) * 3;
+      wp[0] += a0;
+      wp[1] += a1;
+      wp[2] += a2;
+    }
+    __syncwarp();
+  }
+}
+
+// Combine the deposit windows in warp order into the brick's haloed tile.
+template <int DIM>
+__device__ __forceinline__ void combine_windows(const Geo& g, const double* win, int wsize,
+                                                int64_t brick, double* dpart, int t0,
+                                                int stride) {
+  for (int t = t0; t < g.ev; t += stride) {
+    const int ex = t % g.e[0], ey = (t / g.e[0]) % g.e[1], ez = t / (g.e[0] * g.e[1]);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int w = 0; w < kWarps; ++w) {
+      int col = ex - w;
+      if (col < 0) continue;
+      if (col >= 3) {
+        if (DIM == 3 || col < 8 || col >= 11) continue;
+        col -= 5;
+      }
+      const double* wp = win + w * wsize + ((col * g.e[2] + ez) * g.e[1] + ey) * 3;
+      s0 += wp[0];
+      s1 += wp[1];
+      s2 += wp[2];
+    }
+    dpart[(brick * 3 + 0) * g.ev + t] = s0;
+    dpart[(brick * 3 + 1) * g.ev + t] = s1;
+    dpart[(brick * 3 + 2) * g.ev + t] = s2;
+  }
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id, int nthreads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Common prologue: TMA of the haloed box on an mbarrier (bounded wait),
+// cell_start of the brick, zeroed windows.  Returns false (after reporting
+// ST_TIMEOUT) if the copy did not land.
+template <int NT>
+__device__ __forceinline__ bool brick_prologue(const CUtensorMap* tmap, const Geo& g,
+                                               double* sbox, int bvol, uint32_t* scs,
+                                               uint64_t* bar, int* sflag, double* win,
+                                               int nwin, const uint32_t* cstart,
+                                               int64_t brick, const int* org, int* status) {
   const int tid = threadIdx.x;
-  const int bvol = g.box[0] * g.box[1] * g.box[2];
-  double* sbox = reinterpret_cast<double*>(smem);
-  uint32_t* scs = reinterpret_cast<uint32_t*>(smem + L.cs);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
-  int* sflag = reinterpret_cast<int*>(smem + L.bar + 8);
-  double* rw = reinterpret_cast<double*>(smem + L.rec);  // [9][kRS] wz*wy
-  double* rf = rw + 9 * kRS;                             // [9][kRS] wx[k]*F[c]
-  double* win = reinterpret_cast<double*>(smem + L.win); // [warp][slot][e2][e1][3]
-  constexpr int NS = kslots(DIM);
-  const int wsize = NS * g.e[1] * g.e[2] * 3;
-  const int warp = tid >> 5, lane = tid & 31;
-
-  const int64_t brick = blockIdx.x;
-  const int bx = (int)(brick % g.nb[0]);
-  const int by = (int)((brick / g.nb[0]) % g.nb[1]);
-  const int bz = (int)(brick / ((int64_t)g.nb[0] * g.nb[1]));
-  const int o0 = bx * g.b[0], o1 = by * g.b[1], o2 = bz * g.b[2];
-
   if (tid == 0) {
     mbar_init(bar, 1);
     *sflag = 0;
@@ -114,11 +267,10 @@ __global__ void __launch_bounds__(kT, 1)
     mbar_arrive_expect_tx(bar, (uint32_t)(6 * bvol * 8));
     // padded index of cell c is c + h, so the box starting one cell below the
     // brick origin starts at padded coordinate o
-    tma_load_4d(sbox, &tmap, bar, o0, o1, o2, 0);
+    tma_load_4d(sbox, tmap, bar, org[0], org[1], org[2], 0);
   }
-  for (int i = tid; i <= g.V; i += kT) scs[i] = cstart[brick * g.V + i];
-  if (DEP)
-    for (int i = tid; i < kWarps * wsize; i += kT) win[i] = 0.0;
+  for (int i = tid; i <= g.V; i += NT) scs[i] = cstart[brick * g.V + i];
+  for (int i = tid; i < nwin; i += NT) win[i] = 0.0;
   if (!mbar_wait_bounded(bar, 0)) atomicOr(sflag, 1);
   __syncthreads();
   if (*sflag) {
@@ -126,168 +278,117 @@ __global__ void __launch_bounds__(kT, 1)
       atomicOr(status, ST_TIMEOUT);
       mbar_wait_bounded(bar, 0);
     }
-    return;
+    return false;
   }
+  return true;
+}
 
+// Without deposit: 256 threads walk the brick's particles in chunks.
+template <int SHAPE, int DIM>
+__global__ void __launch_bounds__(kT, 1)
+    k_boris_brick_f64(const __grid_constant__ CUtensorMap tmap, const Geo g,
+                      const double* xs, const double* us, const double* ws,
+                      const uint64_t* ids, double* x, double* u, double* wd, uint64_t* idd,
+                      int64_t n,
+                      const uint32_t* __restrict__ cstart, double* __restrict__ dpart,
+                      double qm, double dt, double inv_dt, int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const BrickSmem L = brick_smem(g, 6, 8, false);
+  const int tid = threadIdx.x;
+  const int bvol = g.box[0] * g.box[1] * g.box[2];
+  double* sbox = reinterpret_cast<double*>(smem);
+  uint32_t* scs = reinterpret_cast<uint32_t*>(smem + L.cs);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+  int* sflag = reinterpret_cast<int*>(smem + L.bar + 8);
+  const int64_t brick = blockIdx.x;
+  const int org[3] = {(int)(brick % g.nb[0]) * g.b[0],
+                      (int)((brick / g.nb[0]) % g.nb[1]) * g.b[1],
+                      (int)(brick / ((int64_t)g.nb[0] * g.nb[1])) * g.b[2]};
+  if (!brick_prologue<kT>(&tmap, g, sbox, bvol, scs, bar, sflag, nullptr, 0, cstart, brick,
+                          org, status))
+    return;
   const double h = 0.5 * qm * dt;
   const uint32_t p0 = scs[0], p1 = scs[g.V];
-  const int org[3] = {o0, o1, o2};
-  int cfirst = 0;  // first brick cell with particles at or after `base`
-  for (uint32_t base = p0; base < p1; base += kT) {
-    const uint32_t p = base + tid;
-    double wyz[9], fxc[9];
+  for (uint32_t p = p0 + tid; p < p1; p += kT)
+    push_one<SHAPE, DIM, false>(g, sbox, bvol, scs, org, p, xs, us, ws, ids, x, u, wd, idd, n,
+                                h, dt, inv_dt, status, nullptr, nullptr);
+}
+
+// With deposit: warp-specialised, 512 threads.  Warps 0-7 push chunk k of 256
+// particles and leave its records in buffer k & 1; warps 8-15 deposit chunk
+// k - 1 from the other buffer at the same time.  The hand-off uses named
+// barriers (FULL_b: records of buffer b written; EMPTY_b: buffer b read), so
+// both phases keep the FP64 pipe busy and neither waits for the other's
+// latency.  Both groups derive the same chunk count from cell_start.
+template <int SHAPE, int DIM>
+__global__ void __launch_bounds__(2 * kT, 1)
+    k_boris_brick_f64_dep(const __grid_constant__ CUtensorMap tmap, const Geo g,
+                          const double* xs, const double* us, const double* ws,
+                          const uint64_t* ids, double* x, double* u, double* wd,
+                          uint64_t* idd, int64_t n, const uint32_t* __restrict__ cstart,
+                          double* __restrict__ dpart, double qm, double dt, double inv_dt,
+                          int* __restrict__ status) {
+  constexpr int NT = 2 * kT;
+  constexpr int kFull = 1, kEmpty = 3;  // named barrier ids (0 is __syncthreads)
+  extern __shared__ __align__(128) unsigned char smem[];
+  const BrickSmem L = brick_smem(g, 6, 8, true);
+  const int tid = threadIdx.x;
+  const int bvol = g.box[0] * g.box[1] * g.box[2];
+  double* sbox = reinterpret_cast<double*>(smem);
+  uint32_t* scs = reinterpret_cast<uint32_t*>(smem + L.cs);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+  int* sflag = reinterpret_cast<int*>(smem + L.bar + 8);
+  double* rec = reinterpret_cast<double*>(smem + L.rec);  // [2][18][kRS]
+  double* win = reinterpret_cast<double*>(smem + L.win);  // [warp][slot][e2][e1][3]
+  constexpr int NS = kslots(DIM);
+  const int wsize = NS * g.e[1] * g.e[2] * 3;
+  const int64_t brick = blockIdx.x;
+  const int org[3] = {(int)(brick % g.nb[0]) * g.b[0],
+                      (int)((brick / g.nb[0]) % g.nb[1]) * g.b[1],
+                      (int)(brick / ((int64_t)g.nb[0] * g.nb[1])) * g.b[2]};
+  if (!brick_prologue<NT>(&tmap, g, sbox, bvol, scs, bar, sflag, win, kWarps * wsize, cstart,
+                          brick, org, status))
+    return;
+  const uint32_t p0 = scs[0], p1 = scs[g.V];
+  const int nchunks = (int)((p1 - p0 + kT - 1) / kT);
+  if (tid < kT) {  // producer warps: push
+    const double h = 0.5 * qm * dt;
+    for (int k = 0; k < nchunks; ++k) {
+      const int b = k & 1;
+      const uint32_t p = p0 + (uint32_t)k * kT + tid;
+      double wyz[9], fxc[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) wyz[k] = fxc[k] = 0.0;
-    if (p < p1) {
-      double xp[3], up[3], uo[3];
+      for (int q = 0; q < 9; ++q) wyz[q] = fxc[q] = 0.0;
+      if (p < p1)
+        push_one<SHAPE, DIM, true>(g, sbox, bvol, scs, org, p, xs, us, ws, ids, x, u, wd, idd,
+                                   n, h, dt, inv_dt, status, wyz, fxc);
+      if (k >= 2) named_bar_sync(kEmpty + b, NT);  // deposit of chunk k-2 has read it
+      double* rw = rec + (size_t)b * 18 * kRS;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        xp[a] = xs[a * n + p];
-        up[a] = us[a * n + p];
-        uo[a] = up[a];
+      for (int q = 0; q < 9; ++q) {
+        rw[q * kRS + tid] = wyz[q];
+        rw[(9 + q) * kRS + tid] = fxc[q];
       }
-      const double wp = ws ? ws[p] : 1.0;
-      if (ws && wd != ws) wd[p] = wp;             // carry the read-only planes over
-      if (ids && idd != ids) idd[p] = ids[p];
-      int l[3] = {0, 0, 0};
-      double d[3] = {0.0, 0.0, 0.0};
-      bool ok = true;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        double s = __dmul_rn(__dsub_rn(xp[a], g.xmin[a]), g.inv_dx[a]);
-        int j = floor_clamp_bits(s, g.n[a] - 1);
-        d[a] = __dsub_rn(__dsub_rn(s, (double)j), 0.5);
-        l[a] = j - org[a];
-        ok = ok && l[a] >= 0 && l[a] < g.b[a] && finite_bits(s);
-      }
-      if (ok) {  // the particle must sit in the cell it was sorted into
-        const int lc = (l[2] * g.b[1] + l[1]) * g.b[0] + l[0];
-        ok = p >= scs[lc] && p < scs[lc + 1];
-      }
-      if (!ok) {
-        atomicOr(status, ST_DOMAIN);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {  // left as it was
-          x[a * n + p] = xp[a];
-          u[a * n + p] = up[a];
-        }
-      } else {
-        double wx[3], wy[3], wz[3] = {0.0, 1.0, 0.0};
-        shape_weights<SHAPE>(d[0], wx);
-        shape_weights<SHAPE>(d[1], wy);
-        if (DIM == 3) shape_weights<SHAPE>(d[2], wz);
-        double f[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-        for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
-          const int zz = DIM == 3 ? l[2] + kz : 0;
-#pragma unroll
-          for (int ky = 0; ky < 3; ++ky) {
-            const double wzy = wz[kz] * wy[ky];
-            wyz[kz * 3 + ky] = wzy;
-            const int row = (zz * g.box[1] + l[1] + ky) * g.box[0] + l[0];
-#pragma unroll
-            for (int kx = 0; kx < 3; ++kx) {
-              const double ww = wzy * wx[kx];
-              const double* sp = sbox + row + kx;
-#pragma unroll
-              for (int c = 0; c < 6; ++c) f[c] += ww * sp[c * bvol];
-            }
-          }
-        }
-        boris_f64(up, f, f + 3, h);
-        const double gi = rsqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
-#pragma unroll
-        for (int a = 0; a < DIM; ++a)
-          xp[a] = wrap_axis(xp[a] + dt * (up[a] * gi), g.xmin[a], g.xmax[a], g.L[a]);
-        bool fin = finite_bits(up[0]) && finite_bits(up[1]) && finite_bits(up[2]) &&
-                   finite_bits(xp[0]) && finite_bits(xp[1]) && finite_bits(xp[2]);
-        if (!fin) atomicOr(status, ST_NONFINITE);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          x[a * n + p] = xp[a];
-          u[a * n + p] = up[a];
-        }
-        if (DEP) {
-          const double wdt = wp * inv_dt;
-          double F[3];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) F[a] = (up[a] - uo[a]) * wdt;
-#pragma unroll
-          for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) fxc[kx * 3 + c] = wx[kx] * F[c];
-        }
-      }
+      named_bar_arrive(kFull + b, NT);
     }
-    if (DEP) {
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        rw[k * kRS + tid] = wyz[k];
-        rf[k * kRS + tid] = fxc[k];
-      }
-      __syncthreads();
-      // cells whose particles meet this chunk: [cfirst, clast]
+    // complete the EMPTY instances of the last two chunks
+    for (int k = nchunks > 2 ? nchunks - 2 : 0; k < nchunks; ++k)
+      named_bar_sync(kEmpty + (k & 1), NT);
+  } else {  // consumer warps: deposit
+    const int dw = (tid - kT) >> 5, lane = tid & 31;
+    int cfirst = 0;
+    for (int k = 0; k < nchunks; ++k) {
+      const int b = k & 1;
+      named_bar_sync(kFull + b, NT);
+      const uint32_t base = p0 + (uint32_t)k * kT;
       const uint32_t bend = base + kT < p1 ? base + kT : p1;
-      while (scs[cfirst + 1] <= base) ++cfirst;
-      int clast = cfirst;
-      while (clast + 1 < g.V && scs[clast + 1] < bend) ++clast;
-      // warp w: cells s with s mod 8 == w, one lane per stencil offset; every
-      // lane loops over the same particles, so the loop does not diverge
-      const int s0 = cfirst + ((warp - cfirst % 8) + 8) % 8;
-      for (int sc = s0; sc <= clast; sc += 8) {
-        uint32_t r0 = scs[sc], r1 = scs[sc + 1];
-        r0 = r0 > base ? r0 : base;
-        r1 = r1 < bend ? r1 : bend;
-        const int nk = DIM == 3 ? 27 : 9;
-        if (lane < nk && r0 < r1) {
-          const int kz = DIM == 3 ? lane / 9 : 1;
-          const int ky = DIM == 3 ? (lane / 3) % 3 : lane / 3;
-          const int kx = lane % 3;
-          const double* pw = rw + (kz * 3 + ky) * kRS;
-          const double* pf = rf + (kx * 3) * kRS;
-          double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-          for (uint32_t r = r0; r < r1; ++r) {
-            const int i = (int)(r - base);
-            const double ww = pw[i];
-            a0 += ww * pf[i];
-            a1 += ww * pf[kRS + i];
-            a2 += ww * pf[2 * kRS + i];
-          }
-          const int lx = sc % g.b[0], ly = (sc / g.b[0]) % g.b[1], lz = sc / (g.b[0] * g.b[1]);
-          const int ex = lx + kx, ey = ly + ky, ez = DIM == 3 ? lz + kz : 0;
-          const int col = ex - warp < 3 ? ex - warp : ex - warp - 5;   // slot in the window
-          double* wp = win + warp * wsize + ((col * g.e[2] + ez) * g.e[1] + ey) * 3;
-          wp[0] += a0;
-          wp[1] += a1;
-          wp[2] += a2;
-        }
-        __syncwarp();
-      }
-      __syncthreads();
+      const double* rw = rec + (size_t)b * 18 * kRS;
+      deposit_chunk<DIM>(g, scs, rw, rw + 9 * kRS, win, wsize, dw, lane, base, bend, cfirst);
+      named_bar_arrive(kEmpty + b, NT);
     }
   }
-  if (DEP) {
-    // combine the warp windows in warp order into the brick's haloed tile
-    for (int t = tid; t < g.ev; t += kT) {
-      const int ex = t % g.e[0], ey = (t / g.e[0]) % g.e[1], ez = t / (g.e[0] * g.e[1]);
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-      for (int w = 0; w < kWarps; ++w) {
-        int col = ex - w;
-        if (col < 0) continue;
-        if (col >= 3) {
-          if (DIM == 3 || col < 8 || col >= 11) continue;
-          col -= 5;
-        }
-        const double* wp = win + w * wsize + ((col * g.e[2] + ez) * g.e[1] + ey) * 3;
-        s0 += wp[0];
-        s1 += wp[1];
-        s2 += wp[2];
-      }
-      dpart[(brick * 3 + 0) * g.ev + t] = s0;
-      dpart[(brick * 3 + 1) * g.ev + t] = s1;
-      dpart[(brick * 3 + 2) * g.ev + t] = s2;
-    }
-  }
+  __syncthreads();
+  combine_windows<DIM>(g, win, wsize, brick, dpart, tid, NT);
 }
 
 // ---------------------------------------------------------------- particle order, FP64
@@ -419,13 +520,13 @@ int grid_for(int64_t n, int threads) {
 
 template <int SHAPE, int DIM, bool DEP>
 cudaError_t brick_f64(part_ctx* c, double qm, double dt) {
-  auto kern = k_boris_brick_f64<SHAPE, DIM, DEP>;
-  const BrickSmem L = brick_smem(c->geo, 6, 8);
+  auto kern = DEP ? k_boris_brick_f64_dep<SHAPE, DIM> : k_boris_brick_f64<SHAPE, DIM>;
+  const BrickSmem L = brick_smem(c->geo, 6, 8, DEP);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L.total);
   if (e != cudaSuccess) return e;
   const bool alt = c->pending;  // sorted state waits in the alternate buffers
-  kern<<<(unsigned)c->geo.nbricks, kT, L.total, c->stream>>>(
+  kern<<<(unsigned)c->geo.nbricks, DEP ? 2 * kT : kT, L.total, c->stream>>>(
       c->tmap, c->geo, (const double*)(alt ? c->alt_x : c->x),
       (const double*)(alt ? c->alt_u : c->u),
       (const double*)(c->w ? (alt ? c->alt_w : c->w) : nullptr),
