@@ -50,8 +50,8 @@ FLOP_PER_PSTEP_BORIS_DEP = 12 + 24 + 360 + 58 + 17 + 178
 BYTES_PER_PSTEP_BORIS_DEP = 96 + 8 + 6 + 3
 # DRAM bytes (read + write) per particle of one launch of the FP64 brick kernel,
 # from the ncu capture in profiles/ncu_boris_brick_fp64_64cube.md (64^3 case,
-# 252.7 MB for 2,097,152 particles), scaled to a launch by the particle count.
-TRAFFIC_PER_PARTICLE_BRICK_F64 = 252.713728e6 / 2097152
+# 252.0 MB for 2,097,152 particles), scaled to a launch by the particle count.
+TRAFFIC_PER_PARTICLE_BRICK_F64 = 252.039424e6 / 2097152   # ncu dram r+w, 64^3 capture
 # Same for the mixed brick kernel, profiles/ncu_boris_brick_mixed_128cube.md
 # (128^3 case, 1206.8 MB for 16,777,216 particles).
 TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1206.793984e6 / 16777216
@@ -711,7 +711,7 @@ def main():
                    "l2": "inputs larger than L2 (about 2 GB of state, fields and deposit "
                          "touched per step vs 126 MB L2); no flush",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "kernel": "k_boris_brick_f64 (TSC, 3D, deposit)",
+        "roofline": {"bound": "alu", "kernel": "k_boris_brick_f64_dep (TSC, 3D, warp-specialised push + deposit)",
                      "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tf / FP64_NOMINAL_TFLOPS,
                      "traffic": TRAFFIC_PER_PARTICLE_BRICK_F64 * wl.N,
