@@ -193,10 +193,14 @@ __global__ void __launch_bounds__(256)
 
 // Per LP: dtau = dt/gamma_g; ln A = ln(n_old/n_new)/3; c_r = c0 (|B|^2/2 +
 // u_rad); C = c_r dtau expm1(ln A)/ln A.  Per bin: s = A + C eps;
-// eps <- eps/s; chi <- chi s^2/A.  Bins are unrolled 8 at a time so that
-// eight independent row loads are in flight per thread, and the 8 divisions
-// share one (FP64 division is ~6x an FMA on this part).
-__global__ void __launch_bounds__(256)
+// eps <- eps/s; chi <- chi s^2/A.  Evaluated with t = s/sqrt(A) =
+// sqrt(A) + (C/sqrt(A)) eps, so chi s^2/A = chi t t and eps/s = eps (1/sqrt(A))/t:
+// one FMA, two multiplies for chi and one for eps per bin.  Bins are taken 8
+// at a time so that eight independent row loads are in flight per thread, and
+// the eight 1/t come from one division (Montgomery's simultaneous inversion:
+// prefix products, one reciprocal scaled by 1/sqrt(A), unwind); FP64 division
+// costs several FMAs on this part.
+__global__ void __launch_bounds__(256, 2)
     k_spec_update(double* __restrict__ chi, double* __restrict__ eng, double* __restrict__ n_old,
                   const double* __restrict__ samples, int64_t n, int nb, double dt, double c0,
                   double u_rad, int* __restrict__ status) {
@@ -205,51 +209,50 @@ __global__ void __launch_bounds__(256)
     const double nn = samples[p], b2 = samples[n + p], gam = samples[2 * n + p];
     const double dtau = dt / gam;
     const double L = log(n_old[p] / nn) / 3.0;
-    const double A = exp(L);
-    const double invA = exp(-L);
+    const double rA = exp(-0.5 * L);       // 1/sqrt(A)
+    const double sA = exp(0.5 * L);        // sqrt(A)
     const double cr = c0 * (0.5 * b2 + u_rad);
     const double C = cr * dtau * (L == 0.0 ? 1.0 : expm1(L) / L);
-    if (!(isfinite(A) && isfinite(C))) atomicOr(status, ST_NONFINITE);
+    const double Cs = C * rA;              // C / sqrt(A)
+    if (!(isfinite(sA) && isfinite(Cs))) atomicOr(status, ST_NONFINITE);
     double* ep = eng + p;
     double* cp = chi + p;
     int i = 0;
     for (; i + 8 <= nb; i += 8) {
-      double e[8], c[8], sv[8], pre[8], r[8];
+      double e[8], c[8], tv[8], pre[8], r[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         e[k] = ep[(int64_t)(i + k) * n];
         c[k] = cp[(int64_t)(i + k) * n];
       }
-      // 1/s for the 8 bins from one division (Montgomery's simultaneous
-      // inversion): prefix products, invert the last, unwind.
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        sv[k] = A + C * e[k];
-        pre[k] = k == 0 ? sv[0] : pre[k - 1] * sv[k];
+        tv[k] = sA + Cs * e[k];
+        pre[k] = k == 0 ? tv[0] : pre[k - 1] * tv[k];
       }
-      double inv = 1.0 / pre[7];
+      double inv = rA / pre[7];              // r[k] = (1/sqrt(A)) / t_k
       if (finite_bits(inv) && inv != 0.0) {
 #pragma unroll
         for (int k = 7; k > 0; --k) {
           r[k] = inv * pre[k - 1];
-          inv = inv * sv[k];
+          inv = inv * tv[k];
         }
         r[0] = inv;
       } else {  // products left the double range: divide bin by bin
 #pragma unroll
-        for (int k = 0; k < 8; ++k) r[k] = 1.0 / sv[k];
+        for (int k = 0; k < 8; ++k) r[k] = rA / tv[k];
       }
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         ep[(int64_t)(i + k) * n] = e[k] * r[k];
-        cp[(int64_t)(i + k) * n] = (c[k] * (sv[k] * sv[k])) * invA;
+        cp[(int64_t)(i + k) * n] = (c[k] * tv[k]) * tv[k];
       }
     }
     for (; i < nb; ++i) {
       const double e = ep[(int64_t)i * n];
-      const double s = A + C * e;
-      ep[(int64_t)i * n] = e / s;
-      cp[(int64_t)i * n] = (cp[(int64_t)i * n] * (s * s)) * invA;
+      const double t = sA + Cs * e;
+      ep[(int64_t)i * n] = e * (rA / t);
+      cp[(int64_t)i * n] = (cp[(int64_t)i * n] * t) * t;
     }
     n_old[p] = nn;
   }
