@@ -318,49 +318,93 @@ __global__ void k_shock_cells(const double* __restrict__ fp, const Geo g, double
   }
 }
 
-// Eq. convolution_spectra for each listed LP, one thread per LP, so only
-// shocked LPs do the work and a warp never idles on unshocked lanes.  With
-// chi_in the power law through adjacent bin values, the kernel
+// Eq. convolution_spectra for each listed LP, one warp per LP, so only
+// shocked LPs do the work and a few thousand of them still fill the GPU.
+// With chi_in the power law through adjacent bin values, the kernel
 // (eps_i/e)^(2-q) separates: chi_out_i = cn S_i / w_i, w = eps^(q-2),
 // S_i = sum_{j<=i} dln eps_j h_{j-1} expm1(d_j)/d_j, h = chi w,
-// d_j = ln(h_j/h_{j-1}) -- a running sum over the bins, O(N_b) per LP.
+// d_j = ln(h_j/h_{j-1}) -- a prefix sum over the bins: each lane takes 4
+// consecutive bins of a 128-bin tile, sums them, and a warp scan (shuffles)
+// adds the lanes before it; tiles carry their last bin and running sum.
 // q = 3r/(r-1) (Eq. slope, non-relativistic), cn = q/r (particle number per
 // unit fluid density conserved across the jump).
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
     k_shock_convolve(const uint32_t* __restrict__ list, const double* __restrict__ rs,
                      double* __restrict__ chi, const double* __restrict__ eng, int64_t n,
                      int nb, int* __restrict__ status) {
+  constexpr int K = 4;
   const uint32_t cnt = list[0];
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
-       t += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < cnt; t += warps) {
     const int64_t p = list[1 + t];
     const double r = rs[t];
     const double q = 3.0 * r / (r - 1.0);
     const double cn = q / r;
     const double qm2 = q - 2.0;
-    double ep = eng[p];
-    double lep = log(ep);
-    double hp = chi[p] * exp(qm2 * lep);
-    chi[p] = 0.0;
-    double S = 0.0;
+    double cS = 0.0, cE = 0.0, cL = 0.0, cH = 0.0;  // carry: running sum, last bin
     bool ok = true;
-    for (int j = 1; j < nb; ++j) {
-      const double e = eng[(int64_t)j * n + p];
-      const double cj = chi[(int64_t)j * n + p];
-      const double le = log(e);
-      const double w = exp(qm2 * le);
-      const double h = cj * w;
-      if (hp > 0.0 && h > 0.0 && e > ep) {
-        const double d = log(h / hp);
-        const double D = le - lep;
-        S += d == 0.0 ? D * hp : D * hp * (expm1(d) / d);
+    for (int t0 = 0; t0 < nb; t0 += 32 * K) {
+      double e[K], le[K], w[K], h[K], S[K];
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int j = t0 + lane * K + i;
+        e[i] = j < nb ? eng[(int64_t)j * n + p] : 1.0;
+        const double c = j < nb ? chi[(int64_t)j * n + p] : 0.0;
+        le[i] = log(e[i]);
+        w[i] = exp(qm2 * le[i]);
+        h[i] = c * w[i];
       }
-      const double out = cn * (S / w);
-      ok = ok && isfinite(out);
-      chi[(int64_t)j * n + p] = out;
-      ep = e;
-      lep = le;
-      hp = h;
+      // the bin before this lane's first: the previous lane's last, or the carry
+      double pe = __shfl_up_sync(0xffffffffu, e[K - 1], 1);
+      double pl = __shfl_up_sync(0xffffffffu, le[K - 1], 1);
+      double ph = __shfl_up_sync(0xffffffffu, h[K - 1], 1);
+      if (lane == 0) {
+        pe = cE;
+        pl = cL;
+        ph = cH;
+      }
+      double run = 0.0;
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int j = t0 + lane * K + i;
+        double seg = 0.0;
+        if (j >= 1 && j < nb && ph > 0.0 && h[i] > 0.0 && e[i] > pe) {
+          const double d = log(h[i] / ph);
+          const double D = le[i] - pl;
+          seg = d == 0.0 ? D * ph : D * ph * (expm1(d) / d);
+        }
+        run += seg;
+        S[i] = run;
+        pe = e[i];
+        pl = le[i];
+        ph = h[i];
+      }
+      // prefix of the lane totals; the exclusive one is the previous lane's
+      // inclusive value (not incl - run: h can grow by orders of magnitude
+      // from bin to bin, and that difference would cancel)
+      double incl = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+      if (lane == 0) excl = 0.0;
+      const double before = cS + excl;
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int j = t0 + lane * K + i;
+        if (j < nb) {
+          const double out = j == 0 ? 0.0 : cn * ((before + S[i]) / w[i]);
+          ok = ok && isfinite(out);
+          chi[(int64_t)j * n + p] = out;
+        }
+      }
+      cS = __shfl_sync(0xffffffffu, cS + incl, 31);
+      cE = __shfl_sync(0xffffffffu, e[K - 1], 31);
+      cL = __shfl_sync(0xffffffffu, le[K - 1], 31);
+      cH = __shfl_sync(0xffffffffu, h[K - 1], 31);
     }
     if (!ok) atomicOr(status, ST_NONFINITE);
   }
@@ -385,9 +429,9 @@ cudaError_t launch_shock_cells(part_ctx* c) {
 
 cudaError_t launch_shock_convolve(part_ctx* c) {
   if (c->n == 0) return cudaSuccess;
-  int64_t b = (c->n + 127) / 128;
-  if (b > 148 * 8) b = 148 * 8;
-  k_shock_convolve<<<(unsigned)b, 128, 0, c->stream>>>(c->shock_list, c->shock_rs, c->chi,
+  int64_t b = (c->n + 7) / 8;            // 8 warps (LPs) per block
+  if (b > 148 * 16) b = 148 * 16;
+  k_shock_convolve<<<(unsigned)b, 256, 0, c->stream>>>(c->shock_list, c->shock_rs, c->chi,
                                                        c->eng, c->n, c->nbins, c->status);
   c->launches++;
   return cudaGetLastError();
