@@ -324,6 +324,33 @@ def _e1_exact(t):
     return (v + 1) % 2 - 1
 
 
+def test_e1_closed_form_with_analytic_velocity():
+    """Eq. advection_exact_sol against Heun and SSP-RK3 on the analytic velocity
+    dx'/dt = 2 + sin(pi x') (no grid, no interpolation): the errors at t = 10
+    fall as dt^2 and (at least) dt^3, which holds only if the closed form (and
+    the reading of x' as the coordinate along the flow) is right."""
+    def v(y):
+        return 2.0 + math.sin(math.pi * y)
+
+    for order, lo, hi in ((2, 1.9, 2.1), (3, 2.9, 4.0)):
+        errs = []
+        for ns in (1000, 2000, 4000):
+            dt, y = 10.0 / ns, 0.0
+            for _ in range(ns):
+                k1 = v(y)
+                k2 = v(y + dt * k1)
+                if order == 2:
+                    y += dt * 0.5 * (k1 + k2)
+                else:
+                    k3 = v(y + dt * 0.25 * (k1 + k2))
+                    y += dt * (k1 + k2 + 4.0 * k3) / 6.0
+            errs.append(abs((y - _e1_exact(10.0) + 1) % 2 - 1))
+        # RK3 approaches order 3 from above here (a large dt^4 term): 3.6, 3.5
+        for a, b in zip(errs, errs[1:]):
+            assert lo < math.log2(a / b) < hi, (order, errs)
+        assert errs[-1] < (2e-4 if order == 2 else 1e-8)
+
+
 def test_lp_simple_advection_second_order():
     """Sec. 4.1.1: v' = 2 + sin(pi x') along the flow, one LP from x' = 0 to
     t = 10; RK2 with TSC-sampled velocity converges as n^-2 (CFL fixed).
