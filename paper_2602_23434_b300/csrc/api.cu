@@ -3,6 +3,7 @@
 // Validates arguments before any launch, carves the caller's workspace,
 // encodes the TMA tensor map of the padded field copy, and dispatches the
 // kernels on the context's stream.  Allocates no device memory.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -88,7 +89,8 @@ namespace {
 
 struct Layout {
   size_t fpad, keys0, keys1, vals0, vals1, hist, hsum, cstart, tmp, dpart, samples, status,
-      alt_x, alt_off, alt_u, alt_w, alt_id, shock_r, shock_list, shock_rs, total;
+      alt_x, alt_off, alt_u, alt_w, alt_id, shock_r, shock_list, shock_rs, cstart_alt, bcount,
+      bsum, bslot, total;
 };
 
 int ncomp_of(part_mode m) { return m == PART_BORIS ? 6 : 7; }
@@ -136,6 +138,11 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   L.shock_r = take(lp ? (size_t)g.G * 8 : 0);
   L.shock_list = take(lp ? (size_t)(c1 + 1) * 4 : 0);
   L.shock_rs = take(lp ? (size_t)c1 * 8 : 0);
+  // Boris modes: second cell_start and the brick counts of the incremental sort
+  L.cstart_alt = take(alt ? (size_t)(g.nkeys + 1) * 4 : 0);
+  L.bcount = take(alt ? (size_t)(g.nbricks + 1) * 4 : 0);
+  L.bsum = take(alt ? (size_t)((g.nbricks + 1 + kScanBlock - 1) / kScanBlock + 1) * 4 : 0);
+  L.bslot = take(alt ? (size_t)g.nbricks * 27 * 4 : 0);
   L.total = off;
   return L;
 }
@@ -277,6 +284,10 @@ part_status part_init(part_ctx** out, const part_grid* grid, part_prec prec, par
     c->alt_u = c->ws + L.alt_u;
     c->alt_w = c->ws + L.alt_w;
     c->alt_id = (uint64_t*)(c->ws + L.alt_id);
+    c->cstart_alt = (uint32_t*)(c->ws + L.cstart_alt);
+    c->bcount = (uint32_t*)(c->ws + L.bcount);
+    c->bsum = (uint32_t*)(c->ws + L.bsum);
+    c->bslot = (uint32_t*)(c->ws + L.bslot);
   }
   if (mode == PART_LP_RK2) {
     c->shock_r = (double*)(c->ws + L.shock_r);
@@ -346,6 +357,7 @@ part_status part_bind_particles(part_ctx* c, int64_t n, void* x_or_cell, void* o
   c->n_old = c->mode == PART_LP_RK2 ? n_old : nullptr;
   c->shk = nullptr;  // shock flags belong to the previous particle set
   c->shock_listed = false;
+  c->order_kept = false;
   c->bound = true;
   c->sorted = false;
   c->deposit_ready = false;
@@ -357,9 +369,17 @@ part_status part_sort(part_ctx* c) {
   if (check_ctx(c)) return PART_EINVAL;
   if (!c->bound) return fail(c, PART_EINVAL, "no particles bound");
   cudaError_t e = flush_pending(c);
-  if (e == cudaSuccess) e = launch_sort(c);
+  // every particle moved by less than one cell since the last sort: the
+  // per-brick incremental sort gives the same permutation at a fraction of
+  // the radix passes
+  double dxmin = c->geo.dx[0];
+  for (int a = 1; a < c->geo.dim; ++a) dxmin = std::min(dxmin, c->geo.dx[a]);
+  const bool inc = c->order_kept && c->cstart_alt && c->moved < dxmin;
+  if (e == cudaSuccess) e = inc ? launch_sort_incremental(c) : launch_sort(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_sort");
   c->sorted = true;
+  c->order_kept = true;
+  c->moved = 0.0;
   c->samples_ready = false;  // LP samples are in the old particle order
   c->shock_listed = false;
   return PART_OK;
@@ -377,6 +397,7 @@ part_status part_compact(part_ctx* c, const uint8_t* deleted, int64_t* n_new) {
   c->n = nn;
   *n_new = nn;
   c->sorted = false;
+  c->order_kept = false;
   c->deposit_ready = false;
   c->samples_ready = false;
   c->shock_listed = false;
@@ -454,12 +475,14 @@ part_status part_gather_push(part_ctx* c, double q_over_m, double dt, int nsteps
     }
     e = launch_boris(c, q_over_m, dt, nsteps);
     c->pending = false;
+    c->moved += std::fabs(dt) * nsteps;  // |v| < 1: displacement bound
     if (e == cudaErrorNotSupported)
       return fail(c, PART_EUNSUPPORTED, "this precision/mode has no kernel in this build");
     c->deposit_ready = c->deposit_on;
   } else {
     if (nsteps != 1) return fail(c, PART_EINVAL, "LP mode advances one step per call");
     e = launch_lp_push(c, dt, nsteps);
+    c->order_kept = false;  // fluid speeds are not bounded by the library
     c->samples_ready = true;
     c->shock_listed = c->shk != nullptr;
   }
@@ -508,6 +531,7 @@ part_status part_init_particles(part_ctx* c, uint64_t seed, double u_th, double 
   cudaError_t e = launch_init(c, seed, u_th, eps_min, eps_max, p_index, N0);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_init_particles");
   c->sorted = false;
+  c->order_kept = false;
   c->samples_ready = false;
   c->deposit_ready = false;
   return PART_OK;

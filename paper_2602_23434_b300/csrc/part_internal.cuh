@@ -71,6 +71,10 @@ struct part_ctx {
   uint32_t* hist{};   // radix tile histograms (digit-major)
   uint32_t* hsum{};   // scan block sums
   uint32_t* cstart{}; // cell_start [nkeys + 1]
+  uint32_t* cstart_alt{};  // the other cell_start buffer (incremental sort)
+  uint32_t* bcount{};      // [nbricks + 1] particles per brick, then their offsets
+  uint32_t* bsum{};        // scan block sums of bcount
+  uint32_t* bslot{};       // [nbricks][27] particles per (old brick, neighbour slot)
   void* tmp{};        // permute scratch, 8 bytes * capacity
   double* dpart{};    // deposit partials [nbricks][3][ev]
   double* samples{};  // LP samples [3][capacity]: n_new, b2m, gamma_g
@@ -104,6 +108,10 @@ struct part_ctx {
   double r_min{};
   int lp_order{2};         // LP time marching: 2 (Heun) or 3 (SSP-RK3)
   bool shock_listed{};     // the last push filled the list
+  // incremental sort: the arrays are in the order of the last sort, and
+  // `moved` bounds every particle's displacement since (|v| < c = 1)
+  bool order_kept{};
+  double moved{};
   bool bound{}, fields_set{}, sorted{}, deposit_on{}, deposit_ready{}, samples_ready{};
   int64_t launches{};
   std::string err;
@@ -216,6 +224,7 @@ cudaError_t launch_pad_fields(part_ctx* c, const void* src);
 cudaError_t launch_sort(part_ctx* c);
 cudaError_t flush_pending(part_ctx* c);  // copy pending sorted state to the bound arrays
 cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew);
+cudaError_t launch_sort_incremental(part_ctx* c);  // see sort.cu
 cudaError_t launch_shock_cells(part_ctx* c);       // shock_r from the padded LP fields
 cudaError_t launch_shock_convolve(part_ctx* c);    // Eq. convolution_spectra on the list
 cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps);

@@ -5,6 +5,9 @@
 // radix : LSD radix sort of (key, index), 8-bit digits, reduce-then-scan:
 //         per-tile digit histograms -> exclusive scan (digit-major) -> stable
 //         per-tile scatter ranked with warp match masks.  No inter-CTA waits.
+// incremental: after a push that moved every particle by less than a cell,
+//         a per-brick stable counting sort over the brick's own and adjacent
+//         old cells replaces the radix passes (same permutation).
 // permute: every bound array is gathered through the permutation into the
 //         scratch buffer and copied back (in-place semantics for the caller).
 // cell_start: cs[k] = first sorted particle with key >= k, k in [0, nkeys].
@@ -266,6 +269,293 @@ __global__ void k_gather_state(const TX* __restrict__ x, const float* __restrict
   }
 }
 
+// ---- incremental sort.  When the bound arrays are still in the order of the
+// previous sort (old cell_start cs_old: old brick ob owns the contiguous
+// segment [cs_old[ob V], cs_old[(ob+1) V])) and every particle has moved by
+// less than one cell since, each particle's new brick is its old brick or one
+// of the 26 around it: a slot d in 0..26 (per axis: same, +1, -1, periodic).
+//   count : per old brick, particles per slot               (coalesced)
+//   dest  : per new brick b, its sources in increasing id -> where each
+//           source's particles start among b's members; b's member count
+//   place : per old brick, each particle's position among its new brick's
+//           members, in old-index order (stable within the source)
+//   cells : per new brick, stable counting sort of its members by local
+//           cell -> perm and the new cell_start
+// Members of b in old-index order, sorted stably by local cell, is exactly
+// the stable sort by key, so the permutation equals the radix sort's.
+constexpr int kIncT = 256;
+constexpr int kIncMaxV = 512;
+
+__device__ __forceinline__ void brick_coords(const Geo& g, int64_t b, int* c) {
+  c[0] = (int)(b % g.nb[0]);
+  c[1] = (int)((b / g.nb[0]) % g.nb[1]);
+  c[2] = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
+}
+
+// slot of new brick db seen from old brick ob, or -1 if it is not a
+// neighbour (the particle moved more than one cell)
+__device__ __forceinline__ int inc_slot(const Geo& g, const int* oc, int64_t db) {
+  int dc[3];
+  brick_coords(g, db, dc);
+  int slot = 0;
+  for (int a = 2; a >= 0; --a) {
+    const int d = ((dc[a] - oc[a]) % g.nb[a] + g.nb[a]) % g.nb[a];
+    const int code = d == 0 ? 0 : d == 1 ? 1 : d == g.nb[a] - 1 ? 2 : -1;
+    if (code < 0) return -1;
+    slot = slot * 3 + code;
+  }
+  return slot;
+}
+
+// The 27 (possibly repeated) neighbour bricks of ob and their slots, so that
+// a particle's slot is a table lookup; ob itself (the common case) is slot 0.
+__device__ __forceinline__ void inc_table(const Geo& g, int64_t ob, uint32_t* nid) {
+  const int t = threadIdx.x;
+  if (t < 27) {
+    int oc[3];
+    brick_coords(g, ob, oc);
+    const int code[3] = {t % 3, (t / 3) % 3, t / 9};  // slot = (cz*3 + cy)*3 + cx
+    int nc[3];
+    for (int a = 0; a < 3; ++a) {
+      const int d = code[a] == 0 ? 0 : code[a] == 1 ? 1 : -1;
+      nc[a] = ((oc[a] + d) % g.nb[a] + g.nb[a]) % g.nb[a];
+    }
+    // a direction that does not exist on this grid (or repeats another) is
+    // never the slot a particle gets from inc_slot; keep it out of the table
+    const int64_t id = ((int64_t)nc[2] * g.nb[1] + nc[1]) * g.nb[0] + nc[0];
+    nid[t] = inc_slot(g, oc, id) == t ? (uint32_t)id : 0xffffffffu;
+  }
+}
+
+__device__ __forceinline__ int inc_lookup(const uint32_t* nid, uint32_t ob, uint32_t db) {
+  if (db == ob) return 0;
+  for (int k = 1; k < 27; ++k)
+    if (nid[k] == db) return k;
+  return -1;
+}
+
+// Keys from the current positions (same arithmetic as the full sort) and the
+// particle count of every (old brick, slot).
+template <bool CELL>
+__global__ void __launch_bounds__(kIncT)
+    k_inc_count(const void* __restrict__ xv, int64_t n, const uint32_t* __restrict__ cs_old, Geo g,
+                uint32_t* __restrict__ keys, uint32_t* __restrict__ cnt, int* status) {
+  __shared__ uint32_t h[27], nid[27];
+  const int64_t ob = blockIdx.x;
+  if (threadIdx.x < 27) h[threadIdx.x] = 0;
+  inc_table(g, ob, nid);
+  __syncthreads();
+  const uint32_t s0 = cs_old[ob * g.V], s1 = cs_old[(ob + 1) * g.V];
+  for (uint32_t c0 = s0; c0 < s1; c0 += kIncT) {  // uniform trip count per warp
+    const uint32_t i = c0 + threadIdx.x;
+    int slot = 27;
+    if (i < s1) {
+      uint32_t key;
+      if (CELL) {
+        int64_t c = ((const int32_t*)xv)[i];
+        if (c < 0 || c >= g.G) {
+          atomicOr(status, ST_DOMAIN);
+          c = c < 0 ? 0 : g.G - 1;
+        }
+        key = brick_key(g, (int)(c % g.n[0]), (int)((c / g.n[0]) % g.n[1]),
+                        (int)(c / ((int64_t)g.n[0] * g.n[1])));
+      } else {
+        const double* x = (const double*)xv;
+        int j[3] = {0, 0, 0};
+        for (int a = 0; a < g.dim; ++a) j[a] = cell_of(g, a, x[a * n + i], status);
+        key = brick_key(g, j[0], j[1], j[2]);
+      }
+      keys[i] = key;
+      slot = inc_lookup(nid, (uint32_t)ob, key / (uint32_t)g.V);
+      if (slot < 0) {
+        atomicOr(status, ST_DOMAIN);
+        slot = 27;
+      }
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, (uint32_t)slot);
+    if (slot < 27 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[slot], __popc(peers));
+  }
+  __syncthreads();
+  if (threadIdx.x < 27) cnt[ob * 27 + threadIdx.x] = h[threadIdx.x];
+}
+
+// One warp per new brick b: lane d < 27 takes the source brick b - delta(d);
+// repeated sources (one or two bricks along an axis) keep their first lane.
+// In increasing source id, the count of each (source, slot) is replaced by
+// its start among b's members; b's member count goes to bcount.
+__global__ void __launch_bounds__(256)
+    k_inc_dest(uint32_t* __restrict__ cnt, Geo g, uint32_t* __restrict__ bcount) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < g.nbricks;
+       b += nw) {
+    int bc[3];
+    brick_coords(g, b, bc);
+    uint64_t id = ~0ull;
+    uint32_t c = 0, slot = 0;
+    if (lane < 27 && (g.dim == 3 || lane / 9 == 1)) {
+      const int d[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+      int sc[3];
+      for (int a = 0; a < 3; ++a) sc[a] = ((bc[a] - d[a]) % g.nb[a] + g.nb[a]) % g.nb[a];
+      id = ((uint64_t)sc[2] * g.nb[1] + sc[1]) * g.nb[0] + sc[0];
+      slot = (uint32_t)inc_slot(g, sc, b);
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, id);
+    const bool keep = id != ~0ull && lane == __ffs(peers) - 1;
+    if (keep) c = cnt[id * 27 + slot];
+    // exclusive prefix of the kept counts in increasing source id
+    uint32_t before = 0, total = 0;
+    for (int k = 0; k < 27; ++k) {
+      const uint64_t idk = __shfl_sync(0xffffffffu, id, k);
+      const uint32_t ck = __shfl_sync(0xffffffffu, keep ? c : 0u, k);
+      const bool kk = __shfl_sync(0xffffffffu, keep ? 1 : 0, k) != 0;
+      if (kk) {
+        total += ck;
+        if (idk < id) before += ck;
+      }
+    }
+    if (keep) cnt[id * 27 + slot] = before;
+    if (lane == 0) bcount[b] = total;
+  }
+}
+
+// Position of every particle of old brick ob among its new brick's members:
+// bbase[db] + start of (ob, slot) + rank within (ob, slot) in index order.
+__global__ void __launch_bounds__(kIncT)
+    k_inc_place(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ cs_old, Geo g,
+                const uint32_t* __restrict__ start, const uint32_t* __restrict__ bbase,
+                uint32_t* __restrict__ memb, uint32_t* __restrict__ mlc, int64_t n) {
+  constexpr int W = kIncT / 32;
+  __shared__ uint32_t wc[W][28], run[28], nid[27];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t ob = blockIdx.x;
+  inc_table(g, ob, nid);
+  if (tid < 28) run[tid] = 0;
+  const uint32_t s0 = cs_old[ob * g.V], s1 = cs_old[(ob + 1) * g.V];
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint32_t c0 = s0; c0 < s1; c0 += kIncT) {
+    for (int q = tid; q < W * 28; q += kIncT) (&wc[0][0])[q] = 0;
+    __syncthreads();
+    const uint32_t i = c0 + tid;
+    const bool valid = i < s1;
+    const uint32_t key = valid ? keys[i] : 0u;
+    int slot = valid ? inc_lookup(nid, (uint32_t)ob, key / (uint32_t)g.V) : 27;
+    if (slot < 0) slot = 27;  // moved too far: reported by the count pass
+    const uint32_t peers = __match_any_sync(0xffffffffu, (uint32_t)slot);
+    const uint32_t rank = __popc(peers & lt);
+    if (lane == __ffs(peers) - 1) wc[warp][slot] = __popc(peers);
+    __syncthreads();
+    if (tid < 28) {  // exclusive prefix over the warps, on top of the running count
+      uint32_t acc = run[tid];
+      for (int w = 0; w < W; ++w) {
+        const uint32_t t = wc[w][tid];
+        wc[w][tid] = acc;
+        acc += t;
+      }
+      run[tid] = acc;
+    }
+    __syncthreads();
+    if (slot < 27) {
+      const uint32_t db = key / (uint32_t)g.V;
+      const uint64_t pos = (uint64_t)bbase[db] + start[ob * 27 + slot] + wc[warp][slot] + rank;
+      if (pos < (uint64_t)n) {
+        memb[pos] = i;
+        mlc[pos] = key % (uint32_t)g.V;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Per new brick: stable counting sort of its members (old-index order) by
+// local cell into perm, and the new cell_start of its cells.
+__global__ void __launch_bounds__(kIncT)
+    k_inc_cells(const uint32_t* __restrict__ bbase, const uint32_t* __restrict__ memb,
+                const uint32_t* __restrict__ mlc, Geo g, uint32_t* __restrict__ perm,
+                uint32_t* __restrict__ cs_new) {
+  constexpr int W = kIncT / 32;
+  constexpr int ITEMS = 8;
+  __shared__ uint32_t wh[W][kIncMaxV];
+  __shared__ uint32_t cofs[kIncMaxV], crun[kIncMaxV];
+  __shared__ uint32_t wt[8], tot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t b = blockIdx.x;
+  const uint32_t base = bbase[b], count = bbase[b + 1] - bbase[b];
+  for (int lc = tid; lc < g.V; lc += kIncT) crun[lc] = 0;
+  __syncthreads();
+  for (uint32_t m = tid; m < count; m += kIncT) atomicAdd(&crun[mlc[base + m]], 1u);
+  __syncthreads();
+  {
+    const int q = g.V / kIncT;  // V is 256 or 512
+    uint32_t c[kIncMaxV / kIncT], sum = 0;
+    for (int r = 0; r < q; ++r) {
+      c[r] = crun[tid * q + r];
+      sum += c[r];
+    }
+    uint32_t e = block_exclusive_scan(sum, wt, &tot);
+    for (int r = 0; r < q; ++r) {
+      cofs[tid * q + r] = e;
+      cs_new[b * g.V + tid * q + r] = base + e;
+      e += c[r];
+    }
+  }
+  __syncthreads();
+  for (int lc = tid; lc < g.V; lc += kIncT) crun[lc] = 0;
+  __syncthreads();
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint32_t tb = 0; tb < count; tb += W * 32 * ITEMS) {
+    for (int q = tid; q < W * kIncMaxV; q += kIncT) (&wh[0][0])[q] = 0;
+    __syncthreads();
+    const uint32_t seg = tb + (uint32_t)warp * 32 * ITEMS;
+    uint32_t li[ITEMS], ll[ITEMS], pos[ITEMS];
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+      const uint32_t m = seg + r * 32 + lane;
+      const bool valid = m < count;
+      const uint32_t lc = valid ? mlc[base + m] : (uint32_t)kIncMaxV;
+      const uint32_t peers = __match_any_sync(0xffffffffu, lc);
+      const uint32_t rank = __popc(peers & lt);
+      const int leader = __ffs(peers) - 1;
+      const uint32_t before = valid ? wh[warp][lc] : 0u;
+      __syncwarp();
+      if (valid && lane == leader) wh[warp][lc] = before + __popc(peers);
+      __syncwarp();
+      li[r] = valid ? memb[base + m] : 0u;
+      ll[r] = lc;
+      pos[r] = before + rank;
+    }
+    __syncthreads();
+    for (int lc = tid; lc < g.V; lc += kIncT) {
+      uint32_t acc = crun[lc];
+      for (int w = 0; w < W; ++w) {
+        const uint32_t t = wh[w][lc];
+        wh[w][lc] = acc;
+        acc += t;
+      }
+      crun[lc] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+      const uint32_t m = seg + r * 32 + lane;
+      if (m < count) {
+        const uint32_t dst = cofs[ll[r]] + wh[warp][ll[r]] + pos[r];
+        if (dst < count) perm[base + dst] = li[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// cs_new[nkeys] = total; a total below n means some particle moved further
+// than one cell since the previous sort (the arrays were changed outside).
+__global__ void k_inc_finish(const uint32_t* __restrict__ bbase, int64_t nbricks, int64_t nkeys,
+                             int64_t n, uint32_t* __restrict__ cs_new, int* status) {
+  const uint32_t total = bbase[nbricks];
+  cs_new[nkeys] = total;
+  if ((int64_t)total != n) atomicOr(status, ST_DOMAIN);
+}
+
 // ---- compaction (Sec. 3.2): D = exclusive scan of the deletion flags over
 // n + 1 entries (D[n] = N_del); the k-th hole below n_keep = n - N_del takes
 // the k-th surviving particle at or beyond n_keep.
@@ -313,6 +603,8 @@ cudaError_t permute_plane(part_ctx* c, T* arr, const uint32_t* perm) {
   return cudaMemcpyAsync(arr, c->tmp, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream);
 }
 
+cudaError_t permute_all(part_ctx* c, const uint32_t* perm);
+
 }  // namespace
 
 cudaError_t launch_sort(part_ctx* c) {
@@ -351,6 +643,55 @@ cudaError_t launch_sort(part_ctx* c) {
     const uint32_t* sk = c->keys[cur];
     k_cell_start<<<grid_for(n + 1, 256), 256, 0, s>>>(sk, n, g.nkeys, c->cstart);
     c->launches++;
+    return permute_all(c, perm);
+  } else {
+    k_cell_start<<<1, 256, 0, s>>>(c->keys[0], 0, g.nkeys, c->cstart);
+    c->launches++;
+  }
+  return cudaGetLastError();
+}
+
+// Incremental path: keys + per-(brick, slot) counts, destinations, scan,
+// placement, per-brick cell sort (see the kernels above).
+cudaError_t launch_sort_incremental(part_ctx* c) {
+  const Geo& g = c->geo;
+  const int64_t n = c->n;
+  cudaStream_t s = c->stream;
+  if (n == 0) return launch_sort(c);
+  const unsigned nbk = (unsigned)g.nbricks;
+  if (c->mode == PART_BORIS && c->prec == PART_MIXED)
+    k_inc_count<true><<<nbk, kIncT, 0, s>>>(c->x, n, c->cstart, g, c->keys[0], c->bslot,
+                                            c->status);
+  else
+    k_inc_count<false><<<nbk, kIncT, 0, s>>>(c->x, n, c->cstart, g, c->keys[0], c->bslot,
+                                             c->status);
+  k_inc_dest<<<grid_for(g.nbricks * 32, 256), 256, 0, s>>>(c->bslot, g, c->bcount);
+  cudaError_t e = cudaMemsetAsync(c->bcount + g.nbricks, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  const int64_t m = g.nbricks + 1;
+  const int64_t nblk = (m + kScanBlock - 1) / kScanBlock;
+  k_scan_reduce<<<(unsigned)nblk, 256, 0, s>>>(c->bcount, m, c->bsum);
+  k_scan_top<<<1, 256, 0, s>>>(c->bsum, nblk);
+  k_scan_down<<<(unsigned)nblk, 256, 0, s>>>(c->bcount, m, c->bsum);
+  k_inc_place<<<nbk, kIncT, 0, s>>>(c->keys[0], c->cstart, g, c->bslot, c->bcount, c->vals[1],
+                                    c->keys[1], n);
+  k_inc_cells<<<nbk, kIncT, 0, s>>>(c->bcount, c->vals[1], c->keys[1], g, c->vals[0],
+                                    c->cstart_alt);
+  k_inc_finish<<<1, 1, 0, s>>>(c->bcount, g.nbricks, g.nkeys, n, c->cstart_alt, c->status);
+  c->launches += 8;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  std::swap(c->cstart, c->cstart_alt);
+  return permute_all(c, c->vals[0]);
+}
+
+namespace {
+
+// Permute every bound array by perm (Boris modes: into the alternate buffers).
+cudaError_t permute_all(part_ctx* c, const uint32_t* perm) {
+  const int64_t n = c->n;
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  {
     // permute the bound arrays
     if (c->mode == PART_BORIS && c->alt_x) {
       if (c->prec == PART_FP64)
@@ -390,12 +731,11 @@ cudaError_t launch_sort(part_ctx* c) {
       if (c->shk && (e = permute_plane<uint8_t>(c, c->shk, perm))) return e;
     }
     if (c->id && (e = permute_plane<uint64_t>(c, c->id, perm))) return e;
-  } else {
-    k_cell_start<<<1, 256, 0, s>>>(c->keys[0], 0, g.nkeys, c->cstart);
-    c->launches++;
   }
   return cudaGetLastError();
 }
+
+}  // namespace
 
 cudaError_t flush_pending(part_ctx* c) {
   if (!c->pending) return cudaSuccess;

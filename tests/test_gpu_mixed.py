@@ -193,3 +193,32 @@ def test_mixed_drift_1000_steps(E):
     assert dphi[well].max() <= 2e-5
     assert np.all(du_perp[~well] <= 2e-5 * 0.2 * 0.1)
     assert egy.max() <= 1e-6
+
+
+def test_mixed_resort_after_push_bit_exact():
+    """The incremental sort on the mixed form (cells moved by the push)."""
+    dim, n, ppc = 3, 20, 8
+    og = O.make_grid(dim, (n, n, n))
+    N, cell, off, uf, wf, ids = _state(dim, n, ppc, 9, u_th=2.0)
+    f = synth.em_fields(dim, n, 3, v_rms=0.05).reshape(6, -1)
+    p = P.Part(P.make_grid(dim, n), P.MIXED, P.TSC, P.BORIS, capacity=N)
+    p.set_fields(torch.as_tensor(f.astype(np.float32)).cuda())
+    cd = torch.as_tensor(cell).cuda()
+    od, ud = torch.as_tensor(off).cuda(), torch.as_tensor(uf).cuda()
+    idd = torch.as_tensor(ids.astype(np.int64)).cuda()
+    p.bind(N, cd, off=od, u=ud, ids=idd)
+    p.sort()
+    tab = _key_table(og, p.brick, n, dim)
+    for _ in range(3):
+        p.gather_push(1.0, 0.95 * 2.0 / n, 1)
+        p.sync()
+        cb, ib, ob = _host(cd).copy(), _host(idd).copy(), _host(od).copy()
+        p.sort()
+        cs = _host(p.cell_start())
+        p.sync()
+        keys = tab[cb]
+        perm = O.stable_sort(keys)
+        assert np.array_equal(_host(idd), ib[perm])
+        assert np.array_equal(_host(cd), cb[perm])
+        assert np.array_equal(_host(od), ob[:, perm])
+        assert np.array_equal(cs, O.cell_start(p.nkeys, keys[perm]).astype(np.int64))

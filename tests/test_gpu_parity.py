@@ -260,3 +260,65 @@ def test_error_paths():
         p.sync()
     assert e.value.name == "PART_ENONFINITE"
     p.sync()                                         # status cleared
+
+
+def _sort_launches(p):
+    l0 = p.launches()
+    p.sort()
+    return p.launches() - l0
+
+
+@pytest.mark.parametrize("dim,n,ppc", [(3, 20, 8), (2, 40, 16), (3, 16, 4), (3, 8, 3),
+                                       (3, 5, 2), (2, 18, 4)])
+def test_resort_after_push_bit_exact(dim, n, ppc):
+    """After a push that moves every particle by less than a cell, part_sort
+    takes the per-brick incremental path; it must give the oracle's stable
+    sort of the pushed positions bit for bit (bricks crossed, periodic
+    wrap, partial bricks, one or two bricks per axis)."""
+    og, pg = _grids(dim, n)
+    N = n ** dim * ppc + 5
+    x, u, w, ids = synth.particles(dim, None, N, 31 + n, u_th=2.0)   # |v| close to 1
+    f = synth.em_fields(dim, n, 7, v_rms=0.05).reshape(6, -1)
+    p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=N)
+    p.set_fields(_dev(f))
+    xd, ud = _dev(x), _dev(u)
+    idd = torch.as_tensor(ids.astype(np.int64)).cuda()
+    p.bind(N, xd, u=ud, ids=idd)
+    full = _sort_launches(p)
+    dt = 0.95 * 2.0 / n
+    for step in range(3):
+        p.gather_push(1.0, dt, 1)
+        p.sync()
+        xb, ib = _host(xd).copy(), _host(idd).copy()
+        inc = _sort_launches(p)
+        cs = _host(p.cell_start())
+        p.sync()
+        assert inc < full                       # the incremental path ran
+        keys = O.keys(og, p.brick, xb)
+        perm = O.stable_sort(keys)
+        assert np.array_equal(_host(idd), ib[perm])
+        assert np.array_equal(_host(xd), xb[:, perm])
+        assert np.array_equal(cs, O.cell_start(p.nkeys, keys[perm]).astype(np.int64))
+
+
+def test_resort_falls_back_after_a_long_move():
+    """A push with dt >= dx (possible moves of a cell or more) or several fused
+    steps make part_sort take the full radix path again."""
+    og, pg = _grids(3, 16)
+    N = 16 ** 3 * 2
+    x, u, w, ids = synth.particles(3, None, N, 12, u_th=2.0)
+    f = synth.em_fields(3, 16, 8, v_rms=0.05).reshape(6, -1)
+    p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=N)
+    p.set_fields(_dev(f))
+    xd, ud = _dev(x), _dev(u)
+    idd = torch.as_tensor(ids.astype(np.int64)).cuda()
+    p.bind(N, xd, u=ud, ids=idd)
+    full = _sort_launches(p)
+    for dt, nsteps in ((1.5 * 2.0 / 16, 1), (0.6 * 2.0 / 16, 2)):
+        p.gather_push(1.0, dt, nsteps)
+        p.sync()
+        xb, ib = _host(xd).copy(), _host(idd).copy()
+        assert _sort_launches(p) == full
+        p.sync()
+        perm = O.stable_sort(O.keys(og, p.brick, xb))
+        assert np.array_equal(_host(idd), ib[perm])
