@@ -536,6 +536,7 @@ def run_e2e(torch, wl: BorisWorkload, K: int):
             wl.u.copy_(hu, non_blocking=True)
             wl.w.copy_(hw, non_blocking=True)
             wl.step()
+            wl.part.flush()
             hx.copy_(wl.x, non_blocking=True)
             hu.copy_(wl.u, non_blocking=True)
             hout.copy_(wl.out, non_blocking=True)

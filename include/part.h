@@ -120,13 +120,23 @@ part_status part_bind_particles(part_ctx* ctx, int64_t n, void* x_or_cell, void*
 
 /* Sort the bound particles by cell key (stable: equal keys keep their current
  * order), permuting every bound array, and rebuild cell_start.  Required
- * before a push with deposit enabled.  Boris modes: the sorted state is
- * gathered into the workspace and the next one-step push reads it from there
- * while writing the bound arrays (no copy-back pass); any other call that
- * needs the bound arrays (part_sync, part_bind_particles, part_sort, a
- * multi-step push) first copies it home.  Between part_sort and the next such
- * call the bound arrays must be neither read nor written by the caller.    */
+ * before a push with deposit enabled.
+ * Boris modes: the sort only computes the permutation.  The next one-step
+ * push reads the particles through it and writes them, sorted, into a second
+ * copy in the workspace, which then holds the current state (the copies
+ * alternate from step to step).  part_flush, part_sync, part_bind_particles,
+ * part_compact and a multi-step push first bring the current state into the
+ * bound arrays, in sorted order.  Between part_sort and the next of those
+ * calls the caller must neither read nor write the bound arrays.
+ * When the previous sort's order has been kept and every push since moved
+ * each particle by less than one cell (sum of nsteps * |dt| below the
+ * smallest dx; |v| < c = 1), a per-brick incremental sort replaces the radix
+ * passes; the permutation is the same.                                     */
 part_status part_sort(part_ctx* ctx);
+
+/* Bring the current particle state into the bound arrays, in sorted order,
+ * asynchronously on the context's stream (see part_sort).                  */
+part_status part_flush(part_ctx* ctx);
 
 /* Remove the particles flagged in deleted (device uint8[n], nonzero = delete)
  * by the hole/filler compaction of Sec. 3.2 ("Ensure coalesced access to
@@ -219,8 +229,8 @@ part_status part_shock_cells(part_ctx* ctx, const double** r_cell, int64_t* ncel
 part_status part_init_particles(part_ctx* ctx, uint64_t seed, double u_th, double eps_min,
                                 double eps_max, double p_index, double N0);
 
-/* Wait for the context's stream; return (and clear) the first latched device
- * error, else PART_OK.                                                     */
+/* part_flush, then wait for the context's stream; return (and clear) the
+ * first latched device error, else PART_OK.                                */
 part_status part_sync(part_ctx* ctx);
 
 /* Message for the last non-OK status of this context (never NULL).        */

@@ -91,6 +91,7 @@ def lib():
         "part_compact": (st, [P, P, C.POINTER(C.c_int64)]),
         "part_enable_shocks": (st, [P, C.c_double, P]),
         "part_set_lp_order": (st, [P, C.c_int]),
+        "part_flush": (st, [P]),
         "part_shock_cells": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
         "part_enable_deposit": (st, [P, C.c_int]),
         "part_gather_push": (st, [P, C.c_double, C.c_double, C.c_int]),
@@ -209,6 +210,10 @@ class Part:
         nn = C.c_int64()
         self._check(self.L.part_compact(self.ctx, _ptr(deleted), C.byref(nn)))
         return nn.value
+
+    def flush(self):
+        """Current particle state into the bound arrays (asynchronous)."""
+        self._check(self.L.part_flush(self.ctx))
 
     def set_lp_order(self, order: int):
         """LP time marching: 2 (Heun) or 3 (SSP-RK3)."""

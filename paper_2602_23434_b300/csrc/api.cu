@@ -333,7 +333,7 @@ part_status part_bind_particles(part_ctx* c, int64_t n, void* x_or_cell, void* o
                                 double* n_old) {
   if (check_ctx(c)) return PART_EINVAL;
   if (n < 0 || n > c->capacity) return fail(c, PART_EINVAL, "n must be in [0, capacity]");
-  if (c->pending) {  // sorted state of the previous arrays goes home first
+  if (c->cur_alt || c->perm_pend) {  // the previous arrays get their current state first
     cudaError_t e = flush_pending(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "part_bind_particles");
   }
@@ -368,7 +368,7 @@ part_status part_bind_particles(part_ctx* c, int64_t n, void* x_or_cell, void* o
 part_status part_sort(part_ctx* c) {
   if (check_ctx(c)) return PART_EINVAL;
   if (!c->bound) return fail(c, PART_EINVAL, "no particles bound");
-  cudaError_t e = flush_pending(c);
+  cudaError_t e = cudaSuccess;
   // every particle moved by less than one cell since the last sort: the
   // per-brick incremental sort gives the same permutation at a fraction of
   // the radix passes
@@ -401,6 +401,13 @@ part_status part_compact(part_ctx* c, const uint8_t* deleted, int64_t* n_new) {
   c->deposit_ready = false;
   c->samples_ready = false;
   c->shock_listed = false;
+  return PART_OK;
+}
+
+part_status part_flush(part_ctx* c) {
+  if (check_ctx(c)) return PART_EINVAL;
+  cudaError_t e = flush_pending(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "part_flush");
   return PART_OK;
 }
 
@@ -467,14 +474,14 @@ part_status part_gather_push(part_ctx* c, double q_over_m, double dt, int nsteps
       return fail(c, PART_EINVAL, "deposit needs nsteps == 1 (fused steps are test particles)");
     if (c->deposit_on && !c->sorted)
       return fail(c, PART_EINVAL, "deposit needs part_sort since the last push");
-    // the brick kernel (sorted, one step) reads the pending sorted state
-    // directly; every other path needs it in the bound arrays first
-    if (c->pending && !(c->sorted && nsteps == 1)) {
+    // the brick kernel (sorted, one step) reads the current buffer through
+    // the sort's permutation; every other path needs the state in the bound
+    // arrays first
+    if (!(c->sorted && nsteps == 1)) {
       e = flush_pending(c);
       if (e != cudaSuccess) return cuda_fail(c, e, "part_gather_push");
     }
     e = launch_boris(c, q_over_m, dt, nsteps);
-    c->pending = false;
     c->moved += std::fabs(dt) * nsteps;  // |v| < 1: displacement bound
     if (e == cudaErrorNotSupported)
       return fail(c, PART_EUNSUPPORTED, "this precision/mode has no kernel in this build");
@@ -527,7 +534,8 @@ part_status part_init_particles(part_ctx* c, uint64_t seed, double u_th, double 
   } else if (!std::isfinite(u_th) || u_th < 0.0) {
     return fail(c, PART_EINVAL, "u_th must be finite and >= 0");
   }
-  c->pending = false;  // every bound array is overwritten
+  c->cur_alt = false;  // every bound array is overwritten
+  c->perm_pend = nullptr;
   cudaError_t e = launch_init(c, seed, u_th, eps_min, eps_max, p_index, N0);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_init_particles");
   c->sorted = false;

@@ -78,15 +78,18 @@ struct part_ctx {
   void* tmp{};        // permute scratch, 8 bytes * capacity
   double* dpart{};    // deposit partials [nbricks][3][ev]
   double* samples{};  // LP samples [3][capacity]: n_new, b2m, gamma_g
-  // Boris modes: alternate particle buffers.  part_sort gathers the bound
-  // arrays into them ("pending"); the next brick push reads them and writes
-  // the caller's arrays, so no copy-back pass is needed.  NULL: in-place sort.
+  // Boris modes: alternate particle buffers.  part_sort only computes the
+  // permutation (perm_pend); the next brick push reads the current buffer
+  // through it and writes the other one, so no separate permutation pass is
+  // needed.  The current state then alternates between the caller's arrays
+  // and these buffers; part_flush / part_sync bring it home.
   void* alt_x{};      // FP64: double[3][cap]   mixed: int32 cell[cap]
   void* alt_off{};    // mixed: float[3][cap]
   void* alt_u{};      // FP64: double[3][cap]   mixed: float[3][cap]
   void* alt_w{};      // FP64: double[cap]      mixed: float[cap]
   uint64_t* alt_id{}; // uint64[cap]
-  bool pending{};     // sorted state lives in the alt buffers
+  bool cur_alt{};                 // the current state is in the alternate buffers
+  const uint32_t* perm_pend{};    // new slot -> index in the current buffer, or NULL
   int* status{};      // device status word
   CUtensorMap tmap{};  // TMA map of fpad
   bool tmap_ok{};
@@ -222,7 +225,22 @@ void make_geo(const part_grid* gr, int esize, Geo* g);
 // of its launch and counts the launches it made in *launches.
 cudaError_t launch_pad_fields(part_ctx* c, const void* src);
 cudaError_t launch_sort(part_ctx* c);
-cudaError_t flush_pending(part_ctx* c);  // copy pending sorted state to the bound arrays
+cudaError_t flush_pending(part_ctx* c);  // current state into the bound arrays, in order
+cudaError_t apply_perm(part_ctx* c);     // a pending permutation into the other buffer
+
+// Particle arrays of one buffer (the caller's or the alternate one).
+struct PState {
+  void* x;
+  void* off;
+  void* u;
+  void* w;
+  uint64_t* id;
+};
+inline PState state_of(const part_ctx* c, bool alt) {
+  if (!alt) return {c->x, c->off, c->u, c->w, c->id};
+  return {c->alt_x, c->off ? c->alt_off : nullptr, c->alt_u, c->w ? c->alt_w : nullptr,
+          c->id ? c->alt_id : nullptr};
+}
 cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew);
 cudaError_t launch_sort_incremental(part_ctx* c);  // see sort.cu
 cudaError_t launch_shock_cells(part_ctx* c);       // shock_r from the padded LP fields

@@ -84,21 +84,21 @@ __device__ __forceinline__ void boris_f64(double* u, const double* E, const doub
 template <int SHAPE, int DIM, bool DEP>
 __device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int bvol,
                                          const uint32_t* scs, const int* org, uint32_t p,
-                                         const double* xs, const double* us,
+                                         uint32_t q, const double* xs, const double* us,
                                          const double* ws, const uint64_t* ids, double* x,
                                          double* u, double* wd, uint64_t* idd, int64_t n,
                                          double h, double dt, double inv_dt, int* status,
                                          double* wyz, double* fxc) {
   double xp[3], up[3], uo[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    xp[a] = xs[a * n + p];
-    up[a] = us[a * n + p];
+  for (int a = 0; a < 3; ++a) {  // particle q of the current buffer goes to slot p
+    xp[a] = xs[a * n + q];
+    up[a] = us[a * n + q];
     uo[a] = up[a];
   }
-  const double wp = ws ? ws[p] : 1.0;
+  const double wp = ws ? ws[q] : 1.0;
   if (ws && wd != ws) wd[p] = wp;             // carry the read-only planes over
-  if (ids && idd != ids) idd[p] = ids[p];
+  if (ids && idd != ids) idd[p] = ids[q];
   int l[3] = {0, 0, 0};
   double d[3] = {0.0, 0.0, 0.0};
   bool ok = true;
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kT, 1)
     k_boris_brick_f64(const __grid_constant__ CUtensorMap tmap, const Geo g,
                       const double* xs, const double* us, const double* ws,
                       const uint64_t* ids, double* x, double* u, double* wd, uint64_t* idd,
-                      int64_t n,
+                      int64_t n, const uint32_t* __restrict__ perm,
                       const uint32_t* __restrict__ cstart, double* __restrict__ dpart,
                       double qm, double dt, double inv_dt, int* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -310,8 +310,8 @@ __global__ void __launch_bounds__(kT, 1)
   const double h = 0.5 * qm * dt;
   const uint32_t p0 = scs[0], p1 = scs[g.V];
   for (uint32_t p = p0 + tid; p < p1; p += kT)
-    push_one<SHAPE, DIM, false>(g, sbox, bvol, scs, org, p, xs, us, ws, ids, x, u, wd, idd, n,
-                                h, dt, inv_dt, status, nullptr, nullptr);
+    push_one<SHAPE, DIM, false>(g, sbox, bvol, scs, org, p, perm ? perm[p] : p, xs, us, ws,
+                                ids, x, u, wd, idd, n, h, dt, inv_dt, status, nullptr, nullptr);
 }
 
 // With deposit: warp-specialised, 512 threads.  Warps 0-7 push chunk k of 256
@@ -325,7 +325,8 @@ __global__ void __launch_bounds__(2 * kT, 1)
     k_boris_brick_f64_dep(const __grid_constant__ CUtensorMap tmap, const Geo g,
                           const double* xs, const double* us, const double* ws,
                           const uint64_t* ids, double* x, double* u, double* wd,
-                          uint64_t* idd, int64_t n, const uint32_t* __restrict__ cstart,
+                          uint64_t* idd, int64_t n, const uint32_t* __restrict__ perm,
+                          const uint32_t* __restrict__ cstart,
                           double* __restrict__ dpart, double qm, double dt, double inv_dt,
                           int* __restrict__ status) {
   constexpr int NT = 2 * kT;
@@ -360,8 +361,8 @@ __global__ void __launch_bounds__(2 * kT, 1)
 #pragma unroll
       for (int q = 0; q < 9; ++q) wyz[q] = fxc[q] = 0.0;
       if (p < p1)
-        push_one<SHAPE, DIM, true>(g, sbox, bvol, scs, org, p, xs, us, ws, ids, x, u, wd, idd,
-                                   n, h, dt, inv_dt, status, wyz, fxc);
+        push_one<SHAPE, DIM, true>(g, sbox, bvol, scs, org, p, perm ? perm[p] : p, xs, us, ws,
+                                   ids, x, u, wd, idd, n, h, dt, inv_dt, status, wyz, fxc);
       if (k >= 2) named_bar_sync(kEmpty + b, NT);  // deposit of chunk k-2 has read it
       double* rw = rec + (size_t)b * 18 * kRS;
 #pragma unroll
@@ -525,14 +526,19 @@ cudaError_t brick_f64(part_ctx* c, double qm, double dt) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L.total);
   if (e != cudaSuccess) return e;
-  const bool alt = c->pending;  // sorted state waits in the alternate buffers
+  // read the current buffer (through the sort's permutation, if one is
+  // pending, into the other buffer; else in place)
+  const PState src = state_of(c, c->cur_alt);
+  const PState dst = c->perm_pend ? state_of(c, !c->cur_alt) : src;
   kern<<<(unsigned)c->geo.nbricks, DEP ? 2 * kT : kT, L.total, c->stream>>>(
-      c->tmap, c->geo, (const double*)(alt ? c->alt_x : c->x),
-      (const double*)(alt ? c->alt_u : c->u),
-      (const double*)(c->w ? (alt ? c->alt_w : c->w) : nullptr),
-      c->id ? (alt ? c->alt_id : c->id) : nullptr, (double*)c->x, (double*)c->u,
-      (double*)c->w, c->id, c->n, c->cstart, c->dpart, qm, dt, 1.0 / dt, c->status);
+      c->tmap, c->geo, (const double*)src.x, (const double*)src.u, (const double*)src.w, src.id,
+      (double*)dst.x, (double*)dst.u, (double*)dst.w, dst.id, c->n, c->perm_pend, c->cstart,
+      c->dpart, qm, dt, 1.0 / dt, c->status);
   c->launches++;
+  if (c->perm_pend) {
+    c->perm_pend = nullptr;
+    c->cur_alt = !c->cur_alt;
+  }
   return cudaGetLastError();
 }
 

@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(kT, 2)
                         const int32_t* cells, const float* offs, const float* us,
                         const float* w, const uint64_t* ids, int32_t* cell, float* off,
                         float* u, float* wd, uint64_t* idd, int64_t n,
+                        const uint32_t* __restrict__ perm,
                         const uint32_t* __restrict__ cstart, double* __restrict__ dpart,
                         float h, float hl, float dtdx0, float dtdx1, float dtdx2, float inv_dt,
                         int* __restrict__ status) {
@@ -217,14 +218,15 @@ __global__ void __launch_bounds__(kT, 2)
     uint32_t p = sb + tid;
     int32_t nc = 0;
     float no[3] = {0.f, 0.f, 0.f}, nu[3] = {0.f, 0.f, 0.f}, nw = 1.0f;
-    if (p < se) {
-      nc = cells[p];
+    if (p < se) {  // particle q of the current buffer goes to slot p
+      const uint32_t q = perm ? perm[p] : p;
+      nc = cells[q];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        no[a] = offs[a * n + p];
-        nu[a] = us[a * n + p];
+        no[a] = offs[a * n + q];
+        nu[a] = us[a * n + q];
       }
-      if (w) nw = w[p];
+      if (w) nw = w[q];
     }
     for (; p < se; p += kT) {
       const int i = (int)(p - sb);
@@ -233,16 +235,17 @@ __global__ void __launch_bounds__(kT, 2)
       const float wcur = nw;
       if (p + kT < se) {
         const uint32_t pn = p + kT;
-        nc = cells[pn];
+        const uint32_t qn = perm ? perm[pn] : pn;
+        nc = cells[qn];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          no[a] = offs[a * n + pn];
-          nu[a] = us[a * n + pn];
+          no[a] = offs[a * n + qn];
+          nu[a] = us[a * n + qn];
         }
-        if (w) nw = w[pn];
+        if (w) nw = w[qn];
       }
       if (w && wd != w) wd[p] = wcur;             // carry the read-only planes over
-      if (ids && idd != ids) idd[p] = ids[p];
+      if (ids && idd != ids) idd[p] = ids[perm ? perm[p] : p];
       int j[3];
       cell_coords(g, ccur, j);
       int l[3];
@@ -535,15 +538,20 @@ cudaError_t brick_mixed(part_ctx* c, const MixedArgs& a) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L.total);
   if (e != cudaSuccess) return e;
-  const bool alt = c->pending;  // sorted state waits in the alternate buffers
+  // read the current buffer (through the sort's permutation, if one is
+  // pending, into the other buffer; else in place)
+  const PState src = state_of(c, c->cur_alt);
+  const PState dst = c->perm_pend ? state_of(c, !c->cur_alt) : src;
   kern<<<(unsigned)c->geo.nbricks, kT, L.total, c->stream>>>(
-      c->tmap, c->geo, (const int32_t*)(alt ? c->alt_x : c->x),
-      (const float*)(alt ? c->alt_off : c->off), (const float*)(alt ? c->alt_u : c->u),
-      (const float*)(c->w ? (alt ? c->alt_w : c->w) : nullptr),
-      c->id ? (alt ? c->alt_id : c->id) : nullptr, (int32_t*)c->x, (float*)c->off,
-      (float*)c->u, (float*)c->w, c->id, c->n, c->cstart, c->dpart, a.h, a.hl, a.dtdx[0],
+      c->tmap, c->geo, (const int32_t*)src.x, (const float*)src.off, (const float*)src.u,
+      (const float*)src.w, src.id, (int32_t*)dst.x, (float*)dst.off, (float*)dst.u,
+      (float*)dst.w, dst.id, c->n, c->perm_pend, c->cstart, c->dpart, a.h, a.hl, a.dtdx[0],
       a.dtdx[1], a.dtdx[2], a.inv_dt, c->status);
   c->launches++;
+  if (c->perm_pend) {
+    c->perm_pend = nullptr;
+    c->cur_alt = !c->cur_alt;
+  }
   return cudaGetLastError();
 }
 

@@ -611,13 +611,15 @@ cudaError_t launch_sort(part_ctx* c) {
   const Geo& g = c->geo;
   const int64_t n = c->n;
   cudaStream_t s = c->stream;
-  cudaError_t e;
+  cudaError_t e = apply_perm(c);  // a permutation not yet used by a push
+  if (e != cudaSuccess) return e;
+  const void* xcur = state_of(c, c->cur_alt).x;
   if (n > 0) {
     if (c->mode == PART_BORIS && c->prec == PART_MIXED)
-      k_keys_cell<<<grid_for(n, 256), 256, 0, s>>>((const int32_t*)c->x, n, g, c->keys[0],
+      k_keys_cell<<<grid_for(n, 256), 256, 0, s>>>((const int32_t*)xcur, n, g, c->keys[0],
                                                    c->vals[0], c->status);
     else
-      k_keys_f64<<<grid_for(n, 256), 256, 0, s>>>((const double*)c->x, n, g, c->keys[0],
+      k_keys_f64<<<grid_for(n, 256), 256, 0, s>>>((const double*)xcur, n, g, c->keys[0],
                                                   c->vals[0], c->status);
     c->launches++;
     int bits = 0;
@@ -658,15 +660,18 @@ cudaError_t launch_sort_incremental(part_ctx* c) {
   const int64_t n = c->n;
   cudaStream_t s = c->stream;
   if (n == 0) return launch_sort(c);
+  cudaError_t e = apply_perm(c);
+  if (e != cudaSuccess) return e;
+  const void* xcur = state_of(c, c->cur_alt).x;
   const unsigned nbk = (unsigned)g.nbricks;
   if (c->mode == PART_BORIS && c->prec == PART_MIXED)
-    k_inc_count<true><<<nbk, kIncT, 0, s>>>(c->x, n, c->cstart, g, c->keys[0], c->bslot,
+    k_inc_count<true><<<nbk, kIncT, 0, s>>>(xcur, n, c->cstart, g, c->keys[0], c->bslot,
                                             c->status);
   else
-    k_inc_count<false><<<nbk, kIncT, 0, s>>>(c->x, n, c->cstart, g, c->keys[0], c->bslot,
+    k_inc_count<false><<<nbk, kIncT, 0, s>>>(xcur, n, c->cstart, g, c->keys[0], c->bslot,
                                              c->status);
   k_inc_dest<<<grid_for(g.nbricks * 32, 256), 256, 0, s>>>(c->bslot, g, c->bcount);
-  cudaError_t e = cudaMemsetAsync(c->bcount + g.nbricks, 0, sizeof(uint32_t), s);
+  e = cudaMemsetAsync(c->bcount + g.nbricks, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   const int64_t m = g.nbricks + 1;
   const int64_t nblk = (m + kScanBlock - 1) / kScanBlock;
@@ -692,19 +697,11 @@ cudaError_t permute_all(part_ctx* c, const uint32_t* perm) {
   cudaStream_t s = c->stream;
   cudaError_t e;
   {
-    // permute the bound arrays
+    // Boris modes with alternate buffers: the next brick push (or
+    // apply_perm) moves the particles; nothing is copied here
     if (c->mode == PART_BORIS && c->alt_x) {
-      if (c->prec == PART_FP64)
-        k_gather_state<double, 3, double><<<grid_for(n, 256), 256, 0, s>>>(
-            (const double*)c->x, nullptr, (const double*)c->u, (const double*)c->w, c->id,
-            (double*)c->alt_x, nullptr, (double*)c->alt_u, (double*)c->alt_w, c->alt_id, perm, n);
-      else
-        k_gather_state<int32_t, 1, float><<<grid_for(n, 256), 256, 0, s>>>(
-            (const int32_t*)c->x, (const float*)c->off, (const float*)c->u, (const float*)c->w,
-            c->id, (int32_t*)c->alt_x, (float*)c->alt_off, (float*)c->alt_u, (float*)c->alt_w,
-            c->alt_id, perm, n);
-      c->launches++;
-      c->pending = true;
+      c->perm_pend = perm;
+      (void)s;
       return cudaGetLastError();
     }
     if (c->mode == PART_BORIS && c->prec == PART_FP64) {
@@ -737,14 +734,38 @@ cudaError_t permute_all(part_ctx* c, const uint32_t* perm) {
 
 }  // namespace
 
+// Gather the current buffer through the pending permutation into the other
+// buffer, which becomes current.
+cudaError_t apply_perm(part_ctx* c) {
+  if (!c->perm_pend) return cudaSuccess;
+  const uint32_t* perm = c->perm_pend;
+  c->perm_pend = nullptr;
+  const int64_t n = c->n;
+  if (n == 0) return cudaSuccess;
+  const PState a = state_of(c, c->cur_alt), b = state_of(c, !c->cur_alt);
+  if (c->prec == PART_FP64)
+    k_gather_state<double, 3, double><<<grid_for(n, 256), 256, 0, c->stream>>>(
+        (const double*)a.x, nullptr, (const double*)a.u, (const double*)a.w, a.id,
+        (double*)b.x, nullptr, (double*)b.u, (double*)b.w, b.id, perm, n);
+  else
+    k_gather_state<int32_t, 1, float><<<grid_for(n, 256), 256, 0, c->stream>>>(
+        (const int32_t*)a.x, (const float*)a.off, (const float*)a.u, (const float*)a.w, a.id,
+        (int32_t*)b.x, (float*)b.off, (float*)b.u, (float*)b.w, b.id, perm, n);
+  c->launches++;
+  c->cur_alt = !c->cur_alt;
+  return cudaGetLastError();
+}
+
+// Bring the current state into the caller's arrays, in sorted order.
 cudaError_t flush_pending(part_ctx* c) {
-  if (!c->pending) return cudaSuccess;
-  c->pending = false;
+  cudaError_t r = apply_perm(c);
+  if (r != cudaSuccess || !c->cur_alt) return r;
+  c->cur_alt = false;
   const int64_t n = c->n;
   if (n == 0) return cudaSuccess;
   const size_t e = c->prec == PART_FP64 ? 8 : 4;
   const int nx = c->prec == PART_FP64 ? 3 : 1;
-  cudaError_t r = cudaMemcpyAsync(c->x, c->alt_x, e * nx * n, cudaMemcpyDeviceToDevice, c->stream);
+  r = cudaMemcpyAsync(c->x, c->alt_x, e * nx * n, cudaMemcpyDeviceToDevice, c->stream);
   if (r == cudaSuccess && c->off)
     r = cudaMemcpyAsync(c->off, c->alt_off, 12 * n, cudaMemcpyDeviceToDevice, c->stream);
   if (r == cudaSuccess)
