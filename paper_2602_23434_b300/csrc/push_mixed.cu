@@ -215,37 +215,44 @@ __global__ void __launch_bounds__(kT, 2)
     const uint32_t se = p1 - sb < (uint32_t)kM ? p1 : sb + kM;
     // ---- A: push, one thread per particle; the next particle's state is
     // loaded before the current one is computed
+    // particle q of the current buffer goes to slot p; the permutation is
+    // read two slots ahead and the state one slot ahead of the computation
     uint32_t p = sb + tid;
     int32_t nc = 0;
     float no[3] = {0.f, 0.f, 0.f}, nu[3] = {0.f, 0.f, 0.f}, nw = 1.0f;
-    if (p < se) {  // particle q of the current buffer goes to slot p
-      const uint32_t q = perm ? perm[p] : p;
-      nc = cells[q];
+    uint32_t qc = p, qn = p + kT;
+    if (perm) {
+      if (p < se) qc = perm[p];
+      if (p + kT < se) qn = perm[p + kT];
+    }
+    if (p < se) {
+      nc = cells[qc];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        no[a] = offs[a * n + q];
-        nu[a] = us[a * n + q];
+        no[a] = offs[a * n + qc];
+        nu[a] = us[a * n + qc];
       }
-      if (w) nw = w[q];
+      if (w) nw = w[qc];
     }
     for (; p < se; p += kT) {
       const int i = (int)(p - sb);
       const int32_t ccur = nc;
       float o[3] = {no[0], no[1], no[2]}, up[3] = {nu[0], nu[1], nu[2]};
       const float wcur = nw;
+      const uint32_t qcur = qc;
       if (p + kT < se) {
-        const uint32_t pn = p + kT;
-        const uint32_t qn = perm ? perm[pn] : pn;
-        nc = cells[qn];
+        qc = qn;
+        if (p + 2 * kT < se) qn = perm ? perm[p + 2 * kT] : p + 2 * kT;
+        nc = cells[qc];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          no[a] = offs[a * n + qn];
-          nu[a] = us[a * n + qn];
+          no[a] = offs[a * n + qc];
+          nu[a] = us[a * n + qc];
         }
-        if (w) nw = w[qn];
+        if (w) nw = w[qc];
       }
       if (w && wd != w) wd[p] = wcur;             // carry the read-only planes over
-      if (ids && idd != ids) idd[p] = ids[perm ? perm[p] : p];
+      if (ids && idd != ids) idd[p] = ids[qcur];
       int j[3];
       cell_coords(g, ccur, j);
       int l[3];
