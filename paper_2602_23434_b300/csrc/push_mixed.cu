@@ -13,10 +13,12 @@
 //      and the force w du/dt are left in shared memory.  du is formed from the
 //      Boris rotation increment (u' x s + 2hE), not as u_new - u_old, so f32
 //      cancellation does not enter the force;
-//   B. one thread per source cell sums its particles' 27 x 3 contributions in
-//      registers, then 27 passes (one per stencil offset, separated by
-//      barriers) add them into the haloed tile's two-float accumulators: in a
-//      pass no two threads share a target, and the order is fixed.
+//   B. one thread per (source cell, force component) sums its particles' 27
+//      contributions in registers, then 27 passes (one per stencil offset,
+//      separated by barriers) add them into the haloed tile's two-float
+//      accumulators: in a pass no two threads share a target, and the order
+//      is fixed.  Super-chunks of 512 particles keep shared memory at ~71 KB
+//      and the registers under 85, so three CTAs share an SM.
 // Particle-order kernel: nsteps fused steps, state in registers, stencil read
 // from the padded global f32 copy (test particles, serving).
 #include "part_internal.cuh"
@@ -24,7 +26,7 @@
 namespace {
 
 constexpr int kT = kPushThreads;
-constexpr int kM = 2048;  // particles per super-chunk
+constexpr int kM = 512;   // particles per super-chunk
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -158,7 +160,7 @@ __device__ __forceinline__ void move_axis(float& off, int& j, float dv, int n) {
 }
 
 template <int SHAPE, int DIM, bool DEP>
-__global__ void __launch_bounds__(kT, 2)
+__global__ void __launch_bounds__(kT, 3)
     k_boris_brick_mixed(const __grid_constant__ CUtensorMap tmap, const Geo g,
                         const int32_t* cells, const float* offs, const float* us,
                         const float* w, const uint64_t* ids, int32_t* cell, float* off,
@@ -328,20 +330,22 @@ __global__ void __launch_bounds__(kT, 2)
     }
     if (!DEP) continue;
     __syncthreads();
-    // ---- B: one thread per source cell of this super-chunk, then 27 ordered
-    // passes
+    // ---- B: one thread per (source cell, component) of this super-chunk
+    // sums its particles' 27 contributions, then 27 (3^dim) ordered passes
     const int hz = DIM == 3 ? 1 : 0;
     while (scs[cfirst + 1] <= sb) ++cfirst;
     int clast = cfirst;
     while (clast + 1 < g.V && scs[clast + 1] < se) ++clast;
-    for (int c0 = cfirst; c0 <= clast; c0 += kT) {
-      const int ls = c0 + tid;
-      float T[27][3];
+    constexpr int CB = kT / 3;  // cells per batch
+    const int comp = tid % 3;
+    for (int c0 = cfirst; c0 <= clast; c0 += CB) {
+      const int ls = c0 + tid / 3;
+      float T[27];
 #pragma unroll
-      for (int k = 0; k < 27; ++k) T[k][0] = T[k][1] = T[k][2] = 0.0f;
+      for (int k = 0; k < 27; ++k) T[k] = 0.0f;
       bool any = false;
       int lx = 0, ly = 0, lz = 0;
-      if (ls <= clast) {
+      if (tid < 3 * CB && ls <= clast) {
         lx = ls % g.b[0];
         ly = (ls / g.b[0]) % g.b[1];
         lz = ls / (g.b[0] * g.b[1]);
@@ -354,37 +358,29 @@ __global__ void __launch_bounds__(kT, 2)
           shape_weights<SHAPE>(rd[i], wx);
           shape_weights<SHAPE>(rd[kM + i], wy);
           if (DIM == 3) shape_weights<SHAPE>(rd[2 * kM + i], wz);
-          const float F0 = rF[i], F1 = rF[kM + i], F2 = rF[2 * kM + i];
+          const float Fc = rF[comp * kM + i];
 #pragma unroll
           for (int kz = 0; kz < 3; ++kz)
 #pragma unroll
             for (int ky = 0; ky < 3; ++ky) {
               const float wzy = wz[kz] * wy[ky];
 #pragma unroll
-              for (int kx = 0; kx < 3; ++kx) {
-                const float ww = wzy * wx[kx];
-                const int k = (kz * 3 + ky) * 3 + kx;
-                T[k][0] += ww * F0;
-                T[k][1] += ww * F1;
-                T[k][2] += ww * F2;
-              }
+              for (int kx = 0; kx < 3; ++kx) T[(kz * 3 + ky) * 3 + kx] += (wzy * wx[kx]) * Fc;
             }
           any = true;
         }
       }
 #pragma unroll
-      for (int kz = 0; kz < 3; ++kz)
+      for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz)
 #pragma unroll
         for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
           for (int kx = 0; kx < 3; ++kx) {
-            const int k = (kz * 3 + ky) * 3 + kx;
-            if (any && (DIM == 3 || kz == 1)) {
+            if (any) {
               const int ex = lx + kx, ey = ly + ky, ez = lz + hz + (kz - 1);
               const int t = (ez * g.e[1] + ey) * g.e[0] + ex;
-#pragma unroll
-              for (int c = 0; c < 3; ++c)
-                two_sum_add(&ahi[c * g.ev + t], &alo[c * g.ev + t], T[k][c]);
+              two_sum_add(&ahi[comp * g.ev + t], &alo[comp * g.ev + t],
+                          T[(kz * 3 + ky) * 3 + kx]);
             }
             __syncthreads();
           }
