@@ -322,3 +322,33 @@ def test_resort_falls_back_after_a_long_move():
         p.sync()
         perm = O.stable_sort(O.keys(og, p.brick, xb))
         assert np.array_equal(_host(idd), ib[perm])
+
+
+def test_flush_brings_the_sorted_state_home():
+    """After a sort and a push the current state may live in the workspace
+    copy; part_flush (asynchronous) puts it into the bound arrays, sorted, and
+    gives what part_sync gives."""
+    og, pg = _grids(3, 16)
+    N = 16 ** 3 * 4 + 3
+    x, u, w, ids = synth.particles(3, None, N, 21, u_th=0.5)
+    f = synth.em_fields(3, 16, 4, v_rms=0.05).reshape(6, -1)
+    runs = []
+    for use_flush in (True, False):
+        p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=N)
+        p.set_fields(_dev(f))
+        xd, ud = _dev(x), _dev(u)
+        idd = torch.as_tensor(ids.astype(np.int64)).cuda()
+        p.bind(N, xd, u=ud, ids=idd)
+        for _ in range(3):                       # odd number: state ends in the other copy
+            p.sort()
+            p.gather_push(1.0, 0.5 * 2.0 / 16, 1)
+        if use_flush:
+            p.flush()
+            torch.cuda.synchronize()
+        else:
+            p.sync()
+        runs.append((_host(xd), _host(ud), _host(idd)))
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+    # ids are a permutation of the originals (nothing lost or duplicated)
+    assert np.array_equal(np.sort(runs[0][2]), np.arange(N))
