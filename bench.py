@@ -554,6 +554,18 @@ def run_e2e(torch, wl: BorisWorkload, K: int):
 
 
 # ----------------------------------------------------------------------------- oracle
+def headline_config(grid: int, particles: int, dt: float, world: int) -> dict:
+    """The `config` object of the headline line (both arms)."""
+    return {"workload": "3D periodic 128^3, B = z + turbulent dB (64 Kolmogorov modes, "
+                        "dB/B0 = 1), E = -v x B (solenoidal v, rms 0.01 c), "
+                        "16,777,216 particles (8/cell), u_th = 0.1, step = sort + "
+                        "Boris/TSC gather + TSC force deposit, FP64",
+            "particles": particles, "grid": [grid] * 3, "dt": dt,
+            "l2": "inputs larger than L2 (about 2 GB of state, fields and deposit "
+                  "touched per step vs 126 MB L2); no flush",
+            "parallelism": f"replicas x{world}"}
+
+
 def cpu_baseline(budget_s: float = 12.0, n=128, seed=1236):
     """The oracle as it stands (OpenMP over particles in the push; sort and
     deposit sequential), one step = keys + stable sort + permute + Boris step
@@ -587,7 +599,7 @@ def cpu_baseline(budget_s: float = 12.0, n=128, seed=1236):
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": Ns * steps / el, "unit": "particle-steps/s", "cores": cores,
-            "kind": "oracle",
+            "kind": "oracle", "dt": dt,
             "sample": f"{Ns} of the 16,777,216 particles of the 128^3 workload, {steps} "
                       f"steps (keys, stable sort, permute, Boris step, deposit), {el:.1f} s"}
 
@@ -597,12 +609,12 @@ def reference_arm(args):
     if rank != 0:
         return 0
     cb = cpu_baseline(budget_s=max(5.0, 4.0 * args.steps / max(args.steps, 1)))
+    N = 128 ** 3 * 8
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"],
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "3D periodic 128^3 turbulent B, E=-vxB, 16,777,216 "
-                                   "particles (8/cell), Boris + TSC gather + TSC deposit, "
-                                   "FP64 (oracle, host cores, bounded sample)"},
+            "ms_per_step": N / cb["value"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "dtype": "f64", "data": "synthetic",
+            "config": headline_config(128, N, cb["dt"], 1),
             "cpu_baseline": {"value": cb["value"], "unit": cb["unit"], "cores": cb["cores"],
                              "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
@@ -704,14 +716,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "3D periodic 128^3, B = z + turbulent dB (64 Kolmogorov modes, "
-                               "dB/B0 = 1), E = -v x B (solenoidal v, rms 0.01 c), "
-                               "16,777,216 particles (8/cell), u_th = 0.1, step = sort + "
-                               "Boris/TSC gather + TSC force deposit, FP64",
-                   "particles": wl.N, "grid": [args.grid] * 3, "dt": wl.dt,
-                   "l2": "inputs larger than L2 (about 2 GB of state, fields and deposit "
-                         "touched per step vs 126 MB L2); no flush",
-                   "parallelism": f"replicas x{world}"},
+        "config": headline_config(args.grid, wl.N, wl.dt, world),
         "roofline": {"bound": "alu", "kernel": "k_boris_brick_f64_dep (TSC, 3D, warp-specialised push + deposit)",
                      "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tf / FP64_NOMINAL_TFLOPS,
@@ -766,7 +771,9 @@ def main():
         except Exception as e:
             line["serving"] = {"error": repr(e)}
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline()
+        cb = cpu_baseline()
+        cb.pop("dt", None)
+        line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
