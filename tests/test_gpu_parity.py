@@ -352,3 +352,56 @@ def test_flush_brings_the_sorted_state_home():
         assert np.array_equal(a, b)
     # ids are a permutation of the originals (nothing lost or duplicated)
     assert np.array_equal(np.sort(runs[0][2]), np.arange(N))
+
+
+def test_pipeline_sort_push_compact_deposit():
+    """A run mixing the paths: full sort, pushes with incremental sorts,
+    compaction (full sort after it), and a deposit, against the oracle doing
+    the same operations on its own copy (stable sort of the keys, Boris step,
+    the compaction map)."""
+    n = 16
+    og, pg = _grids(3, n)
+    N = n ** 3 * 4 + 9
+    x, u, w, ids = synth.particles(3, None, N, 44, u_th=0.8)
+    w = np.random.default_rng(2).uniform(0.5, 2.0, N)
+    f = synth.em_fields(3, n, 9, v_rms=0.05).reshape(6, -1)
+    p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=N)
+    p.set_fields(_dev(f))
+    xd, ud, wd = _dev(x), _dev(u), _dev(w)
+    idd = torch.as_tensor(ids.astype(np.int64)).cuda()
+    p.bind(N, xd, u=ud, w=wd, ids=idd)
+    dt = 0.7 * 2.0 / n
+    xr, ur, wr, ir = x.copy(), u.copy(), w.copy(), ids.astype(np.int64)
+
+    def oracle_sort():
+        nonlocal xr, ur, wr, ir
+        perm = O.stable_sort(O.keys(og, p.brick, xr))
+        xr, ur, wr, ir = xr[:, perm], ur[:, perm], wr[perm], ir[perm]
+
+    for step in range(4):
+        p.sort()
+        oracle_sort()
+        p.gather_push(1.0, dt, 1)
+        xr, ur, _, _ = O.boris_step(og, P.TSC, f, xr, ur, wr, 1.0, dt)
+        if step == 1:                            # delete a fifth of the particles
+            p.sync()
+            d = np.random.default_rng(7).random(xr.shape[1]) < 0.2
+            nn = p.compact(torch.as_tensor(d.astype(np.uint8)).cuda())
+            k, src = O.compact_map(d)
+            assert nn == k
+            xr, ur, wr, ir = xr[:, src], ur[:, src], wr[src], ir[src]
+    p.enable_deposit(True)
+    p.sort()
+    oracle_sort()
+    p.gather_push(1.0, dt, 1)
+    out = torch.empty((3, n ** 3), dtype=torch.float64, device="cuda")
+    p.deposit(out)
+    p.sync()
+    x1, u1, F, xo = O.boris_step(og, P.TSC, f, xr, ur, wr, 1.0, dt, True)
+    k = xr.shape[1]
+    assert np.array_equal(_host(idd)[:k], ir)
+    assert np.max(np.abs(_pdiff(_host(xd).reshape(-1)[:3 * k].reshape(3, k), x1))) <= 1e-11
+    assert _rel(_host(ud).reshape(-1)[:3 * k].reshape(3, k), u1, 1e-3) <= 1e-11
+    dref = O.deposit(og, P.TSC, xo, F)
+    dabs = O.deposit(og, P.TSC, xo, np.abs(F))
+    assert np.max(np.abs(_host(out) - dref) / np.maximum(dabs, 1e-300)) <= 1e-11

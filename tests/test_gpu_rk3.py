@@ -138,3 +138,43 @@ def test_lp_order_errors():
             p.set_lp_order(bad)
     p.set_lp_order(3)
     p.set_lp_order(2)
+
+
+def test_rk3_with_shocks_matches_oracle():
+    """SSP-RK3 advection with the shock update on the stationary shock."""
+    n, N, nb = 40, 2001, 64
+    r = 40.0 / 11.0
+    og = O.make_grid(2, (n, n, n))
+    xc = -1.0 + (np.arange(n) + 0.5) * (2.0 / n)
+    down = np.broadcast_to(xc[None, :] > 0.0, (n, n)).reshape(-1)
+    f7 = np.zeros((7, n * n))
+    f7[0] = np.where(down, 0.1 / r, 0.1)
+    f7[3] = np.where(down, 50.0 * r, 50.0)
+    f7[4] = 1.0
+    rng = np.random.default_rng(12)
+    x = np.zeros((3, N))
+    x[0] = rng.uniform(-0.12, 0.02, N)
+    x[1] = rng.uniform(-1.0, 1.0, N)
+    lp = LP(2, n, f7, x, nb=nb, order=3)
+    e1, c1 = O.init_spectrum(nb, 1e2, 1e4, 9.0, 1e-6)
+    eng, chi = np.repeat(e1[:, None], N, 1), np.repeat(c1[:, None], N, 1)
+    no = np.array([O.gather(og, P.TSC, f7[3:4], x[:, i])[0] for i in range(N)])
+    lp.eng.copy_(torch.as_tensor(eng))
+    lp.chi.copy_(torch.as_tensor(chi))
+    lp.nold.copy_(torch.as_tensor(no))
+    st = torch.zeros(N, dtype=torch.uint8, device="cuda")
+    lp.p.enable_shocks(1.5, st)
+    rc = O.shock_cells(og, f7[:3], f7[3:4], 1.5)
+    sr = np.zeros(N, np.uint8)
+    dt = 0.5 * (2.0 / n) / 0.1
+    for _ in range(2):
+        lp.p.gather_push(0.0, dt, 1)
+        lp.p.spec_update(dt, 1e-6, 0.0)
+        x, nn, b2, gm = O.lp_rk3_step(og, P.TSC, f7[:3], f7[3:4], f7[4:], x, dt)
+        chi, eng, no = O.spec_update(chi, eng, no, nn, b2, gm, dt, 1e-6)
+        chi, sr = O.lp_shock(og, rc, x, chi, eng, sr)
+    lp.p.sync()
+    assert int(sr.sum()) > 100
+    assert np.array_equal(_host(st), sr)
+    assert np.max(np.abs(_host(lp.x) - x)) <= 1e-12
+    assert np.max(np.abs(_host(lp.chi) - chi) / np.maximum(np.abs(chi), 1e-300)) <= 1e-12
