@@ -8,8 +8,11 @@
 // incremental: after a push that moved every particle by less than a cell,
 //         a per-brick stable counting sort over the brick's own and adjacent
 //         old cells replaces the radix passes (same permutation).
-// permute: every bound array is gathered through the permutation into the
-//         scratch buffer and copied back (in-place semantics for the caller).
+// permute: Boris modes leave the permutation to the next brick push, which
+//         reads the current copy of the state through it and writes the
+//         other copy (apply_perm does the same gather when no push follows);
+//         LP mode gathers each bound array through the scratch row and copies
+//         it back.
 // cell_start: cs[k] = first sorted particle with key >= k, k in [0, nkeys].
 #include <algorithm>
 #include "part_internal.cuh"
@@ -243,9 +246,9 @@ __global__ void k_cell_start(const uint32_t* __restrict__ sk, int64_t n, int64_t
   }
 }
 
-// One pass over the permutation: every bound plane of particle perm[i] is
-// copied to slot i of the alternate buffers.  NP double/float planes of the
-// position-like arrays are handled by the caller's choice of template.
+// One pass over the permutation: every bound plane of particle perm[i] of one
+// copy of the state is written to slot i of the other copy.  NX planes of the
+// position-like array (3 doubles, or 1 int32 cell) by the template.
 template <typename TX, int NX, typename TV>
 __global__ void k_gather_state(const TX* __restrict__ x, const float* __restrict__ off,
                                const TV* __restrict__ u, const TV* __restrict__ w,
@@ -691,7 +694,7 @@ cudaError_t launch_sort_incremental(part_ctx* c) {
 
 namespace {
 
-// Permute every bound array by perm (Boris modes: into the alternate buffers).
+// Permute every bound array by perm (Boris modes: only recorded, see above).
 cudaError_t permute_all(part_ctx* c, const uint32_t* perm) {
   const int64_t n = c->n;
   cudaStream_t s = c->stream;
