@@ -4,15 +4,18 @@
  * The library advances particles on a periodic Cartesian grid, one CUDA
  * stream per context:
  *   - Lagrangian particles (LPs): advection with the fluid velocity (Eq. push,
- *     Sec. 2) by a two-stage Runge-Kutta step (Sec. 3.3, Table codeTiming:
- *     Particles_RK#1 / Particles_RK#2), and the per-particle energy-spectrum
- *     update of Eq. cr_chi (Sec. 2; Particles_Spectra in Table codeTiming);
+ *     Sec. 2) by a two- or three-stage Runge-Kutta step (Sec. 3.3, Table
+ *     codeTiming: Particles_RK#1 / Particles_RK#2; Sec. 4.1.1), the
+ *     per-particle energy-spectrum update of Eq. cr_chi (Sec. 2;
+ *     Particles_Spectra in Table codeTiming) and, at shocks, the diffusive
+ *     shock acceleration of Eq. convolution_spectra with Eq. slope;
  *   - charged test/cosmic-ray particles: relativistic Boris push with fields
  *     gathered by TSC or CIC weights, and the deposit of the particle force
  *     density back onto the grid (the MHD-PIC coupling named in Sec. 1).
  * Particles are stored as structures of arrays (Sec. 3.2, "Ensure coalesced
  * access to memory"), with the record of Appendix A (pos, speed, chi[nb],
- * eng[nb], id).
+ * eng[nb], id); deleted particles are removed by the hole/filler compaction
+ * of Sec. 3.2 (part_compact).
  *
  * Conventions (all entry points):
  *   - Every call returns a part_status and never aborts.  Argument errors are
