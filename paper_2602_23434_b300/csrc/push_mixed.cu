@@ -359,13 +359,15 @@ __global__ void __launch_bounds__(kT, 3)
           shape_weights<SHAPE>(rd[kM + i], wy);
           if (DIM == 3) shape_weights<SHAPE>(rd[2 * kM + i], wz);
           const float Fc = rF[comp * kM + i];
+          const float wxF[3] = {wx[0] * Fc, wx[1] * Fc, wx[2] * Fc};
 #pragma unroll
-          for (int kz = 0; kz < 3; ++kz)
+          for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz)
 #pragma unroll
             for (int ky = 0; ky < 3; ++ky) {
               const float wzy = wz[kz] * wy[ky];
 #pragma unroll
-              for (int kx = 0; kx < 3; ++kx) T[(kz * 3 + ky) * 3 + kx] += (wzy * wx[kx]) * Fc;
+              for (int kx = 0; kx < 3; ++kx)
+                T[(kz * 3 + ky) * 3 + kx] = fmaf(wzy, wxF[kx], T[(kz * 3 + ky) * 3 + kx]);
             }
           any = true;
         }
