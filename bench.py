@@ -781,6 +781,9 @@ def main():
             line["mixed_128"] = mx
             line["mixed_256"] = run_mixed(torch, P, 256, 8, max(5, args.steps // 2), 3, 1237)
             line["mixed_error_vs_fp64"] = mixed_error_vs_fp64(torch, P)
+            # the stated case: 256^3, 134M particles, 200 steps
+            line["mixed_error_vs_fp64_256"] = mixed_error_vs_fp64(torch, P, n=256, steps=200,
+                                                                  seed=1237)
         except Exception as e:
             line["mixed"] = {"error": repr(e)}
         try:
