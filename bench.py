@@ -609,6 +609,15 @@ def cpu_baseline(budget_s: float = 12.0, n=128, seed=1236):
         O.deposit(g, O.TSC, xo, F)
         return x1, u1, w
 
+    # one host thread first, on a small sample
+    cores = O.max_threads()
+    O.set_threads(1)
+    N1 = 1 << 16
+    x, u, w, _ = O.init_particles(g, N1, seed, 0.1)
+    t0 = time.perf_counter()
+    one_step(x, u, w)
+    e1 = time.perf_counter() - t0
+    O.set_threads(cores)
     Ns = 1 << 16
     x, u, w, _ = O.init_particles(g, Ns, seed, 0.1)
     t0 = time.perf_counter()
@@ -622,9 +631,10 @@ def cpu_baseline(budget_s: float = 12.0, n=128, seed=1236):
     for _ in range(steps):
         x, u, w = one_step(x, u, w)
     el = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": Ns * steps / el, "unit": "particle-steps/s", "cores": cores,
             "kind": "oracle", "dt": dt,
+            "single_thread": {"value": N1 / e1, "unit": "particle-steps/s",
+                              "sample": f"{N1} particles, 1 step"},
             "sample": f"{Ns} of the 16,777,216 particles of the 128^3 workload, {steps} "
                       f"steps (keys, stable sort, permute, Boris step, deposit), {el:.1f} s"}
 

@@ -99,6 +99,8 @@ def lib():
                                          _U64]),
             "or_compact_map": (C.c_int64, [C.c_int64, C.POINTER(C.c_uint8),
                                            C.POINTER(C.c_int64)]),
+            "or_set_threads": (None, [C.c_int]),
+            "or_max_threads": (C.c_int, []),
             "or_rh_compression": (C.c_double, [C.c_double, C.c_double]),
             "or_dsa_index": (C.c_double, [C.c_double]),
             "or_shock_cells": (None, [G, _D, _D, C.c_double, _D]),
@@ -317,3 +319,12 @@ def lp_shock(g: Grid, r_cell, x, chi, eng, state):
     lib().or_lp_shock(C.byref(g), _d(_f64(r_cell)), nb, n, _d(_f64(x)), _d(chi),
                       _d(_f64(eng)), st.ctypes.data_as(C.POINTER(C.c_uint8)))
     return chi, st
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's parallel loops (timing only)."""
+    lib().or_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())

@@ -14,6 +14,7 @@
  */
 #include "part_oracle.h"
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -532,3 +533,8 @@ void or_lp_shock(const or_grid* g, const double* r_cell, int nb, int64_t n, cons
     free(e); free(ci); free(co);
   }
 }
+
+/* Threads the OpenMP loops above may use (timing runs; results do not depend
+ * on it: every parallel loop writes disjoint particles). */
+void or_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int or_max_threads(void) { return omp_get_max_threads(); }

@@ -106,4 +106,7 @@ void or_shock_convolve(int nb, const double* eng, const double* chi_in, double q
 /* shock update of n LP spectra at positions x; state[n] = inside a shock cell */
 void or_lp_shock(const or_grid* g, const double* r_cell, int nb, int64_t n, const double* x,
                  double* chi, const double* eng, uint8_t* state);
+/* OpenMP thread count of the loops above (timing only) */
+void or_set_threads(int n);
+int or_max_threads(void);
 #endif
