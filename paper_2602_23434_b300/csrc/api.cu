@@ -78,6 +78,11 @@ void make_geo(const part_grid* gr, int esize, Geo* g) {
   g->box[1] = g->b[1] + 2 * g->h[1];
   g->box[2] = g->b[2] + 2 * g->h[2];
   g->V = g->b[0] * g->b[1] * g->b[2];
+  for (int a = 0; a < 3; ++a) {
+    g->bshift[a] = 0;
+    while ((1 << g->bshift[a]) < g->b[a]) ++g->bshift[a];
+  }
+  g->vshift = g->bshift[0] + g->bshift[1] + g->bshift[2];
   g->ev = g->e[0] * g->e[1] * g->e[2];
   g->G = (int64_t)g->n[0] * g->n[1] * g->n[2];
   g->nbricks = (int64_t)g->nb[0] * g->nb[1] * g->nb[2];

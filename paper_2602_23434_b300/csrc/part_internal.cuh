@@ -46,6 +46,8 @@ struct Geo {
   int64_t pplane;  // padded elements per field component
   double xmin[3], dx[3], inv_dx[3], L[3], xmax[3];
   float invn[3];   // 1/n per axis, for the float-reciprocal cell decode
+  int bshift[3];   // log2 b per axis (brick sides are powers of two)
+  int vshift;      // log2 V
 };
 
 // Every member has a default initializer: a context built on the stack (the
@@ -194,6 +196,35 @@ __device__ __forceinline__ int floor_clamp_bits(double s, int hi) {
   const long long m = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
   const int j = (int)(m >> (52 - e));
   return j > hi ? hi : j;
+}
+
+// q = c / n, r = c % n for 0 <= c < 2^24 by a float reciprocal and one exact
+// integer correction (the float quotient is within 1 of the true one).
+__device__ __forceinline__ int divmod_f(int c, int n, float invn, int* r) {
+  int q = (int)(__int2float_rn(c) * invn);
+  int rr = c - q * n;
+  if (rr < 0) {
+    --q;
+    rr += n;
+  } else if (rr >= n) {
+    ++q;
+    rr -= n;
+  }
+  *r = rr;
+  return q;
+}
+
+// Cell coordinates of a linear cell index c = (jz n1 + jy) n0 + jx.
+__device__ __forceinline__ void cell_coords(const Geo& g, int32_t c, int* j) {
+  if (g.G <= (1 << 24) && c >= 0) {
+    const int r = divmod_f(c, g.n[0], g.invn[0], &j[0]);
+    j[2] = divmod_f(r, g.n[1], g.invn[1], &j[1]);
+  } else {
+    j[0] = c % g.n[0];
+    const int r = c / g.n[0];
+    j[1] = r % g.n[1];
+    j[2] = r / g.n[1];
+  }
 }
 
 // ---------------------------------------------------------------- shape weights

@@ -112,34 +112,6 @@ __device__ __forceinline__ void two_sum_add(float* hi, float* lo, float x) {
   *lo += err;
 }
 
-// q = c / n, r = c % n for 0 <= c < 2^24 by a float reciprocal and one exact
-// integer correction (the float quotient is within 1 of the true one).
-__device__ __forceinline__ int divmod_f(int c, int n, float invn, int* r) {
-  int q = (int)(__int2float_rn(c) * invn);
-  int rr = c - q * n;
-  if (rr < 0) {
-    --q;
-    rr += n;
-  } else if (rr >= n) {
-    ++q;
-    rr -= n;
-  }
-  *r = rr;
-  return q;
-}
-
-__device__ __forceinline__ void cell_coords(const Geo& g, int32_t c, int* j) {
-  if (g.G <= (1 << 24) && c >= 0) {
-    const int r = divmod_f(c, g.n[0], g.invn[0], &j[0]);
-    j[2] = divmod_f(r, g.n[1], g.invn[1], &j[1]);
-  } else {
-    j[0] = c % g.n[0];
-    const int r = c / g.n[0];
-    j[1] = r % g.n[1];
-    j[2] = r / g.n[1];
-  }
-}
-
 // Stencil point accumulate: six field components of one cell (two 16-byte
 // loads of the cell-interleaved copy) weighted by ww, as three paired FMAs.
 __device__ __forceinline__ void acc_point(float2* f, float ww, float4 a, float4 b) {

@@ -19,11 +19,13 @@
 
 namespace {
 
+// Brick sides are powers of two (8^3, 16^2), so the split is by shifts.
 __device__ __forceinline__ uint32_t brick_key(const Geo& g, int jx, int jy, int jz) {
-  int bx = jx / g.b[0], by = jy / g.b[1], bz = jz / g.b[2];
-  int lx = jx - bx * g.b[0], ly = jy - by * g.b[1], lz = jz - bz * g.b[2];
-  int64_t brick = ((int64_t)bz * g.nb[1] + by) * g.nb[0] + bx;
-  return (uint32_t)(brick * g.V + (lz * g.b[1] + ly) * g.b[0] + lx);
+  const int bx = jx >> g.bshift[0], by = jy >> g.bshift[1], bz = jz >> g.bshift[2];
+  const int lx = jx & (g.b[0] - 1), ly = jy & (g.b[1] - 1), lz = jz & (g.b[2] - 1);
+  const uint32_t brick = (uint32_t)((bz * g.nb[1] + by) * g.nb[0] + bx);
+  return (brick << g.vshift) |
+         (uint32_t)((((lz << g.bshift[1]) | ly) << g.bshift[0]) | lx);
 }
 
 __device__ __forceinline__ int cell_of(const Geo& g, int a, double xa, int* status) {
@@ -52,16 +54,14 @@ __global__ void k_keys_cell(const int32_t* __restrict__ cell, int64_t n, Geo g,
                             int* status) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t c = cell[i];
+    int32_t c = cell[i];
     if (c < 0 || c >= g.G) {
       atomicOr(status, ST_DOMAIN);
-      c = c < 0 ? 0 : g.G - 1;
+      c = c < 0 ? 0 : (int32_t)(g.G - 1);
     }
-    int jx = (int)(c % g.n[0]);
-    int64_t r = c / g.n[0];
-    int jy = (int)(r % g.n[1]);
-    int jz = (int)(r / g.n[1]);
-    keys[i] = brick_key(g, jx, jy, jz);
+    int j[3];
+    cell_coords(g, c, j);
+    keys[i] = brick_key(g, j[0], j[1], j[2]);
     vals[i] = (uint32_t)i;
   }
 }
@@ -355,13 +355,14 @@ __global__ void __launch_bounds__(kIncT)
     if (i < s1) {
       uint32_t key;
       if (CELL) {
-        int64_t c = ((const int32_t*)xv)[i];
+        int32_t c = ((const int32_t*)xv)[i];
         if (c < 0 || c >= g.G) {
           atomicOr(status, ST_DOMAIN);
-          c = c < 0 ? 0 : g.G - 1;
+          c = c < 0 ? 0 : (int32_t)(g.G - 1);
         }
-        key = brick_key(g, (int)(c % g.n[0]), (int)((c / g.n[0]) % g.n[1]),
-                        (int)(c / ((int64_t)g.n[0] * g.n[1])));
+        int jc[3];
+        cell_coords(g, c, jc);
+        key = brick_key(g, jc[0], jc[1], jc[2]);
       } else {
         const double* x = (const double*)xv;
         int j[3] = {0, 0, 0};
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(kIncT)
         key = brick_key(g, j[0], j[1], j[2]);
       }
       keys[i] = key;
-      slot = inc_lookup(nid, (uint32_t)ob, key / (uint32_t)g.V);
+      slot = inc_lookup(nid, (uint32_t)ob, (key >> g.vshift));
       if (slot < 0) {
         atomicOr(status, ST_DOMAIN);
         slot = 27;
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(kIncT)
     const uint32_t i = c0 + tid;
     const bool valid = i < s1;
     const uint32_t key = valid ? keys[i] : 0u;
-    int slot = valid ? inc_lookup(nid, (uint32_t)ob, key / (uint32_t)g.V) : 27;
+    int slot = valid ? inc_lookup(nid, (uint32_t)ob, (key >> g.vshift)) : 27;
     if (slot < 0) slot = 27;  // moved too far: reported by the count pass
     const uint32_t peers = __match_any_sync(0xffffffffu, (uint32_t)slot);
     const uint32_t rank = __popc(peers & lt);
@@ -459,11 +460,11 @@ __global__ void __launch_bounds__(kIncT)
     }
     __syncthreads();
     if (slot < 27) {
-      const uint32_t db = key / (uint32_t)g.V;
+      const uint32_t db = (key >> g.vshift);
       const uint64_t pos = (uint64_t)bbase[db] + start[ob * 27 + slot] + wc[warp][slot] + rank;
       if (pos < (uint64_t)n) {
         memb[pos] = i;
-        mlc[pos] = key % (uint32_t)g.V;
+        mlc[pos] = (key & (uint32_t)(g.V - 1));
       }
     }
     __syncthreads();
