@@ -462,13 +462,51 @@ __global__ void __launch_bounds__(256)
 // out[c][g] = sum over the bricks whose haloed tile covers cell g (or one of
 // its periodic images), in fixed (z, y, x, image) order, of their partials.
 __global__ void __launch_bounds__(256)
-    k_dep_combine(const double* __restrict__ dpart, double* __restrict__ out, const Geo g) {
+    k_dep_combine(const double* __restrict__ dpart, double* __restrict__ out, const Geo g,
+                  bool fast) {
   for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < g.G;
        gi += (int64_t)gridDim.x * blockDim.x) {
     int j[3];
     j[0] = (int)(gi % g.n[0]);
     j[1] = (int)((gi / g.n[0]) % g.n[1]);
     j[2] = (int)(gi / ((int64_t)g.n[0] * g.n[1]));
+    if (fast) {
+      // full bricks and at least three per active axis: the cell is in its
+      // own brick's tile, and in one neighbour's halo when it is on a face
+      // of its brick (previous brick first, as in the general order below)
+      int cb[3][3], ce[3][3], cnt[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int bj = j[a] >> g.bshift[a], l = j[a] & (g.b[a] - 1);
+        cnt[a] = 0;
+        if (g.h[a] != 0 && l == 0) {
+          cb[a][cnt[a]] = bj == 0 ? g.nb[a] - 1 : bj - 1;
+          ce[a][cnt[a]++] = g.b[a] + 1;
+        }
+        cb[a][cnt[a]] = bj;
+        ce[a][cnt[a]++] = l + g.h[a];
+        if (g.h[a] != 0 && l == g.b[a] - 1) {
+          cb[a][cnt[a]] = bj == g.nb[a] - 1 ? 0 : bj + 1;
+          ce[a][cnt[a]++] = 0;
+        }
+      }
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+      for (int qz = 0; qz < cnt[2]; ++qz)
+        for (int qy = 0; qy < cnt[1]; ++qy)
+          for (int qx = 0; qx < cnt[0]; ++qx) {
+            const int64_t br =
+                ((int64_t)cb[2][qz] * g.nb[1] + cb[1][qy]) * g.nb[0] + cb[0][qx];
+            const int t = (ce[2][qz] * g.e[1] + ce[1][qy]) * g.e[0] + ce[0][qx];
+            const double* pp = dpart + br * 3 * g.ev + t;
+            s0 += pp[0];
+            s1 += pp[g.ev];
+            s2 += pp[2 * (int64_t)g.ev];
+          }
+      out[gi] = s0;
+      out[g.G + gi] = s1;
+      out[2 * g.G + gi] = s2;
+      continue;
+    }
     int cb[3][9], ce[3][9], cnt[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -576,7 +614,11 @@ cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps) {
 }
 
 cudaError_t launch_deposit_combine(part_ctx* c, double* out) {
-  k_dep_combine<<<grid_for(c->geo.G, 256), 256, 0, c->stream>>>(c->dpart, out, c->geo);
+  const Geo& g = c->geo;
+  bool fast = true;
+  for (int a = 0; a < 3; ++a)
+    if (g.h[a] != 0 && (g.nb[a] < 3 || g.n[a] % g.b[a] != 0)) fast = false;
+  k_dep_combine<<<grid_for(g.G, 256), 256, 0, c->stream>>>(c->dpart, out, g, fast);
   c->launches++;
   return cudaGetLastError();
 }
