@@ -195,9 +195,9 @@ def test_mixed_drift_1000_steps(E):
     assert egy.max() <= 1e-6
 
 
-def test_mixed_resort_after_push_bit_exact():
+@pytest.mark.parametrize("dim,n,ppc", [(3, 20, 8), (2, 40, 16), (3, 24, 2)])
+def test_mixed_resort_after_push_bit_exact(dim, n, ppc):
     """The incremental sort on the mixed form (cells moved by the push)."""
-    dim, n, ppc = 3, 20, 8
     og = O.make_grid(dim, (n, n, n))
     N, cell, off, uf, wf, ids = _state(dim, n, ppc, 9, u_th=2.0)
     f = synth.em_fields(dim, n, 3, v_rms=0.05).reshape(6, -1)
