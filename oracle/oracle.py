@@ -39,11 +39,12 @@ def build(force: bool = False) -> str:
 
 class Grid(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3),
-                ("xmin", C.c_double * 3), ("dx", C.c_double * 3)]
+                ("xmin", C.c_double * 3), ("dx", C.c_double * 3), ("open", C.c_int * 3)]
 
 
-def make_grid(dim: int, n, xmin=(-1.0, -1.0, -1.0), dx=None) -> Grid:
-    """Grid on [xmin, xmin + n dx); default domain [-1, 1]^dim (Sec. 4.1)."""
+def make_grid(dim: int, n, xmin=(-1.0, -1.0, -1.0), dx=None, open_axes=(0, 0, 0)) -> Grid:
+    """Grid on [xmin, xmin + n dx); default domain [-1, 1]^dim (Sec. 4.1);
+    open_axes[a] = 1 makes axis a open (outflow) instead of periodic."""
     n = list(n) + [1] * (3 - len(n))
     if dim == 2:
         n[2] = 1
@@ -56,6 +57,7 @@ def make_grid(dim: int, n, xmin=(-1.0, -1.0, -1.0), dx=None) -> Grid:
         g.n[a] = int(n[a])
         g.xmin[a] = float(xmin[a])
         g.dx[a] = float(dx[a])
+        g.open[a] = int(open_axes[a])
     return g
 
 
@@ -100,6 +102,7 @@ def lib():
             "or_compact_map": (C.c_int64, [C.c_int64, C.POINTER(C.c_uint8),
                                            C.POINTER(C.c_int64)]),
             "or_set_threads": (None, [C.c_int]),
+            "or_outside": (C.c_int, [G, _D]),
             "or_max_threads": (C.c_int, []),
             "or_rh_compression": (C.c_double, [C.c_double, C.c_double]),
             "or_dsa_index": (C.c_double, [C.c_double]),
@@ -328,3 +331,10 @@ def set_threads(n: int) -> None:
 
 def max_threads() -> int:
     return int(lib().or_max_threads())
+
+
+def outside(g: Grid, x):
+    """Per particle: 1 if it lies outside the domain along an open axis."""
+    x = _f64(x)
+    return np.array([lib().or_outside(C.byref(g), _d(np.ascontiguousarray(x[:, i])))
+                     for i in range(x.shape[1])], dtype=np.uint8)

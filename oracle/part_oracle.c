@@ -32,12 +32,19 @@ double or_shape(int shape, double xi) {
 }
 
 /* Cell index j = floor((x - xmin) / dx) with 1/dx formed once; the upper edge
- * tie (rounding to j == n) goes to n-1.  delta = (s - j) - 1/2.             */
+ * tie (rounding to j == n) goes to n-1.  delta = (s - j) - 1/2.  On an open
+ * axis s is first clamped to [0, n]: beyond the boundary a particle samples
+ * (and deposits at) the boundary itself, which with the zero-gradient ghost
+ * layer below continues the edge values outwards.                          */
 void or_cell_coord(const or_grid* g, const double* x, int* j, double* delta) {
   for (int a = 0; a < 3; ++a) {
     if (a >= g->dim) { j[a] = 0; delta[a] = 0.0; continue; }
     double inv = 1.0 / g->dx[a];
     double s = (x[a] - g->xmin[a]) * inv;
+    if (g->open[a]) {
+      if (s < 0.0) s = 0.0;
+      if (s > (double)g->n[a]) s = (double)g->n[a];
+    }
     double f = floor(s);
     int jj = (int)f;
     if (jj >= g->n[a]) jj = g->n[a] - 1;
@@ -47,8 +54,10 @@ void or_cell_coord(const or_grid* g, const double* x, int* j, double* delta) {
   }
 }
 
-/* Periodic wrap by one domain length L = n dx into [xmin, xmin + L). */
+/* Periodic wrap by one domain length L = n dx into [xmin, xmin + L); an open
+ * axis is not wrapped. */
 double or_wrap(const or_grid* g, int axis, double x) {
+  if (g->open[axis]) return x;
   double L = (double)g->n[axis] * g->dx[axis];
   double xmax = g->xmin[axis] + L;
   if (x < g->xmin[axis]) x = x + L;
@@ -61,6 +70,23 @@ static int64_t cell_linear(const or_grid* g, int jx, int jy, int jz) {
 }
 
 static int pmod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+
+/* Neighbour index along an axis: periodic, or clamped to the edge cell on an
+ * open axis (a zero-gradient ghost layer; deposits there fold onto the edge
+ * cell, the exact adjoint of that gather). */
+static int nbr(const or_grid* g, int a, int j) {
+  if (!g->open[a]) return pmod(j, g->n[a]);
+  return j < 0 ? 0 : (j >= g->n[a] ? g->n[a] - 1 : j);
+}
+
+int or_outside(const or_grid* g, const double* x) {
+  for (int a = 0; a < g->dim; ++a) {
+    if (!g->open[a]) continue;
+    double L = (double)g->n[a] * g->dx[a];
+    if (x[a] < g->xmin[a] || x[a] >= g->xmin[a] + L) return 1;
+  }
+  return 0;
+}
 
 /* F(x_p) = sum_k W(k_x - d_x) W(k_y - d_y) W(k_z - d_z) f[j + k], periodic,
  * k in {-1,0,1}^dim, cell-centred fields [comp][z][y][x].                   */
@@ -78,8 +104,8 @@ void or_gather(const or_grid* g, int shape, const double* fields, int ncomp,
       for (int kx = -1; kx <= 1; ++kx) {
         double wx = or_shape(shape, kx - d[0]);
         double w = (wz * wy) * wx;
-        int64_t cell = cell_linear(g, pmod(j[0] + kx, g->n[0]), pmod(j[1] + ky, g->n[1]),
-                                   pmod(j[2] + kz, g->n[2]));
+        int64_t cell = cell_linear(g, nbr(g, 0, j[0] + kx), nbr(g, 1, j[1] + ky),
+                                   nbr(g, 2, j[2] + kz));
         for (int c = 0; c < ncomp; ++c) out[c] += w * fields[(int64_t)c * G + cell];
       }
     }
@@ -148,8 +174,8 @@ void or_deposit(const or_grid* g, int shape, int64_t n, const double* x,
         for (int kx = -1; kx <= 1; ++kx) {
           double wx = or_shape(shape, kx - d[0]);
           double w = (wz * wy) * wx;
-          int64_t cell = cell_linear(g, pmod(j[0] + kx, g->n[0]), pmod(j[1] + ky, g->n[1]),
-                                     pmod(j[2] + kz, g->n[2]));
+          int64_t cell = cell_linear(g, nbr(g, 0, j[0] + kx), nbr(g, 1, j[1] + ky),
+                                     nbr(g, 2, j[2] + kz));
           for (int c = 0; c < 3; ++c) out[(int64_t)c * G + cell] += w * F[(int64_t)c * n + p];
         }
       }
@@ -168,8 +194,8 @@ void or_deposit_cell(const or_grid* g, int shape, int64_t n, const double* x,
     for (int kz = kz0; kz <= kz1; ++kz) {
       for (int ky = -1; ky <= 1; ++ky) {
         for (int kx = -1; kx <= 1; ++kx) {
-          int64_t c0 = cell_linear(g, pmod(j[0] + kx, g->n[0]), pmod(j[1] + ky, g->n[1]),
-                                   pmod(j[2] + kz, g->n[2]));
+          int64_t c0 = cell_linear(g, nbr(g, 0, j[0] + kx), nbr(g, 1, j[1] + ky),
+                                   nbr(g, 2, j[2] + kz));
           if (c0 != cell) continue;
           double wz = g->dim == 3 ? or_shape(shape, kz - d[2]) : 1.0;
           double w = (wz * or_shape(shape, ky - d[1])) * or_shape(shape, kx - d[0]);
@@ -452,8 +478,8 @@ void or_shock_cells(const or_grid* g, const double* vel, const double* rho, doub
         double best = 0.0;
         for (int a = 0; a < g->dim; ++a) {
           int jp[3] = {jx, jy, jz}, jm[3] = {jx, jy, jz};
-          jp[a] = pmod(j[a] + 1, g->n[a]);
-          jm[a] = pmod(j[a] - 1, g->n[a]);
+          jp[a] = nbr(g, a, j[a] + 1);
+          jm[a] = nbr(g, a, j[a] - 1);
           int64_t cp = cell_linear(g, jp[0], jp[1], jp[2]);
           int64_t cm = cell_linear(g, jm[0], jm[1], jm[2]);
           double dv = vel[a * G + cp] - vel[a * G + cm];

@@ -33,6 +33,7 @@ typedef struct {
   int n[3];         /* cells per axis; n[2] == 1 when dim == 2            */
   double xmin[3];   /* lower domain corner                               */
   double dx[3];     /* cell width per axis                               */
+  int open[3];      /* 1: open (outflow) axis, 0: periodic               */
 } or_grid;
 
 enum { OR_CIC = 1, OR_TSC = 2 };
@@ -41,8 +42,11 @@ enum { OR_CIC = 1, OR_TSC = 2 };
 double or_shape(int shape, double xi);
 /* cell coordinate j and offset delta = s - j - 1/2 of position x, per axis */
 void or_cell_coord(const or_grid* g, const double* x, int* j, double* delta);
-/* wrap one coordinate periodically into [xmin, xmin + n dx) */
+/* wrap one coordinate periodically into [xmin, xmin + n dx); identity on an
+ * open axis */
 double or_wrap(const or_grid* g, int axis, double x);
+/* 1 if x lies outside the domain along an open axis (the particle has left) */
+int or_outside(const or_grid* g, const double* x);
 /* interpolate ncomp cell-centred fields [comp][z][y][x] at x */
 void or_gather(const or_grid* g, int shape, const double* fields, int ncomp,
                const double* x, double* out);

@@ -796,3 +796,79 @@ def test_shock_test_end_to_end_on_the_oracle():
         up = eng[:, p] >= eng[-1, p] / 10.0
         slope = -np.polyfit(np.log(eng[up, p]), np.log(chi[up, p]), 1)[0]
         assert abs(slope - (q - 2.0)) / (q - 2.0) <= e2["slope_rel_err"]
+
+
+# ---------------------------------------------------------------- open axes
+def _tsc_brute(fx, n, s):
+    """Brute-force TSC interpolation along one axis of a field given at cell
+    centres 0..n-1, extended by its edge values (zero gradient), at s in cell
+    units clamped to [0, n]: the quadratic B-spline summed over every cell."""
+    s = min(max(s, 0.0), float(n))
+    tot = 0.0
+    for k in range(-2, n + 2):
+        xi = abs((k + 0.5) - s)
+        w = 0.75 - xi * xi if xi <= 0.5 else (0.5 * (1.5 - xi) ** 2 if xi < 1.5 else 0.0)
+        tot += w * fx[min(max(k, 0), n - 1)]
+    return tot
+
+
+@pytest.mark.parametrize("shape", [O.TSC, O.CIC])
+def test_open_axis_uniform_field_everywhere(shape):
+    """With open x (and y) axes a uniform field is reproduced exactly at any
+    position, inside, on the boundary or beyond it."""
+    n = 8
+    g = O.make_grid(2, (n, n), open_axes=(1, 1, 0))
+    f = np.full((1, n * n), 3.25)
+    for px in (-1.3, -1.0, -0.99, 0.0, 0.999, 1.0, 1.4):
+        for py in (-1.05, 0.3, 1.2):   # y open too
+            assert abs(O.gather(g, shape, f, [px, py, 0.0])[0] - 3.25) < 1e-14
+
+
+def test_open_axis_zero_gradient_against_brute_force():
+    """Open x: the TSC gather of a field that varies along x equals the spline
+    sum over the field extended by its edge values, for positions near and
+    beyond both faces (y stays periodic and the field is constant in y)."""
+    n = 8
+    g = O.make_grid(2, (n, n), open_axes=(1, 0, 0))
+    fx = np.array([0.3, -1.2, 2.0, 0.7, 1.1, -0.4, 0.9, 2.6])
+    f = np.tile(fx, n)[None, :]
+    for px in (-1.2, -1.0, -0.97, -0.8, -0.3, 0.1, 0.74, 0.9, 0.99, 1.0, 1.3):
+        s = (px + 1.0) * n / 2.0
+        got = O.gather(g, O.TSC, f, [px, 0.12, 0.0])[0]
+        assert abs(got - _tsc_brute(fx, n, s)) < 1e-14, px
+
+
+@pytest.mark.parametrize("shape", [O.TSC, O.CIC])
+def test_open_axis_deposit_total_and_adjoint(shape):
+    """Open axes fold the deposit onto the edge cells: the total is kept and
+    the deposit stays the exact transpose of the (zero-gradient) gather."""
+    n = 8
+    g = O.make_grid(3, (n, n, n), open_axes=(1, 0, 1))
+    rng = np.random.default_rng(5)
+    N = 400
+    x = rng.uniform(-1.2, 1.2, (3, N))                  # some beyond the open faces
+    x[1] = rng.uniform(-1.0, 1.0, N)                    # y is periodic: inside
+    F = rng.standard_normal((3, N))
+    out = O.deposit(g, shape, x, F)
+    assert np.allclose(out.sum(axis=1), F.sum(axis=1), rtol=1e-13, atol=1e-12)
+    f = rng.standard_normal((3, n ** 3))
+    lhs = np.sum(f * out)
+    rhs = sum(F[:, p] @ O.gather(g, shape, f, x[:, p]) for p in range(N))
+    assert abs(lhs - rhs) < 1e-12 * np.sum(np.abs(F))
+
+
+def test_open_axis_no_wrap_and_outside():
+    """An open axis is never wrapped; a particle beyond it is outside; a
+    Boris step carries a particle across the open face instead of around."""
+    g = O.make_grid(3, (8, 8, 8), open_axes=(1, 0, 0))
+    assert O.wrap(g, 0, 1.3) == 1.3 and O.wrap(g, 0, -1.3) == -1.3
+    assert abs(O.wrap(g, 1, 1.3) - (-0.7)) < 1e-15
+    x = np.array([[0.0, 0.999, 1.0, -1.0, -1.0001], [0.0, 1.5, 0.2, 0.0, 0.0],
+                  [0.0, 0.0, 0.0, 0.0, 0.0]])
+    assert O.outside(g, x).tolist() == [0, 0, 1, 0, 1]
+    f = np.zeros((6, 8 ** 3))
+    f[5] = 1.0                                               # B = z
+    x0 = np.array([[0.98], [0.0], [0.0]])
+    u0 = np.array([[0.5], [0.0], [0.0]])
+    x1, u1, _, _ = O.boris_step(g, O.TSC, f, x0, u0, None, 1.0, 0.1)
+    assert x1[0, 0] > 1.0 and O.outside(g, x1).tolist() == [1]
