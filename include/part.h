@@ -33,8 +33,16 @@
  *   - All pointers to particle, field and output data are DEVICE pointers.
  *   - Units: c = 1, particle mass m = 1, u = gamma v.
  *   - Grid: cell-centred fields, layout [comp][z][y][x] (x fastest), cell
- *     (jx,jy,jz) centred at xmin + (j + 1/2) dx.  All axes periodic.  For
- *     dim == 2 the grid has n[2] == 1 and only x, y move (2D3V).
+ *     (jx,jy,jz) centred at xmin + (j + 1/2) dx.  For dim == 2 the grid has
+ *     n[2] == 1 and only x, y move (2D3V).
+ *   - Boundaries, per axis: periodic (wrap), or open (outflow, as the x axis
+ *     of the paper's shock test, Sec. 4.1.2).  On an open axis the fields are
+ *     continued by a zero-gradient ghost layer; a particle samples at its
+ *     position clamped into the domain; deposits beyond the face fold onto
+ *     the edge cell (the adjoint of that gather); positions are not wrapped,
+ *     and a particle that ends a push outside the domain is flagged in the
+ *     outflow mask (part_set_outflow) for removal by part_compact before the
+ *     next sort or push.  The serving API needs periodic grids.
  */
 #ifndef PART_H
 #define PART_H
@@ -68,7 +76,7 @@ typedef struct {
   int n[3];         /* cells per axis, each >= 1; n[2] must be 1 if dim==2 */
   double xmin[3];   /* lower corner                                        */
   double dx[3];     /* cell widths (> 0)                                   */
-  int periodic[3];  /* must all be 1 (open boundaries are not built)       */
+  int periodic[3];  /* 1: periodic; 0: open (outflow) axis, see below      */
 } part_grid;
 
 /* Brick (cell tile) dimensions the library sorts and stages by: 8x8x8 in 3D,
@@ -150,6 +158,14 @@ part_status part_flush(part_ctx* ctx);
  * becomes n_new.  Synchronises the stream once to read N_del.  Invalidates
  * the sort.                                                                 */
 part_status part_compact(part_ctx* ctx, const uint8_t* deleted, int64_t* n_new);
+
+/* Outflow mask (grids with an open axis): every push writes, per bound
+ * particle, 1 if it ended outside the domain along an open axis, else 0
+ * (device uint8[n], caller-owned, in the order of the bound arrays after the
+ * push).  A fused multi-step push stops advancing a particle once it is out.
+ * Pass the mask to part_compact to remove those particles.  NULL: not
+ * written.  part_bind_particles resets it to NULL.                         */
+part_status part_set_outflow(part_ctx* ctx, uint8_t* mask);
 
 /* Device pointer to cell_start[nkeys + 1] (valid after part_sort): the
  * particles of key k are [cell_start[k], cell_start[k+1]).                */

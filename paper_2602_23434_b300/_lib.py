@@ -36,8 +36,10 @@ class Grid(C.Structure):
                 ("dx", C.c_double * 3), ("periodic", C.c_int * 3)]
 
 
-def make_grid(dim: int, n, xmin=(-1.0, -1.0, -1.0), L=(2.0, 2.0, 2.0)) -> Grid:
-    """Periodic grid of n cells per axis on [xmin, xmin + L); dim 2 -> n[2] = 1."""
+def make_grid(dim: int, n, xmin=(-1.0, -1.0, -1.0), L=(2.0, 2.0, 2.0),
+              open_axes=(0, 0, 0)) -> Grid:
+    """Grid of n cells per axis on [xmin, xmin + L); dim 2 -> n[2] = 1;
+    periodic, except the axes with open_axes[a] = 1 (outflow)."""
     if isinstance(n, int):
         n = (n, n, n if dim == 3 else 1)
     n = list(n) + [1] * (3 - len(n))
@@ -49,7 +51,7 @@ def make_grid(dim: int, n, xmin=(-1.0, -1.0, -1.0), L=(2.0, 2.0, 2.0)) -> Grid:
         g.n[a] = int(n[a])
         g.xmin[a] = float(xmin[a])
         g.dx[a] = float(L[a]) / n[a] if (a < dim) else float(L[a])
-        g.periodic[a] = 1
+        g.periodic[a] = 0 if open_axes[a] else 1
     return g
 
 
@@ -92,6 +94,7 @@ def lib():
         "part_enable_shocks": (st, [P, C.c_double, P]),
         "part_set_lp_order": (st, [P, C.c_int]),
         "part_flush": (st, [P]),
+        "part_set_outflow": (st, [P, P]),
         "part_shock_cells": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
         "part_enable_deposit": (st, [P, C.c_int]),
         "part_gather_push": (st, [P, C.c_double, C.c_double, C.c_int]),
@@ -210,6 +213,12 @@ class Part:
         nn = C.c_int64()
         self._check(self.L.part_compact(self.ctx, _ptr(deleted), C.byref(nn)))
         return nn.value
+
+    def set_outflow(self, mask):
+        """Device uint8[n] written by every push: 1 where the particle left the
+        domain through an open face (None: not written)."""
+        self._check(self.L.part_set_outflow(self.ctx, _ptr(mask)))
+        self._keep_out = mask
 
     def flush(self):
         """Current particle state into the bound arrays (asynchronous)."""

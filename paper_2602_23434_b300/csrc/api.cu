@@ -42,8 +42,6 @@ part_status check_grid(const part_grid* g) {
     if (!(g->dx[a] > 0.0) || !std::isfinite(g->dx[a]))
       return fail(nullptr, PART_EINVAL, "dx[a] must be finite and > 0");
     if (!std::isfinite(g->xmin[a])) return fail(nullptr, PART_EINVAL, "xmin must be finite");
-    if (!g->periodic[a])
-      return fail(nullptr, PART_EUNSUPPORTED, "only periodic boundaries are built");
   }
   if (g->dim == 2 && g->n[2] != 1) return fail(nullptr, PART_EINVAL, "dim 2 needs n[2] == 1");
   int64_t G = (int64_t)g->n[0] * g->n[1] * g->n[2];
@@ -83,6 +81,11 @@ void make_geo(const part_grid* gr, int esize, Geo* g) {
     while ((1 << g->bshift[a]) < g->b[a]) ++g->bshift[a];
   }
   g->vshift = g->bshift[0] + g->bshift[1] + g->bshift[2];
+  g->any_open = 0;
+  for (int a = 0; a < 3; ++a) {
+    g->open[a] = a < gr->dim && !gr->periodic[a] ? 1 : 0;
+    g->any_open |= g->open[a];
+  }
   g->ev = g->e[0] * g->e[1] * g->e[2];
   g->G = (int64_t)g->n[0] * g->n[1] * g->n[2];
   g->nbricks = (int64_t)g->nb[0] * g->nb[1] * g->nb[2];
@@ -361,6 +364,7 @@ part_status part_bind_particles(part_ctx* c, int64_t n, void* x_or_cell, void* o
   c->eng = c->mode == PART_LP_RK2 ? eng : nullptr;
   c->n_old = c->mode == PART_LP_RK2 ? n_old : nullptr;
   c->shk = nullptr;  // shock flags belong to the previous particle set
+  c->outmask = nullptr;
   c->shock_listed = false;
   c->order_kept = false;
   c->bound = true;
@@ -379,7 +383,7 @@ part_status part_sort(part_ctx* c) {
   // the radix passes
   double dxmin = c->geo.dx[0];
   for (int a = 1; a < c->geo.dim; ++a) dxmin = std::min(dxmin, c->geo.dx[a]);
-  const bool inc = c->order_kept && c->cstart_alt && c->moved < dxmin;
+  const bool inc = c->order_kept && c->cstart_alt && c->moved < dxmin && !c->geo.any_open;
   if (e == cudaSuccess) e = inc ? launch_sort_incremental(c) : launch_sort(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_sort");
   c->sorted = true;
@@ -406,6 +410,13 @@ part_status part_compact(part_ctx* c, const uint8_t* deleted, int64_t* n_new) {
   c->deposit_ready = false;
   c->samples_ready = false;
   c->shock_listed = false;
+  return PART_OK;
+}
+
+part_status part_set_outflow(part_ctx* c, uint8_t* mask) {
+  if (check_ctx(c)) return PART_EINVAL;
+  if (mask && !c->geo.any_open) return fail(c, PART_EINVAL, "the grid has no open axis");
+  c->outmask = mask;
   return PART_OK;
 }
 

@@ -136,6 +136,13 @@ __global__ void k_init_lp(const Geo g, int64_t n, int nb, uint64_t seed,
 
 // Ghost-filled padded copy: padded (px, py, pz) <- cell ((px-h) mod n, ...);
 // x columns beyond n + 2 (row-pitch padding) are zero.
+// Source cell of padded coordinate i (cell index, may be -1 or n): periodic
+// image, or the edge cell on an open axis (zero-gradient ghost layer).
+__device__ __forceinline__ int ghost_src(int i, int n, int open) {
+  if (open) return i < 0 ? 0 : (i >= n ? n - 1 : i);
+  return (i + n) % n;
+}
+
 template <typename T>
 __global__ void k_pad_fields(const T* __restrict__ src, T* __restrict__ dst, const Geo g,
                              int ncomp) {
@@ -151,9 +158,9 @@ __global__ void k_pad_fields(const T* __restrict__ src, T* __restrict__ dst, con
       dst[q] = T(0);
       continue;
     }
-    const int sx = (px - g.h[0] + g.n[0]) % g.n[0];
-    const int sy = (py - g.h[1] + g.n[1]) % g.n[1];
-    const int sz = (pz - g.h[2] + g.n[2]) % g.n[2];
+    const int sx = ghost_src(px - g.h[0], g.n[0], g.open[0]);
+    const int sy = ghost_src(py - g.h[1], g.n[1], g.open[1]);
+    const int sz = ghost_src(pz - g.h[2], g.n[2], g.open[2]);
     dst[q] = src[c * g.G + ((int64_t)sz * g.n[1] + sy) * g.n[0] + sx];
   }
 }
@@ -174,9 +181,9 @@ __global__ void k_pad_fields_aos8(const float* __restrict__ src, float* __restri
       dst[q] = 0.0f;
       continue;
     }
-    const int sx = (px - g.h[0] + g.n[0]) % g.n[0];
-    const int sy = (py - g.h[1] + g.n[1]) % g.n[1];
-    const int sz = (pz - g.h[2] + g.n[2]) % g.n[2];
+    const int sx = ghost_src(px - g.h[0], g.n[0], g.open[0]);
+    const int sy = ghost_src(py - g.h[1], g.n[1], g.open[1]);
+    const int sz = ghost_src(pz - g.h[2], g.n[2], g.open[2]);
     dst[q] = src[(int64_t)c * g.G + ((int64_t)sz * g.n[1] + sy) * g.n[0] + sx];
   }
 }

@@ -8,9 +8,11 @@
 
 namespace {
 
-__device__ __forceinline__ double wrap_axis(double v, double lo, double hi, double L) {
-  if (v < lo) v = v + L;
-  else if (v >= hi) v = v - L;
+// Periodic wrap of coordinate a, or none on an open axis.
+__device__ __forceinline__ double wrap_axis(const Geo& g, int a, double v) {
+  if (g.open[a]) return v;
+  if (v < g.xmin[a]) v = v + g.L[a];
+  else if (v >= g.xmax[a]) v = v - g.L[a];
   return v;
 }
 
@@ -32,6 +34,7 @@ struct Stencil {
         finite = false;
         s = 0.0;
       }
+      if (g.open[a]) s = fmin(fmax(s, 0.0), (double)g.n[a]);  // sample at the boundary
       j[a] = floor_clamp_bits(s, g.n[a] - 1);
       d[a] = __dsub_rn(__dsub_rn(s, (double)j[a]), 0.5);
     }
@@ -133,7 +136,8 @@ __global__ void __launch_bounds__(256)
     k_lp_rk2(const double* __restrict__ fp, const Geo g, double* __restrict__ x, int64_t n,
              double dt, double* __restrict__ samples, int* __restrict__ status,
              const double* __restrict__ shock_r, uint8_t* __restrict__ shk,
-             uint32_t* __restrict__ list, double* __restrict__ rs) {
+             uint32_t* __restrict__ list, double* __restrict__ rs,
+             uint8_t* __restrict__ outmask) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     double x0[3], xs[3], x1[3];
@@ -143,26 +147,25 @@ __global__ void __launch_bounds__(256)
     Stencil<SHAPE, DIM> s0(g, x0);
     s0.gather_vb(fp, g, v1, b0);
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) xs[a] = wrap_axis(x0[a] + dt * v1[a], g.xmin[a], g.xmax[a], g.L[a]);
+    for (int a = 0; a < DIM; ++a) xs[a] = wrap_axis(g, a, x0[a] + dt * v1[a]);
     Stencil<SHAPE, DIM> ss(g, xs);
     ss.template gather<3>(fp, g, 0, v2);
     bool fin = s0.finite && ss.finite;
     if (ORDER == 2) {
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
-        x1[a] = wrap_axis(x0[a] + dt * (0.5 * (v1[a] + v2[a])), g.xmin[a], g.xmax[a], g.L[a]);
+        x1[a] = wrap_axis(g, a, x0[a] + dt * (0.5 * (v1[a] + v2[a])));
     } else {
       double xb[3] = {x0[0], x0[1], x0[2]}, k3[3];
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
-        xb[a] = wrap_axis(x0[a] + dt * (0.25 * (v1[a] + v2[a])), g.xmin[a], g.xmax[a], g.L[a]);
+        xb[a] = wrap_axis(g, a, x0[a] + dt * (0.25 * (v1[a] + v2[a])));
       Stencil<SHAPE, DIM> sb(g, xb);
       sb.template gather<3>(fp, g, 0, k3);
       fin = fin && sb.finite;
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
-        x1[a] = wrap_axis(x0[a] + dt * ((v1[a] + v2[a] + 4.0 * k3[a]) / 6.0), g.xmin[a],
-                          g.xmax[a], g.L[a]);
+        x1[a] = wrap_axis(g, a, x0[a] + dt * ((v1[a] + v2[a] + 4.0 * k3[a]) / 6.0));
     }
     Stencil<SHAPE, DIM> s1(g, x1);
     {
@@ -178,6 +181,7 @@ __global__ void __launch_bounds__(256)
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) x[a * n + p] = x1[a];
+    if (outmask) outmask[p] = outside_open(g, x1);
     const double bb0 = b0[0] * b0[0] + b0[1] * b0[1] + b0[2] * b0[2];
     const double bb1 = b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2];
     const double vv = v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2];
@@ -273,11 +277,11 @@ cudaError_t lp_launch_order(part_ctx* c, double dt) {
     if (e != cudaSuccess) return e;
     k_lp_rk2<SHAPE, DIM, true, ORDER><<<gb, 256, 0, c->stream>>>(
         (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status,
-        c->shock_r, c->shk, c->shock_list, c->shock_rs);
+        c->shock_r, c->shk, c->shock_list, c->shock_rs, c->outmask);
   } else {
     k_lp_rk2<SHAPE, DIM, false, ORDER><<<gb, 256, 0, c->stream>>>(
         (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status,
-        nullptr, nullptr, nullptr, nullptr);
+        nullptr, nullptr, nullptr, nullptr, c->outmask);
   }
   c->launches++;
   return cudaGetLastError();

@@ -48,6 +48,8 @@ struct Geo {
   float invn[3];   // 1/n per axis, for the float-reciprocal cell decode
   int bshift[3];   // log2 b per axis (brick sides are powers of two)
   int vshift;      // log2 V
+  int open[3];     // 1: open (outflow) axis, 0: periodic
+  int any_open;
 };
 
 // Every member has a default initializer: a context built on the stack (the
@@ -90,6 +92,7 @@ struct part_ctx {
   void* alt_u{};      // FP64: double[3][cap]   mixed: float[3][cap]
   void* alt_w{};      // FP64: double[cap]      mixed: float[cap]
   uint64_t* alt_id{}; // uint64[cap]
+  uint8_t* outmask{};             // caller's outflow flags (open axes), or NULL
   bool cur_alt{};                 // the current state is in the alternate buffers
   const uint32_t* perm_pend{};    // new slot -> index in the current buffer, or NULL
   int* status{};      // device status word
@@ -225,6 +228,15 @@ __device__ __forceinline__ void cell_coords(const Geo& g, int32_t c, int* j) {
     j[1] = r % g.n[1];
     j[2] = r / g.n[1];
   }
+}
+
+// 1 if x lies outside the domain along an open axis (NaN counts as outside).
+__device__ __forceinline__ uint8_t outside_open(const Geo& g, const double* x) {
+  bool out = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (g.open[a]) out = out || !(x[a] >= g.xmin[a] && x[a] < g.xmax[a]);
+  return out ? 1 : 0;
 }
 
 // ---------------------------------------------------------------- shape weights

@@ -81,14 +81,14 @@ __device__ __forceinline__ void boris_f64(double* u, const double* E, const doub
 // One particle of a chunk: weights, gather from the staged box, Boris, drift,
 // wrap, store; with DEP, its deposit record (9 z-y weight products and the 9
 // x-weighted force terms) is returned in wyz / fxc (zero if it has none).
-template <int SHAPE, int DIM, bool DEP>
+template <int SHAPE, int DIM, bool DEP, bool OPEN>
 __device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int bvol,
                                          const uint32_t* scs, const int* org, uint32_t p,
                                          uint32_t q, const double* xs, const double* us,
                                          const double* ws, const uint64_t* ids, double* x,
                                          double* u, double* wd, uint64_t* idd, int64_t n,
                                          double h, double dt, double inv_dt, int* status,
-                                         double* wyz, double* fxc) {
+                                         uint8_t* outmask, double* wyz, double* fxc) {
   double xp[3], up[3], uo[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {  // particle q of the current buffer goes to slot p
@@ -105,10 +105,12 @@ __device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int b
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
     double sa = __dmul_rn(__dsub_rn(xp[a], g.xmin[a]), g.inv_dx[a]);
+    const bool fa = finite_bits(sa);
+    if (OPEN && g.open[a]) sa = fmin(fmax(sa, 0.0), (double)g.n[a]);  // sample at the boundary
     int j = floor_clamp_bits(sa, g.n[a] - 1);
     d[a] = __dsub_rn(__dsub_rn(sa, (double)j), 0.5);
     l[a] = j - org[a];
-    ok = ok && l[a] >= 0 && l[a] < g.b[a] && finite_bits(sa);
+    ok = ok && l[a] >= 0 && l[a] < g.b[a] && fa;
   }
   if (ok) {  // the particle must sit in the cell it was sorted into
     const int lc = (l[2] * g.b[1] + l[1]) * g.b[0] + l[0];
@@ -121,6 +123,7 @@ __device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int b
       x[a * n + p] = xp[a];
       u[a * n + p] = up[a];
     }
+    if (OPEN && outmask) outmask[p] = outside_open(g, xp);
     return;
   }
   double wx[3], wy[3], wz[3] = {0.0, 1.0, 0.0};
@@ -148,8 +151,10 @@ __device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int b
   boris_f64(up, f, f + 3, h);
   const double gi = rsqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
 #pragma unroll
-  for (int a = 0; a < DIM; ++a)
-    xp[a] = wrap_axis(xp[a] + dt * (up[a] * gi), g.xmin[a], g.xmax[a], g.L[a]);
+  for (int a = 0; a < DIM; ++a) {
+    const double xa = xp[a] + dt * (up[a] * gi);
+    xp[a] = OPEN && g.open[a] ? xa : wrap_axis(xa, g.xmin[a], g.xmax[a], g.L[a]);
+  }
   bool fin = finite_bits(up[0]) && finite_bits(up[1]) && finite_bits(up[2]) &&
              finite_bits(xp[0]) && finite_bits(xp[1]) && finite_bits(xp[2]);
   if (!fin) atomicOr(status, ST_NONFINITE);
@@ -158,6 +163,7 @@ __device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int b
     x[a * n + p] = xp[a];
     u[a * n + p] = up[a];
   }
+  if (outmask) outmask[p] = outside_open(g, xp);
   if (DEP) {
     const double wdt = wp * inv_dt;
     double F[3];
@@ -283,15 +289,17 @@ __device__ __forceinline__ bool brick_prologue(const CUtensorMap* tmap, const Ge
   return true;
 }
 
-// Without deposit: 256 threads walk the brick's particles in chunks.
-template <int SHAPE, int DIM>
+// Without deposit: 256 threads walk the brick's particles in chunks.  OPEN:
+// the grid has an open axis (no wrap there, sampling clamped, outflow mask).
+template <int SHAPE, int DIM, bool OPEN>
 __global__ void __launch_bounds__(kT, 1)
     k_boris_brick_f64(const __grid_constant__ CUtensorMap tmap, const Geo g,
                       const double* xs, const double* us, const double* ws,
                       const uint64_t* ids, double* x, double* u, double* wd, uint64_t* idd,
                       int64_t n, const uint32_t* __restrict__ perm,
                       const uint32_t* __restrict__ cstart, double* __restrict__ dpart,
-                      double qm, double dt, double inv_dt, int* __restrict__ status) {
+                      double qm, double dt, double inv_dt, int* __restrict__ status,
+                      uint8_t* __restrict__ outmask) {
   extern __shared__ __align__(128) unsigned char smem[];
   const BrickSmem L = brick_smem(g, 6, 8, false);
   const int tid = threadIdx.x;
@@ -310,8 +318,9 @@ __global__ void __launch_bounds__(kT, 1)
   const double h = 0.5 * qm * dt;
   const uint32_t p0 = scs[0], p1 = scs[g.V];
   for (uint32_t p = p0 + tid; p < p1; p += kT)
-    push_one<SHAPE, DIM, false>(g, sbox, bvol, scs, org, p, perm ? perm[p] : p, xs, us, ws,
-                                ids, x, u, wd, idd, n, h, dt, inv_dt, status, nullptr, nullptr);
+    push_one<SHAPE, DIM, false, OPEN>(g, sbox, bvol, scs, org, p, perm ? perm[p] : p, xs, us, ws,
+                                ids, x, u, wd, idd, n, h, dt, inv_dt, status, outmask, nullptr,
+                                nullptr);
 }
 
 // With deposit: warp-specialised, 512 threads.  Warps 0-7 push chunk k of 256
@@ -320,7 +329,7 @@ __global__ void __launch_bounds__(kT, 1)
 // barriers (FULL_b: records of buffer b written; EMPTY_b: buffer b read), so
 // both phases keep the FP64 pipe busy and neither waits for the other's
 // latency.  Both groups derive the same chunk count from cell_start.
-template <int SHAPE, int DIM>
+template <int SHAPE, int DIM, bool OPEN>
 __global__ void __launch_bounds__(2 * kT, 1)
     k_boris_brick_f64_dep(const __grid_constant__ CUtensorMap tmap, const Geo g,
                           const double* xs, const double* us, const double* ws,
@@ -328,7 +337,7 @@ __global__ void __launch_bounds__(2 * kT, 1)
                           uint64_t* idd, int64_t n, const uint32_t* __restrict__ perm,
                           const uint32_t* __restrict__ cstart,
                           double* __restrict__ dpart, double qm, double dt, double inv_dt,
-                          int* __restrict__ status) {
+                          int* __restrict__ status, uint8_t* __restrict__ outmask) {
   constexpr int NT = 2 * kT;
   constexpr int kFull = 1, kEmpty = 3;  // named barrier ids (0 is __syncthreads)
   extern __shared__ __align__(128) unsigned char smem[];
@@ -361,8 +370,10 @@ __global__ void __launch_bounds__(2 * kT, 1)
 #pragma unroll
       for (int q = 0; q < 9; ++q) wyz[q] = fxc[q] = 0.0;
       if (p < p1)
-        push_one<SHAPE, DIM, true>(g, sbox, bvol, scs, org, p, perm ? perm[p] : p, xs, us, ws,
-                                   ids, x, u, wd, idd, n, h, dt, inv_dt, status, wyz, fxc);
+        push_one<SHAPE, DIM, true, OPEN>(g, sbox, bvol, scs, org, p, perm ? perm[p] : p, xs, us,
+                                         ws,
+                                   ids, x, u, wd, idd, n, h, dt, inv_dt, status, outmask, wyz,
+                                   fxc);
       if (k >= 2) named_bar_sync(kEmpty + b, NT);  // deposit of chunk k-2 has read it
       double* rw = rec + (size_t)b * 18 * kRS;
 #pragma unroll
@@ -397,7 +408,7 @@ template <int SHAPE, int DIM>
 __global__ void __launch_bounds__(256)
     k_boris_particles_f64(const double* __restrict__ fp, const Geo g, double* __restrict__ x,
                           double* __restrict__ u, int64_t n, double qm, double dt, int nsteps,
-                          int* __restrict__ status) {
+                          int* __restrict__ status, uint8_t* __restrict__ outmask) {
   const double h = 0.5 * qm * dt;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -408,7 +419,8 @@ __global__ void __launch_bounds__(256)
       up[a] = u[a * n + p];
     }
     bool bad = false;
-    for (int st = 0; st < nsteps; ++st) {
+    // a particle that has left through an open face is not advanced further
+    for (int st = 0; st < nsteps && !outside_open(g, xp); ++st) {
       int j[3] = {0, 0, 0};
       double d[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -418,6 +430,7 @@ __global__ void __launch_bounds__(256)
           bad = true;
           s = 0.0;
         }
+        if (g.open[a]) s = fmin(fmax(s, 0.0), (double)g.n[a]);
         j[a] = floor_clamp_bits(s, g.n[a] - 1);
         d[a] = __dsub_rn(__dsub_rn(s, (double)j[a]), 0.5);
       }
@@ -444,8 +457,11 @@ __global__ void __launch_bounds__(256)
       boris_f64(up, f, f + 3, h);
       const double gi = rsqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
 #pragma unroll
-      for (int a = 0; a < DIM; ++a)
-        xp[a] = wrap_axis(xp[a] + dt * (up[a] * gi), g.xmin[a], g.xmax[a], g.L[a]);
+      for (int a = 0; a < DIM; ++a) {
+        const double xa = xp[a] + dt * (up[a] * gi);
+        xp[a] = g.open[a] ? xa : wrap_axis(xa, g.xmin[a], g.xmax[a], g.L[a]);
+      }
+      if (bad) break;
     }
     if (bad || !(isfinite(up[0]) && isfinite(up[1]) && isfinite(up[2]) && isfinite(xp[0]) &&
                  isfinite(xp[1]) && isfinite(xp[2])))
@@ -455,6 +471,7 @@ __global__ void __launch_bounds__(256)
       x[a * n + p] = xp[a];
       u[a * n + p] = up[a];
     }
+    if (outmask) outmask[p] = outside_open(g, xp);
   }
 }
 
@@ -518,6 +535,23 @@ __global__ void __launch_bounds__(256)
         continue;
       }
       const int bj = j[a] / g.b[a];
+      if (g.open[a]) {
+        // no periodic images; the edge cell also collects what was deposited
+        // beyond its face (global cell -1 or n), the adjoint of the
+        // zero-gradient gather
+        for (int t = (j[a] == 0 ? -1 : j[a]); t <= (j[a] == g.n[a] - 1 ? g.n[a] : j[a]); ++t)
+          for (int db = -1; db <= 1; ++db) {
+            const int bb = bj + db;
+            if (bb < 0 || bb >= g.nb[a]) continue;
+            const int ee = t - bb * g.b[a] + g.h[a];
+            if (ee >= 0 && ee < g.e[a] && cnt[a] < 9) {
+              cb[a][cnt[a]] = bb;
+              ce[a][cnt[a]] = ee;
+              cnt[a]++;
+            }
+          }
+        continue;
+      }
       for (int db = -1; db <= 1; ++db) {
         int bb = ((bj + db) % g.nb[a] + g.nb[a]) % g.nb[a];
         bool dup = false;
@@ -559,7 +593,11 @@ int grid_for(int64_t n, int threads) {
 
 template <int SHAPE, int DIM, bool DEP>
 cudaError_t brick_f64(part_ctx* c, double qm, double dt) {
-  auto kern = DEP ? k_boris_brick_f64_dep<SHAPE, DIM> : k_boris_brick_f64<SHAPE, DIM>;
+  const bool open = c->geo.any_open != 0;
+  auto kern = DEP ? (open ? k_boris_brick_f64_dep<SHAPE, DIM, true>
+                          : k_boris_brick_f64_dep<SHAPE, DIM, false>)
+                  : (open ? k_boris_brick_f64<SHAPE, DIM, true>
+                          : k_boris_brick_f64<SHAPE, DIM, false>);
   const BrickSmem L = brick_smem(c->geo, 6, 8, DEP);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L.total);
@@ -571,7 +609,7 @@ cudaError_t brick_f64(part_ctx* c, double qm, double dt) {
   kern<<<(unsigned)c->geo.nbricks, DEP ? 2 * kT : kT, L.total, c->stream>>>(
       c->tmap, c->geo, (const double*)src.x, (const double*)src.u, (const double*)src.w, src.id,
       (double*)dst.x, (double*)dst.u, (double*)dst.w, dst.id, c->n, c->perm_pend, c->cstart,
-      c->dpart, qm, dt, 1.0 / dt, c->status);
+      c->dpart, qm, dt, 1.0 / dt, c->status, c->outmask);
   c->launches++;
   if (c->perm_pend) {
     c->perm_pend = nullptr;
@@ -584,7 +622,7 @@ template <int SHAPE, int DIM>
 cudaError_t particles_f64(part_ctx* c, double qm, double dt, int nsteps) {
   k_boris_particles_f64<SHAPE, DIM><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
       (const double*)c->fpad, c->geo, (double*)c->x, (double*)c->u, c->n, qm, dt, nsteps,
-      c->status);
+      c->status, c->outmask);
   c->launches++;
   return cudaGetLastError();
 }
@@ -617,7 +655,7 @@ cudaError_t launch_deposit_combine(part_ctx* c, double* out) {
   const Geo& g = c->geo;
   bool fast = true;
   for (int a = 0; a < 3; ++a)
-    if (g.h[a] != 0 && (g.nb[a] < 3 || g.n[a] % g.b[a] != 0)) fast = false;
+    if (g.h[a] != 0 && (g.nb[a] < 3 || g.n[a] % g.b[a] != 0 || g.open[a])) fast = false;
   k_dep_combine<<<grid_for(g.G, 256), 256, 0, c->stream>>>(c->dpart, out, g, fast);
   c->launches++;
   return cudaGetLastError();

@@ -121,13 +121,24 @@ __device__ __forceinline__ void acc_point(float2* f, float ww, float4 a, float4 
   f[2] = __ffma2_rn(w2, make_float2(b.x, b.y), f[2]);
 }
 
-// Move in cell units: off += dv; whole cells carry into j (periodic).
-__device__ __forceinline__ void move_axis(float& off, int& j, float dv, int n) {
+// Move in cell units: off += dv; whole cells carry into j (periodic).  On an
+// open axis a particle that leaves is held at the face (edge cell, offset
+// -1/2 or +1/2) and marked out.
+__device__ __forceinline__ void move_axis(float& off, int& j, float dv, int n, int open,
+                                          bool& out) {
   off = off + dv;
   const float k = floorf(off + 0.5f);
   off = off - k;
   int jj = j + (int)k;
-  if (jj < 0 || jj >= n) jj = ((jj % n) + n) % n;
+  if (jj < 0 || jj >= n) {
+    if (open) {
+      out = true;
+      off = jj < 0 ? -0.5f : 0.5f;
+      jj = jj < 0 ? 0 : n - 1;
+    } else {
+      jj = ((jj % n) + n) % n;
+    }
+  }
   j = jj;
 }
 
@@ -140,7 +151,7 @@ __global__ void __launch_bounds__(kT, 3)
                         const uint32_t* __restrict__ perm,
                         const uint32_t* __restrict__ cstart, double* __restrict__ dpart,
                         float h, float hl, float dtdx0, float dtdx1, float dtdx2, float inv_dt,
-                        int* __restrict__ status) {
+                        int* __restrict__ status, uint8_t* __restrict__ outmask) {
   extern __shared__ __align__(128) unsigned char smem[];
   const MixedSmem L = mixed_smem(g);
   const int tid = threadIdx.x;
@@ -244,6 +255,7 @@ __global__ void __launch_bounds__(kT, 3)
       float d0[3] = {0.0f, 0.0f, 0.0f};
       if (!ok) {
         atomicOr(status, ST_DOMAIN);
+        if (outmask) outmask[p] = 0;
         cell[p] = ccur;  // left as it was
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -275,11 +287,14 @@ __global__ void __launch_bounds__(kT, 3)
         for (int a = 0; a < 3; ++a) d0[a] = o[a];
         boris_f32(up, f, f + 3, h, hl, du);
         const float gi = rsqrtf(1.0f + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+        bool out = false;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) move_axis(o[a], j[a], up[a] * gi * dtdx[a], g.n[a]);
+        for (int a = 0; a < DIM; ++a)
+          move_axis(o[a], j[a], up[a] * gi * dtdx[a], g.n[a], g.open[a], out);
         if (!(isfinite(up[0]) && isfinite(up[1]) && isfinite(up[2]) && isfinite(o[0]) &&
               isfinite(o[1]) && isfinite(o[2])))
           atomicOr(status, ST_NONFINITE);
+        if (outmask) outmask[p] = out ? 1 : 0;
         cell[p] = (j[2] * g.n[1] + j[1]) * g.n[0] + j[0];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -376,8 +391,8 @@ __global__ void __launch_bounds__(kT, 3)
 template <int SHAPE, int DIM>
 __device__ __forceinline__ void advance_mixed(const float* __restrict__ fp, const Geo& g, int* j,
                                               float* o, float* up, float h, float hl,
-                                              const float* dtdx, int nsteps) {
-  for (int st = 0; st < nsteps; ++st) {
+                                              const float* dtdx, int nsteps, bool& out) {
+  for (int st = 0; st < nsteps && !out; ++st) {
     float wx[3], wy[3], wz[3] = {0.0f, 1.0f, 0.0f};
     shape_weights<SHAPE>(o[0], wx);
     shape_weights<SHAPE>(o[1], wy);
@@ -401,7 +416,8 @@ __device__ __forceinline__ void advance_mixed(const float* __restrict__ fp, cons
     boris_f32(up, f, f + 3, h, hl, du);
     const float gi = rsqrtf(1.0f + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) move_axis(o[a], j[a], up[a] * gi * dtdx[a], g.n[a]);
+    for (int a = 0; a < DIM; ++a)
+      move_axis(o[a], j[a], up[a] * gi * dtdx[a], g.n[a], g.open[a], out);
   }
 }
 
@@ -411,7 +427,8 @@ __device__ __forceinline__ void particle_mixed(const float* __restrict__ fp, con
                                                int32_t* __restrict__ cell, float* __restrict__ off,
                                                float* __restrict__ u, int64_t stride, int64_t p,
                                                float h, float hl, const float* dtdx, int nsteps,
-                                               int* __restrict__ status) {
+                                               int* __restrict__ status,
+                                               uint8_t* __restrict__ outmask) {
   int32_t c = cell[p];
   bool bad = false;
   if (c < 0 || c >= g.G) {
@@ -426,7 +443,9 @@ __device__ __forceinline__ void particle_mixed(const float* __restrict__ fp, con
     o[a] = off[a * stride + p];
     up[a] = u[a * stride + p];
   }
-  advance_mixed<SHAPE, DIM>(fp, g, j, o, up, h, hl, dtdx, nsteps);
+  bool out = false;
+  advance_mixed<SHAPE, DIM>(fp, g, j, o, up, h, hl, dtdx, nsteps, out);
+  if (outmask) outmask[p] = out ? 1 : 0;
   if (bad || !(isfinite(up[0]) && isfinite(up[1]) && isfinite(up[2]) && isfinite(o[0]) &&
                isfinite(o[1]) && isfinite(o[2])))
     atomicOr(status, bad ? ST_DOMAIN : ST_NONFINITE);
@@ -443,11 +462,11 @@ __global__ void __launch_bounds__(256)
     k_boris_particles_mixed(const float* __restrict__ fp, const Geo g, int32_t* __restrict__ cell,
                             float* __restrict__ off, float* __restrict__ u, int64_t n, float h,
                             float hl, float dtdx0, float dtdx1, float dtdx2, int nsteps,
-                            int* __restrict__ status) {
+                            int* __restrict__ status, uint8_t* __restrict__ outmask) {
   const float dtdx[3] = {dtdx0, dtdx1, dtdx2};
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x)
-    particle_mixed<SHAPE, DIM>(fp, g, cell, off, u, n, p, h, hl, dtdx, nsteps, status);
+    particle_mixed<SHAPE, DIM>(fp, g, cell, off, u, n, p, h, hl, dtdx, nsteps, status, outmask);
 }
 
 // Persistent serving kernel: CTA b takes work items b, b + gridDim.x, ...
@@ -483,7 +502,8 @@ __global__ void __launch_bounds__(512)
     const float dtdx[3] = {s_par[2], s_par[3], s_par[4]};
     for (int64_t q = threadIdx.x; q < s_it.count; q += blockDim.x)
       particle_mixed<SHAPE, DIM>(s_sn.fp, s_sn.g, s_it.cell, s_it.off, s_it.u, s_it.stride,
-                                 s_it.first + q, s_par[0], s_par[1], dtdx, s_it.nsteps, status);
+                                 s_it.first + q, s_par[0], s_par[1], dtdx, s_it.nsteps, status,
+                                 nullptr);
   }
 }
 
@@ -523,7 +543,7 @@ cudaError_t brick_mixed(part_ctx* c, const MixedArgs& a) {
       c->tmap, c->geo, (const int32_t*)src.x, (const float*)src.off, (const float*)src.u,
       (const float*)src.w, src.id, (int32_t*)dst.x, (float*)dst.off, (float*)dst.u,
       (float*)dst.w, dst.id, c->n, c->perm_pend, c->cstart, c->dpart, a.h, a.hl, a.dtdx[0],
-      a.dtdx[1], a.dtdx[2], a.inv_dt, c->status);
+      a.dtdx[1], a.dtdx[2], a.inv_dt, c->status, c->outmask);
   c->launches++;
   if (c->perm_pend) {
     c->perm_pend = nullptr;
@@ -540,7 +560,7 @@ cudaError_t dispatch_mixed(part_ctx* c, double qm, double dt, int nsteps) {
                          : brick_mixed<SHAPE, DIM, false>(c, a);
   k_boris_particles_mixed<SHAPE, DIM><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
       (const float*)c->fpad, c->geo, (int32_t*)c->x, (float*)c->off, (float*)c->u, c->n, a.h,
-      a.hl, a.dtdx[0], a.dtdx[1], a.dtdx[2], nsteps, c->status);
+      a.hl, a.dtdx[0], a.dtdx[1], a.dtdx[2], nsteps, c->status, c->outmask);
   c->launches++;
   return cudaGetLastError();
 }

@@ -101,6 +101,8 @@ part_status part_server_init(part_server** out, part_ctx* const* snapshots, int 
     const part_ctx* c = snapshots[i];
     if (!c || c->prec != PART_MIXED || c->mode != PART_BORIS || !c->fields_set)
       return fail(nullptr, PART_EINVAL, "snapshots must be PART_MIXED Boris contexts with fields");
+    if (c->geo.any_open)
+      return fail(nullptr, PART_EUNSUPPORTED, "serving needs periodic snapshots");
     if (c->shape != snapshots[0]->shape || c->geo.dim != snapshots[0]->geo.dim)
       return fail(nullptr, PART_EINVAL, "snapshots must share shape and dim");
   }

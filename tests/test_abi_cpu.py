@@ -45,9 +45,9 @@ def test_workspace_size_and_validation(L):
     bad = P.make_grid(3, 16)
     bad.dim = 4
     assert L.part_workspace_size(C.byref(bad), P.FP64, P.BORIS, 10, 0, C.byref(sz)) == 1
-    bad = P.make_grid(3, 16)
-    bad.periodic[1] = 0
-    assert L.part_workspace_size(C.byref(bad), P.FP64, P.BORIS, 10, 0, C.byref(sz)) == 6
+    opn = P.make_grid(3, 16)
+    opn.periodic[1] = 0                     # an open (outflow) axis is accepted
+    assert L.part_workspace_size(C.byref(opn), P.FP64, P.BORIS, 10, 0, C.byref(sz)) == 0
     bad = P.make_grid(3, 16)
     bad.dx[0] = 0.0
     assert L.part_workspace_size(C.byref(bad), P.FP64, P.BORIS, 10, 0, C.byref(sz)) == 1
