@@ -182,7 +182,11 @@ part_status part_enable_deposit(part_ctx* ctx, int on);
  * PART_LP_RK2: nsteps Heun steps x* = x + dt v(x), x' = x + dt (v(x)+v(x*))/2
  * of Eq. push, then samples at the new position for spec_update: density,
  * the mean of |B|^2 at the old and new position, and gamma_g.  q_over_m is
- * ignored in LP mode.                                                      */
+ * ignored in LP mode.  The fluid v and B sampled at the new positions are
+ * kept (workspace) and stand for the samples at the old positions of the
+ * next push, one stencil pass fewer per LP; part_set_fields, part_sort,
+ * part_compact, part_bind_particles and part_init_particles drop them.  A
+ * caller that moves the LPs itself binds them again.                       */
 part_status part_gather_push(part_ctx* ctx, double q_over_m, double dt, int nsteps);
 
 /* Time marching of the LP push (PART_LP_RK2 contexts; default 2).

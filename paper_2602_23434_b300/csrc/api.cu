@@ -98,7 +98,7 @@ namespace {
 struct Layout {
   size_t fpad, keys0, keys1, vals0, vals1, hist, hsum, cstart, tmp, dpart, samples, status,
       alt_x, alt_off, alt_u, alt_w, alt_id, shock_r, shock_list, shock_rs, cstart_alt, bcount,
-      bsum, bslot, total;
+      bsum, bslot, lpcache, total;
 };
 
 int ncomp_of(part_mode m) { return m == PART_BORIS ? 6 : 7; }
@@ -146,6 +146,7 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   L.shock_r = take(lp ? (size_t)g.G * 8 : 0);
   L.shock_list = take(lp ? (size_t)(c1 + 1) * 4 : 0);
   L.shock_rs = take(lp ? (size_t)c1 * 8 : 0);
+  L.lpcache = take(lp ? (size_t)6 * c1 * 8 : 0);
   // Boris modes: second cell_start and the brick counts of the incremental sort
   L.cstart_alt = take(alt ? (size_t)(g.nkeys + 1) * 4 : 0);
   L.bcount = take(alt ? (size_t)(g.nbricks + 1) * 4 : 0);
@@ -301,6 +302,7 @@ part_status part_init(part_ctx** out, const part_grid* grid, part_prec prec, par
     c->shock_r = (double*)(c->ws + L.shock_r);
     c->shock_list = (uint32_t*)(c->ws + L.shock_list);
     c->shock_rs = (double*)(c->ws + L.shock_rs);
+    c->lpcache = (double*)(c->ws + L.lpcache);
   }
   cudaError_t e = cudaMemsetAsync(c->status, 0, 256, c->stream);
   if (e != cudaSuccess) {
@@ -333,6 +335,7 @@ part_status part_set_fields(part_ctx* c, const void* fields, int ncomp, part_pre
   if (e == cudaSuccess && c->shk) e = launch_shock_cells(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_set_fields");
   c->fields_set = true;
+  c->lp_cache_ok = false;  // the fields changed
   return PART_OK;
 }
 
@@ -367,6 +370,7 @@ part_status part_bind_particles(part_ctx* c, int64_t n, void* x_or_cell, void* o
   c->outmask = nullptr;
   c->shock_listed = false;
   c->order_kept = false;
+  c->lp_cache_ok = false;
   c->bound = true;
   c->sorted = false;
   c->deposit_ready = false;
@@ -390,6 +394,7 @@ part_status part_sort(part_ctx* c) {
   c->order_kept = true;
   c->moved = 0.0;
   c->samples_ready = false;  // LP samples are in the old particle order
+  c->lp_cache_ok = false;
   c->shock_listed = false;
   return PART_OK;
 }
@@ -407,6 +412,7 @@ part_status part_compact(part_ctx* c, const uint8_t* deleted, int64_t* n_new) {
   *n_new = nn;
   c->sorted = false;
   c->order_kept = false;
+  c->lp_cache_ok = false;
   c->deposit_ready = false;
   c->samples_ready = false;
   c->shock_listed = false;
@@ -556,6 +562,7 @@ part_status part_init_particles(part_ctx* c, uint64_t seed, double u_th, double 
   if (e != cudaSuccess) return cuda_fail(c, e, "part_init_particles");
   c->sorted = false;
   c->order_kept = false;
+  c->lp_cache_ok = false;
   c->samples_ready = false;
   c->deposit_ready = false;
   return PART_OK;

@@ -131,26 +131,40 @@ __device__ __forceinline__ void shock_mark(int64_t p, int64_t cell,
 // ORDER 2: Heun, x' = x + dt (k1 + k2)/2.  ORDER 3: three-stage SSP
 // Runge-Kutta (Shu & Osher) in stage-velocity form, k3 = v(x + dt (k1+k2)/4),
 // x' = x + dt (k1 + k2 + 4 k3)/6; the wrap only enters the sampled positions.
-template <int SHAPE, int DIM, bool SHOCK, int ORDER>
+// CACHED: v and B at x (from the previous step's samples at its new
+// position, the same stencil at the same point) are read instead of gathered;
+// every step leaves v and B at x' for the next one (cache [6][n]).
+template <int SHAPE, int DIM, bool SHOCK, int ORDER, bool CACHED>
 __global__ void __launch_bounds__(256)
     k_lp_rk2(const double* __restrict__ fp, const Geo g, double* __restrict__ x, int64_t n,
              double dt, double* __restrict__ samples, int* __restrict__ status,
              const double* __restrict__ shock_r, uint8_t* __restrict__ shk,
              uint32_t* __restrict__ list, double* __restrict__ rs,
-             uint8_t* __restrict__ outmask) {
+             uint8_t* __restrict__ outmask, double* __restrict__ cache) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     double x0[3], xs[3], x1[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) x0[a] = xs[a] = x1[a] = x[a * n + p];
     double v1[3], b0[3], v2[3], v3[3], b1[3], r;
-    Stencil<SHAPE, DIM> s0(g, x0);
-    s0.gather_vb(fp, g, v1, b0);
+    bool fin;
+    if (CACHED) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        v1[c] = cache[c * n + p];
+        b0[c] = cache[(3 + c) * n + p];
+      }
+      fin = finite_bits(x0[0]) && finite_bits(x0[1]) && finite_bits(x0[2]);
+    } else {
+      Stencil<SHAPE, DIM> s0(g, x0);
+      s0.gather_vb(fp, g, v1, b0);
+      fin = s0.finite;
+    }
 #pragma unroll
     for (int a = 0; a < DIM; ++a) xs[a] = wrap_axis(g, a, x0[a] + dt * v1[a]);
     Stencil<SHAPE, DIM> ss(g, xs);
     ss.template gather<3>(fp, g, 0, v2);
-    bool fin = s0.finite && ss.finite;
+    fin = fin && ss.finite;
     if (ORDER == 2) {
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
@@ -181,6 +195,11 @@ __global__ void __launch_bounds__(256)
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) x[a * n + p] = x1[a];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      cache[c * n + p] = v3[c];
+      cache[(3 + c) * n + p] = b1[c];
+    }
     if (outmask) outmask[p] = outside_open(g, x1);
     const double bb0 = b0[0] * b0[0] + b0[1] * b0[1] + b0[2] * b0[2];
     const double bb1 = b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2];
@@ -269,22 +288,29 @@ int grid_for(int64_t n, int threads) {
   return (int)b;
 }
 
-template <int SHAPE, int DIM, int ORDER>
-cudaError_t lp_launch_order(part_ctx* c, double dt) {
+template <int SHAPE, int DIM, int ORDER, bool CACHED>
+cudaError_t lp_launch_cached(part_ctx* c, double dt) {
   const int gb = grid_for(c->n, 256);
   if (c->shk) {
     cudaError_t e = cudaMemsetAsync(c->shock_list, 0, sizeof(uint32_t), c->stream);
     if (e != cudaSuccess) return e;
-    k_lp_rk2<SHAPE, DIM, true, ORDER><<<gb, 256, 0, c->stream>>>(
+    k_lp_rk2<SHAPE, DIM, true, ORDER, CACHED><<<gb, 256, 0, c->stream>>>(
         (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status,
-        c->shock_r, c->shk, c->shock_list, c->shock_rs, c->outmask);
+        c->shock_r, c->shk, c->shock_list, c->shock_rs, c->outmask, c->lpcache);
   } else {
-    k_lp_rk2<SHAPE, DIM, false, ORDER><<<gb, 256, 0, c->stream>>>(
+    k_lp_rk2<SHAPE, DIM, false, ORDER, CACHED><<<gb, 256, 0, c->stream>>>(
         (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status,
-        nullptr, nullptr, nullptr, nullptr, c->outmask);
+        nullptr, nullptr, nullptr, nullptr, c->outmask, c->lpcache);
   }
   c->launches++;
+  c->lp_cache_ok = true;
   return cudaGetLastError();
+}
+
+template <int SHAPE, int DIM, int ORDER>
+cudaError_t lp_launch_order(part_ctx* c, double dt) {
+  return c->lp_cache_ok ? lp_launch_cached<SHAPE, DIM, ORDER, true>(c, dt)
+                        : lp_launch_cached<SHAPE, DIM, ORDER, false>(c, dt);
 }
 
 template <int SHAPE, int DIM>

@@ -82,6 +82,8 @@ struct part_ctx {
   void* tmp{};        // permute scratch, 8 bytes * capacity
   double* dpart{};    // deposit partials [nbricks][3][ev]
   double* samples{};  // LP samples [3][capacity]: n_new, b2m, gamma_g
+  double* lpcache{};  // LP v, B at the current positions [6][capacity]
+  bool lp_cache_ok{}; // lpcache matches the bound LPs, their order and the fields
   // Boris modes: alternate particle buffers.  part_sort only computes the
   // permutation (perm_pend); the next brick push reads the current buffer
   // through it and writes the other one, so no separate permutation pass is
