@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(2 * kT, 1)
 }
 
 // ---------------------------------------------------------------- particle order, FP64
-template <int SHAPE, int DIM>
+template <int SHAPE, int DIM, bool OPEN>
 __global__ void __launch_bounds__(256)
     k_boris_particles_f64(const double* __restrict__ fp, const Geo g, double* __restrict__ x,
                           double* __restrict__ u, int64_t n, double qm, double dt, int nsteps,
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(256)
     }
     bool bad = false;
     // a particle that has left through an open face is not advanced further
-    for (int st = 0; st < nsteps && !outside_open(g, xp); ++st) {
+    for (int st = 0; st < nsteps && !(OPEN && outside_open(g, xp)); ++st) {
       int j[3] = {0, 0, 0};
       double d[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(256)
           bad = true;
           s = 0.0;
         }
-        if (g.open[a]) s = fmin(fmax(s, 0.0), (double)g.n[a]);
+        if (OPEN && g.open[a]) s = fmin(fmax(s, 0.0), (double)g.n[a]);
         j[a] = floor_clamp_bits(s, g.n[a] - 1);
         d[a] = __dsub_rn(__dsub_rn(s, (double)j[a]), 0.5);
       }
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         const double xa = xp[a] + dt * (up[a] * gi);
-        xp[a] = g.open[a] ? xa : wrap_axis(xa, g.xmin[a], g.xmax[a], g.L[a]);
+        xp[a] = OPEN && g.open[a] ? xa : wrap_axis(xa, g.xmin[a], g.xmax[a], g.L[a]);
       }
       if (bad) break;
     }
@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(256)
       x[a * n + p] = xp[a];
       u[a * n + p] = up[a];
     }
-    if (outmask) outmask[p] = outside_open(g, xp);
+    if (OPEN && outmask) outmask[p] = outside_open(g, xp);
   }
 }
 
@@ -620,7 +620,9 @@ cudaError_t brick_f64(part_ctx* c, double qm, double dt) {
 
 template <int SHAPE, int DIM>
 cudaError_t particles_f64(part_ctx* c, double qm, double dt, int nsteps) {
-  k_boris_particles_f64<SHAPE, DIM><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
+  auto kern = c->geo.any_open ? k_boris_particles_f64<SHAPE, DIM, true>
+                              : k_boris_particles_f64<SHAPE, DIM, false>;
+  kern<<<grid_for(c->n, 256), 256, 0, c->stream>>>(
       (const double*)c->fpad, c->geo, (double*)c->x, (double*)c->u, c->n, qm, dt, nsteps,
       c->status, c->outmask);
   c->launches++;
