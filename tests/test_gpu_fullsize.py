@@ -13,8 +13,8 @@ grid cells) and on properties that fix the whole result at any size.
   keys never decrease, equal keys keep index order), which fix it uniquely;
   cell_start against the oracle's; sampled particles and cells against FP64
   oracle steps.
-- LP RK2 + spectra, 128^3, 4,194,304 LPs x 128 bins: two steps (the second
-  reuses the cached samples) on 4096 sampled LPs.
+- LP RK2 and SSP-RK3 + spectra, 128^3, 4,194,304 LPs x 128 bins: two steps
+  (the second reuses the cached samples) on 4096 sampled LPs.
 - LP shock, 160^3, 16,384,000 LPs x 128 bins: one step on LPs at the shock
   and elsewhere; flags bit-exact, spectra 1e-12.
 - Compaction of the 16.8M FP64 state: every slot, bit-exact.
@@ -276,7 +276,8 @@ def test_fullsize_mixed_256():
     torch.cuda.empty_cache()
 
 
-def test_fullsize_lp_128():
+@pytest.mark.parametrize("order", [2, 3])
+def test_fullsize_lp_128(order):
     n, nlp, nb, seed = 128, 1 << 22, 128, 1238
     og = O.make_grid(3, (n, n, n))
     vel, rho, B = synth.fluid_snapshot(3, n, seed)
@@ -288,6 +289,7 @@ def test_fullsize_lp_128():
     eng = torch.empty_like(chi)
     nold = torch.empty(nlp, dtype=torch.float64, device="cuda")
     p.bind(nlp, x, chi=chi, eng=eng, n_old=nold)
+    p.set_lp_order(order)
     p.init_particles(seed, 0.0, 1.0, 1e6, 2.2, 1e-6)
     p.sync()
     x0, _, _, _ = O.init_particles(og, nlp, seed, 0.0)
@@ -312,7 +314,8 @@ def test_fullsize_lp_128():
         p.gather_push(0.0, dt, 1)
         p.spec_update(dt, c0, 0.0)
         xg, cg, eg, ng = sampled()
-        xr, nn, b2, gm = O.lp_rk2_step(og, P.TSC, vel, rho, B, xs, dt)
+        step = O.lp_rk2_step if order == 2 else O.lp_rk3_step
+        xr, nn, b2, gm = step(og, P.TSC, vel, rho, B, xs, dt)
         cr, er, nr = O.spec_update(cs_, es, ns, nn, b2, gm, dt, c0)
         assert np.max(np.abs(_pdiff(xg, xr))) <= 1e-12 * 2.0
         assert np.max(np.abs(eg - er) / er) <= 1e-12
