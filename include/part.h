@@ -63,7 +63,7 @@ typedef enum {
   PART_ECUDA = 3,         /* a CUDA runtime call failed                     */
   PART_ETIMEOUT = 4,      /* a bounded device wait ran out                  */
   PART_ENONFINITE = 5,    /* NaN/Inf met in particle state or samples       */
-  PART_EUNSUPPORTED = 6,  /* valid request this build does not implement    */
+  PART_EUNSUPPORTED = 6,  /* valid request the library does not implement  */
   PART_EDOMAIN = 7        /* a particle was not in the cell it was sorted by */
 } part_status;
 

@@ -506,7 +506,7 @@ part_status part_gather_push(part_ctx* c, double q_over_m, double dt, int nsteps
     e = launch_boris(c, q_over_m, dt, nsteps);
     c->moved += std::fabs(dt) * nsteps;  // |v| < 1: displacement bound
     if (e == cudaErrorNotSupported)
-      return fail(c, PART_EUNSUPPORTED, "this precision/mode has no kernel in this build");
+      return fail(c, PART_EUNSUPPORTED, "no kernel implements this precision/mode combination");
     c->deposit_ready = c->deposit_on;
   } else {
     if (nsteps != 1) return fail(c, PART_EINVAL, "LP mode advances one step per call");
