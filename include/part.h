@@ -262,6 +262,16 @@ const char* part_last_error(const part_ctx* ctx);
 /* Kernel launches this context has enqueued since creation.               */
 int64_t part_launch_count(const part_ctx* ctx);
 
+/* Self-test of the bounded device waits (failure detection without a
+ * fault).  Enqueues one kernel whose thread waits on a shared-memory
+ * mbarrier with the wait every TMA-fed kernel uses, limited to limit_ns
+ * (0 < limit_ns <= 1e10).  arrive = 1: the thread arrives first and the wait
+ * succeeds.  arrive = 0: nothing arrives, the wait gives up after limit_ns,
+ * and the next part_sync returns PART_ETIMEOUT (and clears it); the context
+ * stays usable.  The kernels' own limit is 1 s.  PART_EINVAL on bad
+ * arguments.                                                               */
+part_status part_selftest_wait(part_ctx* ctx, int64_t limit_ns, int arrive);
+
 /* ---- Serving: continuous batching of test-particle requests --------------
  * Test particles (no deposit) of many independent requests advance against
  * field snapshots that stay resident on the device, each snapshot being a

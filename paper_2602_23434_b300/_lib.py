@@ -105,6 +105,7 @@ def lib():
         "part_sync": (st, [P]),
         "part_last_error": (C.c_char_p, [P]),
         "part_launch_count": (C.c_int64, [P]),
+        "part_selftest_wait": (st, [P, C.c_int64, C.c_int]),
         "part_sort_fp64_noalloc": (st, [G, C.c_int64, P, P, P, P, P, P]),
         "part_server_sizes": (st, [C.c_int, C.c_int, C.POINTER(C.c_size_t),
                                    C.POINTER(C.c_size_t)]),
@@ -265,3 +266,7 @@ class Part:
 
     def launches(self) -> int:
         return int(self.L.part_launch_count(self.ctx))
+
+    def selftest_wait(self, limit_ns: int, arrive: bool):
+        """One bounded mbarrier wait on the device (see part_selftest_wait)."""
+        self._check(self.L.part_selftest_wait(self.ctx, int(limit_ns), 1 if arrive else 0))

@@ -592,4 +592,14 @@ const char* part_last_error(const part_ctx* c) {
 
 int64_t part_launch_count(const part_ctx* c) { return c ? c->launches : 0; }
 
+part_status part_selftest_wait(part_ctx* c, int64_t limit_ns, int arrive) {
+  if (check_ctx(c)) return PART_EINVAL;
+  if (limit_ns <= 0 || limit_ns > 10000000000LL)
+    return fail(c, PART_EINVAL, "limit_ns must be in (0, 1e10]");
+  if (arrive != 0 && arrive != 1) return fail(c, PART_EINVAL, "arrive must be 0 or 1");
+  cudaError_t e = launch_selftest_wait(c, limit_ns, arrive);
+  if (e != cudaSuccess) return cuda_fail(c, e, "part_selftest_wait");
+  return PART_OK;
+}
+
 }  // extern "C"

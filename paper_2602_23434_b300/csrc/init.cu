@@ -238,3 +238,25 @@ cudaError_t launch_init(part_ctx* c, uint64_t seed, double u_th, double emin, do
   }
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------- wait self-test
+// One thread waits on a shared-memory mbarrier with the kernels' bounded wait.
+// With arrive = 1 it arrives first (the wait succeeds at once); with arrive = 0
+// nothing ever arrives, the wait gives up after limit_ns and ST_TIMEOUT is
+// latched, exactly as a brick kernel does when its TMA copy never lands.
+namespace {
+__global__ void k_selftest_wait(int* __restrict__ status, uint64_t limit_ns, int arrive) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  if (arrive)
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar)) : "memory");
+  if (!mbar_wait_for(&bar, 0, limit_ns)) atomicOr(status, ST_TIMEOUT);
+}
+}  // namespace
+
+cudaError_t launch_selftest_wait(part_ctx* c, int64_t limit_ns, int arrive) {
+  k_selftest_wait<<<1, 32, 0, c->stream>>>(c->status, (uint64_t)limit_ns, arrive);
+  c->launches++;
+  return cudaGetLastError();
+}

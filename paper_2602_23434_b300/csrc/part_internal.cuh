@@ -165,11 +165,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: gives up after a fixed number of polls and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 20); ++it)
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: polls until the phase completes, limit_ns have passed on the
+// global timer, or (should the timer stall) 2^26 polls were made; returns
+// false when it gave up.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: far above any TMA copy
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity,
+                                              uint64_t limit_ns) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
   return false;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_for(bar, parity, kWaitLimitNs);
 }
 
 // 4-D tiled TMA load global -> shared, completion signalled on bar.
@@ -298,5 +315,6 @@ cudaError_t launch_serve_kernel(int shape, int dim, const ServeHeader* hdr,
 cudaError_t launch_deposit_combine(part_ctx* c, double* out);
 cudaError_t launch_lp_push(part_ctx* c, double dt, int nsteps);
 cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad);
+cudaError_t launch_selftest_wait(part_ctx* c, int64_t limit_ns, int arrive);  // init.cu
 cudaError_t launch_init(part_ctx* c, uint64_t seed, double u_th, double emin, double emax,
                         double p, double N0);

@@ -221,6 +221,46 @@ def test_init_particles_fp64_and_mixed():
     assert _rel(_host(uf).astype(np.float64), uo, 0.1) <= 1e-6
 
 
+def test_bounded_wait_times_out_and_the_context_survives():
+    """Failure detection without a fault: a device wait that nothing
+    completes gives up after its limit, the next part_sync reports
+    PART_ETIMEOUT (and clears it), and the same context then steps and
+    deposits like a fresh one."""
+    import time
+    og, pg, f, x, u, w, ids, N = _boris_case(3, 16, 4, P.TSC, 5)
+    qm, dt = 1.0, 0.5 * (2.0 / 16)
+    p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=N)
+    p.selftest_wait(10_000_000, True)                 # completed wait: no error
+    p.sync()
+    t0 = time.perf_counter()
+    p.selftest_wait(20_000_000, False)                # nothing arrives: 20 ms limit
+    with pytest.raises(P.PartError) as e:
+        p.sync()
+    assert e.value.name == "PART_ETIMEOUT"
+    assert time.perf_counter() - t0 >= 0.02
+    p.sync()                                          # latched once, then cleared
+    for bad in (0, -1, 10 ** 11):
+        with pytest.raises(P.PartError):
+            p.selftest_wait(bad, False)
+    p.set_fields(_dev(f))
+    xd, ud, wd = _dev(x), _dev(u), _dev(w)
+    p.bind(N, xd, u=ud, w=wd)
+    p.enable_deposit(True)
+    p.sort()
+    p.sync()
+    xs, us, ws = _host(xd), _host(ud), _host(wd)
+    p.gather_push(qm, dt, 1)
+    out = torch.empty((3, 16 ** 3), dtype=torch.float64, device="cuda")
+    p.deposit(out)
+    p.sync()
+    xr, ur, F, xo = O.boris_step(og, P.TSC, f, xs, us, ws, qm, dt, True)
+    assert np.max(np.abs(_pdiff(_host(xd), xr))) <= 1e-12 * 2.0
+    assert _rel(_host(ud), ur, np.max(np.abs(ur))) <= 1e-12
+    dref = O.deposit(og, P.TSC, xo, F)
+    dabs = O.deposit(og, P.TSC, xo, np.abs(F))
+    assert np.max(np.abs(_host(out) - dref) / np.maximum(dabs, 1e-300)) <= 1e-12
+
+
 def test_error_paths():
     og, pg = _grids(3, 16)
     N = 1000
