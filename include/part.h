@@ -159,6 +159,22 @@ part_status part_flush(part_ctx* ctx);
  * the sort.                                                                 */
 part_status part_compact(part_ctx* ctx, const uint8_t* deleted, int64_t* n_new);
 
+/* Append k >= 0 particles at run time (the injection of Sec. 3.2, "Minimize
+ * memory allocation/deallocation": the set grows inside memory allocated
+ * once, up to the context's capacity).  Every bound array is re-laid out
+ * from row stride n to row stride n + k (component a of particle p at
+ * a*(n+k) + p) and the new particles fill slots n .. n+k-1; the context's n
+ * becomes n + k.  Each bound array must therefore hold rows x (n + k)
+ * elements (bind arrays allocated at capacity).  Sources are device arrays
+ * in the bound layout with row stride k: x_or_cell, and u (Boris), off
+ * (PART_MIXED), chi, eng, n_old (LP); w and id are read only when the bound
+ * set has w and id planes, and are then required.  Shock flags, when
+ * enabled, are cleared for the new particles.  PART_EINVAL if n + k exceeds
+ * the capacity or a required source is NULL.  Invalidates the sort.        */
+part_status part_inject(part_ctx* ctx, int64_t k, const void* x_or_cell, const void* off,
+                        const void* u, const void* w, const uint64_t* id, const double* chi,
+                        const double* eng, const double* n_old);
+
 /* Outflow mask (grids with an open axis): every push writes, per bound
  * particle, 1 if it ended outside the domain along an open axis, else 0
  * (device uint8[n], caller-owned, in the order of the bound arrays after the

@@ -106,6 +106,7 @@ def lib():
         "part_last_error": (C.c_char_p, [P]),
         "part_launch_count": (C.c_int64, [P]),
         "part_selftest_wait": (st, [P, C.c_int64, C.c_int]),
+        "part_inject": (st, [P, C.c_int64, P, P, P, P, P, P, P, P]),
         "part_sort_fp64_noalloc": (st, [G, C.c_int64, P, P, P, P, P, P]),
         "part_server_sizes": (st, [C.c_int, C.c_int, C.POINTER(C.c_size_t),
                                    C.POINTER(C.c_size_t)]),
@@ -214,6 +215,14 @@ class Part:
         nn = C.c_int64()
         self._check(self.L.part_compact(self.ctx, _ptr(deleted), C.byref(nn)))
         return nn.value
+
+    def inject(self, k, x, off=None, u=None, w=None, ids=None, chi=None, eng=None,
+               n_old=None):
+        """Append k particles (device arrays, bound layout, row stride k); the
+        bound arrays must hold rows x (n + k) elements."""
+        self._check(self.L.part_inject(self.ctx, int(k), _ptr(x), _ptr(off), _ptr(u), _ptr(w),
+                                       _ptr(ids), _ptr(chi), _ptr(eng), _ptr(n_old)))
+        self._keep_inj = (x, off, u, w, ids, chi, eng, n_old)
 
     def set_outflow(self, mask):
         """Device uint8[n] written by every push: 1 where the particle left the

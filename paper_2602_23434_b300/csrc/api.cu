@@ -419,6 +419,37 @@ part_status part_compact(part_ctx* c, const uint8_t* deleted, int64_t* n_new) {
   return PART_OK;
 }
 
+part_status part_inject(part_ctx* c, int64_t k, const void* x_or_cell, const void* off,
+                        const void* u, const void* w, const uint64_t* id, const double* chi,
+                        const double* eng, const double* n_old) {
+  if (check_ctx(c)) return PART_EINVAL;
+  if (!c->bound) return fail(c, PART_EINVAL, "no particles bound");
+  if (k < 0 || k > c->capacity - c->n)
+    return fail(c, PART_EINVAL, "k must be in [0, capacity - n]");
+  if (k > 0) {
+    if (!x_or_cell) return fail(c, PART_EINVAL, "new positions are NULL");
+    if (c->mode == PART_BORIS && !u) return fail(c, PART_EINVAL, "new u is NULL");
+    if (c->prec == PART_MIXED && !off) return fail(c, PART_EINVAL, "new offsets are NULL");
+    if (c->mode == PART_LP_RK2 && (!chi || !eng || !n_old))
+      return fail(c, PART_EINVAL, "LP mode needs the new chi, eng and n_old");
+    if (c->w && !w) return fail(c, PART_EINVAL, "w is bound: the new w are needed");
+    if (c->id && !id) return fail(c, PART_EINVAL, "id is bound: the new ids are needed");
+  }
+  cudaError_t e = flush_pending(c);
+  const InjectSrc src{x_or_cell, off, u, w, id, chi, eng, n_old};
+  if (e == cudaSuccess) e = launch_inject(c, k, src);
+  if (e != cudaSuccess) return cuda_fail(c, e, "part_inject");
+  if (k == 0) return PART_OK;
+  c->n += k;
+  c->sorted = false;
+  c->order_kept = false;
+  c->lp_cache_ok = false;
+  c->deposit_ready = false;
+  c->samples_ready = false;
+  c->shock_listed = false;
+  return PART_OK;
+}
+
 part_status part_set_outflow(part_ctx* c, uint8_t* mask) {
   if (check_ctx(c)) return PART_EINVAL;
   if (mask && !c->geo.any_open) return fail(c, PART_EINVAL, "the grid has no open axis");

@@ -304,6 +304,12 @@ inline PState state_of(const part_ctx* c, bool alt) {
           c->id ? c->alt_id : nullptr};
 }
 cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew);
+struct InjectSrc {
+  const void *x, *off, *u, *w;
+  const uint64_t* id;
+  const double *chi, *eng, *n_old;
+};
+cudaError_t launch_inject(part_ctx* c, int64_t k, const InjectSrc& src);  // sort.cu
 cudaError_t launch_sort_incremental(part_ctx* c);  // see sort.cu
 cudaError_t launch_shock_cells(part_ctx* c);       // shock_r from the padded LP fields
 cudaError_t launch_shock_convolve(part_ctx* c);    // Eq. convolution_spectra on the list

@@ -814,7 +814,67 @@ cudaError_t fill_rows(part_ctx* c, T* base, int rows, const uint8_t* del, int64_
   return cudaGetLastError();
 }
 
+// Injection: rows r >= 1 move up from stride n to stride n + k (row r by
+// S = r k elements), the highest row first so that a row only overwrites
+// source rows already moved; a row that overlaps its own source is copied
+// back to front in stream-ordered chunks of at most S (no chunk overlaps the
+// source still to be read), or through the scratch row when that would take
+// many chunks.  Then the k new elements of each row go to its slots n..n+k-1.
+template <typename T>
+cudaError_t grow_rows(part_ctx* c, T* base, int rows, int64_t n, int64_t k, const T* src) {
+  cudaError_t e = cudaSuccess;
+  const int64_t m = n + k;
+  for (int r = rows - 1; r >= 1 && n > 0 && k > 0 && e == cudaSuccess; --r) {
+    T* from = base + (int64_t)r * n;
+    T* to = base + (int64_t)r * m;
+    const int64_t S = (int64_t)r * k;
+    if (S >= n) {
+      e = cudaMemcpyAsync(to, from, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream);
+    } else if ((n + S - 1) / S <= 16) {
+      for (int64_t hi = n; hi > 0 && e == cudaSuccess; hi -= S) {
+        const int64_t lo = hi > S ? hi - S : 0;
+        e = cudaMemcpyAsync(to + lo, from + lo, sizeof(T) * (hi - lo), cudaMemcpyDeviceToDevice,
+                            c->stream);
+      }
+    } else {
+      e = cudaMemcpyAsync(c->tmp, from, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(to, c->tmp, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream);
+    }
+  }
+  for (int r = 0; r < rows && k > 0 && e == cudaSuccess; ++r)
+    e = cudaMemcpyAsync(base + (int64_t)r * m + n, src + (int64_t)r * k, sizeof(T) * k,
+                        cudaMemcpyDeviceToDevice, c->stream);
+  return e;
+}
+
 }  // namespace
+
+cudaError_t launch_inject(part_ctx* c, int64_t k, const InjectSrc& s) {
+  const int64_t n = c->n;
+  cudaError_t e = cudaSuccess;
+  if (k == 0) return e;
+  if (c->mode == PART_BORIS && c->prec == PART_FP64) {
+    e = grow_rows<double>(c, (double*)c->x, 3, n, k, (const double*)s.x);
+    if (e == cudaSuccess) e = grow_rows<double>(c, (double*)c->u, 3, n, k, (const double*)s.u);
+    if (e == cudaSuccess && c->w)
+      e = grow_rows<double>(c, (double*)c->w, 1, n, k, (const double*)s.w);
+  } else if (c->mode == PART_BORIS) {
+    e = grow_rows<int32_t>(c, (int32_t*)c->x, 1, n, k, (const int32_t*)s.x);
+    if (e == cudaSuccess) e = grow_rows<float>(c, (float*)c->off, 3, n, k, (const float*)s.off);
+    if (e == cudaSuccess) e = grow_rows<float>(c, (float*)c->u, 3, n, k, (const float*)s.u);
+    if (e == cudaSuccess && c->w)
+      e = grow_rows<float>(c, (float*)c->w, 1, n, k, (const float*)s.w);
+  } else {
+    e = grow_rows<double>(c, (double*)c->x, 3, n, k, (const double*)s.x);
+    if (e == cudaSuccess) e = grow_rows<double>(c, c->chi, c->nbins, n, k, s.chi);
+    if (e == cudaSuccess) e = grow_rows<double>(c, c->eng, c->nbins, n, k, s.eng);
+    if (e == cudaSuccess) e = grow_rows<double>(c, c->n_old, 1, n, k, s.n_old);
+    if (e == cudaSuccess && c->shk) e = cudaMemsetAsync(c->shk + n, 0, (size_t)k, c->stream);
+  }
+  if (e == cudaSuccess && c->id) e = grow_rows<uint64_t>(c, c->id, 1, n, k, s.id);
+  return e;
+}
 
 cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew_out) {
   const int64_t n = c->n;

@@ -149,3 +149,109 @@ def test_compact_empty_and_errors():
     with pytest.raises(P.PartError) as e:
         p.compact(None)
     assert e.value.name == "PART_EINVAL"
+
+
+def _flat(t, rows, n):
+    """First rows*n elements of a flat buffer as [rows][n] (row stride n)."""
+    return _host(t.reshape(-1)[: rows * n]).reshape(rows, n)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "lp"])
+def test_inject_then_sort_then_compact(mode):
+    """Run-time injection (Sec. 3.2): buffers allocated once at the capacity;
+    the set grows by k = 0, a ragged k and then exactly to the capacity; every
+    plane equals the concatenation of the old and the new particles at the new
+    row stride; one more particle is refused.  The grown set then sorts like
+    any particle set (the oracle's stable sort) and compacts bit-exactly.  LP
+    shock flags of the new particles are cleared, the old ones kept."""
+    n, C, n0, k2 = 16, 16 ** 3 * 3 + 7, 4000, 1237
+    og = O.make_grid(3, (n, n, n))
+    rng = np.random.default_rng(17)
+    x_all, u_all, _, ids_all = synth.particles(3, None, C, 19)
+    ids_all = ids_all.astype(np.int64) * 5 + 3
+    w_all = rng.uniform(0.5, 2.0, C)
+    nb = 6
+    chi_all = rng.uniform(0.0, 1.0, (nb, C))
+    eng_all = np.sort(rng.uniform(1.0, 10.0, (nb, C)), axis=0)
+    nold_all = rng.uniform(0.5, 2.0, C)
+    if mode == "mixed":
+        dx = 2.0 / n
+        j = np.minimum(np.floor((x_all + 1.0) / dx), n - 1).astype(np.int64)
+        off_all = ((x_all + 1.0) / dx - j - 0.5).astype(np.float32)
+        cell_all = ((j[2] * n + j[1]) * n + j[0]).astype(np.int32)
+        planes = {"x": (cell_all, 1, torch.int32), "off": (off_all, 3, torch.float32),
+                  "u": (u_all.astype(np.float32), 3, torch.float32),
+                  "w": (w_all.astype(np.float32), 1, torch.float32),
+                  "ids": (ids_all, 1, torch.int64)}
+        p = P.Part(P.make_grid(3, n), P.MIXED, P.TSC, P.BORIS, capacity=C)
+    elif mode == "fp64":
+        planes = {"x": (x_all, 3, torch.float64), "u": (u_all, 3, torch.float64),
+                  "w": (w_all, 1, torch.float64), "ids": (ids_all, 1, torch.int64)}
+        p = P.Part(P.make_grid(3, n), P.FP64, P.TSC, P.BORIS, capacity=C)
+    else:
+        planes = {"x": (x_all, 3, torch.float64), "chi": (chi_all, nb, torch.float64),
+                  "eng": (eng_all, nb, torch.float64), "n_old": (nold_all, 1, torch.float64),
+                  "ids": (ids_all, 1, torch.int64)}
+        p = P.Part(P.make_grid(3, n), P.FP64, P.TSC, P.LP_RK2, capacity=C, nbins=nb)
+
+    def rows_of(a, rows):
+        return a.reshape(rows, -1)
+
+    # buffers of capacity rows x C; the first n0 particles at row stride n0
+    buf = {}
+    for k, (a, rows, dt) in planes.items():
+        b = torch.zeros(rows * C, dtype=dt, device="cuda")
+        b[: rows * n0] = torch.as_tensor(np.ascontiguousarray(rows_of(a, rows)[:, :n0])).reshape(-1)
+        buf[k] = b
+    p.bind(n0, buf["x"], off=buf.get("off"), u=buf.get("u"), w=buf.get("w"), ids=buf["ids"],
+           chi=buf.get("chi"), eng=buf.get("eng"), n_old=buf.get("n_old"))
+    st = None
+    if mode == "lp":
+        vel, rho, B = synth.fluid_snapshot(3, n, 5, v_rms=0.05)
+        p.set_fields(torch.as_tensor(np.concatenate([vel, rho, B]).reshape(7, -1)).cuda())
+        st = torch.ones(C, dtype=torch.uint8, device="cuda")
+        p.enable_shocks(1.2, st)
+
+    def src(lo, hi):
+        return {k: torch.as_tensor(np.ascontiguousarray(rows_of(a, rows)[:, lo:hi])).cuda()
+                for k, (a, rows, dt) in planes.items()}
+
+    cur = n0
+    for k in (0, k2, C - n0 - k2):
+        s = src(cur, cur + k)
+        p.inject(k, s["x"], off=s.get("off"), u=s.get("u"), w=s.get("w"), ids=s["ids"],
+                 chi=s.get("chi"), eng=s.get("eng"), n_old=s.get("n_old"))
+        cur += k
+        p.sync()
+        for name, (a, rows, dt) in planes.items():
+            assert np.array_equal(_flat(buf[name], rows, cur), rows_of(a, rows)[:, :cur]), name
+        if st is not None:
+            sh = _host(st)[:cur]
+            assert np.all(sh[:n0] == 1) and np.all(sh[n0:] == 0)
+    assert cur == C
+    s = src(0, 1)
+    with pytest.raises(P.PartError) as e:
+        p.inject(1, s["x"], off=s.get("off"), u=s.get("u"), w=s.get("w"), ids=s["ids"],
+                 chi=s.get("chi"), eng=s.get("eng"), n_old=s.get("n_old"))
+    assert e.value.name == "PART_EINVAL"
+    # sort: the oracle's stable sort of the whole grown set
+    p.sort()
+    p.sync()
+    if mode == "mixed":
+        tab = np.array([O.cell_key(og, p.brick, (c % n, (c // n) % n, c // (n * n)))
+                        for c in range(n ** 3)], dtype=np.uint32)
+        keys = tab[cell_all]
+    else:
+        keys = O.keys(og, p.brick, x_all)
+    perm = O.stable_sort(keys)
+    for name, (a, rows, dt) in planes.items():
+        assert np.array_equal(_flat(buf[name], rows, C), rows_of(a, rows)[:, perm]), name
+    # compaction of the grown, sorted set
+    d = rng.random(C) < 0.3
+    nn = p.compact(torch.as_tensor(d.astype(np.uint8)).cuda())
+    nk, srcmap = O.compact_map(d)
+    assert nn == nk
+    p.sync()
+    for name, (a, rows, dt) in planes.items():
+        assert np.array_equal(_flat(buf[name], rows, nk), rows_of(a, rows)[:, perm][:, srcmap]), \
+            name

@@ -262,3 +262,61 @@ def test_open_errors():
                             C.c_void_p(stage.data_ptr()), hb.value, C.c_void_p(s.cuda_stream),
                             256, 4)
     assert rc == 6 and b"periodic" in L.part_last_error(None)   # PART_EUNSUPPORTED
+
+
+def test_open_inflow_injection_and_outflow_removal():
+    """An open-x run whose particle count is kept up at run time (Sec. 3.2):
+    every step new particles are injected at the inflow face, the set is
+    sorted and pushed, and those that left through any open face are removed
+    by part_compact with the outflow mask.  The oracle does the same
+    (concatenate, stable sort, Boris step, outside flags, compaction map);
+    flags and ids bit-exact, positions within 1e-12 per step."""
+    dim, n, opn = 3, 16, (1, 0, 0)
+    og = O.make_grid(dim, (n, n, n), open_axes=opn)
+    pg = P.make_grid(dim, n, open_axes=opn)
+    C = n ** 3 * 3
+    N0, K = n ** 3 * 2, 900
+    x, u, _, ids = _near_faces(dim, N0, 31, opn)
+    f = synth.em_fields(dim, n, 4, v_rms=0.05).reshape(6, -1)
+    p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=C)
+    p.set_fields(_dev(f))
+    xb = torch.zeros(3 * C, dtype=torch.float64, device="cuda")
+    ub = torch.zeros(3 * C, dtype=torch.float64, device="cuda")
+    ib = torch.zeros(C, dtype=torch.int64, device="cuda")
+    xb[: 3 * N0] = _dev(x).reshape(-1)
+    ub[: 3 * N0] = _dev(u).reshape(-1)
+    ib[:N0] = torch.as_tensor(ids.astype(np.int64)).cuda()
+    out = torch.zeros(C, dtype=torch.uint8, device="cuda")
+    p.bind(N0, xb, u=ub, ids=ib)
+    p.set_outflow(out)
+    dt = 0.8 * 2.0 / n
+    xr, ur, ir = x.copy(), u.copy(), ids.astype(np.int64)
+    rng = np.random.default_rng(37)
+    next_id = N0
+    for step in range(4):
+        # inflow: K particles in the first cell layer, moving in +x
+        xn = np.stack([rng.uniform(-1.0, -1.0 + 2.0 / n, K), rng.uniform(-1.0, 1.0, K),
+                       rng.uniform(-1.0, 1.0, K)])
+        un = rng.normal(0.0, 0.5, (3, K))
+        un[0] = np.abs(un[0])
+        idn = np.arange(next_id, next_id + K, dtype=np.int64)
+        next_id += K
+        p.inject(K, _dev(xn), u=_dev(un), ids=torch.as_tensor(idn).cuda())
+        xr, ur, ir = np.concatenate([xr, xn], 1), np.concatenate([ur, un], 1), \
+            np.concatenate([ir, idn])
+        p.sort()
+        perm = O.stable_sort(O.keys(og, p.brick, xr))
+        xr, ur, ir = xr[:, perm], ur[:, perm], ir[perm]
+        p.gather_push(1.0, dt, 1)
+        xr, ur, _, _ = O.boris_step(og, P.TSC, f, xr, ur, None, 1.0, dt)
+        p.sync()
+        m = O.outside(og, xr)
+        assert np.array_equal(_host(out)[: xr.shape[1]], m)
+        nn = p.compact(out)
+        k, src = O.compact_map(m)
+        assert nn == k and 0 < m.sum()
+        xr, ur, ir = xr[:, src], ur[:, src], ir[src]
+        p.sync()
+        assert np.array_equal(_host(ib)[:k], ir)
+        xg = _host(xb)[: 3 * k].reshape(3, k)
+        assert np.max(np.abs(_pdiff(xg, xr))) <= 1e-12 * 2.0 * (step + 1)
