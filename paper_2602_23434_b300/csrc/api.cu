@@ -32,6 +32,26 @@ part_status cuda_fail(part_ctx* c, cudaError_t e, const char* where) {
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
+// Element alignment of a caller array (the kernels load whole elements).
+bool misaligned(const void* p, size_t elem) {
+  return p && (reinterpret_cast<uintptr_t>(p) % elem) != 0;
+}
+
+// Element sizes of the particle planes of this context: positions (or cells),
+// offsets, u, w.
+size_t pos_elem(const part_ctx* c) { return c->prec == PART_MIXED ? 4 : 8; }
+size_t real_elem(const part_ctx* c) { return c->prec == PART_MIXED ? 4 : 8; }
+
+part_status check_planes(part_ctx* c, const void* x, const void* off, const void* u,
+                         const void* w, const void* id, const void* chi, const void* eng,
+                         const void* n_old) {
+  if (misaligned(x, pos_elem(c)) || misaligned(off, 4) || misaligned(u, real_elem(c)) ||
+      misaligned(w, real_elem(c)) || misaligned(id, 8) || misaligned(chi, 8) ||
+      misaligned(eng, 8) || misaligned(n_old, 8))
+    return fail(c, PART_EINVAL, "a particle array is not aligned to its element size");
+  return PART_OK;
+}
+
 }  // namespace
 
 part_status check_grid(const part_grid* g) {
@@ -331,6 +351,8 @@ part_status part_set_fields(part_ctx* c, const void* fields, int ncomp, part_pre
     return fail(c, PART_EINVAL, c->mode == PART_BORIS ? "Boris mode needs ncomp = 6 (E, B)"
                                                       : "LP mode needs ncomp = 7 (v, rho, B)");
   if (field_prec != c->prec) return fail(c, PART_EINVAL, "field_prec must match the context");
+  if (misaligned(fields, c->prec == PART_MIXED ? 4 : 8))
+    return fail(c, PART_EINVAL, "fields are not aligned to their element size");
   cudaError_t e = launch_pad_fields(c, fields);
   if (e == cudaSuccess && c->shk) e = launch_shock_cells(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_set_fields");
@@ -349,6 +371,7 @@ part_status part_bind_particles(part_ctx* c, int64_t n, void* x_or_cell, void* o
     if (e != cudaSuccess) return cuda_fail(c, e, "part_bind_particles");
   }
   if (n > 0 && !x_or_cell) return fail(c, PART_EINVAL, "positions are NULL");
+  if (check_planes(c, x_or_cell, off, u, w, id, chi, eng, n_old)) return PART_EINVAL;
   if (c->mode == PART_BORIS) {
     if (n > 0 && !u) return fail(c, PART_EINVAL, "u is NULL");
     if (c->prec == PART_MIXED && n > 0 && !off)
@@ -434,6 +457,7 @@ part_status part_inject(part_ctx* c, int64_t k, const void* x_or_cell, const voi
       return fail(c, PART_EINVAL, "LP mode needs the new chi, eng and n_old");
     if (c->w && !w) return fail(c, PART_EINVAL, "w is bound: the new w are needed");
     if (c->id && !id) return fail(c, PART_EINVAL, "id is bound: the new ids are needed");
+    if (check_planes(c, x_or_cell, off, u, w, id, chi, eng, n_old)) return PART_EINVAL;
   }
   cudaError_t e = flush_pending(c);
   const InjectSrc src{x_or_cell, off, u, w, id, chi, eng, n_old};
@@ -554,6 +578,7 @@ part_status part_gather_push(part_ctx* c, double q_over_m, double dt, int nsteps
 part_status part_deposit(part_ctx* c, double* grid_out) {
   if (check_ctx(c)) return PART_EINVAL;
   if (!grid_out) return fail(c, PART_EINVAL, "grid_out is NULL");
+  if (misaligned(grid_out, 8)) return fail(c, PART_EINVAL, "grid_out is not 8-byte aligned");
   if (c->mode != PART_BORIS || !c->deposit_ready)
     return fail(c, PART_EINVAL, "no deposit pending: enable it and push first");
   cudaError_t e = launch_deposit_combine(c, grid_out);

@@ -83,6 +83,10 @@ extern "C" part_status part_sort_fp64_noalloc(const part_grid* grid, int64_t n, 
                 "sort; use part_sort with a workspace for more particles");
   if (n > 0 && (!x || !u)) return fail(nullptr, PART_EINVAL, "x and u must not be NULL");
   if (!cell_start) return fail(nullptr, PART_EINVAL, "cell_start must not be NULL");
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(u) |
+       reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(id)) % 8 != 0 ||
+      reinterpret_cast<uintptr_t>(cell_start) % 4 != 0)
+    return fail(nullptr, PART_EINVAL, "an array is not aligned to its element size");
   void* base = nullptr;
   if ((s = scratch_for_current_device(&base)) != PART_OK) return s;
   char* b = static_cast<char*>(base);

@@ -261,6 +261,27 @@ def test_bounded_wait_times_out_and_the_context_survives():
     assert np.max(np.abs(_host(out) - dref) / np.maximum(dabs, 1e-300)) <= 1e-12
 
 
+def test_misaligned_arrays_refused_on_the_host():
+    """A caller array not aligned to its element size would fault in a
+    kernel; every entry point that takes one refuses it before any launch."""
+    import ctypes as C
+    og, pg = _grids(3, 8)
+    N = 100
+    p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=N)
+    raw = torch.zeros(8 * 6 * N + 64, dtype=torch.uint8, device="cuda")
+    good = raw.data_ptr() + 64 - raw.data_ptr() % 64
+    L = P.lib()
+    bad = C.c_void_p(good + 4)
+    ok = C.c_void_p(good)
+    l0 = p.launches()
+    assert L.part_bind_particles(p.ctx, N, bad, None, ok, None, None, None, None, None) != 0
+    assert L.part_bind_particles(p.ctx, N, ok, None, bad, None, None, None, None, None) != 0
+    assert L.part_set_fields(p.ctx, bad, 6, P.FP64) != 0
+    assert L.part_sort_fp64_noalloc(C.byref(pg), N, bad, ok, None, None, ok, None) != 0
+    assert p.launches() == l0
+    p.sync()
+
+
 def test_error_paths():
     og, pg = _grids(3, 16)
     N = 1000
