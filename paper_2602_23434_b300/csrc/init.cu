@@ -188,13 +188,6 @@ __global__ void k_pad_fields_aos8(const float* __restrict__ src, float* __restri
   }
 }
 
-int grid_for(int64_t n, int threads) {
-  int64_t b = (n + threads - 1) / threads;
-  if (b < 1) b = 1;
-  if (b > 148 * 64) b = 148 * 64;
-  return (int)b;
-}
-
 }  // namespace
 
 cudaError_t launch_pad_fields(part_ctx* c, const void* src) {

@@ -281,13 +281,6 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
-int grid_for(int64_t n, int threads) {
-  int64_t b = (n + threads - 1) / threads;
-  if (b < 1) b = 1;
-  if (b > 148 * 64) b = 148 * 64;
-  return (int)b;
-}
-
 template <int SHAPE, int DIM, int ORDER, bool CACHED>
 cudaError_t lp_launch_cached(part_ctx* c, double dt) {
   const int gb = grid_for(c->n, 256);

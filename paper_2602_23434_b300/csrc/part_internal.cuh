@@ -4,6 +4,7 @@
 // (mbarrier, TMA tensor copies) used by the kernels.  sm_103a only.
 #pragma once
 
+#include <cstdint>
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -321,6 +322,33 @@ cudaError_t launch_serve_kernel(int shape, int dim, const ServeHeader* hdr,
 cudaError_t launch_deposit_combine(part_ctx* c, double* out);
 cudaError_t launch_lp_push(part_ctx* c, double dt, int nsteps);
 cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad);
+
+// Launch shapes.  148 SMs; grid-stride kernels are capped at 64 CTAs per SM.
+constexpr int kSMs = 148;
+inline int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > kSMs * 64) b = kSMs * 64;
+  return (int)b;
+}
+// CTA size (256, 128 or 64 threads, one particle each) that spreads a set too
+// small to fill the GPU most evenly over the SMs: the one whose fullest SM
+// holds the fewest particles (65,536 particles: 64 threads, 448 per SM
+// instead of 512).  Sets of a full wave or more keep 256.
+inline int threads_for_spread(int64_t n) {
+  if (n >= (int64_t)kSMs * 2048) return 256;
+  int best = 256;
+  int64_t best_load = INT64_MAX;
+  for (int t : {256, 128, 64}) {
+    const int64_t blocks = (n + t - 1) / t;
+    const int64_t load = (blocks + kSMs - 1) / kSMs * t;
+    if (load < best_load) {
+      best_load = load;
+      best = t;
+    }
+  }
+  return best;
+}
 cudaError_t launch_selftest_wait(part_ctx* c, int64_t limit_ns, int arrive);  // init.cu
 cudaError_t launch_init(part_ctx* c, uint64_t seed, double u_th, double emin, double emax,
                         double p, double N0);

@@ -584,13 +584,6 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-int grid_for(int64_t n, int threads) {
-  int64_t b = (n + threads - 1) / threads;
-  if (b < 1) b = 1;
-  if (b > 148 * 64) b = 148 * 64;
-  return (int)b;
-}
-
 template <int SHAPE, int DIM, bool DEP>
 cudaError_t brick_f64(part_ctx* c, double qm, double dt) {
   const bool open = c->geo.any_open != 0;
@@ -622,7 +615,8 @@ template <int SHAPE, int DIM>
 cudaError_t particles_f64(part_ctx* c, double qm, double dt, int nsteps) {
   auto kern = c->geo.any_open ? k_boris_particles_f64<SHAPE, DIM, true>
                               : k_boris_particles_f64<SHAPE, DIM, false>;
-  kern<<<grid_for(c->n, 256), 256, 0, c->stream>>>(
+  const int t = threads_for_spread(c->n);
+  kern<<<grid_for(c->n, t), t, 0, c->stream>>>(
       (const double*)c->fpad, c->geo, (double*)c->x, (double*)c->u, c->n, qm, dt, nsteps,
       c->status, c->outmask);
   c->launches++;

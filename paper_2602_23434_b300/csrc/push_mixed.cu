@@ -507,13 +507,6 @@ __global__ void __launch_bounds__(512)
   }
 }
 
-int grid_for(int64_t n, int threads) {
-  int64_t b = (n + threads - 1) / threads;
-  if (b < 1) b = 1;
-  if (b > 148 * 64) b = 148 * 64;
-  return (int)b;
-}
-
 struct MixedArgs {
   float h, hl, dtdx[3], inv_dt;  // h + hl: the half step (q/m) dt/2 as two floats
 };
@@ -558,7 +551,8 @@ cudaError_t dispatch_mixed(part_ctx* c, double qm, double dt, int nsteps) {
   if (c->sorted && nsteps == 1)
     return c->deposit_on ? brick_mixed<SHAPE, DIM, true>(c, a)
                          : brick_mixed<SHAPE, DIM, false>(c, a);
-  k_boris_particles_mixed<SHAPE, DIM><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
+  const int t = threads_for_spread(c->n);
+  k_boris_particles_mixed<SHAPE, DIM><<<grid_for(c->n, t), t, 0, c->stream>>>(
       (const float*)c->fpad, c->geo, (int32_t*)c->x, (float*)c->off, (float*)c->u, c->n, a.h,
       a.hl, a.dtdx[0], a.dtdx[1], a.dtdx[2], nsteps, c->status, c->outmask);
   c->launches++;

@@ -592,13 +592,6 @@ __global__ void k_fill_holes(T* __restrict__ a, const uint8_t* __restrict__ del,
   }
 }
 
-int grid_for(int64_t n, int threads) {
-  int64_t b = (n + threads - 1) / threads;
-  if (b < 1) b = 1;
-  if (b > 148 * 64) b = 148 * 64;
-  return (int)b;
-}
-
 template <typename T>
 cudaError_t permute_plane(part_ctx* c, T* arr, const uint32_t* perm) {
   const int64_t n = c->n;
