@@ -338,7 +338,9 @@ __device__ __forceinline__ int inc_lookup(const uint32_t* nid, uint32_t ob, uint
 }
 
 // Keys from the current positions (same arithmetic as the full sort) and the
-// particle count of every (old brick, slot).
+// particle count of every (old brick, slot).  Each thread has kIncItems
+// elements in flight: their loads are issued before any of them is used.
+constexpr int kIncItems = 4;
 template <bool CELL>
 __global__ void __launch_bounds__(kIncT)
     k_inc_count(const void* __restrict__ xv, int64_t n, const uint32_t* __restrict__ cs_old, Geo g,
@@ -349,35 +351,53 @@ __global__ void __launch_bounds__(kIncT)
   inc_table(g, ob, nid);
   __syncthreads();
   const uint32_t s0 = cs_old[ob * g.V], s1 = cs_old[(ob + 1) * g.V];
-  for (uint32_t c0 = s0; c0 < s1; c0 += kIncT) {  // uniform trip count per warp
-    const uint32_t i = c0 + threadIdx.x;
-    int slot = 27;
-    if (i < s1) {
-      uint32_t key;
+  // uniform trip count per warp
+  for (uint32_t c0 = s0; c0 < s1; c0 += kIncT * kIncItems) {
+    int32_t cv[kIncItems];
+    double xr[kIncItems][3];
+#pragma unroll
+    for (int r = 0; r < kIncItems; ++r) {
+      const uint32_t i = c0 + r * kIncT + threadIdx.x;
       if (CELL) {
-        int32_t c = ((const int32_t*)xv)[i];
-        if (c < 0 || c >= g.G) {
-          atomicOr(status, ST_DOMAIN);
-          c = c < 0 ? 0 : (int32_t)(g.G - 1);
-        }
-        int jc[3];
-        cell_coords(g, c, jc);
-        key = brick_key(g, jc[0], jc[1], jc[2]);
+        cv[r] = i < s1 ? ((const int32_t*)xv)[i] : 0;
       } else {
-        const double* x = (const double*)xv;
-        int j[3] = {0, 0, 0};
-        for (int a = 0; a < g.dim; ++a) j[a] = cell_of(g, a, x[a * n + i], status);
-        key = brick_key(g, j[0], j[1], j[2]);
-      }
-      keys[i] = key;
-      slot = inc_lookup(nid, (uint32_t)ob, (key >> g.vshift));
-      if (slot < 0) {
-        atomicOr(status, ST_DOMAIN);
-        slot = 27;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          xr[r][a] = i < s1 && a < g.dim ? ((const double*)xv)[a * n + i] : 0.0;
       }
     }
-    const uint32_t peers = __match_any_sync(0xffffffffu, (uint32_t)slot);
-    if (slot < 27 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[slot], __popc(peers));
+#pragma unroll
+    for (int r = 0; r < kIncItems; ++r) {
+      const uint32_t i = c0 + r * kIncT + threadIdx.x;
+      int slot = 27;
+      if (i < s1) {
+        uint32_t key;
+        if (CELL) {
+          int32_t c = cv[r];
+          if (c < 0 || c >= g.G) {
+            atomicOr(status, ST_DOMAIN);
+            c = c < 0 ? 0 : (int32_t)(g.G - 1);
+          }
+          int jc[3];
+          cell_coords(g, c, jc);
+          key = brick_key(g, jc[0], jc[1], jc[2]);
+        } else {
+          int j[3] = {0, 0, 0};
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            if (a < g.dim) j[a] = cell_of(g, a, xr[r][a], status);
+          key = brick_key(g, j[0], j[1], j[2]);
+        }
+        keys[i] = key;
+        slot = inc_lookup(nid, (uint32_t)ob, (key >> g.vshift));
+        if (slot < 0) {
+          atomicOr(status, ST_DOMAIN);
+          slot = 27;
+        }
+      }
+      const uint32_t peers = __match_any_sync(0xffffffffu, (uint32_t)slot);
+      if (slot < 27 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[slot], __popc(peers));
+    }
   }
   __syncthreads();
   if (threadIdx.x < 27) cnt[ob * 27 + threadIdx.x] = h[threadIdx.x];
@@ -425,6 +445,11 @@ __global__ void __launch_bounds__(256)
 
 // Position of every particle of old brick ob among its new brick's members:
 // bbase[db] + start of (ob, slot) + rank within (ob, slot) in index order.
+// The brick's particles go in tiles of kIncT * kIncItems; warp w takes the
+// tile's w-th run of 32 * kIncItems consecutive particles, so index order is
+// (tile, warp, item, lane).  Ranks: earlier lanes of the same item by
+// match_any, earlier items of the warp by a per-warp running count, earlier
+// warps and tiles by a prefix over the warps' counts.
 __global__ void __launch_bounds__(kIncT)
     k_inc_place(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ cs_old, Geo g,
                 const uint32_t* __restrict__ start, const uint32_t* __restrict__ bbase,
@@ -437,17 +462,29 @@ __global__ void __launch_bounds__(kIncT)
   if (tid < 28) run[tid] = 0;
   const uint32_t s0 = cs_old[ob * g.V], s1 = cs_old[(ob + 1) * g.V];
   const uint32_t lt = (1u << lane) - 1u;
-  for (uint32_t c0 = s0; c0 < s1; c0 += kIncT) {
+  for (uint32_t c0 = s0; c0 < s1; c0 += kIncT * kIncItems) {
     for (int q = tid; q < W * 28; q += kIncT) (&wc[0][0])[q] = 0;
     __syncthreads();
-    const uint32_t i = c0 + tid;
-    const bool valid = i < s1;
-    const uint32_t key = valid ? keys[i] : 0u;
-    int slot = valid ? inc_lookup(nid, (uint32_t)ob, (key >> g.vshift)) : 27;
-    if (slot < 0) slot = 27;  // moved too far: reported by the count pass
-    const uint32_t peers = __match_any_sync(0xffffffffu, (uint32_t)slot);
-    const uint32_t rank = __popc(peers & lt);
-    if (lane == __ffs(peers) - 1) wc[warp][slot] = __popc(peers);
+    const uint32_t seg = c0 + (uint32_t)warp * 32 * kIncItems;
+    uint32_t key[kIncItems], rank[kIncItems];
+    int slot[kIncItems];
+#pragma unroll
+    for (int r = 0; r < kIncItems; ++r) {
+      const uint32_t i = seg + r * 32 + lane;
+      key[r] = i < s1 ? keys[i] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kIncItems; ++r) {
+      const uint32_t i = seg + r * 32 + lane;
+      int sl = i < s1 ? inc_lookup(nid, (uint32_t)ob, (key[r] >> g.vshift)) : 27;
+      if (sl < 0) sl = 27;  // moved too far: reported by the count pass
+      slot[r] = sl;
+      const uint32_t peers = __match_any_sync(0xffffffffu, (uint32_t)sl);
+      rank[r] = wc[warp][sl] + __popc(peers & lt);  // this warp's earlier items
+      __syncwarp();
+      if (lane == __ffs(peers) - 1) wc[warp][sl] += __popc(peers);
+      __syncwarp();
+    }
     __syncthreads();
     if (tid < 28) {  // exclusive prefix over the warps, on top of the running count
       uint32_t acc = run[tid];
@@ -459,12 +496,17 @@ __global__ void __launch_bounds__(kIncT)
       run[tid] = acc;
     }
     __syncthreads();
-    if (slot < 27) {
-      const uint32_t db = (key >> g.vshift);
-      const uint64_t pos = (uint64_t)bbase[db] + start[ob * 27 + slot] + wc[warp][slot] + rank;
-      if (pos < (uint64_t)n) {
-        memb[pos] = i;
-        mlc[pos] = (key & (uint32_t)(g.V - 1));
+#pragma unroll
+    for (int r = 0; r < kIncItems; ++r) {
+      if (slot[r] < 27) {
+        const uint32_t i = seg + r * 32 + lane;
+        const uint32_t db = (key[r] >> g.vshift);
+        const uint64_t pos =
+            (uint64_t)bbase[db] + start[ob * 27 + slot[r]] + wc[warp][slot[r]] + rank[r];
+        if (pos < (uint64_t)n) {
+          memb[pos] = i;
+          mlc[pos] = (key[r] & (uint32_t)(g.V - 1));
+        }
       }
     }
     __syncthreads();
