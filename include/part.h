@@ -110,7 +110,8 @@ part_status part_destroy(part_ctx* ctx);
  * context) or f32 (PART_MIXED context); field_prec must match.
  * PART_BORIS: ncomp = 6 (E then B).  PART_LP_RK2: ncomp = 7 (fluid velocity
  * v[3], density rho, B[3]) -- the fluid quantities LPs sample (Sec. 2).
- * The copy is stream-ordered; the source may be freed once it completes.  */
+ * The copy is stream-ordered; the source may be freed once it completes.
+ * fields must be aligned to its element size (PART_EINVAL otherwise).     */
 part_status part_set_fields(part_ctx* ctx, const void* fields, int ncomp, part_prec field_prec);
 
 /* Bind caller-owned particle arrays (device, component-major, row stride n):
@@ -124,7 +125,8 @@ part_status part_set_fields(part_ctx* ctx, const void* fields, int ncomp, part_p
  *                       (bin-major), n_old = double[n] (density sampled at
  *                       the previous step); u, w = NULL
  * id (uint64[n]) is optional in every mode; when given it is permuted with
- * the particles so the caller can undo a sort.  0 <= n <= capacity.       */
+ * the particles so the caller can undo a sort.  0 <= n <= capacity.  Every
+ * array must be aligned to its element size (PART_EINVAL otherwise).     */
 part_status part_bind_particles(part_ctx* ctx, int64_t n, void* x_or_cell, void* off,
                                 void* u, void* w, uint64_t* id, double* chi, double* eng,
                                 double* n_old);
@@ -219,7 +221,7 @@ part_status part_set_lp_order(part_ctx* ctx, int order);
  * grid_out (device, double[3][G], overwritten):
  *   F_g = sum_p W(x_g - x_p^n) F_p.
  * Deterministic: no floating-point atomics; the same inputs give the same
- * bits on every run.                                                       */
+ * bits on every run.  grid_out must be 8-byte aligned (PART_EINVAL).      */
 part_status part_deposit(part_ctx* ctx, double* grid_out);
 
 /* Spectral update of every LP (Eq. cr_chi with Eq. rad_losses), using the
