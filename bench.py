@@ -709,6 +709,8 @@ def only(args):
     elif args.only == "lp":
         res = run_lp(torch, P, args.steps, args.warmup, n=args.grid,
                      nlp=max(1 << 16, 2 * args.grid ** 3))
+    elif args.only == "boris2d":
+        res = run_2d(torch, P)
     else:
         res = run_serving(torch, requests=args.serve_requests)
     print(json.dumps({"only": args.only, "grid": args.grid, **res}), flush=True)
@@ -728,7 +730,7 @@ def main():
     ap.add_argument("--grid", type=int, default=128,
                     help="cells per axis of the headline workload (128 = the stated one; "
                          "smaller only for profiling captures)")
-    ap.add_argument("--only", choices=["mixed", "lp", "serving", "compact", "shock"],
+    ap.add_argument("--only", choices=["mixed", "lp", "serving", "compact", "shock", "boris2d"],
                     default=None,
                     help="run one secondary workload alone at --grid cells per axis and print "
                          "its result (for profiling captures); no headline line")
