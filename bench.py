@@ -625,7 +625,7 @@ def headline_config(grid: int, particles: int, dt: float, world: int) -> dict:
             "parallelism": f"replicas x{world}"}
 
 
-def cpu_baseline(budget_s: float = 12.0, n=128, seed=1236):
+def cpu_baseline(budget_s: float = 15.0, n=128, seed=1236):
     """The oracle as it stands (OpenMP over particles in the push; sort and
     deposit sequential), one step = keys + stable sort + permute + Boris step
     + deposit, on a sample of the headline workload's particles."""
@@ -659,7 +659,7 @@ def cpu_baseline(budget_s: float = 12.0, n=128, seed=1236):
     t1 = time.perf_counter() - t0
     # scale the sample so that ~budget seconds of steps are timed
     steps = 3
-    Ns = int(min(1 << 22, max(1 << 16, Ns * budget_s / steps / max(t1, 1e-3))))
+    Ns = int(min(1 << 23, max(1 << 16, Ns * budget_s / steps / max(t1, 1e-3))))
     x, u, w, _ = O.init_particles(g, Ns, seed, 0.1)
     t0 = time.perf_counter()
     for _ in range(steps):
