@@ -30,7 +30,10 @@
  *     aligned) and the particle/field/output arrays.  The caller keeps every
  *     buffer alive until the work that uses it has completed (part_sync or a
  *     stream synchronisation).
- *   - All pointers to particle, field and output data are DEVICE pointers.
+ *   - Pointers to particle, field and output data are device pointers of the
+ *     context's device (or managed memory, or pinned host memory mapped into
+ *     the unified address space, which the kernels then reach over the host
+ *     link).  Pageable host memory is refused with PART_EINVAL.
  *   - Units: c = 1, particle mass m = 1, u = gamma v.
  *   - Grid: cell-centred fields, layout [comp][z][y][x] (x fastest), cell
  *     (jx,jy,jz) centred at xmin + (j + 1/2) dx.  For dim == 2 the grid has
@@ -111,7 +114,11 @@ part_status part_destroy(part_ctx* ctx);
  * PART_BORIS: ncomp = 6 (E then B).  PART_LP_RK2: ncomp = 7 (fluid velocity
  * v[3], density rho, B[3]) -- the fluid quantities LPs sample (Sec. 2).
  * The copy is stream-ordered; the source may be freed once it completes.
- * fields must be aligned to its element size (PART_EINVAL otherwise).     */
+ * fields must be aligned to its element size, and be device memory of the
+ * context's device, managed memory, or pinned host memory (read once by the
+ * padding kernel over the host link); anything else, such as pageable host
+ * memory, is refused with PART_EINVAL before any launch.  The same rule
+ * holds for every array argument of the library.                          */
 part_status part_set_fields(part_ctx* ctx, const void* fields, int ncomp, part_prec field_prec);
 
 /* Bind caller-owned particle arrays (device, component-major, row stride n):
@@ -221,7 +228,8 @@ part_status part_set_lp_order(part_ctx* ctx, int order);
  * grid_out (device, double[3][G], overwritten):
  *   F_g = sum_p W(x_g - x_p^n) F_p.
  * Deterministic: no floating-point atomics; the same inputs give the same
- * bits on every run.  grid_out must be 8-byte aligned (PART_EINVAL).      */
+ * bits on every run.  grid_out must be 8-byte aligned (PART_EINVAL); it may
+ * be pinned host memory, written directly over the host link.             */
 part_status part_deposit(part_ctx* ctx, double* grid_out);
 
 /* Spectral update of every LP (Eq. cr_chi with Eq. rad_losses), using the

@@ -186,7 +186,8 @@ class Part:
 
     # ------------------------------------------------------------------ calls
     def set_fields(self, fields):
-        assert fields.is_cuda and fields.is_contiguous()
+        """Device tensor, or pinned host tensor (read once over the host link)."""
+        assert (fields.is_cuda or fields.is_pinned()) and fields.is_contiguous()
         prec = FP64 if fields.dtype == self.torch.float64 else MIXED
         self._check(self.L.part_set_fields(self.ctx, _ptr(fields), fields.shape[0], prec))
         self._fields = fields
@@ -259,7 +260,9 @@ class Part:
         self._check(self.L.part_gather_push(self.ctx, qm, dt, nsteps))
 
     def deposit(self, out):
-        assert out.is_cuda and out.dtype == self.torch.float64 and out.is_contiguous()
+        """Device tensor, or pinned host tensor (written over the host link)."""
+        assert (out.is_cuda or out.is_pinned()) and out.dtype == self.torch.float64 \
+            and out.is_contiguous()
         self._check(self.L.part_deposit(self.ctx, _ptr(out)))
 
     def spec_update(self, dt: float, c0: float, u_rad: float = 0.0):

@@ -24,6 +24,24 @@ part_status fail(part_ctx* c, part_status s, const std::string& msg) {
   return s;
 }
 
+// Memory a kernel on `device` may touch: device memory of that device,
+// managed memory, or pinned host memory mapped into the unified address space
+// at the same address (read or written over the host link).  Pageable host
+// memory and other devices' memory are refused: a kernel would fault on them.
+// NULL passes (optional arrays).
+bool device_accessible(int device, const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the non-sticky error
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type == cudaMemoryTypeDevice) return a.device == device;
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer == p;
+  return false;
+}
+
 namespace {
 
 part_status cuda_fail(part_ctx* c, cudaError_t e, const char* where) {
@@ -42,6 +60,13 @@ bool misaligned(const void* p, size_t elem) {
 size_t pos_elem(const part_ctx* c) { return c->prec == PART_MIXED ? 4 : 8; }
 size_t real_elem(const part_ctx* c) { return c->prec == PART_MIXED ? 4 : 8; }
 
+part_status check_access(part_ctx* c, const void* p, const char* what) {
+  if (device_accessible(c->device, p)) return PART_OK;
+  return fail(c, PART_EINVAL,
+              std::string(what) + " is not memory the kernels can reach (device memory of the "
+                                  "context's device, managed memory or pinned host memory)");
+}
+
 part_status check_planes(part_ctx* c, const void* x, const void* off, const void* u,
                          const void* w, const void* id, const void* chi, const void* eng,
                          const void* n_old) {
@@ -49,6 +74,9 @@ part_status check_planes(part_ctx* c, const void* x, const void* off, const void
       misaligned(w, real_elem(c)) || misaligned(id, 8) || misaligned(chi, 8) ||
       misaligned(eng, 8) || misaligned(n_old, 8))
     return fail(c, PART_EINVAL, "a particle array is not aligned to its element size");
+  const void* planes[8] = {x, off, u, w, id, chi, eng, n_old};
+  for (const void* q : planes)
+    if (check_access(c, q, "a particle array") != PART_OK) return PART_EINVAL;
   return PART_OK;
 }
 
@@ -284,6 +312,10 @@ part_status part_init(part_ctx** out, const part_grid* grid, part_prec prec, par
   c->capacity = capacity;
   c->nbins = mode == PART_LP_RK2 ? nbins : 0;
   c->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return fail(nullptr, PART_ECUDA, "cudaGetDevice failed");
+  }
   c->ncomp = ncomp_of(mode);
   c->fcomp = fcomp_of(prec, mode);
   c->esize = esize_of(prec);
@@ -353,6 +385,7 @@ part_status part_set_fields(part_ctx* c, const void* fields, int ncomp, part_pre
   if (field_prec != c->prec) return fail(c, PART_EINVAL, "field_prec must match the context");
   if (misaligned(fields, c->prec == PART_MIXED ? 4 : 8))
     return fail(c, PART_EINVAL, "fields are not aligned to their element size");
+  if (check_access(c, fields, "fields") != PART_OK) return PART_EINVAL;
   cudaError_t e = launch_pad_fields(c, fields);
   if (e == cudaSuccess && c->shk) e = launch_shock_cells(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_set_fields");
@@ -427,6 +460,7 @@ part_status part_compact(part_ctx* c, const uint8_t* deleted, int64_t* n_new) {
   if (!c->bound) return fail(c, PART_EINVAL, "no particles bound");
   if (!n_new) return fail(c, PART_EINVAL, "n_new is NULL");
   if (c->n > 0 && !deleted) return fail(c, PART_EINVAL, "deleted mask is NULL");
+  if (check_access(c, deleted, "deleted") != PART_OK) return PART_EINVAL;
   cudaError_t e = flush_pending(c);
   int64_t nn = c->n;
   if (e == cudaSuccess) e = launch_compact(c, deleted, &nn);
@@ -477,6 +511,7 @@ part_status part_inject(part_ctx* c, int64_t k, const void* x_or_cell, const voi
 part_status part_set_outflow(part_ctx* c, uint8_t* mask) {
   if (check_ctx(c)) return PART_EINVAL;
   if (mask && !c->geo.any_open) return fail(c, PART_EINVAL, "the grid has no open axis");
+  if (check_access(c, mask, "mask") != PART_OK) return PART_EINVAL;
   c->outmask = mask;
   return PART_OK;
 }
@@ -505,6 +540,7 @@ part_status part_enable_shocks(part_ctx* c, double r_min, uint8_t* state) {
     return PART_OK;
   }
   if (!(std::isfinite(r_min) && r_min > 1.0)) return fail(c, PART_EINVAL, "r_min must be > 1");
+  if (check_access(c, state, "state") != PART_OK) return PART_EINVAL;
   if (!c->bound) return fail(c, PART_EINVAL, "bind the particles first");
   if (!c->fields_set) return fail(c, PART_EINVAL, "part_set_fields first");
   c->shk = state;
@@ -579,6 +615,7 @@ part_status part_deposit(part_ctx* c, double* grid_out) {
   if (check_ctx(c)) return PART_EINVAL;
   if (!grid_out) return fail(c, PART_EINVAL, "grid_out is NULL");
   if (misaligned(grid_out, 8)) return fail(c, PART_EINVAL, "grid_out is not 8-byte aligned");
+  if (check_access(c, grid_out, "grid_out") != PART_OK) return PART_EINVAL;
   if (c->mode != PART_BORIS || !c->deposit_ready)
     return fail(c, PART_EINVAL, "no deposit pending: enable it and push first");
   cudaError_t e = launch_deposit_combine(c, grid_out);

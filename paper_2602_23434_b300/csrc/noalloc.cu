@@ -87,6 +87,11 @@ extern "C" part_status part_sort_fp64_noalloc(const part_grid* grid, int64_t n, 
        reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(id)) % 8 != 0 ||
       reinterpret_cast<uintptr_t>(cell_start) % 4 != 0)
     return fail(nullptr, PART_EINVAL, "an array is not aligned to its element size");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, PART_ECUDA, "cudaGetDevice failed");
+  if (!device_accessible(dev, x) || !device_accessible(dev, u) || !device_accessible(dev, w) ||
+      !device_accessible(dev, id) || !device_accessible(dev, cell_start))
+    return fail(nullptr, PART_EINVAL, "an array is not memory the kernels can reach");
   void* base = nullptr;
   if ((s = scratch_for_current_device(&base)) != PART_OK) return s;
   char* b = static_cast<char*>(base);

@@ -63,6 +63,7 @@ struct part_ctx {
   int64_t capacity{};
   int nbins{};
   cudaStream_t stream{};
+  int device{};       // CUDA device current at part_init
   Geo geo{};
   int ncomp{};        // field components (6 Boris, 7 LP)
   int fcomp{};        // components per cell as stored: SoA ncomp, or 8 (cell-interleaved f32)
@@ -281,6 +282,7 @@ __device__ __forceinline__ void shape_weights(T d, T* w) {
 // Host helpers of api.cu: record an error message, validate a grid, derive
 // the kernel geometry for a field element size.
 part_status fail(part_ctx* c, part_status s, const std::string& msg);
+bool device_accessible(int device, const void* p);  // see api.cu
 part_status check_grid(const part_grid* g);
 void make_geo(const part_grid* gr, int esize, Geo* g);
 

@@ -161,6 +161,13 @@ part_status part_server_run(part_server* s, int nitems) {
       return sfail(s, PART_EINVAL, "work item " + std::to_string(i) + ": bad slice");
     if (w.count > 0 && (!w.cell || !w.off || !w.u))
       return sfail(s, PART_EINVAL, "work item " + std::to_string(i) + ": NULL state");
+    if (w.count > 0 &&
+        (((uintptr_t)w.cell | (uintptr_t)w.off | (uintptr_t)w.u) % 4 != 0 ||
+         !device_accessible(s->snaps[0]->device, w.cell) ||
+         !device_accessible(s->snaps[0]->device, w.off) ||
+         !device_accessible(s->snaps[0]->device, w.u)))
+      return sfail(s, PART_EINVAL,
+                   "work item " + std::to_string(i) + ": state not aligned or not reachable");
     if (!std::isfinite(w.q_over_m) || !std::isfinite(w.dt) || w.dt == 0.0)
       return sfail(s, PART_EINVAL, "work item " + std::to_string(i) + ": bad q_over_m / dt");
   }

@@ -282,6 +282,52 @@ def test_misaligned_arrays_refused_on_the_host():
     p.sync()
 
 
+def test_pinned_host_fields_and_output_and_pageable_refused():
+    """Fields read from pinned host memory and the deposit written into pinned
+    host memory give the same bits as device buffers.  Pageable host memory is
+    refused on the host before any launch: first through bind (which launches
+    nothing on the arrays in any case), then the fields and the output."""
+    og, pg, f, x, u, w, ids, N = _boris_case(3, 16, 4, P.TSC, 9)
+    qm, dt = 1.0, 0.5 * (2.0 / 16)
+    outs = []
+    for host in (False, True):
+        p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=N)
+        ft = torch.as_tensor(f).pin_memory() if host else _dev(f)
+        p.set_fields(ft)
+        xd, ud, wd = _dev(x), _dev(u), _dev(w)
+        p.bind(N, xd, u=ud, w=wd)
+        p.enable_deposit(True)
+        p.sort()
+        p.gather_push(qm, dt, 1)
+        out = torch.zeros((3, 16 ** 3), dtype=torch.float64)
+        out = out.pin_memory() if host else out.cuda()
+        p.deposit(out)
+        p.sync()
+        outs.append((_host(xd), _host(ud), out.cpu().numpy()))
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    import ctypes as C
+    L = P.lib()
+    pageable = torch.zeros(3 * N, dtype=torch.float64)        # not pinned
+    assert not pageable.is_pinned()
+    q = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=N)
+    l0 = q.launches()
+    pp = C.c_void_p(pageable.data_ptr())
+    ok = _dev(u)
+    assert L.part_bind_particles(q.ctx, N, pp, None, C.c_void_p(ok.data_ptr()), None, None,
+                                 None, None, None) == 1
+    assert "reach" in L.part_last_error(q.ctx).decode()
+    assert L.part_set_fields(q.ctx, pp, 6, P.FP64) == 1
+    assert q.launches() == l0
+    q.set_fields(_dev(f))
+    q.bind(N, _dev(x), u=ok)
+    q.enable_deposit(True)
+    q.sort()
+    q.gather_push(qm, dt, 1)
+    assert L.part_deposit(q.ctx, pp) == 1
+    q.sync()
+
+
 def test_error_paths():
     og, pg = _grids(3, 16)
     N = 1000
