@@ -45,8 +45,11 @@ def _compile(src: str, extra: list[str], verbose: bool) -> str:
 
 
 def build(verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    newest_src = max(os.path.getmtime(p) for p in srcs + _headers())
+    if not ptxas_info and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest_src:
+        return LIB  # up to date, whether or not the objects are at hand
+    os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_info else []
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra, verbose or ptxas_info), srcs))
