@@ -10,6 +10,7 @@ of ``part_oracle.h``: positions and velocities ``[3][n]``, fields
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -24,16 +25,22 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 CIC, TSC = 1, 2
 
 
+def compile_source(src: str, out: str) -> str:
+    """gcc -O2, no FP contraction, OpenMP: the one way the oracle is built."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call([
+        "gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+        "-Wl,-Bsymbolic", "-I", _HERE, "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile ``liboracle.so`` (gcc, -O2, no FP contraction, OpenMP)."""
+    """Compile ``liboracle.so`` if it is missing or older than its sources."""
     stale = (not os.path.exists(_LIB)) or any(
         os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR))
     if force or stale:
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call([
-            "gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-            "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+        compile_source(_SRC, _LIB)
     return _LIB
 
 
@@ -71,52 +78,70 @@ _I = C.POINTER(C.c_int)
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
-        G = C.POINTER(Grid)
-        sig = {
-            "or_shape": (C.c_double, [C.c_int, C.c_double]),
-            "or_cell_coord": (None, [G, _D, _I, _D]),
-            "or_wrap": (C.c_double, [G, C.c_int, C.c_double]),
-            "or_gather": (None, [G, C.c_int, _D, C.c_int, _D, _D]),
-            "or_boris_kick": (None, [_D, _D, _D, C.c_double, C.c_double]),
-            "or_boris_step": (None, [G, C.c_int, _D, C.c_int64, _D, _D, _D, C.c_double,
-                                     C.c_double, _D, _D]),
-            "or_deposit": (None, [G, C.c_int, C.c_int64, _D, _D, _D]),
-            "or_deposit_cell": (None, [G, C.c_int, C.c_int64, _D, _D, C.c_int64, _D]),
-            "or_cell_key": (C.c_uint32, [G, _I, _I]),
-            "or_key_count": (C.c_int64, [G, _I]),
-            "or_keys": (None, [G, _I, C.c_int64, _D, _U32]),
-            "or_stable_sort": (None, [C.c_int64, _U32, _U32]),
-            "or_cell_start": (None, [C.c_int64, C.c_int64, _U32, _U32]),
-            "or_lp_rk2_step": (None, [G, C.c_int, _D, _D, _D, C.c_int64, _D, C.c_double,
-                                      _D, _D, _D]),
-            "or_lp_rk3_step": (None, [G, C.c_int, _D, _D, _D, C.c_int64, _D, C.c_double,
-                                      _D, _D, _D]),
-            "or_spec_update": (None, [C.c_int, C.c_int64, _D, _D, _D, _D, _D, _D,
-                                      C.c_double, C.c_double, C.c_double]),
-            "or_init_spectrum": (None, [C.c_int, C.c_double, C.c_double, C.c_double,
-                                        C.c_double, _D, _D]),
-            "or_philox4x32_10": (None, [_U32, _U32, _U32]),
-            "or_init_particles": (None, [G, C.c_int64, C.c_uint64, C.c_double, _D, _D, _D,
-                                         _U64]),
-            "or_compact_map": (C.c_int64, [C.c_int64, C.POINTER(C.c_uint8),
-                                           C.POINTER(C.c_int64)]),
-            "or_set_threads": (None, [C.c_int]),
-            "or_outside": (C.c_int, [G, _D]),
-            "or_max_threads": (C.c_int, []),
-            "or_rh_compression": (C.c_double, [C.c_double, C.c_double]),
-            "or_dsa_index": (C.c_double, [C.c_double]),
-            "or_shock_cells": (None, [G, _D, _D, C.c_double, _D]),
-            "or_shock_convolve": (None, [C.c_int, _D, _D, C.c_double, C.c_double, _D]),
-            "or_lp_shock": (None, [G, _D, C.c_int, C.c_int64, _D, _D, _D,
-                                   C.POINTER(C.c_uint8)]),
-        }
-        for name, (res, args) in sig.items():
-            f = getattr(L, name)
-            f.restype = res
-            f.argtypes = args
-        _lib = L
+        _lib = load(build())
     return _lib
+
+
+@contextlib.contextmanager
+def using(path: str):
+    """Run the wrappers against another build of part_oracle.c (the tests plant
+    single mistakes in copies of it to show that the pins catch them)."""
+    global _lib
+    saved = _lib
+    _lib = load(path)
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def load(path: str):
+    """Open a build of part_oracle.c and declare its C signatures."""
+    L = C.CDLL(path)
+    G = C.POINTER(Grid)
+    sig = {
+        "or_shape": (C.c_double, [C.c_int, C.c_double]),
+        "or_cell_coord": (None, [G, _D, _I, _D]),
+        "or_wrap": (C.c_double, [G, C.c_int, C.c_double]),
+        "or_gather": (None, [G, C.c_int, _D, C.c_int, _D, _D]),
+        "or_boris_kick": (None, [_D, _D, _D, C.c_double, C.c_double]),
+        "or_boris_step": (None, [G, C.c_int, _D, C.c_int64, _D, _D, _D, C.c_double,
+                                 C.c_double, _D, _D]),
+        "or_deposit": (None, [G, C.c_int, C.c_int64, _D, _D, _D]),
+        "or_deposit_cell": (None, [G, C.c_int, C.c_int64, _D, _D, C.c_int64, _D]),
+        "or_cell_key": (C.c_uint32, [G, _I, _I]),
+        "or_key_count": (C.c_int64, [G, _I]),
+        "or_keys": (None, [G, _I, C.c_int64, _D, _U32]),
+        "or_stable_sort": (None, [C.c_int64, _U32, _U32]),
+        "or_cell_start": (None, [C.c_int64, C.c_int64, _U32, _U32]),
+        "or_lp_rk2_step": (None, [G, C.c_int, _D, _D, _D, C.c_int64, _D, C.c_double,
+                                  _D, _D, _D]),
+        "or_lp_rk3_step": (None, [G, C.c_int, _D, _D, _D, C.c_int64, _D, C.c_double,
+                                  _D, _D, _D]),
+        "or_spec_update": (None, [C.c_int, C.c_int64, _D, _D, _D, _D, _D, _D,
+                                  C.c_double, C.c_double, C.c_double]),
+        "or_init_spectrum": (None, [C.c_int, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, _D, _D]),
+        "or_philox4x32_10": (None, [_U32, _U32, _U32]),
+        "or_init_particles": (None, [G, C.c_int64, C.c_uint64, C.c_double, _D, _D, _D,
+                                     _U64]),
+        "or_compact_map": (C.c_int64, [C.c_int64, C.POINTER(C.c_uint8),
+                                       C.POINTER(C.c_int64)]),
+        "or_set_threads": (None, [C.c_int]),
+        "or_outside": (C.c_int, [G, _D]),
+        "or_max_threads": (C.c_int, []),
+        "or_rh_compression": (C.c_double, [C.c_double, C.c_double]),
+        "or_dsa_index": (C.c_double, [C.c_double]),
+        "or_shock_cells": (None, [G, _D, _D, C.c_double, _D]),
+        "or_shock_convolve": (None, [C.c_int, _D, _D, C.c_double, C.c_double, _D]),
+        "or_lp_shock": (None, [G, _D, C.c_int, C.c_int64, _D, _D, _D,
+                               C.POINTER(C.c_uint8)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
 
 
 def _d(a):

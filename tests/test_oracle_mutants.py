@@ -1,0 +1,122 @@
+"""The pins must catch plausible slips in the oracle.  Each case plants one
+mistake in a copy of part_oracle.c: a wrong sign, a dropped term or factor, a
+transposed index, a wrong constant, a reversed order.  The copy is built like
+the oracle, the wrappers are pointed at it, and the pin aimed at that part of
+the oracle must then fail.  The same pins pass on the real oracle
+(test_oracle_pins).  CPU only; mutant builds go to _build/oracle_mutants/."""
+import concurrent.futures as cf
+import os
+
+import pytest
+
+from oracle import oracle as O
+
+import test_oracle_pins as pins
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "part_oracle.c")
+OUT = os.path.join(ROOT, "_build", "oracle_mutants")
+
+# name: (text in part_oracle.c, its replacement, pins that must fail)
+MUTANTS = {
+    "boris_cross_product_sign": (
+        "upl[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);",
+        "upl[0] = um[0] + (um[2] * t[1] - um[1] * t[2]);",
+        [pins.test_boris_conserves_u_in_pure_B]),
+    "boris_rotation_factor_dropped": (
+        "s[a] = 2.0 * t[a] / (1.0 + t2);",
+        "s[a] = t[a] / (1.0 + t2);",
+        [pins.test_boris_conserves_u_in_pure_B]),
+    "boris_second_half_kick_dropped": (
+        "for (int a = 0; a < 3; ++a) u[a] = up[a] + h * E[a];",
+        "for (int a = 0; a < 3; ++a) u[a] = up[a];",
+        [pins.test_boris_exb_drift_second_order]),
+    "tsc_centre_weight": (
+        "if (a <= 0.5) return 0.75 - a * a;",
+        "if (a <= 0.5) return 0.75 - 0.5 * a * a;",
+        [lambda: pins.test_shape_partition_of_unity_and_first_moment(O.TSC)]),
+    "gather_z_weight_dropped": (
+        "double w = (wz * wy) * wx;\n        int64_t cell = cell_linear(g, nbr(g, 0, j[0] + kx), "
+        "nbr(g, 1, j[1] + ky),\n                                   nbr(g, 2, j[2] + kz));\n"
+        "        for (int c = 0; c < ncomp; ++c)",
+        "double w = wy * wx;\n        int64_t cell = cell_linear(g, nbr(g, 0, j[0] + kx), "
+        "nbr(g, 1, j[1] + ky),\n                                   nbr(g, 2, j[2] + kz));\n"
+        "        for (int c = 0; c < ncomp; ++c)",
+        [lambda: pins.test_gather_uniform_and_linear(O.TSC, 3)]),
+    "deposit_index_transposed": (
+        "int64_t cell = cell_linear(g, nbr(g, 0, j[0] + kx), nbr(g, 1, j[1] + ky),\n"
+        "                                     nbr(g, 2, j[2] + kz));\n"
+        "          for (int c = 0; c < 3; ++c) out",
+        "int64_t cell = cell_linear(g, nbr(g, 0, j[0] + ky), nbr(g, 1, j[1] + kx),\n"
+        "                                     nbr(g, 2, j[2] + kz));\n"
+        "          for (int c = 0; c < 3; ++c) out",
+        [lambda: pins.test_deposit_total_and_adjoint(O.TSC, 3)]),
+    "sort_ties_reversed": (
+        "return x->idx < y->idx ? -1 : (x->idx > y->idx);",
+        "return x->idx > y->idx ? -1 : (x->idx < y->idx);",
+        [pins.test_stable_sort_matches_python_sorted]),
+    "rk2_corrector_average_dropped": (
+        "x1[a] = or_wrap(g, a, x0[a] + dt * (0.5 * (v1[a] + v2[a])));",
+        "x1[a] = or_wrap(g, a, x0[a] + dt * v2[a]);",
+        [pins.test_lp_rk_orders_on_solid_rotation]),
+    "spectrum_loss_sign": (
+        "double s = A + C * e;",
+        "double s = A - C * e;",
+        [pins.test_spec_pure_synchrotron_closed_form]),
+    "spectrum_chi_power": (
+        "chi[(int64_t)i * n + p] = (chi[(int64_t)i * n + p] * (s * s)) / A;",
+        "chi[(int64_t)i * n + p] = (chi[(int64_t)i * n + p] * s) / A;",
+        [pins.test_spec_pure_adiabatic_closed_form]),
+    "shock_kernel_exponent_sign": (
+        "sum += c0 * pow(eng[i] / e0, 2.0 - q) * I;",
+        "sum += c0 * pow(eng[i] / e0, q - 2.0) * I;",
+        [pins.test_shock_convolution_of_a_power_law_is_exact]),
+    "dsa_index_denominator": (
+        "double or_dsa_index(double r) { return 3.0 * r / (r - 1.0); }",
+        "double or_dsa_index(double r) { return 3.0 * r / (r + 1.0); }",
+        [pins.test_rh_compression_and_slope_match_the_shock_test]),
+    "compaction_holes_reversed": (
+        "src[holes[k]] = i;",
+        "src[holes[ndel - 1 - k]] = i;",
+        [pins.test_compaction_invariants]),
+    "philox_multiplier": (
+        "uint64_t p0 = (uint64_t)0xD2511F53u * c0;",
+        "uint64_t p0 = (uint64_t)0xD2511F52u * c0;",
+        [pins.test_philox_known_answers]),
+    "open_axis_upper_clamp_dropped": (
+        "if (s > (double)g->n[a]) s = (double)g->n[a];",
+        ";",
+        [lambda: pins.test_open_axis_uniform_field_everywhere(O.TSC)]),
+}
+
+
+def _build(name):
+    old, new, _ = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
+    os.makedirs(OUT, exist_ok=True)
+    path = os.path.join(OUT, f"{name}.c")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    return O.compile_source(path, os.path.join(OUT, f"lib{name}.so"))
+
+
+@pytest.fixture(scope="module")
+def mutant_libs():
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        return dict(zip(MUTANTS, ex.map(_build, MUTANTS)))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pin_catches_planted_mistake(name, mutant_libs):
+    _, _, aimed = MUTANTS[name]
+    for pin in aimed:
+        pin()                                  # holds on the real oracle
+    caught = False
+    with O.using(mutant_libs[name]):
+        for pin in aimed:
+            try:
+                pin()
+            except AssertionError:
+                caught = True
+    assert caught, f"no pin caught the planted mistake {name}"
