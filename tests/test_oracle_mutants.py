@@ -7,6 +7,7 @@ the oracle must then fail.  The same pins pass on the real oracle
 import concurrent.futures as cf
 import os
 
+import numpy as np
 import pytest
 
 from oracle import oracle as O
@@ -17,7 +18,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "part_oracle.c")
 OUT = os.path.join(ROOT, "_build", "oracle_mutants")
 
-# name: (text in part_oracle.c, its replacement, pins that must fail)
+# name: (text in part_oracle.c, its replacement, pins that must fail[, which
+# occurrence of the text, when it occurs more than once])
 MUTANTS = {
     "boris_cross_product_sign": (
         "upl[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);",
@@ -83,6 +85,38 @@ MUTANTS = {
         "uint64_t p0 = (uint64_t)0xD2511F53u * c0;",
         "uint64_t p0 = (uint64_t)0xD2511F52u * c0;",
         [pins.test_philox_known_answers]),
+    "cell_key_bricks_transposed": (
+        "int64_t brick = ((int64_t)(j[2] / b[2]) * nb1 + j[1] / b[1]) * nb0 + j[0] / b[0];",
+        "int64_t brick = ((int64_t)(j[2] / b[2]) * nb1 + j[0] / b[0]) * nb0 + j[1] / b[1];",
+        [pins.test_cell_key_is_brick_bijection]),
+    "periodic_wrap_direction": (
+        "if (x < g->xmin[axis]) x = x + L;",
+        "if (x < g->xmin[axis]) x = x - L;",
+        [pins.test_cell_coord_edges_and_wrap]),
+    "force_weight_dropped": (
+        "F_out[a * n + p] = wp * ((up[a] - u0[a]) / dt);",
+        "F_out[a * n + p] = (up[a] - u0[a]) / dt;",
+        [pins.test_boris_step_drift_and_force, pins.test_deposit_momentum_balance]),
+    "rk3_final_stage_weight": (
+        "x1[a] = or_wrap(g, a, x0[a] + dt * ((k1[a] + k2[a] + 4.0 * k3[a]) / 6.0));",
+        "x1[a] = or_wrap(g, a, x0[a] + dt * ((k1[a] + k2[a] + 2.0 * k3[a]) / 6.0));",
+        [pins.test_lp_rk3_uniform_velocity_exact]),
+    "rk3_middle_stage_point": (
+        "xb[a] = or_wrap(g, a, x0[a] + dt * (0.25 * (k1[a] + k2[a])));",
+        "xb[a] = or_wrap(g, a, x0[a] + dt * (0.5 * (k1[a] + k2[a])));",
+        [pins.test_lp_rk_orders_on_solid_rotation]),
+    "lp_b2_start_sample_dropped": (                       # the RK2 step's copy (first)
+        "b2m[p] = 0.5 * (bb0 + bb1);",
+        "b2m[p] = bb1;",
+        [pins.test_lp_samples_in_linear_fields], 0),
+    "init_spectrum_norm_sign": (
+        "double norm = N0 * (1.0 - p) / (pow(emax, 1.0 - p) - pow(emin, 1.0 - p));",
+        "double norm = N0 * (p - 1.0) / (pow(emax, 1.0 - p) - pow(emin, 1.0 - p));",
+        [pins.test_init_spectrum_power_law_and_norm]),
+    "shock_convergence_sign": (
+        "if (dv < 0.0) {",
+        "if (dv > 0.0) {",
+        [pins.test_shock_cells_on_the_rh_snapshot]),
     "open_axis_upper_clamp_dropped": (
         "if (s > (double)g->n[a]) s = (double)g->n[a];",
         ";",
@@ -91,13 +125,19 @@ MUTANTS = {
 
 
 def _build(name):
-    old, new, _ = MUTANTS[name]
+    old, new = MUTANTS[name][:2]
+    nth = MUTANTS[name][3] if len(MUTANTS[name]) > 3 else None
     src = open(SRC).read()
-    assert src.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
+    if nth is None:
+        assert src.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
+        nth = 0
+    at = -1
+    for _ in range(nth + 1):
+        at = src.index(old, at + 1)
     os.makedirs(OUT, exist_ok=True)
     path = os.path.join(OUT, f"{name}.c")
     with open(path, "w") as f:
-        f.write(src.replace(old, new))
+        f.write(src[:at] + new + src[at + len(old):])
     return O.compile_source(path, os.path.join(OUT, f"lib{name}.so"))
 
 
@@ -109,11 +149,11 @@ def mutant_libs():
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pin_catches_planted_mistake(name, mutant_libs):
-    _, _, aimed = MUTANTS[name]
+    aimed = MUTANTS[name][2]
     for pin in aimed:
         pin()                                  # holds on the real oracle
     caught = False
-    with O.using(mutant_libs[name]):
+    with O.using(mutant_libs[name]), np.errstate(all="ignore"):
         for pin in aimed:
             try:
                 pin()

@@ -317,6 +317,36 @@ def test_lp_uniform_velocity_exact():
     assert np.allclose(n_new, 1.0) and np.allclose(b2m, 1.0)
 
 
+def test_lp_samples_in_linear_fields():
+    """The samples an LP step returns, against fields TSC reproduces exactly
+    (linear, away from the periodic seam): n_new = rho(x1), b2m = the mean of
+    |B|^2 at the start and the end of the step, gamma from v at x1."""
+    n = 32
+    g = O.make_grid(3, (n, n, n))
+    G = n ** 3
+    xc = -1.0 + (np.arange(n) + 0.5) * (2.0 / n)
+    X = np.broadcast_to(xc[None, None, :], (n, n, n)).reshape(-1)
+    Y = np.broadcast_to(xc[None, :, None], (n, n, n)).reshape(-1)
+    vel = np.zeros((3, G))
+    vel[0], vel[1] = 0.1, -0.05
+    rho = (2.0 + 0.3 * X)[None]
+    bf = np.zeros((3, G))
+    bf[0] = 0.5 + 0.2 * Y
+    bf[2] = 1.0 - 0.4 * X
+    rng = np.random.default_rng(11)
+    x0 = rng.uniform(-0.6, 0.6, (3, 40))
+    dt = 0.05
+    x1, n_new, b2m, gam = O.lp_rk2_step(g, O.TSC, vel, rho, bf, x0, dt)
+
+    def b2(x):
+        return (0.5 + 0.2 * x[1]) ** 2 + (1.0 - 0.4 * x[0]) ** 2
+
+    assert np.max(np.abs(x1 - (x0 + dt * np.array([[0.1], [-0.05], [0.0]])))) < 1e-14
+    assert np.max(np.abs(n_new - (2.0 + 0.3 * x1[0]))) < 1e-13
+    assert np.max(np.abs(b2m - 0.5 * (b2(x0) + b2(x1)))) < 1e-13
+    assert np.allclose(gam, 1.0 / math.sqrt(1.0 - 0.0125), rtol=1e-14)
+
+
 def _e1_exact(t):
     """Eq. advection_exact_sol (Sec. 4.1.1), wrapped to [-1, 1)."""
     s3 = math.sqrt(3)
