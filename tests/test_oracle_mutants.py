@@ -117,6 +117,42 @@ MUTANTS = {
         "if (dv < 0.0) {",
         "if (dv > 0.0) {",
         [pins.test_shock_cells_on_the_rh_snapshot]),
+    "cic_weight_slope": (
+        "return a < 1.0 ? 1.0 - a : 0.0;",
+        "return a < 1.0 ? 1.0 - 0.5 * a : 0.0;",
+        [lambda: pins.test_shape_partition_of_unity_and_first_moment(O.CIC)]),
+    "gather_index_transposed": (
+        "int64_t cell = cell_linear(g, nbr(g, 0, j[0] + kx), nbr(g, 1, j[1] + ky),\n"
+        "                                   nbr(g, 2, j[2] + kz));\n"
+        "        for (int c = 0; c < ncomp; ++c)",
+        "int64_t cell = cell_linear(g, nbr(g, 0, j[0] + ky), nbr(g, 1, j[1] + kx),\n"
+        "                                   nbr(g, 2, j[2] + kz));\n"
+        "        for (int c = 0; c < ncomp; ++c)",
+        [lambda: pins.test_gather_uniform_and_linear(O.TSC, 3)]),
+    "cell_start_off_by_one": (
+        "while (p < n && (int64_t)sk[p] < c) ++p;",
+        "while (p < n && (int64_t)sk[p] <= c) ++p;",
+        [pins.test_stable_sort_matches_python_sorted]),
+    "shock_applied_every_step": (
+        "if (!state[p]) {",
+        "if (1) {",
+        [pins.test_lp_shock_applies_once_per_crossing]),
+    "rh_compression_gamma": (
+        "return (gamma + 1.0) * m2 / (2.0 + (gamma - 1.0) * m2);",
+        "return (gamma - 1.0) * m2 / (2.0 + (gamma - 1.0) * m2);",
+        [pins.test_rh_compression_and_slope_match_the_shock_test]),
+    "maxwellian_radius": (
+        "double rad0 = sqrt(-2.0 * log(u01(r1[0])));",
+        "double rad0 = sqrt(-1.0 * log(u01(r1[0])));",
+        [pins.test_init_particles_statistics]),
+    "open_outside_lower_face": (
+        "if (x[a] < g->xmin[a] || x[a] >= g->xmin[a] + L) return 1;",
+        "if (x[a] >= g->xmin[a] + L) return 1;",
+        [pins.test_open_axis_no_wrap_and_outside]),
+    "upper_edge_tie_dropped": (
+        "if (jj >= g->n[a]) jj = g->n[a] - 1;",
+        ";",
+        [pins.test_cell_coord_edges_and_wrap]),
     "open_axis_upper_clamp_dropped": (
         "if (s > (double)g->n[a]) s = (double)g->n[a];",
         ";",
