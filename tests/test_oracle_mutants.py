@@ -153,6 +153,26 @@ MUTANTS = {
         "if (jj >= g->n[a]) jj = g->n[a] - 1;",
         ";",
         [pins.test_cell_coord_edges_and_wrap]),
+    "spectrum_proper_time": (
+        "double dtau = dt / gam[p];",
+        "double dtau = dt * gam[p];",
+        [pins.test_spec_pure_synchrotron_closed_form]),
+    "spectrum_expm1_factor_dropped": (
+        "double C = cr * dtau * (L == 0.0 ? 1.0 : expm1(L) / L);",
+        "double C = cr * dtau;",
+        [pins.test_spec_combined_integrating_factor]),
+    "boris_drift_without_gamma": (
+        "for (int a = 0; a < g->dim; ++a) xp[a] = or_wrap(g, a, xp[a] + dt * (up[a] / gam));",
+        "for (int a = 0; a < g->dim; ++a) xp[a] = or_wrap(g, a, xp[a] + dt * up[a]);",
+        [pins.test_boris_step_drift_and_force]),
+    "init_spectrum_spacing": (
+        "double e = nb > 1 ? exp(la + (lb - la) * ((double)i / (double)(nb - 1))) : emin;",
+        "double e = nb > 1 ? exp(la + (lb - la) * ((double)i / (double)nb)) : emin;",
+        [pins.test_init_spectrum_power_law_and_norm]),
+    "shock_ratio_inverted": (
+        "double ratio = hi / lo;",
+        "double ratio = lo / hi;",
+        [pins.test_shock_cells_on_the_rh_snapshot]),
     "open_axis_upper_clamp_dropped": (
         "if (s > (double)g->n[a]) s = (double)g->n[a];",
         ";",
