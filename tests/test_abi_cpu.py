@@ -60,3 +60,26 @@ def test_workspace_size_and_validation(L):
     assert L.part_init(C.byref(ctx), C.byref(g), 0, 2, 0, 10, 0, None, 0, None) == 1
     assert L.part_init(C.byref(ctx), C.byref(g), 0, 2, 0, 10, 0, C.c_void_p(0x1001), 1 << 30,
                        None) == 1
+
+
+def test_size_limits(L):
+    """The largest accepted sizes and the first refused ones: capacity below
+    2^31 (particle slots are 32-bit), at most 2^30 cells (keys are 32-bit),
+    spectra of 1..4096 bins; the workspace of the largest case is computed
+    without overflow."""
+    sz = C.c_size_t()
+    g = P.make_grid(3, 1024)                               # 2^30 cells
+    assert L.part_workspace_size(C.byref(g), P.FP64, P.BORIS, (1 << 31) - 1, 0,
+                                 C.byref(sz)) == 0
+    assert (1 << 31) * 24 < sz.value < 1 << 45             # state copies + sort buffers
+    assert L.part_workspace_size(C.byref(g), P.FP64, P.BORIS, 1 << 31, 0, C.byref(sz)) == 1
+    assert L.part_workspace_size(C.byref(g), P.FP64, P.BORIS, -1, 0, C.byref(sz)) == 1
+    big = P.make_grid(3, (1024, 1024, 1025))
+    assert L.part_workspace_size(C.byref(big), P.FP64, P.BORIS, 10, 0, C.byref(sz)) == 1
+    assert b"2^30" in L.part_last_error(None)
+    for nb, ok in ((1, 0), (4096, 0), (4097, 1)):
+        assert L.part_workspace_size(C.byref(P.make_grid(3, 16)), P.FP64, P.LP_RK2, 10, nb,
+                                     C.byref(sz)) == ok
+    b = (C.c_int * 3)()
+    nk = C.c_int64()
+    assert L.part_brick_dims(C.byref(g), b, C.byref(nk)) == 0 and nk.value == 1 << 30
