@@ -19,6 +19,8 @@
 //      accumulators: in a pass no two threads share a target, and the order
 //      is fixed.  Super-chunks of 512 particles keep shared memory at ~71 KB
 //      and the registers under 85, so three CTAs share an SM.
+// Each thread loads the state of its first particle of the next super-chunk
+// before the deposit of the current one, so phase A never starts cold.
 // Particle-order kernel: nsteps fused steps, state in registers, stencil read
 // from the padded global f32 copy (test particles, serving).
 #include "part_internal.cuh"
@@ -196,21 +198,21 @@ __global__ void __launch_bounds__(kT, 3)
   const float dtdx[3] = {dtdx0, dtdx1, dtdx2};
   const uint32_t p0 = scs[0], p1 = scs[g.V];
   int cfirst = 0;  // first brick cell with particles at or after the super-chunk start
-  for (uint32_t sb = p0; sb < p1; sb += kM) {
-    const uint32_t se = p1 - sb < (uint32_t)kM ? p1 : sb + kM;
-    // ---- A: push, one thread per particle; the next particle's state is
-    // loaded before the current one is computed
-    // particle q of the current buffer goes to slot p; the permutation is
-    // read two slots ahead and the state one slot ahead of the computation
-    uint32_t p = sb + tid;
-    int32_t nc = 0;
-    float no[3] = {0.f, 0.f, 0.f}, nu[3] = {0.f, 0.f, 0.f}, nw = 1.0f;
-    uint32_t qc = p, qn = p + kT;
+  // state of each thread's first particle of a super-chunk, loaded before the
+  // previous super-chunk's deposit so that phase A starts with it at hand
+  int32_t nc = 0;
+  float no[3] = {0.f, 0.f, 0.f}, nu[3] = {0.f, 0.f, 0.f}, nw = 1.0f;
+  uint32_t qc = 0, qn = 0;
+  auto prefetch = [&](uint32_t sbx) {
+    const uint32_t sex = p1 - sbx < (uint32_t)kM ? p1 : sbx + kM;
+    const uint32_t px = sbx + tid;
+    qc = px;
+    qn = px + kT;
     if (perm) {
-      if (p < se) qc = perm[p];
-      if (p + kT < se) qn = perm[p + kT];
+      if (px < sex) qc = perm[px];
+      if (px + kT < sex) qn = perm[px + kT];
     }
-    if (p < se) {
+    if (px < sex) {
       nc = cells[qc];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -219,6 +221,15 @@ __global__ void __launch_bounds__(kT, 3)
       }
       if (w) nw = w[qc];
     }
+  };
+  prefetch(p0);
+  for (uint32_t sb = p0; sb < p1; sb += kM) {
+    const uint32_t se = p1 - sb < (uint32_t)kM ? p1 : sb + kM;
+    // ---- A: push, one thread per particle; the next particle's state is
+    // loaded before the current one is computed
+    // particle q of the current buffer goes to slot p; the permutation is
+    // read two slots ahead and the state one slot ahead of the computation
+    uint32_t p = sb + tid;
     for (; p < se; p += kT) {
       const int i = (int)(p - sb);
       const int32_t ccur = nc;
@@ -315,6 +326,7 @@ __global__ void __launch_bounds__(kT, 3)
         }
       }
     }
+    if (sb + kM < p1) prefetch(sb + kM);
     if (!DEP) continue;
     __syncthreads();
     // ---- B: one thread per (source cell, component) of this super-chunk
