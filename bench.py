@@ -54,7 +54,7 @@ BYTES_PER_PSTEP_BORIS_DEP = 96 + 8 + 6 + 3
 TRAFFIC_PER_PARTICLE_BRICK_F64 = 265.788928e6 / 2097152   # ncu dram r+w, 64^3 capture
 # Same for the mixed brick kernel, from an ncu capture of the 128^3 case
 # (1299.8 MB for 16,777,216 particles).
-TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1299.821824e6 / 16777216   # ncu dram r+w, 128^3 capture
+TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1294.579712e6 / 16777216   # ncu dram r+w, 128^3 capture
 # LP step: x r/w 48, chi+eng r/w 4096 (128 bins), n_old r/w 16, samples w+r 48,
 # fields: 7 comps * 8 B per cell / 2 LPs per cell, 3 gathers at ~one cell = 84
 BYTES_PER_LPSTEP = 48 + 4096 + 16 + 48 + 84
