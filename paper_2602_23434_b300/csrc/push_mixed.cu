@@ -105,13 +105,14 @@ __device__ __forceinline__ void boris_f32(float* u, const float* E, const float*
   u[2] = (um2 + r2) + k2;
 }
 
-// Knuth's TwoSum: hi + lo carries the sum with the rounding error of hi.
-__device__ __forceinline__ void two_sum_add(float* hi, float* lo, float x) {
-  const float s = *hi + x;
-  const float bp = s - *hi;
-  const float err = (*hi - (s - bp)) + (x - bp);
-  *hi = s;
-  *lo += err;
+// Knuth's TwoSum into a (hi, lo) pair: hi + lo carries the sum with the
+// rounding error of hi.
+__device__ __forceinline__ float2 two_sum_add(float2 v, float x) {
+  const float s = v.x + x;
+  const float bp = s - v.x;
+  v.y += (v.x - (s - bp)) + (x - bp);
+  v.x = s;
+  return v;
 }
 
 // Stencil point accumulate: six field components of one cell (two 16-byte
@@ -164,8 +165,7 @@ __global__ void __launch_bounds__(kT, 3)
   int* sflag = reinterpret_cast<int*>(smem + L.bar + 8);
   float* rd = reinterpret_cast<float*>(smem + L.rec);  // [3][kM] old offsets
   float* rF = rd + 3 * kM;                              // [3][kM] force
-  float* ahi = reinterpret_cast<float*>(smem + L.acc);  // [3][ev]
-  float* alo = ahi + 3 * g.ev;                          // [3][ev]
+  float2* acc = reinterpret_cast<float2*>(smem + L.acc);  // [3][ev] (hi, lo)
 
   const int64_t brick = blockIdx.x;
   const int bx = (int)(brick % g.nb[0]);
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kT, 3)
   }
   for (int i = tid; i <= g.V; i += kT) scs[i] = cstart[brick * g.V + i];
   if (DEP)
-    for (int i = tid; i < 6 * g.ev; i += kT) ahi[i] = 0.0f;
+    for (int i = tid; i < 3 * g.ev; i += kT) acc[i] = make_float2(0.0f, 0.0f);
   if (!mbar_wait_bounded(bar, 0)) atomicOr(sflag, 1);
   __syncthreads();
   if (*sflag) {
@@ -380,8 +380,7 @@ __global__ void __launch_bounds__(kT, 3)
             if (any) {
               const int ex = lx + kx, ey = ly + ky, ez = lz + hz + (kz - 1);
               const int t = (ez * g.e[1] + ey) * g.e[0] + ex;
-              two_sum_add(&ahi[comp * g.ev + t], &alo[comp * g.ev + t],
-                          T[(kz * 3 + ky) * 3 + kx]);
+              acc[comp * g.ev + t] = two_sum_add(acc[comp * g.ev + t], T[(kz * 3 + ky) * 3 + kx]);
             }
             __syncthreads();
           }
@@ -393,7 +392,7 @@ __global__ void __launch_bounds__(kT, 3)
 #pragma unroll
       for (int c = 0; c < 3; ++c)
         dpart[(brick * 3 + c) * g.ev + t] =
-            (double)ahi[c * g.ev + t] + (double)alo[c * g.ev + t];
+            (double)acc[c * g.ev + t].x + (double)acc[c * g.ev + t].y;
   }
 }
 
