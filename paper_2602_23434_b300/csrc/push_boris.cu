@@ -81,6 +81,22 @@ __device__ __forceinline__ void boris_f64(double* u, const double* E, const doub
 // One particle of a chunk: weights, gather from the staged box, Boris, drift,
 // wrap, store; with DEP, its deposit record (9 z-y weight products and the 9
 // x-weighted force terms) is returned in wyz / fxc (zero if it has none).
+struct PState64 {
+  double x[3], u[3], w;
+  uint64_t id;
+};
+__device__ __forceinline__ void load_state64(PState64& s, uint32_t q, const double* xs,
+                                             const double* us, const double* ws,
+                                             const uint64_t* ids, int64_t n) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    s.x[a] = xs[a * n + q];
+    s.u[a] = us[a * n + q];
+  }
+  s.w = ws ? ws[q] : 1.0;
+  s.id = ids ? ids[q] : 0ull;
+}
+
 template <int SHAPE, int DIM, bool DEP, bool OPEN>
 __device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int bvol,
                                          const uint32_t* scs, const int* org, uint32_t p,
@@ -88,17 +104,21 @@ __device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int b
                                          const double* ws, const uint64_t* ids, double* x,
                                          double* u, double* wd, uint64_t* idd, int64_t n,
                                          double h, double dt, double inv_dt, int* status,
-                                         uint8_t* outmask, double* wyz, double* fxc) {
+                                         uint8_t* outmask, double* wyz, double* fxc,
+                                         const PState64* pre = nullptr) {
   double xp[3], up[3], uo[3];
+  PState64 st;
+  if (pre) st = *pre;
+  else load_state64(st, q, xs, us, ws, ids, n);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {  // particle q of the current buffer goes to slot p
-    xp[a] = xs[a * n + q];
-    up[a] = us[a * n + q];
+    xp[a] = st.x[a];
+    up[a] = st.u[a];
     uo[a] = up[a];
   }
-  const double wp = ws ? ws[q] : 1.0;
+  const double wp = st.w;
   if (ws && wd != ws) wd[p] = wp;             // carry the read-only planes over
-  if (ids && idd != ids) idd[p] = ids[q];
+  if (ids && idd != ids) idd[p] = st.id;
   int l[3] = {0, 0, 0};
   double d[3] = {0.0, 0.0, 0.0};
   bool ok = true;
@@ -292,7 +312,7 @@ __device__ __forceinline__ bool brick_prologue(const CUtensorMap* tmap, const Ge
 // Without deposit: 256 threads walk the brick's particles in chunks.  OPEN:
 // the grid has an open axis (no wrap there, sampling clamped, outflow mask).
 template <int SHAPE, int DIM, bool OPEN>
-__global__ void __launch_bounds__(kT, 1)
+__global__ void __launch_bounds__(kT, 2)
     k_boris_brick_f64(const __grid_constant__ CUtensorMap tmap, const Geo g,
                       const double* xs, const double* us, const double* ws,
                       const uint64_t* ids, double* x, double* u, double* wd, uint64_t* idd,
@@ -317,10 +337,25 @@ __global__ void __launch_bounds__(kT, 1)
     return;
   const double h = 0.5 * qm * dt;
   const uint32_t p0 = scs[0], p1 = scs[g.V];
-  for (uint32_t p = p0 + tid; p < p1; p += kT)
-    push_one<SHAPE, DIM, false, OPEN>(g, sbox, bvol, scs, org, p, perm ? perm[p] : p, xs, us, ws,
-                                ids, x, u, wd, idd, n, h, dt, inv_dt, status, outmask, nullptr,
-                                nullptr);
+  // the next particle's permutation entry and state are loaded while the
+  // current one is pushed
+  PState64 nxt;
+  uint32_t qnext = 0;
+  if (p0 + tid < p1) {
+    qnext = perm ? perm[p0 + tid] : p0 + tid;
+    load_state64(nxt, qnext, xs, us, ws, ids, n);
+  }
+  for (uint32_t p = p0 + tid; p < p1; p += kT) {
+    const PState64 cur = nxt;
+    const uint32_t qcur = qnext;
+    if (p + kT < p1) {
+      qnext = perm ? perm[p + kT] : p + kT;
+      load_state64(nxt, qnext, xs, us, ws, ids, n);
+    }
+    push_one<SHAPE, DIM, false, OPEN>(g, sbox, bvol, scs, org, p, qcur, xs, us, ws, ids, x, u, wd,
+                                      idd, n, h, dt, inv_dt, status, outmask, nullptr, nullptr,
+                                      &cur);
+  }
 }
 
 // With deposit: warp-specialised, 512 threads.  Warps 0-7 push chunk k of 256
@@ -363,17 +398,34 @@ __global__ void __launch_bounds__(2 * kT, 1)
   const int nchunks = (int)((p1 - p0 + kT - 1) / kT);
   if (tid < kT) {  // producer warps: push
     const double h = 0.5 * qm * dt;
+    // each thread's particle of the next chunk is loaded while this one is
+    // finished, so a chunk never starts with the permutation and state reads
+    PState64 nxt;
+    uint32_t qnext = 0;
+    {
+      const uint32_t pn = p0 + tid;
+      if (pn < p1) {
+        qnext = perm ? perm[pn] : pn;
+        load_state64(nxt, qnext, xs, us, ws, ids, n);
+      }
+    }
     for (int k = 0; k < nchunks; ++k) {
       const int b = k & 1;
       const uint32_t p = p0 + (uint32_t)k * kT + tid;
       double wyz[9], fxc[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) wyz[q] = fxc[q] = 0.0;
-      if (p < p1)
-        push_one<SHAPE, DIM, true, OPEN>(g, sbox, bvol, scs, org, p, perm ? perm[p] : p, xs, us,
-                                         ws,
-                                   ids, x, u, wd, idd, n, h, dt, inv_dt, status, outmask, wyz,
-                                   fxc);
+      if (p < p1) {
+        const PState64 cur = nxt;
+        const uint32_t qcur = qnext;
+        if (p + kT < p1) {
+          qnext = perm ? perm[p + kT] : p + kT;
+          load_state64(nxt, qnext, xs, us, ws, ids, n);
+        }
+        push_one<SHAPE, DIM, true, OPEN>(g, sbox, bvol, scs, org, p, qcur, xs, us, ws, ids, x,
+                                         u, wd, idd, n, h, dt, inv_dt, status, outmask, wyz,
+                                         fxc, &cur);
+      }
       if (k >= 2) named_bar_sync(kEmpty + b, NT);  // deposit of chunk k-2 has read it
       double* rw = rec + (size_t)b * 18 * kRS;
 #pragma unroll
