@@ -63,7 +63,8 @@ class WorkItem(C.Structure):
                 ("q_over_m", C.c_double), ("dt", C.c_double)]
 
 
-assert C.sizeof(WorkItem) == 72
+if C.sizeof(WorkItem) != 72:
+    raise ImportError("part_work_item layout mismatch with include/part.h (72 bytes)")
 
 _lib = None
 
@@ -187,7 +188,8 @@ class Part:
     # ------------------------------------------------------------------ calls
     def set_fields(self, fields):
         """Device tensor, or pinned host tensor (read once over the host link)."""
-        assert (fields.is_cuda or fields.is_pinned()) and fields.is_contiguous()
+        if not ((fields.is_cuda or fields.is_pinned()) and fields.is_contiguous()):
+            raise ValueError("fields must be a contiguous device or pinned host tensor")
         prec = FP64 if fields.dtype == self.torch.float64 else MIXED
         self._check(self.L.part_set_fields(self.ctx, _ptr(fields), fields.shape[0], prec))
         self._fields = fields
@@ -261,8 +263,9 @@ class Part:
 
     def deposit(self, out):
         """Device tensor, or pinned host tensor (written over the host link)."""
-        assert (out.is_cuda or out.is_pinned()) and out.dtype == self.torch.float64 \
-            and out.is_contiguous()
+        if not ((out.is_cuda or out.is_pinned()) and out.dtype == self.torch.float64
+                and out.is_contiguous()):
+            raise ValueError("out must be a contiguous float64 device or pinned host tensor")
         self._check(self.L.part_deposit(self.ctx, _ptr(out)))
 
     def spec_update(self, dt: float, c0: float, u_rad: float = 0.0):
