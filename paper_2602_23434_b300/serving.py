@@ -262,7 +262,7 @@ def autotune(torch, snapshots, candidates=None, n=1 << 21, steps=16, cache_path=
             cache = json.load(f)
         if key in cache:
             return cache[key]
-    except Exception:
+    except (OSError, ValueError):  # no cache yet, or an unreadable one
         cache = {}
     candidates = candidates or [(t, c, ch) for t in (128, 256, 512) for c in (2, 4, 8)
                                 for ch in (1024, 4096)]
@@ -289,6 +289,6 @@ def autotune(torch, snapshots, candidates=None, n=1 << 21, steps=16, cache_path=
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)
         with open(cache_path, "w") as f:
             json.dump(cache, f)
-    except Exception:
+    except OSError:  # a read-only location only costs the next run a re-tune
         pass
     return out
