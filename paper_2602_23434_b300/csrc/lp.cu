@@ -204,11 +204,11 @@ __global__ void __launch_bounds__(256)
     const double bb0 = b0[0] * b0[0] + b0[1] * b0[1] + b0[2] * b0[2];
     const double bb1 = b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2];
     const double vv = v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2];
-    const double gam = 1.0 / sqrt(1.0 - vv);
+    const double igam = sqrt(1.0 - vv);  // 1/gamma_g: d tau = dt / gamma_g = dt * igam
     samples[p] = r;
     samples[n + p] = 0.5 * (bb0 + bb1);
-    samples[2 * n + p] = gam;
-    if (!(fin && s1.finite && isfinite(gam) && isfinite(r) && r > 0.0))
+    samples[2 * n + p] = igam;
+    if (!(fin && s1.finite && igam > 0.0 && isfinite(r) && r > 0.0))
       atomicOr(status, ST_NONFINITE);
     if (SHOCK) shock_mark(p, s1.cell, shock_r, shk, list, rs);
   }
@@ -229,13 +229,16 @@ __global__ void __launch_bounds__(256, 2)
                   double u_rad, int* __restrict__ status) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
-    const double nn = samples[p], b2 = samples[n + p], gam = samples[2 * n + p];
-    const double dtau = dt / gam;
-    const double L = log(n_old[p] / nn) / 3.0;
-    const double rA = exp(-0.5 * L);       // 1/sqrt(A)
-    const double sA = exp(0.5 * L);        // sqrt(A)
+    const double nn = samples[p], b2 = samples[n + p], igam = samples[2 * n + p];
+    const double dtau = dt * igam;
+    const double L = log(n_old[p] / nn) * (1.0 / 3.0);
+    // one expm1 gives sqrt(A) = 1 + em and expm1(L) = em (em + 2) without
+    // cancellation; 1/sqrt(A) by one division
+    const double em = expm1(0.5 * L);
+    const double sA = 1.0 + em;            // sqrt(A)
+    const double rA = 1.0 / sA;            // 1/sqrt(A)
     const double cr = c0 * (0.5 * b2 + u_rad);
-    const double C = cr * dtau * (L == 0.0 ? 1.0 : expm1(L) / L);
+    const double C = cr * dtau * (L == 0.0 ? 1.0 : em * (em + 2.0) / L);
     const double Cs = C * rA;              // C / sqrt(A)
     if (!(isfinite(sA) && isfinite(Cs))) atomicOr(status, ST_NONFINITE);
     double* ep = eng + p;

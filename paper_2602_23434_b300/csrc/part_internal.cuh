@@ -83,7 +83,7 @@ struct part_ctx {
   uint32_t* bslot{};       // [nbricks][27] particles per (old brick, neighbour slot)
   void* tmp{};        // permute scratch, 8 bytes * capacity
   double* dpart{};    // deposit partials [nbricks][3][ev]
-  double* samples{};  // LP samples [3][capacity]: n_new, b2m, gamma_g
+  double* samples{};  // LP samples [3][capacity]: n_new, b2m, 1/gamma_g
   double* lpcache{};  // LP v, B at the current positions [6][capacity]
   bool lp_cache_ok{}; // lpcache matches the bound LPs, their order and the fields
   // Boris modes: alternate particle buffers.  part_sort only computes the
