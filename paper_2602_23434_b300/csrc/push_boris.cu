@@ -66,12 +66,13 @@ __device__ __forceinline__ void boris_f64(double* u, const double* E, const doub
   double t0 = hg * B[0], t1 = hg * B[1], t2 = hg * B[2];
   double sf = 2.0 / (1.0 + (t0 * t0 + t1 * t1 + t2 * t2));
   double s0 = sf * t0, s1 = sf * t1, s2 = sf * t2;
-  double p0 = um0 + (um1 * t2 - um2 * t1);
-  double p1 = um1 + (um2 * t0 - um0 * t2);
-  double p2 = um2 + (um0 * t1 - um1 * t0);
-  double q0 = um0 + (p1 * s2 - p2 * s1);
-  double q1 = um1 + (p2 * s0 - p0 * s2);
-  double q2 = um2 + (p0 * s1 - p1 * s0);
+  // u' = u- + u- x t and u+ = u- + u' x s, each component as two FMAs
+  double p0 = fma(um1, t2, fma(-um2, t1, um0));
+  double p1 = fma(um2, t0, fma(-um0, t2, um1));
+  double p2 = fma(um0, t1, fma(-um1, t0, um2));
+  double q0 = fma(p1, s2, fma(-p2, s1, um0));
+  double q1 = fma(p2, s0, fma(-p0, s2, um1));
+  double q2 = fma(p0, s1, fma(-p1, s0, um2));
   u[0] = q0 + h * E[0];
   u[1] = q1 + h * E[1];
   u[2] = q2 + h * E[2];
@@ -170,9 +171,10 @@ __device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int b
   }
   boris_f64(up, f, f + 3, h);
   const double gi = rsqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+  const double dgi = dt * gi;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    const double xa = xp[a] + dt * (up[a] * gi);
+    const double xa = fma(up[a], dgi, xp[a]);
     xp[a] = OPEN && g.open[a] ? xa : wrap_axis(xa, g.xmin[a], g.xmax[a], g.L[a]);
   }
   bool fin = finite_bits(up[0]) && finite_bits(up[1]) && finite_bits(up[2]) &&
@@ -508,9 +510,10 @@ __global__ void __launch_bounds__(256)
       }
       boris_f64(up, f, f + 3, h);
       const double gi = rsqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+      const double dgi = dt * gi;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
-        const double xa = xp[a] + dt * (up[a] * gi);
+        const double xa = fma(up[a], dgi, xp[a]);
         xp[a] = OPEN && g.open[a] ? xa : wrap_axis(xa, g.xmin[a], g.xmax[a], g.L[a]);
       }
       if (bad) break;
