@@ -57,14 +57,19 @@ __device__ __forceinline__ double wrap_axis(double v, double lo, double hi, doub
   return v;
 }
 
+// 1 + |v|^2 as three FMAs
+__device__ __forceinline__ double one_plus_norm2(double a, double b, double c) {
+  return fma(c, c, fma(b, b, fma(a, a, 1.0)));
+}
+
 // Relativistic Boris kick (c = 1): half E kick, rotation about B with
 // t = h B / gamma-, s = 2t/(1+t^2), half E kick; h = (q/m) dt / 2.
 __device__ __forceinline__ void boris_f64(double* u, const double* E, const double* B, double h) {
   double um0 = u[0] + h * E[0], um1 = u[1] + h * E[1], um2 = u[2] + h * E[2];
-  double gi = rsqrt(1.0 + (um0 * um0 + um1 * um1 + um2 * um2));
+  double gi = rsqrt(one_plus_norm2(um0, um1, um2));
   double hg = h * gi;
   double t0 = hg * B[0], t1 = hg * B[1], t2 = hg * B[2];
-  double sf = 2.0 / (1.0 + (t0 * t0 + t1 * t1 + t2 * t2));
+  double sf = 2.0 / one_plus_norm2(t0, t1, t2);
   double s0 = sf * t0, s1 = sf * t1, s2 = sf * t2;
   // u' = u- + u- x t and u+ = u- + u' x s, each component as two FMAs
   double p0 = fma(um1, t2, fma(-um2, t1, um0));
@@ -170,7 +175,7 @@ __device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int b
     }
   }
   boris_f64(up, f, f + 3, h);
-  const double gi = rsqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+  const double gi = rsqrt(one_plus_norm2(up[0], up[1], up[2]));
   const double dgi = dt * gi;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
@@ -509,7 +514,7 @@ __global__ void __launch_bounds__(256)
         }
       }
       boris_f64(up, f, f + 3, h);
-      const double gi = rsqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+      const double gi = rsqrt(one_plus_norm2(up[0], up[1], up[2]));
       const double dgi = dt * gi;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
