@@ -131,6 +131,7 @@ __device__ __forceinline__ void shock_mark(int64_t p, int64_t cell,
 // ORDER 2: Heun, x' = x + dt (k1 + k2)/2.  ORDER 3: three-stage SSP
 // Runge-Kutta (Shu & Osher) in stage-velocity form, k3 = v(x + dt (k1+k2)/4),
 // x' = x + dt (k1 + k2 + 4 k3)/6; the wrap only enters the sampled positions.
+// Each update is one FMA with dt/2, dt/4 or dt/6 (no division per LP).
 // CACHED: v and B at x (from the previous step's samples at its new
 // position, the same stencil at the same point) are read instead of gathered;
 // every step leaves v and B at x' for the next one (cache [6][n]).
@@ -161,25 +162,26 @@ __global__ void __launch_bounds__(256)
       fin = s0.finite;
     }
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) xs[a] = wrap_axis(g, a, x0[a] + dt * v1[a]);
+    for (int a = 0; a < DIM; ++a) xs[a] = wrap_axis(g, a, fma(dt, v1[a], x0[a]));
     Stencil<SHAPE, DIM> ss(g, xs);
     ss.template gather<3>(fp, g, 0, v2);
     fin = fin && ss.finite;
     if (ORDER == 2) {
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
-        x1[a] = wrap_axis(g, a, x0[a] + dt * (0.5 * (v1[a] + v2[a])));
+        x1[a] = wrap_axis(g, a, fma(0.5 * dt, v1[a] + v2[a], x0[a]));
     } else {
       double xb[3] = {x0[0], x0[1], x0[2]}, k3[3];
+      const double dt6 = dt * (1.0 / 6.0);
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
-        xb[a] = wrap_axis(g, a, x0[a] + dt * (0.25 * (v1[a] + v2[a])));
+        xb[a] = wrap_axis(g, a, fma(0.25 * dt, v1[a] + v2[a], x0[a]));
       Stencil<SHAPE, DIM> sb(g, xb);
       sb.template gather<3>(fp, g, 0, k3);
       fin = fin && sb.finite;
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
-        x1[a] = wrap_axis(g, a, x0[a] + dt * ((v1[a] + v2[a] + 4.0 * k3[a]) / 6.0));
+        x1[a] = wrap_axis(g, a, fma(dt6, fma(4.0, k3[a], v1[a] + v2[a]), x0[a]));
     }
     Stencil<SHAPE, DIM> s1(g, x1);
     {
@@ -201,9 +203,9 @@ __global__ void __launch_bounds__(256)
       cache[(3 + c) * n + p] = b1[c];
     }
     if (outmask) outmask[p] = outside_open(g, x1);
-    const double bb0 = b0[0] * b0[0] + b0[1] * b0[1] + b0[2] * b0[2];
-    const double bb1 = b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2];
-    const double vv = v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2];
+    const double bb0 = fma(b0[2], b0[2], fma(b0[1], b0[1], b0[0] * b0[0]));
+    const double bb1 = fma(b1[2], b1[2], fma(b1[1], b1[1], b1[0] * b1[0]));
+    const double vv = fma(v3[2], v3[2], fma(v3[1], v3[1], v3[0] * v3[0]));
     const double igam = sqrt(1.0 - vv);  // 1/gamma_g: d tau = dt / gamma_g = dt * igam
     samples[p] = r;
     samples[n + p] = 0.5 * (bb0 + bb1);
