@@ -136,70 +136,99 @@ __global__ void k_init_lp(const Geo g, int64_t n, int nb, uint64_t seed,
 
 // Ghost-filled padded copy: padded (px, py, pz) <- cell ((px-h) mod n, ...);
 // x columns beyond n + 2 (row-pitch padding) are zero.
-// Source cell of padded coordinate i (cell index, may be -1 or n): periodic
-// image, or the edge cell on an open axis (zero-gradient ghost layer).
+// Source cell of padded coordinate i (cell index, -h <= i < n + h with h <= 1):
+// periodic image, or the edge cell on an open axis (zero-gradient ghost layer).
 __device__ __forceinline__ int ghost_src(int i, int n, int open) {
   if (open) return i < 0 ? 0 : (i >= n ? n - 1 : i);
-  return (i + n) % n;
+  return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 
+// One warp per padded row (component, pz, py): the row's source row is fixed,
+// so the lanes read it coalesced (x ghosts aside) and write the padded row
+// contiguously; U loads per lane are in flight before the stores (the source
+// may be pinned host memory read over the link).
 template <typename T>
 __global__ void k_pad_fields(const T* __restrict__ src, T* __restrict__ dst, const Geo g,
                              int ncomp) {
-  const int64_t total = (int64_t)ncomp * g.pplane;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = q / g.pplane;
-    const int64_t r = q - c * g.pplane;
-    const int px = (int)(r % g.pn[0]);
-    const int py = (int)((r / g.pn[0]) % g.pn[1]);
-    const int pz = (int)(r / ((int64_t)g.pn[0] * g.pn[1]));
-    if (px >= g.n[0] + 2 * g.h[0]) {
-      dst[q] = T(0);
-      continue;
-    }
-    const int sx = ghost_src(px - g.h[0], g.n[0], g.open[0]);
+  constexpr int U = 4;
+  const int lane = threadIdx.x & 31;
+  const int64_t rows = (int64_t)ncomp * g.pn[2] * g.pn[1];
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int nx = g.n[0] + 2 * g.h[0];
+  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows;
+       r += wstride) {
+    const int py = (int)(r % g.pn[1]);
+    const int64_t t = r / g.pn[1];
+    const int pz = (int)(t % g.pn[2]);
+    const int c = (int)(t / g.pn[2]);
     const int sy = ghost_src(py - g.h[1], g.n[1], g.open[1]);
     const int sz = ghost_src(pz - g.h[2], g.n[2], g.open[2]);
-    dst[q] = src[c * g.G + ((int64_t)sz * g.n[1] + sy) * g.n[0] + sx];
+    const T* srow = src + (int64_t)c * g.G + ((int64_t)sz * g.n[1] + sy) * g.n[0];
+    T* drow = dst + r * g.pn[0];
+    for (int px0 = 0; px0 < g.pn[0]; px0 += 32 * U) {
+      T v[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int px = px0 + k * 32 + lane;
+        v[k] = T(0);
+        if (px < nx) v[k] = srow[ghost_src(px - g.h[0], g.n[0], g.open[0])];
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int px = px0 + k * 32 + lane;
+        if (px < g.pn[0]) drow[px] = v[k];
+      }
+    }
   }
 }
 
 // Mixed form: cell-interleaved copy, 8 floats per padded cell (6 components,
-// 2 zero pads), so one stencil point is two 16-byte loads.
+// 2 zero pads), so one stencil point is two 16-byte loads.  One warp per
+// padded row (pz, py); each lane gathers one cell's components (coalesced per
+// component across the warp) and writes its 32 bytes as two 16-byte stores.
 __global__ void k_pad_fields_aos8(const float* __restrict__ src, float* __restrict__ dst,
                                   const Geo g, int ncomp) {
-  const int64_t total = 8 * g.pplane;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(q & 7);
-    const int64_t r = q >> 3;
-    const int px = (int)(r % g.pn[0]);
-    const int py = (int)((r / g.pn[0]) % g.pn[1]);
-    const int pz = (int)(r / ((int64_t)g.pn[0] * g.pn[1]));
-    if (c >= ncomp || px >= g.n[0] + 2 * g.h[0]) {
-      dst[q] = 0.0f;
-      continue;
-    }
-    const int sx = ghost_src(px - g.h[0], g.n[0], g.open[0]);
+  const int lane = threadIdx.x & 31;
+  const int64_t rows = (int64_t)g.pn[2] * g.pn[1];
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int nx = g.n[0] + 2 * g.h[0];
+  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows;
+       r += wstride) {
+    const int py = (int)(r % g.pn[1]);
+    const int pz = (int)(r / g.pn[1]);
     const int sy = ghost_src(py - g.h[1], g.n[1], g.open[1]);
     const int sz = ghost_src(pz - g.h[2], g.n[2], g.open[2]);
-    dst[q] = src[(int64_t)c * g.G + ((int64_t)sz * g.n[1] + sy) * g.n[0] + sx];
+    const float* srow = src + ((int64_t)sz * g.n[1] + sy) * g.n[0];
+    for (int px = lane; px < g.pn[0]; px += 32) {
+      float v[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) v[c] = 0.0f;
+      if (px < nx) {
+        const int sx = ghost_src(px - g.h[0], g.n[0], g.open[0]);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c < ncomp) v[c] = srow[(int64_t)c * g.G + sx];
+      }
+      float4* d = reinterpret_cast<float4*>(dst + (r * g.pn[0] + px) * 8);
+      d[0] = make_float4(v[0], v[1], v[2], v[3]);
+      d[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
   }
 }
 
 }  // namespace
 
 cudaError_t launch_pad_fields(part_ctx* c, const void* src) {
-  const int64_t total = (int64_t)c->fcomp * c->geo.pplane;
+  // one warp per padded row, 8 warps per CTA
+  const int64_t rows = (int64_t)c->geo.pn[2] * c->geo.pn[1];
   if (c->fcomp == 8 && c->esize == 4)
-    k_pad_fields_aos8<<<grid_for(total, 256), 256, 0, c->stream>>>(
+    k_pad_fields_aos8<<<grid_for(rows * 32, 256), 256, 0, c->stream>>>(
         (const float*)src, (float*)c->fpad, c->geo, c->ncomp);
   else if (c->esize == 8)
-    k_pad_fields<double><<<grid_for(total, 256), 256, 0, c->stream>>>(
+    k_pad_fields<double><<<grid_for(rows * c->ncomp * 32, 256), 256, 0, c->stream>>>(
         (const double*)src, (double*)c->fpad, c->geo, c->ncomp);
   else
-    k_pad_fields<float><<<grid_for(total, 256), 256, 0, c->stream>>>(
+    k_pad_fields<float><<<grid_for(rows * c->ncomp * 32, 256), 256, 0, c->stream>>>(
         (const float*)src, (float*)c->fpad, c->geo, c->ncomp);
   c->launches++;
   return cudaGetLastError();
