@@ -113,6 +113,9 @@ void make_geo(const part_grid* gr, int esize, Geo* g) {
     g->L[a] = (double)gr->n[a] * gr->dx[a];
     g->xmax[a] = gr->xmin[a] + g->L[a];
     g->invn[a] = 1.0f / (float)gr->n[a];
+    g->xminf[a] = (float)g->xmin[a];
+    g->inv_dxf[a] = (float)g->inv_dx[a];
+    g->xmin_cells[a] = (float)(std::fabs(g->xmin[a]) * g->inv_dx[a]);
   }
   // FP64: component planes with the x pitch rounded to 16 bytes.  f32 (mixed
   // form): cells interleave 8 floats (32 bytes), so no x rounding is needed.

@@ -47,6 +47,7 @@ struct Geo {
   int64_t pplane;  // padded elements per field component
   double xmin[3], dx[3], inv_dx[3], L[3], xmax[3];
   float invn[3];   // 1/n per axis, for the float-reciprocal cell decode
+  float xminf[3], inv_dxf[3], xmin_cells[3];  // f32 images of xmin, inv_dx; |xmin| inv_dx
   int bshift[3];   // log2 b per axis (brick sides are powers of two)
   int vshift;      // log2 V
   int open[3];     // 1: open (outflow) axis, 0: periodic

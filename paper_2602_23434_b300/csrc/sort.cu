@@ -28,7 +28,38 @@ __device__ __forceinline__ uint32_t brick_key(const Geo& g, int jx, int jy, int 
          (uint32_t)((((lz << g.bshift[1]) | ly) << g.bshift[0]) | lx);
 }
 
+// Cell index floor((x - xmin) inv_dx), rounded as in FP64, clamped to
+// [0, n-1].  The FP64 rate bounds a pass that only computes keys, so the
+// floor is first taken from an f32 image of the same expression: x's f32
+// image by truncating its significand on the integer pipe (relative error
+// <= 2^-23), then an f32 subtract and multiply.  That value is within
+// 1.3 * 2^-22 * (|xmin| inv_dx + |s|) of the exact s, and the FP64 s is
+// within a few ulp of it, so whenever the f32 value is farther than
+// 4e-7 * (|xmin| inv_dx + |s| + 1) from an integer both floors agree.  The
+// rest (about 1e-4 of the positions per axis, and non-finite or huge
+// coordinates) take the FP64 expression.
 __device__ __forceinline__ int cell_of(const Geo& g, int a, double xa, int* status) {
+  {
+    const uint32_t hi = (uint32_t)__double2hiint(xa), lo = (uint32_t)__double2loint(xa);
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    // binary64 exponents that are normal in binary32; +-0 is exact as well
+    const bool zero = ((hi & 0x7fffffffu) | lo) == 0u;
+    if ((e >= 1023 - 126 && e <= 1023 + 127) || zero) {
+      const float xf = zero ? 0.0f
+                            : __uint_as_float((hi & 0x80000000u) | ((uint32_t)(e - 896) << 23) |
+                                              ((hi & 0xfffffu) << 3) | (lo >> 29));
+      const float sf = (xf - g.xminf[a]) * g.inv_dxf[a];
+      if (fabsf(sf) < 4194304.0f) {  // 2^22: floorf and the fraction are exact
+        const float fl = floorf(sf);
+        const float fr = sf - fl;
+        const float m = 4e-7f * (g.xmin_cells[a] + fabsf(sf) + 1.0f);
+        if (fr > m && fr < 1.0f - m) {
+          const int j = (int)fl;
+          return j < 0 ? 0 : (j > g.n[a] - 1 ? g.n[a] - 1 : j);
+        }
+      }
+    }
+  }
   double s = __dmul_rn(__dsub_rn(xa, g.xmin[a]), g.inv_dx[a]);
   if (!finite_bits(s)) {
     atomicOr(status, ST_NONFINITE);

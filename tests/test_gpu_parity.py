@@ -62,6 +62,65 @@ def test_sort_bit_exact(dim, n, ppc):
     assert np.array_equal(cs, O.cell_start(p.nkeys, keys[perm]).astype(np.int64))
 
 
+def _face_positions(rng, N, n, xmin, dx):
+    """Coordinates on the cell faces xmin + j dx (j = 0..n, in FP64) moved by
+    -3..3 ulp, at the upper domain edge minus one ulp, and inside cells."""
+    j = rng.integers(0, n + 1, N)
+    x = xmin + j * dx
+    k = rng.integers(-3, 4, N)
+    for _ in range(3):
+        up, dn = k > 0, k < 0
+        x = np.where(up, np.nextafter(x, np.inf), np.where(dn, np.nextafter(x, -np.inf), x))
+        k = k - up + dn
+    xmax = xmin + n * dx
+    x = np.where(x >= xmax, np.nextafter(xmax, -np.inf), x)
+    x = np.where(x < xmin, xmin, x)
+    inside = rng.random(N) < 0.3
+    return np.where(inside, xmin + rng.uniform(0.0, n, N) * dx, x)
+
+
+@pytest.mark.parametrize("n,xmin", [(16, (-1.0, -1.0, -1.0)), (20, (-1.0, -1.0, -1.0)),
+                                    (24, (3.7, -10.25, 0.5))])
+def test_sort_keys_at_cell_faces(n, xmin):
+    """Cell keys of positions on and a few ulp around every cell face (dx = 0.125
+    exact, 0.1 inexact, an offset domain): the full sort's keys and, after a
+    push that leaves the positions where they are, the incremental sort's,
+    both bit-exact against the oracle.  The key passes take the floor from an
+    f32 image and fall back to the FP64 expression near faces, so this is
+    where they could differ."""
+    dim, L = 3, 2.0
+    og = O.make_grid(dim, (n, n, n), xmin=xmin, dx=(L / n,) * 3)
+    pg = P.make_grid(dim, n, xmin=xmin, L=(L,) * 3)
+    rng = np.random.default_rng(n)
+    N = 20000
+    x = np.stack([_face_positions(rng, N, n, xmin[a], L / n) for a in range(3)])
+    u = np.zeros((3, N))
+    ids = np.arange(N, dtype=np.int64)
+    p = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=N)
+    p.set_fields(_dev(np.zeros((6, n ** 3))))
+    xd, ud, idd = _dev(x), _dev(u), torch.as_tensor(ids).cuda()
+    p.bind(N, xd, u=ud, ids=idd)
+    p.sort()
+    cs = _host(p.cell_start())
+    p.sync()
+    keys = O.keys(og, p.brick, x)
+    perm = O.stable_sort(keys)
+    assert np.array_equal(_host(idd), ids[perm])
+    assert np.array_equal(cs, O.cell_start(p.nkeys, keys[perm]).astype(np.int64))
+    # u = 0: the push leaves every position as it is; the next sort is incremental
+    p.gather_push(1.0, 0.5 * L / n, 1)
+    p.sync()
+    xb, ib = _host(xd).copy(), _host(idd).copy()
+    assert np.array_equal(xb, x[:, perm])
+    p.sort()
+    cs = _host(p.cell_start())
+    p.sync()
+    keys = O.keys(og, p.brick, xb)
+    perm = O.stable_sort(keys)
+    assert np.array_equal(_host(idd), ib[perm])
+    assert np.array_equal(cs, O.cell_start(p.nkeys, keys[perm]).astype(np.int64))
+
+
 @pytest.mark.parametrize("N", [0, 1, 31, 33, 4096, 4097])
 def test_sort_edge_counts(N):
     og, pg = _grids(3, 16)
