@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(256, 2)
     // cancellation; 1/sqrt(A) by one division
     const double em = expm1(0.5 * L);
     const double sA = 1.0 + em;            // sqrt(A)
-    const double rA = 1.0 / sA;            // 1/sqrt(A)
+    const double rA = __drcp_rn(sA);       // 1/sqrt(A), as 1.0 / sA rounds it
     const double cr = c0 * (0.5 * b2 + u_rad);
     const double C = cr * dtau * (L == 0.0 ? 1.0 : em * (em + 2.0) / L);
     const double Cs = C * rA;              // C / sqrt(A)
@@ -258,7 +258,9 @@ __global__ void __launch_bounds__(256, 2)
         tv[k] = sA + Cs * e[k];
         pre[k] = k == 0 ? tv[0] : pre[k - 1] * tv[k];
       }
-      double inv = rA / pre[7];              // r[k] = (1/sqrt(A)) / t_k
+      // r[k] = (1/sqrt(A)) / t_k: one correctly rounded reciprocal of the
+      // product, times 1/sqrt(A)
+      double inv = rA * __drcp_rn(pre[7]);
       if (finite_bits(inv) && inv != 0.0) {
 #pragma unroll
         for (int k = 7; k > 0; --k) {

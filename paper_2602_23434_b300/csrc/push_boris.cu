@@ -69,7 +69,9 @@ __device__ __forceinline__ void boris_f64(double* u, const double* E, const doub
   double gi = rsqrt(one_plus_norm2(um0, um1, um2));
   double hg = h * gi;
   double t0 = hg * B[0], t1 = hg * B[1], t2 = hg * B[2];
-  double sf = 2.0 / one_plus_norm2(t0, t1, t2);
+  // 2/x = 2 * rn(1/x) exactly (scaling by two is exact): the reciprocal
+  // alone, not a general division
+  double sf = 2.0 * __drcp_rn(one_plus_norm2(t0, t1, t2));
   double s0 = sf * t0, s1 = sf * t1, s2 = sf * t2;
   // u' = u- + u- x t and u+ = u- + u' x s, each component as two FMAs
   double p0 = fma(um1, t2, fma(-um2, t1, um0));
