@@ -208,6 +208,8 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
     c0 = 1.0 / (1e3 * 1.0 * 100 * dt)
     evs = []
 
+    calls = [0]
+
     def step(ev):
         p.gather_push(0.0, dt, 1)
         if ev is not None:
@@ -215,6 +217,9 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
         p.spec_update(dt, c0, 0.0)
         if ev is not None:
             ev[1].record(p.stream)
+        calls[0] += 1
+        if calls[0] == W + K:  # spectra back as (chi, eps), inside the timed region
+            p.flush()
 
     l0 = p.launches()
     total, kern = time_steps(torch, p.stream, step, K, W, per_step_events=True)
@@ -312,6 +317,8 @@ def run_lp_shock(torch, P, K: int, W: int, n=160, ppc=4, nb=128, seed=1241):
     p.sync()
     dt = 0.5 * (2.0 / n) / 0.1
 
+    calls = [0]
+
     def step(ev):
         p.gather_push(0.0, dt, 1)
         if ev is not None:
@@ -319,6 +326,9 @@ def run_lp_shock(torch, P, K: int, W: int, n=160, ppc=4, nb=128, seed=1241):
         p.spec_update(dt, 1e-8, 0.0)
         if ev is not None:
             ev[1].record(p.stream)
+        calls[0] += 1
+        if calls[0] == W + K:  # spectra back as (chi, eps), inside the timed region
+            p.flush()
 
     l0 = p.launches()
     total, kern = time_steps(torch, p.stream, step, K, W, per_step_events=True)

@@ -240,7 +240,13 @@ part_status part_deposit(part_ctx* ctx, double* grid_out);
  * With shocks enabled, every LP that the last push moved into a shock cell
  * (from outside one) then takes the shock update of part_enable_shocks.
  * part_sort or part_compact between the push and this call invalidate the
- * samples (PART_EINVAL).                                                   */
+ * samples (PART_EINVAL).
+ * The step is applied in the variables it is linear in, y = 1/eps and
+ * psi = chi eps^2 (y <- A y + C, psi <- psi/A: the same update exactly), and
+ * the bound chi and eng arrays hold psi and y from the first update until the
+ * next part_flush, part_sync, part_bind_particles, part_compact or
+ * part_inject, which turn them back into chi and eps.  In between the caller
+ * must neither read nor write them.  Energies must be positive.            */
 part_status spec_update(part_ctx* ctx, double dt, double c0, double u_rad);
 
 /* Diffusive shock acceleration of the LP spectra (PART_LP_RK2 only).

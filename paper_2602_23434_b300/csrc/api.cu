@@ -654,6 +654,7 @@ part_status part_init_particles(part_ctx* c, uint64_t seed, double u_th, double 
   }
   c->cur_alt = false;  // every bound array is overwritten
   c->perm_pend = nullptr;
+  c->spec_inv = false;
   cudaError_t e = launch_init(c, seed, u_th, eps_min, eps_max, p_index, N0);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_init_particles");
   c->sorted = false;

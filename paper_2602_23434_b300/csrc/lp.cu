@@ -216,16 +216,18 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Per LP: dtau = dt/gamma_g; ln A = ln(n_old/n_new)/3; c_r = c0 (|B|^2/2 +
-// u_rad); C = c_r dtau expm1(ln A)/ln A.  Per bin: s = A + C eps;
-// eps <- eps/s; chi <- chi s^2/A.  Evaluated with t = s/sqrt(A) =
-// sqrt(A) + (C/sqrt(A)) eps, so chi s^2/A = chi t t and eps/s = eps (1/sqrt(A))/t:
-// one FMA, two multiplies for chi and one for eps per bin.  Bins are taken 8
-// at a time so that eight independent row loads are in flight per thread, and
-// the eight 1/t come from one division (Montgomery's simultaneous inversion:
-// prefix products, one reciprocal scaled by 1/sqrt(A), unwind); FP64 division
-// costs several FMAs on this part.
-__global__ void __launch_bounds__(256, 2)
+// Eq. cr_chi along exact characteristics, in the variables the step is
+// linear in: y = 1/eps and psi = chi eps^2.  With a3 and c_r frozen over the
+// step, dy/dtau = a3 y + c_r gives y1 = A y0 + C, A = exp(a3 dtau) =
+// (n_old/n_new)^(1/3), C = c_r dtau expm1(a3 dtau)/(a3 dtau); number
+// conservation along the characteristic (chi deps fixed) gives
+// chi1 = chi0 (y1/y0)^2 / A, i.e. psi1 = psi0 / A.  Per bin that is one FMA
+// and one multiply, so the pass is bound by HBM instead of the FP64 rate.
+// FROM_PLAIN: the arrays still hold chi and eps (first update since they
+// were bound, initialised or brought back) and are converted on the way.
+// dtau = dt / gamma_g, gamma_g from the push (its sample 1/gamma_g).
+template <bool FROM_PLAIN>
+__global__ void __launch_bounds__(256)
     k_spec_update(double* __restrict__ chi, double* __restrict__ eng, double* __restrict__ n_old,
                   const double* __restrict__ samples, int64_t n, int nb, double dt, double c0,
                   double u_rad, int* __restrict__ status) {
@@ -233,58 +235,54 @@ __global__ void __launch_bounds__(256, 2)
        p += (int64_t)gridDim.x * blockDim.x) {
     const double nn = samples[p], b2 = samples[n + p], igam = samples[2 * n + p];
     const double dtau = dt * igam;
-    const double L = log(n_old[p] / nn) * (1.0 / 3.0);
-    // one expm1 gives sqrt(A) = 1 + em and expm1(L) = em (em + 2) without
-    // cancellation; 1/sqrt(A) by one division
-    const double em = expm1(0.5 * L);
-    const double sA = 1.0 + em;            // sqrt(A)
-    const double rA = __drcp_rn(sA);       // 1/sqrt(A), as 1.0 / sA rounds it
+    const double L = log(n_old[p] / nn) * (1.0 / 3.0);  // a3 dtau
+    const double em = expm1(L);                          // A - 1, no cancellation
+    const double A = 1.0 + em;
+    const double iA = __drcp_rn(A);
     const double cr = c0 * (0.5 * b2 + u_rad);
-    const double C = cr * dtau * (L == 0.0 ? 1.0 : em * (em + 2.0) / L);
-    const double Cs = C * rA;              // C / sqrt(A)
-    if (!(isfinite(sA) && isfinite(Cs))) atomicOr(status, ST_NONFINITE);
+    const double C = cr * dtau * (L == 0.0 ? 1.0 : em / L);
+    if (!(isfinite(A) && A > 0.0 && isfinite(C) && isfinite(iA))) atomicOr(status, ST_NONFINITE);
     double* ep = eng + p;
     double* cp = chi + p;
     int i = 0;
-    for (; i + 8 <= nb; i += 8) {
-      double e[8], c[8], tv[8], pre[8], r[8];
+    for (; i + 8 <= nb; i += 8) {  // eight rows' loads in flight per thread
+      double y[8], ps[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        e[k] = ep[(int64_t)(i + k) * n];
-        c[k] = cp[(int64_t)(i + k) * n];
+        y[k] = ep[(int64_t)(i + k) * n];
+        ps[k] = cp[(int64_t)(i + k) * n];
       }
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        tv[k] = sA + Cs * e[k];
-        pre[k] = k == 0 ? tv[0] : pre[k - 1] * tv[k];
-      }
-      // r[k] = (1/sqrt(A)) / t_k: one correctly rounded reciprocal of the
-      // product, times 1/sqrt(A)
-      double inv = rA * __drcp_rn(pre[7]);
-      if (finite_bits(inv) && inv != 0.0) {
-#pragma unroll
-        for (int k = 7; k > 0; --k) {
-          r[k] = inv * pre[k - 1];
-          inv = inv * tv[k];
+        if (FROM_PLAIN) {
+          ps[k] = (ps[k] * y[k]) * y[k];
+          y[k] = __drcp_rn(y[k]);
         }
-        r[0] = inv;
-      } else {  // products left the double range: divide bin by bin
-#pragma unroll
-        for (int k = 0; k < 8; ++k) r[k] = rA / tv[k];
-      }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        ep[(int64_t)(i + k) * n] = e[k] * r[k];
-        cp[(int64_t)(i + k) * n] = (c[k] * tv[k]) * tv[k];
+        ep[(int64_t)(i + k) * n] = fma(A, y[k], C);
+        cp[(int64_t)(i + k) * n] = ps[k] * iA;
       }
     }
     for (; i < nb; ++i) {
-      const double e = ep[(int64_t)i * n];
-      const double t = sA + Cs * e;
-      ep[(int64_t)i * n] = e * (rA / t);
-      cp[(int64_t)i * n] = (cp[(int64_t)i * n] * t) * t;
+      double y = ep[(int64_t)i * n], ps = cp[(int64_t)i * n];
+      if (FROM_PLAIN) {
+        ps = (ps * y) * y;
+        y = __drcp_rn(y);
+      }
+      ep[(int64_t)i * n] = fma(A, y, C);
+      cp[(int64_t)i * n] = ps * iA;
     }
     n_old[p] = nn;
+  }
+}
+
+// Back from (y, psi) to (chi, eps): eps = 1/y, chi = psi y^2.
+__global__ void __launch_bounds__(256)
+    k_spec_to_plain(double* __restrict__ chi, double* __restrict__ eng, int64_t total) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double y = eng[i], ps = chi[i];
+    eng[i] = __drcp_rn(y);
+    chi[i] = (ps * y) * y;
   }
 }
 
@@ -358,6 +356,7 @@ __global__ void k_shock_cells(const double* __restrict__ fp, const Geo g, double
 // adds the lanes before it; tiles carry their last bin and running sum.
 // q = 3r/(r-1) (Eq. slope, non-relativistic), cn = q/r (particle number per
 // unit fluid density conserved across the jump).
+template <bool INV>
 __global__ void __launch_bounds__(256)
     k_shock_convolve(const uint32_t* __restrict__ list, const double* __restrict__ rs,
                      double* __restrict__ chi, const double* __restrict__ eng, int64_t n,
@@ -379,8 +378,11 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int i = 0; i < K; ++i) {
         const int j = t0 + lane * K + i;
-        e[i] = j < nb ? eng[(int64_t)j * n + p] : 1.0;
-        const double c = j < nb ? chi[(int64_t)j * n + p] : 0.0;
+        // INV: the arrays hold y = 1/eps and psi = chi eps^2 (see k_spec_update)
+        const double ev = j < nb ? eng[(int64_t)j * n + p] : 1.0;
+        double c = j < nb ? chi[(int64_t)j * n + p] : 0.0;
+        e[i] = INV ? __drcp_rn(ev) : ev;
+        if (INV) c = (c * ev) * ev;
         le[i] = log(e[i]);
         w[i] = exp(qm2 * le[i]);
         h[i] = c * w[i];
@@ -428,7 +430,7 @@ __global__ void __launch_bounds__(256)
         if (j < nb) {
           const double out = j == 0 ? 0.0 : cn * ((before + S[i]) / w[i]);
           ok = ok && isfinite(out);
-          chi[(int64_t)j * n + p] = out;
+          chi[(int64_t)j * n + p] = INV ? (out * e[i]) * e[i] : out;
         }
       }
       cS = __shfl_sync(0xffffffffu, cS + incl, 31);
@@ -461,16 +463,35 @@ cudaError_t launch_shock_convolve(part_ctx* c) {
   if (c->n == 0) return cudaSuccess;
   int64_t b = (c->n + 7) / 8;            // 8 warps (LPs) per block
   if (b > 148 * 16) b = 148 * 16;
-  k_shock_convolve<<<(unsigned)b, 256, 0, c->stream>>>(c->shock_list, c->shock_rs, c->chi,
-                                                       c->eng, c->n, c->nbins, c->status);
+  if (c->spec_inv)
+    k_shock_convolve<true><<<(unsigned)b, 256, 0, c->stream>>>(c->shock_list, c->shock_rs, c->chi,
+                                                             c->eng, c->n, c->nbins, c->status);
+  else
+    k_shock_convolve<false><<<(unsigned)b, 256, 0, c->stream>>>(
+        c->shock_list, c->shock_rs, c->chi, c->eng, c->n, c->nbins, c->status);
   c->launches++;
   return cudaGetLastError();
 }
 
 cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad) {
   if (c->n == 0) return cudaSuccess;
-  k_spec_update<<<grid_for(c->n, 256), 256, 0, c->stream>>>(
-      c->chi, c->eng, c->n_old, c->samples, c->n, c->nbins, dt, c0, u_rad, c->status);
+  if (c->spec_inv)
+    k_spec_update<false><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
+        c->chi, c->eng, c->n_old, c->samples, c->n, c->nbins, dt, c0, u_rad, c->status);
+  else
+    k_spec_update<true><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
+        c->chi, c->eng, c->n_old, c->samples, c->n, c->nbins, dt, c0, u_rad, c->status);
+  c->launches++;
+  c->spec_inv = true;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spec_to_plain(part_ctx* c) {
+  if (!c->spec_inv) return cudaSuccess;
+  c->spec_inv = false;
+  const int64_t total = (int64_t)c->nbins * c->n;
+  if (total == 0) return cudaSuccess;
+  k_spec_to_plain<<<grid_for(total, 256), 256, 0, c->stream>>>(c->chi, c->eng, total);
   c->launches++;
   return cudaGetLastError();
 }

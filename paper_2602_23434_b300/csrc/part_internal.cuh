@@ -125,6 +125,9 @@ struct part_ctx {
   // `moved` bounds every particle's displacement since (|v| < c = 1)
   bool order_kept{};
   double moved{};
+  // LP spectra: the bound chi/eng arrays hold psi = chi eps^2 and y = 1/eps
+  // (the variables the spectral step is linear in) until the next flush
+  bool spec_inv{};
   bool bound{}, fields_set{}, sorted{}, deposit_on{}, deposit_ready{}, samples_ready{};
   int64_t launches{};
   std::string err;
@@ -332,6 +335,8 @@ cudaError_t launch_serve_kernel(int shape, int dim, const ServeHeader* hdr,
 cudaError_t launch_deposit_combine(part_ctx* c, double* out);
 cudaError_t launch_lp_push(part_ctx* c, double dt, int nsteps);
 cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad);
+// (y, psi) back to (chi, eps) in the bound arrays, if the updates left them so
+cudaError_t launch_spec_to_plain(part_ctx* c);
 
 // Launch shapes.  148 SMs; grid-stride kernels are capped at 64 CTAs per SM.
 constexpr int kSMs = 148;

@@ -828,7 +828,9 @@ cudaError_t apply_perm(part_ctx* c) {
 
 // Bring the current state into the caller's arrays, in sorted order.
 cudaError_t flush_pending(part_ctx* c) {
-  cudaError_t r = apply_perm(c);
+  cudaError_t r = launch_spec_to_plain(c);
+  if (r != cudaSuccess) return r;
+  r = apply_perm(c);
   if (r != cudaSuccess || !c->cur_alt) return r;
   c->cur_alt = false;
   const int64_t n = c->n;
