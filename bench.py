@@ -51,7 +51,7 @@ BYTES_PER_PSTEP_BORIS_DEP = 96 + 8 + 6 + 3
 # DRAM bytes (read + write) per particle of one launch of the FP64 brick kernel,
 # from an ncu capture of the kernel on the 64^3 case of the same workload (
 # 265.6 MB for 2,097,152 particles), scaled to a launch by the particle count.
-TRAFFIC_PER_PARTICLE_BRICK_F64 = 264.697856e6 / 2097152  # ncu dram r+w, 64^3 capture
+TRAFFIC_PER_PARTICLE_BRICK_F64 = 265.092864e6 / 2097152  # ncu dram r+w, 64^3 capture
 # Same for the mixed brick kernel, from an ncu capture of the 128^3 case
 # (1299.8 MB for 16,777,216 particles).
 TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1294.579712e6 / 16777216   # ncu dram r+w, 128^3 capture

@@ -250,6 +250,64 @@ def test_lp_step_and_spectra(dim, n):
     assert _rel(_host(nold), nor, 0) <= 1e-12
 
 
+def test_lp_spectra_across_flushes_and_injection():
+    """Several LP steps with no sync in between (the spectra stay in the
+    library's 1/eps, chi eps^2 form), a flush in the middle, then an injection
+    (which brings them back first) and more steps: chi and eps after the final
+    sync against the oracle's (chi, eps) steps, 1e-12 relative."""
+    dim, n, nb = 3, 16, 32
+    og, pg = _grids(dim, n)
+    vel, rho, B = synth.fluid_snapshot(dim, n, 43, v_rms=0.05)
+    f7 = np.concatenate([vel, rho, B]).reshape(7, -1)
+    N0, K = 3000, 200
+    p = P.Part(pg, P.FP64, P.TSC, P.LP_RK2, capacity=N0 + K, nbins=nb)
+    p.set_fields(_dev(f7))
+    xd = torch.zeros((3, N0 + K), dtype=torch.float64, device="cuda")
+    chi = torch.zeros((nb, N0 + K), dtype=torch.float64, device="cuda")
+    eng = torch.zeros_like(chi)
+    nold = torch.zeros(N0 + K, dtype=torch.float64, device="cuda")
+    p.bind(N0, xd, chi=chi, eng=eng, n_old=nold)
+    p.init_particles(5, 0.0, 1.0, 1e6, 2.2, 1e-6)
+    p.sync()
+
+    def plain(N):
+        v = lambda t, r: _host(t).reshape(-1)[: r * N].reshape(r, N).copy()  # noqa: E731
+        return v(xd, 3), v(chi, nb), v(eng, nb), _host(nold)[:N].copy()
+
+    x, ch, en, no = plain(N0)
+    dt, c0 = 0.5 * 2.0 / n, 3e-3
+
+    def steps(k, x, ch, en, no):
+        for _ in range(k):
+            p.gather_push(0.0, dt, 1)
+            p.spec_update(dt, c0, 0.05)
+            x, nn, b2, gm = O.lp_rk2_step(og, P.TSC, vel.reshape(3, -1), rho.reshape(1, -1),
+                                          B.reshape(3, -1), x, dt)
+            ch, en, no = O.spec_update(ch, en, no, nn, b2, gm, dt, c0, 0.05)
+        return x, ch, en, no
+
+    x, ch, en, no = steps(3, x, ch, en, no)
+    p.flush()
+    x, ch, en, no = steps(2, x, ch, en, no)
+    rng = np.random.default_rng(9)
+    xn = rng.uniform(-1.0, 1.0, (3, K))
+    e1, c1 = O.init_spectrum(nb, 1.0, 1e6, 2.2, 1e-6)
+    cn = np.repeat(c1[:, None], K, 1) * rng.uniform(0.5, 2.0, (1, K))
+    en_ = np.repeat(e1[:, None], K, 1)
+    nn0 = np.array([O.gather(og, P.TSC, rho.reshape(1, -1), xn[:, i])[0] for i in range(K)])
+    p.inject(K, x=_dev(xn), chi=_dev(cn), eng=_dev(en_), n_old=_dev(nn0))
+    N = N0 + K
+    x, ch = np.concatenate([x, xn], 1), np.concatenate([ch, cn], 1)
+    en, no = np.concatenate([en, en_], 1), np.concatenate([no, nn0])
+    x, ch, en, no = steps(3, x, ch, en, no)
+    p.sync()
+    xg, cg, eg, ng = plain(N)
+    assert np.max(np.abs(_pdiff(xg, x))) <= 1e-12 * 2.0
+    assert _rel(eg, en, 0) <= 1e-12
+    assert _rel(cg, ch, 0) <= 1e-12
+    assert _rel(ng, no, 0) <= 1e-12
+
+
 def test_init_particles_fp64_and_mixed():
     og, pg = _grids(3, 24)
     N = 50001
