@@ -216,6 +216,29 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// r[k] = 1/v[k] for eight values by Montgomery's simultaneous inversion:
+// prefix products, one correctly rounded reciprocal, then unwinding (three
+// multiplies per value instead of a reciprocal each).  Products that leave
+// the double range fall back to eight reciprocals.
+__device__ __forceinline__ void recip8(const double* v, double* r) {
+  double pre[8];
+  pre[0] = v[0];
+#pragma unroll
+  for (int k = 1; k < 8; ++k) pre[k] = pre[k - 1] * v[k];
+  double inv = __drcp_rn(pre[7]);
+  if (finite_bits(inv) && inv != 0.0 && finite_bits(pre[7]) && pre[7] != 0.0) {
+#pragma unroll
+    for (int k = 7; k > 0; --k) {
+      r[k] = inv * pre[k - 1];
+      inv = inv * v[k];
+    }
+    r[0] = inv;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r[k] = __drcp_rn(v[k]);
+  }
+}
+
 // Eq. cr_chi along exact characteristics, in the variables the step is
 // linear in: y = 1/eps and psi = chi eps^2.  With a3 and c_r frozen over the
 // step, dy/dtau = a3 y + c_r gives y1 = A y0 + C, A = exp(a3 dtau) =
@@ -252,12 +275,17 @@ __global__ void __launch_bounds__(256)
         y[k] = ep[(int64_t)(i + k) * n];
         ps[k] = cp[(int64_t)(i + k) * n];
       }
+      if (FROM_PLAIN) {  // y[] holds eps: psi = chi eps^2, y = 1/eps
+        double r[8];
+        recip8(y, r);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          ps[k] = (ps[k] * y[k]) * y[k];
+          y[k] = r[k];
+        }
+      }
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        if (FROM_PLAIN) {
-          ps[k] = (ps[k] * y[k]) * y[k];
-          y[k] = __drcp_rn(y[k]);
-        }
         ep[(int64_t)(i + k) * n] = fma(A, y[k], C);
         cp[(int64_t)(i + k) * n] = ps[k] * iA;
       }
@@ -275,14 +303,34 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Back from (y, psi) to (chi, eps): eps = 1/y, chi = psi y^2.
+// Back from (y, psi) to (chi, eps): eps = 1/y, chi = psi y^2; one thread
+// per LP, eight bins per batch inversion.
 __global__ void __launch_bounds__(256)
-    k_spec_to_plain(double* __restrict__ chi, double* __restrict__ eng, int64_t total) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double y = eng[i], ps = chi[i];
-    eng[i] = __drcp_rn(y);
-    chi[i] = (ps * y) * y;
+    k_spec_to_plain(double* __restrict__ chi, double* __restrict__ eng, int64_t n, int nb) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    double* ep = eng + p;
+    double* cp = chi + p;
+    int i = 0;
+    for (; i + 8 <= nb; i += 8) {
+      double y[8], ps[8], r[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        y[k] = ep[(int64_t)(i + k) * n];
+        ps[k] = cp[(int64_t)(i + k) * n];
+      }
+      recip8(y, r);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        ep[(int64_t)(i + k) * n] = r[k];
+        cp[(int64_t)(i + k) * n] = (ps[k] * y[k]) * y[k];
+      }
+    }
+    for (; i < nb; ++i) {
+      const double y = ep[(int64_t)i * n], ps = cp[(int64_t)i * n];
+      ep[(int64_t)i * n] = __drcp_rn(y);
+      cp[(int64_t)i * n] = (ps * y) * y;
+    }
   }
 }
 
@@ -489,9 +537,8 @@ cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad) 
 cudaError_t launch_spec_to_plain(part_ctx* c) {
   if (!c->spec_inv) return cudaSuccess;
   c->spec_inv = false;
-  const int64_t total = (int64_t)c->nbins * c->n;
-  if (total == 0) return cudaSuccess;
-  k_spec_to_plain<<<grid_for(total, 256), 256, 0, c->stream>>>(c->chi, c->eng, total);
+  if (c->n == 0 || c->nbins == 0) return cudaSuccess;
+  k_spec_to_plain<<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->chi, c->eng, c->n, c->nbins);
   c->launches++;
   return cudaGetLastError();
 }
