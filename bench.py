@@ -37,7 +37,11 @@ from paper_2602_23434_b300 import synth  # noqa: E402
 METRIC = ("particle-steps/s and % HBM roofline, FP64 vs mixed FP32 at stated error; "
           "serving p50/p99")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP64_NOMINAL_TFLOPS = 1.25      # B300 dense FP64 (non-tensor), nominal
+# B300 dense FP64 (non-tensor), nominal figure of the profiling notes; 2 FP64
+# FMA lanes per SM-cycle on 148 SMs at the 2032 MHz maximum clock would give
+# 2 x 2 x 148 x 2.032e9 = 1.20 TFLOP/s.  Reported beside the measured peak,
+# which is the roofline's denominator.
+FP64_NOMINAL_TFLOPS = 1.25
 FALLBACK_HBM_GBS = 6400.0
 
 # Algorithmic FP64 flops of one fused particle step (TSC, 3D, deposit on),
@@ -524,6 +528,24 @@ def run_2d(torch, P, n=64, ppc=16, steps=100, seed=1235):
             "ms_per_run": total / 5}
 
 
+def fp64_peak_measured(torch, P, stream):
+    """The FP64 FMA rate of this GPU, measured now (part_probe_fp64_fma: 16
+    independent DFMA chains per thread, 4 CTAs of 256 threads per SM, best of
+    5 launches), with the SM clock read just after."""
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tf, ms = P.probe_fp64_fma(stream.cuda_stream, sink, ctas_per_sm=4, iters=8192, reps=5)
+    sm = None
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(torch.cuda.current_device()),
+                              "--query-gpu=clocks.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=10).stdout.strip()
+        sm = float(out.splitlines()[0])
+    except Exception:
+        pass
+    return tf, {"tflops": tf, "best_launch_ms": ms, "sm_mhz_after": sm,
+                "what": "independent DFMA chains on every SM, CUDA events, best of 5"}
+
+
 # ----------------------------------------------------------------------------- e2e
 def run_e2e(torch, wl: BorisWorkload, K: int):
     """The step as a coupled code runs it through the C ABI: the particles stay
@@ -658,10 +680,10 @@ def headline_config(grid: int, particles: int, dt: float, world: int) -> dict:
             "parallelism": f"replicas x{world}"}
 
 
-def cpu_baseline(budget_s: float = 15.0, n=128, seed=1236):
-    """The oracle as it stands (OpenMP over particles in the push; sort and
-    deposit sequential), one step = keys + stable sort + permute + Boris step
-    + deposit, on a sample of the headline workload's particles."""
+def _oracle_boris_stepper(n: int, seed: int, deposit: bool = True):
+    """(one_step, grid, dt) of the oracle on the turbulent n^3 workload: keys,
+    stable sort, permute, Boris step, deposit (or the Boris step alone for
+    test particles)."""
     from oracle import oracle as O
     f = synth.em_fields(3, n, seed).reshape(6, -1)
     g = O.make_grid(3, (n, n, n))
@@ -669,6 +691,9 @@ def cpu_baseline(budget_s: float = 15.0, n=128, seed=1236):
     brick = (8, 8, 8)
 
     def one_step(x, u, w):
+        if not deposit:
+            x1, u1, _, _ = O.boris_step(g, O.TSC, f, x, u, w, 1.0, dt, False)
+            return x1, u1, w
         k = O.keys(g, brick, x)
         perm = O.stable_sort(k)
         x, u, w = x[:, perm], u[:, perm], w[perm]
@@ -676,24 +701,42 @@ def cpu_baseline(budget_s: float = 15.0, n=128, seed=1236):
         O.deposit(g, O.TSC, xo, F)
         return x1, u1, w
 
+    return one_step, g, dt
+
+
+def _sample_size(one_step, init, budget_s: float, steps: int, n_max: int) -> int:
+    """Particles per sampled step so that `steps` steps take about budget_s."""
+    ns = 1 << 16
+    x, u, w = init(ns)
+    t0 = time.perf_counter()
+    one_step(x, u, w)
+    t1 = max(time.perf_counter() - t0, 1e-3)
+    return int(min(n_max, max(1 << 14, ns * budget_s / steps / t1)))
+
+
+def cpu_baseline(budget_s: float = 15.0, n=128, seed=1236):
+    """The oracle as it stands (OpenMP over particles in the push; sort and
+    deposit sequential), one step = keys + stable sort + permute + Boris step
+    + deposit, on a sample of the headline workload's particles."""
+    from oracle import oracle as O
+    one_step, g, dt = _oracle_boris_stepper(n, seed)
+
+    def init(k):
+        x, u, w, _ = O.init_particles(g, k, seed, 0.1)
+        return x, u, w
+
     # one host thread first, on a small sample
     cores = O.max_threads()
     O.set_threads(1)
     N1 = 1 << 16
-    x, u, w, _ = O.init_particles(g, N1, seed, 0.1)
+    x, u, w = init(N1)
     t0 = time.perf_counter()
     one_step(x, u, w)
     e1 = time.perf_counter() - t0
     O.set_threads(cores)
-    Ns = 1 << 16
-    x, u, w, _ = O.init_particles(g, Ns, seed, 0.1)
-    t0 = time.perf_counter()
-    one_step(x, u, w)
-    t1 = time.perf_counter() - t0
-    # scale the sample so that ~budget seconds of steps are timed
     steps = 3
-    Ns = int(min(1 << 23, max(1 << 16, Ns * budget_s / steps / max(t1, 1e-3))))
-    x, u, w, _ = O.init_particles(g, Ns, seed, 0.1)
+    Ns = _sample_size(one_step, init, budget_s, steps, 1 << 23)
+    x, u, w = init(Ns)
     t0 = time.perf_counter()
     for _ in range(steps):
         x, u, w = one_step(x, u, w)
@@ -706,20 +749,135 @@ def cpu_baseline(budget_s: float = 15.0, n=128, seed=1236):
                       f"steps (keys, stable sort, permute, Boris step, deposit), {el:.1f} s"}
 
 
+def cpu_baseline_mixed(budget_s: float = 8.0, n=256, seed=1237):
+    """The oracle (FP64: it has no mixed form) on the mixed-form workload's
+    inputs: the turbulent 256^3 fields, a sample of its 134,217,728
+    particles, sort + Boris + deposit, in the same unit."""
+    from oracle import oracle as O
+    one_step, g, _ = _oracle_boris_stepper(n, seed)
+
+    def init(k):
+        x, u, w, _ = O.init_particles(g, k, seed, 0.1)
+        return x, u, w
+
+    steps = 2
+    Ns = _sample_size(one_step, init, budget_s, steps, 1 << 22)
+    x, u, w = init(Ns)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        x, u, w = one_step(x, u, w)
+    el = time.perf_counter() - t0
+    return {"value": Ns * steps / el, "unit": "particle-steps/s", "cores": O.max_threads(),
+            "kind": "oracle",
+            "sample": f"{Ns} of the 134,217,728 particles of the 256^3 mixed-form workload, "
+                      f"{steps} steps of the FP64 oracle (keys, stable sort, permute, Boris "
+                      f"step, deposit), {el:.1f} s"}
+
+
+def cpu_baseline_lp(budget_s: float = 8.0, n=128, nb=128, seed=1238):
+    """The oracle on the LP workload: the 128^3 fluid snapshot, a sample of
+    its 4,194,304 LPs with 128 bins each, Heun RK2 + spectral update."""
+    from oracle import oracle as O
+    vel, rho, B = synth.fluid_snapshot(3, n, seed)
+    vel, rho, B = vel.reshape(3, -1), rho.reshape(1, -1), B.reshape(3, -1)
+    g = O.make_grid(3, (n, n, n))
+    dt = 0.5 * 2.0 / n
+    c0 = 1.0 / (1e3 * 1.0 * 100 * dt)
+    e0, x0 = O.init_spectrum(nb, 1.0, 1e6, 2.2, 1e-6)
+
+    def init(k):
+        x = np.random.default_rng(seed).uniform(-1.0, 1.0, (3, k))
+        chi = np.repeat(x0[:, None], k, axis=1)
+        eng = np.repeat(e0[:, None], k, axis=1)
+        _, n_new, _, _ = O.lp_rk2_step(g, O.TSC, vel, rho, B, x, 0.0)
+        return x, (chi, eng), n_new
+
+    def one_step(x, spec, n_old):
+        x, n_new, b2m, gam = O.lp_rk2_step(g, O.TSC, vel, rho, B, x, dt)
+        chi, eng, n_old = O.spec_update(spec[0], spec[1], n_old, n_new, b2m, gam, dt, c0)
+        return x, (chi, eng), n_old
+
+    steps = 2
+    Ns = _sample_size(one_step, init, budget_s, steps, 1 << 20)
+    x, spec, n_old = init(Ns)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        x, spec, n_old = one_step(x, spec, n_old)
+    el = time.perf_counter() - t0
+    return {"value": Ns * steps / el, "unit": "LP-steps/s", "cores": O.max_threads(),
+            "kind": "oracle",
+            "sample": f"{Ns} of the 4,194,304 LPs x {nb} bins of the 128^3 LP workload, "
+                      f"{steps} steps (Heun RK2 + spectral update), {el:.1f} s"}
+
+
+def cpu_baseline_serving(budget_s: float = 6.0, n=256, seed=1241):
+    """No-batching reference for the serving stream: the oracle advances
+    one request's test particles alone (FP64 Boris steps, no deposit) on a
+    256^3 snapshot; a request of N particles and S steps would take N S /
+    rate seconds on the host cores."""
+    from oracle import oracle as O
+    one_step, g, _ = _oracle_boris_stepper(n, seed, deposit=False)
+
+    def init(k):
+        x, u, w, _ = O.init_particles(g, k, seed, 0.1)
+        return x, u, w
+
+    steps = 3
+    Ns = _sample_size(one_step, init, budget_s, steps, 1 << 22)
+    x, u, w = init(Ns)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        x, u, w = one_step(x, u, w)
+    el = time.perf_counter() - t0
+    rate = Ns * steps / el
+    med = np.exp(0.5 * (np.log(1e3) + np.log(1e7))) * np.exp(0.5 * (np.log(10) + np.log(1000)))
+    return {"value": rate, "unit": "particle-steps/s", "cores": O.max_threads(),
+            "kind": "oracle",
+            "sample": f"one request of {Ns} test particles on a 256^3 snapshot, {steps} FP64 "
+                      f"Boris steps alone (no batching), {el:.1f} s",
+            "median_request_s": med / rate,
+            "largest_request_s": 1e7 * 1000 / rate}
+
+
 def reference_arm(args):
+    """The oracle, timed on the host cores, on the headline workload's config
+    and metric: W untimed and K timed steps, each step one pass of keys,
+    stable sort, permute, Boris step and deposit over a bounded sample of the
+    16,777,216 particles, sized so that the run ends within about two
+    minutes.  value = sampled particles x K / timed seconds."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    cb = cpu_baseline(budget_s=max(5.0, 4.0 * args.steps / max(args.steps, 1)))
+    from oracle import oracle as O
+    n, seed = 128, 1236
+    one_step, g, dt = _oracle_boris_stepper(n, seed)
+
+    def init(k):
+        x, u, w, _ = O.init_particles(g, k, seed, 0.1)
+        return x, u, w
+
+    K, W = args.steps, args.warmup
+    Ns = _sample_size(one_step, init, 90.0, K + W, 128 ** 3 * 8)
+    x, u, w = init(Ns)
+    for _ in range(W):
+        x, u, w = one_step(x, u, w)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        x, u, w = one_step(x, u, w)
+    el = time.perf_counter() - t0
+    value = Ns * K / el
     N = 128 ** 3 * 8
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"],
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": N / cb["value"] * 1e3,
+    sample = (f"{Ns} of the {N} particles of the 128^3 workload per step, {W} warm-up + {K} "
+              f"timed steps (keys, stable sort, permute, Boris step, deposit), {el:.1f} s timed")
+    cfg = headline_config(128, N, dt, 1)
+    cfg["sample_particles_per_step"] = Ns
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": el / K * 1e3,
             "higher_is_better": True, "scaling": "weak", "dtype": "f64", "data": "synthetic",
-            "config": headline_config(128, N, cb["dt"], 1),
-            "cpu_baseline": {"value": cb["value"], "unit": cb["unit"], "cores": cb["cores"],
-                             "kind": "oracle", "sample": cb["sample"]},
-            "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
+            "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s",
+                             "cores": O.max_threads(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "vs_baseline": None}
     print(json.dumps(line), flush=True)
@@ -758,8 +916,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-extras", action="store_true", help="headline workload only")
-    ap.add_argument("--serve-requests", type=int, default=200,
-                    help="requests in the serving stream (the full stated stream is 2000)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests in the serving stream (the stated stream is 2000)")
     ap.add_argument("--grid", type=int, default=128,
                     help="cells per axis of the headline workload (128 = the stated one; "
                          "smaller only for profiling captures)")
@@ -814,6 +972,7 @@ def main():
     hbm, hbm_kind = peaks()
     achieved_tf = FLOP_PER_PSTEP_BORIS_DEP * wl.N / (kmean / 1e3) / 1e12
     achieved_gbs = BYTES_PER_PSTEP_BORIS_DEP * wl.N / (kmean / 1e3) / 1e9
+    fp64_peak, fp64_probe = fp64_peak_measured(torch, P, stream)
 
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
@@ -822,15 +981,19 @@ def main():
         "data": "synthetic",
         "config": headline_config(args.grid, wl.N, wl.dt, world),
         "roofline": {"bound": "alu", "kernel": "k_boris_brick_f64_dep (TSC, 3D, warp-specialised push + deposit)",
-                     "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_NOMINAL_TFLOPS,
+                     "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tf / fp64_peak, "peak_kind": "measured",
+                     "peak_probe": fp64_probe,
+                     "peak_nominal": FP64_NOMINAL_TFLOPS,
+                     "frac_of_nominal": achieved_tf / FP64_NOMINAL_TFLOPS,
                      "traffic": TRAFFIC_PER_PARTICLE_BRICK_F64 * wl.N,
                      "traffic_unit": "bytes per launch (ncu dram read+write, scaled by "
                                      "particles from the 64^3 capture)",
                      "flop_per_particle_step": FLOP_PER_PSTEP_BORIS_DEP,
                      "kernel_ms": kmean,
-                     "peak_note": "FP64 non-tensor nominal (recipe); FP64 is 1/64 of FP32 on "
-                                  "B300"},
+                     "peak_note": "FP64 non-tensor FMA rate measured on this GPU by "
+                                  "part_probe_fp64_fma right after the timed steps (burst); "
+                                  "peak_nominal is the recipe's nominal figure"},
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                          "frac": achieved_gbs / hbm,
                          "bytes_per_particle_step": BYTES_PER_PSTEP_BORIS_DEP,
@@ -881,6 +1044,15 @@ def main():
         cb = cpu_baseline()
         cb.pop("dt", None)
         line["cpu_baseline"] = cb
+        if not args.no_extras:
+            rows = {}
+            for key, fn in (("lp", cpu_baseline_lp), ("mixed_256", cpu_baseline_mixed),
+                            ("serving", cpu_baseline_serving)):
+                try:
+                    rows[key] = fn()
+                except Exception as e:  # report, do not hide
+                    rows[key] = {"error": repr(e)}
+            line["cpu_baseline_rows"] = rows
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

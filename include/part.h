@@ -362,6 +362,23 @@ part_status part_server_run(part_server* s, int nitems);
 part_status part_server_sync(part_server* s);
 part_status part_server_destroy(part_server* s);
 
+/* ---- Measurement -----------------------------------------------------------
+ * FP64 fused multiply-add rate of the current device, measured: the
+ * denominator of the arithmetic roofline of this library's FP64 kernels (on
+ * B300 every FP64 kernel that does real arithmetic per byte is bound by the
+ * FP64 pipe, not by HBM).  Not in the paper.  Runs ctas_per_sm CTAs of 256
+ * threads on every SM, each thread 16 independent chains of iters dependent
+ * fma steps, once untimed and then reps times, each timed with CUDA events
+ * on cuda_stream (NULL = legacy default stream); synchronises that stream.
+ * *tflops = 2 flop x threads x 16 x iters / best time (TFLOP/s); *best_ms
+ * (may be NULL) = that time.  sink: device memory of one double, caller-owned
+ * (never written in practice; it keeps the chains from being optimised away).
+ * Errors: PART_EINVAL for NULL sink/tflops, an unaligned or unreachable
+ * sink, ctas_per_sm outside 1..8, iters outside 1..2^20, reps outside 1..100;
+ * PART_ECUDA if a launch or event call fails.  Nothing is allocated.        */
+part_status part_probe_fp64_fma(void* cuda_stream, double* sink, int ctas_per_sm, int iters,
+                                int reps, double* tflops, double* best_ms);
+
 /* ---- Sort without any device allocation ----------------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory when they need a sort, so cannot provide the
@@ -378,14 +395,27 @@ part_status part_server_destroy(part_server* s);
  * default stream).
  *
  * Scratch: a static array of PART_NOALLOC_SORT_SCRATCH_BYTES compiled into
- * libpart.so, held by every GPU that loads the library until the process
- * exits.  The first call on each device (with that device current) looks up
- * the array's device address; make that first call before any stream
- * capture.  All calls share the array, so calls that overlap on the GPU race:
- * serialise them.  Nothing is allocated or freed.
- * Errors: PART_EINVAL if n > PART_NOALLOC_SORT_MAX_N or a pointer is NULL
- * (message in part_last_error(NULL)).  Non-finite positions are sorted as if
- * in cell 0 of that axis and are not reported by this entry point.          */
+ * libpart.so.  Each device holds it until the process exits: from the
+ * library's load when CUDA loads modules eagerly, else (CUDA_MODULE_LOADING
+ * = LAZY, the default) from the first use of the library's kernels on that
+ * device.  The first call on each device (with that device current) looks up
+ * the array's device address and caches it per device ordinal; the cache
+ * assumes the device's primary context (the one the CUDA runtime uses) for
+ * the life of the process, so do not call this entry point again after a
+ * cudaDeviceReset or from another driver-API context.  Make that first call
+ * before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU race: serialise them.  Nothing is allocated or freed.
+ * Errors (message in part_last_error(NULL)):
+ *   PART_EINVAL       n < 0 or n > PART_NOALLOC_SORT_MAX_N; x or u NULL with
+ *                     n > 0; cell_start NULL; an array not aligned to its
+ *                     element size; an array the kernels cannot reach
+ *                     (pageable host memory, another device's memory);
+ *                     an invalid grid;
+ *   PART_EUNSUPPORTED the current device's ordinal is 128 or more;
+ *   PART_ECUDA        a CUDA runtime call (device query, symbol lookup,
+ *                     launch) failed.
+ * Non-finite positions are sorted as if in cell 0 of that axis and are not
+ * reported by this entry point.                                             */
 #define PART_NOALLOC_SORT_MAX_N 1048576
 #define PART_NOALLOC_SORT_SCRATCH_BYTES 25428736
 part_status part_sort_fp64_noalloc(const part_grid* grid, int64_t n, double* x, double* u,

@@ -109,6 +109,8 @@ def lib():
         "part_selftest_wait": (st, [P, C.c_int64, C.c_int]),
         "part_inject": (st, [P, C.c_int64, P, P, P, P, P, P, P, P]),
         "part_sort_fp64_noalloc": (st, [G, C.c_int64, P, P, P, P, P, P]),
+        "part_probe_fp64_fma": (st, [P, P, C.c_int, C.c_int, C.c_int,
+                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "part_server_sizes": (st, [C.c_int, C.c_int, C.POINTER(C.c_size_t),
                                    C.POINTER(C.c_size_t)]),
         "part_server_init": (st, [C.POINTER(P), C.POINTER(P), C.c_int, C.c_int, P, C.c_size_t,
@@ -285,3 +287,18 @@ class Part:
     def selftest_wait(self, limit_ns: int, arrive: bool):
         """One bounded mbarrier wait on the device (see part_selftest_wait)."""
         self._check(self.L.part_selftest_wait(self.ctx, int(limit_ns), 1 if arrive else 0))
+
+
+def probe_fp64_fma(stream_ptr: int, sink, ctas_per_sm: int = 4, iters: int = 8192,
+                   reps: int = 5) -> tuple[float, float]:
+    """Measured FP64 FMA rate of the current device (part_probe_fp64_fma):
+    (TFLOP/s, best launch ms).  sink: a device tensor of at least one
+    float64; stream_ptr: a cudaStream_t as an integer (0 = default)."""
+    L = lib()
+    tf, ms = C.c_double(0.0), C.c_double(0.0)
+    code = L.part_probe_fp64_fma(C.c_void_p(stream_ptr or None), C.c_void_p(sink.data_ptr()),
+                                 int(ctas_per_sm), int(iters), int(reps), C.byref(tf),
+                                 C.byref(ms))
+    if code != 0:
+        raise PartError(code, L.part_last_error(None).decode())
+    return tf.value, ms.value

@@ -315,9 +315,11 @@ part_status part_init(part_ctx** out, const part_grid* grid, part_prec prec, par
   c->capacity = capacity;
   c->nbins = mode == PART_LP_RK2 ? nbins : 0;
   c->stream = (cudaStream_t)cuda_stream;
-  if (cudaGetDevice(&c->device) != cudaSuccess) {
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) !=
+          cudaSuccess || c->sms < 1) {
     delete c;
-    return fail(nullptr, PART_ECUDA, "cudaGetDevice failed");
+    return fail(nullptr, PART_ECUDA, "cudaGetDevice / multiprocessor count query failed");
   }
   c->ncomp = ncomp_of(mode);
   c->fcomp = fcomp_of(prec, mode);

@@ -222,13 +222,13 @@ cudaError_t launch_pad_fields(part_ctx* c, const void* src) {
   // one warp per padded row, 8 warps per CTA
   const int64_t rows = (int64_t)c->geo.pn[2] * c->geo.pn[1];
   if (c->fcomp == 8 && c->esize == 4)
-    k_pad_fields_aos8<<<grid_for(rows * 32, 256), 256, 0, c->stream>>>(
+    k_pad_fields_aos8<<<grid_for(c, rows * 32, 256), 256, 0, c->stream>>>(
         (const float*)src, (float*)c->fpad, c->geo, c->ncomp);
   else if (c->esize == 8)
-    k_pad_fields<double><<<grid_for(rows * c->ncomp * 32, 256), 256, 0, c->stream>>>(
+    k_pad_fields<double><<<grid_for(c, rows * c->ncomp * 32, 256), 256, 0, c->stream>>>(
         (const double*)src, (double*)c->fpad, c->geo, c->ncomp);
   else
-    k_pad_fields<float><<<grid_for(rows * c->ncomp * 32, 256), 256, 0, c->stream>>>(
+    k_pad_fields<float><<<grid_for(c, rows * c->ncomp * 32, 256), 256, 0, c->stream>>>(
         (const float*)src, (float*)c->fpad, c->geo, c->ncomp);
   c->launches++;
   return cudaGetLastError();
@@ -238,7 +238,7 @@ cudaError_t launch_init(part_ctx* c, uint64_t seed, double u_th, double emin, do
                         double pidx, double N0) {
   const int64_t n = c->n;
   if (n == 0) return cudaSuccess;
-  const int gb = grid_for(n, 256);
+  const int gb = grid_for(c, n, 256);
   if (c->mode == PART_BORIS && c->prec == PART_FP64) {
     k_init_boris_f64<<<gb, 256, 0, c->stream>>>(c->geo, n, seed, u_th, (double*)c->x,
                                                 (double*)c->u, (double*)c->w, c->id);

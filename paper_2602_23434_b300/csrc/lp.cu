@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(256)
 
 template <int SHAPE, int DIM, int ORDER, bool CACHED>
 cudaError_t lp_launch_cached(part_ctx* c, double dt) {
-  const int gb = grid_for(c->n, 256);
+  const int gb = grid_for(c, c->n, 256);
   if (c->shk) {
     cudaError_t e = cudaMemsetAsync(c->shock_list, 0, sizeof(uint32_t), c->stream);
     if (e != cudaSuccess) return e;
@@ -501,7 +501,7 @@ cudaError_t launch_lp_push(part_ctx* c, double dt, int nsteps) {
 }
 
 cudaError_t launch_shock_cells(part_ctx* c) {
-  k_shock_cells<<<grid_for(c->geo.G, 256), 256, 0, c->stream>>>(
+  k_shock_cells<<<grid_for(c, c->geo.G, 256), 256, 0, c->stream>>>(
       (const double*)c->fpad, c->geo, c->r_min, c->shock_r);
   c->launches++;
   return cudaGetLastError();
@@ -510,7 +510,7 @@ cudaError_t launch_shock_cells(part_ctx* c) {
 cudaError_t launch_shock_convolve(part_ctx* c) {
   if (c->n == 0) return cudaSuccess;
   int64_t b = (c->n + 7) / 8;            // 8 warps (LPs) per block
-  if (b > 148 * 16) b = 148 * 16;
+  if (b > (int64_t)c->sms * 16) b = (int64_t)c->sms * 16;
   if (c->spec_inv)
     k_shock_convolve<true><<<(unsigned)b, 256, 0, c->stream>>>(c->shock_list, c->shock_rs, c->chi,
                                                              c->eng, c->n, c->nbins, c->status);
@@ -524,10 +524,10 @@ cudaError_t launch_shock_convolve(part_ctx* c) {
 cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad) {
   if (c->n == 0) return cudaSuccess;
   if (c->spec_inv)
-    k_spec_update<false><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
+    k_spec_update<false><<<grid_for(c, c->n, 256), 256, 0, c->stream>>>(
         c->chi, c->eng, c->n_old, c->samples, c->n, c->nbins, dt, c0, u_rad, c->status);
   else
-    k_spec_update<true><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
+    k_spec_update<true><<<grid_for(c, c->n, 256), 256, 0, c->stream>>>(
         c->chi, c->eng, c->n_old, c->samples, c->n, c->nbins, dt, c0, u_rad, c->status);
   c->launches++;
   c->spec_inv = true;
@@ -538,7 +538,7 @@ cudaError_t launch_spec_to_plain(part_ctx* c) {
   if (!c->spec_inv) return cudaSuccess;
   c->spec_inv = false;
   if (c->n == 0 || c->nbins == 0) return cudaSuccess;
-  k_spec_to_plain<<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->chi, c->eng, c->n, c->nbins);
+  k_spec_to_plain<<<grid_for(c, c->n, 256), 256, 0, c->stream>>>(c->chi, c->eng, c->n, c->nbins);
   c->launches++;
   return cudaGetLastError();
 }
@@ -560,7 +560,7 @@ __global__ void k_lp_sample_rho(const double* __restrict__ fp, const Geo g,
 
 cudaError_t launch_lp_sample_rho(part_ctx* c) {
   if (c->n == 0) return cudaSuccess;
-  const int gb = grid_for(c->n, 256);
+  const int gb = grid_for(c, c->n, 256);
   const double* fp = (const double*)c->fpad;
   const double* x = (const double*)c->x;
   if (c->shape == PART_TSC) {

@@ -87,8 +87,10 @@ extern "C" part_status part_sort_fp64_noalloc(const part_grid* grid, int64_t n, 
        reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(id)) % 8 != 0 ||
       reinterpret_cast<uintptr_t>(cell_start) % 4 != 0)
     return fail(nullptr, PART_EINVAL, "an array is not aligned to its element size");
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, PART_ECUDA, "cudaGetDevice failed");
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return fail(nullptr, PART_ECUDA, "cudaGetDevice / multiprocessor count query failed");
   if (!device_accessible(dev, x) || !device_accessible(dev, u) || !device_accessible(dev, w) ||
       !device_accessible(dev, id) || !device_accessible(dev, cell_start))
     return fail(nullptr, PART_EINVAL, "an array is not memory the kernels can reach");
@@ -107,6 +109,8 @@ extern "C" part_status part_sort_fp64_noalloc(const part_grid* grid, int64_t n, 
   c.capacity = kMaxN;
   c.nbins = 0;
   c.stream = (cudaStream_t)cuda_stream;
+  c.device = dev;
+  c.sms = sms;
   c.ncomp = 6;
   c.esize = 8;
   make_geo(grid, 8, &c.geo);

@@ -65,6 +65,7 @@ struct part_ctx {
   int nbins{};
   cudaStream_t stream{};
   int device{};       // CUDA device current at part_init
+  int sms{};          // its multiprocessor count (launch shapes)
   Geo geo{};
   int ncomp{};        // field components (6 Boris, 7 LP)
   int fcomp{};        // components per cell as stored: SoA ncomp, or 8 (cell-interleaved f32)
@@ -338,25 +339,28 @@ cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad);
 // (y, psi) back to (chi, eps) in the bound arrays, if the updates left them so
 cudaError_t launch_spec_to_plain(part_ctx* c);
 
-// Launch shapes.  148 SMs; grid-stride kernels are capped at 64 CTAs per SM.
-constexpr int kSMs = 148;
-inline int grid_for(int64_t n, int threads) {
+// Launch shapes.  The SM count is read from the device at part_init
+// (cudaDevAttrMultiProcessorCount: 148 on a full B300, fewer on a smaller
+// SKU or a MIG slice); grid-stride kernels are capped at 64 CTAs per SM.
+inline int grid_for(const part_ctx* c, int64_t n, int threads) {
+  const int64_t cap = (int64_t)(c->sms > 0 ? c->sms : 1) * 64;
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
-  if (b > kSMs * 64) b = kSMs * 64;
+  if (b > cap) b = cap;
   return (int)b;
 }
 // CTA size (256, 128 or 64 threads, one particle each) that spreads a set too
 // small to fill the GPU most evenly over the SMs: the one whose fullest SM
-// holds the fewest particles (65,536 particles: 64 threads, 448 per SM
-// instead of 512).  Sets of a full wave or more keep 256.
-inline int threads_for_spread(int64_t n) {
-  if (n >= (int64_t)kSMs * 2048) return 256;
+// holds the fewest particles (65,536 particles on 148 SMs: 64 threads, 448 per
+// SM instead of 512).  Sets of a full wave or more keep 256.
+inline int threads_for_spread(const part_ctx* c, int64_t n) {
+  const int64_t sms = c->sms > 0 ? c->sms : 1;
+  if (n >= sms * 2048) return 256;
   int best = 256;
   int64_t best_load = INT64_MAX;
   for (int t : {256, 128, 64}) {
     const int64_t blocks = (n + t - 1) / t;
-    const int64_t load = (blocks + kSMs - 1) / kSMs * t;
+    const int64_t load = (blocks + sms - 1) / sms * t;
     if (load < best_load) {
       best_load = load;
       best = t;

@@ -677,8 +677,8 @@ template <int SHAPE, int DIM>
 cudaError_t particles_f64(part_ctx* c, double qm, double dt, int nsteps) {
   auto kern = c->geo.any_open ? k_boris_particles_f64<SHAPE, DIM, true>
                               : k_boris_particles_f64<SHAPE, DIM, false>;
-  const int t = threads_for_spread(c->n);
-  kern<<<grid_for(c->n, t), t, 0, c->stream>>>(
+  const int t = threads_for_spread(c, c->n);
+  kern<<<grid_for(c, c->n, t), t, 0, c->stream>>>(
       (const double*)c->fpad, c->geo, (double*)c->x, (double*)c->u, c->n, qm, dt, nsteps,
       c->status, c->outmask);
   c->launches++;
@@ -714,7 +714,7 @@ cudaError_t launch_deposit_combine(part_ctx* c, double* out) {
   bool fast = true;
   for (int a = 0; a < 3; ++a)
     if (g.h[a] != 0 && (g.nb[a] < 3 || g.n[a] % g.b[a] != 0 || g.open[a])) fast = false;
-  k_dep_combine<<<grid_for(g.G, 256), 256, 0, c->stream>>>(c->dpart, out, g, fast);
+  k_dep_combine<<<grid_for(c, g.G, 256), 256, 0, c->stream>>>(c->dpart, out, g, fast);
   c->launches++;
   return cudaGetLastError();
 }

@@ -562,8 +562,8 @@ cudaError_t dispatch_mixed(part_ctx* c, double qm, double dt, int nsteps) {
   if (c->sorted && nsteps == 1)
     return c->deposit_on ? brick_mixed<SHAPE, DIM, true>(c, a)
                          : brick_mixed<SHAPE, DIM, false>(c, a);
-  const int t = threads_for_spread(c->n);
-  k_boris_particles_mixed<SHAPE, DIM><<<grid_for(c->n, t), t, 0, c->stream>>>(
+  const int t = threads_for_spread(c, c->n);
+  k_boris_particles_mixed<SHAPE, DIM><<<grid_for(c, c->n, t), t, 0, c->stream>>>(
       (const float*)c->fpad, c->geo, (int32_t*)c->x, (float*)c->off, (float*)c->u, c->n, a.h,
       a.hl, a.dtdx[0], a.dtdx[1], a.dtdx[2], nsteps, c->status, c->outmask);
   c->launches++;

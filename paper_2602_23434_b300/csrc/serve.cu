@@ -123,9 +123,13 @@ part_status part_server_init(part_server** out, part_ctx* const* snapshots, int 
   s->h_stage = (char*)host_stage;
   s->stage_bytes = L.stage;
   s->threads = threads;
-  int dev = 0, nsm = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      nsm < 1) {
+    delete s;
+    return fail(nullptr, PART_ECUDA, "cudaGetDevice / multiprocessor count query failed");
+  }
   s->grid = nsm * ctas_per_sm;
   std::memset(s->h_stage, 0, L.stage);
   SnapEntry tab[kMaxSnaps];

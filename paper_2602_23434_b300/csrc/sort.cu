@@ -668,7 +668,7 @@ __global__ void k_fill_holes(T* __restrict__ a, const uint8_t* __restrict__ del,
 template <typename T>
 cudaError_t permute_plane(part_ctx* c, T* arr, const uint32_t* perm) {
   const int64_t n = c->n;
-  k_gather<T><<<grid_for(n, 256), 256, 0, c->stream>>>(arr, (T*)c->tmp, perm, n);
+  k_gather<T><<<grid_for(c, n, 256), 256, 0, c->stream>>>(arr, (T*)c->tmp, perm, n);
   c->launches++;
   return cudaMemcpyAsync(arr, c->tmp, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream);
 }
@@ -686,10 +686,10 @@ cudaError_t launch_sort(part_ctx* c) {
   const void* xcur = state_of(c, c->cur_alt).x;
   if (n > 0) {
     if (c->mode == PART_BORIS && c->prec == PART_MIXED)
-      k_keys_cell<<<grid_for(n, 256), 256, 0, s>>>((const int32_t*)xcur, n, g, c->keys[0],
+      k_keys_cell<<<grid_for(c, n, 256), 256, 0, s>>>((const int32_t*)xcur, n, g, c->keys[0],
                                                    c->vals[0], c->status);
     else
-      k_keys_f64<<<grid_for(n, 256), 256, 0, s>>>((const double*)xcur, n, g, c->keys[0],
+      k_keys_f64<<<grid_for(c, n, 256), 256, 0, s>>>((const double*)xcur, n, g, c->keys[0],
                                                   c->vals[0], c->status);
     c->launches++;
     int bits = 0;
@@ -713,7 +713,7 @@ cudaError_t launch_sort(part_ctx* c) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const uint32_t* perm = c->vals[cur];
     const uint32_t* sk = c->keys[cur];
-    k_cell_start<<<grid_for(n + 1, 256), 256, 0, s>>>(sk, n, g.nkeys, c->cstart);
+    k_cell_start<<<grid_for(c, n + 1, 256), 256, 0, s>>>(sk, n, g.nkeys, c->cstart);
     c->launches++;
     return permute_all(c, perm);
   } else {
@@ -740,7 +740,7 @@ cudaError_t launch_sort_incremental(part_ctx* c) {
   else
     k_inc_count<false><<<nbk, kIncT, 0, s>>>(xcur, n, c->cstart, g, c->keys[0], c->bslot,
                                              c->status);
-  k_inc_dest<<<grid_for(g.nbricks * 32, 256), 256, 0, s>>>(c->bslot, g, c->bcount);
+  k_inc_dest<<<grid_for(c, g.nbricks * 32, 256), 256, 0, s>>>(c->bslot, g, c->bcount);
   e = cudaMemsetAsync(c->bcount + g.nbricks, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   const int64_t m = g.nbricks + 1;
@@ -814,11 +814,11 @@ cudaError_t apply_perm(part_ctx* c) {
   if (n == 0) return cudaSuccess;
   const PState a = state_of(c, c->cur_alt), b = state_of(c, !c->cur_alt);
   if (c->prec == PART_FP64)
-    k_gather_state<double, 3, double><<<grid_for(n, 256), 256, 0, c->stream>>>(
+    k_gather_state<double, 3, double><<<grid_for(c, n, 256), 256, 0, c->stream>>>(
         (const double*)a.x, nullptr, (const double*)a.u, (const double*)a.w, a.id,
         (double*)b.x, nullptr, (double*)b.u, (double*)b.w, b.id, perm, n);
   else
-    k_gather_state<int32_t, 1, float><<<grid_for(n, 256), 256, 0, c->stream>>>(
+    k_gather_state<int32_t, 1, float><<<grid_for(c, n, 256), 256, 0, c->stream>>>(
         (const int32_t*)a.x, (const float*)a.off, (const float*)a.u, (const float*)a.w, a.id,
         (int32_t*)b.x, (float*)b.off, (float*)b.u, (float*)b.w, b.id, perm, n);
   c->launches++;
@@ -951,7 +951,7 @@ cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew_out) {
     *nnew_out = 0;
     return cudaSuccess;
   }
-  const int gb = grid_for(n + 1, 256);
+  const int gb = grid_for(c, n + 1, 256);
   const int64_t m = n + 1;
   const int64_t nblk = (m + kScanBlock - 1) / kScanBlock;
   uint32_t* D = c->keys[0];
