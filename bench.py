@@ -352,10 +352,11 @@ def run_lp_shock(torch, P, K: int, W: int, n=160, ppc=4, nb=128, seed=1241):
             "dt": dt, "gpu_launches_per_step": launches}
 
 
-# Mixed form: per particle-step, state read 32 B (cell 4, offsets 12, u 12,
-# w 4) + written 28 B, f32 field stencil 24 B per cell / 8 ppc = 3, deposit
-# partials 3 x 8 B per cell / 8 ppc = 3.
-BYTES_PER_PSTEP_MIXED_DEP = 32 + 28 + 3 + 3
+# Mixed form: per particle-step, state read 44 B (cell 4, offsets 12, the
+# momentum as a compensated f32 pair 24, w 4) + written 40 B, f32 field
+# stencil 6 x 4 B per cell / 8 ppc = 3, deposit partials 3 x 8 B per cell /
+# 8 ppc = 3.
+BYTES_PER_PSTEP_MIXED_DEP = 44 + 40 + 3 + 3
 
 
 class MixedWorkload:
@@ -373,7 +374,7 @@ class MixedWorkload:
         self.part.set_fields(self.f)
         self.cell = torch.empty(self.N, dtype=torch.int32, device=dev)
         self.off = torch.empty((3, self.N), dtype=torch.float32, device=dev)
-        self.u = torch.empty((3, self.N), dtype=torch.float32, device=dev)
+        self.u = torch.empty((6, self.N), dtype=torch.float32, device=dev)  # (hi, lo) pair
         self.w = torch.empty(self.N, dtype=torch.float32, device=dev)
         self.ids = torch.empty(self.N, dtype=torch.int64, device=dev) if with_ids else None
         self.out = torch.empty((3, n ** 3), dtype=torch.float64, device=dev)
@@ -435,7 +436,7 @@ def mixed_error_vs_fp64(torch, P, n=128, ppc=8, steps=20, seed=1236):
     xd = d.x[:, idd]
     dd = (xm - xd) / dx
     dd = dd - n * torch.round(dd / n)
-    um = m.u[:, im].to(torch.float64)
+    um = m.u[:3, im].to(torch.float64) + m.u[3:, im].to(torch.float64)
     ud = d.u[:, idd]
     du = (um - ud).norm(dim=0) / ud.norm(dim=0)
     gm = torch.sqrt(1 + (um * um).sum(0))

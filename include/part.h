@@ -126,8 +126,11 @@ part_status part_set_fields(part_ctx* ctx, const void* fields, int ncomp, part_p
  *                       u = double[3][n], w = double[n] or NULL (w = 1)
  *   PART_MIXED / BORIS: x_or_cell = int32[n] linear cell (jz*ny+jy)*nx+jx,
  *                       off = float[3][n] offsets from the cell centre in
- *                       cell units, in [-1/2, 1/2]; u = float[3][n];
- *                       w = float[n] or NULL
+ *                       cell units, in [-1/2, 1/2]; u = float[6][n], the
+ *                       momentum as a compensated pair: rows 0-2 its f32
+ *                       value, rows 3-5 the f32 residual (u = hi + lo; start
+ *                       the residual at 0, or at u - hi when u is known more
+ *                       precisely); w = float[n] or NULL
  *   PART_LP_RK2       : x_or_cell = double[3][n], chi, eng = double[nb][n]
  *                       (bin-major), n_old = double[n] (density sampled at
  *                       the previous step); u, w = NULL
@@ -317,7 +320,7 @@ part_status part_selftest_wait(part_ctx* ctx, int64_t limit_ns, int arrive);
 typedef struct {
   int32_t* cell;       /* request state, device: int32 cell[stride]          */
   float* off;          /*   f32 off[3][stride] (cell units, [-1/2, 1/2))     */
-  float* u;            /*   f32 u[3][stride]                                 */
+  float* u;            /*   f32 u[6][stride]: hi rows 0-2, residual 3-5      */
   int64_t stride;      /* particles of the request (row stride of off, u)    */
   int64_t first;       /* first particle of this item                        */
   int32_t count;       /* particles in this item, >= 0                       */

@@ -189,7 +189,7 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   const size_t e = esize_of(prec);
   L.alt_x = take(alt ? (size_t)c1 * (prec == PART_FP64 ? 3 * 8 : 4) : 0);
   L.alt_off = take(alt && prec == PART_MIXED ? (size_t)c1 * 12 : 0);
-  L.alt_u = take(alt ? (size_t)c1 * 3 * e : 0);
+  L.alt_u = take(alt ? (size_t)c1 * (prec == PART_MIXED ? 6 : 3) * e : 0);
   L.alt_w = take(alt ? (size_t)c1 * e : 0);
   L.alt_id = take(alt ? (size_t)c1 * 8 : 0);
   // LP mode: shock cells and the list of LPs shocked by the last push

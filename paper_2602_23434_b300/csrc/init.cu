@@ -96,7 +96,10 @@ __global__ void k_init_boris_mixed(const Geo g, int64_t n, uint64_t seed, double
         dd = (float)((s - (double)j[a]) - 0.5);
       }
       off[a * n + p] = dd;
-      u[a * n + p] = (float)(u_th * d.g[a]);
+      const double ua = u_th * d.g[a];
+      const float hi = (float)ua;
+      u[a * n + p] = hi;                        // u = hi + lo, the compensated pair
+      u[(a + 3) * n + p] = (float)(ua - (double)hi);
     }
     cell[p] = (int32_t)(((int64_t)j[2] * g.n[1] + j[1]) * g.n[0] + j[0]);
     if (w) w[p] = 1.0f;

@@ -95,7 +95,7 @@ struct part_ctx {
   // and these buffers; part_flush / part_sync bring it home.
   void* alt_x{};      // FP64: double[3][cap]   mixed: int32 cell[cap]
   void* alt_off{};    // mixed: float[3][cap]
-  void* alt_u{};      // FP64: double[3][cap]   mixed: float[3][cap]
+  void* alt_u{};      // FP64: double[3][cap]   mixed: float[6][cap] (hi, lo)
   void* alt_w{};      // FP64: double[cap]      mixed: float[cap]
   uint64_t* alt_id{}; // uint64[cap]
   uint8_t* outmask{};             // caller's outflow flags (open axes), or NULL
@@ -304,6 +304,11 @@ cudaError_t launch_pad_fields(part_ctx* c, const void* src);
 cudaError_t launch_sort(part_ctx* c);
 cudaError_t flush_pending(part_ctx* c);  // current state into the bound arrays, in order
 cudaError_t apply_perm(part_ctx* c);     // a pending permutation into the other buffer
+
+// Rows of the momentum array: FP64 u[3][n]; mixed u[6][n], the f32 momentum
+// in rows 0-2 and its f32 residual in rows 3-5 (u = hi + lo, a compensated
+// pair, so the stored momentum is not rounded to f32 every step).
+inline int u_rows(const part_ctx* c) { return c->prec == PART_MIXED ? 6 : 3; }
 
 // Particle arrays of one buffer (the caller's or the alternate one).
 struct PState {

@@ -1,7 +1,8 @@
 // push_mixed.cu -- mixed-precision form of the gather + Boris push (+ deposit).
 //
 // State: int32 linear cell + f32 offset from the cell centre (cell units, in
-// [-1/2, 1/2)) + f32 u (+ optional f32 w).  Fields are staged as f32.  The
+// [-1/2, 1/2)) + the momentum as a compensated f32 pair u[6] = (hi[3], lo[3])
+// (+ optional f32 w).  Fields are staged as f32.  The
 // push runs in f32; the deposit reduces f32 contributions into compensated
 // (two-float) accumulators and leaves FP64 partials, so the grid sums carry
 // about 48 significant bits.
@@ -46,20 +47,40 @@ __host__ __device__ inline MixedSmem mixed_smem(const Geo& g) {
   return s;
 }
 
-// f32 relativistic Boris kick.  The rotation parameters are the quantities
-// whose rounding repeats identically every step (in a steady field), so they
-// are formed to about half an ulp with error-free transformations (TwoProd
-// by fma, exact residuals of 1 + q): 1/gamma- is refined from rsqrtf by one
-// Newton step evaluated in two-float, h = h_hi + h_lo is the two-float half
-// step, t = h B / gamma- and s = 2 t / (1 + |t|^2) are each kept as an f32
-// value plus its f32 residual.
+// Knuth's TwoSum: returns s = fl(a + b) and sets e so that s + e = a + b.
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+  return s;
+}
+
+// f32 relativistic Boris kick of the compensated momentum u + ul (ul the f32
+// residual of u).  The momentum is kept as that pair because rounding it to
+// f32 after every step is a random walk that the gyrophase budget (1e-5 rad
+// per 1000 steps) cannot absorb, least of all for particles gyrating on a
+// small circle: the step's increment u^{n+1} - u^n is added to the pair
+// exactly (TwoSum), so only the increment's own rounding (a fraction of the
+// rotation angle's worth) enters each step.
+// The rotation parameters are the quantities whose rounding repeats
+// identically every step (in a steady field), so they are formed to about
+// half an ulp with error-free transformations (TwoProd by fma, exact residuals
+// of 1 + q): 1/gamma- is refined from rsqrtf by one Newton step evaluated in
+// two-float, h = h_hi + h_lo is the two-float half step, t = h B / gamma- and
+// s = 2 t / (1 + |t|^2) are each kept as an f32 value plus its f32 residual.
+// The rotation, being linear in u-, is applied to u-'s value and, to first
+// order, to its residual.
 // du gets u^{n+1} - u^n from the rotation increment and the two half-kicks.
-__device__ __forceinline__ void boris_f32(float* u, const float* E, const float* B, float h,
-                                          float hl, float* du) {
+__device__ __forceinline__ void boris_f32(float* u, float* ul, const float* E, const float* B,
+                                          float h, float hl, float* du) {
   // half kick h E with the two-float h
   const float k0 = fmaf(h, E[0], hl * E[0]), k1 = fmaf(h, E[1], hl * E[1]);
   const float k2 = fmaf(h, E[2], hl * E[2]);
-  const float um0 = u[0] + k0, um1 = u[1] + k1, um2 = u[2] + k2;
+  // u- = u + h E as a pair (um, ml)
+  float e0, e1, e2;
+  const float um0 = two_sum(u[0], k0, e0), um1 = two_sum(u[1], k1, e1);
+  const float um2 = two_sum(u[2], k2, e2);
+  const float ml0 = ul[0] + e0, ml1 = ul[1] + e1, ml2 = ul[2] + e2;
   const float q = um0 * um0 + um1 * um1 + um2 * um2;
   const float a = 1.0f + q;
   const float res = q - (a - 1.0f);             // exact: a + res = 1 + q
@@ -97,12 +118,30 @@ __device__ __forceinline__ void boris_f32(float* u, const float* E, const float*
   const float r0 = (p1 * s2 - p2 * s1) + (p1 * sl2 - p2 * sl1);  // u+ - u-
   const float r1 = (p2 * s0 - p0 * s2) + (p2 * sl0 - p0 * sl2);
   const float r2 = (p0 * s1 - p1 * s0) + (p0 * sl1 - p1 * sl0);
-  du[0] = r0 + 2.0f * k0;
-  du[1] = r1 + 2.0f * k1;
-  du[2] = r2 + 2.0f * k2;
-  u[0] = (um0 + r0) + k0;
-  u[1] = (um1 + r1) + k1;
-  u[2] = (um2 + r2) + k2;
+  // the same rotation of u-'s residual, to first order
+  const float pl0 = ml0 + (ml1 * t2 - ml2 * t1);
+  const float pl1 = ml1 + (ml2 * t0 - ml0 * t2);
+  const float pl2 = ml2 + (ml0 * t1 - ml1 * t0);
+  const float rl0 = pl1 * s2 - pl2 * s1, rl1 = pl2 * s0 - pl0 * s2, rl2 = pl0 * s1 - pl1 * s0;
+  // increment D = r + rl + 2 h E, added to the pair exactly:
+  // (u + ul) + D = su + (ul + g + f + rl) with d + f = r + 2k, su + g = u + d
+  float f0, f1, f2, g0, g1, g2;
+  const float d0 = two_sum(r0, 2.0f * k0, f0), d1 = two_sum(r1, 2.0f * k1, f1);
+  const float d2 = two_sum(r2, 2.0f * k2, f2);
+  du[0] = d0;
+  du[1] = d1;
+  du[2] = d2;
+  const float su0 = two_sum(u[0], d0, g0), su1 = two_sum(u[1], d1, g1);
+  const float su2 = two_sum(u[2], d2, g2);
+  const float lo0 = ul[0] + (g0 + (f0 + rl0)), lo1 = ul[1] + (g1 + (f1 + rl1));
+  const float lo2 = ul[2] + (g2 + (f2 + rl2));
+  // renormalise (FastTwoSum: |su| >= |lo|)
+  u[0] = su0 + lo0;
+  u[1] = su1 + lo1;
+  u[2] = su2 + lo2;
+  ul[0] = lo0 - (u[0] - su0);
+  ul[1] = lo1 - (u[1] - su1);
+  ul[2] = lo2 - (u[2] - su2);
 }
 
 // Knuth's TwoSum into a (hi, lo) pair: hi + lo carries the sum with the
@@ -201,7 +240,7 @@ __global__ void __launch_bounds__(kT, 3)
   // state of each thread's first particle of a super-chunk, loaded before the
   // previous super-chunk's deposit so that phase A starts with it at hand
   int32_t nc = 0;
-  float no[3] = {0.f, 0.f, 0.f}, nu[3] = {0.f, 0.f, 0.f}, nw = 1.0f;
+  float no[3] = {0.f, 0.f, 0.f}, nu[3] = {0.f, 0.f, 0.f}, nl[3] = {0.f, 0.f, 0.f}, nw = 1.0f;
   uint32_t qc = 0, qn = 0;
   auto prefetch = [&](uint32_t sbx) {
     const uint32_t sex = p1 - sbx < (uint32_t)kM ? p1 : sbx + kM;
@@ -218,6 +257,7 @@ __global__ void __launch_bounds__(kT, 3)
       for (int a = 0; a < 3; ++a) {
         no[a] = offs[a * n + qc];
         nu[a] = us[a * n + qc];
+        nl[a] = us[(a + 3) * n + qc];
       }
       if (w) nw = w[qc];
     }
@@ -234,6 +274,7 @@ __global__ void __launch_bounds__(kT, 3)
       const int i = (int)(p - sb);
       const int32_t ccur = nc;
       float o[3] = {no[0], no[1], no[2]}, up[3] = {nu[0], nu[1], nu[2]};
+      float ul[3] = {nl[0], nl[1], nl[2]};
       const float wcur = nw;
       const uint32_t qcur = qc;
       if (p + kT < se) {
@@ -244,6 +285,7 @@ __global__ void __launch_bounds__(kT, 3)
         for (int a = 0; a < 3; ++a) {
           no[a] = offs[a * n + qc];
           nu[a] = us[a * n + qc];
+          nl[a] = us[(a + 3) * n + qc];
         }
         if (w) nw = w[qc];
       }
@@ -272,6 +314,7 @@ __global__ void __launch_bounds__(kT, 3)
         for (int a = 0; a < 3; ++a) {
           off[a * n + p] = o[a];
           u[a * n + p] = up[a];
+          u[(a + 3) * n + p] = ul[a];
         }
       } else {
         float wx[3], wy[3], wz[3] = {0.0f, 1.0f, 0.0f};
@@ -296,7 +339,7 @@ __global__ void __launch_bounds__(kT, 3)
         float du[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) d0[a] = o[a];
-        boris_f32(up, f, f + 3, h, hl, du);
+        boris_f32(up, ul, f, f + 3, h, hl, du);
         const float gi = rsqrtf(1.0f + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
         bool out = false;
 #pragma unroll
@@ -311,6 +354,7 @@ __global__ void __launch_bounds__(kT, 3)
         for (int a = 0; a < 3; ++a) {
           off[a * n + p] = o[a];
           u[a * n + p] = up[a];
+          u[(a + 3) * n + p] = ul[a];
         }
         if (DEP) {
           const float wdt = wcur * inv_dt;
@@ -401,7 +445,7 @@ __global__ void __launch_bounds__(kT, 3)
 // serving kernel so a particle gets the same bits whichever runs it.
 template <int SHAPE, int DIM>
 __device__ __forceinline__ void advance_mixed(const float* __restrict__ fp, const Geo& g, int* j,
-                                              float* o, float* up, float h, float hl,
+                                              float* o, float* up, float* ul, float h, float hl,
                                               const float* dtdx, int nsteps, bool& out) {
   for (int st = 0; st < nsteps && !out; ++st) {
     float wx[3], wy[3], wz[3] = {0.0f, 1.0f, 0.0f};
@@ -424,7 +468,7 @@ __device__ __forceinline__ void advance_mixed(const float* __restrict__ fp, cons
     }
     float f[6] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y};
     float du[3];
-    boris_f32(up, f, f + 3, h, hl, du);
+    boris_f32(up, ul, f, f + 3, h, hl, du);
     const float gi = rsqrtf(1.0f + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
@@ -448,14 +492,15 @@ __device__ __forceinline__ void particle_mixed(const float* __restrict__ fp, con
   }
   int j[3];
   cell_coords(g, c, j);
-  float o[3], up[3];
+  float o[3], up[3], ul[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     o[a] = off[a * stride + p];
     up[a] = u[a * stride + p];
+    ul[a] = u[(a + 3) * stride + p];
   }
   bool out = false;
-  advance_mixed<SHAPE, DIM>(fp, g, j, o, up, h, hl, dtdx, nsteps, out);
+  advance_mixed<SHAPE, DIM>(fp, g, j, o, up, ul, h, hl, dtdx, nsteps, out);
   if (outmask) outmask[p] = out ? 1 : 0;
   if (bad || !(isfinite(up[0]) && isfinite(up[1]) && isfinite(up[2]) && isfinite(o[0]) &&
                isfinite(o[1]) && isfinite(o[2])))
@@ -465,6 +510,7 @@ __device__ __forceinline__ void particle_mixed(const float* __restrict__ fp, con
   for (int a = 0; a < 3; ++a) {
     off[a * stride + p] = o[a];
     u[a * stride + p] = up[a];
+    u[(a + 3) * stride + p] = ul[a];
   }
 }
 

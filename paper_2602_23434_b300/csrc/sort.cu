@@ -280,7 +280,7 @@ __global__ void k_cell_start(const uint32_t* __restrict__ sk, int64_t n, int64_t
 // One pass over the permutation: every bound plane of particle perm[i] of one
 // copy of the state is written to slot i of the other copy.  NX planes of the
 // position-like array (3 doubles, or 1 int32 cell) by the template.
-template <typename TX, int NX, typename TV>
+template <typename TX, int NX, typename TV, int NU>
 __global__ void k_gather_state(const TX* __restrict__ x, const float* __restrict__ off,
                                const TV* __restrict__ u, const TV* __restrict__ w,
                                const uint64_t* __restrict__ id, TX* __restrict__ ax,
@@ -297,7 +297,7 @@ __global__ void k_gather_state(const TX* __restrict__ x, const float* __restrict
 #pragma unroll
       for (int a = 0; a < 3; ++a) aoff[a * n + i] = off[a * n + s];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) au[a * n + i] = u[a * n + s];
+    for (int a = 0; a < NU; ++a) au[a * n + i] = u[a * n + s];
     if (w) aw[i] = w[s];
     if (id) aid[i] = id[s];
   }
@@ -782,10 +782,10 @@ cudaError_t permute_all(part_ctx* c, const uint32_t* perm) {
       if (c->w && (e = permute_plane<double>(c, (double*)c->w, perm))) return e;
     } else if (c->mode == PART_BORIS) {
       if ((e = permute_plane<int32_t>(c, (int32_t*)c->x, perm))) return e;
-      for (int a = 0; a < 3; ++a) {
+      for (int a = 0; a < 3; ++a)
         if ((e = permute_plane<float>(c, (float*)c->off + a * n, perm))) return e;
+      for (int a = 0; a < 6; ++a)
         if ((e = permute_plane<float>(c, (float*)c->u + a * n, perm))) return e;
-      }
       if (c->w && (e = permute_plane<float>(c, (float*)c->w, perm))) return e;
     } else {
       for (int a = 0; a < 3; ++a)
@@ -814,11 +814,11 @@ cudaError_t apply_perm(part_ctx* c) {
   if (n == 0) return cudaSuccess;
   const PState a = state_of(c, c->cur_alt), b = state_of(c, !c->cur_alt);
   if (c->prec == PART_FP64)
-    k_gather_state<double, 3, double><<<grid_for(c, n, 256), 256, 0, c->stream>>>(
+    k_gather_state<double, 3, double, 3><<<grid_for(c, n, 256), 256, 0, c->stream>>>(
         (const double*)a.x, nullptr, (const double*)a.u, (const double*)a.w, a.id,
         (double*)b.x, nullptr, (double*)b.u, (double*)b.w, b.id, perm, n);
   else
-    k_gather_state<int32_t, 1, float><<<grid_for(c, n, 256), 256, 0, c->stream>>>(
+    k_gather_state<int32_t, 1, float, 6><<<grid_for(c, n, 256), 256, 0, c->stream>>>(
         (const int32_t*)a.x, (const float*)a.off, (const float*)a.u, (const float*)a.w, a.id,
         (int32_t*)b.x, (float*)b.off, (float*)b.u, (float*)b.w, b.id, perm, n);
   c->launches++;
@@ -841,7 +841,8 @@ cudaError_t flush_pending(part_ctx* c) {
   if (r == cudaSuccess && c->off)
     r = cudaMemcpyAsync(c->off, c->alt_off, 12 * n, cudaMemcpyDeviceToDevice, c->stream);
   if (r == cudaSuccess)
-    r = cudaMemcpyAsync(c->u, c->alt_u, 3 * e * n, cudaMemcpyDeviceToDevice, c->stream);
+    r = cudaMemcpyAsync(c->u, c->alt_u, u_rows(c) * e * n, cudaMemcpyDeviceToDevice,
+                        c->stream);
   if (r == cudaSuccess && c->w)
     r = cudaMemcpyAsync(c->w, c->alt_w, e * n, cudaMemcpyDeviceToDevice, c->stream);
   if (r == cudaSuccess && c->id)
@@ -930,7 +931,7 @@ cudaError_t launch_inject(part_ctx* c, int64_t k, const InjectSrc& s) {
   } else if (c->mode == PART_BORIS) {
     e = grow_rows<int32_t>(c, (int32_t*)c->x, 1, n, k, (const int32_t*)s.x);
     if (e == cudaSuccess) e = grow_rows<float>(c, (float*)c->off, 3, n, k, (const float*)s.off);
-    if (e == cudaSuccess) e = grow_rows<float>(c, (float*)c->u, 3, n, k, (const float*)s.u);
+    if (e == cudaSuccess) e = grow_rows<float>(c, (float*)c->u, 6, n, k, (const float*)s.u);
     if (e == cudaSuccess && c->w)
       e = grow_rows<float>(c, (float*)c->w, 1, n, k, (const float*)s.w);
   } else {
@@ -974,7 +975,7 @@ cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew_out) {
   } else if (c->mode == PART_BORIS) {
     if ((e = fill_rows<int32_t>(c, (int32_t*)c->x, 1, del, n, nnew, gb))) return e;
     if ((e = fill_rows<float>(c, (float*)c->off, 3, del, n, nnew, gb))) return e;
-    if ((e = fill_rows<float>(c, (float*)c->u, 3, del, n, nnew, gb))) return e;
+    if ((e = fill_rows<float>(c, (float*)c->u, 6, del, n, nnew, gb))) return e;
     if (c->w && (e = fill_rows<float>(c, (float*)c->w, 1, del, n, nnew, gb))) return e;
   } else {
     if ((e = fill_rows<double>(c, (double*)c->x, 3, del, n, nnew, gb))) return e;

@@ -25,7 +25,8 @@ import numpy as np
 
 from . import _lib as P
 
-STATE_BYTES_PER_PARTICLE = 4 + 12 + 12     # int32 cell, f32 off[3], f32 u[3]
+# int32 cell, f32 off[3], f32 u[6] (the momentum as a compensated pair)
+STATE_BYTES_PER_PARTICLE = 4 + 12 + 24
 
 
 @dataclass
@@ -171,7 +172,7 @@ class Server:
             with torch.cuda.stream(self.stream):   # allocations belong to the serving stream
                 r.cell = torch.empty(r.n, dtype=torch.int32, device=dev)
                 r.off = torch.empty((3, r.n), dtype=torch.float32, device=dev)
-                r.u = torch.empty((3, r.n), dtype=torch.float32, device=dev)
+                r.u = torch.empty((6, r.n), dtype=torch.float32, device=dev)
             sp = self.snaps[r.snapshot].part
             sp.bind(r.n, r.cell, off=r.off, u=r.u)
             sp.init_particles(r.seed, r.u_th)

@@ -97,7 +97,9 @@ def test_compact_mixed_boris(which):
     rng = np.random.default_rng(8)
     cell = rng.integers(0, n ** 3, N).astype(np.int32)
     off = rng.uniform(-0.5, 0.5, (3, N)).astype(np.float32)
-    u = rng.normal(0, 0.3, (3, N)).astype(np.float32)
+    # the momentum is a compensated pair [6][N]: f32 value and residual
+    u = rng.normal(0, 0.3, (6, N)).astype(np.float32)
+    u[3:] *= 1e-8
     w = rng.uniform(0.5, 2.0, N).astype(np.float32)
     ids = np.arange(N, dtype=np.int64) * 3 + 1
     d = _masks(N, 9)[which]
@@ -110,7 +112,7 @@ def test_compact_mixed_boris(which):
     assert nn == nk
     assert np.array_equal(_host(cd)[:nk], cell[src])
     assert np.array_equal(_rows(od, 3, nk), off[:, src])
-    assert np.array_equal(_rows(ud, 3, nk), u[:, src])
+    assert np.array_equal(_rows(ud, 6, nk), u[:, src])
     assert np.array_equal(_host(wd)[:nk], w[src])
     assert np.array_equal(_host(idd)[:nk], ids[src])
 
@@ -180,7 +182,9 @@ def test_inject_then_sort_then_compact(mode):
         off_all = ((x_all + 1.0) / dx - j - 0.5).astype(np.float32)
         cell_all = ((j[2] * n + j[1]) * n + j[0]).astype(np.int32)
         planes = {"x": (cell_all, 1, torch.int32), "off": (off_all, 3, torch.float32),
-                  "u": (u_all.astype(np.float32), 3, torch.float32),
+                  "u": (np.concatenate([u_all.astype(np.float32),
+                                        (u_all - u_all.astype(np.float32)).astype(np.float32)]),
+                        6, torch.float32),
                   "w": (w_all.astype(np.float32), 1, torch.float32),
                   "ids": (ids_all, 1, torch.int64)}
         p = P.Part(P.make_grid(3, n), P.MIXED, P.TSC, P.BORIS, capacity=C)

@@ -41,6 +41,11 @@ def _host(t):
     return t.detach().cpu().numpy()
 
 
+def _pair(u6):
+    """The mixed form's compensated momentum [6][N] as f64 values hi + lo."""
+    return u6[:3].astype(np.float64) + u6[3:].astype(np.float64)
+
+
 def _pdiff(a, b, L=2.0):
     d = a - b
     return d - L * np.round(d / L)
@@ -204,7 +209,7 @@ def test_fullsize_mixed_256():
     p.set_fields(torch.as_tensor(f).cuda())
     cell = torch.empty(N, dtype=torch.int32, device="cuda")
     off = torch.empty((3, N), dtype=torch.float32, device="cuda")
-    u = torch.empty((3, N), dtype=torch.float32, device="cuda")
+    u = torch.empty((6, N), dtype=torch.float32, device="cuda")   # compensated pair
     w = torch.empty(N, dtype=torch.float32, device="cuda")
     ids = torch.empty(N, dtype=torch.int64, device="cuda")
     out = torch.empty((3, n ** 3), dtype=torch.float64, device="cuda")
@@ -234,7 +239,7 @@ def test_fullsize_mixed_256():
     def init_state(o):
         ot = torch.as_tensor(o).cuda()
         return (_mixed_to_x(_host(cell0_d[ot]), _host(off0_d[:, ot]), n),
-                _host(u0_d[:, ot]).astype(np.float64), _host(w0_d[ot]).astype(np.float64))
+                _pair(_host(u0_d[:, ot])), _host(w0_d[ot]).astype(np.float64))
 
     # sampled particles against FP64 oracle steps from the same state
     s = np.random.default_rng(3).choice(N, 8192, replace=False)
@@ -244,7 +249,7 @@ def test_fullsize_mixed_256():
     xg = _mixed_to_x(_host(cell[st]), _host(off[:, st]), n)
     d = _pdiff(xg, xr) / (2.0 / n)
     assert np.max(np.abs(d)) <= 1e-6
-    assert np.max(np.abs(_host(u[:, st]) - ur)) <= 2e-6 * np.max(np.abs(ur))
+    assert np.max(np.abs(_pair(_host(u[:, st])) - ur)) <= 2e-6 * np.max(np.abs(ur))
     # deposit at sampled cells
     cells = _sample_cells(n, p.brick, 24, 4)
     con = _contributors(cells, n, lambda c: int(ktab[c]), cs, ia)
@@ -446,19 +451,19 @@ def test_fullsize_serving_request_256():
     p.set_fields(snap.fields)
     cell = torch.empty(N, dtype=torch.int32, device="cuda")
     off = torch.empty((3, N), dtype=torch.float32, device="cuda")
-    u = torch.empty((3, N), dtype=torch.float32, device="cuda")
+    u = torch.empty((6, N), dtype=torch.float32, device="cuda")
     p.bind(N, cell, off=off, u=u)
     p.init_particles(seed, 0.1)
     p.sort()
     p.sync()
     s = torch.as_tensor(np.random.default_rng(8).choice(N, 2048, replace=False)).cuda()
     xr = _mixed_to_x(_host(cell[s]), _host(off[:, s]), n)
-    ur = _host(u[:, s]).astype(np.float64)
+    ur = _pair(_host(u[:, s]))
     f64 = _host(snap.fields).astype(np.float64)
     for _ in range(steps):
         xr, ur, _, _ = O.boris_step(og, P.TSC, f64, xr, ur, None, 1.0, dt)
     xg = _mixed_to_x(_host(cg[s]), _host(og_[:, s]), n)
     assert np.max(np.abs(_pdiff(xg, xr) / (2.0 / n))) <= 1e-6 * steps
-    assert np.max(np.abs(_host(ug[:, s]) - ur)) <= 1e-6 * steps * np.max(np.abs(ur))
+    assert np.max(np.abs(_pair(_host(ug[:, s])) - ur)) <= 1e-6 * steps * np.max(np.abs(ur))
     del p, cell, off, u, snap, cg, og_, ug
     torch.cuda.empty_cache()

@@ -161,7 +161,7 @@ def test_open_mixed_step_and_outflow():
     off = ((x + 1.0) / dx - j - 0.5).astype(np.float32)
     x = -1.0 + (j + 0.5 + off.astype(np.float64)) * dx        # exactly representable
     cell = ((j[2] * n + j[1]) * n + j[0]).astype(np.int32)
-    uf = u.astype(np.float32)
+    uf = np.concatenate([u.astype(np.float32), np.zeros((3, N), dtype=np.float32)])  # hi, lo
     f = synth.em_fields(dim, n, 29, v_rms=0.05).reshape(6, -1)
     p = P.Part(pg, P.MIXED, P.TSC, P.BORIS, capacity=N)
     p.set_fields(torch.as_tensor(f.astype(np.float32)).cuda())
@@ -178,7 +178,8 @@ def test_open_mixed_step_and_outflow():
     p.gather_push(1.0, dt, 1)
     p.sync()
     xr, ur, _, _ = O.boris_step(og, P.TSC, f.astype(np.float32).astype(np.float64), x0,
-                                u0.astype(np.float64), None, 1.0, dt)
+                                u0[:3].astype(np.float64) + u0[3:].astype(np.float64), None,
+                                1.0, dt)
     flags = O.outside(og, xr)
     got = _host(out)
     near = np.abs(np.minimum(np.abs(xr[0] - 1.0), np.abs(xr[0] + 1.0))) < 1e-5 * dx

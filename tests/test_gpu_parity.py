@@ -326,7 +326,7 @@ def test_init_particles_fp64_and_mixed():
     pm = P.Part(pg, P.MIXED, P.TSC, P.BORIS, capacity=N)
     cell = torch.zeros(N, dtype=torch.int32, device="cuda")
     off = torch.zeros((3, N), dtype=torch.float32, device="cuda")
-    uf = torch.zeros((3, N), dtype=torch.float32, device="cuda")
+    uf = torch.zeros((6, N), dtype=torch.float32, device="cuda")   # compensated pair
     pm.bind(N, cell, off=off, u=uf)
     pm.init_particles(1235, 0.1)
     pm.sync()
@@ -335,7 +335,10 @@ def test_init_particles_fp64_and_mixed():
     pos = -1.0 + (j + 0.5 + _host(off)) * (2.0 / 24)
     assert np.max(np.abs(pos - xo)) <= 2.0 / 24 * 6e-8
     assert np.all(np.abs(_host(off)) <= 0.5)
-    assert _rel(_host(uf).astype(np.float64), uo, 0.1) <= 1e-6
+    assert _rel(_host(uf)[:3].astype(np.float64), uo, 0.1) <= 1e-6
+    # the pair carries the draw beyond f32: hi + lo is u to ~2^-48 relative
+    u_pair = _host(uf)[:3].astype(np.float64) + _host(uf)[3:].astype(np.float64)
+    assert _rel(u_pair, uo, 0.1) <= 1e-13
 
 
 def test_bounded_wait_times_out_and_the_context_survives():

@@ -58,7 +58,7 @@ def test_request_alone_equals_mixed_and_fused_push(snaps):
     p.set_fields(snaps[1].fields)
     cell = torch.empty(5000, dtype=torch.int32, device="cuda")
     off = torch.empty((3, 5000), dtype=torch.float32, device="cuda")
-    u = torch.empty((3, 5000), dtype=torch.float32, device="cuda")
+    u = torch.empty((6, 5000), dtype=torch.float32, device="cuda")   # compensated pair
     p.bind(5000, cell, off=off, u=u)
     p.init_particles(11, 0.1)
     p.sort()
