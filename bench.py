@@ -14,7 +14,8 @@ roofline of the dominant kernel, end-to-end throughput through host buffers,
 and the oracle timed on the host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun each rank runs its own replica (no data-path collective).
+Under torchrun each rank advances its own particles against the replicated
+fields, and the ranks' deposits are summed every step (weak scaling).
 """
 from __future__ import annotations
 
@@ -678,7 +679,10 @@ def headline_config(grid: int, particles: int, dt: float, world: int) -> dict:
             "particles": particles, "grid": [grid] * 3, "dt": dt,
             "l2": "inputs larger than L2 (about 2 GB of state, fields and deposit "
                   "touched per step vs 126 MB L2); no flush",
-            "parallelism": f"replicas x{world}"}
+            "parallelism": ("one GPU" if world == 1 else
+                            f"{world} ranks: particles partitioned (each rank its own "
+                            f"16,777,216), fields replicated, deposit summed across ranks "
+                            f"every step in rank order")}
 
 
 def _oracle_boris_stepper(n: int, seed: int, deposit: bool = True):
@@ -953,9 +957,21 @@ def main():
     wl = BorisWorkload(torch, P, n=args.grid, seed=1236, pseed=R.rank_seed(1236, rank))
     stream = wl.part.stream
     l0 = wl.part.launches()
+    step = wl.step
+    if world > 1:
+        # particles partitioned over the ranks (each its own set), fields
+        # replicated: every step the ranks' deposits are summed in rank order
+        # (all-to-all of slices, part_sum_ordered, all-gather) so every rank
+        # holds the whole deposit, the same bits on every rank
+        from paper_2602_23434_b300 import multirank as M
+        ops = M.LibOps(wl.part, wl.N)
+
+        def step(ev=None):
+            wl.step(ev)
+            wl.out.view(-1).copy_(M.combine_replicated(ops, dist, wl.out.view(-1)))
     # warm-up
     for _ in range(args.warmup):
-        wl.step()
+        step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -963,7 +979,7 @@ def main():
     clk.start()
     time.sleep(0.3)
     l1 = wl.part.launches()
-    total_ms, kern_ms = time_steps(torch, stream, wl.step, args.steps, 0, per_step_events=True)
+    total_ms, kern_ms = time_steps(torch, stream, step, args.steps, 0, per_step_events=True)
     launches = wl.part.launches() - l1
     clocks = clk.stop()
     wl.part.sync()

@@ -365,6 +365,76 @@ part_status part_server_run(part_server* s, int nitems);
 part_status part_server_sync(part_server* s);
 part_status part_server_destroy(part_server* s);
 
+/* ---- Several ranks (Sec. 3.3, "Multi-core communication") ----------------
+ * A run split over ranks gives each rank a context whose grid is its box of
+ * cells plus, along every split axis, one halo cell on each side holding the
+ * neighbour's fields (those axes are open in the context's grid, so nothing
+ * wraps there).  Particles live in the interior; after a push, the ones in a
+ * halo cell belong to a neighbour.  Per split axis, in turn (the paper's
+ * three directions), the caller:
+ *   1. part_exchange_pack: flags and counts the leaving particles and packs
+ *      them into one buffer per neighbour (the paper's steps 1, 3, 4);
+ *   2. exchanges the counts, then the buffers, with both neighbours
+ *      (non-blocking sends and receives, steps 2, 5, 7);
+ *   3. part_compact with the flags, then part_exchange_unpack of what came
+ *      from the left and from the right (steps 6, 8).
+ * Positions are moved into the receiver's frame while packing: FP64 and LP
+ * positions are global coordinates and only change across the periodic seam
+ * of the whole domain (x_axis += dx, the same rounding as the wrap of a
+ * one-rank run); the mixed form's cell index is local and is re-based
+ * (j_axis += dj) and re-linearised with the receiver's n_axis.             */
+typedef struct {
+  double dx;       /* added to the position along the axis (FP64, LP)       */
+  int32_t dj;      /* added to the cell index along the axis (mixed)        */
+  int32_t n_axis;  /* receiver's cells along the axis (mixed; >= 1)         */
+} part_xshift;
+
+/* Bytes of a packed exchange buffer holding k particles of this context
+ * (every bound plane at row stride k, 8-byte planes first).                */
+part_status part_exchange_bytes(const part_ctx* ctx, int64_t k, size_t* bytes);
+
+/* Classify the bound particles along axis (0 <= axis < dim) against the
+ * interior cell range [lo, hi) of the context's grid (FP64 and LP: s = (x -
+ * xmin)/dx with the library's roundings, left if s < lo, right if s >= hi;
+ * mixed: the cell index), write leaving[n] (device uint8, 1 = leaves), and
+ * set counts[0] (left) and counts[1] (right).  If send_left / send_right hold
+ * part_exchange_bytes(count) bytes (device, 8-byte aligned; NULL allowed for
+ * a count of 0), pack the leaving particles into them in index order, moved
+ * into the receiver's frame by to_left / to_right; otherwise return
+ * PART_ENOMEM with the counts set and nothing packed, so the caller can
+ * resize and call again.  Brings the current state home first (part_flush)
+ * and synchronises the stream once, to read the counts.  PART_EINVAL on bad
+ * arguments.                                                                */
+part_status part_exchange_pack(part_ctx* ctx, int axis, int lo, int hi,
+                               const part_xshift* to_left, const part_xshift* to_right,
+                               void* send_left, size_t left_bytes, void* send_right,
+                               size_t right_bytes, uint8_t* leaving, int64_t counts[2]);
+
+/* Append k particles from a buffer packed by part_exchange_pack on a rank
+ * with the same bound planes (recv: device, 8-byte aligned, at least
+ * part_exchange_bytes(k) bytes); as part_inject, and LP shock flags are
+ * carried along.  PART_EINVAL if n + k exceeds the capacity.               */
+part_status part_exchange_unpack(part_ctx* ctx, int64_t k, const void* recv, size_t recv_bytes);
+
+/* Deposit halos.  part_box_pack copies the box [lo, lo + ext) of a device
+ * array double[ncomp][dims[2]][dims[1]][dims[0]] into dst, packed
+ * [ncomp][ext[2]][ext[1]][ext[0]]; part_box_add adds such a packed src into
+ * the box of dst (one rounded add per element).  Asynchronous on
+ * cuda_stream (NULL = legacy default stream).  PART_EINVAL if the box leaves
+ * the array, a pointer is NULL, unaligned or unreachable.                   */
+part_status part_box_pack(const double* src, int ncomp, const int dims[3], const int lo[3],
+                          const int ext[3], double* dst, void* cuda_stream);
+part_status part_box_add(double* dst, int ncomp, const int dims[3], const int lo[3],
+                         const int ext[3], const double* src, void* cuda_stream);
+
+/* Replicated grids (particles partitioned over ranks, fields replicated):
+ * out[i] = (((parts[0][i] + parts[1][i]) + parts[2][i]) + ...), parts laid
+ * out [nparts][count], summed in that order, so every rank that holds the
+ * same parts gets the same bits.  out may alias parts' first row.
+ * Asynchronous on cuda_stream.  PART_EINVAL on bad arguments.              */
+part_status part_sum_ordered(double* out, const double* parts, int64_t count, int nparts,
+                             void* cuda_stream);
+
 /* ---- Measurement -----------------------------------------------------------
  * FP64 fused multiply-add rate of the current device, measured: the
  * denominator of the arithmetic roofline of this library's FP64 kernels (on

@@ -37,9 +37,11 @@ class Grid(C.Structure):
 
 
 def make_grid(dim: int, n, xmin=(-1.0, -1.0, -1.0), L=(2.0, 2.0, 2.0),
-              open_axes=(0, 0, 0)) -> Grid:
+              open_axes=(0, 0, 0), dx=None) -> Grid:
     """Grid of n cells per axis on [xmin, xmin + L); dim 2 -> n[2] = 1;
-    periodic, except the axes with open_axes[a] = 1 (outflow)."""
+    periodic, except the axes with open_axes[a] = 1 (outflow).  dx, if
+    given, sets the cell widths directly (a subdomain's grid keeps the whole
+    domain's dx bit for bit)."""
     if isinstance(n, int):
         n = (n, n, n if dim == 3 else 1)
     n = list(n) + [1] * (3 - len(n))
@@ -50,7 +52,10 @@ def make_grid(dim: int, n, xmin=(-1.0, -1.0, -1.0), L=(2.0, 2.0, 2.0),
     for a in range(3):
         g.n[a] = int(n[a])
         g.xmin[a] = float(xmin[a])
-        g.dx[a] = float(L[a]) / n[a] if (a < dim) else float(L[a])
+        if dx is not None:
+            g.dx[a] = float(dx[a])
+        else:
+            g.dx[a] = float(L[a]) / n[a] if (a < dim) else float(L[a])
         g.periodic[a] = 0 if open_axes[a] else 1
     return g
 
@@ -61,6 +66,11 @@ class WorkItem(C.Structure):
                 ("stride", C.c_int64), ("first", C.c_int64), ("count", C.c_int32),
                 ("nsteps", C.c_int32), ("snapshot", C.c_int32), ("reserved", C.c_int32),
                 ("q_over_m", C.c_double), ("dt", C.c_double)]
+
+
+class XShift(C.Structure):
+    """part_xshift: a packed particle's move into the receiver's frame."""
+    _fields_ = [("dx", C.c_double), ("dj", C.c_int32), ("n_axis", C.c_int32)]
 
 
 if C.sizeof(WorkItem) != 72:
@@ -111,6 +121,16 @@ def lib():
         "part_sort_fp64_noalloc": (st, [G, C.c_int64, P, P, P, P, P, P]),
         "part_probe_fp64_fma": (st, [P, P, C.c_int, C.c_int, C.c_int,
                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "part_exchange_bytes": (st, [P, C.c_int64, C.POINTER(C.c_size_t)]),
+        "part_exchange_pack": (st, [P, C.c_int, C.c_int, C.c_int, C.POINTER(XShift),
+                                    C.POINTER(XShift), P, C.c_size_t, P, C.c_size_t, P,
+                                    C.POINTER(C.c_int64)]),
+        "part_exchange_unpack": (st, [P, C.c_int64, P, C.c_size_t]),
+        "part_box_pack": (st, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                               C.POINTER(C.c_int), P, P]),
+        "part_box_add": (st, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                              C.POINTER(C.c_int), P, P]),
+        "part_sum_ordered": (st, [P, P, C.c_int64, C.c_int, P]),
         "part_server_sizes": (st, [C.c_int, C.c_int, C.POINTER(C.c_size_t),
                                    C.POINTER(C.c_size_t)]),
         "part_server_init": (st, [C.POINTER(P), C.POINTER(P), C.c_int, C.c_int, P, C.c_size_t,
@@ -281,6 +301,34 @@ class Part:
     def sync(self):
         self._check(self.L.part_sync(self.ctx))
 
+    def exchange_bytes(self, k: int) -> int:
+        """Bytes of a packed exchange buffer for k particles (part_exchange_bytes)."""
+        b = C.c_size_t()
+        self._check(self.L.part_exchange_bytes(self.ctx, int(k), C.byref(b)))
+        return b.value
+
+    def exchange_pack(self, axis: int, lo: int, hi: int, to_left, to_right, send_left,
+                      send_right, leaving):
+        """part_exchange_pack; to_left / to_right are (dx, dj, n_axis).  Returns
+        (count_left, count_right, packed): packed is False when a buffer was too
+        small (nothing packed; resize to exchange_bytes(count) and call again)."""
+        cnt = (C.c_int64 * 2)()
+        sl, sr = XShift(*to_left), XShift(*to_right)
+        nl = send_left.numel() if send_left is not None else 0
+        nr = send_right.numel() if send_right is not None else 0
+        code = self.L.part_exchange_pack(self.ctx, int(axis), int(lo), int(hi), C.byref(sl),
+                                         C.byref(sr), _ptr(send_left), nl, _ptr(send_right), nr,
+                                         _ptr(leaving), cnt)
+        if code == 2:   # PART_ENOMEM: counts set, buffers too small
+            return int(cnt[0]), int(cnt[1]), False
+        self._check(code)
+        return int(cnt[0]), int(cnt[1]), True
+
+    def exchange_unpack(self, k: int, recv):
+        """part_exchange_unpack: append k particles from a packed buffer."""
+        self._check(self.L.part_exchange_unpack(self.ctx, int(k), _ptr(recv),
+                                                recv.numel() if recv is not None else 0))
+
     def launches(self) -> int:
         return int(self.L.part_launch_count(self.ctx))
 
@@ -302,3 +350,33 @@ def probe_fp64_fma(stream_ptr: int, sink, ctas_per_sm: int = 4, iters: int = 819
     if code != 0:
         raise PartError(code, L.part_last_error(None).decode())
     return tf.value, ms.value
+
+
+def _raise(code: int):
+    if code != 0:
+        msg = lib().part_last_error(None)
+        raise PartError(code, msg.decode() if msg else "")
+
+
+def _i3(v):
+    return (C.c_int * 3)(*[int(a) for a in v])
+
+
+def box_pack(src, ncomp: int, dims, lo, ext, dst, stream_ptr: int = 0):
+    """part_box_pack: dst (packed [ncomp][ext z][ext y][ext x]) <- the box of
+    src ([ncomp][dims z][dims y][dims x]); device float64 tensors."""
+    _raise(lib().part_box_pack(_ptr(src), int(ncomp), _i3(dims), _i3(lo), _i3(ext), _ptr(dst),
+                               C.c_void_p(stream_ptr or None)))
+
+
+def box_add(dst, ncomp: int, dims, lo, ext, src, stream_ptr: int = 0):
+    """part_box_add: the box of dst += src (packed)."""
+    _raise(lib().part_box_add(_ptr(dst), int(ncomp), _i3(dims), _i3(lo), _i3(ext), _ptr(src),
+                              C.c_void_p(stream_ptr or None)))
+
+
+def sum_ordered(out, parts, stream_ptr: int = 0):
+    """part_sum_ordered: out[i] = parts[0][i] + parts[1][i] + ... in row order;
+    parts a contiguous device float64 tensor [nparts][count]."""
+    _raise(lib().part_sum_ordered(_ptr(out), _ptr(parts), int(parts.shape[1]),
+                                  int(parts.shape[0]), C.c_void_p(stream_ptr or None)))

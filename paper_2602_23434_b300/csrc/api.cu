@@ -42,11 +42,11 @@ bool device_accessible(int device, const void* p) {
   return false;
 }
 
-namespace {
-
 part_status cuda_fail(part_ctx* c, cudaError_t e, const char* where) {
   return fail(c, PART_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
+
+namespace {
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
@@ -60,12 +60,16 @@ bool misaligned(const void* p, size_t elem) {
 size_t pos_elem(const part_ctx* c) { return c->prec == PART_MIXED ? 4 : 8; }
 size_t real_elem(const part_ctx* c) { return c->prec == PART_MIXED ? 4 : 8; }
 
+}  // namespace
+
 part_status check_access(part_ctx* c, const void* p, const char* what) {
   if (device_accessible(c->device, p)) return PART_OK;
   return fail(c, PART_EINVAL,
               std::string(what) + " is not memory the kernels can reach (device memory of the "
                                   "context's device, managed memory or pinned host memory)");
 }
+
+namespace {
 
 part_status check_planes(part_ctx* c, const void* x, const void* off, const void* u,
                          const void* w, const void* id, const void* chi, const void* eng,
@@ -172,7 +176,7 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   const int64_t nblk = (hlen + kScanBlock - 1) / kScanBlock;
   L.fpad = take((size_t)fcomp_of(prec, mode) * g.pplane * esize_of(prec));
   L.keys0 = take((size_t)(c1 + 1) * 4);  // +1: compaction scans n + 1 flags
-  L.keys1 = take((size_t)c1 * 4);
+  L.keys1 = take((size_t)(c1 + 1) * 4);  // +1: the exchange scans n + 1 flags per side
   L.vals0 = take((size_t)c1 * 4);
   L.vals1 = take((size_t)c1 * 4);
   L.hist = take((size_t)hlen * 4);
@@ -263,12 +267,12 @@ part_status encode_tmap(part_ctx* c) {
   return PART_OK;
 }
 
+}  // namespace
+
 part_status check_ctx(part_ctx* c) {
   if (!c) return fail(nullptr, PART_EINVAL, "ctx is NULL");
   return PART_OK;
 }
-
-}  // namespace
 
 extern "C" {
 

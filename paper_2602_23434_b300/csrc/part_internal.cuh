@@ -324,6 +324,10 @@ inline PState state_of(const part_ctx* c, bool alt) {
           c->id ? c->alt_id : nullptr};
 }
 cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew);
+cudaError_t launch_exclusive_scan(part_ctx* c, uint32_t* a, int64_t m, uint32_t* sums);
+part_status check_ctx(part_ctx* c);                                    // api.cu
+part_status cuda_fail(part_ctx* c, cudaError_t e, const char* where);  // api.cu
+part_status check_access(part_ctx* c, const void* p, const char* what);  // api.cu
 struct InjectSrc {
   const void *x, *off, *u, *w;
   const uint64_t* id;

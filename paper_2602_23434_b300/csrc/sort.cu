@@ -945,6 +945,18 @@ cudaError_t launch_inject(part_ctx* c, int64_t k, const InjectSrc& s) {
   return e;
 }
 
+// In-place exclusive scan of m 32-bit counts (m <= capacity + 1); sums needs
+// (m + kScanBlock - 1) / kScanBlock + 1 entries.  a[m - 1] ends as the total
+// of the first m - 1 counts when the last count is 0.
+cudaError_t launch_exclusive_scan(part_ctx* c, uint32_t* a, int64_t m, uint32_t* sums) {
+  const int64_t nblk = (m + kScanBlock - 1) / kScanBlock;
+  k_scan_reduce<<<(unsigned)nblk, 256, 0, c->stream>>>(a, m, sums);
+  k_scan_top<<<1, 256, 0, c->stream>>>(sums, nblk);
+  k_scan_down<<<(unsigned)nblk, 256, 0, c->stream>>>(a, m, sums);
+  c->launches += 3;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew_out) {
   const int64_t n = c->n;
   cudaStream_t s = c->stream;
