@@ -184,6 +184,18 @@ __device__ __forceinline__ void move_axis(float& off, int& j, float dv, int n, i
   j = jj;
 }
 
+// First index i in [lo, hi] with s[i] > v (s nondecreasing), hi if none.
+__device__ __forceinline__ int first_above(const uint32_t* s, int lo, int hi, uint32_t v) {
+  while (lo < hi) {
+    const int m = (lo + hi) >> 1;
+    if (s[m] > v)
+      hi = m;
+    else
+      lo = m + 1;
+  }
+  return lo;
+}
+
 template <int SHAPE, int DIM, bool DEP>
 __global__ void __launch_bounds__(kT, 3)
     k_boris_brick_mixed(const __grid_constant__ CUtensorMap tmap, const Geo g,
@@ -376,9 +388,10 @@ __global__ void __launch_bounds__(kT, 3)
     // ---- B: one thread per (source cell, component) of this super-chunk
     // sums its particles' 27 contributions, then 27 (3^dim) ordered passes
     const int hz = DIM == 3 ? 1 : 0;
-    while (scs[cfirst + 1] <= sb) ++cfirst;
-    int clast = cfirst;
-    while (clast + 1 < g.V && scs[clast + 1] < se) ++clast;
+    // cells of this super-chunk: cfirst holds slot sb, clast is the last cell
+    // with a slot below se (binary searches of the brick's cell_start)
+    cfirst = first_above(scs, 1, g.V, sb) - 1;
+    const int clast = first_above(scs, 0, g.V, se - 1) - 1;
     constexpr int CB = kT / 3;  // cells per batch
     const int comp = tid % 3;
     for (int c0 = cfirst; c0 <= clast; c0 += CB) {
@@ -389,9 +402,9 @@ __global__ void __launch_bounds__(kT, 3)
       bool any = false;
       int lx = 0, ly = 0, lz = 0;
       if (tid < 3 * CB && ls <= clast) {
-        lx = ls % g.b[0];
-        ly = (ls / g.b[0]) % g.b[1];
-        lz = ls / (g.b[0] * g.b[1]);
+        lx = ls & (g.b[0] - 1);   // brick sides are powers of two
+        ly = (ls >> g.bshift[0]) & (g.b[1] - 1);
+        lz = ls >> (g.bshift[0] + g.bshift[1]);
         uint32_t r0 = scs[ls], r1 = scs[ls + 1];
         r0 = r0 > sb ? r0 : sb;
         r1 = r1 < se ? r1 : se;
