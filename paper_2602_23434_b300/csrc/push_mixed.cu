@@ -18,8 +18,9 @@
 //      contributions in registers, then 27 passes (one per stencil offset,
 //      separated by barriers) add them into the haloed tile's two-float
 //      accumulators: in a pass no two threads share a target, and the order
-//      is fixed.  Super-chunks of 512 particles keep shared memory at ~71 KB
-//      and the registers under 85, so three CTAs share an SM.
+//      is fixed.  Super-chunks of 640 particles (about 80 cells, so about
+//      240 of the 255 phase-B lanes busy) keep shared memory at ~74 KB and
+//      the registers at 80, so three CTAs share an SM.
 // Each thread loads the state of its first particle of the next super-chunk
 // before the deposit of the current one, so phase A never starts cold.
 // Particle-order kernel: nsteps fused steps, state in registers, stencil read
@@ -29,7 +30,7 @@
 namespace {
 
 constexpr int kT = kPushThreads;
-constexpr int kM = 512;   // particles per super-chunk
+constexpr int kM = 640;   // particles per super-chunk (~80 cells: 240 of the 255 phase-B lanes)
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -428,6 +429,10 @@ __global__ void __launch_bounds__(kT, 3)
           any = true;
         }
       }
+      // target of stencil offset (kx, ky, kz) in the haloed tile:
+      // a0 + kz * sz + ky * e0 + kx
+      const int sz = g.e[0] * g.e[1];
+      float2* a0 = acc + comp * g.ev + ((lz + hz - 1) * g.e[1] + ly) * g.e[0] + lx;
 #pragma unroll
       for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz)
 #pragma unroll
@@ -435,9 +440,8 @@ __global__ void __launch_bounds__(kT, 3)
 #pragma unroll
           for (int kx = 0; kx < 3; ++kx) {
             if (any) {
-              const int ex = lx + kx, ey = ly + ky, ez = lz + hz + (kz - 1);
-              const int t = (ez * g.e[1] + ey) * g.e[0] + ex;
-              acc[comp * g.ev + t] = two_sum_add(acc[comp * g.ev + t], T[(kz * 3 + ky) * 3 + kx]);
+              float2* a = a0 + kz * sz + ky * g.e[0] + kx;
+              *a = two_sum_add(*a, T[(kz * 3 + ky) * 3 + kx]);
             }
             __syncthreads();
           }
