@@ -361,8 +361,10 @@ BYTES_PER_PSTEP_MIXED_DEP = 44 + 40 + 3 + 3
 
 
 class MixedWorkload:
-    """Mixed form: int32 cell + f32 offsets, f32 push and fields, FP64-accurate
-    deposit sums; turbulent fields; Boris + TSC + deposit."""
+    """Mixed form: int32 cell + f32 offsets, the momentum as a compensated f32
+    pair, f32 push and fields; deposit sums in f32 within a source cell's
+    particles, two-float across cells, FP64 across bricks; turbulent fields;
+    Boris + TSC + deposit."""
 
     def __init__(self, torch, P, n, ppc, seed, with_ids=False):
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -404,7 +406,9 @@ def run_mixed(torch, P, n, ppc, K, W, seed):
     hbm, kind = peaks()
     gbs = BYTES_PER_PSTEP_MIXED_DEP * wl.N / (km / 1e3) / 1e9
     res = {"workload": f"3D {n}^3 turbulent, {wl.N} particles ({ppc}/cell), mixed form "
-                       "(int32 cell + f32 offset, f32 push/fields, FP64-accurate deposit sums), "
+                       "(int32 cell + f32 offset, u as a compensated f32 pair, f32 push/fields; "
+                       "deposit: f32 sums within a source cell, two-float across cells, FP64 "
+                       "across bricks), "
                        "Boris + TSC + deposit",
            "value": wl.N * K / (total / 1e3), "unit": "particle-steps/s",
            "ms_per_step": total / K, "push_kernel_ms": km,
@@ -464,8 +468,7 @@ def run_serving(torch, requests=200, seed=1239, load=0.7, budget_gb=16.0):
     cap = 10 ** 7
     snaps = [S.make_snapshot(torch, 128, seed, cap), S.make_snapshot(torch, 128, seed + 1, cap),
              S.make_snapshot(torch, 256, seed + 2, cap), S.make_snapshot(torch, 256, seed + 3, cap)]
-    tune = S.autotune(torch, snaps, candidates=[(128, 4, 2048), (256, 4, 2048), (256, 8, 2048),
-                                                (512, 4, 4096)], n=1 << 22, steps=16,
+    tune = S.autotune(torch, snaps, n=1 << 22,
                       cache_path=os.path.join(ROOT, "_build", "autotune.json"))
     rate = tune["psteps_per_s"]
     en = (1e7 - 1e3) / np.log(1e4)
@@ -477,19 +480,24 @@ def run_serving(torch, requests=200, seed=1239, load=0.7, budget_gb=16.0):
     ns = np.exp(rng.uniform(np.log(1e3), np.log(1e7), requests)).astype(np.int64)
     steps = np.exp(rng.uniform(np.log(10), np.log(1000), requests)).astype(np.int64)
     which = rng.integers(0, 4, requests)
-    srv = S.Server(torch, snaps, int(budget_gb * 2 ** 30), chunk=tune["chunk"], slice_steps=32,
-                   threads=tune["threads"], ctas_per_sm=tune["ctas_per_sm"])
+    srv = S.Server(torch, snaps, int(budget_gb * 2 ** 30), chunk=tune["chunk"],
+                   slice_steps=tune["slice_steps"], threads=tune["threads"],
+                   ctas_per_sm=tune["ctas_per_sm"], keep_results=False)
     t0 = time.perf_counter()
     srv.clock = lambda: time.perf_counter() - t0
     k = 0
-    while k < requests or srv.queue or srv.active:
+    while k < requests or srv.queue or srv.active or srv.inflight:
         now = srv.clock()
         while k < requests and arrivals[k] <= now:
             srv.submit(int(which[k]), int(ns[k]), int(steps[k]), seed=seed * 1000 + k,
                        arrival=float(arrivals[k]))
             k += 1
-        if not srv.round() and k < requests:
-            time.sleep(max(0.0, min(0.01, arrivals[k] - srv.clock())))
+        if not srv.round():
+            # nothing to enqueue: poll again shortly (rounds in flight, or the
+            # next arrival), so arrivals are admitted while the GPU works
+            nxt = arrivals[k] - srv.clock() if k < requests else 0.001
+            time.sleep(max(0.0, min(0.0005, nxt)))
+    srv.drain()
     wall = srv.clock()
     st = srv.stats()
     srv.close()
@@ -500,7 +508,10 @@ def run_serving(torch, requests=200, seed=1239, load=0.7, budget_gb=16.0):
            "throughput_busy": st["throughput_busy"], "p50_s": st["p50_s"],
            "p99_s": st["p99_s"], "rounds": st["rounds"], "wall_s": wall,
            "arrival_rate_per_s": lam, "capacity_psteps_per_s": rate,
-           "autotune": {k2: tune[k2] for k2 in ("threads", "ctas_per_sm", "chunk")}}
+           "autotune": {k2: tune[k2] for k2 in ("threads", "ctas_per_sm", "chunk",
+                                                 "slice_steps")},
+           "pipeline": "two work lists: round k + 1 staged and enqueued while round k runs; "
+                       "admission (device init + sort) enqueued without host synchronisation"}
     del snaps
     torch.cuda.empty_cache()
     return res

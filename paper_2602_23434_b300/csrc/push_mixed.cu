@@ -3,9 +3,10 @@
 // State: int32 linear cell + f32 offset from the cell centre (cell units, in
 // [-1/2, 1/2)) + the momentum as a compensated f32 pair u[6] = (hi[3], lo[3])
 // (+ optional f32 w).  Fields are staged as f32.  The
-// push runs in f32; the deposit reduces f32 contributions into compensated
-// (two-float) accumulators and leaves FP64 partials, so the grid sums carry
-// about 48 significant bits.
+// push runs in f32.  The deposit sums each source cell's particles in f32
+// (a handful of terms: ~8 at 8 particles per cell), adds those per-cell sums
+// into compensated (two-float, about 48-bit) accumulators of the brick's
+// haloed tile, and leaves FP64 partials that are combined in FP64.
 //
 // Brick kernel (sorted): TMA stages the brick's haloed f32 field box; the
 // brick's particles are processed in super-chunks of up to kM particles:

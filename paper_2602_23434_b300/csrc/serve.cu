@@ -157,6 +157,9 @@ part_status part_server_run(part_server* s, int nitems) {
   if (nitems < 0 || nitems > s->max_items)
     return sfail(s, PART_EINVAL, "nitems must be in [0, max_items]");
   const part_work_item* it = part_server_items(s);
+  // the chunks of one request share their state arrays: look each array set
+  // up once (cudaPointerGetAttributes is a host call per pointer)
+  const void *ok_cell = nullptr, *ok_off = nullptr, *ok_u = nullptr;
   for (int i = 0; i < nitems; ++i) {
     const part_work_item& w = it[i];
     if (w.snapshot < 0 || w.snapshot >= s->nsnap)
@@ -165,13 +168,17 @@ part_status part_server_run(part_server* s, int nitems) {
       return sfail(s, PART_EINVAL, "work item " + std::to_string(i) + ": bad slice");
     if (w.count > 0 && (!w.cell || !w.off || !w.u))
       return sfail(s, PART_EINVAL, "work item " + std::to_string(i) + ": NULL state");
-    if (w.count > 0 &&
-        (((uintptr_t)w.cell | (uintptr_t)w.off | (uintptr_t)w.u) % 4 != 0 ||
-         !device_accessible(s->snaps[0]->device, w.cell) ||
-         !device_accessible(s->snaps[0]->device, w.off) ||
-         !device_accessible(s->snaps[0]->device, w.u)))
-      return sfail(s, PART_EINVAL,
-                   "work item " + std::to_string(i) + ": state not aligned or not reachable");
+    if (w.count > 0 && !(w.cell == ok_cell && w.off == ok_off && w.u == ok_u)) {
+      if (((uintptr_t)w.cell | (uintptr_t)w.off | (uintptr_t)w.u) % 4 != 0 ||
+          !device_accessible(s->snaps[0]->device, w.cell) ||
+          !device_accessible(s->snaps[0]->device, w.off) ||
+          !device_accessible(s->snaps[0]->device, w.u))
+        return sfail(s, PART_EINVAL,
+                     "work item " + std::to_string(i) + ": state not aligned or not reachable");
+      ok_cell = w.cell;
+      ok_off = w.off;
+      ok_u = w.u;
+    }
     if (!std::isfinite(w.q_over_m) || !std::isfinite(w.dt) || w.dt == 0.0)
       return sfail(s, PART_EINVAL, "work item " + std::to_string(i) + ": bad q_over_m / dt");
   }

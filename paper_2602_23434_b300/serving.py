@@ -3,15 +3,19 @@
 Requests (N particles, S Boris steps, one of several field snapshots that stay
 resident on the device) arrive at any time.  Each scheduling round:
   1. admits queued requests in arrival order while their particle state fits
-     in the device-memory budget (admission by free HBM), initialises them on
-     the device (Philox draws, then a cell sort for gather locality);
-  2. cuts every active request into work items of `chunk` particles that
-     advance min(remaining, slice_steps) steps;
-  3. runs the round through the C ABI (one persistent kernel replayed from a
-     CUDA graph), waits for it, and completes the requests that are done.
-Requests that arrive while others are on the GPU join at the next round, so
-their work overlaps on the device with the running ones.  All arithmetic runs
-in libpart.so; this module schedules and bookkeeps only.
+     in the device-memory budget (admission by free HBM); their device
+     initialisation (Philox draws, then a cell sort for gather locality) is
+     enqueued on the serving stream, with no host synchronisation;
+  2. cuts every request with steps left to schedule into work items of
+     `chunk` particles that advance min(left, slice_steps) steps;
+  3. enqueues the round through the C ABI (the work-list copy and one
+     persistent kernel, replayed from a CUDA graph) and records an event.
+Two work lists are staged alternately, so round k + 1 is planned and
+enqueued while round k runs; the host only waits when both are in flight.
+Requests are completed when the event of the round holding their last slice
+has passed.  Requests that arrive while others are on the GPU join at the
+next round, so their work overlaps on the device with the running ones.  All
+arithmetic runs in libpart.so; this module schedules and bookkeeps only.
 """
 from __future__ import annotations
 
@@ -42,7 +46,8 @@ class Request:
     arrival: float
     admitted: float | None = None
     done: float | None = None
-    remaining: int = 0
+    remaining: int = 0        # steps not yet completed on the device
+    unplanned: int = 0        # steps not yet put into a round
     cell: object = None
     off: object = None
     u: object = None
@@ -94,9 +99,15 @@ def make_snapshot(torch, n: int, seed: int, capacity: int, device=None):
 
 
 class Server:
+    """Continuous batching over resident snapshots (see the module docstring).
+    keep_results=False releases a request's device state when it completes
+    (a long stream then holds only the admitted requests' memory)."""
+
+    PIPELINE = 2          # work lists in flight: round k + 1 is staged while k runs
+
     def __init__(self, torch, snapshots, mem_budget_bytes: int, max_items: int = 1 << 16,
                  chunk: int = 2048, slice_steps: int = 32, threads: int = 256,
-                 ctas_per_sm: int = 4, clock=time.perf_counter):
+                 ctas_per_sm: int = 4, clock=time.perf_counter, keep_results: bool = True):
         self.torch = torch
         self.L = P.lib()
         self.snaps = snapshots
@@ -106,26 +117,37 @@ class Server:
         self.slice_steps = int(slice_steps)
         self.max_items = int(max_items)
         self.clock = clock
+        self.keep_results = keep_results
         dbytes, hbytes = C.c_size_t(), C.c_size_t()
         self._check(self.L.part_server_sizes(len(snapshots), max_items, C.byref(dbytes),
                                              C.byref(hbytes)))
         dev = snapshots[0].part.device
-        self.ws = torch.empty(dbytes.value, dtype=torch.uint8, device=dev)
-        self.stage = torch.empty(hbytes.value, dtype=torch.uint8, pin_memory=True)
         arr = (C.c_void_p * len(snapshots))(*[s.part.ctx.value for s in snapshots])
-        self.h = C.c_void_p()
-        self._check(self.L.part_server_init(C.byref(self.h), arr, len(snapshots), max_items,
-                                            C.c_void_p(self.ws.data_ptr()), dbytes.value,
-                                            C.c_void_p(self.stage.data_ptr()), hbytes.value,
-                                            C.c_void_p(self.stream.cuda_stream), threads,
-                                            ctas_per_sm))
-        self.items = self.L.part_server_items(self.h)
+        self.ws, self.stage, self.hs, self.item_lists = [], [], [], []
+        for _ in range(self.PIPELINE):
+            ws = torch.empty(dbytes.value, dtype=torch.uint8, device=dev)
+            stage = torch.empty(hbytes.value, dtype=torch.uint8, pin_memory=True)
+            h = C.c_void_p()
+            self._check(self.L.part_server_init(C.byref(h), arr, len(snapshots), max_items,
+                                                C.c_void_p(ws.data_ptr()), dbytes.value,
+                                                C.c_void_p(stage.data_ptr()), hbytes.value,
+                                                C.c_void_p(self.stream.cuda_stream), threads,
+                                                ctas_per_sm))
+            self.ws.append(ws)
+            self.stage.append(stage)
+            self.hs.append(h)
+            self.item_lists.append(self.L.part_server_items(h))
+        self.h = self.hs[0]
+        self.items = self.item_lists[0]
+        self.inflight = []        # (event, slot, plan) in enqueue order
+        self._slot = 0
         self.queue: list[Request] = []
         self.active: list[Request] = []
         self.finished: list[Request] = []
         self.used = 0
         self.rounds = 0
         self.busy_s = 0.0
+        self._busy_from = None
         self.psteps = 0
         self._next = 0
 
@@ -135,10 +157,11 @@ class Server:
             raise P.PartError(code, msg.decode() if msg else "")
 
     def close(self):
-        if getattr(self, "h", None) is not None and self.h.value:
-            self.L.part_server_sync(self.h)
-            self.L.part_server_destroy(self.h)
-            self.h = C.c_void_p()
+        for h in getattr(self, "hs", []):
+            if h is not None and h.value:
+                self.L.part_server_sync(h)
+                self.L.part_server_destroy(h)
+                h.value = None
 
     # ------------------------------------------------------------------ API
     def submit(self, snapshot: int, n: int, steps: int, seed: int, q_over_m: float = 1.0,
@@ -155,7 +178,7 @@ class Server:
             dt = 0.5 * 2.0 / g
         r = Request(self._next, snapshot, int(n), int(steps), int(seed), float(q_over_m),
                     float(dt), float(u_th), self.clock() if arrival is None else arrival)
-        r.remaining = int(steps)
+        r.remaining = r.unplanned = int(steps)
         self._next += 1
         self.queue.append(r)
         return r
@@ -177,7 +200,7 @@ class Server:
             sp.bind(r.n, r.cell, off=r.off, u=r.u)
             sp.init_particles(r.seed, r.u_th)
             sp.sort()
-            sp.sync()                      # sorted state into the request's arrays
+            sp.flush()                     # sorted state into the request's arrays (async)
             self.used += need
             r.admitted = self.clock()
             if r.remaining == 0:
@@ -188,18 +211,51 @@ class Server:
     def _finish(self, r):
         r.done = self.clock()
         self.used -= r.n * STATE_BYTES_PER_PARTICLE
+        if not self.keep_results:
+            r.cell = r.off = r.u = None
         self.finished.append(r)
 
+    def _reap(self, block: bool = False) -> int:
+        """Complete the rounds whose events have passed (block: wait for the
+        oldest one at least).  Returns how many rounds were completed."""
+        done = 0
+        while self.inflight:
+            ev, slot, plan = self.inflight[0]
+            if not ev.query():
+                if not (block and done == 0):
+                    break
+                ev.synchronize()
+            self.inflight.pop(0)
+            done += 1
+            for r, s in plan:
+                r.remaining -= s
+                self.psteps += r.n * s
+                if r.remaining == 0:
+                    self.active.remove(r)
+                    self._finish(r)
+        if not self.inflight and self._busy_from is not None:
+            self.busy_s += self.clock() - self._busy_from
+            self._busy_from = None
+        return done
+
     def round(self) -> bool:
-        """One scheduling round; returns False when there was nothing to run."""
+        """Complete finished rounds, admit, and enqueue one round if any
+        admitted request has steps left to schedule (waiting for a work list
+        only when both are in flight).  Returns True if a round was enqueued."""
+        self._reap()
         self._admit()
-        if not self.active:
+        todo = [r for r in self.active if r.unplanned > 0]
+        if not todo:
             return False
-        its = self.items
+        if len(self.inflight) >= self.PIPELINE:   # both work lists in use
+            self._reap(block=True)
+        slot = self._slot
+        self._slot = (self._slot + 1) % self.PIPELINE
+        its = self.item_lists[slot]
         k = 0
         plan = []
-        for r in self.active:
-            s = min(r.remaining, self.slice_steps)
+        for r in todo:
+            s = min(r.unplanned, self.slice_steps)
             nchunks = (r.n + self.chunk - 1) // self.chunk
             if k + nchunks > self.max_items:
                 break
@@ -215,29 +271,32 @@ class Server:
                 w.q_over_m = r.q_over_m
                 w.dt = r.dt
                 k += 1
+            r.unplanned -= s
             plan.append((r, s))
-        t0 = self.clock()
-        self._check(self.L.part_server_run(self.h, k))
-        self._check(self.L.part_server_sync(self.h))
-        self.busy_s += self.clock() - t0
+        if self._busy_from is None:
+            self._busy_from = self.clock()
+        self._check(self.L.part_server_run(self.hs[slot], k))
+        ev = self.torch.cuda.Event()
+        ev.record(self.stream)
+        self.inflight.append((ev, slot, plan))
         self.rounds += 1
-        still = []
-        planned = {id(r) for r, _ in plan}
-        for r, s in plan:
-            r.remaining -= s
-            self.psteps += r.n * s
-        for r in self.active:
-            if id(r) in planned and r.remaining == 0:
-                self._finish(r)
-            else:
-                still.append(r)
-        self.active = still
         return True
 
+    def drain(self):
+        """Wait for every enqueued round and complete its requests."""
+        while self.inflight:
+            self._reap(block=True)
+        for h in self.hs:
+            self._check(self.L.part_server_sync(h))
+
     def run_until_idle(self):
-        while self.queue or self.active:
-            if not self.round() and self.queue:
-                raise RuntimeError("queued request cannot be admitted")
+        while self.queue or self.active or self.inflight:
+            if not self.round():
+                if self.inflight:
+                    self._reap(block=True)
+                elif self.queue:
+                    raise RuntimeError("queued request cannot be admitted")
+        self.drain()
 
     def stats(self):
         lat = np.array([r.latency for r in self.finished if r.latency is not None])
@@ -250,14 +309,20 @@ class Server:
 
 
 # ---------------------------------------------------------------------- autotuner
-def autotune(torch, snapshots, candidates=None, n=1 << 21, steps=16, cache_path=None):
-    """Pick (threads, ctas_per_sm, chunk) of the serving kernel by timing one
-    round of a fixed synthetic batch per candidate; cached in a JSON file
-    keyed by device name and snapshot grids."""
+def autotune(torch, snapshots, candidates=None, n=1 << 21, slices=4, cache_path=None):
+    """Pick the serving shape by timing a fixed synthetic batch per candidate:
+    (threads per CTA, persistent CTAs per SM, chunk = particles per work item,
+    i.e. the tile of sorted cells one CTA takes at a time, slice = steps per
+    round).  One thread advances one particle.  Each candidate runs n
+    particles for `slices` rounds after a warm-up round; the result is cached
+    in a JSON file keyed by device name and snapshot grids."""
     cache_path = cache_path or os.environ.get(
         "PART_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache",
                                             "paper_2602_23434_b300_autotune.json"))
-    key = json.dumps([torch.cuda.get_device_name(), [s.n_cells for s in snapshots], n, steps])
+    candidates = candidates or [(t, c, ch, sl) for (t, c) in ((256, 4), (512, 4), (256, 8))
+                                for ch in (2048, 8192) for sl in (16, 64)]
+    key = json.dumps([torch.cuda.get_device_name(), [s.n_cells for s in snapshots], n, slices,
+                      [list(c) for c in candidates]])
     try:
         with open(cache_path) as f:
             cache = json.load(f)
@@ -265,24 +330,24 @@ def autotune(torch, snapshots, candidates=None, n=1 << 21, steps=16, cache_path=
             return cache[key]
     except (OSError, ValueError):  # no cache yet, or an unreadable one
         cache = {}
-    candidates = candidates or [(t, c, ch) for t in (128, 256, 512) for c in (2, 4, 8)
-                                for ch in (1024, 4096)]
     best, results = None, []
-    for t, c, ch in candidates:
+    for t, c, ch, sl in candidates:
         srv = Server(torch, snapshots, mem_budget_bytes=n * STATE_BYTES_PER_PARTICLE * 2,
-                     chunk=ch, slice_steps=steps, threads=t, ctas_per_sm=c)
-        r = srv.submit(len(snapshots) - 1, n, steps * 3, seed=7)
-        srv.round()                                   # warm-up round (also admits)
+                     chunk=ch, slice_steps=sl, threads=t, ctas_per_sm=c)
+        srv.submit(len(snapshots) - 1, n, sl * (slices + 1), seed=7)
+        srv.round()                                   # warm-up round (admits, captures)
+        srv.drain()
         t0 = time.perf_counter()
-        srv.round()
-        srv.round()
+        while srv.active or srv.inflight:
+            srv.round()
+        srv.drain()
         el = time.perf_counter() - t0
-        rate = 2 * n * steps / el
-        results.append({"threads": t, "ctas_per_sm": c, "chunk": ch, "psteps_per_s": rate})
+        rate = n * sl * slices / el
+        results.append({"threads": t, "ctas_per_sm": c, "chunk": ch, "slice_steps": sl,
+                        "psteps_per_s": rate})
         if best is None or rate > best["psteps_per_s"]:
             best = results[-1]
         srv.close()
-        del r
     out = dict(best)
     out["candidates"] = results
     cache[key] = out

@@ -86,6 +86,7 @@ def test_bad_work_item_refused_on_host(snaps):
     srv = S.Server(torch, snaps, 1 << 26, chunk=1024)
     r = srv.submit(0, 2000, 5, seed=3)
     srv.round()                                               # admits and runs one round
+    srv.drain()              # that round's work list is read by the GPU: let it finish first
     w = srv.items[0]
     w.cell, w.off, w.u = r.cell.data_ptr(), r.off.data_ptr(), r.u.data_ptr()
     w.stride, w.first, w.count, w.nsteps = 2000, 1500, 1000, 1   # slice past the end
