@@ -58,8 +58,8 @@ BYTES_PER_PSTEP_BORIS_DEP = 96 + 8 + 6 + 3
 # 265.6 MB for 2,097,152 particles), scaled to a launch by the particle count.
 TRAFFIC_PER_PARTICLE_BRICK_F64 = 265.092864e6 / 2097152  # ncu dram r+w, 64^3 capture
 # Same for the mixed brick kernel, from an ncu capture of the 128^3 case
-# (1299.8 MB for 16,777,216 particles).
-TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1294.579712e6 / 16777216   # ncu dram r+w, 128^3 capture
+# (1714.9 MB for 16,777,216 particles).
+TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1714.857728e6 / 16777216   # ncu dram r+w, 128^3 capture
 # LP step: x r/w 48, chi+eng r/w 4096 (128 bins), n_old r/w 16, samples w+r 48,
 # fields: 7 comps * 8 B per cell / 2 LPs per cell, 3 gathers at ~one cell = 84
 BYTES_PER_LPSTEP = 48 + 4096 + 16 + 48 + 84
@@ -193,7 +193,8 @@ def time_steps(torch, stream, fn, K: int, W: int, per_step_events=False):
     return total_ms, kern_ms
 
 
-def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, order=2):
+def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, order=2,
+           fp64_tflops=None):
     dev = torch.device("cuda", torch.cuda.current_device())
     vel, rho, B = synth.fluid_snapshot(3, n, seed)
     f7 = torch.as_tensor(np.concatenate([vel, rho, B]).reshape(7, -1)).to(dev)
@@ -211,11 +212,14 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
     dt = 0.5 * 2.0 / n
     # cooling break near eps ~ 1e3 after 100 steps with <U_B> = (B0^2 + dB^2)/2 = 1
     c0 = 1.0 / (1e3 * 1.0 * 100 * dt)
-    evs = []
-
     calls = [0]
+    push_ev = []              # (start, end) of each timed step's push
 
     def step(ev):
+        if ev is not None:
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(p.stream)
+            push_ev.append(e)
         p.gather_push(0.0, dt, 1)
         if ev is not None:
             ev[0].record(p.stream)
@@ -227,17 +231,40 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
             p.flush()
 
     l0 = p.launches()
-    total, kern = time_steps(torch, p.stream, step, K, W, per_step_events=True)
+    kev = []
+    total, kern = time_steps(torch, p.stream, lambda ev: (kev.append(ev), step(ev)), K, W,
+                             per_step_events=True)
     p.sync()
     launches = (p.launches() - l0) // (K + W)
     ms = total / K
     spec_ms = float(np.mean(kern))
+    kev = [e for e in kev if e is not None]
+    push_ms = float(np.mean([a.elapsed_time(e[0]) for a, e in zip(push_ev, kev)]))
+    # the two bounds of the step: the push on the FP64 pipe (about 440 FP64
+    # pipe slots per LP-step for RK2, 560 for RK3, at 2 slots per SM-cycle =
+    # half the measured FP64 FLOP/s), the spectral update on HBM
+    slots = 440 if order == 2 else 560
+    spec_bytes = nlp * 2 * 2 * nb * 8
+    hbm, _ = peaks()
     del chi, eng
     return {"workload": f"LP 3D {n}^3 snapshot, {nlp} LPs x {nb} bins, "
                         f"{'RK2' if order == 2 else 'SSP-RK3'} + TSC + spectra, FP64",
             "value": nlp * K / (total / 1e3), "unit": "LP-steps/s", "ms_per_step": ms,
             "spec_update_ms": spec_ms,
-            "spec_update_GBps": nlp * 2 * 2 * nb * 8 / (spec_ms / 1e3) / 1e9,
+            "spec_update_GBps": spec_bytes / (spec_ms / 1e3) / 1e9,
+            "push_ms": push_ms,
+            "roofline_step": {
+                "push": {"bound": "fp64 pipe", "slots_per_lp_step": slots,
+                         "bound_ms_at_measured_peak": (
+                             nlp * slots / (fp64_tflops * 1e12 / 2) * 1e3
+                             if fp64_tflops else None),
+                         "frac": (nlp * slots / (fp64_tflops * 1e12 / 2) * 1e3 / push_ms
+                                  if fp64_tflops else None),
+                         "kernel_ms": push_ms},
+                "spec_update": {"bound": "hbm", "bytes": spec_bytes,
+                                "bound_ms": spec_bytes / (hbm * 1e9) * 1e3,
+                                "kernel_ms": spec_ms,
+                                "frac": spec_bytes / (spec_ms / 1e3) / 1e9 / hbm}},
             "c0": c0, "dt": dt, "gpu_launches_per_step": launches}
 
 
@@ -1034,11 +1061,12 @@ def main():
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_extras:
         try:
-            line["lp"] = run_lp(torch, P, max(5, args.steps // 2), 3)
+            line["lp"] = run_lp(torch, P, max(5, args.steps // 2), 3, fp64_tflops=fp64_peak)
         except Exception as e:  # report, do not hide
             line["lp"] = {"error": repr(e)}
         try:
-            line["lp_rk3"] = run_lp(torch, P, max(5, args.steps // 2), 3, order=3)
+            line["lp_rk3"] = run_lp(torch, P, max(5, args.steps // 2), 3, order=3,
+                                    fp64_tflops=fp64_peak)
         except Exception as e:
             line["lp_rk3"] = {"error": repr(e)}
         try:

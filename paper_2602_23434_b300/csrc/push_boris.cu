@@ -205,6 +205,18 @@ __device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int b
   }
 }
 
+// First index i in [lo, hi] with s[i] > v (s nondecreasing), hi if none.
+__device__ __forceinline__ int first_above64(const uint32_t* s, int lo, int hi, uint32_t v) {
+  while (lo < hi) {
+    const int m = (lo + hi) >> 1;
+    if (s[m] > v)
+      hi = m;
+    else
+      lo = m + 1;
+  }
+  return lo;
+}
+
 // Deposit of one chunk [base, bend) by deposit warp `warp` (0..7): the cells
 // s with s mod 8 == warp, one lane per stencil offset; every lane loops over
 // the same particles, so the loop does not diverge.  Adds into the warp's
@@ -215,9 +227,9 @@ __device__ __forceinline__ void deposit_chunk(const Geo& g, const uint32_t* scs,
                                               const double* rw, const double* rf, double* win,
                                               int wsize, int warp, int lane, uint32_t base,
                                               uint32_t bend, int& cfirst) {
-  while (scs[cfirst + 1] <= base) ++cfirst;
-  int clast = cfirst;
-  while (clast + 1 < g.V && scs[clast + 1] < bend) ++clast;
+  // the chunk's cells by two binary searches of the brick's cell_start
+  cfirst = first_above64(scs, 1, g.V, base) - 1;
+  const int clast = first_above64(scs, 0, g.V, bend - 1) - 1;
   const int s0 = cfirst + ((warp - cfirst % 8) + 8) % 8;
   for (int sc = s0; sc <= clast; sc += 8) {
     uint32_t r0 = scs[sc], r1 = scs[sc + 1];
@@ -238,7 +250,8 @@ __device__ __forceinline__ void deposit_chunk(const Geo& g, const uint32_t* scs,
         a1 += ww * pf[kRS + i];
         a2 += ww * pf[2 * kRS + i];
       }
-      const int lx = sc % g.b[0], ly = (sc / g.b[0]) % g.b[1], lz = sc / (g.b[0] * g.b[1]);
+      const int lx = sc & (g.b[0] - 1), ly = (sc >> g.bshift[0]) & (g.b[1] - 1),
+                lz = sc >> (g.bshift[0] + g.bshift[1]);   // brick sides are powers of two
       const int ex = lx + kx, ey = ly + ky, ez = DIM == 3 ? lz + kz : 0;
       const int col = ex - warp < 3 ? ex - warp : ex - warp - 5;   // slot in the window
       double* wp = win + warp * wsize + ((col * g.e[2] + ez) * g.e[1] + ey) * 3;

@@ -32,11 +32,15 @@ namespace {
 
 constexpr int kT = kPushThreads;
 constexpr int kM = 640;   // particles per super-chunk (~80 cells: 240 of the 255 phase-B lanes)
+// Row stride of the record planes: kM + 11 floats puts the three force rows
+// (read at once by a cell's three component lanes) on different banks.
+constexpr int kR = kM + 11;
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct MixedSmem {
   size_t cs, bar, rec, acc, total;
+  int evp;  // component stride of the two-float tile (in float2)
 };
 __host__ __device__ inline MixedSmem mixed_smem(const Geo& g) {
   MixedSmem s;
@@ -44,8 +48,11 @@ __host__ __device__ inline MixedSmem mixed_smem(const Geo& g) {
   s.cs = align_up(bbytes, 128);
   s.bar = align_up(s.cs + (size_t)(g.V + 1) * 4, 16);
   s.rec = align_up(s.bar + 16, 128);
-  s.acc = s.rec + (size_t)6 * kM * 4;
-  s.total = s.acc + (size_t)6 * g.ev * 4;
+  s.acc = align_up(s.rec + (size_t)6 * kR * 4, 16);
+  // components (hi, lo) strided by evp = 6 mod 16 float2: the three component
+  // lanes of a cell, adding to the same target offset, land on different banks
+  s.evp = g.ev + ((6 - g.ev % 16) + 16) % 16;
+  s.total = s.acc + (size_t)3 * s.evp * 8;
   return s;
 }
 
@@ -216,9 +223,9 @@ __global__ void __launch_bounds__(kT, 3)
   uint32_t* scs = reinterpret_cast<uint32_t*>(smem + L.cs);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
   int* sflag = reinterpret_cast<int*>(smem + L.bar + 8);
-  float* rd = reinterpret_cast<float*>(smem + L.rec);  // [3][kM] old offsets
-  float* rF = rd + 3 * kM;                              // [3][kM] force
-  float2* acc = reinterpret_cast<float2*>(smem + L.acc);  // [3][ev] (hi, lo)
+  float* rd = reinterpret_cast<float*>(smem + L.rec);  // [3][kR] old offsets
+  float* rF = rd + 3 * kR;                              // [3][kR] force
+  float2* acc = reinterpret_cast<float2*>(smem + L.acc);  // [3][evp] (hi, lo)
 
   const int64_t brick = blockIdx.x;
   const int bx = (int)(brick % g.nb[0]);
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(kT, 3)
   }
   for (int i = tid; i <= g.V; i += kT) scs[i] = cstart[brick * g.V + i];
   if (DEP)
-    for (int i = tid; i < 3 * g.ev; i += kT) acc[i] = make_float2(0.0f, 0.0f);
+    for (int i = tid; i < 3 * L.evp; i += kT) acc[i] = make_float2(0.0f, 0.0f);
   if (!mbar_wait_bounded(bar, 0)) atomicOr(sflag, 1);
   __syncthreads();
   if (*sflag) {
@@ -379,8 +386,8 @@ __global__ void __launch_bounds__(kT, 3)
       if (DEP) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          rd[a * kM + i] = d0[a];
-          rF[a * kM + i] = F[a];
+          rd[a * kR + i] = d0[a];
+          rF[a * kR + i] = F[a];
         }
       }
     }
@@ -414,9 +421,9 @@ __global__ void __launch_bounds__(kT, 3)
           const int i = (int)(r - sb);
           float wx[3], wy[3], wz[3] = {0.0f, 1.0f, 0.0f};
           shape_weights<SHAPE>(rd[i], wx);
-          shape_weights<SHAPE>(rd[kM + i], wy);
-          if (DIM == 3) shape_weights<SHAPE>(rd[2 * kM + i], wz);
-          const float Fc = rF[comp * kM + i];
+          shape_weights<SHAPE>(rd[kR + i], wy);
+          if (DIM == 3) shape_weights<SHAPE>(rd[2 * kR + i], wz);
+          const float Fc = rF[comp * kR + i];
           const float wxF[3] = {wx[0] * Fc, wx[1] * Fc, wx[2] * Fc};
 #pragma unroll
           for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz)
@@ -433,7 +440,7 @@ __global__ void __launch_bounds__(kT, 3)
       // target of stencil offset (kx, ky, kz) in the haloed tile:
       // a0 + kz * sz + ky * e0 + kx
       const int sz = g.e[0] * g.e[1];
-      float2* a0 = acc + comp * g.ev + ((lz + hz - 1) * g.e[1] + ly) * g.e[0] + lx;
+      float2* a0 = acc + comp * L.evp + ((lz + hz - 1) * g.e[1] + ly) * g.e[0] + lx;
 #pragma unroll
       for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz)
 #pragma unroll
@@ -454,7 +461,7 @@ __global__ void __launch_bounds__(kT, 3)
 #pragma unroll
       for (int c = 0; c < 3; ++c)
         dpart[(brick * 3 + c) * g.ev + t] =
-            (double)acc[c * g.ev + t].x + (double)acc[c * g.ev + t].y;
+            (double)acc[c * L.evp + t].x + (double)acc[c * L.evp + t].y;
   }
 }
 
