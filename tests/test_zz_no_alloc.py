@@ -93,3 +93,27 @@ def test_noalloc_sort_rejects_more_than_its_scratch_holds():
            cs.data_ptr(), None)
     assert rc == 1
     assert b"1048576" in L.part_last_error(None)
+
+
+def test_noalloc_sort_allocates_nothing():
+    """After a first call on the device (which loads the library's kernels
+    and looks up the scratch address), a call changes neither the device's
+    free memory nor what torch's allocator holds."""
+    L, f = _noalloc()
+    g = P.make_grid(3, 16)
+    a = _particles(16, 16 ** 3 * 4 + 7, 303)
+    nkeys = 16 ** 3  # 16^3: two whole bricks per axis, no key gaps
+    cs = torch.zeros(nkeys + 1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def call():
+        rc = f(C.byref(g), a[0].shape[1], a[0].data_ptr(), a[1].data_ptr(), a[2].data_ptr(),
+               a[3].data_ptr(), cs.data_ptr(), stream.cuda_stream)
+        assert rc == 0, L.part_last_error(None)
+        torch.cuda.synchronize()
+
+    call()
+    free0, held0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    call()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == held0
