@@ -559,9 +559,13 @@ __global__ void __launch_bounds__(256)
   for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < g.G;
        gi += (int64_t)gridDim.x * blockDim.x) {
     int j[3];
-    j[0] = (int)(gi % g.n[0]);
-    j[1] = (int)((gi / g.n[0]) % g.n[1]);
-    j[2] = (int)(gi / ((int64_t)g.n[0] * g.n[1]));
+    if (g.G <= INT32_MAX) {
+      cell_coords(g, (int32_t)gi, j);  // float-reciprocal divmod, no 64-bit division
+    } else {
+      j[0] = (int)(gi % g.n[0]);
+      j[1] = (int)((gi / g.n[0]) % g.n[1]);
+      j[2] = (int)(gi / ((int64_t)g.n[0] * g.n[1]));
+    }
     if (fast) {
       // full bricks and at least three per active axis: the cell is in its
       // own brick's tile, and in one neighbour's halo when it is on a face
