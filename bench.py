@@ -485,7 +485,7 @@ def mixed_error_vs_fp64(torch, P, n=128, ppc=8, steps=20, seed=1236):
     return res
 
 
-def run_serving(torch, requests=200, seed=1239, load=0.7, budget_gb=16.0):
+def run_serving(torch, requests=200, seed=1239, load=0.7, budget_gb=16.0, round_ms=10.0):
     """Poisson stream of test-particle requests against 4 resident snapshots
     (128^3 x2, 256^3 x2, turbulent, f32): N log-uniform in [1e3, 1e7],
     steps log-uniform in [10, 1000], mixed precision, admitted by device
@@ -509,7 +509,8 @@ def run_serving(torch, requests=200, seed=1239, load=0.7, budget_gb=16.0):
     which = rng.integers(0, 4, requests)
     srv = S.Server(torch, snaps, int(budget_gb * 2 ** 30), chunk=tune["chunk"],
                    slice_steps=tune["slice_steps"], threads=tune["threads"],
-                   ctas_per_sm=tune["ctas_per_sm"], keep_results=False)
+                   ctas_per_sm=tune["ctas_per_sm"], keep_results=False,
+                   round_psteps=rate * round_ms / 1e3 if round_ms else None)
     t0 = time.perf_counter()
     srv.clock = lambda: time.perf_counter() - t0
     k = 0
@@ -538,7 +539,9 @@ def run_serving(torch, requests=200, seed=1239, load=0.7, budget_gb=16.0):
            "autotune": {k2: tune[k2] for k2 in ("threads", "ctas_per_sm", "chunk",
                                                  "slice_steps")},
            "pipeline": "two work lists: round k + 1 staged and enqueued while round k runs; "
-                       "admission (device init + sort) enqueued without host synchronisation"}
+                       "admission (device init + sort) enqueued without host synchronisation",
+           "round_budget": f"{round_ms} ms of capacity per round, shared equally by the "
+                           f"active requests (whole remainders that fit are done at once)"}
     del snaps
     torch.cuda.empty_cache()
     return res

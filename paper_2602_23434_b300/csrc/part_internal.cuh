@@ -137,7 +137,8 @@ struct part_ctx {
 // Serving: the device header of a work list and one resident snapshot.
 struct ServeHeader {
   int nitems;
-  int pad[63];
+  unsigned next;  // next unclaimed item (the staged copy carries 0 into every round)
+  int pad[62];
 };
 struct SnapEntry {
   const float* fp;  // padded f32 field copy of the snapshot's context
@@ -339,7 +340,7 @@ cudaError_t launch_shock_cells(part_ctx* c);       // shock_r from the padded LP
 cudaError_t launch_shock_convolve(part_ctx* c);    // Eq. convolution_spectra on the list
 cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps);
 cudaError_t launch_boris_mixed(part_ctx* c, double qm, double dt, int nsteps);
-cudaError_t launch_serve_kernel(int shape, int dim, const ServeHeader* hdr,
+cudaError_t launch_serve_kernel(int shape, int dim, ServeHeader* hdr,
                                 const part_work_item* items, const SnapEntry* snaps, int nsnap,
                                 int* status, int grid, int threads, cudaStream_t stream);
 cudaError_t launch_deposit_combine(part_ctx* c, double* out);

@@ -551,21 +551,29 @@ __global__ void __launch_bounds__(256)
     particle_mixed<SHAPE, DIM>(fp, g, cell, off, u, n, p, h, hl, dtdx, nsteps, status, outmask);
 }
 
-// Persistent serving kernel: CTA b takes work items b, b + gridDim.x, ...
-// (static assignment, no inter-CTA waits).  Each item is a slice of one
+// Persistent serving kernel: each CTA claims the next unclaimed work item
+// (one atomic on the work list's counter per item; the host lists the items
+// costliest first), so CTAs finish a round together however uneven the
+// items are.  No CTA waits on another.  Each item is a slice of one
 // request's particles to advance nsteps steps against one resident field
-// snapshot; the per-item step parameters are formed in FP64 exactly as the
-// host forms them for part_gather_push.
+// snapshot; every particle gets the same arithmetic whichever CTA takes it.
+// The per-item step parameters are formed in FP64 exactly as the host forms
+// them for part_gather_push.
 template <int SHAPE, int DIM>
 __global__ void __launch_bounds__(512)
-    k_serve_mixed(const ServeHeader* __restrict__ hdr, const part_work_item* __restrict__ items,
+    k_serve_mixed(ServeHeader* __restrict__ hdr, const part_work_item* __restrict__ items,
                   const SnapEntry* __restrict__ snaps, int nsnap, int* __restrict__ status) {
   __shared__ part_work_item s_it;
   __shared__ SnapEntry s_sn;
   __shared__ float s_par[5];
+  __shared__ int s_next;
   const int nitems = hdr->nitems;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  for (;;) {
     __syncthreads();
+    if (threadIdx.x == 0) s_next = (int)atomicAdd(&hdr->next, 1u);
+    __syncthreads();
+    const int it = s_next;
+    if (it >= nitems) break;
     if (threadIdx.x == 0) {
       s_it = items[it];
       int sn = s_it.snapshot;
@@ -653,7 +661,7 @@ cudaError_t launch_boris_mixed(part_ctx* c, double qm, double dt, int nsteps) {
                   : dispatch_mixed<PART_CIC, 2>(c, qm, dt, nsteps);
 }
 
-cudaError_t launch_serve_kernel(int shape, int dim, const ServeHeader* hdr,
+cudaError_t launch_serve_kernel(int shape, int dim, ServeHeader* hdr,
                                 const part_work_item* items, const SnapEntry* snaps, int nsnap,
                                 int* status, int grid, int threads, cudaStream_t stream) {
   if (shape == PART_TSC) {

@@ -183,6 +183,7 @@ part_status part_server_run(part_server* s, int nitems) {
       return sfail(s, PART_EINVAL, "work item " + std::to_string(i) + ": bad q_over_m / dt");
   }
   ((ServeHeader*)s->h_stage)->nitems = nitems;
+  ((ServeHeader*)s->h_stage)->next = 0;
   cudaError_t e = cudaSuccess;
   if (!s->captured) {
     e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);

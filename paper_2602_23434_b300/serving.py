@@ -32,6 +32,14 @@ from . import _lib as P
 # int32 cell, f32 off[3], f32 u[6] (the momentum as a compensated pair)
 STATE_BYTES_PER_PARTICLE = 4 + 12 + 24
 
+# part_work_item as a numpy record (the layout of include/part.h), so a
+# request's work items are written into the pinned work list in one go
+ITEM_DTYPE = np.dtype({
+    "names": [f[0] for f in P.WorkItem._fields_],
+    "formats": ["u8", "u8", "u8", "i8", "i8", "i4", "i4", "i4", "i4", "f8", "f8"],
+    "offsets": [getattr(P.WorkItem, f[0]).offset for f in P.WorkItem._fields_],
+    "itemsize": C.sizeof(P.WorkItem)})
+
 
 @dataclass
 class Request:
@@ -107,7 +115,8 @@ class Server:
 
     def __init__(self, torch, snapshots, mem_budget_bytes: int, max_items: int = 1 << 16,
                  chunk: int = 2048, slice_steps: int = 32, threads: int = 256,
-                 ctas_per_sm: int = 4, clock=time.perf_counter, keep_results: bool = True):
+                 ctas_per_sm: int = 4, clock=time.perf_counter, keep_results: bool = True,
+                 round_psteps: float | None = None):
         self.torch = torch
         self.L = P.lib()
         self.snaps = snapshots
@@ -118,12 +127,19 @@ class Server:
         self.max_items = int(max_items)
         self.clock = clock
         self.keep_results = keep_results
+        # work per round (particle-steps): with a budget, every round gives
+        # each request an equal share of it (requests whose whole remaining
+        # work fits take all of it), so small requests finish in a round or
+        # two; every request still advances at least slice_steps steps per
+        # round, so large ones keep their pace.  Without a budget every
+        # request advances slice_steps steps per round.
+        self.round_psteps = round_psteps
         dbytes, hbytes = C.c_size_t(), C.c_size_t()
         self._check(self.L.part_server_sizes(len(snapshots), max_items, C.byref(dbytes),
                                              C.byref(hbytes)))
         dev = snapshots[0].part.device
         arr = (C.c_void_p * len(snapshots))(*[s.part.ctx.value for s in snapshots])
-        self.ws, self.stage, self.hs, self.item_lists = [], [], [], []
+        self.ws, self.stage, self.hs, self.item_lists, self.item_arrays = [], [], [], [], []
         for _ in range(self.PIPELINE):
             ws = torch.empty(dbytes.value, dtype=torch.uint8, device=dev)
             stage = torch.empty(hbytes.value, dtype=torch.uint8, pin_memory=True)
@@ -137,6 +153,9 @@ class Server:
             self.stage.append(stage)
             self.hs.append(h)
             self.item_lists.append(self.L.part_server_items(h))
+            raw = (C.c_char * (max_items * C.sizeof(P.WorkItem))).from_address(
+                C.cast(self.item_lists[-1], C.c_void_p).value)
+            self.item_arrays.append(np.frombuffer(raw, dtype=ITEM_DTYPE))
         self.h = self.hs[0]
         self.items = self.item_lists[0]
         self.inflight = []        # (event, slot, plan) in enqueue order
@@ -251,26 +270,32 @@ class Server:
             self._reap(block=True)
         slot = self._slot
         self._slot = (self._slot + 1) % self.PIPELINE
-        its = self.item_lists[slot]
+        its = self.item_arrays[slot]
+        steps = self._steps_this_round(todo)
+        # costliest items first: the kernel's CTAs claim items in list order,
+        # so the round ends evenly (longest-processing-time-first)
+        todo.sort(key=lambda r: -steps[id(r)])
         k = 0
         plan = []
         for r in todo:
-            s = min(r.unplanned, self.slice_steps)
+            s = steps[id(r)]
             nchunks = (r.n + self.chunk - 1) // self.chunk
             if k + nchunks > self.max_items:
                 break
-            for c in range(nchunks):
-                w = its[k]
-                w.cell, w.off, w.u = r.cell.data_ptr(), r.off.data_ptr(), r.u.data_ptr()
-                w.stride = r.n
-                w.first = c * self.chunk
-                w.count = min(self.chunk, r.n - c * self.chunk)
-                w.nsteps = s
-                w.snapshot = r.snapshot
-                w.reserved = 0
-                w.q_over_m = r.q_over_m
-                w.dt = r.dt
-                k += 1
+            blk = its[k:k + nchunks]
+            first = np.arange(nchunks, dtype=np.int64) * self.chunk
+            blk["cell"] = r.cell.data_ptr()
+            blk["off"] = r.off.data_ptr()
+            blk["u"] = r.u.data_ptr()
+            blk["stride"] = r.n
+            blk["first"] = first
+            blk["count"] = np.minimum(self.chunk, r.n - first)
+            blk["nsteps"] = s
+            blk["snapshot"] = r.snapshot
+            blk["reserved"] = 0
+            blk["q_over_m"] = r.q_over_m
+            blk["dt"] = r.dt
+            k += nchunks
             r.unplanned -= s
             plan.append((r, s))
         if self._busy_from is None:
@@ -281,6 +306,28 @@ class Server:
         self.inflight.append((ev, slot, plan))
         self.rounds += 1
         return True
+
+    def _steps_this_round(self, todo):
+        """Steps each request advances in this round (see round_psteps)."""
+        if not self.round_psteps:
+            return {id(r): min(r.unplanned, self.slice_steps) for r in todo}
+        budget = float(self.round_psteps)
+        out, rest = {}, list(todo)
+        while rest:      # water-filling: whole remainders that fit an equal share
+            share = budget / len(rest)
+            fits = [r for r in rest if r.n * r.unplanned <= share]
+            if not fits:
+                break
+            for r in fits:
+                out[id(r)] = r.unplanned
+                budget -= r.n * r.unplanned
+            rest = [r for r in rest if id(r) not in out]
+        for r in rest:
+            out[id(r)] = min(r.unplanned, int(budget / len(rest) / r.n))
+        # never fewer than slice_steps: large requests keep their pace
+        for r in todo:
+            out[id(r)] = max(out[id(r)], min(r.unplanned, self.slice_steps))
+        return out
 
     def drain(self):
         """Wait for every enqueued round and complete its requests."""

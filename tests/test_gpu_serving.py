@@ -52,6 +52,19 @@ def test_request_alone_equals_mixed_and_fused_push(snaps):
     st = s2.stats()
     assert st["completed"] == 4 and st["p50_s"] is not None and st["p99_s"] >= st["p50_s"]
     s2.close()
+    # A in the same mix under a work budget per round (every request an equal
+    # share of 2e5 particle-steps per round: other slicings, same bits)
+    s3 = S.Server(torch, snaps, budget, chunk=1024, round_psteps=2e5)
+    s3.submit(0, 12000, 300, seed=21, dt=0.03)
+    s3.round()
+    a3 = s3.submit(1, 5000, 137, seed=11, dt=0.02)
+    s3.submit(1, 3000, 40, seed=31, dt=0.01)
+    s3.round()
+    s3.submit(0, 999, 7, seed=41, dt=0.05)
+    s3.run_until_idle()
+    assert _same(_state(a3), alone)
+    assert s3.stats()["completed"] == 4
+    s3.close()
     # the same request through part_gather_push (fused nsteps, one launch)
     n = 48
     p = P.Part(P.make_grid(3, n), P.MIXED, P.TSC, P.BORIS, capacity=5000)
