@@ -251,3 +251,155 @@ def test_two_ranks_one_gpu_match_one_domain(mode):
     assert not np.any(np.isnan(dep))
     tol = 1e-12 if mode == "fp64" else 1e-5
     assert np.max(np.abs(dep - ref["dep"]) / np.maximum(ref["dabs"], 1e-300)) <= tol
+
+
+def _replicated_rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2602_23434_b300 import _lib as P
+        from paper_2602_23434_b300 import multirank as M
+        torch.cuda.set_device(0)
+        dev = torch.device("cuda", 0)
+        f, x, u, w, ids, dt = _problem("fp64")
+        sel = ids % world == rank                 # particles partitioned over the ranks
+        n = int(sel.sum())
+        p = P.Part(P.make_grid(3, NG), P.FP64, P.TSC, P.BORIS, capacity=n)
+        p.set_fields(torch.as_tensor(f.reshape(6, -1)).to(dev))
+        xd = torch.as_tensor(np.ascontiguousarray(x[:, sel])).to(dev)
+        ud = torch.as_tensor(np.ascontiguousarray(u[:, sel])).to(dev)
+        wd = torch.as_tensor(np.ascontiguousarray(w[sel])).to(dev)
+        p.bind(n, xd, u=ud, w=wd)
+        p.enable_deposit(True)
+        p.sort()
+        p.gather_push(1.0, dt, 1)
+        out = torch.empty(3 * NG ** 3, dtype=torch.float64, device=dev)
+        p.deposit(out)
+        p.sync()
+        tot = M.combine_replicated(M.LibOps(p, n), dist, out)
+        torch.cuda.synchronize()
+        q.put((rank, tot.cpu().numpy()))
+    except Exception:
+        import traceback
+        q.put((rank, "error", traceback.format_exc()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_one_gpu_replicated_deposit_sum():
+    """Fields replicated, particles split by id over two ranks: the ranks'
+    deposits summed in rank order by part_sum_ordered equal the one-rank
+    oracle deposit within 1e-12 of sum |contrib|, the same bits on both."""
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_replicated_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+    for g in got:
+        assert not isinstance(g[1], str), g[2]
+    res = dict(got)
+    assert np.array_equal(res[0], res[1])
+    f, x, u, w, ids, dt = _problem("fp64")
+    g = O.make_grid(3, (NG,) * 3)
+    _, _, F, xo = O.boris_step(g, O.TSC, f.reshape(6, -1), x, u, w, 1.0, dt, True)
+    dref = O.deposit(g, O.TSC, xo, F).reshape(-1)
+    dabs = O.deposit(g, O.TSC, xo, np.abs(F)).reshape(-1)
+    assert np.max(np.abs(res[0] - dref) / np.maximum(dabs, 1e-300)) <= 1e-12
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "lp"])
+def test_exchange_pack_unpack_every_plane_bit_exact(mode):
+    """part_exchange_pack on rank 0 of a 2 x 1 x 1 split, part_exchange_unpack
+    into rank 1's context (one process): every bound plane of every leaving
+    particle arrives bit for bit, in index order, moved into the receiver's
+    frame (FP64/LP: x + L across the seam; mixed: the cell re-based), LP shock
+    flags included; the flags mark exactly the particles in halo cells."""
+    from paper_2602_23434_b300 import _lib as P
+    from paper_2602_23434_b300 import multirank as M
+    dev = torch.device("cuda", 0)
+    d0, d1 = (M.Decomp(3, (NG,) * 3, (2, 1, 1), r) for r in (0, 1))
+    rng = np.random.default_rng(5)
+    n, cap, nb = 3001, 8000, 6
+    nl = d0.n_local
+    # positions over rank 0's whole local grid: interior and both halo layers
+    s = rng.uniform(0.0, 1.0, (3, n)) * np.array(nl)[:, None]
+    s[:, :7] = [[0.0], [3.5], [4.5]]                 # exactly on the lower face
+    x = np.array(d0.xmin_local)[:, None] + s * np.array(d0.dx)[:, None]
+    ids = np.arange(n, dtype=np.int64) * 7 + 3
+    mk = {"fp64": (P.FP64, P.BORIS, 0), "mixed": (P.MIXED, P.BORIS, 0), "lp": (P.FP64, P.LP_RK2, nb)}
+    prec, mode_c, nbins = mk[mode]
+    ctx = [P.Part(d.grid(), prec, P.TSC, mode_c, capacity=cap, nbins=nbins) for d in (d0, d1)]
+
+    def buf(a, rows, dt):
+        b = torch.zeros(rows * cap, dtype=dt, device=dev)
+        b[: a.size] = torch.as_tensor(np.ascontiguousarray(a).reshape(-1)).to(dev)
+        return b
+
+    planes = {"ids": (ids, 1, torch.int64)}
+    if mode == "fp64":
+        planes.update(x=(x, 3, torch.float64), u=(rng.normal(0, 1, (3, n)), 3, torch.float64),
+                      w=(rng.uniform(0.5, 2, n), 1, torch.float64))
+    elif mode == "mixed":
+        j = np.minimum(np.floor(s), np.array(nl)[:, None] - 1).astype(np.int64)
+        cell = ((j[2] * nl[1] + j[1]) * nl[0] + j[0]).astype(np.int32)
+        planes.update(x=(cell, 1, torch.int32),
+                      off=((s - j - 0.5).astype(np.float32), 3, torch.float32),
+                      u=(rng.normal(0, 1, (6, n)).astype(np.float32), 6, torch.float32),
+                      w=(rng.uniform(0.5, 2, n).astype(np.float32), 1, torch.float32))
+    else:
+        planes.update(x=(x, 3, torch.float64), chi=(rng.uniform(0, 1, (nb, n)), nb, torch.float64),
+                      eng=(np.sort(rng.uniform(1, 10, (nb, n)), axis=0), nb, torch.float64),
+                      n_old=(rng.uniform(0.5, 2, n), 1, torch.float64))
+    b0 = {k: buf(a, r, dt) for k, (a, r, dt) in planes.items()}
+    ctx[0].bind(n, b0["x"], off=b0.get("off"), u=b0.get("u"), w=b0.get("w"), ids=b0["ids"],
+                chi=b0.get("chi"), eng=b0.get("eng"), n_old=b0.get("n_old"))
+    m = 11                                           # rank 1 already holds a few particles
+    b1 = {k: buf(np.asarray(a)[..., :m] if np.asarray(a).ndim > 1 else np.asarray(a)[:m], r, dt)
+          for k, (a, r, dt) in planes.items()}
+    ctx[1].bind(m, b1["x"], off=b1.get("off"), u=b1.get("u"), w=b1.get("w"), ids=b1["ids"],
+                chi=b1.get("chi"), eng=b1.get("eng"), n_old=b1.get("n_old"))
+    shk0 = shk1 = None
+    if mode == "lp":
+        f7 = np.ones((7, int(np.prod(nl))))
+        for c in ctx:
+            c.set_fields(torch.as_tensor(f7).to(dev))
+        shk0 = torch.as_tensor(rng.integers(0, 2, cap).astype(np.uint8)).to(dev)
+        shk1 = torch.zeros(cap, dtype=torch.uint8, device=dev)
+        ctx[0].enable_shocks(1.5, shk0)
+        ctx[1].enable_shocks(1.5, shk1)
+    sh0 = shk0.cpu().numpy()[:n].copy() if shk0 is not None else None
+    to_l, to_r = d0.shifts(0)
+    lo, hi = d0.interior[0]
+    leaving = torch.zeros(n, dtype=torch.uint8, device=dev)
+    big = torch.empty(ctx[0].exchange_bytes(n) + 8, dtype=torch.uint8, device=dev)
+    big2 = torch.empty_like(big)
+    kl, kr, ok = ctx[0].exchange_pack(0, lo, hi, to_l, to_r, big, big2, leaving)
+    assert ok
+    torch.cuda.synchronize()
+    # the library's own rounding of s = (x - xmin) / dx (the cell index in mixed form)
+    sx = s[0] if mode == "mixed" else (x[0] - d0.xmin_local[0]) * (1.0 / d0.dx[0])
+    left, right = sx < lo, sx >= hi
+    assert (kl, kr) == (int(left.sum()), int(right.sum())) and kl > 0 and kr > 0
+    assert np.array_equal(leaving.cpu().numpy(), (left | right).astype(np.uint8))
+    # the right-moving ones into rank 1 (its left neighbour is rank 0)
+    ctx[1].exchange_unpack(kr, big2[: ctx[1].exchange_bytes(kr)])
+    ctx[1].sync()
+    sel = np.nonzero(right)[0]
+    tot = m + kr
+    for k, (a, rows, dt) in planes.items():
+        got = b1[k][: rows * tot].view(rows, tot).cpu().numpy()[:, m:]
+        want = np.asarray(a).reshape(rows, -1)[:, sel].copy()
+        if k == "x" and mode != "mixed":
+            want[0] = want[0] + to_r[0]
+        if k == "x" and mode == "mixed":
+            c = want[0].astype(np.int64)
+            jx, jy, jz = c % nl[0], (c // nl[0]) % nl[1], c // (nl[0] * nl[1])
+            n1 = d1.n_local
+            want[0] = ((jz * n1[1] + jy) * n1[0] + jx + to_r[1]).astype(np.int32)
+        assert np.array_equal(got, want), k
+    if mode == "lp":
+        assert np.array_equal(shk1.cpu().numpy()[m:tot], sh0[sel])
