@@ -916,6 +916,7 @@ def reference_arm(args):
     sample = (f"{Ns} of the {N} particles of the 128^3 workload per step, {W} warm-up + {K} "
               f"timed steps (keys, stable sort, permute, Boris step, deposit), {el:.1f} s timed")
     cfg = headline_config(128, N, dt, 1)
+    cfg["parallelism"] = f"the oracle, OpenMP over particles on {O.max_threads()} host cores"
     cfg["sample_particles_per_step"] = Ns
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
             "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": el / K * 1e3,
