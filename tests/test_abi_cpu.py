@@ -83,3 +83,30 @@ def test_size_limits(L):
     b = (C.c_int * 3)()
     nk = C.c_int64()
     assert L.part_brick_dims(C.byref(g), b, C.byref(nk)) == 0 and nk.value == 1 << 30
+
+
+def test_multirank_and_probe_entry_points_refuse_bad_arguments(L):
+    """The several-rank helpers and the FP64 probe check their arguments on
+    the host before any device call (PART_EINVAL = 1)."""
+    I3 = C.c_int * 3
+    dims, lo, ext = I3(4, 4, 4), I3(0, 0, 0), I3(4, 4, 1)
+    src = C.c_void_p(0x1000)
+    assert L.part_box_pack(None, 3, dims, lo, ext, src, None) == 1            # NULL source
+    assert L.part_box_pack(src, 0, dims, lo, ext, src, None) == 1             # ncomp < 1
+    assert L.part_box_add(src, 3, dims, I3(0, 0, 3), I3(4, 4, 2), src, None) == 1  # outside
+    assert b"outside" in L.part_last_error(None)
+    assert L.part_box_pack(C.c_void_p(0x1004), 3, dims, lo, ext, src, None) == 1   # unaligned
+    assert L.part_sum_ordered(None, src, 10, 2, None) == 1
+    assert L.part_sum_ordered(src, src, 10, 0, None) == 1
+    assert L.part_sum_ordered(src, src, -1, 2, None) == 1
+    sz = C.c_size_t()
+    assert L.part_exchange_bytes(None, 10, C.byref(sz)) == 1
+    n = C.c_int64 * 2
+    sh = P.XShift(0.0, 0, 4)
+    assert L.part_exchange_pack(None, 0, 1, 2, C.byref(sh), C.byref(sh), None, 0, None, 0,
+                                None, n()) == 1
+    assert L.part_exchange_unpack(None, 1, None, 0) == 1
+    tf, ms = C.c_double(), C.c_double()
+    assert L.part_probe_fp64_fma(None, None, 4, 8192, 5, C.byref(tf), C.byref(ms)) == 1
+    assert L.part_probe_fp64_fma(None, src, 9, 8192, 5, C.byref(tf), C.byref(ms)) == 1
+    assert L.part_probe_fp64_fma(None, src, 4, 0, 5, C.byref(tf), C.byref(ms)) == 1
