@@ -55,11 +55,11 @@ FLOP_PER_PSTEP_BORIS_DEP = 12 + 24 + 360 + 58 + 17 + 178
 BYTES_PER_PSTEP_BORIS_DEP = 96 + 8 + 6 + 3
 # DRAM bytes (read + write) per particle of one launch of the FP64 brick kernel,
 # from an ncu capture of the kernel on the 64^3 case of the same workload (
-# 265.6 MB for 2,097,152 particles), scaled to a launch by the particle count.
-TRAFFIC_PER_PARTICLE_BRICK_F64 = 265.092864e6 / 2097152  # ncu dram r+w, 64^3 capture
+# 265.0 MB for 2,097,152 particles), scaled to a launch by the particle count.
+TRAFFIC_PER_PARTICLE_BRICK_F64 = 264.987392e6 / 2097152  # ncu dram r+w, 64^3 capture
 # Same for the mixed brick kernel, from an ncu capture of the 128^3 case
-# (1714.9 MB for 16,777,216 particles).
-TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1714.857728e6 / 16777216   # ncu dram r+w, 128^3 capture
+# (1715.1 MB for 16,777,216 particles).
+TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1715.104512e6 / 16777216   # ncu dram r+w, 128^3 capture
 # LP step: x r/w 48, chi+eng r/w 4096 (128 bins), n_old r/w 16, samples w+r 48,
 # fields: 7 comps * 8 B per cell / 2 LPs per cell, 3 gathers at ~one cell = 84
 BYTES_PER_LPSTEP = 48 + 4096 + 16 + 48 + 84
