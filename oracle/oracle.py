@@ -134,7 +134,11 @@ def load(path: str):
         "or_dsa_index": (C.c_double, [C.c_double]),
         "or_shock_cells": (None, [G, _D, _D, C.c_double, _D]),
         "or_shock_convolve": (None, [C.c_int, _D, _D, C.c_double, C.c_double, _D]),
-        "or_lp_shock": (None, [G, _D, C.c_int, C.c_int64, _D, _D, _D,
+        "or_kw_index": (C.c_double, [C.c_double, C.c_double]),
+        "or_shock_frame_speeds": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double,
+                                            C.c_double, C.c_double, _D, _D]),
+        "or_shock_slopes": (None, [G, _D, _D, _D, C.c_int, _D]),
+        "or_lp_shock": (None, [G, _D, _D, C.c_int, C.c_int64, _D, _D, _D,
                                C.POINTER(C.c_uint8)]),
     }
     for name, (res, args) in sig.items():
@@ -331,6 +335,28 @@ def shock_cells(g: Grid, vel, rho, r_min: float):
     return out
 
 
+def kw_index(beta_u: float, beta_d: float) -> float:
+    """Eq. slope for a relativistic shock from its shock-frame flow speeds."""
+    return lib().or_kw_index(beta_u, beta_d)
+
+
+def shock_frame_speeds(v_u, s2_u, rho_u, v_d, s2_d, rho_d):
+    """(beta_u, beta_d) in the shock frame, or None where there is none."""
+    bu, bd = C.c_double(), C.c_double()
+    ok = lib().or_shock_frame_speeds(v_u, s2_u, rho_u, v_d, s2_d, rho_d,
+                                     C.byref(bu), C.byref(bd))
+    return (bu.value, bd.value) if ok else None
+
+
+def shock_slopes(g: Grid, vel, rho, r_cell, relativistic: bool):
+    """Per-cell q of Eq. slope for the shock cells r_cell > 0, shape [G]."""
+    rho = _f64(rho).reshape(-1)
+    out = np.zeros(rho.shape[0])
+    lib().or_shock_slopes(C.byref(g), _d(_f64(vel).reshape(3, -1)), _d(rho),
+                          _d(_f64(r_cell)), int(bool(relativistic)), _d(out))
+    return out
+
+
 def shock_convolve(eng, chi, q: float, cn: float):
     """Eq. convolution_spectra on one spectrum; returns chi_out."""
     eng, chi = _f64(eng), _f64(chi)
@@ -339,13 +365,16 @@ def shock_convolve(eng, chi, q: float, cn: float):
     return out
 
 
-def lp_shock(g: Grid, r_cell, x, chi, eng, state):
-    """Shock update on copies; returns (chi, state)."""
+def lp_shock(g: Grid, r_cell, x, chi, eng, state, q_cell=None):
+    """Shock update on copies; returns (chi, state).  q_cell: per-cell index
+    of Eq. slope (None: 3r/(r-1))."""
     chi = _f64(chi).copy()
     st = np.ascontiguousarray(state, dtype=np.uint8).copy()
     nb, n = chi.shape
-    lib().or_lp_shock(C.byref(g), _d(_f64(r_cell)), nb, n, _d(_f64(x)), _d(chi),
-                      _d(_f64(eng)), st.ctypes.data_as(C.POINTER(C.c_uint8)))
+    qc = None if q_cell is None else _f64(q_cell)
+    lib().or_lp_shock(C.byref(g), _d(_f64(r_cell)), None if qc is None else _d(qc), nb, n,
+                      _d(_f64(x)), _d(chi), _d(_f64(eng)),
+                      st.ctypes.data_as(C.POINTER(C.c_uint8)))
     return chi, st
 
 

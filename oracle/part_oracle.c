@@ -462,6 +462,105 @@ double or_rh_compression(double gamma, double mach) {
  * shock (the relativistic correction q_R is zero): q = 3r/(r-1).            */
 double or_dsa_index(double r) { return 3.0 * r / (r - 1.0); }
 
+/* Eq. slope for a relativistic shock.  The paper adds a correction q_R that
+ * depends on the upstream and downstream flow speeds and takes its form from
+ * the literature; this oracle takes the index of Keshet & Waxman (2005) for
+ * isotropic small-angle scattering, with beta_u > beta_d the normal flow
+ * speeds on either side in the shock's rest frame, in units of c:
+ *   q = (3 beta_u - 2 beta_u beta_d^2 + beta_d^3) / (beta_u - beta_d),
+ * i.e. q_R = q - 3r/(r-1).  At small speeds mass conservation gives
+ * beta_u / beta_d = r and q -> 3r/(r-1); an ultra-relativistic shock
+ * (beta_u -> 1, beta_d -> 1/3) gives q = 38/9, the energy index 20/9.      */
+double or_kw_index(double beta_u, double beta_d) {
+  return (3.0 * beta_u - 2.0 * beta_u * beta_d * beta_d + beta_d * beta_d * beta_d) /
+         (beta_u - beta_d);
+}
+
+/* Normal flow speeds on both sides of a shock in its rest frame.  Inputs:
+ * the lab-frame velocity component v along the shock normal, the squared
+ * speed s2 = |v|^2 (all components; c = 1), and the proper density rho, for
+ * the upstream (u) and downstream (d) states.  The lab-frame mass density is
+ * D = rho / sqrt(1 - s2); continuity, d_t D + d_n (D v) = 0, across a front
+ * moving at v_sh requires v_sh (D_d - D_u) = D_d v_d - D_u v_u.  A boost
+ * along the normal by v_sh turns a normal velocity v into
+ * (v - v_sh) / (1 - v v_sh) (relativistic velocity addition); the speeds are
+ * the magnitudes of those.  Returns 0 (no frame) if a speed is not below 1,
+ * D_d = D_u, |v_sh| >= 1, or the flow does not slow down across the front
+ * (beta_d >= beta_u); NaN inputs fail these tests too.                     */
+int or_shock_frame_speeds(double v_u, double s2_u, double rho_u, double v_d, double s2_d,
+                          double rho_d, double* beta_u, double* beta_d) {
+  if (!(s2_u < 1.0 && s2_d < 1.0)) return 0;
+  double D_u = rho_u / sqrt(1.0 - s2_u);
+  double D_d = rho_d / sqrt(1.0 - s2_d);
+  if (!(D_d != D_u)) return 0;
+  double v_sh = (D_d * v_d - D_u * v_u) / (D_d - D_u);
+  if (!(fabs(v_sh) < 1.0)) return 0;
+  double bu = fabs((v_u - v_sh) / (1.0 - v_u * v_sh));
+  double bd = fabs((v_d - v_sh) / (1.0 - v_d * v_sh));
+  if (!(bd < bu)) return 0;
+  *beta_u = bu;
+  *beta_d = bd;
+  return 1;
+}
+
+/* Index q of Eq. slope for every shock cell of or_shock_cells (r_cell > 0;
+ * q_cell = 0 elsewhere).  relativistic = 0: q = 3r/(r-1).  relativistic = 1:
+ * along the axis that set r (the first axis with the largest ratio, as in
+ * or_shock_cells) the lower-density neighbour is upstream and the other one
+ * downstream; q = or_kw_index of their shock-frame speeds
+ * (or_shock_frame_speeds), or 3r/(r-1) where no shock frame exists.        */
+void or_shock_slopes(const or_grid* g, const double* vel, const double* rho,
+                     const double* r_cell, int relativistic, double* q_cell) {
+  int64_t G = (int64_t)g->n[0] * g->n[1] * g->n[2];
+  for (int jz = 0; jz < g->n[2]; ++jz)
+    for (int jy = 0; jy < g->n[1]; ++jy)
+      for (int jx = 0; jx < g->n[0]; ++jx) {
+        int64_t c = cell_linear(g, jx, jy, jz);
+        double r = r_cell[c];
+        if (!(r > 0.0)) {
+          q_cell[c] = 0.0;
+          continue;
+        }
+        double q = or_dsa_index(r);
+        if (relativistic) {
+          int j[3] = {jx, jy, jz};
+          double best = 0.0;
+          int64_t up = -1, down = -1;
+          int axis = -1;
+          for (int a = 0; a < g->dim; ++a) {
+            int jp[3] = {jx, jy, jz}, jm[3] = {jx, jy, jz};
+            jp[a] = nbr(g, a, j[a] + 1);
+            jm[a] = nbr(g, a, j[a] - 1);
+            int64_t cp = cell_linear(g, jp[0], jp[1], jp[2]);
+            int64_t cm = cell_linear(g, jm[0], jm[1], jm[2]);
+            if (vel[a * G + cp] - vel[a * G + cm] < 0.0) {
+              int64_t dn = rho[cp] > rho[cm] ? cp : cm;   /* denser side: downstream */
+              int64_t un = dn == cp ? cm : cp;
+              double rr = rho[dn] / rho[un];
+              if (rr > best) {
+                best = rr;
+                axis = a;
+                down = dn;
+                up = un;
+              }
+            }
+          }
+          if (axis >= 0) {
+            double s2u = 0.0, s2d = 0.0;
+            for (int a = 0; a < 3; ++a) {
+              s2u += vel[a * G + up] * vel[a * G + up];
+              s2d += vel[a * G + down] * vel[a * G + down];
+            }
+            double bu, bd;
+            if (or_shock_frame_speeds(vel[axis * G + up], s2u, rho[up], vel[axis * G + down],
+                                      s2d, rho[down], &bu, &bd))
+              q = or_kw_index(bu, bd);
+          }
+        }
+        q_cell[c] = q;
+      }
+}
+
 /* Shock cells.  The paper leaves the detection criterion to the fluid code;
  * this oracle uses: cell c is a shock cell if, along some axis a < dim, the
  * flow converges across c (v_a(c + e_a) - v_a(c - e_a) < 0) and the density
@@ -524,12 +623,13 @@ void or_shock_convolve(int nb, const double* eng, const double* chi_in, double q
 /* Shock update of the LP spectra after a step's smooth update.  An LP whose
  * cell at x (the cell containing it) is a shock cell, and that was not in a
  * shock cell at the end of its previous step (state[p] == 0), takes
- * Eq. convolution_spectra with q = or_dsa_index(r) and cn = q / r: the
- * test-particle solution conserves particle number per unit fluid density,
- * chi = N/n (Eq. chi), across a jump n_d = r n_u.  state[p] becomes 1 in a
- * shock cell and 0 elsewhere.  chi, eng bin-major [nb][n].                  */
-void or_lp_shock(const or_grid* g, const double* r_cell, int nb, int64_t n, const double* x,
-                 double* chi, const double* eng, uint8_t* state) {
+ * Eq. convolution_spectra with the cell's q (q_cell, or or_dsa_index(r) when
+ * q_cell is NULL) and cn = q / r: the non-relativistic test-particle solution
+ * conserves particle number per unit fluid density, chi = N/n (Eq. chi),
+ * across a jump n_d = r n_u.  state[p] becomes 1 in a shock cell and 0
+ * elsewhere.  chi, eng bin-major [nb][n].                                   */
+void or_lp_shock(const or_grid* g, const double* r_cell, const double* q_cell, int nb,
+                 int64_t n, const double* x, double* chi, const double* eng, uint8_t* state) {
 #pragma omp parallel
   {
     double* e = (double*)malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1));
@@ -540,10 +640,11 @@ void or_lp_shock(const or_grid* g, const double* r_cell, int nb, int64_t n, cons
       double xp[3] = {x[p], x[n + p], x[2 * n + p]};
       int j[3]; double d[3];
       or_cell_coord(g, xp, j, d);
-      double r = r_cell[cell_linear(g, j[0], j[1], j[2])];
+      int64_t c = cell_linear(g, j[0], j[1], j[2]);
+      double r = r_cell[c];
       if (r > 0.0) {
         if (!state[p]) {
-          double q = or_dsa_index(r);
+          double q = q_cell ? q_cell[c] : or_dsa_index(r);
           for (int i = 0; i < nb; ++i) {
             e[i] = eng[(int64_t)i * n + p];
             ci[i] = chi[(int64_t)i * n + p];

@@ -14,12 +14,14 @@
  *   Eq. cr_chi          d chi/d tau + d_eps[(-eps/3 div u - c_r eps^2) chi] = 0
  *   Eq. initSpec        chi_i = N0 (1-p)/(emax^(1-p)-emin^(1-p)) eps_i^-p  (Sec. 4.1.2)
  *   Eq. convolution_spectra  chi_out = C int chi_in (eps/eps')^(2-q) d eps'/eps'  (Sec. 2)
- *   Eq. slope           q(r) = 3r/(r-1) (+ q_R, zero for non-relativistic shocks)
+ *   Eq. slope           q(r) = 3r/(r-1) + q_R(r, beta_u, beta_d)
  *   Rankine-Hugoniot    r = (gamma+1) M^2/(2 + (gamma-1) M^2)      (Sec. 4.1.2)
  *   Appendix A          particle record: pos, speed, chi[128], eng[128], id
  * Where the paper is silent the oracle uses textbook definitions:
  *   TSC / CIC shape functions (Hockney & Eastwood), relativistic Boris push
- *   (Boris 1970; Birdsall & Langdon), Philox4x32-10 (Salmon et al., SC'11).
+ *   (Boris 1970; Birdsall & Langdon), Philox4x32-10 (Salmon et al., SC'11),
+ *   and for q_R of Eq. slope the index of Keshet & Waxman (2005, PRL 94,
+ *   111102), one of the works the paper cites for it.
  *
  * Parity unpinned: the absolute synchrotron coefficient scaling (c0, U_B in
  * code units) -- the paper gives c_r only in cgs form.
@@ -107,9 +109,22 @@ void or_shock_cells(const or_grid* g, const double* vel, const double* rho, doub
 /* Eq. convolution_spectra on one spectrum (piecewise power law in chi_in) */
 void or_shock_convolve(int nb, const double* eng, const double* chi_in, double q, double cn,
                        double* chi_out);
-/* shock update of n LP spectra at positions x; state[n] = inside a shock cell */
-void or_lp_shock(const or_grid* g, const double* r_cell, int nb, int64_t n, const double* x,
-                 double* chi, const double* eng, uint8_t* state);
+/* Eq. slope for a relativistic shock: the index from the upstream and
+ * downstream normal flow speeds in the shock frame (units of c) */
+double or_kw_index(double beta_u, double beta_d);
+/* shock-frame normal speeds from lab-frame normal velocities v, squared
+ * speeds s2 (all components, for the Lorentz factors) and proper densities;
+ * 1 on success, 0 where no shock frame exists */
+int or_shock_frame_speeds(double v_u, double s2_u, double rho_u, double v_d, double s2_d,
+                          double rho_d, double* beta_u, double* beta_d);
+/* per-cell q of Eq. slope for the shock cells r_cell > 0 (0 elsewhere);
+ * relativistic = 0: 3r/(r-1); 1: with q_R from the cell's neighbours */
+void or_shock_slopes(const or_grid* g, const double* vel, const double* rho,
+                     const double* r_cell, int relativistic, double* q_cell);
+/* shock update of n LP spectra at positions x; state[n] = inside a shock cell;
+ * q_cell = the per-cell index (NULL: 3r/(r-1)) */
+void or_lp_shock(const or_grid* g, const double* r_cell, const double* q_cell, int nb,
+                 int64_t n, const double* x, double* chi, const double* eng, uint8_t* state);
 /* OpenMP thread count of the loops above (timing only) */
 void or_set_threads(int n);
 int or_max_threads(void);

@@ -173,6 +173,38 @@ MUTANTS = {
         "double ratio = hi / lo;",
         "double ratio = lo / hi;",
         [pins.test_shock_cells_on_the_rh_snapshot]),
+    "kw_index_middle_term_sign": (
+        "return (3.0 * beta_u - 2.0 * beta_u * beta_d * beta_d + beta_d * beta_d * beta_d) /",
+        "return (3.0 * beta_u + 2.0 * beta_u * beta_d * beta_d + beta_d * beta_d * beta_d) /",
+        [pins.test_kw_index_limits]),
+    "kw_index_cubic_term_dropped": (
+        "return (3.0 * beta_u - 2.0 * beta_u * beta_d * beta_d + beta_d * beta_d * beta_d) /",
+        "return (3.0 * beta_u - 2.0 * beta_u * beta_d * beta_d) /",
+        [pins.test_kw_index_limits]),
+    "shock_speed_from_proper_density": (
+        "double v_sh = (D_d * v_d - D_u * v_u) / (D_d - D_u);",
+        "double v_sh = (rho_d * v_d - rho_u * v_u) / (rho_d - rho_u);",
+        [pins.test_shock_frame_speeds_recover_a_boosted_shock]),
+    "shock_frame_galilean": (
+        "double bu = fabs((v_u - v_sh) / (1.0 - v_u * v_sh));",
+        "double bu = fabs(v_u - v_sh);",
+        [pins.test_shock_frame_speeds_recover_a_boosted_shock]),
+    "shock_lorentz_tangential_dropped": (
+        "double D_u = rho_u / sqrt(1.0 - s2_u);",
+        "double D_u = rho_u / sqrt(1.0 - v_u * v_u);",
+        [pins.test_shock_frame_speeds_recover_a_boosted_shock]),
+    "slopes_upstream_side_fixed": (
+        "int64_t un = dn == cp ? cm : cp;",
+        "int64_t un = cm;",
+        [pins.test_shock_slopes_on_a_relativistic_snapshot]),
+    "slopes_normal_component_transposed": (
+        "if (or_shock_frame_speeds(vel[axis * G + up], s2u, rho[up], vel[axis * G + down],",
+        "if (or_shock_frame_speeds(vel[(1 - axis) * G + up], s2u, rho[up], vel[axis * G + down],",
+        [pins.test_shock_slopes_on_a_relativistic_snapshot]),
+    "lp_shock_ignores_cell_slope": (
+        "double q = q_cell ? q_cell[c] : or_dsa_index(r);",
+        "double q = or_dsa_index(r);",
+        [pins.test_lp_shock_takes_the_cell_slope]),
     "open_axis_upper_clamp_dropped": (
         "if (s > (double)g->n[a]) s = (double)g->n[a];",
         ";",

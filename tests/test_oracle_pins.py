@@ -764,6 +764,116 @@ def test_shock_cells_on_the_rh_snapshot():
     assert np.all(O.shock_cells(g, v2, r2, 1.5) == 0.0)
 
 
+def test_kw_index_limits():
+    """Eq. slope with q_R (Keshet & Waxman 2005): an ultra-relativistic shock,
+    beta_u = 1 and beta_d = 1/3 (downstream sound speed c/sqrt(3)), gives the
+    energy index q - 2 = 20/9; slow shocks, beta_u / beta_d = r, reduce to the
+    non-relativistic 3r/(r-1) with a correction O(beta^2); a strong slow shock
+    (r = 4) gives q = 4."""
+    assert abs(O.kw_index(1.0, 1.0 / 3.0) - 38.0 / 9.0) < 2e-15
+    for r in (4.0, 40.0 / 11.0, 1.7):
+        for b in (1e-3, 1e-5):
+            q = O.kw_index(b, b / r)
+            q0 = 3.0 * r / (r - 1.0)
+            assert abs(q - q0) <= 3.0 * b * b * q0          # O(beta^2) correction
+            assert q < q0                                    # and it steepens less
+    # a moderately relativistic pair by hand: (2.7 - 0.2205 + 0.042875) / 0.55
+    assert abs(O.kw_index(0.9, 0.35) - 2.522375 / 0.55) < 1e-14
+
+
+def _boosted_shock(beta_b, bu=0.9, btu=0.2, bd=0.35, btd=0.1, rho_u=1.0):
+    """A shock at rest in its own frame (normal speeds bu > bd, tangential
+    btu, btd, proper densities with the mass flux Gamma rho beta_n equal on
+    both sides), seen from a frame in which the shock moves at beta_b along
+    the normal.  Returns lab-frame (v_n, v_t, rho) upstream and downstream."""
+    def gam(b2):
+        return 1.0 / np.sqrt(1.0 - b2)
+    rho_d = gam(bu * bu + btu * btu) * rho_u * bu / (gam(bd * bd + btd * btd) * bd)
+    gb = gam(beta_b * beta_b)
+
+    def lab(bn, bt):
+        den = 1.0 + bn * beta_b
+        return (bn + beta_b) / den, bt / (gb * den)
+    return lab(bu, btu) + (rho_u,), lab(bd, btd) + (rho_d,)
+
+
+def test_shock_frame_speeds_recover_a_boosted_shock():
+    """Whatever frame a shock is seen from, the shock-frame normal speeds are
+    recovered (lab-frame mass D = Gamma rho with the tangential motion in
+    Gamma, velocity addition along the normal), for either flow direction;
+    no frame exists for superluminal, equal-mass or expanding states."""
+    for beta_b in (-0.6, 0.0, 0.3, 0.8):
+        for sgn in (1.0, -1.0):                 # -1: the same shock mirrored
+            (vu, tu, ru), (vd, td, rd) = _boosted_shock(beta_b)
+            vu, vd = sgn * vu, sgn * vd
+            got = O.shock_frame_speeds(vu, vu * vu + tu * tu, ru, vd, vd * vd + td * td, rd)
+            assert got is not None
+            assert abs(got[0] - 0.9) < 1e-13 and abs(got[1] - 0.35) < 1e-13
+    assert O.shock_frame_speeds(0.5, 1.0, 1.0, 0.1, 0.01, 3.0) is None      # |v| = 1
+    assert O.shock_frame_speeds(0.5, 0.25, 2.0, 0.5, 0.25, 2.0) is None     # D_d = D_u
+    assert O.shock_frame_speeds(0.1, 0.01, 3.0, 0.5, 0.25, 1.0) is None     # speeds up
+
+
+def _rel_snapshot(n, beta_b, mirror=False):
+    """The boosted shock of _boosted_shock on [-1,1]^2, front at x = 0:
+    upstream on the side the flow comes from.  vel [3][1][n][n], rho."""
+    (vu, tu, ru), (vd, td, rd) = _boosted_shock(beta_b)
+    xc = -1.0 + (np.arange(n) + 0.5) * (2.0 / n)
+    down = np.broadcast_to((xc < 0.0 if mirror else xc > 0.0)[None, :], (n, n))
+    s = -1.0 if mirror else 1.0
+    vel = np.zeros((3, 1, n, n))
+    vel[0, 0] = np.where(down, s * vd, s * vu)
+    vel[1, 0] = np.where(down, td, tu)
+    rho = np.where(down, rd, ru)[None]
+    return vel, rho
+
+
+def test_shock_slopes_on_a_relativistic_snapshot():
+    """The two shock columns of a moving relativistic shock take the index of
+    its shock-frame speeds, whichever way the flow runs; without the
+    correction they take 3r/(r-1) of their ratio."""
+    n = 32
+    g = O.make_grid(2, (n, n, 1))
+    q_true = O.kw_index(0.9, 0.35)
+    for beta_b in (0.0, 0.3, -0.5):
+        for mirror in (False, True):
+            vel, rho = _rel_snapshot(n, beta_b, mirror)
+            rc = O.shock_cells(g, vel, rho, 1.5)
+            assert np.count_nonzero(rc) == 2 * n
+            q0 = O.shock_slopes(g, vel, rho, rc, False)
+            assert np.all(q0[rc > 0] == np.array([O.dsa_index(r) for r in rc[rc > 0]]))
+            assert np.all(q0[rc == 0] == 0.0)
+            q1 = O.shock_slopes(g, vel, rho, rc, True)
+            assert np.max(np.abs(q1[rc > 0] - q_true)) < 1e-12 * q_true
+            assert np.all(q1[rc == 0] == 0.0)
+    # a slow shock: the correction is O(v^2)
+    vel, rho = _shock_snapshot(n, 40.0 / 11.0, v_u=1e-4)
+    rc = O.shock_cells(g, vel, rho, 1.5)
+    q1 = O.shock_slopes(g, vel, rho, rc, True)
+    assert np.max(np.abs(q1[rc > 0] / O.dsa_index(40.0 / 11.0) - 1.0)) < 1e-7
+
+
+def test_lp_shock_takes_the_cell_slope():
+    """With per-cell indices the convolution uses the LP's cell q and
+    cn = q / r."""
+    n = 32
+    g = O.make_grid(2, (n, n, 1))
+    vel, rho = _rel_snapshot(n, 0.3)
+    rc = O.shock_cells(g, vel, rho, 1.5)
+    qc = O.shock_slopes(g, vel, rho, rc, True)
+    x = np.array([[-0.01, -0.5], [0.3, 0.3], [0.0, 0.0]])   # LP 0 in a shock cell
+    eng1, chi1 = O.init_spectrum(64, 1e2, 1e4, 9.0, 1e-6)
+    eng = np.repeat(eng1[:, None], 2, axis=1)
+    chi = np.repeat(chi1[:, None], 2, axis=1)
+    c1, s1 = O.lp_shock(g, rc, x, chi, eng, np.zeros(2, np.uint8), q_cell=qc)
+    c0 = int((0.3 + 1.0) / (2.0 / n)) * n + n // 2 - 1     # LP 0's cell
+    r, q = rc[c0], qc[c0]
+    assert r > 0.0
+    assert q != O.dsa_index(r)
+    assert np.array_equal(c1[:, 0], O.shock_convolve(eng1, chi1, q, q / r))
+    assert np.array_equal(c1[:, 1], chi1) and s1.tolist() == [1, 0]
+
+
 def test_lp_shock_applies_once_per_crossing():
     """An LP sitting in a shock cell is convolved once; after leaving the
     shock its state resets."""
