@@ -267,9 +267,10 @@ part_status spec_update(part_ctx* ctx, double dt, double c0, double u_rad);
  * elsewhere).  spec_update applies Eq. convolution_spectra to each listed LP
  * after the smooth update:
  *   chi(eps_i) <- cn * integral_{eps_0}^{eps_i} chi(e) (eps_i/e)^(2-q) de/e,
- * q = 3r/(r-1) (Eq. slope; the relativistic correction q_R is not built),
- * cn = q/r (particle number per unit fluid density is conserved across the
- * jump n_d = r n_u), chi between adjacent bins taken as the power law through
+ * q = the index of Eq. slope of the LP's shock cell (part_set_shock_slope),
+ * cn = q/r (for a non-relativistic shock, particle number per unit fluid
+ * density is conserved across the jump n_d = r n_u), the q and r being those
+ * of the cell at the push, chi between adjacent bins taken as the power law through
  * the two bin values, eps_0 = the LP's lowest bin energy (chi there becomes
  * 0).  Bin energies are unchanged.  Requires bound particles and fields.   */
 part_status part_enable_shocks(part_ctx* ctx, double r_min, uint8_t* state);
@@ -277,6 +278,30 @@ part_status part_enable_shocks(part_ctx* ctx, double r_min, uint8_t* state);
 /* Device pointer to the shock cells r[G] (cell order as the fields; 0 = no
  * shock), valid while shocks are enabled and the fields are unchanged.     */
 part_status part_shock_cells(part_ctx* ctx, const double** r_cell, int64_t* ncells);
+
+/* Index q of Eq. slope, q(r) = 3r/(r-1) + q_R (PART_LP_RK2 only).
+ * relativistic = 0 (the default): q_R = 0, the non-relativistic shock.
+ * relativistic = 1: q_R from the flow speeds on both sides of the shock
+ * (velocities in units of c, as in the LP push's gamma_g).  The paper takes
+ * q_R from the literature; this library uses the index of Keshet & Waxman
+ * (2005, PRL 94, 111102), one of the works it cites:
+ *   q = (3 b_u - 2 b_u b_d^2 + b_d^3) / (b_u - b_d),
+ * b_u > b_d the normal flow speeds upstream and downstream in the shock's
+ * rest frame.  For a shock cell whose ratio r was set along axis a, the
+ * neighbour along a with the lower density is upstream and the other one
+ * downstream; the shock moves at v_sh = (D_d v_d - D_u v_u)/(D_d - D_u), the
+ * speed that conserves the lab-frame mass D = rho/sqrt(1 - |v|^2) across it
+ * (v: the a components; |v|: all three), and there the normal speeds are
+ * |v - v_sh|/(1 - v v_sh).  Where that frame does not exist (a speed >= 1,
+ * D_d = D_u, |v_sh| >= 1, or b_d >= b_u) the cell keeps 3r/(r-1).
+ * Recomputes the shock cells when shocks are enabled; otherwise the setting
+ * is taken up by part_enable_shocks.  It survives part_bind_particles.
+ * Errors: PART_EINVAL for another mode or relativistic not 0/1.           */
+part_status part_set_shock_slope(part_ctx* ctx, int relativistic);
+
+/* Device pointer to the per-cell index q[G] of Eq. slope (0 = no shock),
+ * valid like part_shock_cells.                                             */
+part_status part_shock_slopes(part_ctx* ctx, const double** q_cell, int64_t* ncells);
 
 /* Initialise the bound particles on the device from Philox4x32-10 draws
  * (key = seed; counter (p, 0) -> uniform position over the domain, counter

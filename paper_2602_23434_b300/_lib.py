@@ -107,6 +107,8 @@ def lib():
         "part_flush": (st, [P]),
         "part_set_outflow": (st, [P, P]),
         "part_shock_cells": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
+        "part_set_shock_slope": (st, [P, C.c_int]),
+        "part_shock_slopes": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
         "part_enable_deposit": (st, [P, C.c_int]),
         "part_gather_push": (st, [P, C.c_double, C.c_double, C.c_int]),
         "part_deposit": (st, [P, P]),
@@ -274,6 +276,18 @@ class Part:
         p = C.c_void_p()
         nc = C.c_int64()
         self._check(self.L.part_shock_cells(self.ctx, C.byref(p), C.byref(nc)))
+        off = p.value - self.ws.data_ptr()
+        return self.ws[off: off + 8 * nc.value].view(self.torch.float64)
+
+    def set_shock_slope(self, relativistic: bool):
+        """Eq. slope with (True) or without (False, the default) q_R."""
+        self._check(self.L.part_set_shock_slope(self.ctx, 1 if relativistic else 0))
+
+    def shock_slopes(self):
+        """View of the per-cell index q[G] of Eq. slope (0: no shock)."""
+        p = C.c_void_p()
+        nc = C.c_int64()
+        self._check(self.L.part_shock_slopes(self.ctx, C.byref(p), C.byref(nc)))
         off = p.value - self.ws.data_ptr()
         return self.ws[off: off + 8 * nc.value].view(self.torch.float64)
 

@@ -152,7 +152,8 @@ namespace {
 
 struct Layout {
   size_t fpad, keys0, keys1, vals0, vals1, hist, hsum, cstart, tmp, dpart, samples, status,
-      alt_x, alt_off, alt_u, alt_w, alt_id, shock_r, shock_list, shock_rs, cstart_alt, bcount,
+      alt_x, alt_off, alt_u, alt_w, alt_id, shock_r, shock_q, shock_list, shock_rs, shock_qs,
+      cstart_alt, bcount,
       bsum, bslot, lpcache, total;
 };
 
@@ -199,8 +200,10 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   // LP mode: shock cells and the list of LPs shocked by the last push
   const bool lp = mode == PART_LP_RK2;
   L.shock_r = take(lp ? (size_t)g.G * 8 : 0);
+  L.shock_q = take(lp ? (size_t)g.G * 8 : 0);
   L.shock_list = take(lp ? (size_t)(c1 + 1) * 4 : 0);
   L.shock_rs = take(lp ? (size_t)c1 * 8 : 0);
+  L.shock_qs = take(lp ? (size_t)c1 * 8 : 0);
   L.lpcache = take(lp ? (size_t)6 * c1 * 8 : 0);
   // Boris modes: second cell_start and the brick counts of the incremental sort
   L.cstart_alt = take(alt ? (size_t)(g.nkeys + 1) * 4 : 0);
@@ -363,6 +366,8 @@ part_status part_init(part_ctx** out, const part_grid* grid, part_prec prec, par
     c->shock_r = (double*)(c->ws + L.shock_r);
     c->shock_list = (uint32_t*)(c->ws + L.shock_list);
     c->shock_rs = (double*)(c->ws + L.shock_rs);
+    c->shock_q = (double*)(c->ws + L.shock_q);
+    c->shock_qs = (double*)(c->ws + L.shock_qs);
     c->lpcache = (double*)(c->ws + L.lpcache);
   }
   cudaError_t e = cudaMemsetAsync(c->status, 0, 256, c->stream);
@@ -557,6 +562,27 @@ part_status part_enable_shocks(part_ctx* c, double r_min, uint8_t* state) {
   c->shock_listed = false;
   cudaError_t e = launch_shock_cells(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_enable_shocks");
+  return PART_OK;
+}
+
+part_status part_set_shock_slope(part_ctx* c, int relativistic) {
+  if (check_ctx(c)) return PART_EINVAL;
+  if (c->mode != PART_LP_RK2) return fail(c, PART_EINVAL, "shocks need LP mode");
+  if (relativistic != 0 && relativistic != 1)
+    return fail(c, PART_EINVAL, "relativistic must be 0 or 1");
+  c->shock_rel = relativistic;
+  if (!c->shk) return PART_OK;  // taken up by the next part_enable_shocks
+  cudaError_t e = launch_shock_cells(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "part_set_shock_slope");
+  return PART_OK;
+}
+
+part_status part_shock_slopes(part_ctx* c, const double** q_cell, int64_t* ncells) {
+  if (check_ctx(c)) return PART_EINVAL;
+  if (!q_cell || !ncells) return fail(c, PART_EINVAL, "NULL output");
+  if (!c->shk) return fail(c, PART_EINVAL, "shocks are not enabled");
+  *q_cell = c->shock_q;
+  *ncells = c->geo.G;
   return PART_OK;
 }
 

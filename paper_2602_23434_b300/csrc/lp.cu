@@ -98,14 +98,16 @@ struct Stencil {
 };
 
 // Shock bookkeeping of one LP at its new cell: an LP entering a shock cell
-// (flag 0 -> 1) is appended to the list with the cell's compression ratio;
-// the flag follows the cell.  Appends are warp-aggregated (one atomic per
+// (flag 0 -> 1) is appended to the list with the cell's compression ratio
+// and slope index; the flag follows the cell.  Appends are warp-aggregated (one atomic per
 // warp); list order is irrelevant, each entry is processed on its own.
 __device__ __forceinline__ void shock_mark(int64_t p, int64_t cell,
                                            const double* __restrict__ shock_r,
+                                           const double* __restrict__ shock_q,
                                            uint8_t* __restrict__ shk,
                                            uint32_t* __restrict__ list,
-                                           double* __restrict__ rs) {
+                                           double* __restrict__ rs,
+                                           double* __restrict__ qs) {
   const double rr = shock_r[cell];
   const uint8_t st = shk[p];
   const bool take = rr > 0.0 && st == 0;
@@ -125,6 +127,7 @@ __device__ __forceinline__ void shock_mark(int64_t p, int64_t cell,
     const uint32_t slot = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
     list[1 + slot] = (uint32_t)p;
     rs[slot] = rr;
+    qs[slot] = shock_q[cell];
   }
 }
 
@@ -139,9 +142,10 @@ template <int SHAPE, int DIM, bool SHOCK, int ORDER, bool CACHED>
 __global__ void __launch_bounds__(256)
     k_lp_rk2(const double* __restrict__ fp, const Geo g, double* __restrict__ x, int64_t n,
              double dt, double* __restrict__ samples, int* __restrict__ status,
-             const double* __restrict__ shock_r, uint8_t* __restrict__ shk,
-             uint32_t* __restrict__ list, double* __restrict__ rs,
-             uint8_t* __restrict__ outmask, double* __restrict__ cache) {
+             const double* __restrict__ shock_r, const double* __restrict__ shock_q,
+             uint8_t* __restrict__ shk, uint32_t* __restrict__ list, double* __restrict__ rs,
+             double* __restrict__ qs, uint8_t* __restrict__ outmask,
+             double* __restrict__ cache) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     double x0[3], xs[3], x1[3];
@@ -212,7 +216,7 @@ __global__ void __launch_bounds__(256)
     samples[2 * n + p] = igam;
     if (!(fin && s1.finite && igam > 0.0 && isfinite(r) && r > 0.0))
       atomicOr(status, ST_NONFINITE);
-    if (SHOCK) shock_mark(p, s1.cell, shock_r, shk, list, rs);
+    if (SHOCK) shock_mark(p, s1.cell, shock_r, shock_q, shk, list, rs, qs);
   }
 }
 
@@ -342,11 +346,12 @@ cudaError_t lp_launch_cached(part_ctx* c, double dt) {
     if (e != cudaSuccess) return e;
     k_lp_rk2<SHAPE, DIM, true, ORDER, CACHED><<<gb, 256, 0, c->stream>>>(
         (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status,
-        c->shock_r, c->shk, c->shock_list, c->shock_rs, c->outmask, c->lpcache);
+        c->shock_r, c->shock_q, c->shk, c->shock_list, c->shock_rs, c->shock_qs, c->outmask,
+        c->lpcache);
   } else {
     k_lp_rk2<SHAPE, DIM, false, ORDER, CACHED><<<gb, 256, 0, c->stream>>>(
         (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status,
-        nullptr, nullptr, nullptr, nullptr, c->outmask, c->lpcache);
+        nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->outmask, c->lpcache);
   }
   c->launches++;
   c->lp_cache_ok = true;
@@ -368,9 +373,31 @@ cudaError_t lp_launch(part_ctx* c, double dt) {
 // Shock cells from the padded fields (periodic ghost layer of one cell):
 // along each axis a < dim, a converging flow across the cell (v_a(+1) -
 // v_a(-1) < 0) with neighbour density ratio max/min >= r_min marks it; the
-// cell keeps the largest such ratio, 0 if none.
+// cell keeps the largest such ratio r (the first axis reaching it), 0 if
+// none, and the index q of Eq. slope: 3r/(r-1), or with REL the relativistic
+// index of Keshet & Waxman (2005) from the shock-frame normal speeds of the
+// lower-density (upstream) and denser (downstream) neighbours along that
+// axis.  The shock frame moves at the speed that conserves the lab-frame
+// mass D = rho/sqrt(1 - |v|^2) across the front (c = 1):
+// v_sh = (D_d v_d - D_u v_u)/(D_d - D_u); there the normal speeds are
+// |v - v_sh|/(1 - v v_sh).  Where no such frame exists (a speed >= 1,
+// D_d = D_u, |v_sh| >= 1, no slowdown) q stays 3r/(r-1).
+__device__ __forceinline__ bool shock_frame_speeds(double vu, double s2u, double rhou, double vd,
+                                                   double s2d, double rhod, double& bu,
+                                                   double& bd) {
+  if (!(s2u < 1.0 && s2d < 1.0)) return false;
+  const double Du = rhou / sqrt(1.0 - s2u), Dd = rhod / sqrt(1.0 - s2d);
+  if (!(Dd != Du)) return false;
+  const double vsh = (Dd * vd - Du * vu) / (Dd - Du);
+  if (!(fabs(vsh) < 1.0)) return false;
+  bu = fabs((vu - vsh) / (1.0 - vu * vsh));
+  bd = fabs((vd - vsh) / (1.0 - vd * vsh));
+  return bd < bu;
+}
+
+template <bool REL>
 __global__ void k_shock_cells(const double* __restrict__ fp, const Geo g, double r_min,
-                              double* __restrict__ r_cell) {
+                              double* __restrict__ r_cell, double* __restrict__ q_cell) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.G;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int jx = (int)(c % g.n[0]);
@@ -378,6 +405,8 @@ __global__ void k_shock_cells(const double* __restrict__ fp, const Geo g, double
     const int jz = (int)(c / ((int64_t)g.n[0] * g.n[1]));
     const int64_t q = ((int64_t)(jz + g.h[2]) * g.pn[1] + (jy + g.h[1])) * g.pn[0] + (jx + g.h[0]);
     double best = 0.0;
+    int axis = -1;
+    int64_t up = 0, down = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (a >= g.dim) break;
@@ -387,10 +416,34 @@ __global__ void k_shock_cells(const double* __restrict__ fp, const Geo g, double
         const double rp = fp[3 * g.pplane + q + st], rm = fp[3 * g.pplane + q - st];
         const double hi = rp > rm ? rp : rm, lo = rp > rm ? rm : rp;
         const double ratio = hi / lo;
-        if (ratio > best) best = ratio;
+        if (ratio > best) {
+          best = ratio;
+          axis = a;
+          down = rp > rm ? q + st : q - st;
+          up = rp > rm ? q - st : q + st;
+        }
       }
     }
-    r_cell[c] = best >= r_min ? best : 0.0;
+    const bool shock = best >= r_min;
+    double qi = 0.0;
+    if (shock) {
+      qi = 3.0 * best / (best - 1.0);
+      if (REL) {
+        double s2u = 0.0, s2d = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const double vu = fp[a * g.pplane + up], vd = fp[a * g.pplane + down];
+          s2u += vu * vu;
+          s2d += vd * vd;
+        }
+        double bu, bd;
+        if (shock_frame_speeds(fp[axis * g.pplane + up], s2u, fp[3 * g.pplane + up],
+                               fp[axis * g.pplane + down], s2d, fp[3 * g.pplane + down], bu, bd))
+          qi = (3.0 * bu - 2.0 * bu * bd * bd + bd * bd * bd) / (bu - bd);
+      }
+    }
+    r_cell[c] = shock ? best : 0.0;
+    q_cell[c] = qi;
   }
 }
 
@@ -402,12 +455,13 @@ __global__ void k_shock_cells(const double* __restrict__ fp, const Geo g, double
 // d_j = ln(h_j/h_{j-1}) -- a prefix sum over the bins: each lane takes 4
 // consecutive bins of a 128-bin tile, sums them, and a warp scan (shuffles)
 // adds the lanes before it; tiles carry their last bin and running sum.
-// q = 3r/(r-1) (Eq. slope, non-relativistic), cn = q/r (particle number per
-// unit fluid density conserved across the jump).
+// q from the LP's shock cell (Eq. slope, with or without q_R), cn = q/r (for
+// a non-relativistic shock: particle number per unit fluid density conserved
+// across the jump).
 template <bool INV>
 __global__ void __launch_bounds__(256)
     k_shock_convolve(const uint32_t* __restrict__ list, const double* __restrict__ rs,
-                     double* __restrict__ chi, const double* __restrict__ eng, int64_t n,
+                     const double* __restrict__ qs, double* __restrict__ chi, const double* __restrict__ eng, int64_t n,
                      int nb, int* __restrict__ status) {
   constexpr int K = 4;
   const uint32_t cnt = list[0];
@@ -416,7 +470,7 @@ __global__ void __launch_bounds__(256)
   for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < cnt; t += warps) {
     const int64_t p = list[1 + t];
     const double r = rs[t];
-    const double q = 3.0 * r / (r - 1.0);
+    const double q = qs[t];
     const double cn = q / r;
     const double qm2 = q - 2.0;
     double cS = 0.0, cE = 0.0, cL = 0.0, cH = 0.0;  // carry: running sum, last bin
@@ -501,8 +555,12 @@ cudaError_t launch_lp_push(part_ctx* c, double dt, int nsteps) {
 }
 
 cudaError_t launch_shock_cells(part_ctx* c) {
-  k_shock_cells<<<grid_for(c, c->geo.G, 256), 256, 0, c->stream>>>(
-      (const double*)c->fpad, c->geo, c->r_min, c->shock_r);
+  if (c->shock_rel)
+    k_shock_cells<true><<<grid_for(c, c->geo.G, 256), 256, 0, c->stream>>>(
+        (const double*)c->fpad, c->geo, c->r_min, c->shock_r, c->shock_q);
+  else
+    k_shock_cells<false><<<grid_for(c, c->geo.G, 256), 256, 0, c->stream>>>(
+        (const double*)c->fpad, c->geo, c->r_min, c->shock_r, c->shock_q);
   c->launches++;
   return cudaGetLastError();
 }
@@ -512,11 +570,11 @@ cudaError_t launch_shock_convolve(part_ctx* c) {
   int64_t b = (c->n + 7) / 8;            // 8 warps (LPs) per block
   if (b > (int64_t)c->sms * 16) b = (int64_t)c->sms * 16;
   if (c->spec_inv)
-    k_shock_convolve<true><<<(unsigned)b, 256, 0, c->stream>>>(c->shock_list, c->shock_rs, c->chi,
-                                                             c->eng, c->n, c->nbins, c->status);
+    k_shock_convolve<true><<<(unsigned)b, 256, 0, c->stream>>>(
+        c->shock_list, c->shock_rs, c->shock_qs, c->chi, c->eng, c->n, c->nbins, c->status);
   else
     k_shock_convolve<false><<<(unsigned)b, 256, 0, c->stream>>>(
-        c->shock_list, c->shock_rs, c->chi, c->eng, c->n, c->nbins, c->status);
+        c->shock_list, c->shock_rs, c->shock_qs, c->chi, c->eng, c->n, c->nbins, c->status);
   c->launches++;
   return cudaGetLastError();
 }

@@ -118,8 +118,11 @@ struct part_ctx {
   double* shock_r{};       // [G] compression ratio of each shock cell, 0 elsewhere
   uint32_t* shock_list{};  // [0]: count; [1 + k]: LPs shocked by the last push
   double* shock_rs{};      // [k]: compression ratio each listed LP saw
+  double* shock_q{};       // [G] Eq. slope index q of each shock cell, 0 elsewhere
+  double* shock_qs{};      // [k]: the index q each listed LP saw
   uint8_t* shk{};          // caller's per-LP "in a shock cell" flags; NULL: shocks off
   double r_min{};
+  int shock_rel{};         // 1: q with the relativistic correction q_R
   int lp_order{2};         // LP time marching: 2 (Heun) or 3 (SSP-RK3)
   bool shock_listed{};     // the last push filled the list
   // incremental sort: the arrays are in the order of the last sort, and
@@ -336,7 +339,7 @@ struct InjectSrc {
 };
 cudaError_t launch_inject(part_ctx* c, int64_t k, const InjectSrc& src);  // sort.cu
 cudaError_t launch_sort_incremental(part_ctx* c);  // see sort.cu
-cudaError_t launch_shock_cells(part_ctx* c);       // shock_r from the padded LP fields
+cudaError_t launch_shock_cells(part_ctx* c);       // shock_r, shock_q from the padded LP fields
 cudaError_t launch_shock_convolve(part_ctx* c);    // Eq. convolution_spectra on the list
 cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps);
 cudaError_t launch_boris_mixed(part_ctx* c, double qm, double dt, int nsteps);

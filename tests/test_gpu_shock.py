@@ -18,6 +18,8 @@ pytestmark = pytest.mark.gpu
 
 from paper_2602_23434_b300 import _lib as P  # noqa: E402
 
+import test_oracle_pins as pins  # noqa: E402  (the boosted relativistic shock state)
+
 R_E2 = 40.0 / 11.0        # Rankine-Hugoniot r of the shock test (M^2 = 30, gamma 5/3)
 
 
@@ -45,7 +47,7 @@ def _rh_fields(n, r=R_E2, rho_u=50.0, v_u=0.1):
 class LPRun:
     """GPU LP context with shocks plus the oracle's copy of the same state."""
 
-    def __init__(self, dim, n, vel, rho, B, x, nb, r_min, eps=(1e2, 1e4), p=9.0):
+    def __init__(self, dim, n, vel, rho, B, x, nb, r_min, eps=(1e2, 1e4), p=9.0, rel=False):
         self.og = O.make_grid(dim, (n, n, n))
         self.vel, self.rho, self.B = vel, rho, B
         N = x.shape[1]
@@ -62,8 +64,11 @@ class LPRun:
         self.noldd = torch.as_tensor(self.nold).cuda()
         self.std = torch.zeros(N, dtype=torch.uint8, device="cuda")
         self.p.bind(N, self.xd, chi=self.chid, eng=self.engd, n_old=self.noldd)
+        if rel:
+            self.p.set_shock_slope(True)
         self.p.enable_shocks(r_min, self.std)
         self.r_cell = O.shock_cells(self.og, vel, rho, r_min)
+        self.q_cell = O.shock_slopes(self.og, vel, rho, self.r_cell, rel) if rel else None
 
     def step(self, dt, c0, gpu=True, cpu=True):
         if gpu:
@@ -75,7 +80,7 @@ class LPRun:
             self.chi, self.eng, self.nold = O.spec_update(self.chi, self.eng, self.nold, nn,
                                                           b2, gm, dt, c0)
             self.chi, self.st = O.lp_shock(self.og, self.r_cell, self.x, self.chi, self.eng,
-                                           self.st)
+                                           self.st, q_cell=self.q_cell)
 
     def compare(self, tol):
         self.p.sync()
@@ -181,6 +186,72 @@ def test_shock_3d_turbulent_with_sort_and_compaction():
     assert _rel(chi_g, run.chi[:, src]) <= 1e-11
 
 
+def _rel_fields(n, beta_b, mirror=False):
+    """A relativistic shock (shock-frame normal speeds 0.9 and 0.35, with
+    tangential motion) seen from a frame where it moves at beta_b, front at
+    x = 0 on [-1,1]^2; B = (1, 0, 0).  vel[3,G], rho[1,G], B[3,G]."""
+    vel, rho = pins._rel_snapshot(n, beta_b, mirror)
+    B = np.zeros((3, n * n))
+    B[0] = 1.0
+    return vel.reshape(3, -1), rho.reshape(1, -1), B
+
+
+def test_relativistic_slopes_match_oracle():
+    """Eq. slope with q_R per shock cell: the moving relativistic shock in
+    both flow directions, 1e-13 relative (a few FP64 roundings of the same
+    steps), and a 3D turbulent snapshot with speeds up to about c (valid and
+    missing shock frames, weak jumps with q up to ~1e5), 1e-13 q relative.
+    Without the correction q = 3r/(r-1) bit-exact, and the setting switches
+    both ways on enabled shocks."""
+    n = 40
+    q_true = O.kw_index(0.9, 0.35)
+    for beta_b, mirror in ((0.3, False), (0.3, True), (-0.5, False), (0.0, True)):
+        vel, rho, B = _rel_fields(n, beta_b, mirror)
+        run = LPRun(2, n, vel, rho, B, np.zeros((3, 1)), 8, 1.5, rel=True)
+        assert np.array_equal(_host(run.p.shock_cells()), run.r_cell)
+        got = _host(run.p.shock_slopes())
+        assert np.array_equal(got > 0, run.r_cell > 0) and np.count_nonzero(got) == 2 * n
+        assert _rel(got[got > 0], run.q_cell[got > 0]) <= 1e-13
+        assert abs(got[got > 0] / q_true - 1.0).max() <= 1e-12
+        run.p.set_shock_slope(False)
+        q0 = O.shock_slopes(run.og, vel, rho, run.r_cell, False)
+        assert np.array_equal(_host(run.p.shock_slopes()), q0)
+        run.p.set_shock_slope(True)
+        assert _rel(_host(run.p.shock_slopes()), run.q_cell) <= 1e-13
+    n3 = 24
+    v3, r3, b3 = synth.fluid_snapshot(3, n3, 52, v_rms=0.45)
+    v3, r3, b3 = v3.reshape(3, -1), r3.reshape(1, -1), b3.reshape(3, -1)
+    run3 = LPRun(3, n3, v3, r3, b3, np.zeros((3, 1)), 8, 1.2, rel=True)
+    assert np.array_equal(_host(run3.p.shock_cells()), run3.r_cell)
+    got3 = _host(run3.p.shock_slopes())
+    sh = run3.r_cell > 0
+    assert np.array_equal(got3 > 0, sh) and sh.sum() > 20
+    # q divides by b_u - b_d, so its rounding grows with q: against extended
+    # precision the oracle itself is within 2.5e-14 q relative on this snapshot
+    qr = run3.q_cell[sh]
+    assert np.max(np.abs(got3[sh] - qr) / (qr * np.maximum(1.0, qr))) <= 1e-13
+    q0 = 3.0 * run3.r_cell[sh] / (run3.r_cell[sh] - 1.0)
+    assert np.count_nonzero(run3.q_cell[sh] != q0) > 0      # the correction applied
+
+
+def test_relativistic_shock_step_matches_oracle():
+    """LPs crossing the moving relativistic shock (speeds ~0.6-0.95 c):
+    flags, positions and spectra after each of three steps against the
+    oracle with its per-cell q."""
+    n, N, nb = 40, 2001, 64
+    vel, rho, B = _rel_fields(n, 0.3)
+    rng = np.random.default_rng(8)
+    x = np.zeros((3, N))
+    x[0] = rng.uniform(-0.15, 0.02, N)
+    x[1] = rng.uniform(-1.0, 1.0, N)
+    run = LPRun(2, n, vel, rho, B, x, nb, 1.5, rel=True)
+    dt = 0.5 * (2.0 / n) / 0.95
+    for _ in range(3):
+        run.step(dt, 1e-6)
+        run.compare(1e-12)
+    assert 100 < int(run.st.sum()) < N
+
+
 def test_shock_error_paths():
     pg = P.make_grid(2, 16)
     pb = P.Part(pg, P.FP64, P.TSC, P.BORIS, capacity=8)
@@ -199,7 +270,14 @@ def test_shock_error_paths():
     for bad in (1.0, 0.5, float("nan")):
         with pytest.raises(P.PartError):
             p.enable_shocks(bad, st)
+    for bad in (-1, 2):
+        with pytest.raises(P.PartError):
+            p._check(p.L.part_set_shock_slope(p.ctx, bad))
+    with pytest.raises(P.PartError):
+        pb.set_shock_slope(True)                              # Boris mode
     p.enable_shocks(1.5, st)
     p.enable_shocks(1.5, None)                                # off again
+    with pytest.raises(P.PartError):
+        p.shock_slopes()
     with pytest.raises(P.PartError):
         p.shock_cells()
