@@ -193,8 +193,16 @@ def time_steps(torch, stream, fn, K: int, W: int, per_step_events=False):
     return total_ms, kern_ms
 
 
+# algorithmic bytes of one LP-step, the state it must read and write: the
+# spectra (chi, eps: 2 x 2 x 8 B per bin), positions (2 x 24 B) and n_old
+# (2 x 8 B).  The samples handed from the push to the spectral update and the
+# v, B cache are the implementation's own traffic and are not counted.
+def lp_step_bytes(nb):
+    return 2 * 2 * 8 * nb + 48 + 16
+
+
 def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, order=2,
-           fp64_tflops=None):
+           fp64_tflops=None, paired=False):
     dev = torch.device("cuda", torch.cuda.current_device())
     vel, rho, B = synth.fluid_snapshot(3, n, seed)
     f7 = torch.as_tensor(np.concatenate([vel, rho, B]).reshape(7, -1)).to(dev)
@@ -206,6 +214,7 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
     nold = torch.empty(nlp, dtype=torch.float64, device=dev)
     p.bind(nlp, x, chi=chi, eng=eng, n_old=nold)
     p.set_lp_order(order)
+    p.set_lp_arith(paired)
     p.init_particles(seed, 0.0, 1.0, 1e6, 2.2, 1e-6)
     p.sort()                                   # once: locality of the field gathers
     p.sync()
@@ -247,20 +256,32 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
     spec_bytes = nlp * 2 * 2 * nb * 8
     hbm, _ = peaks()
     del chi, eng
+    if paired:
+        push_roof = {"bound": "f32 issue (paired-f32 arithmetic)", "kernel_ms": push_ms,
+                     "fp64_kernel_bound_ms_at_measured_peak": (
+                         nlp * slots / (fp64_tflops * 1e12 / 2) * 1e3 if fp64_tflops else None)}
+    else:
+        push_roof = {"bound": "fp64 pipe", "slots_per_lp_step": slots,
+                     "bound_ms_at_measured_peak": (
+                         nlp * slots / (fp64_tflops * 1e12 / 2) * 1e3
+                         if fp64_tflops else None),
+                     "frac": (nlp * slots / (fp64_tflops * 1e12 / 2) * 1e3 / push_ms
+                              if fp64_tflops else None),
+                     "kernel_ms": push_ms}
+    arith = ("push in paired-f32 arithmetic (~48-bit), FP64 state and spectra" if paired
+             else "FP64")
     return {"workload": f"LP 3D {n}^3 snapshot, {nlp} LPs x {nb} bins, "
-                        f"{'RK2' if order == 2 else 'SSP-RK3'} + TSC + spectra, FP64",
+                        f"{'RK2' if order == 2 else 'SSP-RK3'} + TSC + spectra, {arith}",
             "value": nlp * K / (total / 1e3), "unit": "LP-steps/s", "ms_per_step": ms,
             "spec_update_ms": spec_ms,
             "spec_update_GBps": spec_bytes / (spec_ms / 1e3) / 1e9,
             "push_ms": push_ms,
+            "step_hbm": {"bytes_per_lp_step": lp_step_bytes(nb),
+                         "achieved_GBps": lp_step_bytes(nb) * nlp / (ms / 1e3) / 1e9,
+                         "frac": lp_step_bytes(nb) * nlp / (ms / 1e3) / 1e9 / hbm,
+                         "peak_kind": "measured"},
             "roofline_step": {
-                "push": {"bound": "fp64 pipe", "slots_per_lp_step": slots,
-                         "bound_ms_at_measured_peak": (
-                             nlp * slots / (fp64_tflops * 1e12 / 2) * 1e3
-                             if fp64_tflops else None),
-                         "frac": (nlp * slots / (fp64_tflops * 1e12 / 2) * 1e3 / push_ms
-                                  if fp64_tflops else None),
-                         "kernel_ms": push_ms},
+                "push": push_roof,
                 "spec_update": {"bound": "hbm", "bytes": spec_bytes,
                                 "bound_ms": spec_bytes / (hbm * 1e9) * 1e3,
                                 "kernel_ms": spec_ms,
@@ -944,9 +965,9 @@ def only(args):
         res = run_lp_shock(torch, P, max(3, args.steps), 3, n=args.grid)
     elif args.only == "compact":
         res = run_compact(torch, P, n=args.grid, K=max(3, args.steps))
-    elif args.only == "lp":
+    elif args.only in ("lp", "lp_paired"):
         res = run_lp(torch, P, args.steps, args.warmup, n=args.grid,
-                     nlp=max(1 << 16, 2 * args.grid ** 3))
+                     nlp=max(1 << 16, 2 * args.grid ** 3), paired=args.only == "lp_paired")
     elif args.only == "boris2d":
         res = run_2d(torch, P)
     else:
@@ -968,7 +989,8 @@ def main():
     ap.add_argument("--grid", type=int, default=128,
                     help="cells per axis of the headline workload (128 = the stated one; "
                          "smaller only for profiling captures)")
-    ap.add_argument("--only", choices=["mixed", "lp", "serving", "compact", "shock", "boris2d"],
+    ap.add_argument("--only", choices=["mixed", "lp", "lp_paired", "serving", "compact", "shock",
+                                       "boris2d"],
                     default=None,
                     help="run one secondary workload alone at --grid cells per axis and print "
                          "its result (for profiling captures); no headline line")
@@ -1073,6 +1095,12 @@ def main():
                                     fp64_tflops=fp64_peak)
         except Exception as e:
             line["lp_rk3"] = {"error": repr(e)}
+        for key, order in (("lp_paired", 2), ("lp_rk3_paired", 3)):
+            try:
+                line[key] = run_lp(torch, P, max(5, args.steps // 2), 3, order=order,
+                                   fp64_tflops=fp64_peak, paired=True)
+            except Exception as e:
+                line[key] = {"error": repr(e)}
         try:
             line["boris_2d"] = run_2d(torch, P)
         except Exception as e:

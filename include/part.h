@@ -227,6 +227,21 @@ part_status part_gather_push(part_ctx* ctx, double q_over_m, double dt, int nste
  * Other orders or modes: PART_EINVAL.                                      */
 part_status part_set_lp_order(part_ctx* ctx, int order);
 
+/* Arithmetic of the LP push (PART_LP_RK2 contexts; default 0).
+ * paired = 0: FP64.  paired = 1: paired f32 -- every value of the step
+ * (offsets, weights, stencil sums, position updates, samples) is carried as
+ * the unevaluated sum of two floats, about 48 significant bits, built from
+ * error-free transformations (TwoSum, FMA product errors) and evaluated on
+ * the f32 pipes, two field components per packed f32x2 instruction; the
+ * stencil sums are Dot2 accumulations (Ogita, Rump & Oishi 2005).  B300
+ * runs FP64 at about 1/64 of its f32 rate, and the FP64 push is bound by
+ * it.  Positions, spectra and everything the caller sees stay FP64; the
+ * step agrees with the FP64 one to ~1e-15 in position and ~1e-13 relative
+ * in the samples (offsets within ~1e-13 cell).  The spectral update
+ * (spec_update) stays FP64 in both.  Changing it drops the cached v, B
+ * (the next push gathers them again).  Other values or modes: PART_EINVAL. */
+part_status part_set_lp_arith(part_ctx* ctx, int paired);
+
 /* Write the force density deposited by the last part_gather_push into
  * grid_out (device, double[3][G], overwritten):
  *   F_g = sum_p W(x_g - x_p^n) F_p.

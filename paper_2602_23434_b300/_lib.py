@@ -104,6 +104,7 @@ def lib():
         "part_compact": (st, [P, P, C.POINTER(C.c_int64)]),
         "part_enable_shocks": (st, [P, C.c_double, P]),
         "part_set_lp_order": (st, [P, C.c_int]),
+        "part_set_lp_arith": (st, [P, C.c_int]),
         "part_flush": (st, [P]),
         "part_set_outflow": (st, [P, P]),
         "part_shock_cells": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
@@ -264,6 +265,10 @@ class Part:
     def set_lp_order(self, order: int):
         """LP time marching: 2 (Heun) or 3 (SSP-RK3)."""
         self._check(self.L.part_set_lp_order(self.ctx, order))
+
+    def set_lp_arith(self, paired: bool):
+        """LP push arithmetic: FP64 (False, the default) or paired f32 (True)."""
+        self._check(self.L.part_set_lp_arith(self.ctx, 1 if paired else 0))
 
     def enable_shocks(self, r_min: float, state):
         """Diffusive shock acceleration of the LP spectra (Eq. convolution_spectra);

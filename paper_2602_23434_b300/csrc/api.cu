@@ -154,7 +154,7 @@ struct Layout {
   size_t fpad, keys0, keys1, vals0, vals1, hist, hsum, cstart, tmp, dpart, samples, status,
       alt_x, alt_off, alt_u, alt_w, alt_id, shock_r, shock_q, shock_list, shock_rs, shock_qs,
       cstart_alt, bcount,
-      bsum, bslot, lpcache, total;
+      bsum, bslot, lpcache, fpair, total;
 };
 
 int ncomp_of(part_mode m) { return m == PART_BORIS ? 6 : 7; }
@@ -205,6 +205,7 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   L.shock_rs = take(lp ? (size_t)c1 * 8 : 0);
   L.shock_qs = take(lp ? (size_t)c1 * 8 : 0);
   L.lpcache = take(lp ? (size_t)6 * c1 * 8 : 0);
+  L.fpair = take(lp ? (size_t)16 * g.pplane * 4 : 0);
   // Boris modes: second cell_start and the brick counts of the incremental sort
   L.cstart_alt = take(alt ? (size_t)(g.nkeys + 1) * 4 : 0);
   L.bcount = take(alt ? (size_t)(g.nbricks + 1) * 4 : 0);
@@ -369,6 +370,7 @@ part_status part_init(part_ctx** out, const part_grid* grid, part_prec prec, par
     c->shock_q = (double*)(c->ws + L.shock_q);
     c->shock_qs = (double*)(c->ws + L.shock_qs);
     c->lpcache = (double*)(c->ws + L.lpcache);
+    c->fpair = (float*)(c->ws + L.fpair);
   }
   cudaError_t e = cudaMemsetAsync(c->status, 0, 256, c->stream);
   if (e != cudaSuccess) {
@@ -401,6 +403,7 @@ part_status part_set_fields(part_ctx* c, const void* fields, int ncomp, part_pre
     return fail(c, PART_EINVAL, "fields are not aligned to their element size");
   if (check_access(c, fields, "fields") != PART_OK) return PART_EINVAL;
   cudaError_t e = launch_pad_fields(c, fields);
+  if (e == cudaSuccess && c->mode == PART_LP_RK2) e = launch_pad_pair_lp(c);
   if (e == cudaSuccess && c->shk) e = launch_shock_cells(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_set_fields");
   c->fields_set = true;
@@ -545,6 +548,15 @@ part_status part_set_lp_order(part_ctx* c, int order) {
   return PART_OK;
 }
 
+part_status part_set_lp_arith(part_ctx* c, int paired) {
+  if (check_ctx(c)) return PART_EINVAL;
+  if (c->mode != PART_LP_RK2) return fail(c, PART_EINVAL, "the LP arithmetic is an LP-mode setting");
+  if (paired != 0 && paired != 1) return fail(c, PART_EINVAL, "paired must be 0 or 1");
+  if (paired != c->lp_paired) c->lp_cache_ok = false;  // the cache is kept in the push's format
+  c->lp_paired = paired;
+  return PART_OK;
+}
+
 part_status part_enable_shocks(part_ctx* c, double r_min, uint8_t* state) {
   if (check_ctx(c)) return PART_EINVAL;
   if (c->mode != PART_LP_RK2) return fail(c, PART_EINVAL, "shocks need LP mode");
@@ -636,7 +648,8 @@ part_status part_gather_push(part_ctx* c, double q_over_m, double dt, int nsteps
     c->deposit_ready = c->deposit_on;
   } else {
     if (nsteps != 1) return fail(c, PART_EINVAL, "LP mode advances one step per call");
-    e = launch_lp_push(c, dt, nsteps);
+    e = c->lp_paired ? launch_lp_push_pair(c, dt) : launch_lp_push(c, dt, nsteps);
+    c->samples_paired = c->lp_paired != 0;
     c->order_kept = false;  // fluid speeds are not bounded by the library
     c->samples_ready = true;
     c->shock_listed = c->shk != nullptr;

@@ -4,6 +4,7 @@
 // Fields: padded FP64 copy with 7 components: v[3], rho, B[3] (the fluid
 // quantities an LP samples, Sec. 2).  Spectra are bin-major [nb][n], so every
 // bin access of a warp is one coalesced 256-byte row.
+#include "lp_shock.cuh"
 #include "part_internal.cuh"
 
 namespace {
@@ -96,40 +97,6 @@ struct Stencil {
     }
   }
 };
-
-// Shock bookkeeping of one LP at its new cell: an LP entering a shock cell
-// (flag 0 -> 1) is appended to the list with the cell's compression ratio
-// and slope index; the flag follows the cell.  Appends are warp-aggregated (one atomic per
-// warp); list order is irrelevant, each entry is processed on its own.
-__device__ __forceinline__ void shock_mark(int64_t p, int64_t cell,
-                                           const double* __restrict__ shock_r,
-                                           const double* __restrict__ shock_q,
-                                           uint8_t* __restrict__ shk,
-                                           uint32_t* __restrict__ list,
-                                           double* __restrict__ rs,
-                                           double* __restrict__ qs) {
-  const double rr = shock_r[cell];
-  const uint8_t st = shk[p];
-  const bool take = rr > 0.0 && st == 0;
-  if (rr > 0.0) {
-    if (st == 0) shk[p] = 1;
-  } else if (st != 0) {
-    shk[p] = 0;
-  }
-  const unsigned act = __activemask();
-  const unsigned m = __ballot_sync(act, take);
-  if (take) {
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(list, (uint32_t)__popc(m));
-    base = __shfl_sync(m, base, leader);
-    const uint32_t slot = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
-    list[1 + slot] = (uint32_t)p;
-    rs[slot] = rr;
-    qs[slot] = shock_q[cell];
-  }
-}
 
 // ORDER 2: Heun, x' = x + dt (k1 + k2)/2.  ORDER 3: three-stage SSP
 // Runge-Kutta (Shu & Osher) in stage-velocity form, k3 = v(x + dt (k1+k2)/4),
@@ -253,14 +220,26 @@ __device__ __forceinline__ void recip8(const double* v, double* r) {
 // FROM_PLAIN: the arrays still hold chi and eps (first update since they
 // were bound, initialised or brought back) and are converted on the way.
 // dtau = dt / gamma_g, gamma_g from the push (its sample 1/gamma_g).
-template <bool FROM_PLAIN>
+// PAIRED: the samples are float pairs [6][n] (h rows, then l rows) from the
+// paired-f32 push, converted here.
+template <bool FROM_PLAIN, bool PAIRED>
 __global__ void __launch_bounds__(256)
     k_spec_update(double* __restrict__ chi, double* __restrict__ eng, double* __restrict__ n_old,
                   const double* __restrict__ samples, int64_t n, int nb, double dt, double c0,
                   double u_rad, int* __restrict__ status) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
-    const double nn = samples[p], b2 = samples[n + p], igam = samples[2 * n + p];
+    double nn, b2, igam;
+    if (PAIRED) {
+      const float* sf = reinterpret_cast<const float*>(samples);
+      nn = (double)sf[p] + (double)sf[3 * n + p];
+      b2 = (double)sf[n + p] + (double)sf[4 * n + p];
+      igam = (double)sf[2 * n + p] + (double)sf[5 * n + p];
+    } else {
+      nn = samples[p];
+      b2 = samples[n + p];
+      igam = samples[2 * n + p];
+    }
     const double dtau = dt * igam;
     const double L = log(n_old[p] / nn) * (1.0 / 3.0);  // a3 dtau
     const double em = expm1(L);                          // A - 1, no cancellation
@@ -581,12 +560,15 @@ cudaError_t launch_shock_convolve(part_ctx* c) {
 
 cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad) {
   if (c->n == 0) return cudaSuccess;
+  const int gb = grid_for(c, c->n, 256);
+  auto go = [&](auto kern) {
+    kern<<<gb, 256, 0, c->stream>>>(c->chi, c->eng, c->n_old, c->samples, c->n, c->nbins, dt, c0,
+                                    u_rad, c->status);
+  };
   if (c->spec_inv)
-    k_spec_update<false><<<grid_for(c, c->n, 256), 256, 0, c->stream>>>(
-        c->chi, c->eng, c->n_old, c->samples, c->n, c->nbins, dt, c0, u_rad, c->status);
+    c->samples_paired ? go(k_spec_update<false, true>) : go(k_spec_update<false, false>);
   else
-    k_spec_update<true><<<grid_for(c, c->n, 256), 256, 0, c->stream>>>(
-        c->chi, c->eng, c->n_old, c->samples, c->n, c->nbins, dt, c0, u_rad, c->status);
+    c->samples_paired ? go(k_spec_update<true, true>) : go(k_spec_update<true, false>);
   c->launches++;
   c->spec_inv = true;
   return cudaGetLastError();

@@ -86,8 +86,11 @@ struct part_ctx {
   void* tmp{};        // permute scratch, 8 bytes * capacity
   double* dpart{};    // deposit partials [nbricks][3][ev]
   double* samples{};  // LP samples [3][capacity]: n_new, b2m, 1/gamma_g
-  double* lpcache{};  // LP v, B at the current positions [6][capacity]
+  double* lpcache{};  // LP v, B at the current positions [6][capacity] (paired: [12] f32)
   bool lp_cache_ok{}; // lpcache matches the bound LPs, their order and the fields
+  float* fpair{};     // LP: paired-f32 copy of the padded fields, 16 floats per cell
+  int lp_paired{};    // LP push arithmetic: 0 FP64, 1 paired f32
+  bool samples_paired{};  // the last LP push left its samples as pairs ([6] f32)
   // Boris modes: alternate particle buffers.  part_sort only computes the
   // permutation (perm_pend); the next brick push reads the current buffer
   // through it and writes the other one, so no separate permutation pass is
@@ -339,6 +342,8 @@ struct InjectSrc {
 };
 cudaError_t launch_inject(part_ctx* c, int64_t k, const InjectSrc& src);  // sort.cu
 cudaError_t launch_sort_incremental(part_ctx* c);  // see sort.cu
+cudaError_t launch_lp_push_pair(part_ctx* c, double dt);   // the LP step in paired f32
+cudaError_t launch_pad_pair_lp(part_ctx* c);               // fpair from fpad
 cudaError_t launch_shock_cells(part_ctx* c);       // shock_r, shock_q from the padded LP fields
 cudaError_t launch_shock_convolve(part_ctx* c);    // Eq. convolution_spectra on the list
 cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps);
