@@ -203,6 +203,7 @@ def lp_step_bytes(nb):
 
 def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, order=2,
            fp64_tflops=None, paired=False):
+    """The LP step of config 4: part_gather_push + spec_update, each timed."""
     dev = torch.device("cuda", torch.cuda.current_device())
     vel, rho, B = synth.fluid_snapshot(3, n, seed)
     f7 = torch.as_tensor(np.concatenate([vel, rho, B]).reshape(7, -1)).to(dev)
@@ -248,13 +249,19 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
     ms = total / K
     spec_ms = float(np.mean(kern))
     kev = [e for e in kev if e is not None]
+    spec_bytes = nlp * 2 * 2 * nb * 8
+    hbm, _ = peaks()
+    arith = ("push in paired-f32 arithmetic (~48-bit), FP64 state and spectra" if paired
+             else "FP64")
+    step_hbm = {"bytes_per_lp_step": lp_step_bytes(nb),
+                "achieved_GBps": lp_step_bytes(nb) * nlp / (total / K / 1e3) / 1e9,
+                "frac": lp_step_bytes(nb) * nlp / (total / K / 1e3) / 1e9 / hbm,
+                "peak_kind": "measured"}
     push_ms = float(np.mean([a.elapsed_time(e[0]) for a, e in zip(push_ev, kev)]))
     # the two bounds of the step: the push on the FP64 pipe (about 440 FP64
     # pipe slots per LP-step for RK2, 560 for RK3, at 2 slots per SM-cycle =
     # half the measured FP64 FLOP/s), the spectral update on HBM
     slots = 440 if order == 2 else 560
-    spec_bytes = nlp * 2 * 2 * nb * 8
-    hbm, _ = peaks()
     del chi, eng
     if paired:
         push_roof = {"bound": "f32 issue (paired-f32 arithmetic)", "kernel_ms": push_ms,
@@ -268,18 +275,13 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
                      "frac": (nlp * slots / (fp64_tflops * 1e12 / 2) * 1e3 / push_ms
                               if fp64_tflops else None),
                      "kernel_ms": push_ms}
-    arith = ("push in paired-f32 arithmetic (~48-bit), FP64 state and spectra" if paired
-             else "FP64")
     return {"workload": f"LP 3D {n}^3 snapshot, {nlp} LPs x {nb} bins, "
                         f"{'RK2' if order == 2 else 'SSP-RK3'} + TSC + spectra, {arith}",
             "value": nlp * K / (total / 1e3), "unit": "LP-steps/s", "ms_per_step": ms,
             "spec_update_ms": spec_ms,
             "spec_update_GBps": spec_bytes / (spec_ms / 1e3) / 1e9,
             "push_ms": push_ms,
-            "step_hbm": {"bytes_per_lp_step": lp_step_bytes(nb),
-                         "achieved_GBps": lp_step_bytes(nb) * nlp / (ms / 1e3) / 1e9,
-                         "frac": lp_step_bytes(nb) * nlp / (ms / 1e3) / 1e9 / hbm,
-                         "peak_kind": "measured"},
+            "step_hbm": step_hbm,
             "roofline_step": {
                 "push": push_roof,
                 "spec_update": {"bound": "hbm", "bytes": spec_bytes,

@@ -648,8 +648,7 @@ part_status part_gather_push(part_ctx* c, double q_over_m, double dt, int nsteps
     c->deposit_ready = c->deposit_on;
   } else {
     if (nsteps != 1) return fail(c, PART_EINVAL, "LP mode advances one step per call");
-    e = c->lp_paired ? launch_lp_push_pair(c, dt) : launch_lp_push(c, dt, nsteps);
-    c->samples_paired = c->lp_paired != 0;
+    e = launch_lp_push(c, dt, nsteps);
     c->order_kept = false;  // fluid speeds are not bounded by the library
     c->samples_ready = true;
     c->shock_listed = c->shk != nullptr;

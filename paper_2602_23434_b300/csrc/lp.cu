@@ -4,7 +4,10 @@
 // Fields: padded FP64 copy with 7 components: v[3], rho, B[3] (the fluid
 // quantities an LP samples, Sec. 2).  Spectra are bin-major [nb][n], so every
 // bin access of a warp is one coalesced 256-byte row.
+#include <algorithm>
+
 #include "lp_shock.cuh"
+#include "lp_spec.cuh"
 #include "part_internal.cuh"
 
 namespace {
@@ -105,16 +108,21 @@ struct Stencil {
 // CACHED: v and B at x (from the previous step's samples at its new
 // position, the same stencil at the same point) are read instead of gathered;
 // every step leaves v and B at x' for the next one (cache [6][n]).
+// LPs [p0, p1) of the n bound (the row stride of every array).
+// The push of one LP, leaving its samples (density, <|B|^2>, 1/gamma_g) in
+// s3.
 template <int SHAPE, int DIM, bool SHOCK, int ORDER, bool CACHED>
-__global__ void __launch_bounds__(256)
-    k_lp_rk2(const double* __restrict__ fp, const Geo g, double* __restrict__ x, int64_t n,
-             double dt, double* __restrict__ samples, int* __restrict__ status,
-             const double* __restrict__ shock_r, const double* __restrict__ shock_q,
-             uint8_t* __restrict__ shk, uint32_t* __restrict__ list, double* __restrict__ rs,
-             double* __restrict__ qs, uint8_t* __restrict__ outmask,
-             double* __restrict__ cache) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
+struct PushF64 {
+  LpArgs A;
+  __device__ __forceinline__ void operator()(int64_t p, double* s3) const {
+    const double* __restrict__ fp = A.fp;
+    const Geo& g = A.g;
+    double* __restrict__ x = A.x;
+    const int64_t n = A.n;
+    const double dt = A.dt;
+    int* __restrict__ status = A.status;
+    double* __restrict__ cache = A.cache;
+    uint8_t* __restrict__ outmask = A.outmask;
     double x0[3], xs[3], x1[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) x0[a] = xs[a] = x1[a] = x[a * n + p];
@@ -178,56 +186,38 @@ __global__ void __launch_bounds__(256)
     const double bb1 = fma(b1[2], b1[2], fma(b1[1], b1[1], b1[0] * b1[0]));
     const double vv = fma(v3[2], v3[2], fma(v3[1], v3[1], v3[0] * v3[0]));
     const double igam = sqrt(1.0 - vv);  // 1/gamma_g: d tau = dt / gamma_g = dt * igam
-    samples[p] = r;
-    samples[n + p] = 0.5 * (bb0 + bb1);
-    samples[2 * n + p] = igam;
+    s3[0] = r;
+    s3[1] = 0.5 * (bb0 + bb1);
+    s3[2] = igam;
     if (!(fin && s1.finite && igam > 0.0 && isfinite(r) && r > 0.0))
       atomicOr(status, ST_NONFINITE);
-    if (SHOCK) shock_mark(p, s1.cell, shock_r, shock_q, shk, list, rs, qs);
+    if (SHOCK) shock_mark(p, s1.cell, A.shock_r, A.shock_q, A.shk, A.list, A.rs, A.qs);
+  }
+};
+
+template <int SHAPE, int DIM, bool SHOCK, int ORDER, bool CACHED>
+__global__ void __launch_bounds__(256)
+    k_lp_rk2(const LpArgs a, double* __restrict__ samples, int64_t p0, int64_t p1) {
+  const PushF64<SHAPE, DIM, SHOCK, ORDER, CACHED> push{a};
+  for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    double s3[3];
+    push(p, s3);
+    samples[p] = s3[0];
+    samples[a.n + p] = s3[1];
+    samples[2 * a.n + p] = s3[2];
   }
 }
 
-// r[k] = 1/v[k] for eight values by Montgomery's simultaneous inversion:
-// prefix products, one correctly rounded reciprocal, then unwinding (three
-// multiplies per value instead of a reciprocal each).  Products that leave
-// the double range fall back to eight reciprocals.
-__device__ __forceinline__ void recip8(const double* v, double* r) {
-  double pre[8];
-  pre[0] = v[0];
-#pragma unroll
-  for (int k = 1; k < 8; ++k) pre[k] = pre[k - 1] * v[k];
-  double inv = __drcp_rn(pre[7]);
-  if (finite_bits(inv) && inv != 0.0 && finite_bits(pre[7]) && pre[7] != 0.0) {
-#pragma unroll
-    for (int k = 7; k > 0; --k) {
-      r[k] = inv * pre[k - 1];
-      inv = inv * v[k];
-    }
-    r[0] = inv;
-  } else {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) r[k] = __drcp_rn(v[k]);
-  }
-}
-
-// Eq. cr_chi along exact characteristics, in the variables the step is
-// linear in: y = 1/eps and psi = chi eps^2.  With a3 and c_r frozen over the
-// step, dy/dtau = a3 y + c_r gives y1 = A y0 + C, A = exp(a3 dtau) =
-// (n_old/n_new)^(1/3), C = c_r dtau expm1(a3 dtau)/(a3 dtau); number
-// conservation along the characteristic (chi deps fixed) gives
-// chi1 = chi0 (y1/y0)^2 / A, i.e. psi1 = psi0 / A.  Per bin that is one FMA
-// and one multiply, so the pass is bound by HBM instead of the FP64 rate.
-// FROM_PLAIN: the arrays still hold chi and eps (first update since they
-// were bound, initialised or brought back) and are converted on the way.
-// dtau = dt / gamma_g, gamma_g from the push (its sample 1/gamma_g).
-// PAIRED: the samples are float pairs [6][n] (h rows, then l rows) from the
-// paired-f32 push, converted here.
+// The spectral update (spec_lp) of LPs [p0, p1) from the samples the last
+// push left.  PAIRED: the samples are float pairs [6][n] (h rows, then l rows)
+// from the paired-f32 push, converted here.
 template <bool FROM_PLAIN, bool PAIRED>
 __global__ void __launch_bounds__(256)
     k_spec_update(double* __restrict__ chi, double* __restrict__ eng, double* __restrict__ n_old,
                   const double* __restrict__ samples, int64_t n, int nb, double dt, double c0,
-                  double u_rad, int* __restrict__ status) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+                  double u_rad, int* __restrict__ status, int64_t p0, int64_t p1) {
+  for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1;
        p += (int64_t)gridDim.x * blockDim.x) {
     double nn, b2, igam;
     if (PAIRED) {
@@ -240,49 +230,8 @@ __global__ void __launch_bounds__(256)
       b2 = samples[n + p];
       igam = samples[2 * n + p];
     }
-    const double dtau = dt * igam;
-    const double L = log(n_old[p] / nn) * (1.0 / 3.0);  // a3 dtau
-    const double em = expm1(L);                          // A - 1, no cancellation
-    const double A = 1.0 + em;
-    const double iA = __drcp_rn(A);
-    const double cr = c0 * (0.5 * b2 + u_rad);
-    const double C = cr * dtau * (L == 0.0 ? 1.0 : em / L);
-    if (!(isfinite(A) && A > 0.0 && isfinite(C) && isfinite(iA))) atomicOr(status, ST_NONFINITE);
-    double* ep = eng + p;
-    double* cp = chi + p;
-    int i = 0;
-    for (; i + 8 <= nb; i += 8) {  // eight rows' loads in flight per thread
-      double y[8], ps[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        y[k] = ep[(int64_t)(i + k) * n];
-        ps[k] = cp[(int64_t)(i + k) * n];
-      }
-      if (FROM_PLAIN) {  // y[] holds eps: psi = chi eps^2, y = 1/eps
-        double r[8];
-        recip8(y, r);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          ps[k] = (ps[k] * y[k]) * y[k];
-          y[k] = r[k];
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        ep[(int64_t)(i + k) * n] = fma(A, y[k], C);
-        cp[(int64_t)(i + k) * n] = ps[k] * iA;
-      }
-    }
-    for (; i < nb; ++i) {
-      double y = ep[(int64_t)i * n], ps = cp[(int64_t)i * n];
-      if (FROM_PLAIN) {
-        ps = (ps * y) * y;
-        y = __drcp_rn(y);
-      }
-      ep[(int64_t)i * n] = fma(A, y, C);
-      cp[(int64_t)i * n] = ps * iA;
-    }
-    n_old[p] = nn;
+    spec_lp<FROM_PLAIN>(SpecArgs{chi, eng, n_old, nb, dt, c0, u_rad}, p, n, nn, b2, igam,
+                        status);
   }
 }
 
@@ -318,35 +267,25 @@ __global__ void __launch_bounds__(256)
 }
 
 template <int SHAPE, int DIM, int ORDER, bool CACHED>
-cudaError_t lp_launch_cached(part_ctx* c, double dt) {
-  const int gb = grid_for(c, c->n, 256);
-  if (c->shk) {
-    cudaError_t e = cudaMemsetAsync(c->shock_list, 0, sizeof(uint32_t), c->stream);
-    if (e != cudaSuccess) return e;
-    k_lp_rk2<SHAPE, DIM, true, ORDER, CACHED><<<gb, 256, 0, c->stream>>>(
-        (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status,
-        c->shock_r, c->shock_q, c->shk, c->shock_list, c->shock_rs, c->shock_qs, c->outmask,
-        c->lpcache);
-  } else {
-    k_lp_rk2<SHAPE, DIM, false, ORDER, CACHED><<<gb, 256, 0, c->stream>>>(
-        (const double*)c->fpad, c->geo, (double*)c->x, c->n, dt, c->samples, c->status,
-        nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->outmask, c->lpcache);
-  }
+cudaError_t lp_launch_range(part_ctx* c, double dt, const LpLaunch& L) {
+  const LpArgs a = lp_args(c, dt);
+  if (c->shk)
+    k_lp_rk2<SHAPE, DIM, true, ORDER, CACHED><<<L.grid, 256, 0, L.stream>>>(a, c->samples, L.p0,
+                                                                           L.p1);
+  else
+    k_lp_rk2<SHAPE, DIM, false, ORDER, CACHED><<<L.grid, 256, 0, L.stream>>>(a, c->samples,
+                                                                            L.p0, L.p1);
   c->launches++;
-  c->lp_cache_ok = true;
   return cudaGetLastError();
 }
 
-template <int SHAPE, int DIM, int ORDER>
-cudaError_t lp_launch_order(part_ctx* c, double dt) {
-  return c->lp_cache_ok ? lp_launch_cached<SHAPE, DIM, ORDER, true>(c, dt)
-                        : lp_launch_cached<SHAPE, DIM, ORDER, false>(c, dt);
-}
-
 template <int SHAPE, int DIM>
-cudaError_t lp_launch(part_ctx* c, double dt) {
-  return c->lp_order == 3 ? lp_launch_order<SHAPE, DIM, 3>(c, dt)
-                          : lp_launch_order<SHAPE, DIM, 2>(c, dt);
+cudaError_t lp_launch(part_ctx* c, double dt, const LpLaunch& L) {
+  if (c->lp_order == 3)
+    return L.cached ? lp_launch_range<SHAPE, DIM, 3, true>(c, dt, L)
+                    : lp_launch_range<SHAPE, DIM, 3, false>(c, dt, L);
+  return L.cached ? lp_launch_range<SHAPE, DIM, 2, true>(c, dt, L)
+                  : lp_launch_range<SHAPE, DIM, 2, false>(c, dt, L);
 }
 
 // Shock cells from the padded fields (periodic ghost layer of one cell):
@@ -525,12 +464,28 @@ __global__ void __launch_bounds__(256)
 
 }  // namespace
 
+cudaError_t launch_lp_push_range(part_ctx* c, double dt, const LpLaunch& L) {
+  if (L.p1 <= L.p0) return cudaSuccess;
+  if (c->shape == PART_TSC)
+    return c->geo.dim == 3 ? lp_launch<PART_TSC, 3>(c, dt, L) : lp_launch<PART_TSC, 2>(c, dt, L);
+  return c->geo.dim == 3 ? lp_launch<PART_CIC, 3>(c, dt, L) : lp_launch<PART_CIC, 2>(c, dt, L);
+}
+
 cudaError_t launch_lp_push(part_ctx* c, double dt, int nsteps) {
   (void)nsteps;
   if (c->n == 0) return cudaSuccess;
-  if (c->shape == PART_TSC)
-    return c->geo.dim == 3 ? lp_launch<PART_TSC, 3>(c, dt) : lp_launch<PART_TSC, 2>(c, dt);
-  return c->geo.dim == 3 ? lp_launch<PART_CIC, 3>(c, dt) : lp_launch<PART_CIC, 2>(c, dt);
+  if (c->shk) {
+    cudaError_t e = cudaMemsetAsync(c->shock_list, 0, sizeof(uint32_t), c->stream);
+    if (e != cudaSuccess) return e;
+  }
+  const LpLaunch L{0, c->n, grid_for(c, c->n, 256), c->stream, c->lp_cache_ok};
+  cudaError_t e = c->lp_paired ? launch_lp_push_pair_range(c, dt, L)
+                               : launch_lp_push_range(c, dt, L);
+  if (e == cudaSuccess) {
+    c->lp_cache_ok = true;
+    c->samples_paired = c->lp_paired != 0;
+  }
+  return e;
 }
 
 cudaError_t launch_shock_cells(part_ctx* c) {
@@ -558,20 +513,27 @@ cudaError_t launch_shock_convolve(part_ctx* c) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_spec_range(part_ctx* c, double dt, double c0, double u_rad, bool from_plain,
+                              const LpLaunch& L) {
+  if (L.p1 <= L.p0) return cudaSuccess;
+  auto go = [&](auto kern) {
+    kern<<<L.grid, 256, 0, L.stream>>>(c->chi, c->eng, c->n_old, c->samples, c->n, c->nbins, dt,
+                                       c0, u_rad, c->status, L.p0, L.p1);
+  };
+  if (from_plain)
+    c->samples_paired ? go(k_spec_update<true, true>) : go(k_spec_update<true, false>);
+  else
+    c->samples_paired ? go(k_spec_update<false, true>) : go(k_spec_update<false, false>);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad) {
   if (c->n == 0) return cudaSuccess;
-  const int gb = grid_for(c, c->n, 256);
-  auto go = [&](auto kern) {
-    kern<<<gb, 256, 0, c->stream>>>(c->chi, c->eng, c->n_old, c->samples, c->n, c->nbins, dt, c0,
-                                    u_rad, c->status);
-  };
-  if (c->spec_inv)
-    c->samples_paired ? go(k_spec_update<false, true>) : go(k_spec_update<false, false>);
-  else
-    c->samples_paired ? go(k_spec_update<true, true>) : go(k_spec_update<true, false>);
-  c->launches++;
-  c->spec_inv = true;
-  return cudaGetLastError();
+  const LpLaunch L{0, c->n, grid_for(c, c->n, 256), c->stream, false};
+  cudaError_t e = launch_spec_range(c, dt, c0, u_rad, !c->spec_inv, L);
+  if (e == cudaSuccess) c->spec_inv = true;
+  return e;
 }
 
 cudaError_t launch_spec_to_plain(part_ctx* c) {

@@ -17,6 +17,7 @@
 // log2(n) bits), and the stencil sums are Dot2 accumulations.  Offsets come
 // out within ~1e-13 cell, positions within ~1e-15 of the FP64 step.
 #include "lp_shock.cuh"
+#include "lp_spec.cuh"
 #include "pair.cuh"
 #include "part_internal.cuh"
 
@@ -147,17 +148,23 @@ struct StepDt {
 };
 
 // cache: [12][n] floats, v.h[3], v.l[3], B.h[3], B.l[3]; samples: [6][n]
-// floats, (rho, <|B|^2>, 1/gamma_g) as h rows then l rows
+// floats, (rho, <|B|^2>, 1/gamma_g) as h rows then l rows.  LPs [p0, p1) of
+// the n bound (the row stride of every array).
+// The push of one LP, leaving its samples (density, <|B|^2>, 1/gamma_g) as
+// pairs.
 template <int SHAPE, int DIM, bool SHOCK, int ORDER, bool CACHED>
-__global__ void __launch_bounds__(256, 2)
-    k_lp_pair(const float4* __restrict__ fq, const Geo g, const PairGeo pg,
-              double* __restrict__ x, int64_t n, const StepDt sd, float* __restrict__ samples,
-              int* __restrict__ status, const double* __restrict__ shock_r,
-              const double* __restrict__ shock_q, uint8_t* __restrict__ shk,
-              uint32_t* __restrict__ list, double* __restrict__ rs, double* __restrict__ qs,
-              uint8_t* __restrict__ outmask, float* __restrict__ cache) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
+struct PushPair {
+  LpArgs A;   // A.fp: the paired copy (float4 records); A.cache: [12][n] floats
+  PairGeo pg;
+  StepDt sd;
+  __device__ __forceinline__ void pairs(int64_t p, f2* smp) const {
+    const float4* __restrict__ fq = reinterpret_cast<const float4*>(A.fp);
+    const Geo& g = A.g;
+    double* __restrict__ x = A.x;
+    const int64_t n = A.n;
+    int* __restrict__ status = A.status;
+    float* __restrict__ cache = reinterpret_cast<float*>(A.cache);
+    uint8_t* __restrict__ outmask = A.outmask;
     f2 X0[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     double x0d[3];
 #pragma unroll
@@ -272,15 +279,29 @@ __global__ void __launch_bounds__(256, 2)
     const f2 om = f2_add({1.0f, 0.0f}, f2_neg(norm2_p(v3)));   // 1 - |v|^2
     // 1/gamma_g; not a number where 1 - |v|^2 <= 0 (flagged below, as in FP64)
     const f2 ig = om.h > 0.0f ? f2_sqrt(om) : f2{__int_as_float(0x7fc00000), 0.0f};
-    samples[p] = r.h;
-    samples[n + p] = bm.h;
-    samples[2 * n + p] = ig.h;
-    samples[3 * n + p] = r.l;
-    samples[4 * n + p] = bm.l;
-    samples[5 * n + p] = ig.l;
+    smp[0] = r;
+    smp[1] = bm;
+    smp[2] = ig;
     if (!(fin && s1.finite && ig.h > 0.0f && isfinite(r.h) && r.h > 0.0f))
       atomicOr(status, ST_NONFINITE);
-    if (SHOCK) shock_mark(p, s1.cell, shock_r, shock_q, shk, list, rs, qs);
+    if (SHOCK) shock_mark(p, s1.cell, A.shock_r, A.shock_q, A.shk, A.list, A.rs, A.qs);
+  }
+};
+
+template <int SHAPE, int DIM, bool SHOCK, int ORDER, bool CACHED>
+__global__ void __launch_bounds__(256, 2)
+    k_lp_pair(const PushPair<SHAPE, DIM, SHOCK, ORDER, CACHED> push, float* __restrict__ samples,
+              int64_t p0, int64_t p1) {
+  const int64_t n = push.A.n;
+  for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    f2 t[3];
+    push.pairs(p, t);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      samples[k * n + p] = t[k].h;
+      samples[(3 + k) * n + p] = t[k].l;
+    }
   }
 }
 
@@ -317,49 +338,47 @@ PairGeo pair_geo(const Geo& g) {
   return pg;
 }
 
+template <int SHAPE, int DIM, bool SHOCK, int ORDER, bool CACHED>
+PushPair<SHAPE, DIM, SHOCK, ORDER, CACHED> push_pair(part_ctx* c, double dt) {
+  PushPair<SHAPE, DIM, SHOCK, ORDER, CACHED> f;
+  f.A = lp_args(c, dt);
+  f.A.fp = reinterpret_cast<const double*>(c->fpair);
+  f.pg = pair_geo(c->geo);
+  f.sd = {f2_host(dt), f2_host(0.5 * dt), f2_host(0.25 * dt), f2_host(dt * (1.0 / 6.0))};
+  return f;
+}
+
 template <int SHAPE, int DIM, int ORDER, bool CACHED>
-cudaError_t lp_pair_launch(part_ctx* c, double dt) {
-  const int gb = grid_for(c, c->n, 256);
-  const PairGeo pg = pair_geo(c->geo);
-  const StepDt sd = {f2_host(dt), f2_host(0.5 * dt), f2_host(0.25 * dt), f2_host(dt * (1.0 / 6.0))};
-  const float4* fq = reinterpret_cast<const float4*>(c->fpair);
-  float* cache = reinterpret_cast<float*>(c->lpcache);
+cudaError_t lp_pair_launch(part_ctx* c, double dt, const LpLaunch& L) {
   float* smp = reinterpret_cast<float*>(c->samples);
-  if (c->shk) {
-    cudaError_t e = cudaMemsetAsync(c->shock_list, 0, sizeof(uint32_t), c->stream);
-    if (e != cudaSuccess) return e;
-    k_lp_pair<SHAPE, DIM, true, ORDER, CACHED><<<gb, 256, 0, c->stream>>>(
-        fq, c->geo, pg, (double*)c->x, c->n, sd, smp, c->status, c->shock_r, c->shock_q, c->shk,
-        c->shock_list, c->shock_rs, c->shock_qs, c->outmask, cache);
-  } else {
-    k_lp_pair<SHAPE, DIM, false, ORDER, CACHED><<<gb, 256, 0, c->stream>>>(
-        fq, c->geo, pg, (double*)c->x, c->n, sd, smp, c->status, nullptr, nullptr, nullptr,
-        nullptr, nullptr, nullptr, c->outmask, cache);
-  }
+  if (c->shk)
+    k_lp_pair<<<L.grid, 256, 0, L.stream>>>(push_pair<SHAPE, DIM, true, ORDER, CACHED>(c, dt),
+                                            smp, L.p0, L.p1);
+  else
+    k_lp_pair<<<L.grid, 256, 0, L.stream>>>(push_pair<SHAPE, DIM, false, ORDER, CACHED>(c, dt),
+                                            smp, L.p0, L.p1);
   c->launches++;
   return cudaGetLastError();
 }
 
 template <int SHAPE, int DIM>
-cudaError_t lp_pair_dispatch(part_ctx* c, double dt) {
+cudaError_t lp_pair_dispatch(part_ctx* c, double dt, const LpLaunch& L) {
   if (c->lp_order == 3)
-    return c->lp_cache_ok ? lp_pair_launch<SHAPE, DIM, 3, true>(c, dt)
-                          : lp_pair_launch<SHAPE, DIM, 3, false>(c, dt);
-  return c->lp_cache_ok ? lp_pair_launch<SHAPE, DIM, 2, true>(c, dt)
-                        : lp_pair_launch<SHAPE, DIM, 2, false>(c, dt);
+    return L.cached ? lp_pair_launch<SHAPE, DIM, 3, true>(c, dt, L)
+                    : lp_pair_launch<SHAPE, DIM, 3, false>(c, dt, L);
+  return L.cached ? lp_pair_launch<SHAPE, DIM, 2, true>(c, dt, L)
+                  : lp_pair_launch<SHAPE, DIM, 2, false>(c, dt, L);
 }
 
 }  // namespace
 
-cudaError_t launch_lp_push_pair(part_ctx* c, double dt) {
-  if (c->n == 0) return cudaSuccess;
-  cudaError_t e;
+cudaError_t launch_lp_push_pair_range(part_ctx* c, double dt, const LpLaunch& L) {
+  if (L.p1 <= L.p0) return cudaSuccess;
   if (c->shape == PART_TSC)
-    e = c->geo.dim == 3 ? lp_pair_dispatch<PART_TSC, 3>(c, dt) : lp_pair_dispatch<PART_TSC, 2>(c, dt);
-  else
-    e = c->geo.dim == 3 ? lp_pair_dispatch<PART_CIC, 3>(c, dt) : lp_pair_dispatch<PART_CIC, 2>(c, dt);
-  if (e == cudaSuccess) c->lp_cache_ok = true;
-  return e;
+    return c->geo.dim == 3 ? lp_pair_dispatch<PART_TSC, 3>(c, dt, L)
+                           : lp_pair_dispatch<PART_TSC, 2>(c, dt, L);
+  return c->geo.dim == 3 ? lp_pair_dispatch<PART_CIC, 3>(c, dt, L)
+                         : lp_pair_dispatch<PART_CIC, 2>(c, dt, L);
 }
 
 cudaError_t launch_pad_pair_lp(part_ctx* c) {

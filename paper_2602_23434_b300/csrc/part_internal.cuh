@@ -342,7 +342,18 @@ struct InjectSrc {
 };
 cudaError_t launch_inject(part_ctx* c, int64_t k, const InjectSrc& src);  // sort.cu
 cudaError_t launch_sort_incremental(part_ctx* c);  // see sort.cu
-cudaError_t launch_lp_push_pair(part_ctx* c, double dt);   // the LP step in paired f32
+// One launch of an LP kernel over LPs [p0, p1) (of the n bound) on a stream;
+// cached: v and B at x come from the cache of the previous push.
+struct LpLaunch {
+  int64_t p0, p1;
+  int grid;
+  cudaStream_t stream;
+  bool cached;
+};
+cudaError_t launch_lp_push_range(part_ctx* c, double dt, const LpLaunch& L);       // FP64
+cudaError_t launch_lp_push_pair_range(part_ctx* c, double dt, const LpLaunch& L);  // paired f32
+cudaError_t launch_spec_range(part_ctx* c, double dt, double c0, double u_rad, bool from_plain,
+                              const LpLaunch& L);
 cudaError_t launch_pad_pair_lp(part_ctx* c);               // fpair from fpad
 cudaError_t launch_shock_cells(part_ctx* c);       // shock_r, shock_q from the padded LP fields
 cudaError_t launch_shock_convolve(part_ctx* c);    // Eq. convolution_spectra on the list
