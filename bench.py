@@ -202,8 +202,10 @@ def lp_step_bytes(nb):
 
 
 def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, order=2,
-           fp64_tflops=None, paired=False):
-    """The LP step of config 4: part_gather_push + spec_update, each timed."""
+           fp64_tflops=None, paired=False, lazy=False):
+    """The LP step of config 4: part_gather_push + spec_update, each timed.
+    lazy: the deferred spectra (per-LP maps; the bins brought up to date by
+    the flush that ends the timed run, which is inside the timed region)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     vel, rho, B = synth.fluid_snapshot(3, n, seed)
     f7 = torch.as_tensor(np.concatenate([vel, rho, B]).reshape(7, -1)).to(dev)
@@ -216,6 +218,7 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
     p.bind(nlp, x, chi=chi, eng=eng, n_old=nold)
     p.set_lp_order(order)
     p.set_lp_arith(paired)
+    p.set_spec_lazy(lazy)
     p.init_particles(seed, 0.0, 1.0, 1e6, 2.2, 1e-6)
     p.sort()                                   # once: locality of the field gathers
     p.sync()
@@ -253,6 +256,9 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
     hbm, _ = peaks()
     arith = ("push in paired-f32 arithmetic (~48-bit), FP64 state and spectra" if paired
              else "FP64")
+    if lazy:
+        arith += (f"; spectra deferred as per-LP maps, brought up to date once per {K} steps "
+                  f"(the flush ending the timed run)")
     step_hbm = {"bytes_per_lp_step": lp_step_bytes(nb),
                 "achieved_GBps": lp_step_bytes(nb) * nlp / (total / K / 1e3) / 1e9,
                 "frac": lp_step_bytes(nb) * nlp / (total / K / 1e3) / 1e9 / hbm,
@@ -967,9 +973,10 @@ def only(args):
         res = run_lp_shock(torch, P, max(3, args.steps), 3, n=args.grid)
     elif args.only == "compact":
         res = run_compact(torch, P, n=args.grid, K=max(3, args.steps))
-    elif args.only in ("lp", "lp_paired"):
+    elif args.only in ("lp", "lp_paired", "lp_lazy", "lp_paired_lazy"):
         res = run_lp(torch, P, args.steps, args.warmup, n=args.grid,
-                     nlp=max(1 << 16, 2 * args.grid ** 3), paired=args.only == "lp_paired")
+                     nlp=max(1 << 16, 2 * args.grid ** 3), paired="paired" in args.only,
+                     lazy=args.only.endswith("lazy"))
     elif args.only == "boris2d":
         res = run_2d(torch, P)
     else:
@@ -991,8 +998,8 @@ def main():
     ap.add_argument("--grid", type=int, default=128,
                     help="cells per axis of the headline workload (128 = the stated one; "
                          "smaller only for profiling captures)")
-    ap.add_argument("--only", choices=["mixed", "lp", "lp_paired", "serving", "compact", "shock",
-                                       "boris2d"],
+    ap.add_argument("--only", choices=["mixed", "lp", "lp_paired", "lp_lazy", "lp_paired_lazy",
+                                       "serving", "compact", "shock", "boris2d"],
                     default=None,
                     help="run one secondary workload alone at --grid cells per axis and print "
                          "its result (for profiling captures); no headline line")
@@ -1097,10 +1104,13 @@ def main():
                                     fp64_tflops=fp64_peak)
         except Exception as e:
             line["lp_rk3"] = {"error": repr(e)}
-        for key, order in (("lp_paired", 2), ("lp_rk3_paired", 3)):
+        for key, order, paired, lazy in (("lp_paired", 2, True, False),
+                                         ("lp_rk3_paired", 3, True, False),
+                                         ("lp_lazy", 2, False, True),
+                                         ("lp_paired_lazy", 2, True, True)):
             try:
                 line[key] = run_lp(torch, P, max(5, args.steps // 2), 3, order=order,
-                                   fp64_tflops=fp64_peak, paired=True)
+                                   fp64_tflops=fp64_peak, paired=paired, lazy=lazy)
             except Exception as e:
                 line[key] = {"error": repr(e)}
         try:

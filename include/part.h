@@ -242,6 +242,23 @@ part_status part_set_lp_order(part_ctx* ctx, int order);
  * (the next push gathers them again).  Other values or modes: PART_EINVAL. */
 part_status part_set_lp_arith(part_ctx* ctx, int paired);
 
+/* How spec_update keeps the LP spectra (PART_LP_RK2 contexts; default 0).
+ * The step of Eq. cr_chi (spec_update) is, for every bin of an LP, the same
+ * affine map in y = 1/eps and psi = chi eps^2: y <- A y + C, psi <- psi / A
+ * (A, C from the LP's samples).  lazy = 0: every bin is updated every step.
+ * lazy = 1: the bins stay as they were, and each LP keeps the composition of
+ * its steps' maps, y = alpha y0 + beta, psi = S psi0 (alpha <- A alpha,
+ * beta <- A beta + C, S <- S / A per step): O(1) work per LP and step
+ * instead of O(N_b).  The bins are brought up to date where the spectra are
+ * handed back anyway -- part_sync, part_flush, part_sort, part_compact,
+ * part_inject, the exchange calls, a rebind -- as eps = eps0 / t,
+ * chi = S chi0 t^2 with t = alpha + beta eps0; an LP that a shock update
+ * takes has its bins brought up to date and its map reset first.  The
+ * results agree with lazy = 0 to rounding (the composed map rounds
+ * differently from the steps one by one).  Changing it brings the bound
+ * spectra up to date first.  Other values or modes: PART_EINVAL.          */
+part_status part_set_spec_lazy(part_ctx* ctx, int lazy);
+
 /* Write the force density deposited by the last part_gather_push into
  * grid_out (device, double[3][G], overwritten):
  *   F_g = sum_p W(x_g - x_p^n) F_p.

@@ -105,6 +105,7 @@ def lib():
         "part_enable_shocks": (st, [P, C.c_double, P]),
         "part_set_lp_order": (st, [P, C.c_int]),
         "part_set_lp_arith": (st, [P, C.c_int]),
+        "part_set_spec_lazy": (st, [P, C.c_int]),
         "part_flush": (st, [P]),
         "part_set_outflow": (st, [P, P]),
         "part_shock_cells": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
@@ -269,6 +270,11 @@ class Part:
     def set_lp_arith(self, paired: bool):
         """LP push arithmetic: FP64 (False, the default) or paired f32 (True)."""
         self._check(self.L.part_set_lp_arith(self.ctx, 1 if paired else 0))
+
+    def set_spec_lazy(self, lazy: bool):
+        """spec_update composes per-LP maps (True) or updates every bin (False,
+        the default); the bins are brought up to date at sync/flush."""
+        self._check(self.L.part_set_spec_lazy(self.ctx, 1 if lazy else 0))
 
     def enable_shocks(self, r_min: float, state):
         """Diffusive shock acceleration of the LP spectra (Eq. convolution_spectra);

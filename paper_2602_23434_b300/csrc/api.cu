@@ -154,7 +154,7 @@ struct Layout {
   size_t fpad, keys0, keys1, vals0, vals1, hist, hsum, cstart, tmp, dpart, samples, status,
       alt_x, alt_off, alt_u, alt_w, alt_id, shock_r, shock_q, shock_list, shock_rs, shock_qs,
       cstart_alt, bcount,
-      bsum, bslot, lpcache, fpair, total;
+      bsum, bslot, lpcache, fpair, smap, total;
 };
 
 int ncomp_of(part_mode m) { return m == PART_BORIS ? 6 : 7; }
@@ -206,6 +206,7 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   L.shock_qs = take(lp ? (size_t)c1 * 8 : 0);
   L.lpcache = take(lp ? (size_t)6 * c1 * 8 : 0);
   L.fpair = take(lp ? (size_t)16 * g.pplane * 4 : 0);
+  L.smap = take(lp ? (size_t)3 * c1 * 8 : 0);
   // Boris modes: second cell_start and the brick counts of the incremental sort
   L.cstart_alt = take(alt ? (size_t)(g.nkeys + 1) * 4 : 0);
   L.bcount = take(alt ? (size_t)(g.nbricks + 1) * 4 : 0);
@@ -371,6 +372,7 @@ part_status part_init(part_ctx** out, const part_grid* grid, part_prec prec, par
     c->shock_qs = (double*)(c->ws + L.shock_qs);
     c->lpcache = (double*)(c->ws + L.lpcache);
     c->fpair = (float*)(c->ws + L.fpair);
+    c->smap = (double*)(c->ws + L.smap);
   }
   cudaError_t e = cudaMemsetAsync(c->status, 0, 256, c->stream);
   if (e != cudaSuccess) {
@@ -416,7 +418,9 @@ part_status part_bind_particles(part_ctx* c, int64_t n, void* x_or_cell, void* o
                                 double* n_old) {
   if (check_ctx(c)) return PART_EINVAL;
   if (n < 0 || n > c->capacity) return fail(c, PART_EINVAL, "n must be in [0, capacity]");
-  if (c->cur_alt || c->perm_pend) {  // the previous arrays get their current state first
+  // the previous arrays get their current state first (Boris: the sorted
+  // copy; LP: the spectra as (chi, eps))
+  if (c->cur_alt || c->perm_pend || c->spec_inv || c->maps_pending) {
     cudaError_t e = flush_pending(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "part_bind_particles");
   }
@@ -461,6 +465,8 @@ part_status part_sort(part_ctx* c) {
   double dxmin = c->geo.dx[0];
   for (int a = 1; a < c->geo.dim; ++a) dxmin = std::min(dxmin, c->geo.dx[a]);
   const bool inc = c->order_kept && c->cstart_alt && c->moved < dxmin && !c->geo.any_open;
+  // the deferred LP spectra: each LP's map applied before the LPs move
+  if (c->maps_pending) e = launch_spec_to_plain(c);
   if (e == cudaSuccess) e = inc ? launch_sort_incremental(c) : launch_sort(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_sort");
   c->sorted = true;
@@ -545,6 +551,18 @@ part_status part_set_lp_order(part_ctx* c, int order) {
   if (c->mode != PART_LP_RK2) return fail(c, PART_EINVAL, "the RK order is an LP-mode setting");
   if (order != 2 && order != 3) return fail(c, PART_EINVAL, "order must be 2 or 3");
   c->lp_order = order;
+  return PART_OK;
+}
+
+part_status part_set_spec_lazy(part_ctx* c, int lazy) {
+  if (check_ctx(c)) return PART_EINVAL;
+  if (c->mode != PART_LP_RK2) return fail(c, PART_EINVAL, "the spectra are an LP-mode setting");
+  if (lazy != 0 && lazy != 1) return fail(c, PART_EINVAL, "lazy must be 0 or 1");
+  if (lazy != c->spec_lazy) {  // the bound spectra as (chi, eps) first
+    cudaError_t e = launch_spec_to_plain(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "part_set_spec_lazy");
+  }
+  c->spec_lazy = lazy;
   return PART_OK;
 }
 
@@ -699,6 +717,7 @@ part_status part_init_particles(part_ctx* c, uint64_t seed, double u_th, double 
   c->cur_alt = false;  // every bound array is overwritten
   c->perm_pend = nullptr;
   c->spec_inv = false;
+  c->maps_pending = false;
   cudaError_t e = launch_init(c, seed, u_th, eps_min, eps_max, p_index, N0);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_init_particles");
   c->sorted = false;

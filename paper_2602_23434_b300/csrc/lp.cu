@@ -376,11 +376,18 @@ __global__ void k_shock_cells(const double* __restrict__ fp, const Geo g, double
 // q from the LP's shock cell (Eq. slope, with or without q_R), cn = q/r (for
 // a non-relativistic shock: particle number per unit fluid density conserved
 // across the jump).
-template <bool INV>
+// FORM: how the bound arrays hold the spectra -- 0 (chi, eps); 1 (y, psi) =
+// (1/eps, chi eps^2); 2 the deferred form (chi0, eps0) with the LP's map
+// smap = (alpha, beta, S), where eps = eps0/t and chi = S chi0 t^2 with
+// t = alpha + beta eps0: the LP's bins are written back as (chi, eps) and
+// its map reset to the identity.
+template <int FORM>
 __global__ void __launch_bounds__(256)
     k_shock_convolve(const uint32_t* __restrict__ list, const double* __restrict__ rs,
-                     const double* __restrict__ qs, double* __restrict__ chi, const double* __restrict__ eng, int64_t n,
-                     int nb, int* __restrict__ status) {
+                     const double* __restrict__ qs, double* __restrict__ chi,
+                     double* __restrict__ eng, double* __restrict__ smap, int64_t n, int nb,
+                     int* __restrict__ status) {
+  constexpr bool INV = FORM == 1;
   constexpr int K = 4;
   const uint32_t cnt = list[0];
   const int lane = threadIdx.x & 31;
@@ -393,6 +400,12 @@ __global__ void __launch_bounds__(256)
     const double qm2 = q - 2.0;
     double cS = 0.0, cE = 0.0, cL = 0.0, cH = 0.0;  // carry: running sum, last bin
     bool ok = true;
+    double al = 1.0, be = 0.0, sc = 1.0;  // FORM 2: the LP's pending map
+    if (FORM == 2) {
+      al = smap[p];
+      be = smap[n + p];
+      sc = smap[2 * n + p];
+    }
     for (int t0 = 0; t0 < nb; t0 += 32 * K) {
       double e[K], le[K], w[K], h[K], S[K];
 #pragma unroll
@@ -403,6 +416,11 @@ __global__ void __launch_bounds__(256)
         double c = j < nb ? chi[(int64_t)j * n + p] : 0.0;
         e[i] = INV ? __drcp_rn(ev) : ev;
         if (INV) c = (c * ev) * ev;
+        if (FORM == 2 && j < nb) {
+          const double tt = fma(be, ev, al);
+          e[i] = ev / tt;
+          c = (sc * c) * (tt * tt);
+        }
         le[i] = log(e[i]);
         w[i] = exp(qm2 * le[i]);
         h[i] = c * w[i];
@@ -451,6 +469,7 @@ __global__ void __launch_bounds__(256)
           const double out = j == 0 ? 0.0 : cn * ((before + S[i]) / w[i]);
           ok = ok && isfinite(out);
           chi[(int64_t)j * n + p] = INV ? (out * e[i]) * e[i] : out;
+          if (FORM == 2) eng[(int64_t)j * n + p] = e[i];
         }
       }
       cS = __shfl_sync(0xffffffffu, cS + incl, 31);
@@ -459,6 +478,85 @@ __global__ void __launch_bounds__(256)
       cH = __shfl_sync(0xffffffffu, h[K - 1], 31);
     }
     if (!ok) atomicOr(status, ST_NONFINITE);
+    if (FORM == 2 && lane == 0) {  // the bins now hold the LP's spectrum as it is
+      smap[p] = 1.0;
+      smap[n + p] = 0.0;
+      smap[2 * n + p] = 1.0;
+    }
+  }
+}
+
+// The deferred form of the spectral update (part_set_spec_lazy): the bins
+// stay as they were at the last materialisation, (chi0, eps0), and each LP
+// carries the composition of its steps' maps in y = 1/eps and psi = chi eps^2,
+// y = alpha y0 + beta, psi = S psi0; a step (coefficients A, C as in
+// k_spec_update) composes one more: alpha <- A alpha, beta <- A beta + C,
+// S <- S / A.  O(1) per LP instead of O(N_b).  FIRST: no map pending (the
+// identity).  PAIRED: samples from the paired-f32 push.
+template <bool FIRST, bool PAIRED>
+__global__ void __launch_bounds__(256)
+    k_spec_lazy(const SpecArgs sa, const double* __restrict__ samples, double* __restrict__ smap,
+                int64_t n, int* __restrict__ status) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    double nn, b2, igam;
+    if (PAIRED) {
+      const float* sf = reinterpret_cast<const float*>(samples);
+      nn = (double)sf[p] + (double)sf[3 * n + p];
+      b2 = (double)sf[n + p] + (double)sf[4 * n + p];
+      igam = (double)sf[2 * n + p] + (double)sf[5 * n + p];
+    } else {
+      nn = samples[p];
+      b2 = samples[n + p];
+      igam = samples[2 * n + p];
+    }
+    const SpecCoef k = spec_coeffs(sa, p, nn, b2, igam, status);
+    double al = 1.0, be = 0.0, sc = 1.0;
+    if (!FIRST) {
+      al = smap[p];
+      be = smap[n + p];
+      sc = smap[2 * n + p];
+    }
+    smap[p] = k.A * al;
+    smap[n + p] = fma(k.A, be, k.C);
+    smap[2 * n + p] = sc * k.iA;
+    sa.n_old[p] = nn;
+  }
+}
+
+// Materialise the deferred form: every LP's map applied to its bins, with
+// t = alpha + beta eps0: eps = eps0 / t, chi = S chi0 t^2 (eight reciprocals
+// at a time by recip8).  The maps become the identity (implicitly).
+__global__ void __launch_bounds__(256)
+    k_spec_apply(double* __restrict__ chi, double* __restrict__ eng,
+                 const double* __restrict__ smap, int64_t n, int nb) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const double al = smap[p], be = smap[n + p], sc = smap[2 * n + p];
+    double* ep = eng + p;
+    double* cp = chi + p;
+    int i = 0;
+    for (; i + 8 <= nb; i += 8) {
+      double e0[8], c0[8], t[8], r[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        e0[k] = ep[(int64_t)(i + k) * n];
+        c0[k] = cp[(int64_t)(i + k) * n];
+        t[k] = fma(be, e0[k], al);
+      }
+      recip8(t, r);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        ep[(int64_t)(i + k) * n] = e0[k] * r[k];
+        cp[(int64_t)(i + k) * n] = (sc * c0[k]) * (t[k] * t[k]);
+      }
+    }
+    for (; i < nb; ++i) {
+      const double e0 = ep[(int64_t)i * n], c0 = cp[(int64_t)i * n];
+      const double t = fma(be, e0, al);
+      ep[(int64_t)i * n] = e0 * __drcp_rn(t);
+      cp[(int64_t)i * n] = (sc * c0) * (t * t);
+    }
   }
 }
 
@@ -503,12 +601,13 @@ cudaError_t launch_shock_convolve(part_ctx* c) {
   if (c->n == 0) return cudaSuccess;
   int64_t b = (c->n + 7) / 8;            // 8 warps (LPs) per block
   if (b > (int64_t)c->sms * 16) b = (int64_t)c->sms * 16;
-  if (c->spec_inv)
-    k_shock_convolve<true><<<(unsigned)b, 256, 0, c->stream>>>(
-        c->shock_list, c->shock_rs, c->shock_qs, c->chi, c->eng, c->n, c->nbins, c->status);
-  else
-    k_shock_convolve<false><<<(unsigned)b, 256, 0, c->stream>>>(
-        c->shock_list, c->shock_rs, c->shock_qs, c->chi, c->eng, c->n, c->nbins, c->status);
+  auto go = [&](auto kern) {
+    kern<<<(unsigned)b, 256, 0, c->stream>>>(c->shock_list, c->shock_rs, c->shock_qs, c->chi,
+                                             c->eng, c->smap, c->n, c->nbins, c->status);
+  };
+  if (c->maps_pending) go(k_shock_convolve<2>);
+  else if (c->spec_inv) go(k_shock_convolve<1>);
+  else go(k_shock_convolve<0>);
   c->launches++;
   return cudaGetLastError();
 }
@@ -530,13 +629,37 @@ cudaError_t launch_spec_range(part_ctx* c, double dt, double c0, double u_rad, b
 
 cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad) {
   if (c->n == 0) return cudaSuccess;
-  const LpLaunch L{0, c->n, grid_for(c, c->n, 256), c->stream, false};
+  const int gb = grid_for(c, c->n, 256);
+  if (c->spec_lazy) {  // the deferred form: compose the step into each LP's map
+    const SpecArgs sa{c->chi, c->eng, c->n_old, c->nbins, dt, c0, u_rad};
+    auto go = [&](auto kern) {
+      kern<<<gb, 256, 0, c->stream>>>(sa, c->samples, c->smap, c->n, c->status);
+    };
+    if (c->maps_pending)
+      c->samples_paired ? go(k_spec_lazy<false, true>) : go(k_spec_lazy<false, false>);
+    else
+      c->samples_paired ? go(k_spec_lazy<true, true>) : go(k_spec_lazy<true, false>);
+    c->launches++;
+    c->maps_pending = true;
+    return cudaGetLastError();
+  }
+  const LpLaunch L{0, c->n, gb, c->stream, false};
   cudaError_t e = launch_spec_range(c, dt, c0, u_rad, !c->spec_inv, L);
   if (e == cudaSuccess) c->spec_inv = true;
   return e;
 }
 
 cudaError_t launch_spec_to_plain(part_ctx* c) {
+  if (c->maps_pending) {  // the deferred form: apply the maps
+    c->maps_pending = false;
+    if (c->n > 0 && c->nbins > 0) {
+      k_spec_apply<<<grid_for(c, c->n, 256), 256, 0, c->stream>>>(c->chi, c->eng, c->smap, c->n,
+                                                                  c->nbins);
+      c->launches++;
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
   if (!c->spec_inv) return cudaSuccess;
   c->spec_inv = false;
   if (c->n == 0 || c->nbins == 0) return cudaSuccess;

@@ -84,18 +84,32 @@ struct SpecArgs {
 // were bound, initialised or brought back) and are converted on the way.
 // nn, b2, igam: the push's samples (density, <|B|^2>, 1/gamma_g at the new
 // position); dtau = dt / gamma_g.  Spectra are bin-major [nb][n].
+// The step's coefficients for LP p: y1 = A y0 + C, psi1 = psi0 iA, iA = 1/A.
+struct SpecCoef {
+  double A, C, iA;
+};
+static __device__ __forceinline__ SpecCoef spec_coeffs(const SpecArgs& a, int64_t p, double nn,
+                                                       double b2, double igam,
+                                                       int* __restrict__ status) {
+  const double dtau = a.dt * igam;
+  const double L = log(a.n_old[p] / nn) * (1.0 / 3.0);  // a3 dtau
+  const double em = expm1(L);                            // A - 1, no cancellation
+  SpecCoef k;
+  k.A = 1.0 + em;
+  k.iA = __drcp_rn(k.A);
+  const double cr = a.c0 * (0.5 * b2 + a.u_rad);
+  k.C = cr * dtau * (L == 0.0 ? 1.0 : em / L);
+  if (!(isfinite(k.A) && k.A > 0.0 && isfinite(k.C) && isfinite(k.iA)))
+    atomicOr(status, ST_NONFINITE);
+  return k;
+}
+
 template <bool FROM_PLAIN>
 static __device__ __forceinline__ void spec_lp(const SpecArgs& a, int64_t p, int64_t n,
                                                double nn, double b2, double igam,
                                                int* __restrict__ status) {
-  const double dtau = a.dt * igam;
-  const double L = log(a.n_old[p] / nn) * (1.0 / 3.0);  // a3 dtau
-  const double em = expm1(L);                            // A - 1, no cancellation
-  const double A = 1.0 + em;
-  const double iA = __drcp_rn(A);
-  const double cr = a.c0 * (0.5 * b2 + a.u_rad);
-  const double C = cr * dtau * (L == 0.0 ? 1.0 : em / L);
-  if (!(isfinite(A) && A > 0.0 && isfinite(C) && isfinite(iA))) atomicOr(status, ST_NONFINITE);
+  const SpecCoef kc = spec_coeffs(a, p, nn, b2, igam, status);
+  const double A = kc.A, C = kc.C, iA = kc.iA;
   double* ep = a.eng + p;
   double* cp = a.chi + p;
   const int nb = a.nb;

@@ -91,6 +91,9 @@ struct part_ctx {
   float* fpair{};     // LP: paired-f32 copy of the padded fields, 16 floats per cell
   int lp_paired{};    // LP push arithmetic: 0 FP64, 1 paired f32
   bool samples_paired{};  // the last LP push left its samples as pairs ([6] f32)
+  double* smap{};     // LP deferred spectra: per-LP map (alpha, beta, S) [3][capacity]
+  int spec_lazy{};    // spec_update composes maps instead of updating every bin
+  bool maps_pending{};  // some LP's map is not the identity (bins not materialised)
   // Boris modes: alternate particle buffers.  part_sort only computes the
   // permutation (perm_pend); the next brick push reads the current buffer
   // through it and writes the other one, so no separate permutation pass is
