@@ -187,7 +187,7 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   if ((size_t)nbins * 16 > tmpb) tmpb = (size_t)nbins * 16;
   L.tmp = take(tmpb);
   L.dpart = take(mode == PART_BORIS ? (size_t)g.nbricks * 3 * g.ev * 8 : 0);
-  L.samples = take(mode == PART_LP_RK2 ? (size_t)3 * c1 * 8 : 0);
+  L.samples = take(mode == PART_LP_RK2 ? (size_t)4 * c1 * 8 : 0);
   L.status = take(256);
   // alternate particle buffers of the Boris modes (sorted state awaiting the push)
   const bool alt = mode == PART_BORIS;

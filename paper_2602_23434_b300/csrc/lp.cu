@@ -201,37 +201,27 @@ __global__ void __launch_bounds__(256)
   const PushF64<SHAPE, DIM, SHOCK, ORDER, CACHED> push{a};
   for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1;
        p += (int64_t)gridDim.x * blockDim.x) {
-    double s3[3];
+    double s3[3], s4[4];
     push(p, s3);
-    samples[p] = s3[0];
-    samples[a.n + p] = s3[1];
-    samples[2 * a.n + p] = s3[2];
+    lp_samples(a.n_old[p], s3[0], s3[1], s3[2], s4);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) samples[k * a.n + p] = s4[k];
   }
 }
 
-// The spectral update (spec_lp) of LPs [p0, p1) from the samples the last
-// push left.  PAIRED: the samples are float pairs [6][n] (h rows, then l rows)
-// from the paired-f32 push, converted here.
-template <bool FROM_PLAIN, bool PAIRED>
+// The spectral update (spec_lp) of LPs [p0, p1) from the samples [4][n] the
+// last push left.
+template <bool FROM_PLAIN>
 __global__ void __launch_bounds__(256)
     k_spec_update(double* __restrict__ chi, double* __restrict__ eng, double* __restrict__ n_old,
                   const double* __restrict__ samples, int64_t n, int nb, double dt, double c0,
                   double u_rad, int* __restrict__ status, int64_t p0, int64_t p1) {
   for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1;
        p += (int64_t)gridDim.x * blockDim.x) {
-    double nn, b2, igam;
-    if (PAIRED) {
-      const float* sf = reinterpret_cast<const float*>(samples);
-      nn = (double)sf[p] + (double)sf[3 * n + p];
-      b2 = (double)sf[n + p] + (double)sf[4 * n + p];
-      igam = (double)sf[2 * n + p] + (double)sf[5 * n + p];
-    } else {
-      nn = samples[p];
-      b2 = samples[n + p];
-      igam = samples[2 * n + p];
-    }
-    spec_lp<FROM_PLAIN>(SpecArgs{chi, eng, n_old, nb, dt, c0, u_rad}, p, n, nn, b2, igam,
-                        status);
+    double s4[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s4[k] = samples[k * n + p];
+    spec_lp<FROM_PLAIN>(SpecArgs{chi, eng, n_old, nb, dt, c0, u_rad}, p, n, s4, status);
   }
 }
 
@@ -492,25 +482,15 @@ __global__ void __launch_bounds__(256)
 // y = alpha y0 + beta, psi = S psi0; a step (coefficients A, C as in
 // k_spec_update) composes one more: alpha <- A alpha, beta <- A beta + C,
 // S <- S / A.  O(1) per LP instead of O(N_b).  FIRST: no map pending (the
-// identity).  PAIRED: samples from the paired-f32 push.
-template <bool FIRST, bool PAIRED>
+// identity).
+template <bool FIRST>
 __global__ void __launch_bounds__(256)
     k_spec_lazy(const SpecArgs sa, const double* __restrict__ samples, double* __restrict__ smap,
                 int64_t n, int* __restrict__ status) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
-    double nn, b2, igam;
-    if (PAIRED) {
-      const float* sf = reinterpret_cast<const float*>(samples);
-      nn = (double)sf[p] + (double)sf[3 * n + p];
-      b2 = (double)sf[n + p] + (double)sf[4 * n + p];
-      igam = (double)sf[2 * n + p] + (double)sf[5 * n + p];
-    } else {
-      nn = samples[p];
-      b2 = samples[n + p];
-      igam = samples[2 * n + p];
-    }
-    const SpecCoef k = spec_coeffs(sa, p, nn, b2, igam, status);
+    const SpecCoef k = spec_coeffs(sa, samples[n + p], samples[2 * n + p], samples[3 * n + p],
+                                   status);
     double al = 1.0, be = 0.0, sc = 1.0;
     if (!FIRST) {
       al = smap[p];
@@ -520,7 +500,7 @@ __global__ void __launch_bounds__(256)
     smap[p] = k.A * al;
     smap[n + p] = fma(k.A, be, k.C);
     smap[2 * n + p] = sc * k.iA;
-    sa.n_old[p] = nn;
+    sa.n_old[p] = samples[p];
   }
 }
 
@@ -581,7 +561,6 @@ cudaError_t launch_lp_push(part_ctx* c, double dt, int nsteps) {
                                : launch_lp_push_range(c, dt, L);
   if (e == cudaSuccess) {
     c->lp_cache_ok = true;
-    c->samples_paired = c->lp_paired != 0;
   }
   return e;
 }
@@ -620,9 +599,9 @@ cudaError_t launch_spec_range(part_ctx* c, double dt, double c0, double u_rad, b
                                        c0, u_rad, c->status, L.p0, L.p1);
   };
   if (from_plain)
-    c->samples_paired ? go(k_spec_update<true, true>) : go(k_spec_update<true, false>);
+    go(k_spec_update<true>);
   else
-    c->samples_paired ? go(k_spec_update<false, true>) : go(k_spec_update<false, false>);
+    go(k_spec_update<false>);
   c->launches++;
   return cudaGetLastError();
 }
@@ -636,9 +615,9 @@ cudaError_t launch_spec_update(part_ctx* c, double dt, double c0, double u_rad) 
       kern<<<gb, 256, 0, c->stream>>>(sa, c->samples, c->smap, c->n, c->status);
     };
     if (c->maps_pending)
-      c->samples_paired ? go(k_spec_lazy<false, true>) : go(k_spec_lazy<false, false>);
+      go(k_spec_lazy<false>);
     else
-      c->samples_paired ? go(k_spec_lazy<true, true>) : go(k_spec_lazy<true, false>);
+      go(k_spec_lazy<true>);
     c->launches++;
     c->maps_pending = true;
     return cudaGetLastError();

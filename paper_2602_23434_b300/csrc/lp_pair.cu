@@ -8,8 +8,8 @@
 // and the position updates are pair arithmetic on the f32 pipes, two field
 // components per packed f32x2 instruction.  The fields are read from a
 // paired copy, 64 bytes per padded cell: hi(vx, vy, vz, rho),
-// hi(Bx, By, Bz, 0), lo(...), lo(...).  The v, B cache and the samples are
-// kept as pairs; spec_update converts the samples.
+// hi(Bx, By, Bz, 0), lo(...), lo(...).  The v, B cache is kept as pairs; the
+// samples for spec_update are FP64, as the FP64 push leaves them.
 //
 // Accuracy: a pair carries ~48 bits, and every step is arranged so that the
 // errors are absolute at that level: the in-cell offset is (x - c_j)/dx with
@@ -147,8 +147,7 @@ struct StepDt {
   f2 dt, half, quarter, sixth;
 };
 
-// cache: [12][n] floats, v.h[3], v.l[3], B.h[3], B.l[3]; samples: [6][n]
-// floats, (rho, <|B|^2>, 1/gamma_g) as h rows then l rows.  LPs [p0, p1) of
+// cache: [12][n] floats, v.h[3], v.l[3], B.h[3], B.l[3].  LPs [p0, p1) of
 // the n bound (the row stride of every array).
 // The push of one LP, leaving its samples (density, <|B|^2>, 1/gamma_g) as
 // pairs.
@@ -288,20 +287,21 @@ struct PushPair {
   }
 };
 
+// The samples [4][n] for spec_update (lp_samples): the step's logarithm and
+// exponential in FP64 on the pipe the paired push leaves idle.
 template <int SHAPE, int DIM, bool SHOCK, int ORDER, bool CACHED>
 __global__ void __launch_bounds__(256, 2)
-    k_lp_pair(const PushPair<SHAPE, DIM, SHOCK, ORDER, CACHED> push, float* __restrict__ samples,
+    k_lp_pair(const PushPair<SHAPE, DIM, SHOCK, ORDER, CACHED> push, double* __restrict__ samples,
               int64_t p0, int64_t p1) {
   const int64_t n = push.A.n;
   for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1;
        p += (int64_t)gridDim.x * blockDim.x) {
     f2 t[3];
     push.pairs(p, t);
+    double s4[4];
+    lp_samples(push.A.n_old[p], f2_to(t[0]), f2_to(t[1]), f2_to(t[2]), s4);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      samples[k * n + p] = t[k].h;
-      samples[(3 + k) * n + p] = t[k].l;
-    }
+    for (int k = 0; k < 4; ++k) samples[k * n + p] = s4[k];
   }
 }
 
@@ -350,7 +350,7 @@ PushPair<SHAPE, DIM, SHOCK, ORDER, CACHED> push_pair(part_ctx* c, double dt) {
 
 template <int SHAPE, int DIM, int ORDER, bool CACHED>
 cudaError_t lp_pair_launch(part_ctx* c, double dt, const LpLaunch& L) {
-  float* smp = reinterpret_cast<float*>(c->samples);
+  double* smp = c->samples;
   if (c->shk)
     k_lp_pair<<<L.grid, 256, 0, L.stream>>>(push_pair<SHAPE, DIM, true, ORDER, CACHED>(c, dt),
                                             smp, L.p0, L.p1);

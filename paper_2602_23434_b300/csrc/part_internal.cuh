@@ -90,7 +90,6 @@ struct part_ctx {
   bool lp_cache_ok{}; // lpcache matches the bound LPs, their order and the fields
   float* fpair{};     // LP: paired-f32 copy of the padded fields, 16 floats per cell
   int lp_paired{};    // LP push arithmetic: 0 FP64, 1 paired f32
-  bool samples_paired{};  // the last LP push left its samples as pairs ([6] f32)
   double* smap{};     // LP deferred spectra: per-LP map (alpha, beta, S) [3][capacity]
   int spec_lazy{};    // spec_update composes maps instead of updating every bin
   bool maps_pending{};  // some LP's map is not the identity (bins not materialised)
