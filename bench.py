@@ -8,10 +8,12 @@ TSC deposit of the force density, FP64.  One step = part_sort + part_gather_push
 (fused deposit) + part_deposit.  Metric: particle-steps/s.
 
 Also reported on the same line: the Lagrangian-particle workload (128^3 fluid
-snapshot, 4M LPs x 128 bins, RK2 + spectral update, FP64), the 2D
-uniform-field workload (64^2, 65,536 particles, 100 fused steps), the FP64
-roofline of the dominant kernel, end-to-end throughput through host buffers,
-and the oracle timed on the host cores.
+snapshot, 4M LPs x 128 bins, RK2 or RK3 + spectral update; FP64, and with the
+paired-f32 push and the deferred spectra), the 160^3 shock configuration, the
+mixed form at 128^3 and 256^3, the 2D uniform-field workload (64^2, 65,536
+particles, 100 fused steps), compaction, the serving stream, the FP64 roofline
+of the dominant kernel, end-to-end throughput through host buffers, and the
+oracle timed on the host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank advances its own particles against the replicated
@@ -60,9 +62,6 @@ TRAFFIC_PER_PARTICLE_BRICK_F64 = 264.987392e6 / 2097152  # ncu dram r+w, 64^3 ca
 # Same for the mixed brick kernel, from an ncu capture of the 128^3 case
 # (1715.1 MB for 16,777,216 particles).
 TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1715.104512e6 / 16777216   # ncu dram r+w, 128^3 capture
-# LP step: x r/w 48, chi+eng r/w 4096 (128 bins), n_old r/w 16, samples w+r 48,
-# fields: 7 comps * 8 B per cell / 2 LPs per cell, 3 gathers at ~one cell = 84
-BYTES_PER_LPSTEP = 48 + 4096 + 16 + 48 + 84
 
 
 def peaks():
@@ -354,13 +353,16 @@ def run_compact(torch, P, n=128, ppc=8, fracs=(0.01, 0.1), K=10, seed=1240):
     return out
 
 
-def run_lp_shock(torch, P, K: int, W: int, n=160, ppc=4, nb=128, seed=1241):
+def run_lp_shock(torch, P, K: int, W: int, n=160, ppc=4, nb=128, seed=1241, paired=False,
+                 lazy=False):
     """The paper's shock configuration per GPU (Sec. 4.1.2 extended to 3D,
     Sec. 5): a stationary planar shock at x = 0 (Rankine-Hugoniot, rho_u = 50,
     v_u = 0.1, r = 40/11, B = (1, 0, 0)) on a 160^3 grid, 4 LPs per cell
     (16.4M), each with 128 bins on [1e2, 1e4], p = 9; step = Heun RK2 + TSC
     gather, smooth spectral update, shock detection and Eq.
-    convolution_spectra for the LPs entering the shock."""
+    convolution_spectra for the LPs entering the shock.  paired / lazy: the
+    paired-f32 push and the deferred spectra (brought up to date by the flush
+    that ends the timed run)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     r = 40.0 / 11.0
     xc = -1.0 + (np.arange(n) + 0.5) * (2.0 / n)
@@ -379,6 +381,8 @@ def run_lp_shock(torch, P, K: int, W: int, n=160, ppc=4, nb=128, seed=1241):
     nold = torch.empty(N, dtype=torch.float64, device=dev)
     st = torch.zeros(N, dtype=torch.uint8, device=dev)
     p.bind(N, x, chi=chi, eng=eng, n_old=nold)
+    p.set_lp_arith(paired)
+    p.set_spec_lazy(lazy)
     p.init_particles(seed, 0.0, 1e2, 1e4, 9.0, 1e-6)
     p.sort()
     p.enable_shocks(1.5, st)
@@ -406,9 +410,12 @@ def run_lp_shock(torch, P, K: int, W: int, n=160, ppc=4, nb=128, seed=1241):
     ms = total / K
     spec_ms = float(np.mean(kern))
     del chi, eng
+    arith = "paired-f32 push (~48-bit), FP64 state and spectra" if paired else "FP64"
+    if lazy:
+        arith += f"; spectra deferred, brought up to date once per {K} steps"
     return {"workload": f"LP 3D stationary planar shock (Rankine-Hugoniot, r = 40/11) {n}^3, "
                         f"{N} LPs x {nb} bins on [1e2, 1e4], p = 9, RK2 + TSC + spectra + "
-                        "shock detection + Eq. convolution_spectra, FP64",
+                        f"shock detection + Eq. convolution_spectra, {arith}",
             "value": N * K / (total / 1e3), "unit": "LP-steps/s", "ms_per_step": ms,
             "spec_update_and_shock_ms": spec_ms, "lps_in_shock_cells_at_end": in_shock,
             "paper_context": "Particles_RK#1 + RK#2 + Spectra = 341 ms per step for 1.65e7 "
@@ -976,8 +983,9 @@ def only(args):
     build()
     if args.only == "mixed":
         res = run_mixed(torch, P, args.grid, 8, args.steps, args.warmup, 1237)
-    elif args.only == "shock":
-        res = run_lp_shock(torch, P, max(3, args.steps), 3, n=args.grid)
+    elif args.only in ("shock", "shock_paired_lazy"):
+        res = run_lp_shock(torch, P, max(3, args.steps), 3, n=args.grid,
+                           paired=args.only != "shock", lazy=args.only != "shock")
     elif args.only == "compact":
         res = run_compact(torch, P, n=args.grid, K=max(3, args.steps))
     elif args.only in ("lp", "lp_paired", "lp_lazy", "lp_paired_lazy"):
@@ -1006,7 +1014,8 @@ def main():
                     help="cells per axis of the headline workload (128 = the stated one; "
                          "smaller only for profiling captures)")
     ap.add_argument("--only", choices=["mixed", "lp", "lp_paired", "lp_lazy", "lp_paired_lazy",
-                                       "serving", "compact", "shock", "boris2d"],
+                                       "serving", "compact", "shock", "shock_paired_lazy",
+                                       "boris2d"],
                     default=None,
                     help="run one secondary workload alone at --grid cells per axis and print "
                          "its result (for profiling captures); no headline line")
@@ -1139,6 +1148,11 @@ def main():
             line["lp_shock"] = run_lp_shock(torch, P, max(5, args.steps // 2), 3)
         except Exception as e:
             line["lp_shock"] = {"error": repr(e)}
+        try:
+            line["lp_shock_paired_lazy"] = run_lp_shock(torch, P, max(5, args.steps // 2), 3,
+                                                        paired=True, lazy=True)
+        except Exception as e:
+            line["lp_shock_paired_lazy"] = {"error": repr(e)}
         try:
             line["compact"] = run_compact(torch, P)
         except Exception as e:
