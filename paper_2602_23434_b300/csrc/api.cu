@@ -268,6 +268,13 @@ part_status encode_tmap(part_ctx* c) {
                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(c, PART_ECUDA, "cuTensorMapEncodeTiled failed");
+  if (c->fcomp == 8 && g.dim == 3) {  // one tile plane per copy (rolling staging)
+    box[3] = 1;
+    r = encode(&c->tmap_plane, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->fpad, dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, PART_ECUDA, "cuTensorMapEncodeTiled failed");
+  }
   c->tmap_ok = true;
   return PART_OK;
 }

@@ -108,6 +108,7 @@ struct part_ctx {
   const uint32_t* perm_pend{};    // new slot -> index in the current buffer, or NULL
   int* status{};      // device status word
   CUtensorMap tmap{};  // TMA map of fpad
+  CUtensorMap tmap_plane{};  // the same with a one-plane box (3D cell-interleaved f32)
   bool tmap_ok{};
   // bound particles
   int64_t n{};

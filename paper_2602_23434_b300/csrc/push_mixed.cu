@@ -465,6 +465,370 @@ __global__ void __launch_bounds__(kT, 3)
   }
 }
 
+// ---- 3D brick kernel with deposit, one brick plane at a time --------------
+// The brick's 8^3 cells are numbered x fastest, so each z-plane of 8 x 8
+// cells holds a contiguous range of the sorted particles.  A plane's
+// particles are taken in chunks of up to kM3 (one chunk unless the plane
+// holds more than kM3 particles); per chunk:
+//   A.  push, one thread per particle, as in the kernel above; a record of the
+//       gather weights (at x^n) and the force w du/dt goes to shared memory;
+//   B1. one thread per (cell, kz) sums, over the cell's particles in index
+//       order, the 27 contributions (ky, kx, component) that land in tile
+//       plane lz + kz: the same f32 products, summed in the same order, as
+//       the per-cell sums of the kernel above;
+//   B2. the sums go to shared memory (over the records, no longer needed);
+//   B3. one thread per (pair of x-adjacent targets, component, kz) takes the
+//       sums of the up to 9 source cells that reach each target, in a fixed
+//       order, into a two-float value (TwoSum), and adds that into a rolling
+//       window of three tile planes held as two-float accumulators.  No two
+//       threads share a target, so no ordered passes are needed.
+// After the plane:
+//   B4. tile plane lz, which no later source plane reaches, is written out as
+//       FP64 partials (hi + lo) and its window slot cleared.
+// Four barriers per chunk and one per plane, where the kernel above takes 27
+// per batch of cells; 70 KB of shared memory, so three CTAs share an SM.
+constexpr int kB3 = 8;             // brick side (3D)
+constexpr int kE3 = kB3 + 2;       // haloed tile side
+constexpr int kPC = kB3 * kB3;     // cells in a brick plane
+constexpr int kPT = kE3 * kE3;     // cells in a tile plane
+constexpr int kM3 = 640;           // particles per chunk (a plane holds ~512 at 8 per cell)
+constexpr int kRec = 12;           // record floats: wx[3] wy[3] wz[3] F[3]
+// stride of the plane sums per (component, kz): 9 * 64 + 11 floats, so the
+// three kz lanes of a cell store to different banks
+constexpr int kTS = 9 * kPC + 11;
+
+constexpr int kSlots = 4;          // tile planes staged at once (a ring)
+constexpr int kPlaneF = 8 * kPT;   // floats per staged tile plane (8 per cell)
+
+struct Mixed3Smem {
+  size_t cs, bar, rec, win, total;
+};
+__host__ __device__ inline Mixed3Smem mixed3_smem() {
+  Mixed3Smem s;
+  s.cs = align_up((size_t)kSlots * kPlaneF * 4, 128);
+  s.bar = align_up(s.cs + (size_t)(kB3 * kB3 * kB3 + 1) * 4, 16);
+  s.rec = align_up(s.bar + 8 * kSlots + 16, 128);
+  const size_t rb = (size_t)kM3 * kRec * 4, tb = (size_t)9 * kTS * 4;
+  s.win = align_up(s.rec + (rb > tb ? rb : tb), 16);
+  s.total = s.win + (size_t)3 * 3 * kPT * 8;
+  return s;
+}
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+// Knuth's TwoSum on two lanes: s + v = s' + err exactly in each; err joins e.
+__device__ __forceinline__ void two_sum_acc2(float2& s, float2& e, float2 v) {
+  const float2 t = add2(s, v);
+  const float2 bp = sub2(t, s);
+  e = add2(e, add2(sub2(s, sub2(t, bp)), sub2(v, bp)));
+  s = t;
+}
+
+template <int SHAPE>
+__global__ void __launch_bounds__(kT, 3)
+    k_boris_brick_mixed3_dep(const __grid_constant__ CUtensorMap tmap, const Geo g,
+                             const int32_t* cells, const float* offs, const float* us,
+                             const float* w, const uint64_t* ids, int32_t* cell, float* off,
+                             float* u, float* wd, uint64_t* idd, int64_t n,
+                             const uint32_t* __restrict__ perm,
+                             const uint32_t* __restrict__ cstart, double* __restrict__ dpart,
+                             float h, float hl, float dtdx0, float dtdx1, float dtdx2,
+                             float inv_dt, int* __restrict__ status,
+                             uint8_t* __restrict__ outmask) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Mixed3Smem L = mixed3_smem();
+  const int tid = threadIdx.x;
+  constexpr int kV3 = kB3 * kB3 * kB3;
+  float* sbox = reinterpret_cast<float*>(smem);           // [slot][100 cells][8]
+  uint32_t* scs = reinterpret_cast<uint32_t*>(smem + L.cs);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);  // one per slot
+  int* sflag = reinterpret_cast<int*>(smem + L.bar + 8 * kSlots);
+  float* rec = reinterpret_cast<float*>(smem + L.rec);   // chunk records, then plane sums
+  float2* win = reinterpret_cast<float2*>(smem + L.win);  // [slot][component][100] (hi, lo)
+
+  const int64_t brick = blockIdx.x;
+  const int bx = (int)(brick % g.nb[0]);
+  const int by = (int)((brick / g.nb[0]) % g.nb[1]);
+  const int bz = (int)(brick / ((int64_t)g.nb[0] * g.nb[1]));
+  const int org[3] = {bx * kB3, by * kB3, bz * kB3};
+
+  // Tile plane tz (0..9) is staged in slot tz % kSlots; its copy completes
+  // phase tz / kSlots of that slot's barrier.  Thread 0 issues the copies:
+  // planes 0..3 now, plane lz + 4 once source plane lz is done with plane lz.
+  auto stage = [&](int tz) {
+    mbar_arrive_expect_tx(&bar[tz % kSlots], (uint32_t)(kPlaneF * 4));
+    tma_load_4d(sbox + (tz % kSlots) * kPlaneF, &tmap, &bar[tz % kSlots], 0, org[0], org[1],
+                org[2] + tz);
+  };
+  auto staged = [&](int tz) { return mbar_wait_bounded(&bar[tz % kSlots], (tz / kSlots) & 1); };
+  if (tid == 0) {
+    for (int k = 0; k < kSlots; ++k) mbar_init(&bar[k], 1);
+    *sflag = 0;
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int tz = 0; tz < kSlots; ++tz) stage(tz);
+  for (int i = tid; i <= kV3; i += kT) scs[i] = cstart[brick * kV3 + i];
+  for (int i = tid; i < 3 * 3 * kPT; i += kT) win[i] = make_float2(0.0f, 0.0f);
+  __syncthreads();
+
+  const float dtdx[3] = {dtdx0, dtdx1, dtdx2};
+  const uint32_t p1 = scs[kV3];
+  // end of the chunk that starts at slot s (s < p1): the end of s's plane or
+  // s + kM3, whichever comes first
+  auto chunk_end = [&](uint32_t s) -> uint32_t {
+    int z = 0;
+    while (scs[(z + 1) * kPC] <= s) ++z;
+    const uint32_t pe = scs[(z + 1) * kPC];
+    return pe - s < (uint32_t)kM3 ? pe : s + kM3;
+  };
+  // state of each thread's first particle of a chunk, loaded before the
+  // previous chunk's deposit so that phase A starts with it at hand
+  int32_t nc = 0;
+  float no[3] = {0.f, 0.f, 0.f}, nu[3] = {0.f, 0.f, 0.f}, nl[3] = {0.f, 0.f, 0.f}, nw = 1.0f;
+  uint32_t qc = 0, qn = 0;
+  auto prefetch = [&](uint32_t sbx, uint32_t sex) {
+    const uint32_t px = sbx + tid;
+    qc = px;
+    qn = px + kT;
+    if (perm) {
+      if (px < sex) qc = perm[px];
+      if (px + kT < sex) qn = perm[px + kT];
+    }
+    if (px < sex) {
+      nc = cells[qc];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        no[a] = offs[a * n + qc];
+        nu[a] = us[a * n + qc];
+        nl[a] = us[(a + 3) * n + qc];
+      }
+      if (w) nw = w[qc];
+    }
+  };
+  if (scs[0] < p1) prefetch(scs[0], chunk_end(scs[0]));
+
+  const int blc = tid / 3, bkz = tid - 3 * (tid / 3);  // B1 role (tid < 3 * kPC)
+  for (int lz = 0; lz < kB3; ++lz) {
+    const uint32_t pb = scs[lz * kPC], pe = scs[(lz + 1) * kPC];
+    // the stencils of plane lz reach tile planes lz .. lz + 2
+    if (pb < pe && !(staged(lz) && staged(lz + 1) && staged(lz + 2))) atomicOr(sflag, 1);
+    const float4* pz[3] = {reinterpret_cast<const float4*>(sbox + (lz % kSlots) * kPlaneF),
+                           reinterpret_cast<const float4*>(sbox + ((lz + 1) % kSlots) * kPlaneF),
+                           reinterpret_cast<const float4*>(sbox + ((lz + 2) % kSlots) * kPlaneF)};
+    for (uint32_t sb = pb; sb < pe; sb += kM3) {
+      const uint32_t se = pe - sb < (uint32_t)kM3 ? pe : sb + kM3;
+      // ---- A: push, one thread per particle; the permutation is read two
+      // slots ahead and the state one slot ahead of the computation
+      for (uint32_t p = sb + tid; p < se; p += kT) {
+        const int i = (int)(p - sb);
+        const int32_t ccur = nc;
+        float o[3] = {no[0], no[1], no[2]}, up[3] = {nu[0], nu[1], nu[2]};
+        float ul[3] = {nl[0], nl[1], nl[2]};
+        const float wcur = nw;
+        const uint32_t qcur = qc;
+        if (p + kT < se) {
+          qc = qn;
+          if (p + 2 * kT < se) qn = perm ? perm[p + 2 * kT] : p + 2 * kT;
+          nc = cells[qc];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            no[a] = offs[a * n + qc];
+            nu[a] = us[a * n + qc];
+            nl[a] = us[(a + 3) * n + qc];
+          }
+          if (w) nw = w[qc];
+        }
+        if (w && wd != w) wd[p] = wcur;  // carry the read-only planes over
+        if (ids && idd != ids) idd[p] = ids[qcur];
+        int j[3];
+        cell_coords(g, ccur, j);
+        int l[3];
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          l[a] = j[a] - org[a];
+          ok = ok && l[a] >= 0 && l[a] < kB3;
+        }
+        if (ok) {  // the particle must sit in the cell it was sorted into
+          const int lc = (l[2] * kB3 + l[1]) * kB3 + l[0];
+          ok = p >= scs[lc] && p < scs[lc + 1];
+        }
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+        if (!ok) {
+          atomicOr(status, ST_DOMAIN);
+          if (outmask) outmask[p] = 0;
+          cell[p] = ccur;  // left as it was
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            off[a * n + p] = o[a];
+            u[a * n + p] = up[a];
+            u[(a + 3) * n + p] = ul[a];
+          }
+        } else {
+          float wx[3], wy[3], wz[3];
+          shape_weights<SHAPE>(o[0], wx);
+          shape_weights<SHAPE>(o[1], wy);
+          shape_weights<SHAPE>(o[2], wz);
+          float2 f2[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+          const int c0 = 2 * (l[1] * kE3 + l[0]);  // the stencil's first cell in a tile plane
+#pragma unroll
+          for (int kz = 0; kz < 3; ++kz)
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+              const float wzy = wz[kz] * wy[ky];
+              const float4* row = pz[kz] + c0 + 2 * ky * kE3;
+#pragma unroll
+              for (int kx = 0; kx < 3; ++kx)
+                acc_point(f2, wzy * wx[kx], row[2 * kx], row[2 * kx + 1]);
+            }
+          const float f[6] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y};
+          float du[3];
+          boris_f32(up, ul, f, f + 3, h, hl, du);
+          const float gi = rsqrtf(1.0f + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+          bool out = false;
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            move_axis(o[a], j[a], up[a] * gi * dtdx[a], g.n[a], g.open[a], out);
+          if (!(isfinite(up[0]) && isfinite(up[1]) && isfinite(up[2]) && isfinite(o[0]) &&
+                isfinite(o[1]) && isfinite(o[2])))
+            atomicOr(status, ST_NONFINITE);
+          if (outmask) outmask[p] = out ? 1 : 0;
+          cell[p] = (j[2] * g.n[1] + j[1]) * g.n[0] + j[0];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            off[a * n + p] = o[a];
+            u[a * n + p] = up[a];
+            u[(a + 3) * n + p] = ul[a];
+          }
+          const float wdt = wcur * inv_dt;
+          r0 = make_float4(wx[0], wx[1], wx[2], wy[0]);
+          r1 = make_float4(wy[1], wy[2], wz[0], wz[1]);
+          r2 = make_float4(wz[2], du[0] * wdt, du[1] * wdt, du[2] * wdt);
+        }
+        float4* rq = reinterpret_cast<float4*>(rec + i * kRec);
+        rq[0] = r0;
+        rq[1] = r1;
+        rq[2] = r2;
+      }
+      if (se < p1) prefetch(se, chunk_end(se));
+      __syncthreads();
+      if (*sflag) {  // a staging copy did not complete: wait for ours (bounded), give up
+        if (tid == 0) {
+          atomicOr(status, ST_TIMEOUT);
+          for (int tz = lz; tz < kE3 && tz < lz + kSlots; ++tz) staged(tz);
+        }
+        return;
+      }
+      // ---- B1: one thread per (cell, kz) of this plane
+      float2 T01[9];  // (component 0, component 1) of target (ky, kx): index ky * 3 + kx
+      float T2[9];    // component 2
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        T01[k] = make_float2(0.0f, 0.0f);
+        T2[k] = 0.0f;
+      }
+      if (tid < 3 * kPC) {
+        uint32_t ra = scs[lz * kPC + blc], rb = scs[lz * kPC + blc + 1];
+        ra = ra > sb ? ra : sb;
+        rb = rb < se ? rb : se;
+        for (uint32_t r = ra; r < rb; ++r) {
+          const float4* q = reinterpret_cast<const float4*>(rec + (r - sb) * kRec);
+          const float4 a = q[0], b = q[1], c4 = q[2];
+          const float wzk = bkz == 0 ? b.z : (bkz == 1 ? b.w : c4.x);
+          const float P[3] = {wzk * a.w, wzk * b.x, wzk * b.y};
+          const float wx[3] = {a.x, a.y, a.z};
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) {
+            const float2 Q01 =
+                __fmul2_rn(make_float2(wx[kx], wx[kx]), make_float2(c4.y, c4.z));
+            const float Q2 = wx[kx] * c4.w;
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+              T01[ky * 3 + kx] = __ffma2_rn(make_float2(P[ky], P[ky]), Q01, T01[ky * 3 + kx]);
+              T2[ky * 3 + kx] = fmaf(P[ky], Q2, T2[ky * 3 + kx]);
+            }
+          }
+        }
+      }
+      __syncthreads();
+      // ---- B2: the chunk's per-cell sums to shared memory
+      if (tid < 3 * kPC) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          rec[(0 * 3 + bkz) * kTS + k * kPC + blc] = T01[k].x;
+          rec[(1 * 3 + bkz) * kTS + k * kPC + blc] = T01[k].y;
+          rec[(2 * 3 + bkz) * kTS + k * kPC + blc] = T2[k];
+        }
+      }
+      __syncthreads();
+      // ---- B3: pull into the window, targets (tx, tx + 1) of tile row ty in
+      // tile plane lz + kz, one component
+      for (int it = tid; it < 3 * 3 * kE3 * (kE3 / 2); it += kT) {
+        const int txp = it % (kE3 / 2);
+        int r = it / (kE3 / 2);
+        const int ty = r % kE3;
+        r /= kE3;
+        const int kz = r % 3;
+        const int c = r / 3;
+        const int tx = 2 * txp;
+        const float* Tb = rec + (c * 3 + kz) * kTS;
+        float2 s = make_float2(0.0f, 0.0f), e = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
+          const int ly = ty - ky;
+          const bool yok = ly >= 0 && ly < kB3;
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) {
+            const int la = tx - kx, lb = tx + 1 - kx;
+            const float* row = Tb + (ky * 3 + kx) * kPC + ly * kB3;
+            float2 v = make_float2(0.0f, 0.0f);
+            if (yok && la >= 0 && la < kB3) v.x = row[la];
+            if (yok && lb >= 0 && lb < kB3) v.y = row[lb];
+            two_sum_acc2(s, e, v);
+          }
+        }
+        float4* wp = reinterpret_cast<float4*>(win + (((lz + kz) % 3) * 3 + c) * kPT + ty * kE3 + tx);
+        const float4 acc = *wp;  // (hi, lo) of target tx, then of tx + 1
+        float2 hi = make_float2(acc.x, acc.z), lo = make_float2(acc.y, acc.w);
+        two_sum_acc2(hi, lo, s);
+        lo = add2(lo, e);
+        *wp = make_float4(hi.x, lo.x, hi.y, lo.y);
+      }
+      __syncthreads();
+    }
+    // ---- B4: tile plane lz is complete (and 8, 9 after the last plane)
+    const int zl = lz == kB3 - 1 ? kE3 - 1 : lz;
+    for (int z = lz; z <= zl; ++z) {
+      float2* ws = win + (z % 3) * 3 * kPT;
+      for (int i = tid; i < 3 * kPT; i += kT) {
+        const int c = i / kPT, t = i - c * kPT;
+        const float2 v = ws[i];
+        dpart[(brick * 3 + c) * g.ev + z * kPT + t] = (double)v.x + (double)v.y;
+        ws[i] = make_float2(0.0f, 0.0f);
+      }
+    }
+    __syncthreads();
+    // tile plane lz is read by no later plane: its slot takes plane lz + 4
+    // (after the slot's previous copy, bounded, should nobody have waited)
+    if (tid == 0 && lz + kSlots < kE3) {
+      if (staged(lz))
+        stage(lz + kSlots);
+      else
+        atomicOr(sflag, 1);  // seen after the next barrier
+    }
+  }
+  // the copies into slots that were not refilled: waited for before the exit
+  // (at once if a plane's stencils already did)
+  if (tid == 0) {
+    bool ok = *sflag == 0;
+    for (int tz = kE3 - kSlots; tz < kE3; ++tz) ok = staged(tz) && ok;
+    if (!ok) atomicOr(status, ST_TIMEOUT);
+  }
+}
+
 // nsteps fused steps of one particle in registers: gather from the padded
 // global f32 copy, Boris, move.  Shared by the particle-order kernel and the
 // serving kernel so a particle gets the same bits whichever runs it.
@@ -613,17 +977,22 @@ MixedArgs mixed_args(const part_ctx* c, double qm, double dt) {
 
 template <int SHAPE, int DIM, bool DEP>
 cudaError_t brick_mixed(part_ctx* c, const MixedArgs& a) {
-  auto kern = k_boris_brick_mixed<SHAPE, DIM, DEP>;
-  const MixedSmem L = mixed_smem(c->geo);
+  // 3D with deposit: the plane-by-plane kernel (8^3 bricks, 10^3 staged box)
+  const bool planes = DIM == 3 && DEP;
+  if (planes && (c->geo.V != kB3 * kB3 * kB3 || c->geo.box[0] != kE3 ||
+                 c->geo.box[1] != kE3 || c->geo.box[2] != kE3 || c->geo.ev != kE3 * kE3 * kE3))
+    return cudaErrorInvalidConfiguration;
+  auto kern = planes ? k_boris_brick_mixed3_dep<SHAPE> : k_boris_brick_mixed<SHAPE, DIM, DEP>;
+  const size_t smem_bytes = planes ? mixed3_smem().total : mixed_smem(c->geo).total;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)L.total);
+                                       (int)smem_bytes);
   if (e != cudaSuccess) return e;
   // read the current buffer (through the sort's permutation, if one is
   // pending, into the other buffer; else in place)
   const PState src = state_of(c, c->cur_alt);
   const PState dst = c->perm_pend ? state_of(c, !c->cur_alt) : src;
-  kern<<<(unsigned)c->geo.nbricks, kT, L.total, c->stream>>>(
-      c->tmap, c->geo, (const int32_t*)src.x, (const float*)src.off, (const float*)src.u,
+  kern<<<(unsigned)c->geo.nbricks, kT, smem_bytes, c->stream>>>(
+      planes ? c->tmap_plane : c->tmap, c->geo, (const int32_t*)src.x, (const float*)src.off, (const float*)src.u,
       (const float*)src.w, src.id, (int32_t*)dst.x, (float*)dst.off, (float*)dst.u,
       (float*)dst.w, dst.id, c->n, c->perm_pend, c->cstart, c->dpart, a.h, a.hl, a.dtdx[0],
       a.dtdx[1], a.dtdx[2], a.inv_dt, c->status, c->outmask);
