@@ -512,10 +512,10 @@ part_status part_probe_fp64_fma(void* cuda_stream, double* sink, int ctas_per_sm
 /* ---- Sort without any device allocation ----------------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory when they need a sort, so cannot provide the
- * workspace that part_init requires.  Examples: code that is being captured
- * into a CUDA graph, a plug-in inside a host code that owns every device byte
- * through its own memory pool, or a latency-critical loop where a cudaMalloc
- * (which may synchronise the device) is not acceptable.
+ * workspace that part_init requires.  Examples: a plug-in inside a host code
+ * that owns every device byte through its own memory pool, or a
+ * latency-critical loop where a cudaMalloc (which may synchronise the device)
+ * is not acceptable.
  *
  * Same result as part_sort on a PART_FP64 / PART_BORIS context: the particles
  * are stably sorted by the brick cell key (see part_brick_dims) and x[3][n],

@@ -2,10 +2,9 @@
 // allocation and without a caller workspace.
 //
 // Some callers cannot allocate device memory at the moment they need a sort:
-// code that is being captured into a CUDA graph, a plug-in whose host
-// application owns every device byte through its own pool, or a
-// latency-critical loop where an allocation (which may synchronise the device)
-// is not acceptable.  This entry point takes its scratch from one fixed
+// a plug-in whose host application owns every device byte through its own
+// pool, or a latency-critical loop where an allocation (which may synchronise
+// the device) is not acceptable.  This entry point takes its scratch from one fixed
 // array compiled into the library instead.
 //
 // The scratch is a file-scope static __device__ array of

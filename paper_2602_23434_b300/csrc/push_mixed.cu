@@ -475,18 +475,22 @@ __global__ void __launch_bounds__(kT, 3)
 //   B1. one thread per (cell, kz) sums, over the cell's particles in index
 //       order, the 27 contributions (ky, kx, component) that land in tile
 //       plane lz + kz: the same f32 products, summed in the same order, as
-//       the per-cell sums of the kernel above;
+//       the per-cell sums of the kernel above.  Cells are handed to threads
+//       fullest first, so a warp's lanes loop over similar counts;
 //   B2. the sums go to shared memory (over the records, no longer needed);
 //   B3. one thread per (pair of x-adjacent targets, component, kz) takes the
 //       sums of the up to 9 source cells that reach each target, in a fixed
 //       order, into a two-float value (TwoSum), and adds that into a rolling
 //       window of three tile planes held as two-float accumulators.  No two
 //       threads share a target, so no ordered passes are needed.
-// After the plane:
-//   B4. tile plane lz, which no later source plane reaches, is written out as
-//       FP64 partials (hi + lo) and its window slot cleared.
-// Four barriers per chunk and one per plane, where the kernel above takes 27
-// per batch of cells; 70 KB of shared memory, so three CTAs share an SM.
+//   B4. tile planes that no later source plane reaches are written out as
+//       FP64 partials (hi + lo) and their window slots cleared, by the threads
+//       that B1 leaves idle (the rest at the end of the brick).
+// Four barriers per chunk, where the kernel above takes 27 per batch of
+// cells.  The field box is staged as a ring of four tile planes, each copied
+// by TMA once no plane's stencil needs the one it replaces: 52 KB of shared
+// memory, three CTAs per SM, and room left in L1 for the state's loads
+// through the sort's permutation.
 constexpr int kB3 = 8;             // brick side (3D)
 constexpr int kE3 = kB3 + 2;       // haloed tile side
 constexpr int kPC = kB3 * kB3;     // cells in a brick plane
@@ -507,7 +511,7 @@ __host__ __device__ inline Mixed3Smem mixed3_smem() {
   Mixed3Smem s;
   s.cs = align_up((size_t)kSlots * kPlaneF * 4, 128);
   s.bar = align_up(s.cs + (size_t)(kB3 * kB3 * kB3 + 1) * 4, 16);
-  s.rec = align_up(s.bar + 8 * kSlots + 16, 128);
+  s.rec = align_up(s.bar + 8 * kSlots + 16 + 32 * 4 + 64, 128);
   const size_t rb = (size_t)kM3 * kRec * 4, tb = (size_t)9 * kTS * 4;
   s.win = align_up(s.rec + (rb > tb ? rb : tb), 16);
   s.total = s.win + (size_t)3 * 3 * kPT * 8;
@@ -524,6 +528,39 @@ __device__ __forceinline__ void two_sum_acc2(float2& s, float2& e, float2 v) {
   const float2 bp = sub2(t, s);
   e = add2(e, add2(sub2(s, sub2(t, bp)), sub2(v, bp)));
   s = t;
+}
+
+// Warp 0: order the 64 cells of a brick plane by their particle count in the
+// slot range [sb, se), fullest first (counts above 31 rank as 31), so that
+// the lanes of each B1 warp loop over cells of similar counts.  ord[r] is the
+// cell of rank r.  Equal counts come in any order: which thread sums a cell
+// does not change its sums.
+__device__ __forceinline__ void rank_cells(const uint32_t* cs, uint32_t sb, uint32_t se,
+                                           int* cur, uint8_t* ord, int lane) {
+  auto count = [&](int c) -> int {
+    const uint32_t a = cs[c] > sb ? cs[c] : sb, b = cs[c + 1] < se ? cs[c + 1] : se;
+    const int k = b > a ? (int)(b - a) : 0;
+    return k < 31 ? k : 31;
+  };
+  const int na = count(lane), nb = count(lane + 32);
+  cur[lane] = 0;
+  __syncwarp();
+  atomicAdd(&cur[na], 1);
+  atomicAdd(&cur[nb], 1);
+  __syncwarp();
+  // cells with a count above v, for lane v: a suffix sum over the lanes
+  const int h = cur[lane];
+  int suf = h;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_down_sync(0xffffffffu, suf, d);
+    if (lane + d < 32) suf += t;
+  }
+  __syncwarp();
+  cur[lane] = suf - h;
+  __syncwarp();
+  ord[atomicAdd(&cur[na], 1)] = (uint8_t)lane;
+  ord[atomicAdd(&cur[nb], 1)] = (uint8_t)(lane + 32);
 }
 
 template <int SHAPE>
@@ -545,6 +582,8 @@ __global__ void __launch_bounds__(kT, 3)
   uint32_t* scs = reinterpret_cast<uint32_t*>(smem + L.cs);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);  // one per slot
   int* sflag = reinterpret_cast<int*>(smem + L.bar + 8 * kSlots);
+  int* scur = reinterpret_cast<int*>(smem + L.bar + 8 * kSlots + 16);      // [32] cell ranking
+  uint8_t* sord = reinterpret_cast<uint8_t*>(smem + L.bar + 8 * kSlots + 16 + 32 * 4);  // [64]
   float* rec = reinterpret_cast<float*>(smem + L.rec);   // chunk records, then plane sums
   float2* win = reinterpret_cast<float2*>(smem + L.win);  // [slot][component][100] (hi, lo)
 
@@ -611,6 +650,19 @@ __global__ void __launch_bounds__(kT, 3)
   if (scs[0] < p1) prefetch(scs[0], chunk_end(scs[0]));
 
   const int blc = tid / 3, bkz = tid - 3 * (tid / 3);  // B1 role (tid < 3 * kPC)
+  // tile planes below zw have been written out; tile plane z is complete
+  // once source plane z is, and is written out by the threads that B1 leaves
+  // idle (before the next pull needs its slot), or at the end
+  int zw = 0;
+  auto write_out = [&](int z, int t0, int nt) {
+    float2* ws = win + (z % 3) * 3 * kPT;
+    for (int i = t0; i < 3 * kPT; i += nt) {
+      const int c = i / kPT, t = i - c * kPT;
+      const float2 v = ws[i];
+      dpart[(brick * 3 + c) * g.ev + z * kPT + t] = (double)v.x + (double)v.y;
+      ws[i] = make_float2(0.0f, 0.0f);
+    }
+  };
   for (int lz = 0; lz < kB3; ++lz) {
     const uint32_t pb = scs[lz * kPC], pe = scs[(lz + 1) * kPC];
     // the stencils of plane lz reach tile planes lz .. lz + 2
@@ -620,6 +672,7 @@ __global__ void __launch_bounds__(kT, 3)
                            reinterpret_cast<const float4*>(sbox + ((lz + 2) % kSlots) * kPlaneF)};
     for (uint32_t sb = pb; sb < pe; sb += kM3) {
       const uint32_t se = pe - sb < (uint32_t)kM3 ? pe : sb + kM3;
+      if (tid < 32) rank_cells(scs + lz * kPC, sb, se, scur, sord, tid);
       // ---- A: push, one thread per particle; the permutation is read two
       // slots ahead and the state one slot ahead of the computation
       for (uint32_t p = sb + tid; p < se; p += kT) {
@@ -730,12 +783,15 @@ __global__ void __launch_bounds__(kT, 3)
         T01[k] = make_float2(0.0f, 0.0f);
         T2[k] = 0.0f;
       }
-      if (tid < 3 * kPC) {
-        uint32_t ra = scs[lz * kPC + blc], rb = scs[lz * kPC + blc + 1];
+      if (tid >= 3 * kPC) {
+        for (int z = zw; z < lz; ++z) write_out(z, tid - 3 * kPC, kT - 3 * kPC);
+      } else {
+        const int cl = sord[blc];  // the cell of rank blc
+        uint32_t ra = scs[lz * kPC + cl], rb = scs[lz * kPC + cl + 1];
         ra = ra > sb ? ra : sb;
         rb = rb < se ? rb : se;
-        for (uint32_t r = ra; r < rb; ++r) {
-          const float4* q = reinterpret_cast<const float4*>(rec + (r - sb) * kRec);
+        const float4* q = reinterpret_cast<const float4*>(rec) + (ra - sb) * (kRec / 4);
+        for (uint32_t r = ra; r < rb; ++r, q += kRec / 4) {
           const float4 a = q[0], b = q[1], c4 = q[2];
           const float wzk = bkz == 0 ? b.z : (bkz == 1 ? b.w : c4.x);
           const float P[3] = {wzk * a.w, wzk * b.x, wzk * b.y};
@@ -756,11 +812,12 @@ __global__ void __launch_bounds__(kT, 3)
       __syncthreads();
       // ---- B2: the chunk's per-cell sums to shared memory
       if (tid < 3 * kPC) {
+        const int cl = sord[blc];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-          rec[(0 * 3 + bkz) * kTS + k * kPC + blc] = T01[k].x;
-          rec[(1 * 3 + bkz) * kTS + k * kPC + blc] = T01[k].y;
-          rec[(2 * 3 + bkz) * kTS + k * kPC + blc] = T2[k];
+          rec[(0 * 3 + bkz) * kTS + k * kPC + cl] = T01[k].x;
+          rec[(1 * 3 + bkz) * kTS + k * kPC + cl] = T01[k].y;
+          rec[(2 * 3 + bkz) * kTS + k * kPC + cl] = T2[k];
         }
       }
       __syncthreads();
@@ -798,19 +855,8 @@ __global__ void __launch_bounds__(kT, 3)
         *wp = make_float4(hi.x, lo.x, hi.y, lo.y);
       }
       __syncthreads();
+      zw = lz;
     }
-    // ---- B4: tile plane lz is complete (and 8, 9 after the last plane)
-    const int zl = lz == kB3 - 1 ? kE3 - 1 : lz;
-    for (int z = lz; z <= zl; ++z) {
-      float2* ws = win + (z % 3) * 3 * kPT;
-      for (int i = tid; i < 3 * kPT; i += kT) {
-        const int c = i / kPT, t = i - c * kPT;
-        const float2 v = ws[i];
-        dpart[(brick * 3 + c) * g.ev + z * kPT + t] = (double)v.x + (double)v.y;
-        ws[i] = make_float2(0.0f, 0.0f);
-      }
-    }
-    __syncthreads();
     // tile plane lz is read by no later plane: its slot takes plane lz + 4
     // (after the slot's previous copy, bounded, should nobody have waited)
     if (tid == 0 && lz + kSlots < kE3) {
@@ -820,6 +866,8 @@ __global__ void __launch_bounds__(kT, 3)
         atomicOr(sflag, 1);  // seen after the next barrier
     }
   }
+  // ---- B4: the tile planes not yet written out
+  for (int z = zw; z < kE3; ++z) write_out(z, tid, kT);
   // the copies into slots that were not refilled: waited for before the exit
   // (at once if a plane's stencils already did)
   if (tid == 0) {

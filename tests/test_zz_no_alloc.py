@@ -1,9 +1,9 @@
 """part_sort_fp64_noalloc, the sort entry point that allocates nothing.
 
 Some callers cannot allocate device memory at the point where they sort:
-code being captured into a CUDA graph, a plug-in whose host code owns every
-device byte through its own pool, or a latency-critical loop that cannot
-afford an allocation that may synchronise the device.  For them the library
+a plug-in whose host code owns every device byte through its own pool, or a
+latency-critical loop that cannot afford an allocation that may synchronise
+the device.  For them the library
 keeps a fixed scratch array inside libpart.so.  These tests call that entry
 point through the C ABI and check that it gives bit for bit what part_sort
 (the workspace-based entry point) gives on the same particles, twice in a
