@@ -61,7 +61,7 @@ BYTES_PER_PSTEP_BORIS_DEP = 96 + 8 + 6 + 3
 TRAFFIC_PER_PARTICLE_BRICK_F64 = 264.987392e6 / 2097152  # ncu dram r+w, 64^3 capture
 # Same for the mixed brick kernel, from an ncu capture of the 128^3 case
 # (1715.1 MB for 16,777,216 particles).
-TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1715.104512e6 / 16777216   # ncu dram r+w, 128^3 capture
+TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1710.065664e6 / 16777216   # ncu dram r+w, 128^3 capture
 
 
 def peaks():
