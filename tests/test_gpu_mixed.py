@@ -106,12 +106,11 @@ def test_mixed_sort_bit_exact(dim, n, ppc):
     assert np.array_equal(cs, O.cell_start(p.nkeys, keys[perm]).astype(np.int64))
 
 
-@pytest.mark.parametrize("dim,n,ppc", [(3, 20, 8), (2, 40, 16)])
-@pytest.mark.parametrize("shape", [P.TSC, P.CIC])
-def test_mixed_step_and_deposit_vs_fp64(dim, n, ppc, shape):
+def _check_step_and_deposit(dim, n, shape, f, cell, off, uf, wf):
+    """One sorted mixed step with deposit against the FP64 oracle from the
+    identical state, then the same step again from that state: bitwise equal."""
+    N = cell.shape[0]
     og = O.make_grid(dim, (n, n, n))
-    f = synth.em_fields(dim, n, 23, v_rms=0.05).reshape(6, -1)
-    N, cell, off, uf, wf, ids = _state(dim, n, ppc, 7)
     qm, dt = 1.0, 0.5 * (2.0 / n)
     p = P.Part(P.make_grid(dim, n), P.MIXED, shape, P.BORIS, capacity=N)
     p.set_fields(torch.as_tensor(f.astype(np.float32)).cuda())
@@ -148,6 +147,44 @@ def test_mixed_step_and_deposit_vs_fp64(dim, n, ppc, shape):
     p.deposit(out2)
     p.sync()
     assert torch.equal(out, out2) and torch.equal(cd, cd2) and torch.equal(od, od2)
+
+
+@pytest.mark.parametrize("dim,n,ppc", [(3, 20, 8), (2, 40, 16)])
+@pytest.mark.parametrize("shape", [P.TSC, P.CIC])
+def test_mixed_step_and_deposit_vs_fp64(dim, n, ppc, shape):
+    f = synth.em_fields(dim, n, 23, v_rms=0.05).reshape(6, -1)
+    N, cell, off, uf, wf, ids = _state(dim, n, ppc, 7)
+    _check_step_and_deposit(dim, n, shape, f, cell, off, uf, wf)
+
+
+@pytest.mark.parametrize("case", ["dense", "clustered"])
+def test_mixed_deposit_full_and_empty_planes(case):
+    """The 3D kernel with deposit takes a brick plane (8 x 8 cells) in chunks
+    of up to 640 particles and skips empty planes: planes of about 1536
+    particles (24 per cell, three chunks each, partial bricks on a 12^3
+    grid), and a clustered set (one cell holding 900 particles, a quarter of
+    the particles in one brick corner, the other bricks' planes mostly
+    empty), both against the FP64 oracle."""
+    dim = 3
+    if case == "dense":
+        n = 12
+        N, cell, off, uf, wf, ids = _state(dim, n, 24, 31)
+    else:
+        n = 16
+        rng = np.random.default_rng(32)
+        N = 4000
+        x, u, _, _ = synth.particles(dim, None, N, 33, u_th=0.3)
+        dx = 2.0 / n
+        # 900 particles in cell (5, 6, 7); 1000 in the 2^3 cells at the corner of brick 0
+        x[:, :900] = (-1.0 + (np.array([5, 6, 7])[:, None] + rng.random((3, 900))) * dx)
+        x[:, 900:1900] = -1.0 + rng.random((3, 1000)) * 2 * dx
+        # the rest in the upper half in z only: the lower bricks' upper planes stay empty
+        x[2, 1900:] = rng.random(N - 1900) * 0.999
+        cell, off = _to_mixed(x, n, dim)
+        uf = _u6(u)
+        wf = rng.uniform(0.5, 2.0, N).astype(np.float32)
+    f = synth.em_fields(dim, n, 29, v_rms=0.05).reshape(6, -1)
+    _check_step_and_deposit(dim, n, P.TSC, f, cell, off, uf, wf)
 
 
 def _angle(u):
