@@ -852,65 +852,147 @@ cudaError_t flush_pending(part_ctx* c) {
 
 namespace {
 
+// ---- one row moved within its own buffer: dst[i] = src[i], i < len, where
+// the two ranges may overlap (the new row stride after a compaction or an
+// injection).  Blocks of kMoveB elements are taken in copy order (ascending
+// when dst < src, descending when dst > src) through a ticket counter; a
+// block reads its source into registers, publishes that it has read, and
+// writes only after the at most two blocks whose sources its destination
+// covers have published the same.  Those blocks hold earlier tickets and read
+// before they wait on anything, so every wait ends; each is bounded all the
+// same (ST_TIMEOUT, and the block's writes are skipped).  flags[0] is the
+// ticket counter, flags[1 + b] block b's published read; both start at 0.
+constexpr int kMoveT = 256, kMoveE = 8, kMoveB = kMoveT * kMoveE;
+
 template <typename T>
-cudaError_t fill_rows(part_ctx* c, T* base, int rows, const uint8_t* del, int64_t n,
-                      int64_t nnew, int gb) {
+__device__ __forceinline__ void move_row_body(const T* src, T* dst, int64_t len, uint32_t* flags,
+                                              int* status) {
+  __shared__ int64_t s_b;
+  __shared__ int s_ok;
+  const int64_t nblk = (len + kMoveB - 1) / kMoveB;
+  const bool up = dst > src;
+  const int64_t d = dst - src;  // destination offset in source elements
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int64_t t = (int64_t)atomicAdd(&flags[0], 1u);
+      s_b = t < nblk ? (up ? nblk - 1 - t : t) : -1;
+    }
+    __syncthreads();
+    const int64_t b = s_b;
+    if (b < 0) break;
+    const int64_t i0 = b * kMoveB;
+    T v[kMoveE];
+#pragma unroll
+    for (int k = 0; k < kMoveE; ++k) {
+      const int64_t i = i0 + k * kMoveT + threadIdx.x;
+      if (i < len) v[k] = src[i];
+    }
+    __syncthreads();  // the whole block has read
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicExch(&flags[1 + b], 1u);
+      // source blocks that the destination [i0 + d, i1 + d) covers
+      const int64_t i1 = i0 + kMoveB < len ? i0 + kMoveB : len;
+      int64_t lo = (i0 + d) / kMoveB, hi = (i1 - 1 + d) / kMoveB;
+      if (i0 + d < 0) lo = -1;  // floor for negative offsets (no such block)
+      lo = lo < 0 ? 0 : lo;
+      hi = hi < nblk - 1 ? hi : nblk - 1;
+      bool ok = true;
+      for (int64_t q = lo; q <= hi && ok; ++q) {
+        if (q == b) continue;
+        const uint64_t t0 = global_ns();
+        uint32_t it = 0;
+        while (atomicAdd(&flags[1 + q], 0u) == 0u) {
+          if (++it > (1u << 24) || global_ns() - t0 > kWaitLimitNs) {
+            ok = false;
+            break;
+          }
+        }
+      }
+      __threadfence();
+      if (!ok) atomicOr(status, ST_TIMEOUT);
+      s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_ok) {
+#pragma unroll
+      for (int k = 0; k < kMoveE; ++k) {
+        const int64_t i = i0 + k * kMoveT + threadIdx.x;
+        if (i < len) dst[i] = v[k];
+      }
+    }
+    __syncthreads();  // s_b and s_ok are reused
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMoveT)
+    k_move_row(const T* src, T* dst, int64_t len, uint32_t* flags, int* status) {
+  move_row_body<T>(src, dst, len, flags, status);
+}
+
+// Row r of a compaction: from stride n to stride nnew = n - D[n], with D[n]
+// (the deletion count) read on the device, so the host need not wait for it.
+template <typename T>
+__global__ void __launch_bounds__(kMoveT)
+    k_move_row_compact(T* base, int64_t n, int64_t r, const uint32_t* __restrict__ dn,
+                       uint32_t* flags, int* status) {
+  const int64_t nnew = n - (int64_t)*dn;
+  if (nnew == n) return;
+  move_row_body<T>(base + r * n, base + r * nnew, nnew, flags, status);
+}
+
+// Move len elements from src to dst in the stream, overlap allowed.
+template <typename T>
+cudaError_t move_row(part_ctx* c, const T* src, T* dst, int64_t len) {
+  if (len <= 0 || src == dst) return cudaSuccess;
+  if (src + len <= dst || dst + len <= src)
+    return cudaMemcpyAsync(dst, src, sizeof(T) * len, cudaMemcpyDeviceToDevice, c->stream);
+  const int64_t nblk = (len + kMoveB - 1) / kMoveB;
+  uint32_t* flags = (uint32_t*)c->tmp;  // (1 + nblk) words; tmp holds 8 * capacity bytes
+  cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * (1 + nblk), c->stream);
+  if (e != cudaSuccess) return e;
+  const int64_t grid = std::min<int64_t>(nblk, (int64_t)c->sms * 8);
+  k_move_row<T><<<(unsigned)grid, kMoveT, 0, c->stream>>>(src, dst, len, flags, c->status);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+// Fill the holes of every row, then move rows r >= 1 from stride n to stride
+// nnew (the deletion count stays on the device: D[n]).
+template <typename T>
+cudaError_t fill_rows(part_ctx* c, T* base, int rows, const uint8_t* del, int64_t n, int gb) {
   for (int r = 0; r < rows; ++r) {
     k_fill_holes<T><<<gb, 256, 0, c->stream>>>(base + (int64_t)r * n, del, c->keys[0],
                                                c->keys[1], n);
     c->launches++;
   }
   // Rows r >= 1 move from stride n to stride nnew: row r shifts down by
-  // S = r (n - nnew) elements.  Copied in stream-ordered chunks of S, no chunk
-  // overlaps its own source, and each chunk overwrites only source already
-  // copied; when that would take many chunks, through the scratch row.
-  for (int r = 1; r < rows && nnew < n; ++r) {
-    T* src = base + (int64_t)r * n;
-    T* dst = base + (int64_t)r * nnew;
-    const int64_t S = (int64_t)r * (n - nnew);
-    cudaError_t e = cudaSuccess;
-    if ((nnew + S - 1) / S <= 16) {
-      for (int64_t o = 0; o < nnew && e == cudaSuccess; o += S)
-        e = cudaMemcpyAsync(dst + o, src + o, sizeof(T) * std::min(S, nnew - o),
-                            cudaMemcpyDeviceToDevice, c->stream);
-    } else {
-      e = cudaMemcpyAsync(c->tmp, src, sizeof(T) * nnew, cudaMemcpyDeviceToDevice, c->stream);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dst, c->tmp, sizeof(T) * nnew, cudaMemcpyDeviceToDevice, c->stream);
-    }
+  // r (n - nnew) elements, in place, lowest row first (a row only overwrites
+  // source rows already moved, and its own source as the move allows).
+  const int64_t nblk = (n + kMoveB - 1) / kMoveB;
+  const int64_t grid = std::min<int64_t>(nblk, (int64_t)c->sms * 8);
+  uint32_t* flags = (uint32_t*)c->tmp;  // (1 + nblk) words; tmp holds 8 * capacity bytes
+  for (int r = 1; r < rows; ++r) {
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * (1 + nblk), c->stream);
     if (e != cudaSuccess) return e;
+    k_move_row_compact<T><<<(unsigned)grid, kMoveT, 0, c->stream>>>(base, n, r, c->keys[0] + n,
+                                                                    flags, c->status);
+    c->launches++;
   }
   return cudaGetLastError();
 }
 
 // Injection: rows r >= 1 move up from stride n to stride n + k (row r by
-// S = r k elements), the highest row first so that a row only overwrites
-// source rows already moved; a row that overlaps its own source is copied
-// back to front in stream-ordered chunks of at most S (no chunk overlaps the
-// source still to be read), or through the scratch row when that would take
-// many chunks.  Then the k new elements of each row go to its slots n..n+k-1.
+// r k elements), in place, the highest row first so that a row only
+// overwrites source rows already moved (and its own source as k_move_row
+// allows).  Then the k new elements of each row go to its slots n..n+k-1.
 template <typename T>
 cudaError_t grow_rows(part_ctx* c, T* base, int rows, int64_t n, int64_t k, const T* src) {
   cudaError_t e = cudaSuccess;
   const int64_t m = n + k;
-  for (int r = rows - 1; r >= 1 && n > 0 && k > 0 && e == cudaSuccess; --r) {
-    T* from = base + (int64_t)r * n;
-    T* to = base + (int64_t)r * m;
-    const int64_t S = (int64_t)r * k;
-    if (S >= n) {
-      e = cudaMemcpyAsync(to, from, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream);
-    } else if ((n + S - 1) / S <= 16) {
-      for (int64_t hi = n; hi > 0 && e == cudaSuccess; hi -= S) {
-        const int64_t lo = hi > S ? hi - S : 0;
-        e = cudaMemcpyAsync(to + lo, from + lo, sizeof(T) * (hi - lo), cudaMemcpyDeviceToDevice,
-                            c->stream);
-      }
-    } else {
-      e = cudaMemcpyAsync(c->tmp, from, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(to, c->tmp, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream);
-    }
-  }
+  for (int r = rows - 1; r >= 1 && n > 0 && k > 0 && e == cudaSuccess; --r)
+    e = move_row<T>(c, base + (int64_t)r * n, base + (int64_t)r * m, n);
   for (int r = 0; r < rows && k > 0 && e == cudaSuccess; ++r)
     e = cudaMemcpyAsync(base + (int64_t)r * m + n, src + (int64_t)r * k, sizeof(T) * k,
                         cudaMemcpyDeviceToDevice, c->stream);
@@ -975,28 +1057,30 @@ cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew_out) {
   k_scan_down<<<(unsigned)nblk, 256, 0, s>>>(D, m, sums);
   k_hole_pos<<<gb, 256, 0, s>>>(del, D, n, c->keys[1]);
   c->launches += 5;
+  // every array is filled and moved on the device (the kernels read the
+  // deletion count D[n] there); the host reads the count once, at the end
+  cudaError_t e = cudaSuccess;
+  if (c->mode == PART_BORIS && c->prec == PART_FP64) {
+    if ((e = fill_rows<double>(c, (double*)c->x, 3, del, n, gb))) return e;
+    if ((e = fill_rows<double>(c, (double*)c->u, 3, del, n, gb))) return e;
+    if (c->w && (e = fill_rows<double>(c, (double*)c->w, 1, del, n, gb))) return e;
+  } else if (c->mode == PART_BORIS) {
+    if ((e = fill_rows<int32_t>(c, (int32_t*)c->x, 1, del, n, gb))) return e;
+    if ((e = fill_rows<float>(c, (float*)c->off, 3, del, n, gb))) return e;
+    if ((e = fill_rows<float>(c, (float*)c->u, 6, del, n, gb))) return e;
+    if (c->w && (e = fill_rows<float>(c, (float*)c->w, 1, del, n, gb))) return e;
+  } else {
+    if ((e = fill_rows<double>(c, (double*)c->x, 3, del, n, gb))) return e;
+    if ((e = fill_rows<double>(c, c->chi, c->nbins, del, n, gb))) return e;
+    if ((e = fill_rows<double>(c, c->eng, c->nbins, del, n, gb))) return e;
+    if (c->n_old && (e = fill_rows<double>(c, c->n_old, 1, del, n, gb))) return e;
+    if (c->shk && (e = fill_rows<uint8_t>(c, c->shk, 1, del, n, gb))) return e;
+  }
+  if (c->id && (e = fill_rows<uint64_t>(c, c->id, 1, del, n, gb))) return e;
   uint32_t ndel = 0;
-  cudaError_t e = cudaMemcpyAsync(&ndel, D + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  e = cudaMemcpyAsync(&ndel, D + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
-  const int64_t nnew = n - (int64_t)ndel;
-  if (c->mode == PART_BORIS && c->prec == PART_FP64) {
-    if ((e = fill_rows<double>(c, (double*)c->x, 3, del, n, nnew, gb))) return e;
-    if ((e = fill_rows<double>(c, (double*)c->u, 3, del, n, nnew, gb))) return e;
-    if (c->w && (e = fill_rows<double>(c, (double*)c->w, 1, del, n, nnew, gb))) return e;
-  } else if (c->mode == PART_BORIS) {
-    if ((e = fill_rows<int32_t>(c, (int32_t*)c->x, 1, del, n, nnew, gb))) return e;
-    if ((e = fill_rows<float>(c, (float*)c->off, 3, del, n, nnew, gb))) return e;
-    if ((e = fill_rows<float>(c, (float*)c->u, 6, del, n, nnew, gb))) return e;
-    if (c->w && (e = fill_rows<float>(c, (float*)c->w, 1, del, n, nnew, gb))) return e;
-  } else {
-    if ((e = fill_rows<double>(c, (double*)c->x, 3, del, n, nnew, gb))) return e;
-    if ((e = fill_rows<double>(c, c->chi, c->nbins, del, n, nnew, gb))) return e;
-    if ((e = fill_rows<double>(c, c->eng, c->nbins, del, n, nnew, gb))) return e;
-    if (c->n_old && (e = fill_rows<double>(c, c->n_old, 1, del, n, nnew, gb))) return e;
-    if (c->shk && (e = fill_rows<uint8_t>(c, c->shk, 1, del, n, nnew, gb))) return e;
-  }
-  if (c->id && (e = fill_rows<uint64_t>(c, c->id, 1, del, n, nnew, gb))) return e;
-  *nnew_out = nnew;
+  *nnew_out = n - (int64_t)ndel;
   return cudaGetLastError();
 }
