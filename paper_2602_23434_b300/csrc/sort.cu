@@ -158,18 +158,21 @@ __global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t* __restrict_
   if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
-// Scan phase 2: exclusive scan of the block sums in one CTA.
+// Scan phase 2: exclusive scan of the block sums in one CTA.  Each thread
+// takes a contiguous segment (one block scan in all, whatever the count).
 __global__ void __launch_bounds__(256) k_scan_top(uint32_t* __restrict__ sums, int64_t nblk) {
   __shared__ uint32_t wt[8];
   __shared__ uint32_t tot;
-  uint32_t carry = 0;
-  for (int64_t base = 0; base < nblk; base += 256) {
-    int64_t i = base + threadIdx.x;
-    uint32_t v = i < nblk ? sums[i] : 0;
-    uint32_t e = block_exclusive_scan(v, wt, &tot);
-    if (i < nblk) sums[i] = carry + e;
-    carry += tot;
-    __syncthreads();
+  const int64_t per = (nblk + 255) / 256;
+  const int64_t b0 = (int64_t)threadIdx.x * per;
+  const int64_t b1 = b0 + per < nblk ? b0 + per : nblk;
+  uint32_t s = 0;
+  for (int64_t i = b0; i < b1; ++i) s += sums[i];
+  uint32_t e = block_exclusive_scan(s, wt, &tot);
+  for (int64_t i = b0; i < b1; ++i) {
+    const uint32_t v = sums[i];
+    sums[i] = e;
+    e += v;
   }
 }
 
@@ -650,9 +653,10 @@ __global__ void k_hole_pos(const uint8_t* __restrict__ del, const uint32_t* __re
     if (del[i]) hole_pos[D[i]] = (uint32_t)i;
 }
 
-// Move one plane of element type T (row stride n): filler i -> its hole.
+// Move the fillers of every plane of an array of element type T (rows
+// planes of stride n): filler i -> its hole, in each plane.
 template <typename T>
-__global__ void k_fill_holes(T* __restrict__ a, const uint8_t* __restrict__ del,
+__global__ void k_fill_holes(T* __restrict__ a, int rows, const uint8_t* __restrict__ del,
                              const uint32_t* __restrict__ D,
                              const uint32_t* __restrict__ hole_pos, int64_t n) {
   const int64_t nkeep = n - (int64_t)D[n];
@@ -661,7 +665,8 @@ __global__ void k_fill_holes(T* __restrict__ a, const uint8_t* __restrict__ del,
        i += (int64_t)gridDim.x * blockDim.x) {
     if (del[i]) continue;
     const int64_t k = (i - nkeep) - ((int64_t)D[i] - base);  // filler rank
-    a[hole_pos[k]] = a[i];
+    const int64_t h = hole_pos[k];
+    for (int r = 0; r < rows; ++r) a[r * n + h] = a[r * n + i];
   }
 }
 
@@ -962,11 +967,8 @@ cudaError_t move_row(part_ctx* c, const T* src, T* dst, int64_t len) {
 // nnew (the deletion count stays on the device: D[n]).
 template <typename T>
 cudaError_t fill_rows(part_ctx* c, T* base, int rows, const uint8_t* del, int64_t n, int gb) {
-  for (int r = 0; r < rows; ++r) {
-    k_fill_holes<T><<<gb, 256, 0, c->stream>>>(base + (int64_t)r * n, del, c->keys[0],
-                                               c->keys[1], n);
-    c->launches++;
-  }
+  k_fill_holes<T><<<gb, 256, 0, c->stream>>>(base, rows, del, c->keys[0], c->keys[1], n);
+  c->launches++;
   // Rows r >= 1 move from stride n to stride nnew: row r shifts down by
   // r (n - nnew) elements, in place, lowest row first (a row only overwrites
   // source rows already moved, and its own source as the move allows).
