@@ -569,10 +569,14 @@ __global__ void __launch_bounds__(256)
     if (fast) {
       // full bricks and at least three per active axis: the cell is in its
       // own brick's tile, and in one neighbour's halo when it is on a face
-      // of its brick (previous brick first, as in the general order below)
+      // of its brick.  A warp's lanes share y and z, so the loop over the
+      // (y, z) tiles is uniform; along x a lane has its own tile's partial and
+      // at most one neighbour's (on an x face), added as one pair (0 where
+      // there is none).  The rows are then summed in (z, y) order, starting
+      // from the first: the FP64 adds (this pass's bound) are all full-warp.
       int cb[3][3], ce[3][3], cnt[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
+      for (int a = 1; a < 3; ++a) {
         const int bj = j[a] >> g.bshift[a], l = j[a] & (g.b[a] - 1);
         cnt[a] = 0;
         if (g.h[a] != 0 && l == 0) {
@@ -586,18 +590,39 @@ __global__ void __launch_bounds__(256)
           ce[a][cnt[a]++] = 0;
         }
       }
+      const int bx = j[0] >> g.bshift[0], lx = j[0] & (g.b[0] - 1);
+      int xb = -1, xe = 0;  // the x neighbour whose halo holds the cell, if any
+      if (lx == 0) {
+        xb = bx == 0 ? g.nb[0] - 1 : bx - 1;
+        xe = g.b[0] + 1;
+      } else if (lx == g.b[0] - 1) {
+        xb = bx == g.nb[0] - 1 ? 0 : bx + 1;
+        xe = 0;
+      }
       double s0 = 0.0, s1 = 0.0, s2 = 0.0;
       for (int qz = 0; qz < cnt[2]; ++qz)
-        for (int qy = 0; qy < cnt[1]; ++qy)
-          for (int qx = 0; qx < cnt[0]; ++qx) {
-            const int64_t br =
-                ((int64_t)cb[2][qz] * g.nb[1] + cb[1][qy]) * g.nb[0] + cb[0][qx];
-            const int t = (ce[2][qz] * g.e[1] + ce[1][qy]) * g.e[0] + ce[0][qx];
-            const double* pp = dpart + br * 3 * g.ev + t;
-            s0 += pp[0];
-            s1 += pp[g.ev];
-            s2 += pp[2 * (int64_t)g.ev];
+        for (int qy = 0; qy < cnt[1]; ++qy) {
+          const int64_t rb = ((int64_t)cb[2][qz] * g.nb[1] + cb[1][qy]) * g.nb[0];
+          const int trow = (ce[2][qz] * g.e[1] + ce[1][qy]) * g.e[0];
+          const double* po = dpart + (rb + bx) * 3 * g.ev + trow + lx + 1;
+          double e0 = 0.0, e1 = 0.0, e2 = 0.0;
+          if (xb >= 0) {
+            const double* pe = dpart + (rb + xb) * 3 * g.ev + trow + xe;
+            e0 = pe[0];
+            e1 = pe[g.ev];
+            e2 = pe[2 * (int64_t)g.ev];
           }
+          const double t0 = po[0] + e0, t1 = po[g.ev] + e1, t2 = po[2 * (int64_t)g.ev] + e2;
+          if (qz == 0 && qy == 0) {
+            s0 = t0;
+            s1 = t1;
+            s2 = t2;
+          } else {
+            s0 += t0;
+            s1 += t1;
+            s2 += t2;
+          }
+        }
       out[gi] = s0;
       out[g.G + gi] = s1;
       out[2 * g.G + gi] = s2;
