@@ -60,8 +60,13 @@ BYTES_PER_PSTEP_BORIS_DEP = 96 + 8 + 6 + 3
 # 265.0 MB for 2,097,152 particles), scaled to a launch by the particle count.
 TRAFFIC_PER_PARTICLE_BRICK_F64 = 264.987392e6 / 2097152  # ncu dram r+w, 64^3 capture
 # Same for the mixed brick kernel, from an ncu capture of the 128^3 case
-# (1715.1 MB for 16,777,216 particles).
+# (1710.1 MB for 16,777,216 particles).
 TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1710.065664e6 / 16777216   # ncu dram r+w, 128^3 capture
+
+
+# Nominal HBM3e bandwidth of a B300 (GB/s): fractions against it are reported
+# beside the ones against the measured copy bandwidth.
+HBM_NOMINAL_GBS = 7700.0
 
 
 def peaks():
@@ -252,7 +257,7 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
     spec_ms = float(np.mean(kern))
     kev = [e for e in kev if e is not None]
     spec_bytes = nlp * 2 * 2 * nb * 8
-    hbm, _ = peaks()
+    hbm, hbm_kind = peaks()
     arith = ("push in paired-f32 arithmetic (~48-bit), FP64 state and spectra" if paired
              else "FP64")
     if lazy:
@@ -264,7 +269,8 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
     step_hbm = {"bytes_per_lp_step": step_bytes,
                 "achieved_GBps": step_bytes * nlp / (total / K / 1e3) / 1e9,
                 "frac": step_bytes * nlp / (total / K / 1e3) / 1e9 / hbm,
-                "peak_kind": "measured"}
+                "frac_of_nominal": step_bytes * nlp / (total / K / 1e3) / 1e9 / HBM_NOMINAL_GBS,
+                "peak_kind": hbm_kind}
     if lazy:
         step_hbm["what"] = (f"positions, n_old and the per-LP map every step, the spectra once "
                             f"per {K} steps; the eager update moves {lp_step_bytes(nb)} B per "
@@ -299,7 +305,9 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
                 "spec_update": {"bound": "hbm", "bytes": spec_bytes,
                                 "bound_ms": spec_bytes / (hbm * 1e9) * 1e3,
                                 "kernel_ms": spec_ms,
-                                "frac": spec_bytes / (spec_ms / 1e3) / 1e9 / hbm}},
+                                "frac": spec_bytes / (spec_ms / 1e3) / 1e9 / hbm,
+                                "frac_of_nominal":
+                                    spec_bytes / (spec_ms / 1e3) / 1e9 / HBM_NOMINAL_GBS}},
             "c0": c0, "dt": dt, "gpu_launches_per_step": launches}
 
 
@@ -348,7 +356,8 @@ def run_compact(torch, P, n=128, ppc=8, fracs=(0.01, 0.1), K=10, seed=1240):
         out["cases"].append({"deleted_frac": frac, "n_new": nk, "fillers": nfill, "ms": t,
                              "particles_per_s": N / (t / 1e3),
                              "algorithmic_bytes": alg, "achieved_GBps": alg / (t / 1e3) / 1e9,
-                             "frac": alg / (t / 1e3) / 1e9 / hbm})
+                             "frac": alg / (t / 1e3) / 1e9 / hbm,
+                             "frac_of_nominal": alg / (t / 1e3) / 1e9 / HBM_NOMINAL_GBS})
     del keep, x, u, w, ids
     return out
 
@@ -484,6 +493,7 @@ def run_mixed(torch, P, n, ppc, K, W, seed):
            "ms_per_step": total / K, "push_kernel_ms": km,
            "roofline_push": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                              "frac": gbs / hbm, "peak_kind": kind,
+                             "frac_of_nominal": gbs / HBM_NOMINAL_GBS,
                              "bytes_per_particle_step": BYTES_PER_PSTEP_MIXED_DEP,
                              "traffic": TRAFFIC_PER_PARTICLE_BRICK_MIXED * wl.N},
            "gpu_launches_per_step": (wl.part.launches() - l0) // (K + W)}
@@ -1102,6 +1112,7 @@ def main():
                                   "peak_nominal is the recipe's nominal figure"},
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                          "frac": achieved_gbs / hbm,
+                         "frac_of_nominal": achieved_gbs / HBM_NOMINAL_GBS,
                          "bytes_per_particle_step": BYTES_PER_PSTEP_BORIS_DEP,
                          "peak_kind": hbm_kind},
         "clocks": clocks, "gpu_launches": launches,
