@@ -890,7 +890,7 @@ __device__ __forceinline__ void advance_mixed(const float* __restrict__ fp, cons
     shape_weights<SHAPE>(o[1], wy);
     if (DIM == 3) shape_weights<SHAPE>(o[2], wz);
     float2 f2[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    const float4* fp4 = reinterpret_cast<const float4*>(fp);
+    const ulonglong4_32a* __restrict__ fp8 = reinterpret_cast<const ulonglong4_32a*>(fp);
 #pragma unroll
     for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
       const int zz = DIM == 3 ? j[2] + kz : 0;
@@ -899,8 +899,15 @@ __device__ __forceinline__ void advance_mixed(const float* __restrict__ fp, cons
         const float wzy = wz[kz] * wy[ky];
         const int64_t row = ((int64_t)zz * g.pn[1] + j[1] + ky) * g.pn[0] + j[0];
 #pragma unroll
-        for (int kx = 0; kx < 3; ++kx)
-          acc_point(f2, wzy * wx[kx], __ldg(fp4 + 2 * (row + kx)), __ldg(fp4 + 2 * (row + kx) + 1));
+        for (int kx = 0; kx < 3; ++kx) {
+          // one 32-byte load per stencil point (the cell's 8 floats)
+          const ulonglong4_32a v = fp8[row + kx];
+          acc_point(f2, wzy * wx[kx],
+                    make_float4(__uint_as_float((uint32_t)v.x), __uint_as_float((uint32_t)(v.x >> 32)),
+                                __uint_as_float((uint32_t)v.y), __uint_as_float((uint32_t)(v.y >> 32))),
+                    make_float4(__uint_as_float((uint32_t)v.z), __uint_as_float((uint32_t)(v.z >> 32)),
+                                0.0f, 0.0f));
+        }
       }
     }
     float f[6] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y};
