@@ -10,8 +10,9 @@ TSC deposit of the force density, FP64.  One step = part_sort + part_gather_push
 Also reported on the same line: the Lagrangian-particle workload (128^3 fluid
 snapshot, 4M LPs x 128 bins, RK2 or RK3 + spectral update; FP64, and with the
 paired-f32 push and the deferred spectra), the 160^3 shock configuration, the
-mixed form at 128^3 and 256^3, the 2D uniform-field workload (64^2, 65,536
-particles, 100 fused steps), compaction, the serving stream, the FP64 roofline
+mixed form at 128^3 and 256^3, mixed-form test particles with fused steps
+(2M on a 256^3 snapshot, as serving runs them), the 2D uniform-field workload
+(64^2, 65,536 particles, 100 fused steps), compaction, the serving stream, the FP64 roofline
 of the dominant kernel, end-to-end throughput through host buffers, and the
 oracle timed on the host cores.
 
@@ -600,6 +601,35 @@ def run_serving(torch, requests=200, seed=1239, load=0.7, budget_gb=16.0, round_
     return res
 
 
+def run_mixed_fused(torch, P, n=256, N=1 << 21, steps=16, reps=5, seed=1239):
+    """Test particles in the mixed form, as serving runs them: N sorted
+    particles on an n^3 turbulent snapshot (sparser than one per cell at the
+    defaults), `steps` fused steps per call (part_gather_push), no deposit."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f = torch.as_tensor(synth.em_fields(3, n, seed).reshape(6, -1).astype(np.float32)).to(dev)
+    p = P.Part(P.make_grid(3, n), P.MIXED, P.TSC, P.BORIS, capacity=N)
+    p.set_fields(f)
+    cell = torch.empty(N, dtype=torch.int32, device=dev)
+    off = torch.empty((3, N), dtype=torch.float32, device=dev)
+    u = torch.empty((6, N), dtype=torch.float32, device=dev)
+    p.bind(N, cell, off=off, u=u)
+    p.init_particles(7, 0.1)
+    p.sort()
+    p.flush()
+    p.sync()
+    dt = 0.5 * 2.0 / n
+
+    def run(ev):
+        p.gather_push(1.0, dt, steps)
+
+    total, _ = time_steps(torch, p.stream, run, reps, 3)
+    p.sync()
+    return {"workload": f"mixed form, {N} sorted test particles on a {n}^3 turbulent snapshot, "
+                        f"{steps} fused Boris steps per call (k_boris_particles_mixed)",
+            "value": N * steps * reps / (total / 1e3), "unit": "particle-steps/s",
+            "ms_per_call": total / reps}
+
+
 def run_2d(torch, P, n=64, ppc=16, steps=100, seed=1235):
     dev = torch.device("cuda", torch.cuda.current_device())
     N = n * n * ppc
@@ -1002,6 +1032,8 @@ def only(args):
         res = run_lp(torch, P, args.steps, args.warmup, n=args.grid,
                      nlp=max(1 << 16, 2 * args.grid ** 3), paired="paired" in args.only,
                      lazy=args.only.endswith("lazy"))
+    elif args.only == "mixed_fused":
+        res = run_mixed_fused(torch, P, n=args.grid, reps=max(1, args.steps))
     elif args.only == "boris2d":
         res = run_2d(torch, P)
     else:
@@ -1025,7 +1057,7 @@ def main():
                          "smaller only for profiling captures)")
     ap.add_argument("--only", choices=["mixed", "lp", "lp_paired", "lp_lazy", "lp_paired_lazy",
                                        "serving", "compact", "shock", "shock_paired_lazy",
-                                       "boris2d"],
+                                       "boris2d", "mixed_fused"],
                     default=None,
                     help="run one secondary workload alone at --grid cells per axis and print "
                          "its result (for profiling captures); no headline line")
@@ -1144,6 +1176,10 @@ def main():
             line["boris_2d"] = run_2d(torch, P)
         except Exception as e:
             line["boris_2d"] = {"error": repr(e)}
+        try:
+            line["mixed_fused"] = run_mixed_fused(torch, P)
+        except Exception as e:
+            line["mixed_fused"] = {"error": repr(e)}
         try:
             mx = run_mixed(torch, P, 128, 8, args.steps, 3, 1236)
             mx["speedup_vs_fp64_same_workload"] = mx["value"] / value
