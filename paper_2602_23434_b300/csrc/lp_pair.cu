@@ -53,6 +53,14 @@ __device__ __forceinline__ void weights_p(f2 d, f2* w) {
   }
 }
 
+// The two float4 of a 32-byte load (one sector).
+__device__ __forceinline__ void split32(const ulonglong4_32a v, float4& a, float4& b) {
+  a = make_float4(__uint_as_float((uint32_t)v.x), __uint_as_float((uint32_t)(v.x >> 32)),
+                  __uint_as_float((uint32_t)v.y), __uint_as_float((uint32_t)(v.y >> 32)));
+  b = make_float4(__uint_as_float((uint32_t)v.z), __uint_as_float((uint32_t)(v.z >> 32)),
+                  __uint_as_float((uint32_t)v.w), __uint_as_float((uint32_t)(v.w >> 32)));
+}
+
 template <int SHAPE, int DIM>
 struct StencilP {
   int64_t base;  // padded index of the (-1,-1,-1) corner
@@ -119,12 +127,16 @@ struct StencilP {
 #pragma unroll
         for (int kx = 0; kx < 3; ++kx) {
           const f2 ww = f2_mul_u(wzy, wx[kx]);
-          const float4* q = fq + 4 * (row + kx);
-          const float4 h0 = __ldg(q), l0 = __ldg(q + 2);
+          // one 32-byte load per half record: (v, rho) high and low parts, then
+          // (B, 0) high and low parts
+          const ulonglong4_32a* q = reinterpret_cast<const ulonglong4_32a*>(fq + 4 * (row + kx));
+          float4 h0, l0;
+          split32(q[0], h0, l0);
           dot2_acc2(ah[0], al[0], ww, make_float2(h0.x, h0.y), make_float2(l0.x, l0.y));
           dot2_acc2(ah[1], al[1], ww, make_float2(h0.z, h0.w), make_float2(l0.z, l0.w));
           if (NP == 4) {
-            const float4 h1 = __ldg(q + 1), l1 = __ldg(q + 3);
+            float4 h1, l1;
+            split32(q[1], h1, l1);
             dot2_acc2(ah[2], al[2], ww, make_float2(h1.x, h1.y), make_float2(l1.x, l1.y));
             dot2_acc2(ah[3], al[3], ww, make_float2(h1.z, h1.w), make_float2(l1.z, l1.w));
           }
@@ -318,9 +330,10 @@ __global__ void k_pad_pair_lp(const double* __restrict__ fp, int64_t pplane,
       l[c] = v.l;
     }
     h[7] = l[7] = 0.0f;
+    // 32-byte halves: (v, rho) high, low; (B, 0) high, low
     fq[4 * q + 0] = make_float4(h[0], h[1], h[2], h[3]);
-    fq[4 * q + 1] = make_float4(h[4], h[5], h[6], h[7]);
-    fq[4 * q + 2] = make_float4(l[0], l[1], l[2], l[3]);
+    fq[4 * q + 1] = make_float4(l[0], l[1], l[2], l[3]);
+    fq[4 * q + 2] = make_float4(h[4], h[5], h[6], h[7]);
     fq[4 * q + 3] = make_float4(l[4], l[5], l[6], l[7]);
   }
 }
