@@ -26,6 +26,7 @@ struct Stencil {
   int64_t base;     // padded index of the (-1,-1,-1) corner
   int64_t cell;     // linear index of the cell containing x
   double wx[3], wy[3], wz[3];
+  double dxo;       // offset from the cell centre along x, in cells (the TSC x quadratic)
   bool finite;
   __device__ __forceinline__ Stencil(const Geo& g, const double* xp) {
     int j[3] = {0, 0, 0};
@@ -42,6 +43,7 @@ struct Stencil {
       j[a] = floor_clamp_bits(s, g.n[a] - 1);
       d[a] = __dsub_rn(__dsub_rn(s, (double)j[a]), 0.5);
     }
+    dxo = d[0];
     shape_weights<SHAPE>(d[0], wx);
     shape_weights<SHAPE>(d[1], wy);
     wz[0] = 0.0;
@@ -74,6 +76,73 @@ struct Stencil {
         }
       }
     }
+  }
+  // TSC from the x quadratics (fxq): along x the three weighted cells of a
+  // row are q0 + d (q1 + d q2) with d the offset from the cell centre, where
+  // q0 = (F[-1] + F[1]) / 8 + 3 F[0] / 4, q1 = (F[1] - F[-1]) / 2 and
+  // q2 = (F[-1] + F[1]) / 2 - F[0] (the expansion of the TSC weights in d):
+  // two FMAs per row and component, one 32-byte load, no x weight products.
+  template <int NC>
+  __device__ __forceinline__ void gather_xq(const double* __restrict__ fxq, const Geo& g, int c0,
+                                            double* out) const {
+    const double4_32a* __restrict__ q4 = reinterpret_cast<const double4_32a*>(fxq);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) out[c] = 0.0;
+#pragma unroll
+    for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
+      const int zo = DIM == 3 ? kz : 0;
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky) {
+        const double wzy = wz[kz] * wy[ky];
+        const int64_t rc = base + ((int64_t)zo * g.pn[1] + ky) * g.pn[0] + 1;  // row centre
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const double4_32a q = q4[(int64_t)(c0 + c) * g.pplane + rc];
+          out[c] = fma(wzy, fma(dxo, fma(dxo, q.z, q.y), q.x), out[c]);
+        }
+      }
+    }
+  }
+  // components {0,1,2} (v) and {4,5,6} (B) in one pass, from the x quadratics
+  __device__ __forceinline__ void gather_vb_xq(const double* __restrict__ fxq, const Geo& g,
+                                               double* v, double* b) const {
+    const double4_32a* __restrict__ q4 = reinterpret_cast<const double4_32a*>(fxq);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = b[c] = 0.0;
+#pragma unroll
+    for (int kz = (DIM == 3 ? 0 : 1); kz < (DIM == 3 ? 3 : 2); ++kz) {
+      const int zo = DIM == 3 ? kz : 0;
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky) {
+        const double wzy = wz[kz] * wy[ky];
+        const int64_t rc = base + ((int64_t)zo * g.pn[1] + ky) * g.pn[0] + 1;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double4_32a qv = q4[(int64_t)c * g.pplane + rc];
+          const double4_32a qb = q4[(int64_t)(4 + c) * g.pplane + rc];
+          v[c] = fma(wzy, fma(dxo, fma(dxo, qv.z, qv.y), qv.x), v[c]);
+          b[c] = fma(wzy, fma(dxo, fma(dxo, qb.z, qb.y), qb.x), b[c]);
+        }
+      }
+    }
+  }
+  // the gathers the push uses: the x quadratics for TSC, the weights for CIC
+  template <int NC>
+  __device__ __forceinline__ void gather_lp(const double* __restrict__ fp,
+                                            const double* __restrict__ fxq, const Geo& g, int c0,
+                                            double* out) const {
+    if (SHAPE == PART_TSC)
+      gather_xq<NC>(fxq, g, c0, out);
+    else
+      gather<NC>(fp, g, c0, out);
+  }
+  __device__ __forceinline__ void gather_vb_lp(const double* __restrict__ fp,
+                                               const double* __restrict__ fxq, const Geo& g,
+                                               double* v, double* b) const {
+    if (SHAPE == PART_TSC)
+      gather_vb_xq(fxq, g, v, b);
+    else
+      gather_vb(fp, g, v, b);
   }
   // components {0,1,2} (v) and {4,5,6} (B) in one stencil pass
   __device__ __forceinline__ void gather_vb(const double* __restrict__ fp, const Geo& g,
@@ -137,13 +206,13 @@ struct PushF64 {
       fin = finite_bits(x0[0]) && finite_bits(x0[1]) && finite_bits(x0[2]);
     } else {
       Stencil<SHAPE, DIM> s0(g, x0);
-      s0.gather_vb(fp, g, v1, b0);
+      s0.gather_vb_lp(fp, A.fxq, g, v1, b0);
       fin = s0.finite;
     }
 #pragma unroll
     for (int a = 0; a < DIM; ++a) xs[a] = wrap_axis(g, a, fma(dt, v1[a], x0[a]));
     Stencil<SHAPE, DIM> ss(g, xs);
-    ss.template gather<3>(fp, g, 0, v2);
+    ss.template gather_lp<3>(fp, A.fxq, g, 0, v2);
     fin = fin && ss.finite;
     if (ORDER == 2) {
 #pragma unroll
@@ -156,7 +225,7 @@ struct PushF64 {
       for (int a = 0; a < DIM; ++a)
         xb[a] = wrap_axis(g, a, fma(0.25 * dt, v1[a] + v2[a], x0[a]));
       Stencil<SHAPE, DIM> sb(g, xb);
-      sb.template gather<3>(fp, g, 0, k3);
+      sb.template gather_lp<3>(fp, A.fxq, g, 0, k3);
       fin = fin && sb.finite;
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
@@ -165,7 +234,7 @@ struct PushF64 {
     Stencil<SHAPE, DIM> s1(g, x1);
     {
       double o[7];  // v, rho, B at the new position in one stencil pass
-      s1.template gather<7>(fp, g, 0, o);
+      s1.template gather_lp<7>(fp, A.fxq, g, 0, o);
       v3[0] = o[0];
       v3[1] = o[1];
       v3[2] = o[2];
@@ -195,8 +264,10 @@ struct PushF64 {
   }
 };
 
+// Two CTAs per SM (128 registers): the x-quadratic gathers take more
+// registers than one CTA per SM can hide the FP64 latency with.
 template <int SHAPE, int DIM, bool SHOCK, int ORDER, bool CACHED>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     k_lp_rk2(const LpArgs a, double* __restrict__ samples, int64_t p0, int64_t p1) {
   const PushF64<SHAPE, DIM, SHOCK, ORDER, CACHED> push{a};
   for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1;
@@ -649,17 +720,50 @@ cudaError_t launch_spec_to_plain(part_ctx* c) {
 
 // Gather of one scalar component, used by the LP initialisation.
 template <int SHAPE, int DIM>
-__global__ void k_lp_sample_rho(const double* __restrict__ fp, const Geo g,
-                                const double* __restrict__ x, int64_t n,
+__global__ void k_lp_sample_rho(const double* __restrict__ fp, const double* __restrict__ fxq,
+                                const Geo g, const double* __restrict__ x, int64_t n,
                                 double* __restrict__ n_old) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     double xp[3] = {x[p], x[n + p], x[2 * n + p]};
     Stencil<SHAPE, DIM> s(g, xp);
     double r;
-    s.template gather<1>(fp, g, 3, &r);
+    s.template gather_lp<1>(fp, fxq, g, 3, &r);  // as the push samples rho
     n_old[p] = r;
   }
+}
+
+// The x quadratics of the padded LP fields (see Stencil::gather_xq): for each
+// component and padded cell with both x neighbours, (q0, q1, q2, 0) as one
+// 32-byte record; 0 elsewhere (never read).
+__global__ void k_pad_xq_lp(const double* __restrict__ fp, const Geo g, double* __restrict__ fxq) {
+  const int64_t pp = g.pplane;
+  double4_32a* __restrict__ q4 = reinterpret_cast<double4_32a*>(fxq);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < pp;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int px = (int)(q % g.pn[0]);
+    const bool in = px >= 1 && px <= g.pn[0] - 2;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      double4_32a o;
+      o.x = o.y = o.z = o.w = 0.0;
+      if (in) {
+        const double fm = fp[c * pp + q - 1], f0 = fp[c * pp + q], fq = fp[c * pp + q + 1];
+        const double sp = fm + fq;
+        o.x = fma(0.75, f0, 0.125 * sp);
+        o.y = 0.5 * (fq - fm);
+        o.z = fma(0.5, sp, -f0);
+      }
+      q4[c * pp + q] = o;
+    }
+  }
+}
+
+cudaError_t launch_pad_xq_lp(part_ctx* c) {
+  k_pad_xq_lp<<<grid_for(c, c->geo.pplane, 256), 256, 0, c->stream>>>((const double*)c->fpad,
+                                                                      c->geo, c->fxq);
+  c->launches++;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_lp_sample_rho(part_ctx* c) {
@@ -669,14 +773,14 @@ cudaError_t launch_lp_sample_rho(part_ctx* c) {
   const double* x = (const double*)c->x;
   if (c->shape == PART_TSC) {
     if (c->geo.dim == 3)
-      k_lp_sample_rho<PART_TSC, 3><<<gb, 256, 0, c->stream>>>(fp, c->geo, x, c->n, c->n_old);
+      k_lp_sample_rho<PART_TSC, 3><<<gb, 256, 0, c->stream>>>(fp, c->fxq, c->geo, x, c->n, c->n_old);
     else
-      k_lp_sample_rho<PART_TSC, 2><<<gb, 256, 0, c->stream>>>(fp, c->geo, x, c->n, c->n_old);
+      k_lp_sample_rho<PART_TSC, 2><<<gb, 256, 0, c->stream>>>(fp, c->fxq, c->geo, x, c->n, c->n_old);
   } else {
     if (c->geo.dim == 3)
-      k_lp_sample_rho<PART_CIC, 3><<<gb, 256, 0, c->stream>>>(fp, c->geo, x, c->n, c->n_old);
+      k_lp_sample_rho<PART_CIC, 3><<<gb, 256, 0, c->stream>>>(fp, c->fxq, c->geo, x, c->n, c->n_old);
     else
-      k_lp_sample_rho<PART_CIC, 2><<<gb, 256, 0, c->stream>>>(fp, c->geo, x, c->n, c->n_old);
+      k_lp_sample_rho<PART_CIC, 2><<<gb, 256, 0, c->stream>>>(fp, c->fxq, c->geo, x, c->n, c->n_old);
   }
   c->launches++;
   return cudaGetLastError();

@@ -30,6 +30,7 @@ static __device__ __forceinline__ void recip8(const double* v, double* r) {
 // shock bookkeeping); fp: the padded FP64 fields, or the paired copy.
 struct LpArgs {
   const double* fp;
+  const double* fxq;  // x quadratics of fp (TSC gathers), 4 doubles per (component, cell)
   Geo g;
   double* x;
   int64_t n;
@@ -50,6 +51,7 @@ struct LpArgs {
 static inline LpArgs lp_args(part_ctx* c, double dt) {
   LpArgs a;
   a.fp = (const double*)c->fpad;
+  a.fxq = c->fxq;
   a.g = c->geo;
   a.x = (double*)c->x;
   a.n = c->n;
