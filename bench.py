@@ -277,10 +277,12 @@ def run_lp(torch, P, K: int, W: int, n=128, nlp=1 << 22, nb=128, seed=1238, orde
                             f"per {K} steps; the eager update moves {lp_step_bytes(nb)} B per "
                             f"LP-step")
     push_ms = float(np.mean([a.elapsed_time(e[0]) for a, e in zip(push_ev, kev)]))
-    # the two bounds of the step: the push on the FP64 pipe (about 440 FP64
-    # pipe slots per LP-step for RK2, 560 for RK3, at 2 slots per SM-cycle =
-    # half the measured FP64 FLOP/s), the spectral update on HBM
-    slots = 440 if order == 2 else 560
+    # the two bounds of the step: the push on the FP64 pipe (FP64 instructions
+    # per LP-step with the TSC x quadratics: 425 for RK2 by an ncu count, 513
+    # for RK3 = that plus the third stencil's 120 of the weight form less its 32
+    # saved; at 2 per SM-cycle = half the measured FP64 FLOP/s), the spectral
+    # update on HBM
+    slots = 425 if order == 2 else 513
     del chi, eng
     if paired:
         push_roof = {"bound": "f32 issue (paired-f32 arithmetic)", "kernel_ms": push_ms,
