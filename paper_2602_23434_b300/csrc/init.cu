@@ -186,9 +186,12 @@ __global__ void k_pad_fields(const T* __restrict__ src, T* __restrict__ dst, con
 }
 
 // Mixed form: cell-interleaved copy, 8 floats per padded cell (6 components,
-// 2 zero pads), so one stencil point is two 16-byte loads.  One warp per
-// padded row (pz, py); each lane gathers one cell's components (coalesced per
-// component across the warp) and writes its 32 bytes as two 16-byte stores.
+// 2 zero pads), so one stencil point is two 16-byte loads.  With the six
+// components E0 E1 E2 B0 B1 B2 the record holds them as E0 E1 B0 B1 E2 B2, so
+// that the push's paired arithmetic finds (E0, E1), (B0, B1) and (E2, B2) as
+// aligned pairs.  One warp per padded row (pz, py); each lane gathers one
+// cell's components (coalesced per component across the warp) and writes its
+// 32 bytes as two 16-byte stores.
 __global__ void k_pad_fields_aos8(const float* __restrict__ src, float* __restrict__ dst,
                                   const Geo g, int ncomp) {
   const int lane = threadIdx.x & 31;
@@ -209,8 +212,11 @@ __global__ void k_pad_fields_aos8(const float* __restrict__ src, float* __restri
       if (px < nx) {
         const int sx = ghost_src(px - g.h[0], g.n[0], g.open[0]);
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-          if (c < ncomp) v[c] = srow[(int64_t)c * g.G + sx];
+        for (int c = 0; c < 8; ++c) {
+          // the component in record slot c
+          const int k = ncomp != 6 || c < 2 ? c : (c < 4 ? c + 1 : (c == 4 ? 2 : 5));
+          if (c < ncomp) v[c] = srow[(int64_t)k * g.G + sx];
+        }
       }
       float4* d = reinterpret_cast<float4*>(dst + (r * g.pn[0] + px) * 8);
       d[0] = make_float4(v[0], v[1], v[2], v[3]);

@@ -64,6 +64,29 @@ __device__ __forceinline__ float two_sum(float a, float b, float& e) {
   return s;
 }
 
+// Paired f32 arithmetic (two lanes per instruction, each rounded to nearest
+// as its scalar form).  sub2 is b * (-1) + a, one rounding of a - b.
+__device__ __forceinline__ float2 sp2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 two_sum2(float2 a, float2 b, float2& e) {
+  const float2 s = add2(a, b);
+  const float2 bp = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bp)), sub2(b, bp));
+  return s;
+}
+// 1/x to about an ulp (the hardware approximation); every use below corrects
+// the quotient with its exact remainder.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // f32 relativistic Boris kick of the compensated momentum u + ul (ul the f32
 // residual of u).  The momentum is kept as that pair because rounding it to
 // f32 after every step is a random walk that the gyrophase budget (1e-5 rad
@@ -76,21 +99,31 @@ __device__ __forceinline__ float two_sum(float a, float b, float& e) {
 // half an ulp with error-free transformations (TwoProd by fma, exact residuals
 // of 1 + q): 1/gamma- is refined from rsqrtf by one Newton step evaluated in
 // two-float, h = h_hi + h_lo is the two-float half step, t = h B / gamma- and
-// s = 2 t / (1 + |t|^2) are each kept as an f32 value plus its f32 residual.
+// s = 2 t / (1 + |t|^2) are each kept as an f32 value plus its f32 residual
+// (2 / (1 + |t|^2) from the approximate reciprocal and the exact remainder of
+// the quotient, so the value plus residual is good to about 2^-46).
 // The rotation, being linear in u-, is applied to u-'s value and, to first
 // order, to its residual.
+// Components 0 and 1 of every vector go as one pair (paired instructions);
+// the cross products mix components and stay scalar.  f holds the gathered
+// fields as the pairs (E0, E1), (B0, B1), (E2, B2).
 // du gets u^{n+1} - u^n from the rotation increment and the two half-kicks.
-__device__ __forceinline__ void boris_f32(float* u, float* ul, const float* E, const float* B,
-                                          float h, float hl, float* du) {
-  // half kick h E with the two-float h
-  const float k0 = fmaf(h, E[0], hl * E[0]), k1 = fmaf(h, E[1], hl * E[1]);
-  const float k2 = fmaf(h, E[2], hl * E[2]);
-  // u- = u + h E as a pair (um, ml)
-  float e0, e1, e2;
-  const float um0 = two_sum(u[0], k0, e0), um1 = two_sum(u[1], k1, e1);
+__device__ __forceinline__ void boris_f32(float* u, float* ul, const float2* f, float h,
+                                          float hl, float* du) {
+  const float2 E01 = f[0], B01 = f[1];
+  const float E2 = f[2].x, B2 = f[2].y;
+  // half kick k = h E with the two-float h
+  const float2 k01 = fma2(sp2(h), E01, mul2(sp2(hl), E01));
+  const float k2 = fmaf(h, E2, hl * E2);
+  // u- = u + k as a pair (um, ml)
+  float2 e01;
+  float e2;
+  const float2 um01 = two_sum2(make_float2(u[0], u[1]), k01, e01);
   const float um2 = two_sum(u[2], k2, e2);
-  const float ml0 = ul[0] + e0, ml1 = ul[1] + e1, ml2 = ul[2] + e2;
-  const float q = um0 * um0 + um1 * um1 + um2 * um2;
+  const float2 ml01 = add2(make_float2(ul[0], ul[1]), e01);
+  const float ml2 = ul[2] + e2;
+  const float um0 = um01.x, um1 = um01.y, ml0 = ml01.x, ml1 = ml01.y;
+  const float q = fmaf(um2, um2, fmaf(um1, um1, um0 * um0));
   const float a = 1.0f + q;
   const float res = q - (a - 1.0f);             // exact: a + res = 1 + q
   const float y = rsqrtf(a);
@@ -100,56 +133,63 @@ __device__ __forceinline__ void boris_f32(float* u, float* ul, const float* E, c
   const float gl = 0.5f * y * r;                // 1/gamma- = y + gl
   const float hg = h * y;
   const float hge = fmaf(h, y, -hg) + fmaf(h, gl, hl * y);      // h/gamma- = hg + hge
-  const float t0 = fmaf(hg, B[0], hge * B[0]);
-  const float t1 = fmaf(hg, B[1], hge * B[1]);
-  const float t2 = fmaf(hg, B[2], hge * B[2]);
-  // residuals: t_true = t + tl to ~2^-46 relative
-  const float tl0 = fmaf(hg, B[0], -t0) + hge * B[0];
-  const float tl1 = fmaf(hg, B[1], -t1) + hge * B[1];
-  const float tl2 = fmaf(hg, B[2], -t2) + hge * B[2];
-  const float tt = t0 * t0 + t1 * t1 + t2 * t2;
+  // t = (h/gamma-) B and its residual tl: t_true = t + tl to ~2^-46 relative
+  const float2 hb01 = mul2(sp2(hge), B01);
+  const float2 t01 = fma2(sp2(hg), B01, hb01);
+  const float2 tl01 = sub2(hb01, fma2(sp2(-hg), B01, t01));
+  const float hb2 = hge * B2;
+  const float t2 = fmaf(hg, B2, hb2);
+  const float tl2 = fmaf(hg, B2, -t2) + hb2;
+  const float t0 = t01.x, t1 = t01.y, tl0 = tl01.x, tl1 = tl01.y;
+  const float tt = fmaf(t2, t2, fmaf(t1, t1, t0 * t0));
   const float d = 1.0f + tt;
   const float dres = tt - (d - 1.0f);           // exact: d + dres = 1 + |t|^2
-  const float sf = __fdiv_rn(2.0f, d);
-  const float sfl = __fdiv_rn(fmaf(-sf, d, 2.0f) - sf * dres, d);  // 2/(1+|t|^2) = sf + sfl
-  const float s0 = fmaf(sf, t0, sfl * t0);
-  const float s1 = fmaf(sf, t1, sfl * t1);
+  const float rd = rcp_approx(d);
+  const float sf = 2.0f * rd;                   // 2 / (1 + |t|^2) to about an ulp
+  const float sfl = (fmaf(-sf, d, 2.0f) - sf * dres) * rd;      // ... = sf + sfl
+  const float2 s01 = fma2(sp2(sf), t01, mul2(sp2(sfl), t01));
+  const float2 sl01 =
+      sub2(fma2(sp2(sfl), t01, mul2(sp2(sf), tl01)), fma2(sp2(-sf), t01, s01));
   const float s2 = fmaf(sf, t2, sfl * t2);
-  const float sl0 = fmaf(sf, t0, -s0) + fmaf(sfl, t0, sf * tl0);
-  const float sl1 = fmaf(sf, t1, -s1) + fmaf(sfl, t1, sf * tl1);
   const float sl2 = fmaf(sf, t2, -s2) + fmaf(sfl, t2, sf * tl2);
+  const float s0 = s01.x, s1 = s01.y, sl0 = sl01.x, sl1 = sl01.y;
   // u' = u- + u- x t and u+ - u- = u' x s with t, s carried as value +
   // residual: the residual terms are first-order small and enter in plain f32,
   // so the rotation angle carries no rounding that repeats from step to step
-  const float p0 = um0 + ((um1 * t2 - um2 * t1) + (um1 * tl2 - um2 * tl1));
-  const float p1 = um1 + ((um2 * t0 - um0 * t2) + (um2 * tl0 - um0 * tl2));
+  const float2 p01 = add2(um01, add2(make_float2(um1 * t2 - um2 * t1, um2 * t0 - um0 * t2),
+                                     make_float2(um1 * tl2 - um2 * tl1, um2 * tl0 - um0 * tl2)));
   const float p2 = um2 + ((um0 * t1 - um1 * t0) + (um0 * tl1 - um1 * tl0));
-  const float r0 = (p1 * s2 - p2 * s1) + (p1 * sl2 - p2 * sl1);  // u+ - u-
-  const float r1 = (p2 * s0 - p0 * s2) + (p2 * sl0 - p0 * sl2);
+  const float p0 = p01.x, p1 = p01.y;
+  const float2 r01 = add2(make_float2(p1 * s2 - p2 * s1, p2 * s0 - p0 * s2),
+                          make_float2(p1 * sl2 - p2 * sl1, p2 * sl0 - p0 * sl2));  // u+ - u-
   const float r2 = (p0 * s1 - p1 * s0) + (p0 * sl1 - p1 * sl0);
   // the same rotation of u-'s residual, to first order
-  const float pl0 = ml0 + (ml1 * t2 - ml2 * t1);
-  const float pl1 = ml1 + (ml2 * t0 - ml0 * t2);
+  const float2 pl01 = add2(ml01, make_float2(ml1 * t2 - ml2 * t1, ml2 * t0 - ml0 * t2));
   const float pl2 = ml2 + (ml0 * t1 - ml1 * t0);
-  const float rl0 = pl1 * s2 - pl2 * s1, rl1 = pl2 * s0 - pl0 * s2, rl2 = pl0 * s1 - pl1 * s0;
+  const float pl0 = pl01.x, pl1 = pl01.y;
+  const float2 rl01 = make_float2(pl1 * s2 - pl2 * s1, pl2 * s0 - pl0 * s2);
+  const float rl2 = pl0 * s1 - pl1 * s0;
   // increment D = r + rl + 2 h E, added to the pair exactly:
   // (u + ul) + D = su + (ul + g + f + rl) with d + f = r + 2k, su + g = u + d
-  float f0, f1, f2, g0, g1, g2;
-  const float d0 = two_sum(r0, 2.0f * k0, f0), d1 = two_sum(r1, 2.0f * k1, f1);
+  float2 f01, g01;
+  float f2, g2;
+  const float2 d01 = two_sum2(r01, add2(k01, k01), f01);
   const float d2 = two_sum(r2, 2.0f * k2, f2);
-  du[0] = d0;
-  du[1] = d1;
+  du[0] = d01.x;
+  du[1] = d01.y;
   du[2] = d2;
-  const float su0 = two_sum(u[0], d0, g0), su1 = two_sum(u[1], d1, g1);
+  const float2 su01 = two_sum2(make_float2(u[0], u[1]), d01, g01);
   const float su2 = two_sum(u[2], d2, g2);
-  const float lo0 = ul[0] + (g0 + (f0 + rl0)), lo1 = ul[1] + (g1 + (f1 + rl1));
+  const float2 lo01 = add2(make_float2(ul[0], ul[1]), add2(g01, add2(f01, rl01)));
   const float lo2 = ul[2] + (g2 + (f2 + rl2));
   // renormalise (FastTwoSum: |su| >= |lo|)
-  u[0] = su0 + lo0;
-  u[1] = su1 + lo1;
+  const float2 un01 = add2(su01, lo01);
+  const float2 uln01 = sub2(lo01, sub2(un01, su01));
+  u[0] = un01.x;
+  u[1] = un01.y;
   u[2] = su2 + lo2;
-  ul[0] = lo0 - (u[0] - su0);
-  ul[1] = lo1 - (u[1] - su1);
+  ul[0] = uln01.x;
+  ul[1] = uln01.y;
   ul[2] = lo2 - (u[2] - su2);
 }
 
@@ -164,7 +204,8 @@ __device__ __forceinline__ float2 two_sum_add(float2 v, float x) {
 }
 
 // Stencil point accumulate: six field components of one cell (two 16-byte
-// loads of the cell-interleaved copy) weighted by ww, as three paired FMAs.
+// loads of the cell-interleaved copy, whose record holds E0 E1 B0 B1 E2 B2)
+// weighted by ww, as three paired FMAs into (E0, E1), (B0, B1), (E2, B2).
 __device__ __forceinline__ void acc_point(float2* f, float ww, float4 a, float4 b) {
   const float2 w2 = make_float2(ww, ww);
   f[0] = __ffma2_rn(w2, make_float2(a.x, a.y), f[0]);
@@ -356,11 +397,10 @@ __global__ void __launch_bounds__(kT, 3)
               acc_point(f2, wzy * wx[kx], sb4[2 * (row + kx)], sb4[2 * (row + kx) + 1]);
           }
         }
-        const float f[6] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y};
         float du[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) d0[a] = o[a];
-        boris_f32(up, ul, f, f + 3, h, hl, du);
+        boris_f32(up, ul, f2, h, hl, du);
         const float gi = rsqrtf(1.0f + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
         bool out = false;
 #pragma unroll
@@ -518,10 +558,6 @@ __host__ __device__ inline Mixed3Smem mixed3_smem() {
   return s;
 }
 
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-  return __fadd2_rn(a, make_float2(-b.x, -b.y));
-}
 // Knuth's TwoSum on two lanes: s + v = s' + err exactly in each; err joins e.
 __device__ __forceinline__ void two_sum_acc2(float2& s, float2& e, float2 v) {
   const float2 t = add2(s, v);
@@ -737,9 +773,8 @@ __global__ void __launch_bounds__(kT, 3)
               for (int kx = 0; kx < 3; ++kx)
                 acc_point(f2, wzy * wx[kx], row[2 * kx], row[2 * kx + 1]);
             }
-          const float f[6] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y};
           float du[3];
-          boris_f32(up, ul, f, f + 3, h, hl, du);
+          boris_f32(up, ul, f2, h, hl, du);
           const float gi = rsqrtf(1.0f + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
           bool out = false;
 #pragma unroll
@@ -910,9 +945,8 @@ __device__ __forceinline__ void advance_mixed(const float* __restrict__ fp, cons
         }
       }
     }
-    float f[6] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y};
     float du[3];
-    boris_f32(up, ul, f, f + 3, h, hl, du);
+    boris_f32(up, ul, f2, h, hl, du);
     const float gi = rsqrtf(1.0f + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
