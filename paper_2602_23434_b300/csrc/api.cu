@@ -154,7 +154,7 @@ struct Layout {
   size_t fpad, keys0, keys1, vals0, vals1, hist, hsum, cstart, tmp, dpart, samples, status,
       alt_x, alt_off, alt_u, alt_w, alt_id, shock_r, shock_q, shock_list, shock_rs, shock_qs,
       cstart_alt, bcount,
-      bsum, bslot, lpcache, fpair, fxq, smap, total;
+      bsum, bslot, lpcache, fpair, fxq, fxq_bytes, smap, total;
 };
 
 int ncomp_of(part_mode m) { return m == PART_BORIS ? 6 : 7; }
@@ -206,7 +206,11 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   L.shock_qs = take(lp ? (size_t)c1 * 8 : 0);
   L.lpcache = take(lp ? (size_t)6 * c1 * 8 : 0);
   L.fpair = take(lp ? (size_t)16 * g.pplane * 4 : 0);
-  L.fxq = take(lp ? (size_t)7 * 4 * g.pplane * 8 : 0);
+  // x quadratics of the FP64 fields: the LP gathers, and the 3D FP64 Boris
+  // brick kernels (TSC) read the fields through them
+  const bool xq = lp || (mode == PART_BORIS && prec == PART_FP64 && g.dim == 3);
+  L.fxq_bytes = xq ? (size_t)(lp ? 7 : 6) * 4 * g.pplane * 8 : 0;
+  L.fxq = take(L.fxq_bytes);
   L.smap = take(lp ? (size_t)3 * c1 * 8 : 0);
   // Boris modes: second cell_start and the brick counts of the incremental sort
   L.cstart_alt = take(alt ? (size_t)(g.nkeys + 1) * 4 : 0);
@@ -380,9 +384,9 @@ part_status part_init(part_ctx** out, const part_grid* grid, part_prec prec, par
     c->shock_qs = (double*)(c->ws + L.shock_qs);
     c->lpcache = (double*)(c->ws + L.lpcache);
     c->fpair = (float*)(c->ws + L.fpair);
-    c->fxq = (double*)(c->ws + L.fxq);
     c->smap = (double*)(c->ws + L.smap);
   }
+  c->fxq = L.fxq_bytes ? (double*)(c->ws + L.fxq) : nullptr;
   cudaError_t e = cudaMemsetAsync(c->status, 0, 256, c->stream);
   if (e != cudaSuccess) {
     part_status r = cuda_fail(nullptr, e, "status reset");
@@ -415,7 +419,8 @@ part_status part_set_fields(part_ctx* c, const void* fields, int ncomp, part_pre
   if (check_access(c, fields, "fields") != PART_OK) return PART_EINVAL;
   cudaError_t e = launch_pad_fields(c, fields);
   if (e == cudaSuccess && c->mode == PART_LP_RK2) e = launch_pad_pair_lp(c);
-  if (e == cudaSuccess && c->mode == PART_LP_RK2) e = launch_pad_xq_lp(c);
+  if (e == cudaSuccess && c->fxq && (c->mode == PART_LP_RK2 || c->shape == PART_TSC))
+    e = launch_pad_xq(c);
   if (e == cudaSuccess && c->shk) e = launch_shock_cells(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "part_set_fields");
   c->fields_set = true;

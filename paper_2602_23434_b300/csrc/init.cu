@@ -225,6 +225,36 @@ __global__ void k_pad_fields_aos8(const float* __restrict__ src, float* __restri
   }
 }
 
+// The x quadratics of the padded FP64 fields, used by the TSC gathers that
+// read the fields from global memory in FP64: along x the three weighted
+// cells of a stencil row sum to q0 + d (q1 + d q2), d the offset from the
+// cell centre, with q0 = (F[-1] + F[1]) / 8 + 3 F[0] / 4,
+// q1 = (F[1] - F[-1]) / 2 and q2 = (F[-1] + F[1]) / 2 - F[0] (the TSC weights
+// expanded in d).  For each component and padded cell with both x neighbours,
+// (q0, q1, q2, 0) as one 32-byte record; 0 elsewhere (never read).
+__global__ void k_pad_xq(const double* __restrict__ fp, const Geo g, int ncomp,
+                         double* __restrict__ fxq) {
+  const int64_t pp = g.pplane;
+  double4_32a* __restrict__ q4 = reinterpret_cast<double4_32a*>(fxq);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < pp;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int px = (int)(q % g.pn[0]);
+    const bool in = px >= 1 && px <= g.pn[0] - 2;
+    for (int c = 0; c < ncomp; ++c) {
+      double4_32a o;
+      o.x = o.y = o.z = o.w = 0.0;
+      if (in) {
+        const double fm = fp[c * pp + q - 1], f0 = fp[c * pp + q], fq = fp[c * pp + q + 1];
+        const double sp = fm + fq;
+        o.x = fma(0.75, f0, 0.125 * sp);
+        o.y = 0.5 * (fq - fm);
+        o.z = fma(0.5, sp, -f0);
+      }
+      q4[c * pp + q] = o;
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_pad_fields(part_ctx* c, const void* src) {
@@ -288,6 +318,13 @@ __global__ void k_selftest_wait(int* __restrict__ status, uint64_t limit_ns, int
 
 cudaError_t launch_selftest_wait(part_ctx* c, int64_t limit_ns, int arrive) {
   k_selftest_wait<<<1, 32, 0, c->stream>>>(c->status, (uint64_t)limit_ns, arrive);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pad_xq(part_ctx* c) {
+  k_pad_xq<<<grid_for(c, c->geo.pplane, 256), 256, 0, c->stream>>>(
+      (const double*)c->fpad, c->geo, c->ncomp, c->fxq);
   c->launches++;
   return cudaGetLastError();
 }

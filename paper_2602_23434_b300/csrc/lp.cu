@@ -733,39 +733,6 @@ __global__ void k_lp_sample_rho(const double* __restrict__ fp, const double* __r
   }
 }
 
-// The x quadratics of the padded LP fields (see Stencil::gather_xq): for each
-// component and padded cell with both x neighbours, (q0, q1, q2, 0) as one
-// 32-byte record; 0 elsewhere (never read).
-__global__ void k_pad_xq_lp(const double* __restrict__ fp, const Geo g, double* __restrict__ fxq) {
-  const int64_t pp = g.pplane;
-  double4_32a* __restrict__ q4 = reinterpret_cast<double4_32a*>(fxq);
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < pp;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int px = (int)(q % g.pn[0]);
-    const bool in = px >= 1 && px <= g.pn[0] - 2;
-#pragma unroll
-    for (int c = 0; c < 7; ++c) {
-      double4_32a o;
-      o.x = o.y = o.z = o.w = 0.0;
-      if (in) {
-        const double fm = fp[c * pp + q - 1], f0 = fp[c * pp + q], fq = fp[c * pp + q + 1];
-        const double sp = fm + fq;
-        o.x = fma(0.75, f0, 0.125 * sp);
-        o.y = 0.5 * (fq - fm);
-        o.z = fma(0.5, sp, -f0);
-      }
-      q4[c * pp + q] = o;
-    }
-  }
-}
-
-cudaError_t launch_pad_xq_lp(part_ctx* c) {
-  k_pad_xq_lp<<<grid_for(c, c->geo.pplane, 256), 256, 0, c->stream>>>((const double*)c->fpad,
-                                                                      c->geo, c->fxq);
-  c->launches++;
-  return cudaGetLastError();
-}
-
 cudaError_t launch_lp_sample_rho(part_ctx* c) {
   if (c->n == 0) return cudaSuccess;
   const int gb = grid_for(c, c->n, 256);

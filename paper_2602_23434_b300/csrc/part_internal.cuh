@@ -89,7 +89,7 @@ struct part_ctx {
   double* lpcache{};  // LP v, B at the current positions [6][capacity] (paired: [12] f32)
   bool lp_cache_ok{}; // lpcache matches the bound LPs, their order and the fields
   float* fpair{};     // LP: paired-f32 copy of the padded fields, 16 floats per cell
-  double* fxq{};      // LP: x quadratics of the padded fields, 4 doubles per (component, cell)
+  double* fxq{};      // x quadratics of the padded FP64 fields (LP; Boris in 3D), 4 doubles per (component, cell)
   int lp_paired{};    // LP push arithmetic: 0 FP64, 1 paired f32
   double* smap{};     // LP deferred spectra: per-LP map (alpha, beta, S) [3][capacity]
   int spec_lazy{};    // spec_update composes maps instead of updating every bin
@@ -359,7 +359,7 @@ cudaError_t launch_lp_push_pair_range(part_ctx* c, double dt, const LpLaunch& L)
 cudaError_t launch_spec_range(part_ctx* c, double dt, double c0, double u_rad, bool from_plain,
                               const LpLaunch& L);
 cudaError_t launch_pad_pair_lp(part_ctx* c);               // fpair from fpad
-cudaError_t launch_pad_xq_lp(part_ctx* c);                 // fxq from fpad
+cudaError_t launch_pad_xq(part_ctx* c);                    // fxq from fpad (FP64)
 cudaError_t launch_shock_cells(part_ctx* c);       // shock_r, shock_q from the padded LP fields
 cudaError_t launch_shock_convolve(part_ctx* c);    // Eq. convolution_spectra on the list
 cudaError_t launch_boris(part_ctx* c, double qm, double dt, int nsteps);

@@ -105,8 +105,9 @@ __device__ __forceinline__ void load_state64(PState64& s, uint32_t q, const doub
   s.id = ids ? ids[q] : 0ull;
 }
 
-template <int SHAPE, int DIM, bool DEP, bool OPEN>
+template <int SHAPE, int DIM, bool DEP, bool OPEN, bool XQ>
 __device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int bvol,
+                                         const double* __restrict__ fxq,
                                          const uint32_t* scs, const int* org, uint32_t p,
                                          uint32_t q, const double* xs, const double* us,
                                          const double* ws, const uint64_t* ids, double* x,
@@ -166,13 +167,27 @@ __device__ __forceinline__ void push_one(const Geo& g, const double* sbox, int b
     for (int ky = 0; ky < 3; ++ky) {
       const double wzy = wz[kz] * wy[ky];
       if (DEP) wyz[kz * 3 + ky] = wzy;
-      const int row = (zz * g.box[1] + l[1] + ky) * g.box[0] + l[0];
+      if (XQ) {
+        // TSC along x from the row's x quadratics (read through L1): the
+        // three weighted cells are q0 + d (q1 + d q2); padded index of cell
+        // j is j + 1, so the row centre is at the particle's own padded x
+        const double4_32a* __restrict__ q4 = reinterpret_cast<const double4_32a*>(fxq);
+        const int64_t rc = ((int64_t)(org[2] + zz) * g.pn[1] + org[1] + l[1] + ky) * g.pn[0] +
+                           org[0] + l[0] + 1;
 #pragma unroll
-      for (int kx = 0; kx < 3; ++kx) {
-        const double ww = wzy * wx[kx];
-        const double* sp = sbox + row + kx;
+        for (int c = 0; c < 6; ++c) {
+          const double4_32a q = q4[(int64_t)c * g.pplane + rc];
+          f[c] = fma(wzy, fma(d[0], fma(d[0], q.z, q.y), q.x), f[c]);
+        }
+      } else {
+        const int row = (zz * g.box[1] + l[1] + ky) * g.box[0] + l[0];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) f[c] += ww * sp[c * bvol];
+        for (int kx = 0; kx < 3; ++kx) {
+          const double ww = wzy * wx[kx];
+          const double* sp = sbox + row + kx;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) f[c] += ww * sp[c * bvol];
+        }
       }
     }
   }
@@ -299,7 +314,7 @@ __device__ __forceinline__ void named_bar_arrive(int id, int nthreads) {
 // Common prologue: TMA of the haloed box on an mbarrier (bounded wait),
 // cell_start of the brick, zeroed windows.  Returns false (after reporting
 // ST_TIMEOUT) if the copy did not land.
-template <int NT>
+template <int NT, bool STAGE>
 __device__ __forceinline__ bool brick_prologue(const CUtensorMap* tmap, const Geo& g,
                                                double* sbox, int bvol, uint32_t* scs,
                                                uint64_t* bar, int* sflag, double* win,
@@ -311,7 +326,7 @@ __device__ __forceinline__ bool brick_prologue(const CUtensorMap* tmap, const Ge
     *sflag = 0;
   }
   __syncthreads();
-  if (tid == 0) {
+  if (STAGE && tid == 0) {
     mbar_arrive_expect_tx(bar, (uint32_t)(6 * bvol * 8));
     // padded index of cell c is c + h, so the box starting one cell below the
     // brick origin starts at padded coordinate o
@@ -319,7 +334,7 @@ __device__ __forceinline__ bool brick_prologue(const CUtensorMap* tmap, const Ge
   }
   for (int i = tid; i <= g.V; i += NT) scs[i] = cstart[brick * g.V + i];
   for (int i = tid; i < nwin; i += NT) win[i] = 0.0;
-  if (!mbar_wait_bounded(bar, 0)) atomicOr(sflag, 1);
+  if (STAGE && !mbar_wait_bounded(bar, 0)) atomicOr(sflag, 1);
   __syncthreads();
   if (*sflag) {
     if (tid == 0) {
@@ -336,14 +351,15 @@ __device__ __forceinline__ bool brick_prologue(const CUtensorMap* tmap, const Ge
 template <int SHAPE, int DIM, bool OPEN>
 __global__ void __launch_bounds__(kT, 2)
     k_boris_brick_f64(const __grid_constant__ CUtensorMap tmap, const Geo g,
-                      const double* xs, const double* us, const double* ws,
+                      const double* __restrict__ fxq, const double* xs, const double* us, const double* ws,
                       const uint64_t* ids, double* x, double* u, double* wd, uint64_t* idd,
                       int64_t n, const uint32_t* __restrict__ perm,
                       const uint32_t* __restrict__ cstart, double* __restrict__ dpart,
                       double qm, double dt, double inv_dt, int* __restrict__ status,
                       uint8_t* __restrict__ outmask) {
+  constexpr bool XQ = SHAPE == PART_TSC && DIM == 3;  // gather from the x quadratics
   extern __shared__ __align__(128) unsigned char smem[];
-  const BrickSmem L = brick_smem(g, 6, 8, false);
+  const BrickSmem L = brick_smem(g, XQ ? 0 : 6, 8, false);
   const int tid = threadIdx.x;
   const int bvol = g.box[0] * g.box[1] * g.box[2];
   double* sbox = reinterpret_cast<double*>(smem);
@@ -354,8 +370,8 @@ __global__ void __launch_bounds__(kT, 2)
   const int org[3] = {(int)(brick % g.nb[0]) * g.b[0],
                       (int)((brick / g.nb[0]) % g.nb[1]) * g.b[1],
                       (int)(brick / ((int64_t)g.nb[0] * g.nb[1])) * g.b[2]};
-  if (!brick_prologue<kT>(&tmap, g, sbox, bvol, scs, bar, sflag, nullptr, 0, cstart, brick,
-                          org, status))
+  if (!brick_prologue<kT, !XQ>(&tmap, g, sbox, bvol, scs, bar, sflag, nullptr, 0, cstart, brick,
+                               org, status))
     return;
   const double h = 0.5 * qm * dt;
   const uint32_t p0 = scs[0], p1 = scs[g.V];
@@ -374,9 +390,9 @@ __global__ void __launch_bounds__(kT, 2)
       qnext = perm ? perm[p + kT] : p + kT;
       load_state64(nxt, qnext, xs, us, ws, ids, n);
     }
-    push_one<SHAPE, DIM, false, OPEN>(g, sbox, bvol, scs, org, p, qcur, xs, us, ws, ids, x, u, wd,
-                                      idd, n, h, dt, inv_dt, status, outmask, nullptr, nullptr,
-                                      &cur);
+    push_one<SHAPE, DIM, false, OPEN, XQ>(g, sbox, bvol, fxq, scs, org, p, qcur, xs, us, ws, ids,
+                                          x, u, wd, idd, n, h, dt, inv_dt, status, outmask,
+                                          nullptr, nullptr, &cur);
   }
 }
 
@@ -389,7 +405,7 @@ __global__ void __launch_bounds__(kT, 2)
 template <int SHAPE, int DIM, bool OPEN>
 __global__ void __launch_bounds__(2 * kT, 1)
     k_boris_brick_f64_dep(const __grid_constant__ CUtensorMap tmap, const Geo g,
-                          const double* xs, const double* us, const double* ws,
+                          const double* __restrict__ fxq, const double* xs, const double* us, const double* ws,
                           const uint64_t* ids, double* x, double* u, double* wd,
                           uint64_t* idd, int64_t n, const uint32_t* __restrict__ perm,
                           const uint32_t* __restrict__ cstart,
@@ -397,8 +413,9 @@ __global__ void __launch_bounds__(2 * kT, 1)
                           int* __restrict__ status, uint8_t* __restrict__ outmask) {
   constexpr int NT = 2 * kT;
   constexpr int kFull = 1, kEmpty = 3;  // named barrier ids (0 is __syncthreads)
+  constexpr bool XQ = SHAPE == PART_TSC && DIM == 3;  // gather from the x quadratics
   extern __shared__ __align__(128) unsigned char smem[];
-  const BrickSmem L = brick_smem(g, 6, 8, true);
+  const BrickSmem L = brick_smem(g, XQ ? 0 : 6, 8, true);
   const int tid = threadIdx.x;
   const int bvol = g.box[0] * g.box[1] * g.box[2];
   double* sbox = reinterpret_cast<double*>(smem);
@@ -413,8 +430,8 @@ __global__ void __launch_bounds__(2 * kT, 1)
   const int org[3] = {(int)(brick % g.nb[0]) * g.b[0],
                       (int)((brick / g.nb[0]) % g.nb[1]) * g.b[1],
                       (int)(brick / ((int64_t)g.nb[0] * g.nb[1])) * g.b[2]};
-  if (!brick_prologue<NT>(&tmap, g, sbox, bvol, scs, bar, sflag, win, kWarps * wsize, cstart,
-                          brick, org, status))
+  if (!brick_prologue<NT, !XQ>(&tmap, g, sbox, bvol, scs, bar, sflag, win, kWarps * wsize,
+                               cstart, brick, org, status))
     return;
   const uint32_t p0 = scs[0], p1 = scs[g.V];
   const int nchunks = (int)((p1 - p0 + kT - 1) / kT);
@@ -444,9 +461,9 @@ __global__ void __launch_bounds__(2 * kT, 1)
           qnext = perm ? perm[p + kT] : p + kT;
           load_state64(nxt, qnext, xs, us, ws, ids, n);
         }
-        push_one<SHAPE, DIM, true, OPEN>(g, sbox, bvol, scs, org, p, qcur, xs, us, ws, ids, x,
-                                         u, wd, idd, n, h, dt, inv_dt, status, outmask, wyz,
-                                         fxc, &cur);
+        push_one<SHAPE, DIM, true, OPEN, XQ>(g, sbox, bvol, fxq, scs, org, p, qcur, xs, us, ws,
+                                             ids, x, u, wd, idd, n, h, dt, inv_dt, status,
+                                             outmask, wyz, fxc, &cur);
       }
       if (k >= 2) named_bar_sync(kEmpty + b, NT);  // deposit of chunk k-2 has read it
       double* rw = rec + (size_t)b * 18 * kRS;
@@ -695,7 +712,8 @@ cudaError_t brick_f64(part_ctx* c, double qm, double dt) {
                           : k_boris_brick_f64_dep<SHAPE, DIM, false>)
                   : (open ? k_boris_brick_f64<SHAPE, DIM, true>
                           : k_boris_brick_f64<SHAPE, DIM, false>);
-  const BrickSmem L = brick_smem(c->geo, 6, 8, DEP);
+  constexpr bool XQ = SHAPE == PART_TSC && DIM == 3;  // no staged box: the x quadratics
+  const BrickSmem L = brick_smem(c->geo, XQ ? 0 : 6, 8, DEP);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L.total);
   if (e != cudaSuccess) return e;
@@ -704,7 +722,7 @@ cudaError_t brick_f64(part_ctx* c, double qm, double dt) {
   const PState src = state_of(c, c->cur_alt);
   const PState dst = c->perm_pend ? state_of(c, !c->cur_alt) : src;
   kern<<<(unsigned)c->geo.nbricks, DEP ? 2 * kT : kT, L.total, c->stream>>>(
-      c->tmap, c->geo, (const double*)src.x, (const double*)src.u, (const double*)src.w, src.id,
+      c->tmap, c->geo, c->fxq, (const double*)src.x, (const double*)src.u, (const double*)src.w, src.id,
       (double*)dst.x, (double*)dst.u, (double*)dst.w, dst.id, c->n, c->perm_pend, c->cstart,
       c->dpart, qm, dt, 1.0 / dt, c->status, c->outmask);
   c->launches++;
