@@ -58,11 +58,11 @@ FLOP_PER_PSTEP_BORIS_DEP = 12 + 24 + 360 + 58 + 17 + 178
 BYTES_PER_PSTEP_BORIS_DEP = 96 + 8 + 6 + 3
 # DRAM bytes (read + write) per particle of one launch of the FP64 brick kernel,
 # from an ncu capture of the kernel on the 64^3 case of the same workload (
-# 265.0 MB for 2,097,152 particles), scaled to a launch by the particle count.
-TRAFFIC_PER_PARTICLE_BRICK_F64 = 264.987392e6 / 2097152  # ncu dram r+w, 64^3 capture
+# 315.4 MB for 2,097,152 particles), scaled to a launch by the particle count.
+TRAFFIC_PER_PARTICLE_BRICK_F64 = 315.386624e6 / 2097152  # ncu dram r+w, 64^3 capture
 # Same for the mixed brick kernel, from an ncu capture of the 128^3 case
-# (1710.1 MB for 16,777,216 particles).
-TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1710.065664e6 / 16777216   # ncu dram r+w, 128^3 capture
+# (1709.7 MB for 16,777,216 particles).
+TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1709.683968e6 / 16777216   # ncu dram r+w, 128^3 capture
 
 
 # Nominal HBM3e bandwidth of a B300 (GB/s): fractions against it are reported
