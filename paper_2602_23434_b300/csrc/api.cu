@@ -206,9 +206,9 @@ Layout layout_of(const Geo& g, part_prec prec, part_mode mode, int64_t cap, int 
   L.shock_qs = take(lp ? (size_t)c1 * 8 : 0);
   L.lpcache = take(lp ? (size_t)6 * c1 * 8 : 0);
   L.fpair = take(lp ? (size_t)16 * g.pplane * 4 : 0);
-  // x quadratics of the FP64 fields: the LP gathers, and the 3D FP64 Boris
-  // brick kernels (TSC) read the fields through them
-  const bool xq = lp || (mode == PART_BORIS && prec == PART_FP64 && g.dim == 3);
+  // x quadratics of the FP64 fields: the LP gathers and the FP64 Boris
+  // kernels (TSC) read the fields through them
+  const bool xq = lp || (mode == PART_BORIS && prec == PART_FP64);
   L.fxq_bytes = xq ? (size_t)(lp ? 7 : 6) * 4 * g.pplane * 8 : 0;
   L.fxq = take(L.fxq_bytes);
   L.smap = take(lp ? (size_t)3 * c1 * 8 : 0);

@@ -89,7 +89,7 @@ struct part_ctx {
   double* lpcache{};  // LP v, B at the current positions [6][capacity] (paired: [12] f32)
   bool lp_cache_ok{}; // lpcache matches the bound LPs, their order and the fields
   float* fpair{};     // LP: paired-f32 copy of the padded fields, 16 floats per cell
-  double* fxq{};      // x quadratics of the padded FP64 fields (LP; Boris in 3D), 4 doubles per (component, cell)
+  double* fxq{};      // x quadratics of the padded FP64 fields (LP; FP64 Boris), 4 doubles per (component, cell)
   int lp_paired{};    // LP push arithmetic: 0 FP64, 1 paired f32
   double* smap{};     // LP deferred spectra: per-LP map (alpha, beta, S) [3][capacity]
   int spec_lazy{};    // spec_update composes maps instead of updating every bin

@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kT, 2)
                       const uint32_t* __restrict__ cstart, double* __restrict__ dpart,
                       double qm, double dt, double inv_dt, int* __restrict__ status,
                       uint8_t* __restrict__ outmask) {
-  constexpr bool XQ = SHAPE == PART_TSC && DIM == 3;  // gather from the x quadratics
+  constexpr bool XQ = SHAPE == PART_TSC;  // gather from the x quadratics
   extern __shared__ __align__(128) unsigned char smem[];
   const BrickSmem L = brick_smem(g, XQ ? 0 : 6, 8, false);
   const int tid = threadIdx.x;
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(2 * kT, 1)
                           int* __restrict__ status, uint8_t* __restrict__ outmask) {
   constexpr int NT = 2 * kT;
   constexpr int kFull = 1, kEmpty = 3;  // named barrier ids (0 is __syncthreads)
-  constexpr bool XQ = SHAPE == PART_TSC && DIM == 3;  // gather from the x quadratics
+  constexpr bool XQ = SHAPE == PART_TSC;  // gather from the x quadratics
   extern __shared__ __align__(128) unsigned char smem[];
   const BrickSmem L = brick_smem(g, XQ ? 0 : 6, 8, true);
   const int tid = threadIdx.x;
@@ -497,7 +497,8 @@ __global__ void __launch_bounds__(2 * kT, 1)
 // ---------------------------------------------------------------- particle order, FP64
 template <int SHAPE, int DIM, bool OPEN>
 __global__ void __launch_bounds__(256)
-    k_boris_particles_f64(const double* __restrict__ fp, const Geo g, double* __restrict__ x,
+    k_boris_particles_f64(const double* __restrict__ fp, const double* __restrict__ fxq,
+                          const Geo g, double* __restrict__ x,
                           double* __restrict__ u, int64_t n, double qm, double dt, int nsteps,
                           int* __restrict__ status, uint8_t* __restrict__ outmask) {
   const double h = 0.5 * qm * dt;
@@ -526,7 +527,7 @@ __global__ void __launch_bounds__(256)
         d[a] = __dsub_rn(__dsub_rn(s, (double)j[a]), 0.5);
       }
       double wx[3], wy[3], wz[3] = {0.0, 1.0, 0.0};
-      shape_weights<SHAPE>(d[0], wx);
+      if (SHAPE != PART_TSC) shape_weights<SHAPE>(d[0], wx);
       shape_weights<SHAPE>(d[1], wy);
       if (DIM == 3) shape_weights<SHAPE>(d[2], wz);
       double f[6] = {0, 0, 0, 0, 0, 0};
@@ -537,11 +538,20 @@ __global__ void __launch_bounds__(256)
         for (int ky = 0; ky < 3; ++ky) {
           const double wzy = wz[kz] * wy[ky];
           const int64_t row = ((int64_t)zz * g.pn[1] + j[1] + ky) * g.pn[0] + j[0];
+          if (SHAPE == PART_TSC) {  // the row from its x quadratics, as in the brick kernels
+            const double4_32a* __restrict__ q4 = reinterpret_cast<const double4_32a*>(fxq);
 #pragma unroll
-          for (int kx = 0; kx < 3; ++kx) {
-            const double ww = wzy * wx[kx];
+            for (int c = 0; c < 6; ++c) {
+              const double4_32a q = q4[(int64_t)c * g.pplane + row + 1];
+              f[c] = fma(wzy, fma(d[0], fma(d[0], q.z, q.y), q.x), f[c]);
+            }
+          } else {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) f[c] += ww * __ldg(fp + c * g.pplane + row + kx);
+            for (int kx = 0; kx < 3; ++kx) {
+              const double ww = wzy * wx[kx];
+#pragma unroll
+              for (int c = 0; c < 6; ++c) f[c] += ww * __ldg(fp + c * g.pplane + row + kx);
+            }
           }
         }
       }
@@ -712,7 +722,7 @@ cudaError_t brick_f64(part_ctx* c, double qm, double dt) {
                           : k_boris_brick_f64_dep<SHAPE, DIM, false>)
                   : (open ? k_boris_brick_f64<SHAPE, DIM, true>
                           : k_boris_brick_f64<SHAPE, DIM, false>);
-  constexpr bool XQ = SHAPE == PART_TSC && DIM == 3;  // no staged box: the x quadratics
+  constexpr bool XQ = SHAPE == PART_TSC;  // no staged box: the x quadratics
   const BrickSmem L = brick_smem(c->geo, XQ ? 0 : 6, 8, DEP);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L.total);
@@ -739,7 +749,7 @@ cudaError_t particles_f64(part_ctx* c, double qm, double dt, int nsteps) {
                               : k_boris_particles_f64<SHAPE, DIM, false>;
   const int t = threads_for_spread(c, c->n);
   kern<<<grid_for(c, c->n, t), t, 0, c->stream>>>(
-      (const double*)c->fpad, c->geo, (double*)c->x, (double*)c->u, c->n, qm, dt, nsteps,
+      (const double*)c->fpad, c->fxq, c->geo, (double*)c->x, (double*)c->u, c->n, qm, dt, nsteps,
       c->status, c->outmask);
   c->launches++;
   return cudaGetLastError();
