@@ -91,7 +91,9 @@ typedef struct {
  * nkeys gets the key-space size nbx*nby*nbz*b0*b1*b2.                      */
 part_status part_brick_dims(const part_grid* grid, int brick[3], int64_t* nkeys);
 
-/* Workspace bytes for a context: padded field copy, sort buffers, cell_start,
+/* Workspace bytes for a context: padded field copy (and, for FP64 fields,
+ * its x quadratics: the TSC gathers read each stencil row as q0 + d (q1 +
+ * d q2), 32 bytes per component and padded cell), sort buffers, cell_start,
  * deposit partials, LP samples, status word.  capacity = maximum particles,
  * nbins = spectral bins (LP mode; ignored otherwise).                     */
 part_status part_workspace_size(const part_grid* grid, part_prec prec, part_mode mode,
@@ -113,7 +115,8 @@ part_status part_destroy(part_ctx* ctx);
  * context) or f32 (PART_MIXED context); field_prec must match.
  * PART_BORIS: ncomp = 6 (E then B).  PART_LP_RK2: ncomp = 7 (fluid velocity
  * v[3], density rho, B[3]) -- the fluid quantities LPs sample (Sec. 2).
- * The copy is stream-ordered; the source may be freed once it completes.
+ * The copy (with the x quadratics of FP64 fields) is stream-ordered; the
+ * source may be freed once it completes.
  * fields must be aligned to its element size, and be device memory of the
  * context's device, managed memory, or pinned host memory (read once by the
  * padding kernel over the host link); anything else, such as pageable host
