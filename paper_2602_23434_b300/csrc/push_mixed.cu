@@ -536,7 +536,10 @@ constexpr int kE3 = kB3 + 2;       // haloed tile side
 constexpr int kPC = kB3 * kB3;     // cells in a brick plane
 constexpr int kPT = kE3 * kE3;     // cells in a tile plane
 constexpr int kM3 = 640;           // particles per chunk (a plane holds ~512 at 8 per cell)
-constexpr int kRec = 12;           // record floats: wx[3] wy[3] wz[3] F[3]
+// record floats: (F[3], wx0), (wy[3], wx1), (wz[3], wx2) -- F and wy start
+// 16-byte rows, so the per-cell sums read (F0, F1) and (wy0, wy1) as aligned
+// pairs for the paired multiplies
+constexpr int kRec = 12;
 // stride of the plane sums per (component, kz): 9 * 64 + 11 floats, so the
 // three kz lanes of a cell store to different banks
 constexpr int kTS = 9 * kPC + 11;
@@ -792,9 +795,9 @@ __global__ void __launch_bounds__(kT, 3)
             u[(a + 3) * n + p] = ul[a];
           }
           const float wdt = wcur * inv_dt;
-          r0 = make_float4(wx[0], wx[1], wx[2], wy[0]);
-          r1 = make_float4(wy[1], wy[2], wz[0], wz[1]);
-          r2 = make_float4(wz[2], du[0] * wdt, du[1] * wdt, du[2] * wdt);
+          r0 = make_float4(du[0] * wdt, du[1] * wdt, du[2] * wdt, wx[0]);
+          r1 = make_float4(wy[0], wy[1], wy[2], wx[1]);
+          r2 = make_float4(wz[0], wz[1], wz[2], wx[2]);
         }
         float4* rq = reinterpret_cast<float4*>(rec + i * kRec);
         rq[0] = r0;
@@ -812,11 +815,14 @@ __global__ void __launch_bounds__(kT, 3)
       }
       // ---- B1: one thread per (cell, kz) of this plane
       float2 T01[9];  // (component 0, component 1) of target (ky, kx): index ky * 3 + kx
-      float T2[9];    // component 2
+      float2 T2p[3];  // component 2 of targets (0, kx) and (1, kx)
+      float T2s[3];   // component 2 of target (2, kx)
 #pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        T01[k] = make_float2(0.0f, 0.0f);
-        T2[k] = 0.0f;
+      for (int k = 0; k < 9; ++k) T01[k] = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        T2p[k] = make_float2(0.0f, 0.0f);
+        T2s[k] = 0.0f;
       }
       if (tid >= 3 * kPC) {
         for (int z = zw; z < lz; ++z) write_out(z, tid - 3 * kPC, kT - 3 * kPC);
@@ -828,19 +834,21 @@ __global__ void __launch_bounds__(kT, 3)
         const float4* q = reinterpret_cast<const float4*>(rec) + (ra - sb) * (kRec / 4);
         for (uint32_t r = ra; r < rb; ++r, q += kRec / 4) {
           const float4 a = q[0], b = q[1], c4 = q[2];
-          const float wzk = bkz == 0 ? b.z : (bkz == 1 ? b.w : c4.x);
-          const float P[3] = {wzk * a.w, wzk * b.x, wzk * b.y};
-          const float wx[3] = {a.x, a.y, a.z};
+          const float wzk = bkz == 0 ? c4.x : (bkz == 1 ? c4.y : c4.z);
+          const float2 P01 = __fmul2_rn(make_float2(wzk, wzk), make_float2(b.x, b.y));
+          const float P2 = wzk * b.z;
+          const float P[3] = {P01.x, P01.y, P2};
+          const float2 F01 = make_float2(a.x, a.y);
+          const float wx[3] = {a.w, b.w, c4.w};
 #pragma unroll
           for (int kx = 0; kx < 3; ++kx) {
-            const float2 Q01 =
-                __fmul2_rn(make_float2(wx[kx], wx[kx]), make_float2(c4.y, c4.z));
-            const float Q2 = wx[kx] * c4.w;
+            const float2 Q01 = __fmul2_rn(make_float2(wx[kx], wx[kx]), F01);
+            const float Q2 = wx[kx] * a.z;
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
+            for (int ky = 0; ky < 3; ++ky)
               T01[ky * 3 + kx] = __ffma2_rn(make_float2(P[ky], P[ky]), Q01, T01[ky * 3 + kx]);
-              T2[ky * 3 + kx] = fmaf(P[ky], Q2, T2[ky * 3 + kx]);
-            }
+            T2p[kx] = __ffma2_rn(P01, make_float2(Q2, Q2), T2p[kx]);
+            T2s[kx] = fmaf(P2, Q2, T2s[kx]);
           }
         }
       }
@@ -852,7 +860,8 @@ __global__ void __launch_bounds__(kT, 3)
         for (int k = 0; k < 9; ++k) {
           rec[(0 * 3 + bkz) * kTS + k * kPC + cl] = T01[k].x;
           rec[(1 * 3 + bkz) * kTS + k * kPC + cl] = T01[k].y;
-          rec[(2 * 3 + bkz) * kTS + k * kPC + cl] = T2[k];
+          rec[(2 * 3 + bkz) * kTS + k * kPC + cl] =
+              k < 3 ? T2p[k].x : (k < 6 ? T2p[k - 3].y : T2s[k - 6]);
         }
       }
       __syncthreads();
