@@ -45,6 +45,37 @@ def test_tsc_values_and_second_moment():
         assert abs(m2 - abs(d) * (1 - abs(d))) < 1e-15
 
 
+def test_tsc_row_as_x_quadratic():
+    """The three TSC-weighted cells of a stencil row are a quadratic in the
+    offset d from the cell centre: sum_k W(k - d) F_k = q0 + d (q1 + d q2) with
+    q0 = (F_-1 + F_1)/8 + 3 F_0/4, q1 = (F_1 - F_-1)/2, q2 = (F_-1 + F_1)/2 - F_0
+    (the weights expanded in d).  The FP64 TSC gathers read the fields through
+    these per-cell quadratics; here the oracle's gather, on random fields and
+    positions, is evaluated the same way row by row."""
+    n = 8
+    g = O.make_grid(3, (n, n, n))
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal((2, n, n, n))        # [comp][z][y][x]
+    dx = 2.0 / n
+    for _ in range(40):
+        p = rng.uniform(-1.0, 1.0, 3)
+        out = O.gather(g, O.TSC, f.reshape(2, -1), p)
+        s = (p + 1.0) / dx
+        j = np.floor(s).astype(int)
+        d = s - j - 0.5
+        w = [[0.5 * (0.5 - d[a]) ** 2, 0.75 - d[a] ** 2, 0.5 * (0.5 + d[a]) ** 2] for a in range(3)]
+        expect = np.zeros(2)
+        for kz in range(3):
+            for ky in range(3):
+                zz, yy = (j[2] + kz - 1) % n, (j[1] + ky - 1) % n
+                fm, f0, fp = (f[:, zz, yy, (j[0] + k) % n] for k in (-1, 0, 1))
+                q0 = (fm + fp) / 8 + 0.75 * f0
+                q1 = 0.5 * (fp - fm)
+                q2 = 0.5 * (fm + fp) - f0
+                expect += w[2][kz] * w[1][ky] * (q0 + d[0] * (q1 + d[0] * q2))
+        assert np.max(np.abs(out - expect)) < 1e-14
+
+
 # --------------------------------------------------------------- cell index
 def test_cell_coord_edges_and_wrap():
     g = O.make_grid(3, (64, 32, 16))
