@@ -60,6 +60,12 @@ BYTES_PER_PSTEP_BORIS_DEP = 96 + 8 + 6 + 3
 # from an ncu capture of the kernel on the 64^3 case of the same workload (
 # 315.4 MB for 2,097,152 particles), scaled to a launch by the particle count.
 TRAFFIC_PER_PARTICLE_BRICK_F64 = 315.386624e6 / 2097152  # ncu dram r+w, 64^3 capture
+# FP64 arithmetic the FP64 brick kernel executes per particle-step, from the
+# same capture's per-thread instruction counts (sass op dfma / dmul / dadd
+# over the 2,097,152 particles): the x-quadratic gather executes fewer
+# products than the method's count above, the Horner weights and the
+# rsqrt / reciprocal refinements more.
+FP64_OPS_PER_PSTEP_BRICK = {"dfma": 299, "dmul": 37, "dadd": 31}
 # Same for the mixed brick kernel, from an ncu capture of the 128^3 case
 # (1709.7 MB for 16,777,216 particles).
 TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1709.683968e6 / 16777216   # ncu dram r+w, 128^3 capture
@@ -796,6 +802,17 @@ def run_e2e(torch, wl: BorisWorkload, K: int):
 
 
 # ----------------------------------------------------------------------------- oracle
+def executed_fp64(N, kernel_ms, peak_tflops):
+    """The FP64 arithmetic the brick kernel executes (ncu counts per
+    particle-step), as a rate against the measured FP64 peak."""
+    ops = FP64_OPS_PER_PSTEP_BRICK
+    flop = 2 * ops["dfma"] + ops["dmul"] + ops["dadd"]
+    tf = flop * N / (kernel_ms / 1e3) / 1e12
+    return {"fp64_ops_per_particle_step": dict(ops), "flop_per_particle_step": flop,
+            "achieved": tf, "frac": tf / peak_tflops if peak_tflops else None,
+            "source": "ncu sass thread-instruction counts of the 64^3 capture"}
+
+
 def headline_config(grid: int, particles: int, dt: float, world: int) -> dict:
     """The `config` object of the headline line (both arms)."""
     return {"workload": "3D periodic 128^3, B = z + turbulent dB (64 Kolmogorov modes, "
@@ -1140,6 +1157,7 @@ def main():
                      "traffic_unit": "bytes per launch (ncu dram read+write, scaled by "
                                      "particles from the 64^3 capture)",
                      "flop_per_particle_step": FLOP_PER_PSTEP_BORIS_DEP,
+                     "executed": executed_fp64(wl.N, kmean, fp64_peak),
                      "kernel_ms": kmean,
                      "peak_note": "FP64 non-tensor FMA rate measured on this GPU by "
                                   "part_probe_fp64_fma right after the timed steps (burst); "
