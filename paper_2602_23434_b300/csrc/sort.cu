@@ -160,7 +160,9 @@ __global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t* __restrict_
 
 // Scan phase 2: exclusive scan of the block sums in one CTA.  Each thread
 // takes a contiguous segment (one block scan in all, whatever the count).
-__global__ void __launch_bounds__(256) k_scan_top(uint32_t* __restrict__ sums, int64_t nblk) {
+// total (if given) gets the sum of all blocks.
+__global__ void __launch_bounds__(256) k_scan_top(uint32_t* __restrict__ sums, int64_t nblk,
+                                                  uint32_t* __restrict__ total = nullptr) {
   __shared__ uint32_t wt[8];
   __shared__ uint32_t tot;
   const int64_t per = (nblk + 255) / 256;
@@ -174,6 +176,7 @@ __global__ void __launch_bounds__(256) k_scan_top(uint32_t* __restrict__ sums, i
     sums[i] = e;
     e += v;
   }
+  if (total && threadIdx.x == 0) *total = tot;
 }
 
 // Scan phase 3: exclusive scan inside each block plus its block offset.
@@ -639,26 +642,68 @@ __global__ void k_inc_finish(const uint32_t* __restrict__ bbase, int64_t nbricks
 // ---- compaction (Sec. 3.2): D = exclusive scan of the deletion flags over
 // n + 1 entries (D[n] = N_del); the k-th hole below n_keep = n - N_del takes
 // the k-th surviving particle at or beyond n_keep.
-__global__ void k_del_flags(const uint8_t* __restrict__ del, int64_t n, uint32_t* __restrict__ f) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    f[i] = (i < n && del[i]) ? 1u : 0u;
+// The scan of the deletion flags reads the mask itself: phase 1 sums the
+// flags of each kScanBlock block of the n + 1 entries (entry n is 0), phase 2
+// is k_scan_top (which also leaves N_del), and phase 3 writes D and, for each
+// deleted slot below n_keep, hole_pos[D[i]] = i.
+__global__ void __launch_bounds__(256) k_del_reduce(const uint8_t* __restrict__ del, int64_t n,
+                                                    uint32_t* __restrict__ sums) {
+  __shared__ uint32_t wt[8];
+  __shared__ uint32_t tot;
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  uint32_t s = 0;
+  for (int k = 0; k < kScanBlock / 256; ++k) {
+    const int64_t i = base + k * 256 + threadIdx.x;
+    if (i < n && del[i]) ++s;
+  }
+  block_exclusive_scan(s, wt, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
-__global__ void k_hole_pos(const uint8_t* __restrict__ del, const uint32_t* __restrict__ D,
-                           int64_t n, uint32_t* __restrict__ hole_pos) {
-  const int64_t nkeep = n - (int64_t)D[n];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nkeep;
-       i += (int64_t)gridDim.x * blockDim.x)
-    if (del[i]) hole_pos[D[i]] = (uint32_t)i;
+__global__ void __launch_bounds__(256) k_del_down(const uint8_t* __restrict__ del, int64_t n,
+                                                  const uint32_t* __restrict__ sums,
+                                                  const uint32_t* __restrict__ ndel,
+                                                  uint32_t* __restrict__ D,
+                                                  uint32_t* __restrict__ hole_pos) {
+  __shared__ uint32_t wt[8];
+  __shared__ uint32_t tot;
+  const int64_t nkeep = n - (int64_t)*ndel;
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  constexpr int per = kScanBlock / 256;
+  uint32_t v[per];
+  uint32_t s = 0;
+  for (int k = 0; k < per; ++k) {
+    const int64_t i = base + (int64_t)threadIdx.x * per + k;
+    v[k] = i < n && del[i] ? 1u : 0u;
+    s += v[k];
+  }
+  uint32_t e = block_exclusive_scan(s, wt, &tot) + sums[blockIdx.x];
+  for (int k = 0; k < per; ++k) {
+    const int64_t i = base + (int64_t)threadIdx.x * per + k;
+    if (i <= n) D[i] = e;
+    if (v[k] && i < nkeep) hole_pos[e] = (uint32_t)i;
+    e += v[k];
+  }
 }
 
-// Move the fillers of every plane of an array of element type T (rows
-// planes of stride n): filler i -> its hole, in each plane.
+// Move the fillers of every plane of every array (rows planes of stride n,
+// elements of 1, 4 or 8 bytes) in one launch: filler i -> its hole.
+struct FillArr {
+  void* base;
+  int rows, esize;
+};
+struct FillSet {
+  FillArr a[6];
+  int k;
+};
 template <typename T>
-__global__ void k_fill_holes(T* __restrict__ a, int rows, const uint8_t* __restrict__ del,
-                             const uint32_t* __restrict__ D,
-                             const uint32_t* __restrict__ hole_pos, int64_t n) {
+__device__ __forceinline__ void fill_planes(void* base, int rows, int64_t n, int64_t h, int64_t i) {
+  T* a = reinterpret_cast<T*>(base);
+  for (int r = 0; r < rows; ++r) a[r * n + h] = a[r * n + i];
+}
+__global__ void k_fill_all(const FillSet fs, const uint8_t* __restrict__ del,
+                           const uint32_t* __restrict__ D, const uint32_t* __restrict__ hole_pos,
+                           int64_t n) {
   const int64_t nkeep = n - (int64_t)D[n];
   const int64_t base = (int64_t)D[nkeep];
   for (int64_t i = nkeep + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -666,7 +711,17 @@ __global__ void k_fill_holes(T* __restrict__ a, int rows, const uint8_t* __restr
     if (del[i]) continue;
     const int64_t k = (i - nkeep) - ((int64_t)D[i] - base);  // filler rank
     const int64_t h = hole_pos[k];
-    for (int r = 0; r < rows; ++r) a[r * n + h] = a[r * n + i];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {  // unrolled: the set stays in the parameter space
+      if (q >= fs.k) break;
+      const FillArr& f = fs.a[q];
+      if (f.esize == 8)
+        fill_planes<uint64_t>(f.base, f.rows, n, h, i);
+      else if (f.esize == 4)
+        fill_planes<uint32_t>(f.base, f.rows, n, h, i);
+      else
+        fill_planes<uint8_t>(f.base, f.rows, n, h, i);
+    }
   }
 }
 
@@ -963,12 +1018,10 @@ cudaError_t move_row(part_ctx* c, const T* src, T* dst, int64_t len) {
   return cudaGetLastError();
 }
 
-// Fill the holes of every row, then move rows r >= 1 from stride n to stride
-// nnew (the deletion count stays on the device: D[n]).
+// Move rows r >= 1 of an array (its holes already filled) from stride n to
+// stride nnew (the deletion count stays on the device: D[n]).
 template <typename T>
-cudaError_t fill_rows(part_ctx* c, T* base, int rows, const uint8_t* del, int64_t n, int gb) {
-  k_fill_holes<T><<<gb, 256, 0, c->stream>>>(base, rows, del, c->keys[0], c->keys[1], n);
-  c->launches++;
+cudaError_t shrink_rows(part_ctx* c, T* base, int rows, int64_t n) {
   // Rows r >= 1 move from stride n to stride nnew: row r shifts down by
   // r (n - nnew) elements, in place, lowest row first (a row only overwrites
   // source rows already moved, and its own source as the move allows).
@@ -1053,32 +1106,49 @@ cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew_out) {
   const int64_t nblk = (m + kScanBlock - 1) / kScanBlock;
   uint32_t* D = c->keys[0];
   uint32_t* sums = c->vals[1];
-  k_del_flags<<<gb, 256, 0, s>>>(del, n, D);
-  k_scan_reduce<<<(unsigned)nblk, 256, 0, s>>>(D, m, sums);
-  k_scan_top<<<1, 256, 0, s>>>(sums, nblk);
-  k_scan_down<<<(unsigned)nblk, 256, 0, s>>>(D, m, sums);
-  k_hole_pos<<<gb, 256, 0, s>>>(del, D, n, c->keys[1]);
-  c->launches += 5;
-  // every array is filled and moved on the device (the kernels read the
-  // deletion count D[n] there); the host reads the count once, at the end
-  cudaError_t e = cudaSuccess;
+  k_del_reduce<<<(unsigned)nblk, 256, 0, s>>>(del, n, sums);
+  k_scan_top<<<1, 256, 0, s>>>(sums, nblk, sums + nblk);
+  k_del_down<<<(unsigned)nblk, 256, 0, s>>>(del, n, sums, sums + nblk, D, c->keys[1]);
+  c->launches += 3;
+  // every array is filled (one launch) and its rows moved on the device (the
+  // kernels read the deletion count D[n] there); the host reads the count
+  // once, at the end
+  FillSet fs{};
+  auto add = [&](void* p, int rows, int esize) {
+    if (p) fs.a[fs.k++] = FillArr{p, rows, esize};
+  };
   if (c->mode == PART_BORIS && c->prec == PART_FP64) {
-    if ((e = fill_rows<double>(c, (double*)c->x, 3, del, n, gb))) return e;
-    if ((e = fill_rows<double>(c, (double*)c->u, 3, del, n, gb))) return e;
-    if (c->w && (e = fill_rows<double>(c, (double*)c->w, 1, del, n, gb))) return e;
+    add(c->x, 3, 8);
+    add(c->u, 3, 8);
+    add(c->w, 1, 8);
   } else if (c->mode == PART_BORIS) {
-    if ((e = fill_rows<int32_t>(c, (int32_t*)c->x, 1, del, n, gb))) return e;
-    if ((e = fill_rows<float>(c, (float*)c->off, 3, del, n, gb))) return e;
-    if ((e = fill_rows<float>(c, (float*)c->u, 6, del, n, gb))) return e;
-    if (c->w && (e = fill_rows<float>(c, (float*)c->w, 1, del, n, gb))) return e;
+    add(c->x, 1, 4);
+    add(c->off, 3, 4);
+    add(c->u, 6, 4);
+    add(c->w, 1, 4);
   } else {
-    if ((e = fill_rows<double>(c, (double*)c->x, 3, del, n, gb))) return e;
-    if ((e = fill_rows<double>(c, c->chi, c->nbins, del, n, gb))) return e;
-    if ((e = fill_rows<double>(c, c->eng, c->nbins, del, n, gb))) return e;
-    if (c->n_old && (e = fill_rows<double>(c, c->n_old, 1, del, n, gb))) return e;
-    if (c->shk && (e = fill_rows<uint8_t>(c, c->shk, 1, del, n, gb))) return e;
+    add(c->x, 3, 8);
+    add(c->chi, c->nbins, 8);
+    add(c->eng, c->nbins, 8);
+    add(c->n_old, 1, 8);
+    add(c->shk, 1, 1);
   }
-  if (c->id && (e = fill_rows<uint64_t>(c, c->id, 1, del, n, gb))) return e;
+  add(c->id, 1, 8);
+  k_fill_all<<<gb, 256, 0, s>>>(fs, del, D, c->keys[1], n);
+  c->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (c->mode == PART_BORIS && c->prec == PART_FP64) {
+    if ((e = shrink_rows<double>(c, (double*)c->x, 3, n))) return e;
+    if ((e = shrink_rows<double>(c, (double*)c->u, 3, n))) return e;
+  } else if (c->mode == PART_BORIS) {
+    if ((e = shrink_rows<float>(c, (float*)c->off, 3, n))) return e;
+    if ((e = shrink_rows<float>(c, (float*)c->u, 6, n))) return e;
+  } else {
+    if ((e = shrink_rows<double>(c, (double*)c->x, 3, n))) return e;
+    if ((e = shrink_rows<double>(c, c->chi, c->nbins, n))) return e;
+    if ((e = shrink_rows<double>(c, c->eng, c->nbins, n))) return e;
+  }
   uint32_t ndel = 0;
   e = cudaMemcpyAsync(&ndel, D + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
