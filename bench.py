@@ -67,8 +67,8 @@ TRAFFIC_PER_PARTICLE_BRICK_F64 = 315.386624e6 / 2097152  # ncu dram r+w, 64^3 ca
 # rsqrt / reciprocal refinements more.
 FP64_OPS_PER_PSTEP_BRICK = {"dfma": 299, "dmul": 37, "dadd": 31}
 # Same for the mixed brick kernel, from an ncu capture of the 128^3 case
-# (1709.7 MB for 16,777,216 particles).
-TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1709.683968e6 / 16777216   # ncu dram r+w, 128^3 capture
+# (1709.8 MB for 16,777,216 particles).
+TRAFFIC_PER_PARTICLE_BRICK_MIXED = 1709.779712e6 / 16777216   # ncu dram r+w, 128^3 capture
 
 
 # Nominal HBM3e bandwidth of a B300 (GB/s): fractions against it are reported
