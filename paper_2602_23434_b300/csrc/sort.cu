@@ -991,15 +991,32 @@ __global__ void __launch_bounds__(kMoveT)
   move_row_body<T>(src, dst, len, flags, status);
 }
 
-// Row r of a compaction: from stride n to stride nnew = n - D[n], with D[n]
-// (the deletion count) read on the device, so the host need not wait for it.
+// Row r of a compaction, for up to three arrays of element type T in one
+// launch: from stride n to stride nnew = n - D[n], with D[n] (the deletion
+// count) read on the device, so the host need not wait for it.  The arrays'
+// rows move one after the other, each with its own ticket counter and flags
+// (at flags + a * fstride); arrays with rows <= r are skipped.
+template <typename T>
+struct MoveRows {
+  T* base[3];
+  int rows[3];
+  int k;
+};
 template <typename T>
 __global__ void __launch_bounds__(kMoveT)
-    k_move_row_compact(T* base, int64_t n, int64_t r, const uint32_t* __restrict__ dn,
-                       uint32_t* flags, int* status) {
+    k_move_rows_compact(const MoveRows<T> m, int64_t n, int64_t r,
+                        const uint32_t* __restrict__ dn, uint32_t* flags, int64_t fstride,
+                        int* status) {
   const int64_t nnew = n - (int64_t)*dn;
   if (nnew == n) return;
-  move_row_body<T>(base + r * n, base + r * nnew, nnew, flags, status);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= m.k) break;
+    if (r < m.rows[a])
+      move_row_body<T>(m.base[a] + r * n, m.base[a] + r * nnew, nnew, flags + a * fstride,
+                       status);
+    __syncthreads();  // the body's shared ticket slot is reused by the next array
+  }
 }
 
 // Move len elements from src to dst in the stream, overlap allowed.
@@ -1018,21 +1035,26 @@ cudaError_t move_row(part_ctx* c, const T* src, T* dst, int64_t len) {
   return cudaGetLastError();
 }
 
-// Move rows r >= 1 of an array (its holes already filled) from stride n to
-// stride nnew (the deletion count stays on the device: D[n]).
+// Move rows r >= 1 of up to three arrays of one element type (their holes
+// already filled) from stride n to stride nnew (the deletion count stays on
+// the device: D[n]); row r of every array in one launch.
 template <typename T>
-cudaError_t shrink_rows(part_ctx* c, T* base, int rows, int64_t n) {
+cudaError_t shrink_rows(part_ctx* c, const MoveRows<T>& m, int64_t n) {
   // Rows r >= 1 move from stride n to stride nnew: row r shifts down by
   // r (n - nnew) elements, in place, lowest row first (a row only overwrites
   // source rows already moved, and its own source as the move allows).
   const int64_t nblk = (n + kMoveB - 1) / kMoveB;
-  const int64_t grid = std::min<int64_t>(nblk, (int64_t)c->sms * 8);
-  uint32_t* flags = (uint32_t*)c->tmp;  // (1 + nblk) words; tmp holds 8 * capacity bytes
+  const int64_t grid = std::min<int64_t>(m.k * nblk, (int64_t)c->sms * 8);
+  const int64_t fstride = 1 + nblk;
+  // k (1 + nblk) words; tmp holds 8 * capacity bytes
+  uint32_t* flags = (uint32_t*)c->tmp;
+  int rows = 0;
+  for (int a = 0; a < m.k; ++a) rows = m.rows[a] > rows ? m.rows[a] : rows;
   for (int r = 1; r < rows; ++r) {
-    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * (1 + nblk), c->stream);
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * m.k * fstride, c->stream);
     if (e != cudaSuccess) return e;
-    k_move_row_compact<T><<<(unsigned)grid, kMoveT, 0, c->stream>>>(base, n, r, c->keys[0] + n,
-                                                                    flags, c->status);
+    k_move_rows_compact<T><<<(unsigned)grid, kMoveT, 0, c->stream>>>(
+        m, n, r, c->keys[0] + n, flags, fstride, c->status);
     c->launches++;
   }
   return cudaGetLastError();
@@ -1139,15 +1161,14 @@ cudaError_t launch_compact(part_ctx* c, const uint8_t* del, int64_t* nnew_out) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (c->mode == PART_BORIS && c->prec == PART_FP64) {
-    if ((e = shrink_rows<double>(c, (double*)c->x, 3, n))) return e;
-    if ((e = shrink_rows<double>(c, (double*)c->u, 3, n))) return e;
+    const MoveRows<double> m{{(double*)c->x, (double*)c->u, nullptr}, {3, 3, 0}, 2};
+    if ((e = shrink_rows<double>(c, m, n))) return e;
   } else if (c->mode == PART_BORIS) {
-    if ((e = shrink_rows<float>(c, (float*)c->off, 3, n))) return e;
-    if ((e = shrink_rows<float>(c, (float*)c->u, 6, n))) return e;
+    const MoveRows<float> m{{(float*)c->off, (float*)c->u, nullptr}, {3, 6, 0}, 2};
+    if ((e = shrink_rows<float>(c, m, n))) return e;
   } else {
-    if ((e = shrink_rows<double>(c, (double*)c->x, 3, n))) return e;
-    if ((e = shrink_rows<double>(c, c->chi, c->nbins, n))) return e;
-    if ((e = shrink_rows<double>(c, c->eng, c->nbins, n))) return e;
+    const MoveRows<double> m{{(double*)c->x, c->chi, c->eng}, {3, c->nbins, c->nbins}, 3};
+    if ((e = shrink_rows<double>(c, m, n))) return e;
   }
   uint32_t ndel = 0;
   e = cudaMemcpyAsync(&ndel, D + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
