@@ -2,11 +2,13 @@
 //
 // Brick kernel (sorted particles, one CTA per 8x8x8 / 16x16 cell brick;
 // with the deposit, warp-specialised: 8 push warps, 8 deposit warps):
-//   1. one thread issues a 4-D TMA copy of the brick's haloed field box
-//      (all components) into shared memory; cell_start of the brick is read;
-//   2. the CTA walks the brick's particles in chunks of blockDim: TSC/CIC
-//      weights, gather from shared memory, Boris kick, drift, periodic wrap,
-//      coalesced SoA loads/stores;
+//   1. CIC: one thread issues a 4-D TMA copy of the brick's haloed field box
+//      (all components) into shared memory.  TSC: nothing is staged; each
+//      stencil row of each component is one 32-byte record (q0, q1, q2) of
+//      the fields' x quadratics, read through L1, and the row's three
+//      weighted cells are q0 + d (q1 + d q2).  cell_start of the brick is read;
+//   2. the CTA walks the brick's particles in chunks of blockDim: weights,
+//      gather, Boris kick, drift, periodic wrap, coalesced SoA loads/stores;
 //   3. deposit (optional): each particle leaves its weights and force in
 //      shared memory; then warp w takes the chunk's source cells with x index
 //      w mod 8, one lane per stencil offset: every lane loops over the same
